@@ -1,0 +1,234 @@
+/*
+ * pg.h -- C ABI of the GB300 guiding-distribution library (libpg.so).
+ *
+ * The library computes the guiding hot path of Photon-Driven Neural Path
+ * Guiding (Zhu et al., ACM TOG 2021): photons -> adaptive hierarchical grid ->
+ * per-leaf cylindrical direction histograms -> CNN reconstruction -> per-leaf
+ * CDFs -> guided direction sampling and pdf evaluation at path vertices.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns a pg_status; nothing throws across the ABI.
+ *  - Work is asynchronous on the context's CUDA stream (pg_create).  A call
+ *    returns once its work is enqueued; results are ready after pg_sync() or
+ *    any later stream-ordered operation.  The exceptions are pg_build_grid
+ *    (it reads the leaf counts back, see there) and pg_export/pg_info.
+ *  - Array arguments named d_* may be DEVICE pointers (used in place) or HOST
+ *    pointers (pinned or pageable; the library stages them through device
+ *    memory on the context stream, copies inside the call).  They are owned
+ *    by the caller and must stay valid until the call's work has finished.
+ *  - Handles (pg_grid, pg_hist, pg_net, pg_map, pg_tables) are owned by the
+ *    library, live in device memory until pg_free(), and may be reused by
+ *    any number of later calls on the same context.
+ *  - Data-dependent errors found by kernels (non-finite input, fixed-point
+ *    overflow) are posted to a per-context status word; pg_sync() returns and
+ *    clears it.
+ *  - Allocations are charged to the context's HBM budget; a call that would
+ *    exceed it fails with PG_ERR_OOM and allocates nothing.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PG_OK = 0,
+  PG_ERR_INVALID_ARG = 1,    /* null pointer, bad size or inconsistent handles */
+  PG_ERR_NOT_DEVICE_PTR = 2, /* a pointer the CUDA runtime cannot classify */
+  PG_ERR_OOM = 3,            /* device allocation failed or HBM budget exceeded */
+  PG_ERR_OVERFLOW = 4,       /* a photon's fixed-point power exceeds (2^63-1)/n */
+  PG_ERR_NOT_POW2 = 5,       /* histogram H or W not a supported power of two */
+  PG_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  PG_ERR_CUDA = 7,           /* a CUDA runtime call failed */
+  PG_ERR_INVALID_INPUT = 8,  /* non-finite position/direction or negative power */
+  PG_ERR_UNSUPPORTED = 9     /* configuration outside what the kernels support */
+} pg_status;
+
+/* Arithmetic of the reconstruction CNN's convolutions (accumulation is FP32
+ * in every case). */
+typedef enum { PG_FP32 = 0, PG_BF16 = 1, PG_FP8_E4M3 = 2 } pg_precision;
+
+/* One photon record, 32 bytes: hit position, unit incident direction, power
+ * (the flux Delta Phi_p carried by the photon, Eq. "photon" of Sec. 4). */
+typedef struct {
+  float px, py, pz;
+  float dx, dy, dz;
+  float power;
+  float pad;
+} pg_photon;
+
+/* Spatial grid parameters (Sec. 7.1).  The domain [lo, hi) is cut into a
+ * regular 2^min_depth grid per axis (the "initial regular grid"); a cell
+ * holding more than split_threshold photons is split into its 8 children
+ * until max_depth.  0 <= min_depth <= max_depth <= 16, min_depth <= 6. */
+typedef struct {
+  float lo[3], hi[3];
+  int32_t max_depth;
+  int32_t min_depth;
+  uint32_t split_threshold;
+} pg_grid_params;
+
+typedef struct pg_ctx pg_ctx;
+typedef struct pg_grid pg_grid;
+typedef struct pg_hist pg_hist;
+typedef struct pg_net pg_net;
+typedef struct pg_map pg_map;
+typedef struct pg_tables pg_tables;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; 0 = the legacy default stream).  hbm_budget caps the
+ * bytes of all live handles and call scratch (0 = no cap). */
+pg_status pg_create(pg_ctx **ctx, void *cuda_stream, size_t hbm_budget);
+pg_status pg_destroy(pg_ctx *ctx);
+/* Rebinds the context to another stream (later calls enqueue there). */
+pg_status pg_set_stream(pg_ctx *ctx, void *cuda_stream);
+/* Waits for the context stream, then returns (and clears) the first error
+ * any kernel posted since the last pg_sync. */
+pg_status pg_sync(pg_ctx *ctx);
+/* Bytes currently charged to the context's budget. */
+pg_status pg_bytes_in_use(const pg_ctx *ctx, uint64_t *bytes);
+
+/* ---- a1-a4: grid ------------------------------------------------------- */
+
+/* Voxel location and adaptive subdivision (Algorithm 1 "Locate voxel j" and
+ * "Subdivide voxel j"; Sec. 7.1 "Voxel subdivision"), octree form:
+ *   cell index per axis  q = clamp(floor(fl32(fl32(x - lo) * s)), 0, 2^D-1),
+ *                        s = fl32(2^D / (hi - lo)) computed in double;
+ *   Morton code          bits (3b, 3b+1, 3b+2) = bit b of (qx, qy, qz);
+ *   photons are stably sorted by code; from depth min_depth down, a cell
+ *   with count > split_threshold and depth < max_depth is replaced by its 8
+ *   children (empty ones kept), so the leaves partition [lo, hi).
+ * d_photons: n records (device or host).  On success *out holds, in device
+ * memory: the Morton-ordered leaf table (start code at depth max_depth,
+ * depth, photon range in sorted order), the sort permutation (sorted slot ->
+ * original index), leaf_of (original index -> leaf) and the active-leaf list
+ * (leaves with >= 1 photon, in leaf order) that owns a map slot.  The call
+ * synchronises the stream once to learn the leaf count.  n < 2^31. */
+pg_status pg_build_grid(pg_ctx *ctx, const pg_photon *d_photons, uint64_t n,
+                        const pg_grid_params *params, pg_grid **out);
+
+/* ---- a5: splat --------------------------------------------------------- */
+
+/* Photon energy and count maps, Eq. (photon) and the input buffers of
+ * Sec. 5: for every active leaf and bin k = row*W + col,
+ *   pow_cur[k]  = sum of round_half_even(power * 2^frac_bits) (uint64),
+ *   cnt_cur[k]  = number of photons,
+ *   pow_prev/cnt_prev = the same over photons with original index < n_prev.
+ * The direction bin: row = clamp(floor(dz * H/2) + H/2, 0, H-1); column =
+ * the sector of phi = atan2(dy, dx) in [0, 2 pi) in W equal sectors, decided
+ * exactly against boundary rays (float(cos 2 pi j/W), float(sin 2 pi j/W)),
+ * exact on the axes; dx = dy = 0 gives column 0.  H, W powers of two,
+ * 4 <= H, W <= 256, H*W <= 16384.  d_photons must be the array the grid was
+ * built from.  Each photon's fixed-point power must be <= (2^63-1)/n
+ * (else PG_ERR_OVERFLOW via pg_sync), so no sum can overflow. */
+pg_status pg_splat_photons(pg_ctx *ctx, const pg_grid *grid, const pg_photon *d_photons,
+                           uint64_t n, uint64_t n_prev, int H, int W, int frac_bits,
+                           pg_hist **out);
+
+/* ---- a6-a7: reconstruction CNN ----------------------------------------- */
+
+/* Loads a network from a host blob (little endian): u32 magic 0x314E4750,
+ * u32 arch (0 = three 3x3 convs ELU/ELU/softplus, 1 = 4-level U-Net),
+ * u32 in_channels (5), u32 n_layers, u32 widths[4], u64 seed; then per layer
+ * u32 {cout, cin, k, stride, act, 0}, float32 weights [cout][k][k][cin],
+ * float32 bias[cout].  The blob is copied; the caller keeps ownership. */
+pg_status pg_net_load(pg_ctx *ctx, const void *host_blob, size_t bytes, pg_net **out);
+
+/* Sampling-map reconstruction (Sec. 5, Sec. 7.2): for every active leaf the
+ * 5-channel input (S_t = Phi HW / sum Phi, S_{t-1} likewise, log(1 + count),
+ * log(1 + count_prev), count > 0) is run through the network; *out holds the
+ * non-negative softplus output y [A][H][W] (float32).  Convolutions run in
+ * `precision` with FP32 accumulation. */
+pg_status pg_reconstruct(pg_ctx *ctx, const pg_hist *hist, const pg_net *net,
+                         pg_precision precision, pg_map **out);
+
+/* Wraps caller-provided maps y [n_maps][H][W] (float32, >= 0) as a pg_map
+ * (copied), so tables can be built from maps computed elsewhere. */
+pg_status pg_map_import(pg_ctx *ctx, const float *d_y, uint64_t n_maps, int H, int W,
+                        pg_map **out);
+
+/* ---- a8-a9: normalisation and CDFs ------------------------------------- */
+
+/* Sampling map and CDFs (Eq. energy_target; Sec. 7.3, a CDF "like sampling
+ * an environment map"): P = y / sum y per map; marginal CDF over rows
+ * Fz[i] = sum_{i'<=i} m_i' / sum m with m_i = sum_j y_ij; conditional CDF
+ * Fphi[i][j] = sum_{j'<=j} y_ij' / m_i ((j+1)/W for an empty row).  Sums and
+ * prefixes in FP64, stored float32 with the last entry of every CDF exactly
+ * 1.  A map with sum 0 is marked invalid (uniform fallback when sampled). */
+pg_status pg_build_cdf(pg_ctx *ctx, const pg_map *map, pg_tables **out);
+
+/* ---- a10-a12: guided sampling and pdf evaluation ----------------------- */
+
+/* For each query t < q at position d_pos[3t..3t+2]: leaf = last leaf whose
+ * start code <= Morton code of the position (the a1 rule); four uniforms
+ * u_k = (r_k >> 8) 2^-24 from Philox4x32-10 (key = seed, counter =
+ * (t mod 2^32, t >> 32, stream_id, 0)); row = first i with u0 < Fz[i],
+ * column = first j with u1 < Fphi[i][j]; z = -1 + 2 (i + u2)/H,
+ * phi = 2 pi (j + u3)/W; pdf = P_ij * H W / (4 pi).  A leaf without a
+ * valid map falls back to uniform sphere sampling (z = 1 - 2 u0,
+ * phi = 2 pi u1, pdf = 1/(4 pi)) and its d_leaf entry has bit 31 set.
+ * Outputs (caller-owned): d_dir [q][3] float32, d_pdf [q] float32, d_leaf [q]
+ * uint32, d_bin [q] uint32 (row*W + col, 0xFFFFFFFF for the fallback; may be
+ * NULL). */
+pg_status pg_sample_dirs(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables,
+                         const float *d_pos, uint64_t q, uint64_t seed, uint32_t stream_id,
+                         float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin);
+
+/* p_guide of direction d_dir[t] at position d_pos[t] (the guide term of
+ * Eq. target_mis / mis_coef): P_k * H W / (4 pi) for the bin k of the
+ * direction (the pg_splat_photons bin rule) in the map of the position's
+ * leaf, 1/(4 pi) for a leaf without a valid map.  d_pdf [q] float32. */
+pg_status pg_eval_pdf(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables,
+                      const float *d_pos, const float *d_dir, uint64_t q, float *d_pdf);
+
+/* ---- inspection -------------------------------------------------------- */
+
+enum {
+  PG_INFO_N_PHOTONS = 1, PG_INFO_N_LEAVES = 2, PG_INFO_N_ACTIVE = 3, PG_INFO_H = 4,
+  PG_INFO_W = 5, PG_INFO_BYTES = 6, PG_INFO_MAX_DEPTH = 7
+};
+pg_status pg_info(const void *handle, int what, uint64_t *value);
+
+/* Copies one array of a handle to dst (host or device), synchronously.
+ * `bytes` must equal the array's size. */
+enum {
+  PG_GRID_CODES = 100,      /* uint64 [n]  Morton code per original photon */
+  PG_GRID_PERM = 101,       /* uint32 [n]  sorted slot -> original index */
+  PG_GRID_LEAF_OF = 102,    /* uint32 [n]  original index -> leaf */
+  PG_GRID_LEAF_CODE = 103,  /* uint64 [L]  start code (depth max_depth) */
+  PG_GRID_LEAF_DEPTH = 104, /* int32  [L] */
+  PG_GRID_LEAF_BEGIN = 105, /* uint32 [L]  first sorted slot */
+  PG_GRID_LEAF_END = 106,   /* uint32 [L]  one past the last sorted slot */
+  PG_GRID_ACTIVE = 107,     /* uint32 [A]  active leaves, ascending */
+  PG_GRID_SLOT_OF_LEAF = 108, /* int32 [L] map slot or -1 */
+  PG_HIST_POW_CUR = 200,    /* uint64 [A][H*W] */
+  PG_HIST_CNT_CUR = 201,    /* uint32 [A][H*W] */
+  PG_HIST_POW_PREV = 202,   /* uint64 [A][H*W] */
+  PG_HIST_CNT_PREV = 203,   /* uint32 [A][H*W] */
+  PG_MAP_Y = 300,           /* float  [A][H][W] */
+  PG_TAB_P = 400,           /* float  [A][H*W] */
+  PG_TAB_CDF_PHI = 401,     /* float  [A][H][W] */
+  PG_TAB_CDF_Z = 402,       /* float  [A][H] */
+  PG_TAB_VALID = 403        /* uint8  [A] */
+};
+pg_status pg_export(pg_ctx *ctx, const void *handle, int what, void *dst, size_t bytes);
+
+/* Releases any handle (grid, hist, net, map, tables); NULL is a no-op.  The
+ * memory is returned in stream order on the stream of the context that made
+ * the handle, which must still exist. */
+void pg_free(void *handle);
+
+const char *pg_status_string(pg_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PG_H */

@@ -1,0 +1,385 @@
+"""Plain FP64 CPU oracle of the guiding-distribution hot path (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import this module.  It
+shares no code with the CUDA library (``paper_2010_01775_gb300``) and imports
+nothing from it; the two meet only through the seeded inputs of
+``paper_2010_01775_gb300.synth``.
+
+The integer-heavy steps (voxel location, grid, binning, splat, convolution
+loops, Philox, sampling) are plain C in ``pg_oracle.c``; this module loads it
+with ctypes and writes the remaining steps (activations, U-Net wiring,
+normalisation, CDFs) as direct NumPy FP64 expressions.  Each function cites the
+passage of the paper it follows.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(closed forms, brute force, library routines, invariants) except the CNN
+*weights and architecture*, which the paper does not print: the network
+definition is this project's reading (architecture in ``net_layers``), so CNN
+outputs are pinned only as convolution/activation arithmetic (against
+``torch.nn.functional.conv2d`` in float64 and closed-form special cases), not
+against any number from the paper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+ERR_OVERFLOW = 4
+ERR_INVALID_INPUT = 8
+
+ARCH_TINY3 = 0
+ARCH_UNET4 = 1
+ACT_NONE, ACT_ELU, ACT_SOFTPLUS = 0, 1, 2
+NET_MAGIC = 0x314E4750
+
+
+def build(force: bool = False) -> str:
+    """Compile pg_oracle.c with gcc (IEEE, no FMA contraction, no fast math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        P = ctypes.c_void_p
+        i64, i32, u32, u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+        L.or_morton3.restype = u64
+        L.or_morton3.argtypes = [u32, u32, u32, i32]
+        L.or_morton_codes.argtypes = [P, i64, i64, P, P, i32, P]
+        L.or_build_grid.restype = i64
+        L.or_build_grid.argtypes = [P, i64, P, P, i32, i32, u32, P, P, P, i64, P, P, P, P]
+        L.or_phi_table.argtypes = [i32, P, P]
+        L.or_dir_bins.argtypes = [P, i64, i64, i32, i32, P, P]
+        L.or_splat.argtypes = [P, i64, i64, P, i64, P, P, i32, i32, i32, P, P, P, P]
+        L.or_assemble_inputs.argtypes = [i64, i64, P, P, P, P, P]
+        L.or_conv2d.argtypes = [P, i64, i32, i32, i32, P, P, i32, i32, i32, P]
+        L.or_philox4x32_10.argtypes = [P, P, P]
+        L.or_sample.argtypes = [P, i64, P, P, i32, P, i64, P, i32, i32, P, P, P, P, u64, u32,
+                                P, P, P, P]
+        L.or_eval_pdf.argtypes = [P, P, i64, P, P, i32, P, i64, P, i32, i32, P, P, P]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+
+
+# --------------------------------------------------------------------------
+# a1-a4: voxel location and the adaptive hierarchical grid (Sec. 7.1,
+# Algorithm 1 "Locate voxel j" and "Subdivide voxel j").
+# --------------------------------------------------------------------------
+def morton_codes(pos, lo, hi, D):
+    pos = _f32(pos)
+    n = pos.shape[0]
+    codes = np.zeros(n, np.uint64)
+    st = lib().or_morton_codes(_p(pos), pos.shape[1], n, _p(_f32(lo)), _p(_f32(hi)), D, _p(codes))
+    return codes, st
+
+
+def build_grid(photons, lo, hi, D, min_depth, thr):
+    """Octree reading of the voxel subdivision rule (split while count > thr and
+    depth < D; every child kept).  Returns a dict with per-photon codes, the
+    stable sort permutation, leaf_of (per original photon) and the Morton-ordered
+    leaf table (start code at full depth, depth, photon range)."""
+    ph = _f32(photons)
+    n = ph.shape[0]
+    codes = np.zeros(n, np.uint64)
+    perm = np.zeros(n, np.uint32)
+    leaf_of = np.zeros(n, np.uint32)
+    cap = max(1024, 8 ** min_depth + 64)
+    while True:
+        lc = np.zeros(cap, np.uint64)
+        ld = np.zeros(cap, np.int32)
+        lb = np.zeros(cap, np.uint32)
+        le = np.zeros(cap, np.uint32)
+        L = lib().or_build_grid(_p(ph), n, _p(_f32(lo)), _p(_f32(hi)), D, min_depth, thr, _p(codes),
+                                _p(perm), _p(leaf_of), cap, _p(lc), _p(ld), _p(lb), _p(le))
+        if L < 0:
+            raise ValueError(f"oracle grid status {-L}")
+        if L <= cap:
+            break
+        cap = int(L)
+    return dict(codes=codes, perm=perm, leaf_of=leaf_of, leaf_code=lc[:L].copy(),
+                leaf_depth=ld[:L].copy(), leaf_begin=lb[:L].copy(), leaf_end=le[:L].copy(),
+                L=int(L), D=D, lo=_f32(lo), hi=_f32(hi), n=n)
+
+
+def active_leaves(grid):
+    """Leaves that received photons get a map (Sec. 7.2: maps are reconstructed
+    for voxels that have photons); slot_of_leaf is -1 for the others."""
+    cnt = grid["leaf_end"].astype(np.int64) - grid["leaf_begin"].astype(np.int64)
+    act = np.nonzero(cnt > 0)[0].astype(np.uint32)
+    slot = np.full(grid["L"], -1, np.int32)
+    slot[act] = np.arange(act.size, dtype=np.int32)
+    return act, slot
+
+
+# --------------------------------------------------------------------------
+# Direction bins (Sec. 4, cylindrical map (z, phi)).
+# --------------------------------------------------------------------------
+def phi_table(W):
+    c = np.zeros(W, np.float32)
+    s = np.zeros(W, np.float32)
+    lib().or_phi_table(W, _p(c), _p(s))
+    return c, s
+
+
+def dir_bins(dirs, H, W):
+    d = _f32(dirs)
+    n = d.shape[0]
+    rows = np.zeros(n, np.int32)
+    cols = np.zeros(n, np.int32)
+    st = lib().or_dir_bins(_p(d), d.shape[1], n, H, W, _p(rows), _p(cols))
+    return rows, cols, st
+
+
+# --------------------------------------------------------------------------
+# a5: photon energy and count maps, Eq. (photon), Sec. 5 input buffers.
+# --------------------------------------------------------------------------
+def splat(photons, grid, n_prev, H, W, F=32):
+    ph = _f32(photons)
+    L, HW = grid["L"], H * W
+    pc = np.zeros((L, HW), np.uint64)
+    pp = np.zeros((L, HW), np.uint64)
+    cc = np.zeros((L, HW), np.uint32)
+    cp = np.zeros((L, HW), np.uint32)
+    st = lib().or_splat(_p(ph), ph.shape[0], n_prev, _p(grid["perm"]), L, _p(grid["leaf_begin"]),
+                        _p(grid["leaf_end"]), H, W, F, _p(pc), _p(cc), _p(pp), _p(cp))
+    return dict(pow_cur=pc, cnt_cur=cc, pow_prev=pp, cnt_prev=cp, H=H, W=W, status=st)
+
+
+def hist_for_active(hist, act):
+    return {k: (v[act] if isinstance(v, np.ndarray) else v) for k, v in hist.items()}
+
+
+# --------------------------------------------------------------------------
+# a6-a7: network input and the reconstruction CNN (Sec. 5, Sec. 5.1).
+# --------------------------------------------------------------------------
+def assemble_inputs(hist):
+    """5-channel input [A][H][W][5] (S_t, S_{t-1}, P_t, P_{t-1}, B), FP64."""
+    A, HW = hist["pow_cur"].shape
+    x = np.zeros((A, HW, 5), np.float64)
+    pc = np.ascontiguousarray(hist["pow_cur"])
+    pp = np.ascontiguousarray(hist["pow_prev"])
+    cc = np.ascontiguousarray(hist["cnt_cur"])
+    cp = np.ascontiguousarray(hist["cnt_prev"])
+    lib().or_assemble_inputs(A, HW, _p(pc), _p(cc), _p(pp), _p(cp), _p(x))
+    return x.reshape(A, hist["H"], hist["W"], 5)
+
+
+def parse_net(blob: bytes):
+    """Layer list [(cout, cin, k, stride, act, w[cout][k][k][cin], b[cout])]."""
+    magic, arch, cin0, nl, w0, w1, w2, w3, seed = struct.unpack_from("<IIII4IQ", blob, 0)
+    if magic != NET_MAGIC:
+        raise ValueError("bad net blob")
+    off = struct.calcsize("<IIII4IQ")
+    layers = []
+    for _ in range(nl):
+        cout, cin, k, stride, act, _z = struct.unpack_from("<6I", blob, off)
+        off += 24
+        w = np.frombuffer(blob, np.float32, cout * k * k * cin, off).reshape(cout, k, k, cin)
+        off += 4 * w.size
+        b = np.frombuffer(blob, np.float32, cout, off)
+        off += 4 * cout
+        layers.append((cout, cin, k, stride, act, np.ascontiguousarray(w), np.ascontiguousarray(b)))
+    return dict(arch=arch, widths=(w0, w1, w2, w3), layers=layers, seed=seed)
+
+
+def conv2d(x, w, b, stride):
+    """One conv layer, 'same' zero padding, channel-last FP64 (plain loops in C)."""
+    x = np.ascontiguousarray(x, np.float64)
+    A, Hin, Win, Cin = x.shape
+    cout, k, _, cin = w.shape
+    assert cin == Cin
+    out = np.zeros((A, Hin // stride, Win // stride, cout), np.float64)
+    lib().or_conv2d(_p(x), A, Hin, Win, Cin, _p(_f32(w)), _p(_f32(b)), cout, k, stride, _p(out))
+    return out
+
+
+def elu(x):
+    """ELU with alpha = 1 (the activation of Sec. 5.1 / the network figure)."""
+    return np.where(x > 0, x, np.expm1(np.minimum(x, 0.0)))
+
+
+def softplus(x):
+    """log(1 + e^x), evaluated stably as max(x, 0) + log1p(e^-|x|)."""
+    return np.maximum(x, 0.0) + np.log1p(np.exp(-np.abs(x)))
+
+
+def _act(x, act):
+    if act == ACT_ELU:
+        return elu(x)
+    if act == ACT_SOFTPLUS:
+        return softplus(x)
+    return x
+
+
+def upsample2(x):
+    """Nearest-neighbour x2 upsampling of [A][h][w][C]."""
+    return np.repeat(np.repeat(x, 2, axis=1), 2, axis=2)
+
+
+def cnn_forward(x, net):
+    """Reconstructed map y [A][H][W] (softplus output, before normalisation).
+
+    Tiny net: three 3x3 convs (ELU, ELU, softplus).  U-Net: two 3x3 convs per
+    level (the first of levels 1-3 with stride 2), decoder levels upsample the
+    deeper output (nearest x2), concatenate [upsampled, skip] and apply two
+    3x3 convs, then a 1x1 head with softplus."""
+    layers = net["layers"]
+    if net["arch"] == ARCH_TINY3:
+        h = x
+        for cout, cin, k, stride, act, w, b in layers:
+            h = _act(conv2d(h, w, b, stride), act)
+        return h[..., 0]
+    assert net["arch"] == ARCH_UNET4 and len(layers) == 15
+
+    def run(h, i):
+        cout, cin, k, stride, act, w, b = layers[i]
+        return _act(conv2d(h, w, b, stride), act)
+
+    e0 = run(run(x, 0), 1)
+    e1 = run(run(e0, 2), 3)
+    e2 = run(run(e1, 4), 5)
+    e3 = run(run(e2, 6), 7)
+    d2 = run(run(np.concatenate([upsample2(e3), e2], axis=3), 8), 9)
+    d1 = run(run(np.concatenate([upsample2(d2), e1], axis=3), 10), 11)
+    d0 = run(run(np.concatenate([upsample2(d1), e0], axis=3), 12), 13)
+    return run(d0, 14)[..., 0]
+
+
+# --------------------------------------------------------------------------
+# a8-a9: sampling map and its CDFs (Eq. energy_target; Sec. 7.3 "CDF built
+# via a cumulative sum over pixels, like sampling an environment map").
+# --------------------------------------------------------------------------
+def normalise(y):
+    """P_k = y_k / sum_k y (FP64).  A map whose sum is zero is invalid."""
+    y = np.asarray(y, np.float64)
+    A = y.shape[0]
+    flat = y.reshape(A, -1)
+    tot = flat.sum(axis=1)
+    valid = tot > 0
+    P = np.zeros_like(flat)
+    P[valid] = flat[valid] / tot[valid, None]
+    return P.reshape(y.shape), valid.astype(np.uint8)
+
+
+def build_cdf(P):
+    """Marginal CDF over rows and conditional CDF along each row (FP64).
+
+    m_i = sum_j P_ij, Fz[i] = sum_{i'<=i} m_i' / sum m, Fphi[i][j] =
+    sum_{j'<=j} P_ij' / m_i (a zero row gets the uniform (j+1)/W)."""
+    A, H, W = P.shape
+    m = P.sum(axis=2)
+    tot = m.sum(axis=1, keepdims=True)
+    Fz = np.cumsum(m, axis=1) / np.where(tot > 0, tot, 1.0)
+    rowc = np.cumsum(P, axis=2)
+    uni = np.broadcast_to((np.arange(W) + 1.0) / W, P.shape)
+    Fphi = np.where(m[:, :, None] > 0, rowc / np.where(m > 0, m, 1.0)[:, :, None], uni)
+    return Fz, Fphi
+
+
+def decision_tables(Fz, Fphi):
+    """The FP32 tables the sampling decision is taken on (last entry 1)."""
+    fz = Fz.astype(np.float32)
+    fp = Fphi.astype(np.float32)
+    fz[:, -1] = 1.0
+    fp[:, :, -1] = 1.0
+    return np.ascontiguousarray(fz), np.ascontiguousarray(fp)
+
+
+def tables_from_map(y):
+    P, valid = normalise(y)
+    Fz, Fphi = build_cdf(P)
+    fz, fp = decision_tables(Fz, Fphi)
+    return dict(P=np.ascontiguousarray(P), valid=valid, Fz=Fz, Fphi=Fphi, fz=fz, fphi=fp,
+                H=P.shape[1], W=P.shape[2])
+
+
+# --------------------------------------------------------------------------
+# a10-a12: guided sampling and pdf evaluation (Sec. 7.3; Eq. target_mis).
+# --------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    ctr = np.ascontiguousarray(np.asarray(ctr, np.uint32))
+    key = np.ascontiguousarray(np.asarray(key, np.uint32))
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_p(ctr), _p(key), _p(out))
+    return out
+
+
+def sample(grid, slot_of_leaf, tables, pos, seed, stream=0):
+    pos = _f32(pos)
+    q = pos.shape[0]
+    dirs = np.zeros((q, 3), np.float64)
+    pdf = np.zeros(q, np.float64)
+    leaf = np.zeros(q, np.uint32)
+    binv = np.zeros(q, np.uint32)
+    slot = np.ascontiguousarray(slot_of_leaf, np.int32)
+    lib().or_sample(_p(pos), q, _p(grid["lo"]), _p(grid["hi"]), grid["D"], _p(grid["leaf_code"]),
+                    grid["L"], _p(slot), tables["H"], tables["W"], _p(tables["P"]), _p(tables["fz"]),
+                    _p(tables["fphi"]), _p(tables["valid"]), seed, stream, _p(dirs), _p(pdf),
+                    _p(leaf), _p(binv))
+    return dict(dir=dirs, pdf=pdf, leaf=leaf, bin=binv)
+
+
+def eval_pdf(grid, slot_of_leaf, tables, pos, dirs):
+    pos = _f32(pos)
+    d = _f32(dirs)
+    q = pos.shape[0]
+    pdf = np.zeros(q, np.float64)
+    slot = np.ascontiguousarray(slot_of_leaf, np.int32)
+    lib().or_eval_pdf(_p(pos), _p(d), q, _p(grid["lo"]), _p(grid["hi"]), grid["D"],
+                      _p(grid["leaf_code"]), grid["L"], _p(slot), tables["H"], tables["W"],
+                      _p(tables["P"]), _p(tables["valid"]), _p(pdf))
+    return pdf
+
+
+# --------------------------------------------------------------------------
+# The whole path, for smoke checks and the CPU baseline.
+# --------------------------------------------------------------------------
+def run_path(photons, n_prev, lo, hi, D, min_depth, thr, H, W, blob, pos, dirs, seed, F=32,
+             max_leaves=None):
+    """Grid -> splat -> CNN -> normalise/CDF -> sample + eval.  With
+    ``max_leaves`` only the first that many active leaves are reconstructed
+    (the others keep no map), to bound the FP64 CNN on large workloads."""
+    g = build_grid(photons, lo, hi, D, min_depth, thr)
+    act, slot = active_leaves(g)
+    if max_leaves is not None and act.size > max_leaves:
+        keep = act[:max_leaves]
+        slot = np.full(g["L"], -1, np.int32)
+        slot[keep] = np.arange(keep.size, dtype=np.int32)
+        act = keep
+    h = splat(photons, g, n_prev, H, W, F)
+    ha = hist_for_active(h, act)
+    x = assemble_inputs(ha)
+    y = cnn_forward(x, parse_net(blob))
+    t = tables_from_map(y)
+    s = sample(g, slot, t, pos, seed)
+    e = eval_pdf(g, slot, t, pos, dirs)
+    return dict(grid=g, act=act, slot=slot, hist=h, x=x, y=y, tables=t, sample=s, eval=e)

@@ -1,0 +1,459 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: a published
+known-answer vector, a closed form, a brute-force restatement of the same rule
+with a different algorithm, an independent library routine, or an invariant
+the paper states.  A plausible mistake in the oracle (dropped term, wrong sign
+or index, transposed operand) fails one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as Fnn
+
+from oracle import oracle as O
+from paper_2010_01775_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LO = np.zeros(3, np.float32)
+HI = np.ones(3, np.float32)
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Philox4x32-10 against the published known-answer vectors."""
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(t, 16) for t in line.split()]
+        assert list(O.philox4x32_10(v[0:4], v[4:6])) == v[6:10]
+        n += 1
+    assert n == 3
+
+
+# ---------------------------------------------------------------- voxel location (a1)
+def _deinterleave(code, D):
+    q = [0, 0, 0]
+    for b in range(D):
+        for a in range(3):
+            q[a] |= ((int(code) >> (3 * b + a)) & 1) << b
+    return q
+
+
+def test_morton_hand_values_and_roundtrip():
+    lib = O.lib()
+    assert lib.or_morton3(1, 0, 0, 2) == 1
+    assert lib.or_morton3(0, 1, 0, 2) == 2
+    assert lib.or_morton3(0, 0, 1, 2) == 4
+    assert lib.or_morton3(2, 0, 0, 2) == 8
+    assert lib.or_morton3(3, 3, 3, 2) == 63
+    assert lib.or_morton3(1023, 0, 0, 10) == int("001" * 10, 2)
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        D = int(rng.integers(1, 17))
+        q = [int(x) for x in rng.integers(0, 2 ** D, 3)]
+        code = lib.or_morton3(*q, D)
+        assert _deinterleave(code, D) == q
+        # Hierarchical nesting: the depth-d ancestor is the code of q >> (D - d).
+        d = int(rng.integers(0, D + 1))
+        assert code >> (3 * (D - d)) == lib.or_morton3(*[x >> (D - d) for x in q], d)
+
+
+def test_quantisation_is_the_containing_cell():
+    """q is the cell [lo + q h, lo + (q+1) h) containing x (h = (hi-lo)/2^D),
+    away from float rounding at cell faces; clamped outside the domain."""
+    rng = np.random.default_rng(2)
+    lo = np.array([-1.5, 0.25, 3.0], np.float32)
+    hi = np.array([2.5, 1.25, 7.0], np.float32)
+    D = 7
+    pos = (lo + (hi - lo) * rng.random((20000, 3))).astype(np.float32)
+    codes, st = O.morton_codes(pos, lo, hi, D)
+    assert st == 0
+    h = (hi.astype(np.float64) - lo) / 2 ** D
+    for i in range(pos.shape[0]):
+        q = _deinterleave(codes[i], D)
+        for a in range(3):
+            t = (float(pos[i, a]) - float(lo[a])) / h[a]
+            if abs(t - round(t)) < 1e-4:
+                continue
+            assert q[a] == math.floor(t)
+    outside = np.array([[-9, 0.75, 100], [2.5, 1.25, 7.0]], np.float32)
+    codes, st = O.morton_codes(outside, lo, hi, D)
+    assert _deinterleave(codes[0], D) == [0, 2 ** (D - 1), 2 ** D - 1]
+    assert _deinterleave(codes[1], D) == [2 ** D - 1] * 3
+    _, st = O.morton_codes(np.array([[np.nan, 0, 0]], np.float32), lo, hi, D)
+    assert st == O.ERR_INVALID_INPUT
+
+
+# ---------------------------------------------------------------- grid (a2-a4)
+def _brute_grid(q, D, min_depth, thr):
+    """Recursive subdivision by direct membership counting over integer cells.
+    Children are visited x-fastest (k = x + 2y + 4z), i.e. Morton order."""
+    leaves = []
+
+    def members(idx, c, d):
+        return [i for i in idx if all((q[i][a] >> (D - d)) == c[a] for a in range(3))]
+
+    def rec(c, d, idx):
+        if len(idx) > thr and d < D:
+            for k in range(8):
+                cc = [2 * c[0] + (k & 1), 2 * c[1] + ((k >> 1) & 1), 2 * c[2] + ((k >> 2) & 1)]
+                rec(cc, d + 1, members(idx, cc, d + 1))
+        else:
+            leaves.append((c, d, sorted(idx)))
+
+    n0 = 2 ** min_depth
+    cells = []
+    for z in range(n0):
+        for y in range(n0):
+            for x in range(n0):
+                cells.append([x, y, z])
+    lib = O.lib()
+    cells.sort(key=lambda c: lib.or_morton3(c[0], c[1], c[2], min_depth))
+    all_idx = list(range(len(q)))
+    for c in cells:
+        rec(c, min_depth, members(all_idx, c, min_depth))
+    return leaves
+
+
+@pytest.mark.parametrize("n,D,min_depth,thr,seed", [
+    (300, 3, 0, 20, 3), (500, 4, 1, 10, 4), (200, 2, 0, 0, 5), (400, 5, 0, 1000, 6), (0, 3, 0, 5, 7),
+    (257, 4, 2, 3, 8)])
+def test_grid_matches_brute_force(n, D, min_depth, thr, seed):
+    ph = synth.photons(n, 3, seed)
+    g = O.build_grid(ph, LO, HI, D, min_depth, thr)
+    q = [_deinterleave(c, D) for c in g["codes"]]
+    leaves = _brute_grid(q, D, min_depth, thr)
+    assert g["L"] == len(leaves)
+    lib = O.lib()
+    for l, (c, d, idx) in enumerate(leaves):
+        assert g["leaf_depth"][l] == d
+        assert g["leaf_code"][l] == lib.or_morton3(c[0], c[1], c[2], d) << (3 * (D - d))
+        got = sorted(int(p) for p in g["perm"][g["leaf_begin"][l]:g["leaf_end"][l]])
+        assert got == idx
+        for p in idx:
+            assert g["leaf_of"][p] == l
+
+
+def test_grid_invariants_tiny_workload():
+    wl = synth.TINY
+    ph = synth.photons(wl.n_photons, wl.n_blobs, wl.seed)
+    g = O.build_grid(ph, LO, HI, wl.max_depth, 0, wl.split_threshold)
+    D = wl.max_depth
+    cnt = g["leaf_end"].astype(np.int64) - g["leaf_begin"]
+    assert cnt.sum() == ph.shape[0]
+    # Leaves partition the cube: volumes sum to one, start codes strictly increase.
+    assert sum(8 ** (D - int(d)) for d in g["leaf_depth"]) == 8 ** D
+    assert np.all(np.diff(g["leaf_code"].astype(np.float64)) > 0)
+    # A leaf above max depth... cannot exist; below max depth it holds <= thr photons.
+    assert np.all(cnt[g["leaf_depth"] < D] <= wl.split_threshold)
+    # Sorted order is by code, ties by original index (a stable sort).
+    key = g["codes"][g["perm"]].astype(np.float64) * 2.0 ** 20 + g["perm"]
+    assert np.all(np.diff(key) > 0)
+    # Single leaf when the threshold covers everything.
+    g1 = O.build_grid(ph[:500], LO, HI, D, 0, 500)
+    assert g1["L"] == 1 and g1["leaf_end"][0] == 500
+
+
+# ---------------------------------------------------------------- direction bins
+def test_axis_directions_hand_bins():
+    H, W = 32, 64
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                     [1, 1e-30, 0], [1, -1e-30, 0], [-1, -1e-30, 0]], np.float32)
+    rows, cols, st = O.dir_bins(dirs, H, W)
+    assert st == 0
+    assert list(rows) == [16, 16, 16, 16, 31, 0, 16, 16, 16]
+    assert list(cols) == [0, 16, 32, 48, 0, 0, 0, 63, 32]
+
+
+def test_bins_match_atan2_away_from_edges():
+    rng = np.random.default_rng(9)
+    for H, W in [(32, 32), (64, 64), (128, 128), (8, 4), (64, 128)]:
+        d = synth.uniform_sphere(rng, 20000).astype(np.float32)
+        rows, cols, _ = O.dir_bins(d, H, W)
+        phi = np.mod(np.arctan2(d[:, 1].astype(np.float64), d[:, 0]), 2 * np.pi)
+        tj = phi * W / (2 * np.pi)
+        ti = (d[:, 2].astype(np.float64) + 1.0) * H / 2
+        okj = np.abs(tj - np.round(tj)) > 1e-4
+        oki = np.abs(ti - np.round(ti)) > 1e-4
+        assert np.array_equal(cols[okj], np.floor(tj[okj]).astype(np.int64) % W)
+        assert np.array_equal(rows[oki], np.clip(np.floor(ti[oki]), 0, H - 1).astype(np.int64))
+
+
+def test_bins_are_equal_area():
+    """Uniform directions fill every bin equally (cylindrical map is
+    area-preserving, Sec. 4): chi-square goodness of fit."""
+    from scipy.stats import chisquare
+    rng = np.random.default_rng(10)
+    H, W = 16, 32
+    d = synth.uniform_sphere(rng, 400000).astype(np.float32)
+    rows, cols, _ = O.dir_bins(d, H, W)
+    counts = np.bincount(rows * W + cols, minlength=H * W)
+    assert chisquare(counts).pvalue > 1e-3
+
+
+# ---------------------------------------------------------------- splat (a5)
+def _brute_splat(ph, g, n_prev, H, W, F):
+    rows, cols, _ = O.dir_bins(ph[:, 3:6], H, W)
+    pfx = [int(v) for v in np.rint(ph[:, 6].astype(np.float64) * 2.0 ** F)]
+    L = g["L"]
+    pc = [[0] * (H * W) for _ in range(L)]
+    cc = [[0] * (H * W) for _ in range(L)]
+    pp = [[0] * (H * W) for _ in range(L)]
+    cp = [[0] * (H * W) for _ in range(L)]
+    for p in range(ph.shape[0]):
+        l, k = int(g["leaf_of"][p]), int(rows[p] * W + cols[p])
+        pc[l][k] += pfx[p]
+        cc[l][k] += 1
+        if p < n_prev:
+            pp[l][k] += pfx[p]
+            cp[l][k] += 1
+    return pc, cc, pp, cp, pfx
+
+
+def test_splat_matches_brute_force_and_conserves_mass():
+    ph = synth.photons(3000, 4, 11)
+    g = O.build_grid(ph, LO, HI, 4, 0, 100)
+    H, W, F = 8, 16, 32
+    h = O.splat(ph, g, 1234, H, W, F)
+    assert h["status"] == 0
+    pc, cc, pp, cp, pfx = _brute_splat(ph, g, 1234, H, W, F)
+    assert h["pow_cur"].tolist() == pc and h["cnt_cur"].tolist() == cc
+    assert h["pow_prev"].tolist() == pp and h["cnt_prev"].tolist() == cp
+    # Eq. (photon): the map of a leaf sums to the power of its photons, exactly.
+    assert sum(int(v) for v in h["pow_cur"].ravel()) == sum(pfx)
+    assert int(h["cnt_cur"].sum()) == 3000
+    # The previous-iteration channels equal the current channels of the first n_prev photons.
+    h2 = O.splat(ph[:1234], O.build_grid(ph[:1234], LO, HI, 4, 0, 10 ** 9), 0, H, W, F)
+    assert sum(int(v) for v in h["pow_prev"].ravel()) == sum(int(v) for v in h2["pow_cur"].ravel())
+
+
+def test_single_photon_single_bin_and_status():
+    ph = np.zeros((1, 8), np.float32)
+    ph[0, :7] = [0.3, 0.3, 0.3, 0.0, 0.0, 1.0, 0.75]
+    g = O.build_grid(ph, LO, HI, 2, 0, 0)
+    h = O.splat(ph, g, 1, 4, 4)
+    l = g["leaf_of"][0]
+    assert np.count_nonzero(h["pow_cur"]) == 1
+    assert h["pow_cur"][l, 3 * 4 + 0] == 3 << 30  # 0.75 * 2^32, top row, column 0
+    bad = ph.copy()
+    bad[0, 6] = np.nan
+    assert O.splat(bad, g, 0, 4, 4)["status"] == O.ERR_INVALID_INPUT
+    big = np.repeat(ph, 4, axis=0)
+    big[:, 6] = 2.0 ** 30  # 2^62 fixed point each: four of them would overflow 2^63
+    gb = O.build_grid(big, LO, HI, 2, 0, 0)
+    assert O.splat(big, gb, 0, 4, 4)["status"] == O.ERR_OVERFLOW
+
+
+def test_fixed_point_rounds_half_even():
+    ph = np.zeros((3, 8), np.float32)
+    ph[:, 3] = 1.0
+    ph[:, 6] = [2.0 ** -33, 3 * 2.0 ** -33, 2.0 ** -34]  # 0.5, 1.5, 0.25 units
+    g = O.build_grid(ph, LO, HI, 1, 0, 10)
+    h = O.splat(ph, g, 0, 4, 4)
+    assert int(h["pow_cur"].sum()) == 0 + 2 + 0
+
+
+# ---------------------------------------------------------------- inputs (a6)
+def test_input_channels():
+    ph = synth.photons(5000, 4, 12)
+    g = O.build_grid(ph, LO, HI, 3, 0, 300)
+    act, _ = O.active_leaves(g)
+    h = O.hist_for_active(O.splat(ph, g, 2500, 16, 16), act)
+    x = O.assemble_inputs(h)
+    HW = 256
+    for a in range(len(act)):
+        s0 = x[a, ..., 0].sum()
+        assert abs(s0 - HW) < 1e-9 * HW  # mean-one density
+        if h["pow_prev"][a].sum() > 0:
+            assert abs(x[a, ..., 1].sum() - HW) < 1e-9 * HW
+        c = h["cnt_cur"][a].reshape(16, 16)
+        assert np.array_equal(x[a, ..., 4], (c > 0).astype(np.float64))
+        assert np.allclose(x[a, ..., 2], np.log1p(c), rtol=0, atol=1e-15)
+        k = int(np.argmax(h["pow_cur"][a]))
+        assert math.isclose(x[a].reshape(HW, 5)[k, 0],
+                            int(h["pow_cur"][a][k]) * HW / int(h["pow_cur"][a].sum()), rel_tol=1e-14)
+
+
+# ---------------------------------------------------------------- CNN (a7)
+@pytest.mark.parametrize("A,H,W,Cin,Cout,k,stride", [
+    (2, 8, 8, 5, 7, 3, 1), (3, 16, 8, 6, 4, 3, 2), (1, 8, 16, 3, 2, 1, 1), (2, 4, 4, 9, 3, 3, 1)])
+def test_conv2d_matches_torch(A, H, W, Cin, Cout, k, stride):
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal((A, H, W, Cin))
+    w = rng.standard_normal((Cout, k, k, Cin)).astype(np.float32)
+    b = rng.standard_normal(Cout).astype(np.float32)
+    got = O.conv2d(x, w, b, stride)
+    ref = Fnn.conv2d(torch.from_numpy(x).permute(0, 3, 1, 2), torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                     torch.from_numpy(b.astype(np.float64)), stride=stride, padding=k // 2)
+    assert np.allclose(got, ref.permute(0, 2, 3, 1).numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_conv2d_delta_kernel_is_identity():
+    rng = np.random.default_rng(14)
+    x = rng.standard_normal((2, 8, 8, 3))
+    w = np.zeros((3, 3, 3, 3), np.float32)
+    for c in range(3):
+        w[c, 1, 1, c] = 1.0
+    assert np.array_equal(O.conv2d(x, w, np.zeros(3, np.float32), 1), x)
+
+
+def test_activations_closed_forms():
+    assert O.elu(np.array([2.0]))[0] == 2.0
+    assert math.isclose(O.elu(np.array([-1.0]))[0], math.exp(-1) - 1, rel_tol=1e-15)
+    assert math.isclose(O.softplus(np.array([0.0]))[0], math.log(2.0), rel_tol=1e-15)
+    assert math.isclose(O.softplus(np.array([-40.0]))[0], math.exp(-40.0), rel_tol=1e-12)
+    assert O.softplus(np.array([800.0]))[0] == 800.0
+
+
+def _torch_unet(x, net):
+    """The same U-Net wired with torch.nn.functional in float64 (library pin)."""
+    t = torch.from_numpy(x).permute(0, 3, 1, 2)
+    Ls = net["layers"]
+
+    def run(h, i):
+        cout, cin, k, stride, act, w, b = Ls[i]
+        h = Fnn.conv2d(h, torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                       torch.from_numpy(b.astype(np.float64)), stride=stride, padding=k // 2)
+        return Fnn.elu(h) if act == O.ACT_ELU else (Fnn.softplus(h) if act == O.ACT_SOFTPLUS else h)
+
+    up = lambda h: Fnn.interpolate(h, scale_factor=2, mode="nearest")
+    e0 = run(run(t, 0), 1)
+    e1 = run(run(e0, 2), 3)
+    e2 = run(run(e1, 4), 5)
+    e3 = run(run(e2, 6), 7)
+    d2 = run(run(torch.cat([up(e3), e2], 1), 8), 9)
+    d1 = run(run(torch.cat([up(d2), e1], 1), 10), 11)
+    d0 = run(run(torch.cat([up(d1), e0], 1), 12), 13)
+    return run(d0, 14)[:, 0].numpy()
+
+
+def test_unet_matches_torch_wiring():
+    net = O.parse_net(synth.net_blob(synth.ARCH_UNET4, (8, 8, 16, 16), 15))
+    rng = np.random.default_rng(15)
+    x = rng.standard_normal((2, 16, 16, 5))
+    assert np.allclose(O.cnn_forward(x, net), _torch_unet(x, net), rtol=1e-10, atol=1e-300)
+
+
+def test_tiny_net_zero_input_interior_closed_form():
+    """All-zero input: layer 1 is elu(b1) everywhere; at pixels two away from
+    the border every tap sees interior values, so the output is
+    softplus(b3 + sum w3 elu(b2 + sum w2 elu(b1)))."""
+    net = O.parse_net(synth.net_blob(synth.ARCH_TINY3, (16,), 16))
+    (c1, _, _, _, _, w1, b1), (c2, _, _, _, _, w2, b2), (c3, _, _, _, _, w3, b3) = net["layers"]
+    y = O.cnn_forward(np.zeros((1, 8, 8, 5)), net)
+    h1 = O.elu(b1.astype(np.float64))
+    h2 = O.elu(b2 + np.einsum("oyxi,i->o", w2.astype(np.float64), h1))
+    ref = O.softplus(b3 + np.einsum("oyxi,i->o", w3.astype(np.float64), h2))[0]
+    assert np.allclose(y[0, 2:6, 2:6], ref, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- normalise / CDF (a8-a9)
+def _random_maps(A, H, W, seed, zero_rows=True):
+    rng = np.random.default_rng(seed)
+    y = rng.lognormal(0, 2, (A, H, W))
+    if zero_rows:
+        y[0, 3, :] = 0.0
+        y[1, :, 5] = 0.0
+    return y
+
+
+def test_pdf_integrates_to_one_and_cdfs_end_at_one():
+    y = _random_maps(4, 16, 32, 17)
+    t = O.tables_from_map(y)
+    H, W = 16, 32
+    dOmega = 4 * np.pi / (H * W)
+    for a in range(4):
+        pdf = t["P"][a] * H * W / (4 * np.pi)
+        assert abs((pdf * dOmega).sum() - 1.0) < 1e-12
+        assert t["Fz"][a, -1] == pytest.approx(1.0, abs=1e-14)
+        assert np.all(np.abs(t["Fphi"][a, :, -1] - 1.0) < 1e-14)
+        assert np.all(np.diff(t["Fz"][a]) >= 0) and np.all(np.diff(t["Fphi"][a], axis=1) >= 0)
+        # Differences of the CDFs reproduce the map.
+        m = np.diff(np.concatenate([[0.0], t["Fz"][a]]))
+        assert np.allclose(m, t["P"][a].sum(axis=1), atol=1e-15)
+        rows_ok = m > 0
+        cond = np.diff(np.concatenate([np.zeros((H, 1)), t["Fphi"][a]], axis=1))
+        assert np.allclose((cond * m[:, None])[rows_ok], t["P"][a][rows_ok], atol=1e-15)
+    assert np.array_equal(t["Fphi"][0, 3], (np.arange(W) + 1.0) / W)  # empty row -> uniform
+    assert t["fz"][0, -1] == 1.0 and np.all(t["fphi"][:, :, -1] == 1.0)
+
+
+def test_invalid_map_flagged():
+    y = np.zeros((2, 4, 4))
+    y[1, 0, 0] = 1.0
+    t = O.tables_from_map(y)
+    assert list(t["valid"]) == [0, 1]
+    assert t["P"][1, 0, 0] == 1.0
+
+
+# ---------------------------------------------------------------- sampling / eval (a10-a12)
+def _one_leaf_grid():
+    ph = np.zeros((1, 8), np.float32)
+    ph[0, :3] = 0.5
+    return O.build_grid(ph, LO, HI, 0, 0, 10)
+
+
+def test_sampling_chi_square_and_bins_and_pdf():
+    from scipy.stats import chisquare
+    H, W = 8, 16
+    g = _one_leaf_grid()
+    y = _random_maps(1, H, W, 18, zero_rows=False)
+    y[0, 2, :] = 0.0
+    y[0, 5, 7] = 0.0
+    t = O.tables_from_map(y)
+    q = 200000
+    pos = np.full((q, 3), 0.25, np.float32)
+    s = O.sample(g, np.zeros(1, np.int32), t, pos, seed=99, stream=3)
+    assert np.all(s["leaf"] == 0)
+    counts = np.bincount(s["bin"].astype(np.int64), minlength=H * W)
+    P = t["P"][0].ravel()
+    assert counts[P == 0].sum() == 0  # zero-mass bins never drawn
+    exp = P * q
+    keep = exp >= 5
+    obs = np.append(counts[keep], counts[~keep].sum())
+    e = np.append(exp[keep], exp[~keep].sum())
+    assert chisquare(obs, e * obs.sum() / e.sum()).pvalue > 1e-3
+    # Sampled directions are unit and land in their bin; returned pdf = eval pdf.
+    d32 = s["dir"].astype(np.float32)
+    assert np.allclose(np.linalg.norm(s["dir"], axis=1), 1.0, atol=1e-12)
+    rows, cols, _ = O.dir_bins(d32, H, W)
+    same = (rows * W + cols) == s["bin"]
+    assert same.mean() > 1 - 1e-4
+    ev = O.eval_pdf(g, np.zeros(1, np.int32), t, pos, d32)
+    assert np.allclose(ev[same], s["pdf"][same], rtol=1e-14)
+    assert np.allclose(s["pdf"], P[s["bin"]] * H * W / (4 * np.pi), rtol=1e-14)
+
+
+def test_pdf_monte_carlo_mean_is_one():
+    """E over uniform directions of p(w) * 4pi equals the integral of p: 1."""
+    H, W = 16, 16
+    g = _one_leaf_grid()
+    t = O.tables_from_map(_random_maps(1, H, W, 19, zero_rows=False))
+    rng = np.random.default_rng(19)
+    d = synth.uniform_sphere(rng, 400000).astype(np.float32)
+    p = O.eval_pdf(g, np.zeros(1, np.int32), t, np.full((d.shape[0], 3), 0.5, np.float32), d) * 4 * np.pi
+    assert abs(p.mean() - 1.0) < 5 * p.std() / math.sqrt(p.size)
+
+
+def test_uniform_fallback_for_leaves_without_map():
+    ph = synth.photons(2000, 2, 20)
+    g = O.build_grid(ph, LO, HI, 3, 0, 50)
+    act, slot = O.active_leaves(g)
+    H, W = 8, 8
+    t = O.tables_from_map(np.ones((act.size, H, W)))
+    pos = synth.query_positions(5000, 20)
+    s = O.sample(g, slot, t, pos, seed=5)
+    leaf = s["leaf"] & 0x7FFFFFFF
+    codes, _ = O.morton_codes(pos, LO, HI, 3)
+    assert np.array_equal(leaf, np.searchsorted(g["leaf_code"], codes, side="right") - 1)
+    empty = slot[leaf] < 0
+    assert empty.any() and (~empty).any()
+    assert np.all((s["leaf"] >> 31) == empty)
+    assert np.allclose(s["pdf"][empty], 1 / (4 * np.pi))
+    assert np.allclose(s["pdf"][~empty], 1 / (4 * np.pi))  # a constant map is the uniform pdf
+    assert np.all(s["bin"][empty] == 0xFFFFFFFF)
