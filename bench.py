@@ -1,0 +1,366 @@
+"""Benchmark of the guiding hot path on GB300.
+
+One step = one pass of the whole path over the workload: grid build (Morton
+codes, radix sort, adaptive split, leaf assignment) -> splat -> CNN
+reconstruction -> normalisation + CDFs -> guided sampling of Q queries -> pdf
+evaluation of Q (position, direction) pairs.  Default workload: 4,194,304
+photons (64 blobs), depth 10, split threshold 2000, 64x64 maps, U-Net
+32-64-128-256, FP32, 8,388,608 queries.
+
+Prints one JSON line.  `value` = guided samples per second over whole steps
+(Q x steps / device time of the steps, inputs resident in HBM); `e2e` = the
+same through the C ABI with inputs in pinned host memory and results read
+back, copies inside the timed region.  `--impl reference` times the CPU
+oracle (FP64, host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "guided samples/s + leaf tables/s, FP32 vs BF16/FP8 at KL≤1e-3; p50/p99 latency"
+LO, HI = [0.0, 0.0, 0.0], [1.0, 1.0, 1.0]
+
+
+def unet_flops_per_leaf(H, W, widths, arch):
+    """2 * MACs of the network per map (zero padding counted as work)."""
+    from paper_2010_01775_gb300 import synth
+    f, h, w = 0, H, W
+    layers = synth.net_layers(arch, widths)
+    res = {0: (H, W)}
+    if arch == synth.ARCH_TINY3:
+        return sum(2 * H * W * k * k * cin * cout for cout, cin, k, s, a in layers)
+    sizes = [(H, W), (H, W), (H // 2, W // 2), (H // 2, W // 2), (H // 4, W // 4), (H // 4, W // 4),
+             (H // 8, W // 8), (H // 8, W // 8), (H // 4, W // 4), (H // 4, W // 4), (H // 2, W // 2),
+             (H // 2, W // 2), (H, W), (H, W), (H, W)]
+    for (cout, cin, k, s, a), (ho, wo) in zip(layers, sizes):
+        f += 2 * ho * wo * k * k * cin * cout
+    return f
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def run_pg(args, wl, prec):
+    import torch
+
+    from paper_2010_01775_gb300 import pg, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ph, pos, dirs, blob = synth.workload_inputs(wl)
+    n, q, H, W = wl.n_photons, wl.n_queries, wl.H, wl.W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = pg.Context(stream.cuda_stream)
+    net = pg.pg_net_load(ctx, blob)
+    d_ph = torch.from_numpy(ph).cuda()
+    d_pos = torch.from_numpy(pos).cuda()
+    d_dir = torch.from_numpy(dirs).cuda()
+    o_dir = torch.empty(q, 3, device="cuda")
+    o_pdf = torch.empty(q, device="cuda")
+    o_leaf = torch.empty(q, dtype=torch.int32, device="cuda")
+    o_bin = torch.empty(q, dtype=torch.int32, device="cuda")
+    o_ev = torch.empty(q, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(p_ph, p_pos, p_dir, outs, marks=None):
+        o_d, o_p, o_l, o_b, o_e = outs
+        if marks is not None:
+            marks[0].record(stream)
+        g = pg.pg_build_grid(ctx, p_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+        if marks is not None:
+            marks[1].record(stream)
+        h = pg.pg_splat_photons(ctx, g, p_ph, n, wl.n_prev, H, W, wl.frac_bits)
+        if marks is not None:
+            marks[2].record(stream)
+        m = pg.pg_reconstruct(ctx, h, net, prec)
+        if marks is not None:
+            marks[3].record(stream)
+        t = pg.pg_build_cdf(ctx, m)
+        if marks is not None:
+            marks[4].record(stream)
+        pg.pg_sample_dirs(ctx, g, t, p_pos, q, 20101775, 0, o_d, o_p, o_l, o_b)
+        if marks is not None:
+            marks[5].record(stream)
+        pg.pg_eval_pdf(ctx, g, t, p_pos, p_dir, q, o_e)
+        if marks is not None:
+            marks[6].record(stream)
+        A = g.info(pg.PG_INFO_N_ACTIVE)
+        L = g.info(pg.PG_INFO_N_LEAVES)
+        for hd in (t, m, h, g):
+            hd.free()
+        return A, L
+
+    outs = (o_dir, o_pdf, o_leaf, o_bin, o_ev)
+    for _ in range(args.warmup):
+        A, L = step(d_ph, d_pos, d_dir, outs)
+    ctx.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    times, stage = [], np.zeros(6)
+    for _ in range(args.steps):
+        flush.zero_()
+        marks = [ev() for _ in range(7)]
+        A, L = step(d_ph, d_pos, d_dir, outs, marks)
+        marks[6].synchronize()
+        times.append(marks[0].elapsed_time(marks[6]))
+        stage += [marks[i].elapsed_time(marks[i + 1]) for i in range(6)]
+    ctx.sync()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+
+    # End to end through the C ABI with pinned host buffers: photons are
+    # copied once per step, query arrays are passed as host pointers (the
+    # library stages them), results land in pinned host memory.
+    h_ph = torch.from_numpy(ph).pin_memory()
+    h_pos = torch.from_numpy(pos).pin_memory()
+    h_dir = torch.from_numpy(dirs).pin_memory()
+    h_outs = (torch.empty(q, 3).pin_memory(), torch.empty(q).pin_memory(),
+              torch.empty(q, dtype=torch.int32).pin_memory(), torch.empty(q, dtype=torch.int32).pin_memory(),
+              torch.empty(q).pin_memory())
+    e2e_steps = max(1, min(args.steps, 3))
+
+    def e2e_step():
+        dph = torch.empty_like(d_ph)
+        dph.copy_(h_ph, non_blocking=True)
+        step(dph, h_pos, h_dir, h_outs)
+        ctx.sync()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = ph.nbytes + pos.nbytes + dirs.nbytes
+    d2h = q * (12 + 4 + 4 + 4 + 4)
+
+    # Dominant kernel: the CNN (all conv launches of one reconstruct call),
+    # timed with events on the launching stream.
+    flops_leaf = unet_flops_per_leaf(H, W, wl.widths, wl.arch)
+    g = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+    h = pg.pg_splat_photons(ctx, g, d_ph, n, wl.n_prev, H, W)
+    cnn_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        a, b = ev(), ev()
+        a.record(stream)
+        m = pg.pg_reconstruct(ctx, h, net, prec)
+        b.record(stream)
+        b.synchronize()
+        cnn_ms.append(a.elapsed_time(b))
+        m.free()
+    cnn_s = statistics.median(cnn_ms) / 1e3
+    peaks, peak_src = load_peaks()
+    if prec == pg.PG_FP32:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+    else:
+        peak = peaks["bf16_tflops"] * (2.0 if prec == pg.PG_FP8_E4M3 else 1.0)
+        bound, unit = "tensor", "TFLOP/s"
+    achieved = flops_leaf * A / cnn_s / 1e12
+    for hd in (h, g):
+        hd.free()
+    ctx.destroy()
+
+    value = q * args.steps * world / (total_ms / 1e3)
+    stage_ms = dict(zip(["grid", "splat", "cnn", "cdf", "sample", "eval"], (stage / args.steps).round(4).tolist()))
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec],
+            "data": "synthetic (seeded photon blobs on room walls, vMF directions, lognormal power; random He-init U-Net)",
+            "config": {"workload": wl.name, "photons": n, "queries": q, "H": H, "W": W, "max_depth": wl.max_depth,
+                       "split_threshold": wl.split_threshold, "leaves": L, "active_leaves": A,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
+            "leaf_tables_per_s": A * args.steps * world / (total_ms / 1e3),
+            "stage_ms": stage_ms,
+            "stage_throughput": {"leaf_tables_per_s_build": A / (sum(list(stage_ms.values())[:4]) / 1e3),
+                                 "guided_samples_per_s_sample_eval": q / ((stage_ms["sample"] + stage_ms["eval"]) / 1e3)},
+            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+            "e2e": {"value": q / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": None,
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                         "traffic": None, "kernel": "CNN convolutions (all layers of one reconstruct call)",
+                         "peak_source": peak_src if prec != pg.PG_FP32 else "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock"},
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves)
+        out["gpu_launches"] = count_launches(wl, A)
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def count_launches(wl, A):
+    """Kernel launches of one step (host-side count of the library's launch
+    sequence for this workload)."""
+    passes = (3 * wl.max_depth + 7) // 8
+    levels = wl.max_depth - wl.min_depth + 1
+    grid = 1 + 3 * passes + 1 + 3 * levels + 1 + 1 + 1
+    splat = 1 if wl.H * wl.W <= 8192 else 2
+    convs = 3 if wl.arch == 0 else 15
+    chunks = 1
+    cnn = chunks * (1 + convs)
+    return grid + splat + cnn + 1 + 1 + 1
+
+
+def oracle_sample_run(wl, n_leaves, n_queries, seed_shift=0):
+    """The FP64 oracle on a bounded sample; returns per-stage seconds and the
+    throughput extrapolated to the full workload."""
+    from oracle import oracle as O
+    from paper_2010_01775_gb300 import synth
+    ph, pos, dirs, blob = synth.workload_inputs(wl)
+    t0 = time.perf_counter()
+    g = O.build_grid(ph, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+    act, slot = O.active_leaves(g)
+    t1 = time.perf_counter()
+    keep = act[:: max(1, act.size // n_leaves)][:n_leaves]
+    gsub = dict(g)
+    h = O.splat(ph, g, wl.n_prev, wl.H, wl.W, wl.frac_bits)
+    t2 = time.perf_counter()
+    hs = O.hist_for_active(h, keep)
+    y = O.cnn_forward(O.assemble_inputs(hs), O.parse_net(blob))
+    t3 = time.perf_counter()
+    tabs = O.tables_from_map(y)
+    t4 = time.perf_counter()
+    slot2 = np.full(g["L"], -1, np.int32)
+    slot2[keep] = np.arange(keep.size, dtype=np.int32)
+    s = O.sample(gsub, slot2, tabs, pos[:n_queries], 20101775)
+    O.eval_pdf(gsub, slot2, tabs, pos[:n_queries], dirs[:n_queries])
+    t5 = time.perf_counter()
+    A = act.size
+    step_s = (t1 - t0) + (t2 - t1) + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
+        (t5 - t4) * wl.n_queries / n_queries
+    return dict(step_s=step_s, samples_per_s=wl.n_queries / step_s, wall_s=t5 - t0, leaves=int(keep.size),
+                A=int(A), queries=n_queries)
+
+
+def cpu_baseline(wl, n_leaves):
+    r = oracle_sample_run(wl, n_leaves, 262_144)
+    return {"value": r["samples_per_s"], "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons, CNN+CDF on "
+                       f"{r['leaves']} of {r['A']} active leaves, sample+eval on {r['queries']} of {wl.n_queries} "
+                       f"queries; per-stage times scaled to the full step ({r['step_s']:.1f} s); "
+                       f"wall {r['wall_s']:.1f} s")}
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample_run(wl, 2, 65_536)
+        if i >= args.warmup:
+            steps.append(r)
+    step_s = statistics.mean(r["step_s"] for r in steps)
+    value = wl.n_queries / step_s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: grid+splat on all photons, CNN+CDF on 2 active leaves, sample+eval on "
+                                   "65536 queries, scaled to the full step"},
+        "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pg", choices=["pg", "reference"])
+    ap.add_argument("--workload", default="scale")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-leaves", type=int, default=6)
+    args = ap.parse_args()
+    from paper_2010_01775_gb300 import synth
+    wl = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_01775_gb300 import pg
+    run_pg(args, wl, pg.PRECISIONS[args.precision])
+
+
+if __name__ == "__main__":
+    main()

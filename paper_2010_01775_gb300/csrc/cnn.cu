@@ -1,0 +1,365 @@
+// a6-a7: network input assembly and the reconstruction CNN (Sec. 5, 5.1).
+//
+// Every convolution is an implicit GEMM over all active leaves at once:
+//   M = leaves x output pixels, N = output channels, K = taps x input channels,
+// activations channel-last ([leaf][y][x][c]) so that a K-chunk of one tap is
+// a contiguous run of channels.  The U-Net's skip concatenations cost
+// nothing: the encoder writes its skip output straight into the channel slice
+// of the decoder's input buffer, and the layer below the concatenation writes
+// its output already upsampled (nearest x2) into the other slice.
+//
+// FP32 form: SIMT FMA tiles (BM x BN per 256-thread CTA, 8 x TN per thread).
+// BF16 / FP8 forms: tcgen05 tensor-core kernels (conv_tc.cu).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "conv.cuh"
+
+namespace pgi {
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------- a6
+// x[slot][k][0..7] = (S_t, S_{t-1}, log1p(C_t), log1p(C_{t-1}), C_t > 0, 0, 0, 0)
+// with S = Phi * HW / sum Phi (0 for a leaf without energy).
+__global__ void k_assemble(const uint64_t *__restrict__ pow_cur, const uint32_t *__restrict__ cnt_cur,
+                           const uint64_t *__restrict__ pow_prev, const uint32_t *__restrict__ cnt_prev,
+                           const uint64_t *__restrict__ tot_cur, const uint64_t *__restrict__ tot_prev,
+                           uint32_t slot0, uint32_t nslots, int HW, float *__restrict__ x) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nslots * HW) return;
+  uint32_t s = slot0 + (uint32_t)(i / HW);
+  size_t g = (size_t)slot0 * HW + i;
+  uint64_t tc = tot_cur[s], tp = tot_prev[s];
+  float ic = tc ? (float)HW / __ull2float_rn(tc) : 0.0f;
+  float ip = tp ? (float)HW / __ull2float_rn(tp) : 0.0f;
+  uint32_t c = cnt_cur[g], cp = cnt_prev[g];
+  float4 a = make_float4(__ull2float_rn(pow_cur[g]) * ic, __ull2float_rn(pow_prev[g]) * ip, log1pf((float)c),
+                         log1pf((float)cp));
+  float4 b = make_float4(c ? 1.0f : 0.0f, 0.0f, 0.0f, 0.0f);
+  float4 *o = reinterpret_cast<float4 *>(x + i * 8);
+  o[0] = a;
+  o[1] = b;
+}
+
+__device__ __forceinline__ float activate(float v, int act) {
+  if (act == 1) return v > 0.0f ? v : expm1f(v);
+  if (act == 2) return fmaxf(v, 0.0f) + log1pf(expf(-fabsf(v)));
+  return v;
+}
+
+// ---------------------------------------------------------------- a7, FP32 SIMT
+// CTA tile BM x BN, K chunk 16.  Thread (tx, ty): rows tx*4+{0..3} and
+// BM/2+tx*4+{0..3}, columns ty*TN..ty*TN+TN-1.  A is gathered channel-last
+// with 16-byte loads (4 channels of one tap), staged k-major in shared memory.
+template <int BM, int BN, int TN>
+__global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
+  constexpr int BK = 16;
+  constexpr int TX = BM / 8;  // threads along M
+  static_assert(TX * (BN / TN) == 256, "256 threads");
+  constexpr int A_VEC = BM * BK / 4 / 256;  // float4 loads of A per thread
+  constexpr int B_VEC = (BN * BK / 4 + 255) / 256;
+  __shared__ __align__(16) float As[BK][BM + 4];
+  __shared__ __align__(16) float Bs[BK][BN];
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const long m0 = (long)blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int K = a.k * a.k * a.Cin;
+  const int HWo = a.Hout * a.Wout;
+
+  // Per-thread A rows: fixed across the K loop.
+  int a_kq = tid & 3;  // which 4-channel quad of the 16-chunk
+  int a_base[A_VEC], a_iy[A_VEC], a_ix[A_VEC];
+#pragma unroll
+  for (int v = 0; v < A_VEC; ++v) {
+    int m = (tid >> 2) + v * 64;
+    long mg = m0 + m;
+    if (mg < a.M) {
+      int leaf = (int)(mg / HWo), r = (int)(mg % HWo);
+      int oy = r / a.Wout, ox = r % a.Wout;
+      a_iy[v] = oy * a.stride - a.pad;
+      a_ix[v] = ox * a.stride - a.pad;
+      a_base[v] = leaf * a.Hin;
+    } else {
+      a_iy[v] = -100000;
+      a_ix[v] = -100000;
+      a_base[v] = 0;
+    }
+  }
+
+  float acc[8][TN];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+
+  float4 ra[A_VEC], rb[B_VEC];
+  auto load = [&](int k0) {
+    int kk = k0 + a_kq * 4;
+    int tap = kk / a.Cin, c = kk - tap * a.Cin;
+    int ky = tap / a.k, kx = tap - ky * a.k;
+#pragma unroll
+    for (int v = 0; v < A_VEC; ++v) {
+      int iy = a_iy[v] + ky, ix = a_ix[v] + kx;
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (kk < K && iy >= 0 && iy < a.Hin && ix >= 0 && ix < a.Win) {
+        const float *p = ((const float *)a.in) + ((size_t)(a_base[v] + iy) * a.Win + ix) * a.in_cs + a.in_co + c;
+        val = __ldg(reinterpret_cast<const float4 *>(p));
+      }
+      ra[v] = val;
+    }
+#pragma unroll
+    for (int v = 0; v < B_VEC; ++v) {
+      int idx = tid + v * 256;  // float4 index within BK x BN
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (idx < BN * BK / 4) {
+        int r = idx / (BN / 4), cq = idx % (BN / 4);
+        int kr = k0 + r, n = n0 + cq * 4;
+        if (kr < K && n < a.Cout) val = __ldg(reinterpret_cast<const float4 *>(a.w + (size_t)kr * a.Cout + n));
+      }
+      rb[v] = val;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int v = 0; v < A_VEC; ++v) {
+      int m = (tid >> 2) + v * 64;
+      As[a_kq * 4 + 0][m] = ra[v].x;
+      As[a_kq * 4 + 1][m] = ra[v].y;
+      As[a_kq * 4 + 2][m] = ra[v].z;
+      As[a_kq * 4 + 3][m] = ra[v].w;
+    }
+#pragma unroll
+    for (int v = 0; v < B_VEC; ++v) {
+      int idx = tid + v * 256;
+      if (idx < BN * BK / 4) {
+        int r = idx / (BN / 4), cq = idx % (BN / 4);
+        *reinterpret_cast<float4 *>(&Bs[r][cq * 4]) = rb[v];
+      }
+    }
+  };
+
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    __syncthreads();
+    store();
+    __syncthreads();
+    if (k0 + BK < K) load(k0 + BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tx * 4]);
+      float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][BM / 2 + tx * 4]);
+      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[TN];
+      if constexpr (TN % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < TN; j += 4) {
+          float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][ty * TN + j]);
+          bv[j] = b4.x; bv[j + 1] = b4.y; bv[j + 2] = b4.z; bv[j + 3] = b4.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][ty * TN + j];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+  }
+
+  // Epilogue: bias + activation, channel-last store (optionally upsampled x2).
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int m = (i < 4) ? tx * 4 + i : BM / 2 + tx * 4 + (i - 4);
+    long mg = m0 + m;
+    if (mg >= a.M) continue;
+    int leaf = (int)(mg / HWo), r = (int)(mg % HWo);
+    int oy = r / a.Wout, ox = r % a.Wout;
+    float o[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      int n = n0 + ty * TN + j;
+      o[j] = n < a.Cout ? activate(acc[i][j] + __ldg(a.bias + n), a.act) : 0.0f;
+    }
+    int nb = n0 + ty * TN;
+    if (nb >= a.Cout) continue;
+    int reps = a.ups ? 2 : 1;
+    int Ho = a.Hout * reps, Wo = a.Wout * reps;
+    for (int dy = 0; dy < reps; ++dy)
+      for (int dx = 0; dx < reps; ++dx) {
+        float *p = ((float *)a.out) + ((size_t)(leaf * Ho + oy * reps + dy) * Wo + ox * reps + dx) * a.out_cs + a.out_co + nb;
+        if constexpr (TN % 4 == 0) {
+#pragma unroll
+          for (int j = 0; j < TN; j += 4) *reinterpret_cast<float4 *>(p + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < TN; ++j) p[j] = o[j];
+        }
+      }
+  }
+}
+
+// Single-output-channel conv (3x3 or 1x1) + activation into the map y.
+__global__ void k_conv_cout1(ConvArgs a) {
+  long mg = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (mg >= a.M) return;
+  int HWo = a.Hout * a.Wout;
+  int leaf = (int)(mg / HWo), r = (int)(mg % HWo);
+  int oy = r / a.Wout, ox = r % a.Wout;
+  float acc = 0.0f;
+  for (int ky = 0; ky < a.k; ++ky) {
+    int iy = oy * a.stride + ky - a.pad;
+    if (iy < 0 || iy >= a.Hin) continue;
+    for (int kx = 0; kx < a.k; ++kx) {
+      int ix = ox * a.stride + kx - a.pad;
+      if (ix < 0 || ix >= a.Win) continue;
+      const float *p = ((const float *)a.in) + ((size_t)(leaf * a.Hin + iy) * a.Win + ix) * a.in_cs + a.in_co;
+      const float *w = a.w + (size_t)(ky * a.k + kx) * a.Cin;  // [K][1]
+      for (int c = 0; c < a.Cin; c += 4) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p + c));
+        acc = fmaf(v.x, __ldg(w + c), acc);
+        acc = fmaf(v.y, __ldg(w + c + 1), acc);
+        acc = fmaf(v.z, __ldg(w + c + 2), acc);
+        acc = fmaf(v.w, __ldg(w + c + 3), acc);
+      }
+    }
+  }
+  ((float *)a.out)[(size_t)mg * a.out_cs + a.out_co] = activate(acc + __ldg(a.bias), a.act);
+}
+
+template <int BM, int BN, int TN>
+void launch_f32(const ConvArgs &a, cudaStream_t st) {
+  dim3 grid((unsigned)((a.M + BM - 1) / BM), (unsigned)((a.Cout + BN - 1) / BN));
+  k_conv_f32<BM, BN, TN><<<grid, 256, 0, st>>>(a);
+}
+
+}  // namespace
+
+pg_status conv_f32(const ConvArgs &a, cudaStream_t st) {
+  if (a.M == 0) return PG_OK;
+  if (a.Cout == 1) {
+    k_conv_cout1<<<ceil_div(a.M, 256), 256, 0, st>>>(a);
+  } else if (a.Cout % 128 == 0) {
+    launch_f32<128, 128, 8>(a, st);
+  } else if (a.Cout == 64) {
+    launch_f32<256, 64, 8>(a, st);
+  } else if (a.Cout == 32) {
+    launch_f32<256, 32, 4>(a, st);
+  } else if (a.Cout == 16) {
+    launch_f32<256, 16, 2>(a, st);
+  } else {
+    return PG_ERR_UNSUPPORTED;
+  }
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
+pg_status net_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
+  if (prec != PG_FP32) return tc_prepare(ctx, net, prec);
+  return PG_OK;
+}
+
+static size_t act_floats_per_leaf(const Net *net, int H, int W) {
+  size_t HW = (size_t)H * W;
+  if (net->arch == 0) return HW * (8 + 2 * (size_t)net->widths[0]);
+  size_t c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
+  return HW * (8 + (c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;
+}
+
+pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m) {
+  const uint32_t A = h->A;
+  if (A == 0) return PG_OK;
+  const int H = h->H, W = h->W, HW = H * W;
+  const size_t elem = prec == PG_FP32 ? 4 : 2;
+  const size_t per_leaf = act_floats_per_leaf(net, H, W) * elem + 8 * (size_t)HW * 4;
+  // Activation working set: leaves are processed in chunks of at most ~6 GB.
+  uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(A, (6ull << 30) / per_leaf));
+  size_t bytes = per_leaf * chunk + 4096;
+  void *scratch;
+  PG_TRY(ctx_alloc(ctx, bytes, &scratch));
+  struct Guard {
+    pg_ctx *c; void *p; size_t b;
+    ~Guard() { ctx_free(c, p, b); }
+  } guard{ctx, scratch, bytes};
+  cudaStream_t st = ctx->stream;
+  for (uint32_t s0 = 0; s0 < A; s0 += chunk) {
+    uint32_t ns = std::min(chunk, A - s0);
+    float *x0 = (float *)scratch;  // FP32 input, 8 channels
+    size_t nx = (size_t)ns * HW;
+    k_assemble<<<ceil_div(nx, 256), 256, 0, st>>>(h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur,
+                                                  h->tot_prev, s0, ns, HW, x0);
+    PG_CUDA(cudaGetLastError());
+    uint8_t *act = (uint8_t *)scratch + align256(nx * 8 * 4);
+    float *y = m->y + (size_t)s0 * HW;
+    if (prec == PG_FP32) PG_TRY(forward_f32(net, x0, act, ns, H, W, y, st));
+    else PG_TRY(forward_tc(ctx, net, prec, x0, act, ns, H, W, y, st));
+  }
+  return PG_OK;
+}
+
+// Plain FP32 forward of one chunk: activations carved from `act`.
+pg_status forward_f32(const Net *net, const float *x0, void *actv, uint32_t ns, int H, int W, float *y,
+                      cudaStream_t st) {
+  float *act = (float *)actv;
+  const Layer *Ls = net->layers;
+  auto conv = [&](const Layer &L, const float *in, int in_cs, int in_co, int Hin, int Win, float *out, int out_cs,
+                  int out_co, int ups) -> pg_status {
+    ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = in; a.in_cs = in_cs; a.in_co = in_co; a.Hin = Hin; a.Win = Win; a.Cin = L.cin;
+    a.out = out; a.out_cs = out_cs; a.out_co = out_co;
+    a.Hout = Hin / L.stride; a.Wout = Win / L.stride; a.Cout = L.cout;
+    a.k = L.k; a.stride = L.stride; a.pad = L.k / 2;
+    a.w = L.w; a.bias = L.b; a.act = L.act; a.ups = ups;
+    a.M = (long)ns * a.Hout * a.Wout;
+    return conv_f32(a, st);
+  };
+  const size_t HW = (size_t)H * W;
+  if (net->arch == 0) {
+    int c = net->widths[0];
+    float *t0 = act, *t1 = act + ns * HW * c;
+    PG_TRY(conv(Ls[0], x0, 8, 0, H, W, t0, c, 0, 0));
+    PG_TRY(conv(Ls[1], t0, c, 0, H, W, t1, c, 0, 0));
+    PG_TRY(conv(Ls[2], t1, c, 0, H, W, y, 1, 0, 0));
+    return PG_OK;
+  }
+  const int c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
+  const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  float *cat0 = act;                               // [ns][H][W][c1+c0]   up(d1) | e0
+  float *t0 = cat0 + ns * HW * (c1 + c0);          // [ns][H][W][c0]
+  float *t0b = t0 + ns * HW * c0;                  // [ns][H][W][c0]
+  float *cat1 = t0b + ns * HW * c0;                // [ns][H1][W1][c2+c1] up(d2) | e1
+  float *t1 = cat1 + ns * HW / 4 * (c2 + c1);      // [ns][H1][W1][c1]
+  float *cat2 = t1 + ns * HW / 4 * c1;             // [ns][H2][W2][c3+c2] up(e3) | e2
+  float *t2 = cat2 + ns * HW / 16 * (c3 + c2);     // [ns][H2][W2][c2]
+  float *t3 = t2 + ns * HW / 16 * c2;              // [ns][H3][W3][c3]
+  const int k0c = c1 + c0, k1c = c2 + c1, k2c = c3 + c2;
+  // Encoder.
+  PG_TRY(conv(Ls[0], x0, 8, 0, H, W, t0, c0, 0, 0));
+  PG_TRY(conv(Ls[1], t0, c0, 0, H, W, cat0, k0c, c1, 0));          // e0
+  PG_TRY(conv(Ls[2], cat0, k0c, c1, H, W, t1, c1, 0, 0));          // stride 2
+  PG_TRY(conv(Ls[3], t1, c1, 0, H1, W1, cat1, k1c, c2, 0));        // e1
+  PG_TRY(conv(Ls[4], cat1, k1c, c2, H1, W1, t2, c2, 0, 0));        // stride 2
+  PG_TRY(conv(Ls[5], t2, c2, 0, H2, W2, cat2, k2c, c3, 0));        // e2
+  PG_TRY(conv(Ls[6], cat2, k2c, c3, H2, W2, t3, c3, 0, 0));        // stride 2
+  PG_TRY(conv(Ls[7], t3, c3, 0, H3, W3, cat2, k2c, 0, 1));         // up(e3)
+  // Decoder.
+  PG_TRY(conv(Ls[8], cat2, k2c, 0, H2, W2, t2, c2, 0, 0));
+  PG_TRY(conv(Ls[9], t2, c2, 0, H2, W2, cat1, k1c, 0, 1));         // up(d2)
+  PG_TRY(conv(Ls[10], cat1, k1c, 0, H1, W1, t1, c1, 0, 0));
+  PG_TRY(conv(Ls[11], t1, c1, 0, H1, W1, cat0, k0c, 0, 1));        // up(d1)
+  PG_TRY(conv(Ls[12], cat0, k0c, 0, H, W, t0, c0, 0, 0));
+  PG_TRY(conv(Ls[13], t0, c0, 0, H, W, t0b, c0, 0, 0));
+  PG_TRY(conv(Ls[14], t0b, c0, 0, H, W, y, 1, 0, 0));              // 1x1 head + softplus
+  return PG_OK;
+}
+
+}  // namespace pgi

@@ -1,0 +1,35 @@
+// Convolution launch descriptor and the per-precision forward passes.
+#pragma once
+
+#include "pg_internal.cuh"
+
+namespace pgi {
+
+// One convolution layer as an implicit GEMM.  Activations are channel-last;
+// `in_cs`/`out_cs` are the channel strides (elements per pixel) and
+// `in_co`/`out_co` the first channel used, so a layer can read or write a
+// channel slice of a concatenation buffer.  With `ups` set the output pixel
+// (y, x) is written to the four pixels (2y + {0,1}, 2x + {0,1}) of a map of
+// twice the size (nearest x2 upsampling folded into the store).
+struct ConvArgs {
+  const void *in;
+  int in_cs, in_co, Hin, Win, Cin;
+  void *out;
+  int out_cs, out_co, Hout, Wout, Cout;
+  int k, stride, pad;
+  const float *w;     // FP32 weights [K][Cout], K = k*k*Cin
+  const float *bias;  // [Cout]
+  long M;             // leaves x Hout x Wout
+  int act;            // 0 none, 1 ELU, 2 softplus
+  int ups;
+};
+
+pg_status conv_f32(const ConvArgs &a, cudaStream_t st);
+pg_status forward_f32(const Net *net, const float *x0, void *act, uint32_t ns, int H, int W, float *y,
+                      cudaStream_t st);
+// Tensor-core (tcgen05) forms.
+pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
+pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float *x0, void *act, uint32_t ns,
+                     int H, int W, float *y, cudaStream_t st);
+
+}  // namespace pgi

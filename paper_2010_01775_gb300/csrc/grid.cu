@@ -1,0 +1,505 @@
+// a1-a4: voxel location and the adaptive hierarchical grid (Sec. 7.1,
+// Algorithm 1 "Locate voxel j" / "Subdivide voxel j"), octree form.
+//
+//   k_morton        per photon: FP32 quantisation + Morton code (a1)
+//   k_sort_*        stable LSD radix sort of (code, index), 8-bit digits (a2):
+//                   upsweep digit histograms per 4096-key tile, per-digit scan
+//                   over tiles, then a scatter that ranks keys stably inside
+//                   the tile (warp match + per-warp digit counters), stages
+//                   them in shared memory and writes digit runs coalesced
+//   k_tree_*        top-down split of cells with count > threshold (a3): one
+//                   launch per level, 8 lanes per cell find the 7 child
+//                   boundaries by binary search inside the parent's range;
+//                   bottom-up leaf counts and top-down offsets put the leaves
+//                   in Morton order without sorting them
+//   k_leaf_assign   per photon: leaf id by binary search of leaf start codes (a4)
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pg_internal.cuh"
+
+namespace pgi {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys
+constexpr int kRadix = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr size_t kScatterSmem =
+    (size_t)kSortTile * 8 + (size_t)kSortTile * 4 + (size_t)kSortWarps * kRadix * 4 + 2 * kRadix * 4;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive block scan (blockDim a multiple of 32, <= 1024).  `sh` holds 32
+// words of shared scratch.  Returns this thread's exclusive prefix; *total is
+// the block sum.  Contains __syncthreads: call from all threads.
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t *total, uint32_t *sh) {
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t x = warp_incl_scan(v);
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < nw ? sh[lane] : 0u;
+    s = warp_incl_scan(s);
+    sh[lane] = s;
+  }
+  __syncthreads();
+  uint32_t prefix = (warp ? sh[warp - 1] : 0u) + x - v;
+  *total = sh[nw - 1];
+  __syncthreads();
+  return prefix;
+}
+
+__device__ __forceinline__ uint32_t lower_bound_u64(const uint64_t *__restrict__ a, uint32_t n, uint64_t key) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- a1
+__global__ void k_morton(const pg_photon *__restrict__ ph, uint32_t n, GridGeom g, uint64_t *__restrict__ codes,
+                         uint32_t *status) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 a = __ldg(reinterpret_cast<const float4 *>(ph + i));
+  uint32_t bad = 0;
+  codes[i] = position_code(g, a.x, a.y, a.z, bad);
+  if (bad) atomicOr(status, ST_INVALID_INPUT);
+}
+
+// ---------------------------------------------------------------- a2: radix sort
+__global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const uint64_t *__restrict__ keys, uint32_t n,
+                                                               int shift, uint32_t *__restrict__ hist,
+                                                               uint32_t nblocks) {
+  __shared__ uint32_t h[kRadix];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t base = blockIdx.x * kSortTile;
+  int lane = threadIdx.x & 31;
+#pragma unroll 4
+  for (int it = 0; it < kSortItems; ++it) {
+    uint32_t i = base + it * kSortThreads + threadIdx.x;
+    uint32_t d = i < n ? (uint32_t)(keys[i] >> shift) & 255u : 0xFFFFFFFFu;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d != 0xFFFFFFFFu && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// One block per digit: exclusive scan of that digit's tile counts, in place.
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t *__restrict__ hist, uint32_t nblocks,
+                                                    uint32_t *__restrict__ digit_total) {
+  __shared__ uint32_t sh[32];
+  uint32_t *row = hist + (size_t)blockIdx.x * nblocks;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < nblocks; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t v = i < nblocks ? row[i] : 0u, tot;
+    uint32_t p = block_excl_scan(v, &tot, sh);
+    if (i < nblocks) row[i] = carry + p;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
+}
+
+template <bool kFirst>
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *__restrict__ kin,
+                                                               const uint32_t *__restrict__ vin,
+                                                               uint64_t *__restrict__ kout,
+                                                               uint32_t *__restrict__ vout, uint32_t n, int shift,
+                                                               const uint32_t *__restrict__ hist,
+                                                               const uint32_t *__restrict__ digit_total,
+                                                               uint32_t nblocks) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *skey = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kSortTile);
+  uint32_t *whist = sval + kSortTile;       // [warp][digit]
+  uint32_t *tstart = whist + kSortWarps * kRadix;  // tile-local start of each digit run
+  uint32_t *gbase = tstart + kRadix;        // global position of this tile's run of each digit
+  __shared__ uint32_t sh[32];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t tile0 = blockIdx.x * kSortTile;
+  const uint32_t nvalid = min((uint32_t)kSortTile, n - tile0);
+
+  for (int i = tid; i < kSortWarps * kRadix; i += kSortThreads) whist[i] = 0;
+  {
+    uint32_t tot;
+    uint32_t dt = digit_total[tid];
+    uint32_t base = block_excl_scan(dt, &tot, sh);
+    gbase[tid] = base + hist[(size_t)tid * nblocks + blockIdx.x];
+  }
+  __syncthreads();
+
+  uint64_t key[kSortItems];
+  uint32_t val[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    uint32_t li = warp * (32 * kSortItems) + r * 32 + lane;
+    uint32_t gi = tile0 + li;
+    bool ok = li < nvalid;
+    key[r] = ok ? kin[gi] : ~0ull;
+    val[r] = ok ? (kFirst ? gi : vin[gi]) : 0u;
+    uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t before = __popc(peers & ((1u << lane) - 1u));
+    uint32_t b = whist[warp * kRadix + d];
+    rank[r] = b + before;
+    __syncwarp();
+    if (before == 0) whist[warp * kRadix + d] = b + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      uint32_t t = whist[w * kRadix + tid];
+      whist[w * kRadix + tid] = run;
+      run += t;
+    }
+    uint32_t tot;
+    tstart[tid] = block_excl_scan(run, &tot, sh);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+    uint32_t pos = tstart[d] + whist[warp * kRadix + d] + rank[r];
+    skey[pos] = key[r];
+    sval[pos] = val[r];
+  }
+  __syncthreads();
+  for (uint32_t p = tid; p < nvalid; p += kSortThreads) {
+    uint64_t k = skey[p];
+    uint32_t d = (uint32_t)(k >> shift) & 255u;
+    uint32_t g = gbase[d] + (p - tstart[d]);
+    kout[g] = k;
+    vout[g] = sval[p];
+  }
+}
+
+__global__ void k_iota(uint32_t *v, uint32_t n) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
+}
+
+// ---------------------------------------------------------------- a3: tree
+struct Tree {
+  uint64_t *code;    // cell prefix at its own depth
+  uint32_t *begin, *end;
+  int32_t *child;    // first of 8 children, or -1 for a leaf
+  uint32_t *nleaf;   // leaves in the subtree
+  uint32_t *off;     // Morton rank of the subtree's first leaf
+  uint32_t *level_start, *level_count;  // [17]
+  uint32_t *counters;  // [0] = L, [1] = A
+  uint32_t cap;
+};
+
+__global__ void k_tree_init(const uint64_t *__restrict__ sorted, uint32_t n, int D, int min_depth, Tree t) {
+  uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t ncell = 1u << (3 * min_depth);
+  if (c == 0) {
+    t.level_start[min_depth] = 0;
+    t.level_count[min_depth] = ncell;
+  }
+  if (c >= ncell) return;
+  int shift = 3 * (D - min_depth);
+  t.code[c] = c;
+  t.begin[c] = lower_bound_u64(sorted, n, (uint64_t)c << shift);
+  t.end[c] = (c + 1 == ncell) ? n : lower_bound_u64(sorted, n, (uint64_t)(c + 1) << shift);
+  t.child[c] = -1;
+}
+
+// Level d: a cell splits when count > thr and d < D.  Lanes 8j..8j+7 of a
+// warp serve one cell: lane k finds the first photon of child k.
+__global__ void k_tree_split(const uint64_t *__restrict__ sorted, int D, int d, uint32_t thr, Tree t,
+                             uint32_t *status) {
+  uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t rel = gid >> 3;
+  int k = gid & 7;
+  uint32_t cnt = t.level_count[d];
+  uint32_t lstart = t.level_start[d];
+  if (gid == 0) t.level_start[d + 1] = lstart + cnt;
+  bool in = rel < cnt;
+  uint32_t c = lstart + rel;
+  uint32_t b = 0, e = 0;
+  bool split = false;
+  uint64_t code = 0;
+  if (in) {
+    b = t.begin[c];
+    e = t.end[c];
+    code = t.code[c];
+    split = (e - b > thr) && d < D;
+  }
+  uint32_t base = 0xFFFFFFFFu;
+  if (split && k == 0) {
+    uint32_t slot = atomicAdd(&t.level_count[d + 1], 8u);
+    base = lstart + cnt + slot;
+    if (base + 8 > t.cap) {
+      atomicOr(status, ST_CAPACITY);
+      base = 0xFFFFFFFFu;
+    }
+  }
+  int lane = threadIdx.x & 31, group0 = lane & ~7;
+  base = __shfl_sync(0xFFFFFFFFu, base, group0);
+  uint32_t cb = b;
+  uint64_t ccode = code * 8 + (uint64_t)k;
+  if (split && base != 0xFFFFFFFFu && k > 0)
+    cb = b + lower_bound_u64(sorted + b, e - b, ccode << (3 * (D - d - 1)));
+  uint32_t ce = __shfl_down_sync(0xFFFFFFFFu, cb, 1);
+  if (k == 7) ce = e;
+  if (!in) return;
+  if (k == 0) t.child[c] = (split && base != 0xFFFFFFFFu) ? (int32_t)base : -1;
+  if (split && base != 0xFFFFFFFFu) {
+    t.code[base + k] = ccode;
+    t.begin[base + k] = cb;
+    t.end[base + k] = ce;
+    t.child[base + k] = -1;
+  }
+}
+
+__global__ void k_tree_count(int d, Tree t) {
+  uint32_t rel = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rel >= t.level_count[d]) return;
+  uint32_t c = t.level_start[d] + rel;
+  int32_t ch = t.child[c];
+  uint32_t s = 1;
+  if (ch >= 0) {
+    s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += t.nleaf[ch + k];
+  }
+  t.nleaf[c] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_tree_root_offsets(int min_depth, Tree t) {
+  __shared__ uint32_t sh[32];
+  uint32_t ncell = 1u << (3 * min_depth), carry = 0;
+  for (uint32_t base = 0; base < ncell; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x, tot;
+    uint32_t v = i < ncell ? t.nleaf[i] : 0u;
+    uint32_t p = block_excl_scan(v, &tot, sh);
+    if (i < ncell) t.off[i] = carry + p;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) t.counters[0] = carry;
+}
+
+__global__ void k_tree_offsets(int D, int d, Tree t, uint64_t *__restrict__ leaf_code,
+                               int32_t *__restrict__ leaf_depth, uint32_t *__restrict__ leaf_begin,
+                               uint32_t *__restrict__ leaf_end) {
+  uint32_t rel = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rel >= t.level_count[d]) return;
+  uint32_t c = t.level_start[d] + rel;
+  int32_t ch = t.child[c];
+  uint32_t o = t.off[c];
+  if (ch >= 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      t.off[ch + k] = o;
+      o += t.nleaf[ch + k];
+    }
+  } else {
+    leaf_code[o] = t.code[c] << (3 * (D - d));
+    leaf_depth[o] = d;
+    leaf_begin[o] = t.begin[c];
+    leaf_end[o] = t.end[c];
+  }
+}
+
+// Active leaves (>= 1 photon) get consecutive map slots in leaf order.
+__global__ void __launch_bounds__(1024) k_active(Tree t, const uint32_t *__restrict__ leaf_begin,
+                                                 const uint32_t *__restrict__ leaf_end, uint32_t *__restrict__ active,
+                                                 int32_t *__restrict__ slot_of_leaf) {
+  __shared__ uint32_t sh[32];
+  uint32_t L = t.counters[0], carry = 0;
+  for (uint32_t base = 0; base < L; base += blockDim.x) {
+    uint32_t l = base + threadIdx.x, tot;
+    uint32_t f = (l < L && leaf_end[l] > leaf_begin[l]) ? 1u : 0u;
+    uint32_t p = block_excl_scan(f, &tot, sh);
+    if (l < L) {
+      slot_of_leaf[l] = f ? (int32_t)(carry + p) : -1;
+      if (f) active[carry + p] = l;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) t.counters[1] = carry;
+}
+
+// ---------------------------------------------------------------- a4
+__global__ void k_leaf_assign(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ perm, uint32_t n,
+                              const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ counters,
+                              uint32_t *__restrict__ leaf_of) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t L = counters[0];
+  leaf_of[perm[i]] = find_leaf(leaf_code, L, sorted[i]);
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_grid_params *p, Grid *g) {
+  cudaStream_t st = ctx->stream;
+  const uint32_t n = (uint32_t)n64;
+  const int D = p->max_depth, dmin = p->min_depth;
+  const uint32_t thr = p->split_threshold;
+  g->n = n;
+  g->D = D;
+  g->min_depth = dmin;
+  g->thr = thr;
+  for (int a = 0; a < 3; ++a) {
+    g->lo[a] = p->lo[a];
+    g->hi[a] = p->hi[a];
+    g->scale[a] = (float)(ldexp(1.0, D) / ((double)p->hi[a] - (double)p->lo[a]));
+  }
+  // Cell capacity: split cells of one level are disjoint and hold > thr
+  // photons each, so each level below min_depth adds at most 8 n/(thr+1).
+  uint64_t per_level = 8ull * (n / ((uint64_t)thr + 1ull));
+  uint64_t cap = 1ull << (3 * dmin), lvl = cap;
+  std::vector<uint64_t> bound(D + 2, 0);
+  bound[dmin] = lvl;
+  for (int d = dmin + 1; d <= D; ++d) {
+    uint64_t full = lvl * 8;
+    lvl = full < per_level ? full : per_level;
+    bound[d] = lvl;
+    cap += lvl;
+  }
+  if (cap >= (1ull << 31)) return PG_ERR_UNSUPPORTED;
+
+  // Handle block.
+  size_t b_codes = align256(8ull * n), b_perm = align256(4ull * n), b_lo = align256(4ull * n);
+  size_t b_lc = align256(8 * cap), b_l4 = align256(4 * cap);
+  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4;
+  PG_TRY(ctx_alloc(ctx, g->h.bytes, &g->block));
+  uint8_t *q = (uint8_t *)g->block;
+  g->codes = (uint64_t *)q; q += b_codes;
+  g->perm = (uint32_t *)q; q += b_perm;
+  g->leaf_of = (uint32_t *)q; q += b_lo;
+  g->leaf_code = (uint64_t *)q; q += b_lc;
+  g->leaf_depth = (int32_t *)q; q += b_l4;
+  g->leaf_begin = (uint32_t *)q; q += b_l4;
+  g->leaf_end = (uint32_t *)q; q += b_l4;
+  g->active = (uint32_t *)q; q += b_l4;
+  g->slot_of_leaf = (int32_t *)q;
+
+  // Scratch: sort ping-pong, digit histograms, cells.
+  const int passes = (3 * D + 7) / 8;
+  const uint32_t nblocks = n ? ceil_div(n, kSortTile) : 0;
+  size_t s_k = align256(8ull * n), s_v = align256(4ull * n), s_h = align256(4ull * kRadix * (nblocks + 1));
+  size_t s_dt = align256(4 * kRadix), s_c8 = align256(8 * cap), s_c4 = align256(4 * cap), s_lv = align256(4 * 64);
+  size_t scratch_bytes = 2 * s_k + s_v + s_h + s_dt + s_c8 + 5 * s_c4 + s_lv;
+  void *scratch = nullptr;
+  pg_status rs = ctx_alloc(ctx, scratch_bytes, &scratch);
+  if (rs != PG_OK) return rs;
+  struct Guard {
+    pg_ctx *c; void *p; size_t b;
+    ~Guard() { ctx_free(c, p, b); }
+  } guard{ctx, scratch, scratch_bytes};
+  q = (uint8_t *)scratch;
+  uint64_t *kA = (uint64_t *)q; q += s_k;
+  uint64_t *kB = (uint64_t *)q; q += s_k;
+  uint32_t *vT = (uint32_t *)q; q += s_v;
+  uint32_t *hist = (uint32_t *)q; q += s_h;
+  uint32_t *dtot = (uint32_t *)q; q += s_dt;
+  Tree t;
+  t.code = (uint64_t *)q; q += s_c8;
+  t.begin = (uint32_t *)q; q += s_c4;
+  t.end = (uint32_t *)q; q += s_c4;
+  t.child = (int32_t *)q; q += s_c4;
+  t.nleaf = (uint32_t *)q; q += s_c4;
+  t.off = (uint32_t *)q; q += s_c4;
+  t.level_start = (uint32_t *)q;
+  t.level_count = t.level_start + 20;
+  t.counters = t.level_count + 20;
+  t.cap = (uint32_t)cap;
+  PG_CUDA(cudaMemsetAsync(t.level_start, 0, 4 * 64, st));
+
+  GridGeom gg = geom_of(g);
+  const int TB = 256;
+  if (n) k_morton<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, gg, g->codes, ctx->d_status);
+
+  // a2: stable LSD radix sort; the final permutation lands in g->perm.
+  const uint64_t *sorted = g->codes;
+  if (n && passes == 0) {
+    k_iota<<<ceil_div(n, TB), TB, 0, st>>>(g->perm, n);
+  } else if (n) {
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    // Value buffers alternate so that the last pass writes g->perm.
+    const uint64_t *kin = g->codes;
+    const uint32_t *vin = nullptr;
+    for (int ps = 0; ps < passes; ++ps) {
+      uint64_t *kout = (ps & 1) ? kB : kA;
+      uint32_t *vout = ((passes - 1 - ps) & 1) ? vT : g->perm;
+      int shift = 8 * ps;
+      k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks);
+      k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot);
+      if (ps == 0)
+        k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist, dtot,
+                                                                          nblocks);
+      else
+        k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                           dtot, nblocks);
+      kin = kout;
+      vin = vout;
+    }
+    sorted = kin;
+  }
+
+  // a3: tree, level by level.
+  {
+    uint32_t ncell0 = 1u << (3 * dmin);
+    k_tree_init<<<ceil_div(ncell0, TB), TB, 0, st>>>(sorted, n, D, dmin, t);
+    // Levels whose cell bound is zero cannot hold cells (no launch).
+    for (int d = dmin; d <= D && bound[d]; ++d) {
+      uint64_t threads = 8 * bound[d];
+      k_tree_split<<<ceil_div(threads, TB), TB, 0, st>>>(sorted, D, d, thr, t, ctx->d_status);
+    }
+    for (int d = D; d >= dmin; --d)
+      if (bound[d]) k_tree_count<<<ceil_div(bound[d], TB), TB, 0, st>>>(d, t);
+    k_tree_root_offsets<<<1, 1024, 0, st>>>(dmin, t);
+    for (int d = dmin; d <= D && bound[d]; ++d)
+      k_tree_offsets<<<ceil_div(bound[d], TB), TB, 0, st>>>(D, d, t, g->leaf_code, g->leaf_depth, g->leaf_begin,
+                                                             g->leaf_end);
+    k_active<<<1, 1024, 0, st>>>(t, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf);
+  }
+  // a4: leaf of every photon.
+  if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of);
+  PG_CUDA(cudaGetLastError());
+
+  uint32_t hc[2];
+  PG_CUDA(cudaMemcpyAsync(hc, t.counters, 8, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaStreamSynchronize(st));
+  uint32_t status = 0;
+  PG_CUDA(cudaMemcpy(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost));
+  if (status & ST_CAPACITY) return PG_ERR_UNSUPPORTED;
+  if (status & ST_INVALID_INPUT) {
+    PG_CUDA(cudaMemset(ctx->d_status, 0, 4));
+    return PG_ERR_INVALID_INPUT;
+  }
+  g->L = hc[0];
+  g->A = hc[1];
+  return PG_OK;
+}
+
+}  // namespace pgi

@@ -1,0 +1,598 @@
+// C-ABI entry points of libpg: argument checks, host/device staging, handle
+// lifetime and the HBM budget.  Every compute step is a kernel launched by
+// the per-step files (grid.cu, splat.cu, cnn.cu, cdf.cu, sample.cu).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "pg_internal.cuh"
+
+namespace pgi {
+
+cudaError_t &last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (ctx->budget && ctx->in_use + bytes > ctx->budget) return PG_ERR_OOM;
+  cudaError_t e = cudaMallocAsync(ptr, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return PG_ERR_OOM;
+  }
+  ctx->in_use += bytes;
+  return PG_OK;
+}
+
+void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes) {
+  if (!ptr) return;
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  cudaFreeAsync(ptr, ctx->stream);
+  ctx->in_use = ctx->in_use >= bytes ? ctx->in_use - bytes : 0;
+}
+
+// Boundary rays of the W phi sectors: (float cos, float sin) of 2 pi j / W,
+// exactly (1,0), (0,1), (-1,0), (0,-1) on the quarter turns.
+pg_status phi_table(pg_ctx *ctx, int W, const float **d_table) {
+  int lg = 0;
+  while ((1 << lg) < W) ++lg;
+  if ((1 << lg) != W || lg > 8) return PG_ERR_NOT_POW2;
+  if (!ctx->d_phi[lg]) {
+    float host[512];
+    for (int j = 0; j < W; ++j) {
+      float c, s;
+      if ((4 * j) % W == 0) {
+        static const float cq[4] = {1.0f, 0.0f, -1.0f, 0.0f}, sq[4] = {0.0f, 1.0f, 0.0f, -1.0f};
+        c = cq[(4 * j) / W];
+        s = sq[(4 * j) / W];
+      } else {
+        double th = 2.0 * M_PI * (double)j / (double)W;
+        c = (float)cos(th);
+        s = (float)sin(th);
+      }
+      host[j] = c;
+      host[W + j] = s;
+    }
+    float *d = nullptr;
+    PG_CUDA(cudaMalloc(&d, sizeof(float) * 2 * W));
+    PG_CUDA(cudaMemcpy(d, host, sizeof(float) * 2 * W, cudaMemcpyHostToDevice));
+    ctx->d_phi[lg] = d;
+  }
+  *d_table = ctx->d_phi[lg];
+  return PG_OK;
+}
+
+// A caller array that may live on the host: device arrays are used in place,
+// host arrays are copied through a device buffer on the context stream.
+struct Staged {
+  pg_ctx *ctx = nullptr;
+  void *dev = nullptr;
+  void *host = nullptr;
+  size_t bytes = 0;
+  bool owned = false, out = false;
+  ~Staged() {
+    if (owned) ctx_free(ctx, dev, bytes);
+  }
+};
+
+static pg_status classify(const void *p, bool *on_device) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PG_ERR_NOT_DEVICE_PTR;
+  }
+  *on_device = (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+  return PG_OK;
+}
+
+static pg_status stage_in(pg_ctx *ctx, const void *p, size_t bytes, Staged &s) {
+  bool dev;
+  PG_TRY(classify(p, &dev));
+  s.ctx = ctx;
+  s.bytes = bytes;
+  if (dev) {
+    s.dev = const_cast<void *>(p);
+    return PG_OK;
+  }
+  PG_TRY(ctx_alloc(ctx, bytes, &s.dev));
+  s.owned = true;
+  PG_CUDA(cudaMemcpyAsync(s.dev, p, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  return PG_OK;
+}
+
+static pg_status stage_out(pg_ctx *ctx, void *p, size_t bytes, Staged &s) {
+  if (!p) return PG_OK;
+  bool dev;
+  PG_TRY(classify(p, &dev));
+  s.ctx = ctx;
+  s.bytes = bytes;
+  if (dev) {
+    s.dev = p;
+    return PG_OK;
+  }
+  PG_TRY(ctx_alloc(ctx, bytes, &s.dev));
+  s.owned = true;
+  s.out = true;
+  s.host = p;
+  return PG_OK;
+}
+
+static pg_status finish_out(Staged &s) {
+  if (s.owned && s.out) PG_CUDA(cudaMemcpyAsync(s.host, s.dev, s.bytes, cudaMemcpyDeviceToHost, s.ctx->stream));
+  return PG_OK;
+}
+
+static bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+template <class T>
+static T *as(const void *h, uint32_t kind) {
+  if (!h) return nullptr;
+  const Handle *b = static_cast<const Handle *>(h);
+  return b->kind == kind ? (T *)h : nullptr;
+}
+
+}  // namespace pgi
+
+using namespace pgi;
+
+extern "C" {
+
+const char *pg_status_string(pg_status s) {
+  switch (s) {
+    case PG_OK: return "ok";
+    case PG_ERR_INVALID_ARG: return "invalid argument";
+    case PG_ERR_NOT_DEVICE_PTR: return "pointer not classifiable by the CUDA runtime";
+    case PG_ERR_OOM: return "out of device memory or over the HBM budget";
+    case PG_ERR_OVERFLOW: return "fixed-point photon power overflow";
+    case PG_ERR_NOT_POW2: return "histogram size not a supported power of two";
+    case PG_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PG_ERR_CUDA: return cudaGetErrorString(last_cuda_error());
+    case PG_ERR_INVALID_INPUT: return "non-finite position/direction or negative photon power";
+    case PG_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+pg_status pg_create(pg_ctx **out, void *stream, size_t budget) {
+  if (!out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  pg_ctx *c = new (std::nothrow) pg_ctx();
+  if (!c) return PG_ERR_OOM;
+  memset(c, 0, sizeof(*c));
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return PG_ERR_CUDA;
+  }
+  c->stream = (cudaStream_t)stream;
+  c->budget = budget;
+  if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
+    delete c;
+    return PG_ERR_CUDA;
+  }
+  *out = c;
+  return PG_OK;
+}
+
+pg_status pg_destroy(pg_ctx *c) {
+  if (!c) return PG_OK;
+  cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < 9; ++i)
+    if (c->d_phi[i]) cudaFree(c->d_phi[i]);
+  cudaFree(c->d_status);
+  delete c;
+  return PG_OK;
+}
+
+pg_status pg_set_stream(pg_ctx *c, void *stream) {
+  if (!c) return PG_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)stream;
+  return PG_OK;
+}
+
+pg_status pg_sync(pg_ctx *c) {
+  if (!c) return PG_ERR_INVALID_ARG;
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  uint32_t st = 0;
+  PG_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  PG_CUDA(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+  if (st & ST_INVALID_INPUT) return PG_ERR_INVALID_INPUT;
+  if (st & ST_OVERFLOW) return PG_ERR_OVERFLOW;
+  if (st & ST_TIMEOUT) return PG_ERR_TIMEOUT;
+  if (st & ST_CAPACITY) return PG_ERR_UNSUPPORTED;
+  return PG_OK;
+}
+
+pg_status pg_bytes_in_use(const pg_ctx *c, uint64_t *bytes) {
+  if (!c || !bytes) return PG_ERR_INVALID_ARG;
+  *bytes = c->in_use;
+  return PG_OK;
+}
+
+pg_status pg_build_grid(pg_ctx *c, const pg_photon *d_ph, uint64_t n, const pg_grid_params *p, pg_grid **out) {
+  if (!c || !p || !out || (n && !d_ph)) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n >= (1ull << 31)) return PG_ERR_UNSUPPORTED;
+  if (p->max_depth < 0 || p->max_depth > 16 || p->min_depth < 0 || p->min_depth > 6 ||
+      p->min_depth > p->max_depth)
+    return PG_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->lo[a]) || !isfinite(p->hi[a]) || !(p->hi[a] > p->lo[a])) return PG_ERR_INVALID_ARG;
+  Staged ph;
+  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
+  Grid *g = new (std::nothrow) Grid();
+  if (!g) return PG_ERR_OOM;
+  memset(g, 0, sizeof(*g));
+  g->h.kind = KIND_GRID;
+  g->h.ctx = c;
+  pg_status s = build_grid(c, (const pg_photon *)ph.dev, n, p, g);
+  if (s != PG_OK) {
+    if (g->block) ctx_free(c, g->block, g->h.bytes);
+    delete g;
+    return s;
+  }
+  *out = (pg_grid *)g;
+  return PG_OK;
+}
+
+pg_status pg_splat_photons(pg_ctx *c, const pg_grid *grid, const pg_photon *d_ph, uint64_t n, uint64_t n_prev,
+                           int H, int W, int F, pg_hist **out) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  if (!c || !g || !out || (n && !d_ph)) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n != g->n || n_prev > n || F < 0 || F > 62) return PG_ERR_INVALID_ARG;
+  if (!pow2_in(H, 4, 256) || !pow2_in(W, 4, 256) || H * W > 16384) return PG_ERR_NOT_POW2;
+  Staged ph;
+  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
+  Hist *h = new (std::nothrow) Hist();
+  if (!h) return PG_ERR_OOM;
+  memset(h, 0, sizeof(*h));
+  h->h.kind = KIND_HIST;
+  h->h.ctx = c;
+  h->A = g->A;
+  h->H = H;
+  h->W = W;
+  pg_status s = splat(c, g, (const pg_photon *)ph.dev, n, n_prev, F, h);
+  if (s != PG_OK) {
+    if (h->block) ctx_free(c, h->block, h->h.bytes);
+    delete h;
+    return s;
+  }
+  *out = (pg_hist *)h;
+  return PG_OK;
+}
+
+pg_status pg_net_load(pg_ctx *c, const void *blob, size_t bytes, pg_net **out) {
+  if (!c || !blob || !out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  const uint8_t *b = (const uint8_t *)blob;
+  if (bytes < 40) return PG_ERR_INVALID_ARG;
+  uint32_t hdr[8];
+  memcpy(hdr, b, 32);
+  if (hdr[0] != 0x314E4750u || hdr[2] != 5u) return PG_ERR_INVALID_ARG;
+  uint32_t arch = hdr[1], nl = hdr[3];
+  static const int expect_layers[2] = {3, 15};
+  if (arch > 1 || nl != (uint32_t)expect_layers[arch]) return PG_ERR_UNSUPPORTED;
+  Net *net = new (std::nothrow) Net();
+  if (!net) return PG_ERR_OOM;
+  memset(net, 0, sizeof(*net));
+  net->h.kind = KIND_NET;
+  net->h.ctx = c;
+  net->arch = (int)arch;
+  net->n_layers = (int)nl;
+  for (int i = 0; i < 4; ++i) net->widths[i] = (int)hdr[4 + i];
+  // First pass: parse descriptors and size the device block.
+  size_t off = 40, total = 0;
+  for (uint32_t l = 0; l < nl; ++l) {
+    if (off + 24 > bytes) { delete net; return PG_ERR_INVALID_ARG; }
+    uint32_t d[6];
+    memcpy(d, b + off, 24);
+    off += 24;
+    Layer &L = net->layers[l];
+    L.cout = (int)d[0]; L.cin = (int)d[1]; L.k = (int)d[2]; L.stride = (int)d[3]; L.act = (int)d[4];
+    if (L.cout <= 0 || L.cin <= 0 || (L.k != 1 && L.k != 3) || (L.stride != 1 && L.stride != 2) || L.act > 2) {
+      delete net;
+      return PG_ERR_INVALID_ARG;
+    }
+    size_t nw = (size_t)L.cout * L.k * L.k * L.cin;
+    if (off + 4 * (nw + L.cout) > bytes) { delete net; return PG_ERR_INVALID_ARG; }
+    off += 4 * (nw + L.cout);
+    // The 5-channel network input is stored with 8 channels (3 zero), so the
+    // first layer's weights are padded to 8 input channels.
+    size_t cin_eff = (l == 0 && L.cin == 5) ? 8 : (size_t)L.cin;
+    size_t nw_eff = (size_t)L.cout * L.k * L.k * cin_eff;
+    total += ((4 * nw_eff + 255) & ~(size_t)255) + ((4 * (size_t)L.cout + 255) & ~(size_t)255);
+  }
+  void *block = nullptr;
+  pg_status s = ctx_alloc(c, total, &block);
+  if (s != PG_OK) { delete net; return s; }
+  net->block = block;
+  net->h.bytes = total;
+  // Second pass: transpose [cout][k][k][cin] to the GEMM layout [k*k*cin][cout].
+  off = 40;
+  uint8_t *dst = (uint8_t *)block;
+  for (uint32_t l = 0; l < nl; ++l) {
+    Layer &L = net->layers[l];
+    off += 24;
+    const int cin = L.cin, cin_eff = (l == 0 && L.cin == 5) ? 8 : L.cin;
+    const size_t taps = (size_t)L.k * L.k, K = taps * cin, Ke = taps * cin_eff;
+    const size_t nw = K * L.cout, nwe = Ke * L.cout;
+    float *tw = (float *)calloc(nwe, 4);
+    if (!tw) { pg_free(net); return PG_ERR_OOM; }
+    const float *src = (const float *)(b + off);
+    for (int o = 0; o < L.cout; ++o)
+      for (size_t t = 0; t < taps; ++t)
+        for (int i = 0; i < cin; ++i) {
+          float v;
+          memcpy(&v, src + (size_t)o * K + t * cin + i, 4);
+          tw[(t * cin_eff + i) * L.cout + o] = v;
+        }
+    L.cin = cin_eff;
+    L.w = (float *)dst;
+    cudaError_t e = cudaMemcpyAsync(L.w, tw, 4 * nwe, cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    free(tw);
+    if (e != cudaSuccess) { last_cuda_error() = e; pg_free(net); return PG_ERR_CUDA; }
+    dst += (4 * nwe + 255) & ~(size_t)255;
+    off += 4 * nw;
+    L.b = (float *)dst;
+    e = cudaMemcpyAsync(L.b, b + off, 4 * (size_t)L.cout, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) { last_cuda_error() = e; pg_free(net); return PG_ERR_CUDA; }
+    dst += (4 * (size_t)L.cout + 255) & ~(size_t)255;
+    off += 4 * (size_t)L.cout;
+  }
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  *out = (pg_net *)net;
+  return PG_OK;
+}
+
+pg_status pg_reconstruct(pg_ctx *c, const pg_hist *hist, const pg_net *netp, pg_precision prec, pg_map **out) {
+  const Hist *h = as<Hist>(hist, KIND_HIST);
+  Net *net = as<Net>(netp, KIND_NET);
+  if (!c || !h || !net || !out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
+  if (net->arch == 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
+  PG_TRY(net_prepare(c, net, prec));
+  Map *m = new (std::nothrow) Map();
+  if (!m) return PG_ERR_OOM;
+  memset(m, 0, sizeof(*m));
+  m->h.kind = KIND_MAP;
+  m->h.ctx = c;
+  m->A = h->A;
+  m->H = h->H;
+  m->W = h->W;
+  m->h.bytes = (size_t)m->A * h->H * h->W * sizeof(float);
+  pg_status s = ctx_alloc(c, m->h.bytes, &m->block);
+  if (s == PG_OK) {
+    m->y = (float *)m->block;
+    s = reconstruct(c, h, net, prec, m);
+  }
+  if (s != PG_OK) {
+    if (m->block) ctx_free(c, m->block, m->h.bytes);
+    delete m;
+    return s;
+  }
+  *out = (pg_map *)m;
+  return PG_OK;
+}
+
+pg_status pg_map_import(pg_ctx *c, const float *d_y, uint64_t n_maps, int H, int W, pg_map **out) {
+  if (!c || !out || (n_maps && !d_y)) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!pow2_in(H, 4, 256) || !pow2_in(W, 4, 256) || H * W > 16384) return PG_ERR_NOT_POW2;
+  if (n_maps >= (1ull << 31)) return PG_ERR_UNSUPPORTED;
+  Map *m = new (std::nothrow) Map();
+  if (!m) return PG_ERR_OOM;
+  memset(m, 0, sizeof(*m));
+  m->h.kind = KIND_MAP;
+  m->h.ctx = c;
+  m->A = (uint32_t)n_maps;
+  m->H = H;
+  m->W = W;
+  m->h.bytes = (size_t)n_maps * H * W * sizeof(float);
+  pg_status s = ctx_alloc(c, m->h.bytes, &m->block);
+  if (s != PG_OK) { delete m; return s; }
+  m->y = (float *)m->block;
+  if (n_maps) {
+    cudaError_t e = cudaMemcpyAsync(m->y, d_y, m->h.bytes, cudaMemcpyDefault, c->stream);
+    if (e != cudaSuccess) { last_cuda_error() = e; pg_free(m); return PG_ERR_CUDA; }
+  }
+  *out = (pg_map *)m;
+  return PG_OK;
+}
+
+pg_status pg_build_cdf(pg_ctx *c, const pg_map *map, pg_tables **out) {
+  const Map *m = as<Map>(map, KIND_MAP);
+  if (!c || !m || !out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  Tables *t = new (std::nothrow) Tables();
+  if (!t) return PG_ERR_OOM;
+  memset(t, 0, sizeof(*t));
+  t->h.kind = KIND_TABLES;
+  t->h.ctx = c;
+  t->A = m->A;
+  t->H = m->H;
+  t->W = m->W;
+  size_t HW = (size_t)m->H * m->W, A = m->A;
+  size_t bP = (A * HW * 4 + 255) & ~(size_t)255, bz = (A * m->H * 4 + 255) & ~(size_t)255;
+  t->h.bytes = 2 * bP + bz + ((A + 255) & ~(size_t)255);
+  pg_status s = ctx_alloc(c, t->h.bytes, &t->block);
+  if (s != PG_OK) { delete t; return s; }
+  uint8_t *p = (uint8_t *)t->block;
+  t->P = (float *)p;
+  t->cdf_phi = (float *)(p + bP);
+  t->cdf_z = (float *)(p + 2 * bP);
+  t->valid = p + 2 * bP + bz;
+  s = build_cdf(c, m, t);
+  if (s != PG_OK) { pg_free(t); return s; }
+  *out = (pg_tables *)t;
+  return PG_OK;
+}
+
+pg_status pg_sample_dirs(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const float *d_pos, uint64_t q,
+                         uint64_t seed, uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf,
+                         uint32_t *d_bin) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  const Tables *t = as<Tables>(tab, KIND_TABLES);
+  if (!c || !g || !t || (q && (!d_pos || !d_dir || !d_pdf || !d_leaf))) return PG_ERR_INVALID_ARG;
+  if (t->A != g->A) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  Staged pos, dir, pdf, leaf, bin;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_out(c, d_dir, q * 12, dir));
+  PG_TRY(stage_out(c, d_pdf, q * 4, pdf));
+  PG_TRY(stage_out(c, d_leaf, q * 4, leaf));
+  if (d_bin) PG_TRY(stage_out(c, d_bin, q * 4, bin));
+  PG_TRY(sample(c, g, t, (const float *)pos.dev, q, seed, stream_id, (float *)dir.dev, (float *)pdf.dev,
+                (uint32_t *)leaf.dev, d_bin ? (uint32_t *)bin.dev : nullptr));
+  PG_TRY(finish_out(dir));
+  PG_TRY(finish_out(pdf));
+  PG_TRY(finish_out(leaf));
+  if (d_bin) PG_TRY(finish_out(bin));
+  return PG_OK;
+}
+
+pg_status pg_eval_pdf(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const float *d_pos, const float *d_dir,
+                      uint64_t q, float *d_pdf) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  const Tables *t = as<Tables>(tab, KIND_TABLES);
+  if (!c || !g || !t || (q && (!d_pos || !d_dir || !d_pdf))) return PG_ERR_INVALID_ARG;
+  if (t->A != g->A) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  Staged pos, dir, pdf;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_in(c, d_dir, q * 12, dir));
+  PG_TRY(stage_out(c, d_pdf, q * 4, pdf));
+  PG_TRY(eval_pdf(c, g, t, (const float *)pos.dev, (const float *)dir.dev, q, (float *)pdf.dev));
+  PG_TRY(finish_out(pdf));
+  return PG_OK;
+}
+
+pg_status pg_info(const void *handle, int what, uint64_t *v) {
+  if (!handle || !v) return PG_ERR_INVALID_ARG;
+  const Handle *b = (const Handle *)handle;
+  switch (b->kind) {
+    case KIND_GRID: {
+      const Grid *g = (const Grid *)handle;
+      if (what == PG_INFO_N_PHOTONS) *v = g->n;
+      else if (what == PG_INFO_N_LEAVES) *v = g->L;
+      else if (what == PG_INFO_N_ACTIVE) *v = g->A;
+      else if (what == PG_INFO_MAX_DEPTH) *v = (uint64_t)g->D;
+      else if (what == PG_INFO_BYTES) *v = b->bytes;
+      else return PG_ERR_INVALID_ARG;
+      return PG_OK;
+    }
+    case KIND_HIST: case KIND_MAP: case KIND_TABLES: {
+      uint32_t A; int H, W;
+      if (b->kind == KIND_HIST) { const Hist *h = (const Hist *)handle; A = h->A; H = h->H; W = h->W; }
+      else if (b->kind == KIND_MAP) { const Map *m = (const Map *)handle; A = m->A; H = m->H; W = m->W; }
+      else { const Tables *t = (const Tables *)handle; A = t->A; H = t->H; W = t->W; }
+      if (what == PG_INFO_N_ACTIVE) *v = A;
+      else if (what == PG_INFO_H) *v = (uint64_t)H;
+      else if (what == PG_INFO_W) *v = (uint64_t)W;
+      else if (what == PG_INFO_BYTES) *v = b->bytes;
+      else return PG_ERR_INVALID_ARG;
+      return PG_OK;
+    }
+    case KIND_NET:
+      if (what == PG_INFO_BYTES) { *v = b->bytes; return PG_OK; }
+      return PG_ERR_INVALID_ARG;
+  }
+  return PG_ERR_INVALID_ARG;
+}
+
+pg_status pg_export(pg_ctx *c, const void *handle, int what, void *dst, size_t bytes) {
+  if (!c || !handle || (bytes && !dst)) return PG_ERR_INVALID_ARG;
+  const Handle *b = (const Handle *)handle;
+  const void *src = nullptr;
+  size_t need = 0;
+  if (b->kind == KIND_GRID) {
+    const Grid *g = (const Grid *)handle;
+    switch (what) {
+      case PG_GRID_CODES: src = g->codes; need = g->n * 8; break;
+      case PG_GRID_PERM: src = g->perm; need = g->n * 4; break;
+      case PG_GRID_LEAF_OF: src = g->leaf_of; need = g->n * 4; break;
+      case PG_GRID_LEAF_CODE: src = g->leaf_code; need = (size_t)g->L * 8; break;
+      case PG_GRID_LEAF_DEPTH: src = g->leaf_depth; need = (size_t)g->L * 4; break;
+      case PG_GRID_LEAF_BEGIN: src = g->leaf_begin; need = (size_t)g->L * 4; break;
+      case PG_GRID_LEAF_END: src = g->leaf_end; need = (size_t)g->L * 4; break;
+      case PG_GRID_ACTIVE: src = g->active; need = (size_t)g->A * 4; break;
+      case PG_GRID_SLOT_OF_LEAF: src = g->slot_of_leaf; need = (size_t)g->L * 4; break;
+      default: return PG_ERR_INVALID_ARG;
+    }
+  } else if (b->kind == KIND_HIST) {
+    const Hist *h = (const Hist *)handle;
+    size_t n = (size_t)h->A * h->H * h->W;
+    switch (what) {
+      case PG_HIST_POW_CUR: src = h->pow_cur; need = n * 8; break;
+      case PG_HIST_CNT_CUR: src = h->cnt_cur; need = n * 4; break;
+      case PG_HIST_POW_PREV: src = h->pow_prev; need = n * 8; break;
+      case PG_HIST_CNT_PREV: src = h->cnt_prev; need = n * 4; break;
+      default: return PG_ERR_INVALID_ARG;
+    }
+  } else if (b->kind == KIND_MAP) {
+    const Map *m = (const Map *)handle;
+    if (what != PG_MAP_Y) return PG_ERR_INVALID_ARG;
+    src = m->y;
+    need = (size_t)m->A * m->H * m->W * 4;
+  } else if (b->kind == KIND_TABLES) {
+    const Tables *t = (const Tables *)handle;
+    size_t n = (size_t)t->A * t->H * t->W;
+    switch (what) {
+      case PG_TAB_P: src = t->P; need = n * 4; break;
+      case PG_TAB_CDF_PHI: src = t->cdf_phi; need = n * 4; break;
+      case PG_TAB_CDF_Z: src = t->cdf_z; need = (size_t)t->A * t->H * 4; break;
+      case PG_TAB_VALID: src = t->valid; need = t->A; break;
+      default: return PG_ERR_INVALID_ARG;
+    }
+  } else {
+    return PG_ERR_INVALID_ARG;
+  }
+  if (bytes != need) return PG_ERR_INVALID_ARG;
+  if (need == 0) return PG_OK;
+  PG_CUDA(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, c->stream));
+  PG_CUDA(cudaStreamSynchronize(c->stream));
+  return PG_OK;
+}
+
+void pg_free(void *handle) {
+  if (!handle) return;
+  Handle *b = (Handle *)handle;
+  void *block = nullptr;
+  switch (b->kind) {
+    case KIND_GRID: block = ((Grid *)handle)->block; break;
+    case KIND_HIST: block = ((Hist *)handle)->block; break;
+    case KIND_NET: {
+      Net *n = (Net *)handle;
+      block = n->block;
+      for (int i = 0; i < n->n_layers; ++i)
+        if (n->layers[i].w_lp) ctx_free(b->ctx, n->layers[i].w_lp, n->layers[i].w_lp_bytes);
+      break;
+    }
+    case KIND_MAP: block = ((Map *)handle)->block; break;
+    case KIND_TABLES: block = ((Tables *)handle)->block; break;
+    default: return;
+  }
+  ctx_free(b->ctx, block, b->bytes);
+  uint32_t kind = b->kind;
+  b->kind = 0;
+  switch (kind) {
+    case KIND_GRID: delete (Grid *)handle; break;
+    case KIND_HIST: delete (Hist *)handle; break;
+    case KIND_NET: delete (Net *)handle; break;
+    case KIND_MAP: delete (Map *)handle; break;
+    default: delete (Tables *)handle; break;
+  }
+}
+
+}  // extern "C"

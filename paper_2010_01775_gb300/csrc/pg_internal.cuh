@@ -1,0 +1,268 @@
+// Internal declarations of libpg: handle layouts, device-side rules shared by
+// the kernels (voxel quantisation, Morton codes, direction bins, Philox), and
+// the host-side launchers each kernel file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pg.h"
+
+namespace pgi {
+
+// ---------------------------------------------------------------- errors
+// Bits of the per-context device status word.
+enum : uint32_t { ST_INVALID_INPUT = 1u, ST_OVERFLOW = 2u, ST_TIMEOUT = 4u, ST_CAPACITY = 8u };
+
+#define PG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      pgi::last_cuda_error() = e_;                      \
+      return PG_ERR_CUDA;                               \
+    }                                                   \
+  } while (0)
+
+#define PG_TRY(call)                    \
+  do {                                  \
+    pg_status s_ = (call);              \
+    if (s_ != PG_OK) return s_;         \
+  } while (0)
+
+cudaError_t &last_cuda_error();
+
+// ---------------------------------------------------------------- handles
+enum : uint32_t {
+  KIND_GRID = 0x50474744u, KIND_HIST = 0x50474848u, KIND_NET = 0x5047484Eu,
+  KIND_MAP = 0x5047484Du, KIND_TABLES = 0x50474854u
+};
+
+struct Handle {
+  uint32_t kind;
+  pg_ctx *ctx;
+  size_t bytes;  // charged to the context budget
+};
+
+struct Grid {
+  Handle h;
+  uint64_t n;
+  uint32_t L, A;
+  int D, min_depth;
+  uint32_t thr;
+  float lo[3], hi[3], scale[3];
+  uint64_t *codes;       // [n]   original order
+  uint32_t *perm;        // [n]   sorted slot -> original index
+  uint32_t *leaf_of;     // [n]   original index -> leaf
+  uint64_t *leaf_code;   // [cap]
+  int32_t *leaf_depth;   // [cap]
+  uint32_t *leaf_begin;  // [cap]
+  uint32_t *leaf_end;    // [cap]
+  uint32_t *active;      // [cap] active leaves (count > 0), ascending
+  int32_t *slot_of_leaf; // [cap]
+  void *block;           // single allocation holding the arrays above
+};
+
+struct Hist {
+  Handle h;
+  uint32_t A;
+  int H, W;
+  uint64_t *pow_cur, *pow_prev;  // [A][HW]
+  uint32_t *cnt_cur, *cnt_prev;  // [A][HW]
+  uint64_t *tot_cur, *tot_prev;  // [A]
+  void *block;
+};
+
+struct Layer {
+  int cout, cin, k, stride, act;
+  float *w;   // device, [k*k*cin][cout] (GEMM B operand, K-major rows)
+  float *b;   // device, [cout]
+  void *w_lp; // device, reduced-precision copy (tensor-core layout), or null
+  size_t w_lp_bytes;
+  int w_lp_prec;  // pg_precision of w_lp
+  float w_scale;  // FP8 per-tensor weight scale (w = w_lp * w_scale)
+};
+
+struct Net {
+  Handle h;
+  int arch, n_layers;
+  int widths[4];
+  Layer layers[16];
+  void *block;
+};
+
+struct Map {
+  Handle h;
+  uint32_t A;
+  int H, W;
+  float *y;  // [A][H][W]
+  void *block;
+};
+
+struct Tables {
+  Handle h;
+  uint32_t A;
+  int H, W;
+  float *P;        // [A][HW]
+  float *cdf_phi;  // [A][HW]
+  float *cdf_z;    // [A][H]
+  uint8_t *valid;  // [A]
+  void *block;
+};
+
+}  // namespace pgi
+
+struct pg_ctx {
+  int device;
+  cudaStream_t stream;
+  size_t budget, in_use;
+  uint32_t *d_status;  // device status word (pgi::ST_* bits)
+  float *d_phi[9];     // boundary-ray tables (cos, sin) per log2(W), W <= 256
+};
+
+namespace pgi {
+
+// ---------------------------------------------------------------- memory
+pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr);
+void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes);
+// Device tables (cos, sin) of the W boundary rays, built once per W on the
+// host of the calling process and cached on the context.
+pg_status phi_table(pg_ctx *ctx, int W, const float **d_table);
+
+// ---------------------------------------------------------------- device rules
+// Voxel quantisation (Algorithm 1 "Locate voxel j"): q = clamp(floor(fl32(
+// fl32(x - lo) * s)), 0, top) with IEEE round-to-nearest FP32 operations
+// (the __f*_rn intrinsics are never contracted into FMAs).
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float s, uint32_t top, uint32_t &bad) {
+  if (!isfinite(x)) {
+    bad = 1u;
+    return 0u;
+  }
+  float f = floorf(__fmul_rn(__fsub_rn(x, lo), s));
+  f = fmaxf(f, 0.0f);
+  f = fminf(f, (float)top);
+  return (uint32_t)f;
+}
+
+// Spread the low 21 bits of v to every third bit (bit b -> bit 3b).
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0x1FFFFFu;
+  x = (x | (x << 32)) & 0x001F00000000FFFFull;
+  x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+  x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+  x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint64_t morton3(uint32_t qx, uint32_t qy, uint32_t qz) {
+  return spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+}
+
+struct GridGeom {
+  float lo[3], scale[3];
+  uint32_t top;  // 2^D - 1
+  int D;
+};
+
+__device__ __forceinline__ uint64_t position_code(const GridGeom &g, float x, float y, float z, uint32_t &bad) {
+  uint32_t qx = quantise(x, g.lo[0], g.scale[0], g.top, bad);
+  uint32_t qy = quantise(y, g.lo[1], g.scale[1], g.top, bad);
+  uint32_t qz = quantise(z, g.lo[2], g.scale[2], g.top, bad);
+  return morton3(qx, qy, qz);
+}
+
+// Last leaf whose start code is <= code (leaf start codes ascend).
+__device__ __forceinline__ uint32_t find_leaf(const uint64_t *__restrict__ leaf_code, uint32_t L, uint64_t code) {
+  uint32_t lo = 0, hi = L;
+  while (lo < hi) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(leaf_code + mid) <= code) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Cylindrical-map row: clamp(floor(z * H/2) + H/2, 0, H-1).  z * H/2 is exact.
+__device__ __forceinline__ int dir_row(float z, int H) {
+  int h2 = H >> 1;
+  float f = floorf(__fmul_rn(z, (float)h2));
+  f = fminf(fmaxf(f, (float)-h2), (float)(h2 - 1));
+  return (int)f + h2;
+}
+
+// Exact sign test "direction (x, y) is not clockwise of boundary ray (c, s)",
+// i.e. c*y - s*x >= 0.  A FP32 evaluation decides when its magnitude clears
+// the rounding error bound (4 ulp of |c y| + |s x|, with normal operands);
+// otherwise the products are formed exactly in FP64 (a float times a float
+// is exact in double) and the rounded difference has the exact sign.
+__device__ __forceinline__ bool not_clockwise(float c, float s, float x, float y) {
+  float a = __fmul_rn(c, y), b = __fmul_rn(s, x);
+  float d = __fsub_rn(a, b);
+  float mag = fabsf(a) + fabsf(b);
+  if (mag > 1e-30f && fabsf(d) > 4.8e-7f * mag) return d >= 0.0f;
+  double dd = __dsub_rn(__dmul_rn((double)c, (double)y), __dmul_rn((double)s, (double)x));
+  return dd >= 0.0;
+}
+
+// Cylindrical-map column: the phi sector of (x, y) among W equal sectors,
+// phi = atan2(y, x) in [0, 2 pi).  Binary search of the last boundary ray the
+// direction is not clockwise of, within the half plane of the direction
+// (upper: phi in [0, pi), rays 0..W/2-1; lower: phi in [pi, 2 pi), rays
+// W/2..W-1).  tab holds cos at [0, W) and sin at [W, 2W).
+__device__ __forceinline__ int dir_col(float x, float y, int W, const float *tab) {
+  if (x == 0.0f && y == 0.0f) return 0;
+  bool upper = (y > 0.0f) || (y == 0.0f && x >= 0.0f);
+  int lo = upper ? 0 : (W >> 1);
+  int hi = lo + (W >> 1) - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (not_clockwise(tab[mid], tab[W + mid], x, y)) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------- launchers
+// grid.cu
+pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n, const pg_grid_params *p, Grid *g);
+// splat.cu
+pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h);
+// cnn.cu
+pg_status net_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
+pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m);
+// cdf.cu
+pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t);
+// sample.cu
+pg_status sample(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, uint64_t q, uint64_t seed,
+                 uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin);
+pg_status eval_pdf(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, const float *d_dir,
+                   uint64_t q, float *d_pdf);
+
+inline GridGeom geom_of(const Grid *g) {
+  GridGeom gg;
+  for (int a = 0; a < 3; ++a) {
+    gg.lo[a] = g->lo[a];
+    gg.scale[a] = g->scale[a];
+  }
+  gg.D = g->D;
+  gg.top = (uint32_t)((1u << g->D) - 1u);
+  return gg;
+}
+
+inline unsigned ceil_div(uint64_t a, uint64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace pgi

@@ -1,0 +1,140 @@
+// a10-a12: guided direction sampling and pdf evaluation at path vertices
+// (Sec. 7.3; the p_guide term of Eq. target_mis / mis_coef).
+//
+// One thread per query: voxel location (the a1 rule), binary search of the
+// leaf start codes, Philox4x32-10 uniforms, then an inverse-CDF search of the
+// marginal (rows) and the conditional (columns) tables; the direction is
+// uniform in (z, phi) inside the chosen bin, i.e. uniform in solid angle on
+// the equal-area cylindrical map, and its pdf is P_ij * HW / (4 pi).
+#include "pg_internal.cuh"
+
+namespace pgi {
+
+namespace {
+
+// First index i in [0, n) with u < F[i]; F ascends and F[n-1] = 1 > u.
+__device__ __forceinline__ int first_above(const float *__restrict__ F, int n, float u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (u < __ldg(F + mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+struct Tab {
+  const uint64_t *leaf_code;
+  const int32_t *slot_of_leaf;
+  const float *P, *Fphi, *Fz;
+  const uint8_t *valid;
+  uint32_t L;
+  int H, W;
+  float pdf_scale;    // HW / (4 pi)
+  float pdf_uniform;  // 1 / (4 pi)
+};
+
+__global__ void k_sample(const float *__restrict__ pos, uint64_t q, GridGeom g, Tab tb, uint2 key, uint32_t stream,
+                         float *__restrict__ dir, float *__restrict__ pdf, uint32_t *__restrict__ leaf_out,
+                         uint32_t *__restrict__ bin_out, uint32_t *status) {
+  uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= q) return;
+  uint32_t bad = 0;
+  uint64_t code = position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  if (bad) atomicOr(status, ST_INVALID_INPUT);
+  uint32_t l = find_leaf(tb.leaf_code, tb.L, code);
+  int32_t s = __ldg(tb.slot_of_leaf + l);
+  uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), stream, 0u), key);
+  const float k24 = 5.9604644775390625e-08f;  // 2^-24
+  float u0 = (float)(r.x >> 8) * k24, u1 = (float)(r.y >> 8) * k24;
+  float u2 = (float)(r.z >> 8) * k24, u3 = (float)(r.w >> 8) * k24;
+  float z, phi, p;
+  uint32_t lo, bo;
+  if (s < 0 || !__ldg(tb.valid + s)) {
+    z = 1.0f - 2.0f * u0;
+    phi = 6.2831853071795865f * u1;
+    p = tb.pdf_uniform;
+    lo = l | 0x80000000u;
+    bo = 0xFFFFFFFFu;
+  } else {
+    const size_t HW = (size_t)tb.H * tb.W;
+    int i = first_above(tb.Fz + (size_t)s * tb.H, tb.H, u0);
+    int j = first_above(tb.Fphi + (size_t)s * HW + (size_t)i * tb.W, tb.W, u1);
+    z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
+    phi = ((float)j + u3) * (6.2831853071795865f / (float)tb.W);
+    p = __ldg(tb.P + (size_t)s * HW + (size_t)i * tb.W + j) * tb.pdf_scale;
+    lo = l;
+    bo = (uint32_t)(i * tb.W + j);
+  }
+  float st = sqrtf(fmaxf(0.0f, 1.0f - z * z)), sn, cs;
+  sincosf(phi, &sn, &cs);
+  dir[3 * t] = st * cs;
+  dir[3 * t + 1] = st * sn;
+  dir[3 * t + 2] = z;
+  pdf[t] = p;
+  leaf_out[t] = lo;
+  if (bin_out) bin_out[t] = bo;
+}
+
+__global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ dirs, uint64_t q, GridGeom g, Tab tb,
+                       const float *__restrict__ phi_tab, float *__restrict__ pdf, uint32_t *status) {
+  uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= q) return;
+  uint32_t bad = 0;
+  uint64_t code = position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  uint32_t l = find_leaf(tb.leaf_code, tb.L, code);
+  int32_t s = __ldg(tb.slot_of_leaf + l);
+  float p = tb.pdf_uniform;
+  if (s >= 0 && __ldg(tb.valid + s)) {
+    float dx = dirs[3 * t], dy = dirs[3 * t + 1], dz = dirs[3 * t + 2];
+    int row = 0, col = 0;
+    if (isfinite(dx) && isfinite(dy) && isfinite(dz)) {
+      row = dir_row(dz, tb.H);
+      col = dir_col(dx, dy, tb.W, phi_tab);
+    } else {
+      bad = 1;
+    }
+    p = __ldg(tb.P + (size_t)s * tb.H * tb.W + (size_t)row * tb.W + col) * tb.pdf_scale;
+  }
+  if (bad) atomicOr(status, ST_INVALID_INPUT);
+  pdf[t] = p;
+}
+
+Tab make_tab(const Grid *g, const Tables *t) {
+  Tab tb;
+  tb.leaf_code = g->leaf_code;
+  tb.slot_of_leaf = g->slot_of_leaf;
+  tb.P = t->P;
+  tb.Fphi = t->cdf_phi;
+  tb.Fz = t->cdf_z;
+  tb.valid = t->valid;
+  tb.L = g->L;
+  tb.H = t->H;
+  tb.W = t->W;
+  tb.pdf_scale = (float)((double)t->H * t->W / (4.0 * 3.14159265358979323846));
+  tb.pdf_uniform = (float)(1.0 / (4.0 * 3.14159265358979323846));
+  return tb;
+}
+
+}  // namespace
+
+pg_status sample(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, uint64_t q, uint64_t seed,
+                 uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin) {
+  uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  k_sample<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, q, geom_of(g), make_tab(g, t), key, stream_id, d_dir,
+                                                      d_pdf, d_leaf, d_bin, ctx->d_status);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
+pg_status eval_pdf(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, const float *d_dir, uint64_t q,
+                   float *d_pdf) {
+  const float *tab;
+  PG_TRY(phi_table(ctx, t->W, &tab));
+  k_eval<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, d_dir, q, geom_of(g), make_tab(g, t), tab, d_pdf,
+                                                    ctx->d_status);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
+}  // namespace pgi

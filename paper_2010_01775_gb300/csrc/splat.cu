@@ -1,0 +1,211 @@
+// a5: photon energy and count maps (Eq. "photon" of Sec. 4; the count maps
+// P_{e,t}, P_{e,t-1} and the previous-iteration map of Sec. 5).
+//
+// One CTA per active leaf.  The leaf's photons are the contiguous range of
+// the sorted permutation; each thread gathers a 32-byte photon record, takes
+// its direction bin and fixed-point power and adds into a shared-memory
+// histogram (64-bit power, 32-bit count).  Photons of one warp that land in
+// the same bin are combined first (warp match), so a hot bin costs one shared
+// atomic per warp instead of one per photon.  The finished histogram is
+// written once, coalesced, with the per-leaf power totals.  Histograms up to
+// 8192 bins keep all four planes in shared memory (24 B/bin = 192 KB); at
+// 16384 bins the current and previous planes run as two launches.
+#include "pg_internal.cuh"
+
+namespace pgi {
+
+namespace {
+
+constexpr int kSplatThreads = 512;
+
+// kMode 0: all four planes; 1: current planes only; 2: previous planes only.
+template <int kMode>
+__global__ void __launch_bounds__(kSplatThreads) k_splat(
+    const pg_photon *__restrict__ ph, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ active,
+    const uint32_t *__restrict__ leaf_begin, const uint32_t *__restrict__ leaf_end, uint32_t n_prev, int H, int W,
+    float two_f, uint64_t limit, const float *__restrict__ phi_tab, uint64_t *__restrict__ pow_cur,
+    uint32_t *__restrict__ cnt_cur, uint64_t *__restrict__ pow_prev, uint32_t *__restrict__ cnt_prev,
+    uint64_t *__restrict__ tot_cur, uint64_t *__restrict__ tot_prev, uint32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int kPlanes = kMode == 0 ? 2 : 1;
+  const int HW = H * W;
+  unsigned long long *s_pow = reinterpret_cast<unsigned long long *>(smem);  // [kPlanes][HW]
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_pow + kPlanes * HW);         // [kPlanes][HW]
+  float *s_tab = reinterpret_cast<float *>(s_cnt + kPlanes * HW);               // [2W]
+  __shared__ unsigned long long s_tot[2][kSplatThreads / 32];
+
+  const uint32_t slot = blockIdx.x;
+  const uint32_t leaf = active[slot];
+  const uint32_t b = leaf_begin[leaf], e = leaf_end[leaf];
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  {
+    uint4 *z = reinterpret_cast<uint4 *>(smem);
+    const int n16 = (kPlanes * HW * 12) / 16;
+    for (int i = tid; i < n16; i += kSplatThreads) z[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 2 * W; i += kSplatThreads) s_tab[i] = phi_tab[i];
+  }
+  __syncthreads();
+
+  uint32_t bad = 0;
+  for (uint32_t base = b; base < e; base += kSplatThreads) {
+    uint32_t i = base + tid;
+    bool live = i < e;
+    int bin = -1;
+    unsigned long long pfx = 0;
+    bool prev = false;
+    if (live) {
+      uint32_t p = perm[i];
+      const float4 *r = reinterpret_cast<const float4 *>(ph + p);
+      float4 r0 = __ldg(r), r1 = __ldg(r + 1);
+      float dx = r0.w, dy = r1.x, dz = r1.y, power = r1.z;
+      int row = 0, col = 0;
+      if (isfinite(dx) && isfinite(dy) && isfinite(dz)) {
+        row = dir_row(dz, H);
+        col = dir_col(dx, dy, W, s_tab);
+      } else {
+        bad |= ST_INVALID_INPUT;
+      }
+      bin = row * W + col;
+      if (!(power >= 0.0f) || !isfinite(power)) {
+        bad |= ST_INVALID_INPUT;
+      } else {
+        float v = __fmul_rn(power, two_f);  // exact: scaling by a power of two
+        if (v >= 9.2233720368547758e18f) {
+          bad |= ST_OVERFLOW;
+        } else {
+          pfx = __float2ull_rn(v);
+          if (pfx > limit) {
+            bad |= ST_OVERFLOW;
+            pfx = 0;
+          }
+        }
+      }
+      prev = p < n_prev;
+      if (kMode == 2 && !prev) bin = -1;
+    }
+    // Combine photons of this warp that share a bin.
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
+    int leader = __ffs(peers) - 1;
+    unsigned long long gsum = pfx;
+    uint32_t gcnt = 1, gsum_p_cnt = prev ? 1u : 0u;
+    unsigned long long gsum_p = prev ? pfx : 0ull;
+    // Sum over the peer group by walking its lanes (all group members loop
+    // the same number of times).
+    {
+      unsigned rest = peers & ~(1u << leader);
+      gsum = __shfl_sync(peers, pfx, leader);
+      gsum_p = __shfl_sync(peers, prev ? pfx : 0ull, leader);
+      gsum_p_cnt = __shfl_sync(peers, prev ? 1u : 0u, leader);
+      while (rest) {
+        int l = __ffs(rest) - 1;
+        rest &= rest - 1;
+        gsum += __shfl_sync(peers, pfx, l);
+        gsum_p += __shfl_sync(peers, prev ? pfx : 0ull, l);
+        gsum_p_cnt += __shfl_sync(peers, prev ? 1u : 0u, l);
+      }
+      gcnt = __popc(peers);
+    }
+    if (lane == leader && bin >= 0) {
+      if (kMode == 0) {
+        atomicAdd(&s_pow[bin], gsum);
+        atomicAdd(&s_cnt[bin], gcnt);
+        if (gsum_p_cnt) {
+          atomicAdd(&s_pow[HW + bin], gsum_p);
+          atomicAdd(&s_cnt[HW + bin], gsum_p_cnt);
+        }
+      } else if (kMode == 1) {
+        atomicAdd(&s_pow[bin], gsum);
+        atomicAdd(&s_cnt[bin], gcnt);
+      } else {
+        atomicAdd(&s_pow[bin], gsum_p);
+        atomicAdd(&s_cnt[bin], gsum_p_cnt);
+      }
+    }
+  }
+  if (bad) atomicOr(status, bad);
+  __syncthreads();
+
+  // Flush: coalesced 16-byte stores, per-leaf totals by block reduction.
+  const size_t o = (size_t)slot * HW;
+  unsigned long long t_cur = 0, t_prev = 0;
+  for (int k = 2 * tid; k < HW; k += 2 * kSplatThreads) {
+    if (kMode != 2) {
+      ulonglong2 v = make_ulonglong2(s_pow[k], s_pow[k + 1]);
+      *reinterpret_cast<ulonglong2 *>(pow_cur + o + k) = v;
+      *reinterpret_cast<uint2 *>(cnt_cur + o + k) = make_uint2(s_cnt[k], s_cnt[k + 1]);
+      t_cur += v.x + v.y;
+    }
+    if (kMode != 1) {
+      const int P = kMode == 0 ? HW : 0;
+      ulonglong2 v = make_ulonglong2(s_pow[P + k], s_pow[P + k + 1]);
+      *reinterpret_cast<ulonglong2 *>(pow_prev + o + k) = v;
+      *reinterpret_cast<uint2 *>(cnt_prev + o + k) = make_uint2(s_cnt[P + k], s_cnt[P + k + 1]);
+      t_prev += v.x + v.y;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    t_cur += __shfl_xor_sync(0xFFFFFFFFu, t_cur, off);
+    t_prev += __shfl_xor_sync(0xFFFFFFFFu, t_prev, off);
+  }
+  if (lane == 0) {
+    s_tot[0][tid >> 5] = t_cur;
+    s_tot[1][tid >> 5] = t_prev;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long a = 0, c = 0;
+    for (int w = 0; w < kSplatThreads / 32; ++w) {
+      a += s_tot[0][w];
+      c += s_tot[1][w];
+    }
+    if (kMode != 2) tot_cur[slot] = a;
+    if (kMode != 1) tot_prev[slot] = c;
+  }
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h) {
+  const size_t A = g->A, HW = (size_t)h->H * h->W;
+  size_t b64 = align256(8 * A * HW), b32 = align256(4 * A * HW), bt = align256(8 * A);
+  h->h.bytes = 2 * b64 + 2 * b32 + 2 * bt;
+  PG_TRY(ctx_alloc(ctx, h->h.bytes, &h->block));
+  uint8_t *q = (uint8_t *)h->block;
+  h->pow_cur = (uint64_t *)q; q += b64;
+  h->pow_prev = (uint64_t *)q; q += b64;
+  h->cnt_cur = (uint32_t *)q; q += b32;
+  h->cnt_prev = (uint32_t *)q; q += b32;
+  h->tot_cur = (uint64_t *)q; q += bt;
+  h->tot_prev = (uint64_t *)q;
+  if (A == 0) return PG_OK;
+  const float *tab;
+  PG_TRY(phi_table(ctx, h->W, &tab));
+  const float two_f = ldexpf(1.0f, F);
+  const uint64_t limit = n ? (uint64_t)INT64_MAX / n : 0;
+  const bool one_pass = HW <= 8192;
+  if (one_pass) {
+    size_t smem = 24 * HW + 8 * (size_t)h->W;
+    PG_CUDA(cudaFuncSetAttribute(k_splat<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_splat<0><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
+        d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
+        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status);
+  } else {
+    size_t smem = 12 * HW + 8 * (size_t)h->W;
+    PG_CUDA(cudaFuncSetAttribute(k_splat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PG_CUDA(cudaFuncSetAttribute(k_splat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_splat<1><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
+        d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
+        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status);
+    k_splat<2><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
+        d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
+        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status);
+  }
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
+}  // namespace pgi

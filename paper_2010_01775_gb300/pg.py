@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libpg.so (include/pg.h), same names as the C ABI.
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Array arguments may be torch tensors (device or host), NumPy
+arrays (host) or raw integer addresses.  The binding fails loudly when the
+library is missing; there is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libpg.so")
+
+PG_FP32, PG_BF16, PG_FP8_E4M3 = 0, 1, 2
+PRECISIONS = {"fp32": PG_FP32, "bf16": PG_BF16, "fp8": PG_FP8_E4M3}
+
+PG_INFO_N_PHOTONS, PG_INFO_N_LEAVES, PG_INFO_N_ACTIVE, PG_INFO_H, PG_INFO_W, PG_INFO_BYTES, PG_INFO_MAX_DEPTH = range(1, 8)
+PG_GRID_CODES, PG_GRID_PERM, PG_GRID_LEAF_OF, PG_GRID_LEAF_CODE, PG_GRID_LEAF_DEPTH = 100, 101, 102, 103, 104
+PG_GRID_LEAF_BEGIN, PG_GRID_LEAF_END, PG_GRID_ACTIVE, PG_GRID_SLOT_OF_LEAF = 105, 106, 107, 108
+PG_HIST_POW_CUR, PG_HIST_CNT_CUR, PG_HIST_POW_PREV, PG_HIST_CNT_PREV = 200, 201, 202, 203
+PG_MAP_Y = 300
+PG_TAB_P, PG_TAB_CDF_PHI, PG_TAB_CDF_Z, PG_TAB_VALID = 400, 401, 402, 403
+
+STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_NOT_DEVICE_PTR", 3: "PG_ERR_OOM",
+          4: "PG_ERR_OVERFLOW", 5: "PG_ERR_NOT_POW2", 6: "PG_ERR_TIMEOUT", 7: "PG_ERR_CUDA",
+          8: "PG_ERR_INVALID_INPUT", 9: "PG_ERR_UNSUPPORTED"}
+
+EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_use", "pg_build_grid",
+            "pg_splat_photons", "pg_net_load", "pg_reconstruct", "pg_map_import", "pg_build_cdf",
+            "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string"]
+
+
+class PgError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        super().__init__(f"{what}: {name} ({_lib.pg_status_string(status).decode() if _lib else ''})")
+
+
+class pg_grid_params(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("max_depth", ctypes.c_int32),
+                ("min_depth", ctypes.c_int32), ("split_threshold", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpg.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpg.so not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, u64, u32, i32, sz = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "pg_create": [PP, P, sz], "pg_destroy": [P], "pg_set_stream": [P, P], "pg_sync": [P],
+        "pg_bytes_in_use": [P, ctypes.POINTER(u64)],
+        "pg_build_grid": [P, P, u64, ctypes.POINTER(pg_grid_params), PP],
+        "pg_splat_photons": [P, P, P, u64, u64, i32, i32, i32, PP],
+        "pg_net_load": [P, P, sz, PP], "pg_reconstruct": [P, P, P, i32, PP],
+        "pg_map_import": [P, P, u64, i32, i32, PP], "pg_build_cdf": [P, P, PP],
+        "pg_sample_dirs": [P, P, P, P, u64, u64, u32, P, P, P, P],
+        "pg_eval_pdf": [P, P, P, P, P, u64, P],
+        "pg_info": [P, i32, ctypes.POINTER(u64)], "pg_export": [P, P, i32, P, sz],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.pg_free.argtypes = [P]
+    L.pg_free.restype = None
+    L.pg_status_string.argtypes = [ctypes.c_int]
+    L.pg_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status, what):
+    if status != 0:
+        raise PgError(status, what)
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "arrays must be contiguous"
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "arrays must be contiguous"
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+class Handle:
+    """Owns one library handle; freed with pg_free."""
+
+    def __init__(self, ctx, ptr, kind):
+        self.ctx, self.ptr, self.kind = ctx, ptr, kind
+
+    def info(self, what):
+        v = ctypes.c_uint64()
+        _check(_lib.pg_info(self.ptr, what, ctypes.byref(v)), "pg_info")
+        return v.value
+
+    def export(self, what, dtype, count):
+        out = np.empty(count, dtype=dtype)
+        if count:
+            _check(_lib.pg_export(self.ctx.ptr, self.ptr, what, out.ctypes.data, out.nbytes), "pg_export")
+        return out
+
+    def free(self):
+        if self.ptr:
+            _lib.pg_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A pg_ctx bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, stream=None, hbm_budget=0):
+        load()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        p = ctypes.c_void_p()
+        _check(_lib.pg_create(ctypes.byref(p), ctypes.c_void_p(stream), hbm_budget), "pg_create")
+        self.ptr = p.value
+
+    def sync(self):
+        _check(_lib.pg_sync(self.ptr), "pg_sync")
+
+    def bytes_in_use(self):
+        v = ctypes.c_uint64()
+        _check(_lib.pg_bytes_in_use(self.ptr, ctypes.byref(v)), "pg_bytes_in_use")
+        return v.value
+
+    def set_stream(self, stream):
+        _check(_lib.pg_set_stream(self.ptr, ctypes.c_void_p(stream)), "pg_set_stream")
+
+    def destroy(self):
+        if self.ptr:
+            _lib.pg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def pg_create(stream=None, hbm_budget=0) -> Context:
+    return Context(stream, hbm_budget)
+
+
+def pg_build_grid(ctx, photons, n, lo, hi, max_depth, min_depth, split_threshold) -> Handle:
+    prm = pg_grid_params((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi), max_depth, min_depth,
+                         split_threshold)
+    out = ctypes.c_void_p()
+    _check(_lib.pg_build_grid(ctx.ptr, _ptr(photons), n, ctypes.byref(prm), ctypes.byref(out)), "pg_build_grid")
+    return Handle(ctx, out.value, "grid")
+
+
+def pg_splat_photons(ctx, grid, photons, n, n_prev, H, W, frac_bits=32) -> Handle:
+    out = ctypes.c_void_p()
+    _check(_lib.pg_splat_photons(ctx.ptr, grid.ptr, _ptr(photons), n, n_prev, H, W, frac_bits, ctypes.byref(out)),
+           "pg_splat_photons")
+    return Handle(ctx, out.value, "hist")
+
+
+def pg_net_load(ctx, blob: bytes) -> Handle:
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.pg_net_load(ctx.ptr, buf, len(blob), ctypes.byref(out)), "pg_net_load")
+    return Handle(ctx, out.value, "net")
+
+
+def pg_reconstruct(ctx, hist, net, precision=PG_FP32) -> Handle:
+    out = ctypes.c_void_p()
+    _check(_lib.pg_reconstruct(ctx.ptr, hist.ptr, net.ptr, precision, ctypes.byref(out)), "pg_reconstruct")
+    return Handle(ctx, out.value, "map")
+
+
+def pg_map_import(ctx, y, n_maps, H, W) -> Handle:
+    out = ctypes.c_void_p()
+    _check(_lib.pg_map_import(ctx.ptr, _ptr(y), n_maps, H, W, ctypes.byref(out)), "pg_map_import")
+    return Handle(ctx, out.value, "map")
+
+
+def pg_build_cdf(ctx, m) -> Handle:
+    out = ctypes.c_void_p()
+    _check(_lib.pg_build_cdf(ctx.ptr, m.ptr, ctypes.byref(out)), "pg_build_cdf")
+    return Handle(ctx, out.value, "tables")
+
+
+def pg_sample_dirs(ctx, grid, tables, pos, q, seed, stream_id, dirs, pdf, leaf, bins=None):
+    _check(_lib.pg_sample_dirs(ctx.ptr, grid.ptr, tables.ptr, _ptr(pos), q, seed, stream_id, _ptr(dirs), _ptr(pdf),
+                               _ptr(leaf), _ptr(bins)), "pg_sample_dirs")
+
+
+def pg_eval_pdf(ctx, grid, tables, pos, dirs, q, pdf):
+    _check(_lib.pg_eval_pdf(ctx.ptr, grid.ptr, tables.ptr, _ptr(pos), _ptr(dirs), q, _ptr(pdf)), "pg_eval_pdf")
+
+
+def pg_sync(ctx):
+    ctx.sync()
+
+
+def pg_free(handle):
+    handle.free()
+
+
+# ------------------------------------------------------------------ exports
+def export_grid(g):
+    n, L, A = g.info(PG_INFO_N_PHOTONS), g.info(PG_INFO_N_LEAVES), g.info(PG_INFO_N_ACTIVE)
+    return dict(codes=g.export(PG_GRID_CODES, np.uint64, n), perm=g.export(PG_GRID_PERM, np.uint32, n),
+                leaf_of=g.export(PG_GRID_LEAF_OF, np.uint32, n),
+                leaf_code=g.export(PG_GRID_LEAF_CODE, np.uint64, L),
+                leaf_depth=g.export(PG_GRID_LEAF_DEPTH, np.int32, L),
+                leaf_begin=g.export(PG_GRID_LEAF_BEGIN, np.uint32, L),
+                leaf_end=g.export(PG_GRID_LEAF_END, np.uint32, L),
+                active=g.export(PG_GRID_ACTIVE, np.uint32, A),
+                slot_of_leaf=g.export(PG_GRID_SLOT_OF_LEAF, np.int32, L), L=L, A=A)
+
+
+def export_hist(h):
+    A, H, W = h.info(PG_INFO_N_ACTIVE), h.info(PG_INFO_H), h.info(PG_INFO_W)
+    c = A * H * W
+    return dict(pow_cur=h.export(PG_HIST_POW_CUR, np.uint64, c).reshape(A, H * W),
+                cnt_cur=h.export(PG_HIST_CNT_CUR, np.uint32, c).reshape(A, H * W),
+                pow_prev=h.export(PG_HIST_POW_PREV, np.uint64, c).reshape(A, H * W),
+                cnt_prev=h.export(PG_HIST_CNT_PREV, np.uint32, c).reshape(A, H * W), H=H, W=W)
+
+
+def export_map(m):
+    A, H, W = m.info(PG_INFO_N_ACTIVE), m.info(PG_INFO_H), m.info(PG_INFO_W)
+    return m.export(PG_MAP_Y, np.float32, A * H * W).reshape(A, H, W)
+
+
+def export_tables(t):
+    A, H, W = t.info(PG_INFO_N_ACTIVE), t.info(PG_INFO_H), t.info(PG_INFO_W)
+    return dict(P=t.export(PG_TAB_P, np.float32, A * H * W).reshape(A, H, W),
+                cdf_phi=t.export(PG_TAB_CDF_PHI, np.float32, A * H * W).reshape(A, H, W),
+                cdf_z=t.export(PG_TAB_CDF_Z, np.float32, A * H).reshape(A, H),
+                valid=t.export(PG_TAB_VALID, np.uint8, A), H=H, W=W)

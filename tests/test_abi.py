@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads on a machine without a GPU, and exports
+every entry point include/pg.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2010_01775_gb300 import build as B
+from paper_2010_01775_gb300 import pg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:pg_status|void|const char \*)\s*\*?\s*(pg_\w+)\s*\(", src, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return pg.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert {"pg_build_grid", "pg_splat_photons", "pg_reconstruct", "pg_build_cdf", "pg_sample_dirs",
+            "pg_eval_pdf"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(pg.EXPORTED) | declared
+
+
+def test_status_strings(lib):
+    for code in range(10):
+        s = lib.pg_status_string(code)
+        assert isinstance(s, bytes) and len(s) > 0
+    assert lib.pg_status_string(0) == b"ok"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    assert lib.pg_build_grid(None, None, 0, None, None) == 1
+    assert lib.pg_sync(None) == 1
+    v = ctypes.c_uint64()
+    assert lib.pg_info(None, 1, ctypes.byref(v)) == 1
+    lib.pg_free(None)

@@ -1,0 +1,329 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Integer work (codes, sort permutation, grid topology, leaf assignment,
+histograms, sampled bins) must match bit for bit; floating-point results
+within the tolerances derived in each test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2010_01775_gb300 import pg, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+LO = [0.0, 0.0, 0.0]
+HI = [1.0, 1.0, 1.0]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    c = pg.Context()
+    yield c
+    c.destroy()
+
+
+def _grid_case(ctx, ph, D, min_depth, thr, lo=LO, hi=HI):
+    n = ph.shape[0]
+    d = torch.from_numpy(ph).cuda() if n else torch.empty(0, 8, device="cuda")
+    g = pg.pg_build_grid(ctx, d if n else 0, n, lo, hi, D, min_depth, thr)
+    ref = O.build_grid(ph, lo, hi, D, min_depth, thr)
+    return g, pg.export_grid(g), ref, d
+
+
+def _assert_grid_equal(got, ref):
+    assert got["L"] == ref["L"]
+    for k in ("codes", "perm", "leaf_of", "leaf_code", "leaf_begin", "leaf_end"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert np.array_equal(got["leaf_depth"], ref["leaf_depth"])
+    act, slot = O.active_leaves(ref)
+    assert np.array_equal(got["active"], act)
+    assert np.array_equal(got["slot_of_leaf"], slot)
+
+
+# ------------------------------------------------------------------ a1-a4
+@pytest.mark.parametrize("n,blobs,D,min_depth,thr,seed", [
+    (100_000, 8, 4, 0, 1000, synth.SEED_BASE),  # tiny workload
+    (77_777, 5, 10, 0, 300, 31),                 # ragged tail of the sort tile, 4 radix passes
+    (4097, 3, 6, 2, 20, 32),                     # initial regular grid
+    (1000, 2, 3, 0, 0, 33),                      # split everything to max depth
+    (513, 2, 16, 0, 5, 34),                      # deepest codes (48 bits, 6 passes)
+    (3000, 4, 5, 0, 10 ** 9, 35),                # threshold above n: one leaf
+    (1, 1, 4, 0, 0, 36),
+])
+def test_grid_bit_exact(ctx, n, blobs, D, min_depth, thr, seed):
+    ph = synth.photons(n, blobs, seed)
+    g, got, ref, _ = _grid_case(ctx, ph, D, min_depth, thr)
+    _assert_grid_equal(got, ref)
+    g.free()
+
+
+def test_grid_empty_and_odd_domain(ctx):
+    g, got, ref, _ = _grid_case(ctx, np.zeros((0, 8), np.float32), 3, 1, 10)
+    _assert_grid_equal(got, ref)
+    assert got["A"] == 0 and got["L"] == 8
+    ph = synth.photons(5000, 4, 37)
+    ph[:, :3] = ph[:, :3] * 7.3 - 2.1  # positions outside a shifted domain are clamped
+    lo, hi = [-1.5, -0.75, 0.25], [4.0, 2.5, 3.0]
+    g2, got2, ref2, _ = _grid_case(ctx, ph, 7, 0, 40, lo, hi)
+    _assert_grid_equal(got2, ref2)
+
+
+def test_nonfinite_position_reported(ctx):
+    ph = synth.photons(100, 1, 38)
+    ph[5, 1] = np.nan
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_build_grid(ctx, torch.from_numpy(ph).cuda(), 100, LO, HI, 3, 0, 10)
+    assert e.value.status == 8
+
+
+# ------------------------------------------------------------------ a5
+@pytest.mark.parametrize("n,D,thr,H,W,n_prev", [
+    (100_000, 4, 1000, 32, 32, 50_000),
+    (60_000, 5, 2000, 64, 64, 20_001),
+    (30_000, 4, 3000, 128, 128, 15_000),   # two-pass (16384 bins)
+    (20_000, 3, 500, 8, 16, 0),            # no previous-iteration photons
+    (9_999, 3, 100, 4, 256, 9_999),
+])
+def test_splat_bit_exact(ctx, n, D, thr, H, W, n_prev):
+    ph = synth.photons(n, 6, 40 + H)
+    g, got, ref, d = _grid_case(ctx, ph, D, 0, thr)
+    h = pg.pg_splat_photons(ctx, g, d, n, n_prev, H, W)
+    hh = pg.export_hist(h)
+    ctx.sync()
+    hr = O.splat(ph, ref, n_prev, H, W)
+    act, _ = O.active_leaves(ref)
+    for k in ("pow_cur", "cnt_cur", "pow_prev", "cnt_prev"):
+        assert np.array_equal(hh[k], hr[k][act]), k
+    # Eq. (photon): mass conservation, exact.
+    pfx = np.rint(ph[:, 6].astype(np.float64) * 2.0 ** 32).astype(np.uint64)
+    assert int(hh["pow_cur"].sum(dtype=np.uint64)) == int(pfx.sum(dtype=np.uint64))
+    h.free()
+    g.free()
+
+
+def test_splat_axis_and_seam_directions(ctx):
+    """Directions on bin edges and the phi seam: the exact rule on both sides."""
+    H, W = 16, 32
+    dirs = [[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1e-30, 0],
+            [1, -1e-30, 0], [-1, -1e-30, 0], [-1, 1e-38, 0], [0.7071068, 0.7071068, 0]]
+    rng = np.random.default_rng(41)
+    th = 2 * np.pi * np.arange(W) / W
+    edge = np.stack([np.cos(th), np.sin(th), np.zeros(W)], 1)  # exactly on rounded boundary rays
+    rand = synth.uniform_sphere(rng, 5000)
+    D = np.concatenate([np.array(dirs, np.float64), edge, rand]).astype(np.float32)
+    n = D.shape[0]
+    ph = np.zeros((n, 8), np.float32)
+    ph[:, :3] = 0.5
+    ph[:, 3:6] = D
+    ph[:, 6] = 1.0
+    g, got, ref, d = _grid_case(ctx, ph, 1, 0, 10 ** 9)
+    h = pg.pg_splat_photons(ctx, g, d, n, 0, H, W)
+    hh = pg.export_hist(h)
+    hr = O.splat(ph, ref, 0, H, W)
+    assert np.array_equal(hh["cnt_cur"], hr["cnt_cur"])
+    assert np.array_equal(hh["pow_cur"], hr["pow_cur"])
+
+
+def test_splat_status_errors(ctx):
+    ph = synth.photons(500, 2, 42)
+    ph[7, 6] = -1.0
+    g, _, _, d = _grid_case(ctx, ph, 3, 0, 50)
+    pg.pg_splat_photons(ctx, g, d, 500, 0, 8, 8)
+    with pytest.raises(pg.PgError) as e:
+        ctx.sync()
+    assert e.value.status == 8
+    ph = synth.photons(4, 1, 43)
+    ph[:, 6] = 2.0 ** 30
+    g, _, _, d = _grid_case(ctx, ph, 2, 0, 0)
+    pg.pg_splat_photons(ctx, g, d, 4, 0, 8, 8)
+    with pytest.raises(pg.PgError) as e:
+        ctx.sync()
+    assert e.value.status == 4
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_splat_photons(ctx, g, d, 4, 0, 12, 8)
+    assert e.value.status == 5
+
+
+# ------------------------------------------------------------------ a8-a12 from a given map
+def _maps(A, H, W, seed):
+    rng = np.random.default_rng(seed)
+    y = rng.lognormal(0, 2, (A, H, W)).astype(np.float32)
+    y[0, 1, :] = 0
+    y[min(1, A - 1), :, 2] = 0
+    if A > 3:
+        y[3] = 0  # an invalid (all-zero) map
+    return y
+
+
+@pytest.fixture(scope="module")
+def tiny_scene(ctx):
+    wl = synth.TINY
+    ph = synth.photons(wl.n_photons, wl.n_blobs, wl.seed)
+    d = torch.from_numpy(ph).cuda()
+    g = pg.pg_build_grid(ctx, d, wl.n_photons, LO, HI, wl.max_depth, 0, wl.split_threshold)
+    ref = O.build_grid(ph, LO, HI, wl.max_depth, 0, wl.split_threshold)
+    act, slot = O.active_leaves(ref)
+    return dict(ph=ph, d=d, g=g, ref=ref, act=act, slot=slot, wl=wl)
+
+
+@pytest.mark.parametrize("H,W", [(32, 32), (64, 64), (16, 128), (128, 128), (4, 4)])
+def test_cdf_tables(ctx, tiny_scene, H, W):
+    A = tiny_scene["g"].info(pg.PG_INFO_N_ACTIVE)
+    y = _maps(A, H, W, H * 1000 + W)
+    m = pg.pg_map_import(ctx, torch.from_numpy(y).cuda(), A, H, W)
+    t = pg.pg_build_cdf(ctx, m)
+    tt = pg.export_tables(t)
+    ref = O.tables_from_map(y.astype(np.float64))
+    assert np.array_equal(tt["valid"], ref["valid"])
+    v = ref["valid"].astype(bool)
+    P, Pr = tt["P"][v].astype(np.float64), ref["P"][v]
+    nz = Pr > 0
+    assert np.all(P[~nz] == 0)
+    assert np.max(np.abs(P[nz] - Pr[nz]) / Pr[nz]) <= 1e-5
+    # Decision tables: float32 of the FP64 CDFs, last entry 1.
+    dz = tt["cdf_z"][v] != ref["fz"][v]
+    dp = tt["cdf_phi"][v] != ref["fphi"][v]
+    assert dz.mean() <= 1e-4 and dp.mean() <= 1e-4
+    assert np.max(np.abs(tt["cdf_z"][v] - ref["fz"][v])) <= 1.2e-7
+    assert np.max(np.abs(tt["cdf_phi"][v] - ref["fphi"][v])) <= 1.2e-7
+    assert np.all(tt["cdf_z"][:, -1] == 1.0) and np.all(tt["cdf_phi"][:, :, -1] == 1.0)
+
+
+def _run_sample(ctx, g, t, pos, seed, stream_id, host=False):
+    q = pos.shape[0]
+    if host:
+        dirs = np.empty((q, 3), np.float32)
+        pdf = np.empty(q, np.float32)
+        leaf = np.empty(q, np.uint32)
+        bins = np.empty(q, np.uint32)
+        pg.pg_sample_dirs(ctx, g, t, np.ascontiguousarray(pos), q, seed, stream_id, dirs, pdf, leaf, bins)
+        ctx.sync()
+        return dirs, pdf, leaf, bins
+    d_pos = torch.from_numpy(pos).cuda()
+    dirs = torch.empty(q, 3, device="cuda")
+    pdf = torch.empty(q, device="cuda")
+    leaf = torch.empty(q, dtype=torch.int32, device="cuda")
+    bins = torch.empty(q, dtype=torch.int32, device="cuda")
+    pg.pg_sample_dirs(ctx, g, t, d_pos, q, seed, stream_id, dirs, pdf, leaf, bins)
+    ctx.sync()
+    return (dirs.cpu().numpy(), pdf.cpu().numpy(), leaf.cpu().numpy().view(np.uint32),
+            bins.cpu().numpy().view(np.uint32))
+
+
+@pytest.mark.parametrize("H,W,q,seed,stream_id", [(32, 32, 65_536, 7, 0), (64, 64, 100_003, 2 ** 40 + 5, 3),
+                                                  (128, 128, 4_099, 11, 1), (8, 4, 1, 1, 0)])
+def test_sample_and_eval(ctx, tiny_scene, H, W, q, seed, stream_id):
+    g, ref, slot = tiny_scene["g"], tiny_scene["ref"], tiny_scene["slot"]
+    A = g.info(pg.PG_INFO_N_ACTIVE)
+    y = _maps(A, H, W, 7 * H + W)
+    m = pg.pg_map_import(ctx, torch.from_numpy(y).cuda(), A, H, W)
+    t = pg.pg_build_cdf(ctx, m)
+    tabs = O.tables_from_map(y.astype(np.float64))
+    pos = synth.query_positions(q, seed & 0xFFFF)
+    dirs, pdf, leaf, bins = _run_sample(ctx, g, t, pos, seed, stream_id)
+    s = O.sample(ref, slot, tabs, pos, seed, stream_id)
+    assert np.array_equal(leaf, s["leaf"])
+    same = bins == s["bin"]
+    assert same.mean() >= 1 - 1e-4
+    assert np.allclose(dirs[same], s["dir"][same], rtol=0, atol=2e-6)
+    nz = same & (s["pdf"] > 0)
+    assert np.max(np.abs(pdf[nz] - s["pdf"][nz]) / s["pdf"][nz], initial=0) <= 1e-5
+    # Host buffers go through the same kernels.
+    hd, hp, hl, hb = _run_sample(ctx, g, t, pos, seed, stream_id, host=True)
+    assert np.array_equal(hb, bins) and np.array_equal(hp, pdf) and np.array_equal(hd, dirs)
+    # Evaluation at uniform directions and at the sampled directions.
+    ev_dirs = synth.query_directions(q, seed & 0xFFFF)
+    for dd in (ev_dirs, dirs):
+        out = torch.empty(q, device="cuda")
+        pg.pg_eval_pdf(ctx, g, t, torch.from_numpy(pos).cuda(), torch.from_numpy(np.ascontiguousarray(dd)).cuda(), q, out)
+        ctx.sync()
+        e = out.cpu().numpy().astype(np.float64)
+        er = O.eval_pdf(ref, slot, tabs, pos, dd)
+        nz = er > 0
+        assert np.all(e[~nz] == 0)
+        assert np.max(np.abs(e[nz] - er[nz]) / er[nz], initial=0) <= 1e-5
+    # Sampled directions evaluate to their own pdf (same bin rule), away from bin edges.
+    ok = (leaf >> 31) == 0
+    out = torch.empty(q, device="cuda")
+    pg.pg_eval_pdf(ctx, g, t, torch.from_numpy(pos).cuda(), torch.from_numpy(dirs).cuda(), q, out)
+    agree = np.isclose(out.cpu().numpy()[ok], pdf[ok], rtol=1e-6)
+    assert agree.mean() >= 1 - 1e-3
+
+
+# ------------------------------------------------------------------ a6-a7: CNN, FP32
+def _cnn_case(ctx, wl_n, blobs, D, thr, H, W, arch, widths, seed, max_check_leaves=None):
+    ph = synth.photons(wl_n, blobs, seed)
+    d = torch.from_numpy(ph).cuda()
+    g = pg.pg_build_grid(ctx, d, wl_n, LO, HI, D, 0, thr)
+    h = pg.pg_splat_photons(ctx, g, d, wl_n, wl_n // 2, H, W)
+    blob = synth.net_blob(arch, widths, seed + 1)
+    net = pg.pg_net_load(ctx, blob)
+    m = pg.pg_reconstruct(ctx, h, net, pg.PG_FP32)
+    t = pg.pg_build_cdf(ctx, m)
+    y = pg.export_map(m)
+    P = pg.export_tables(t)["P"]
+    ctx.sync()
+    ref = O.build_grid(ph, LO, HI, D, 0, thr)
+    act, _ = O.active_leaves(ref)
+    hr = O.hist_for_active(O.splat(ph, ref, wl_n // 2, H, W), act)
+    if max_check_leaves is not None and act.size > max_check_leaves:
+        idx = np.linspace(0, act.size - 1, max_check_leaves).astype(np.int64)
+    else:
+        idx = np.arange(act.size)
+    hsub = {k: (v[idx] if isinstance(v, np.ndarray) else v) for k, v in hr.items()}
+    yr = O.cnn_forward(O.assemble_inputs(hsub), O.parse_net(blob))
+    Pr, _ = O.normalise(yr)
+    return y[idx].astype(np.float64), yr, P[idx].astype(np.float64), Pr
+
+
+def _check_fp32_maps(y, yr, P, Pr):
+    """FP32 accumulation over K <= 3456 terms of a He-initialised net: the
+    pre-activation error is about K * 2^-24 times the sum of |w x|, so a
+    softplus output carries relative error ~ |x| eps for x << 0 and ~ eps
+    otherwise.  Gate: per bin |dP| <= 1e-5 P + 1e-7 max(P of the leaf), and per
+    leaf L1 distance <= 1e-5."""
+    for a in range(P.shape[0]):
+        tol = 1e-5 * Pr[a] + 1e-7 * Pr[a].max()
+        assert np.all(np.abs(P[a] - Pr[a]) <= tol), (a, np.max(np.abs(P[a] - Pr[a]) - tol))
+        assert np.abs(P[a] - Pr[a]).sum() <= 1e-5
+    big = yr > 1e-3 * yr.max(axis=(1, 2), keepdims=True)
+    assert np.max(np.abs(y[big] - yr[big]) / yr[big]) <= 1e-4
+
+
+def test_cnn_tiny_fp32(ctx):
+    wl = synth.TINY
+    y, yr, P, Pr = _cnn_case(ctx, wl.n_photons, wl.n_blobs, wl.max_depth, wl.split_threshold, 32, 32,
+                             synth.ARCH_TINY3, (16,), wl.seed)
+    _check_fp32_maps(y, yr, P, Pr)
+
+
+def test_cnn_unet_fp32_small(ctx):
+    y, yr, P, Pr = _cnn_case(ctx, 30_000, 6, 4, 1500, 32, 32, synth.ARCH_UNET4, (32, 64, 128, 256), 51,
+                             max_check_leaves=12)
+    _check_fp32_maps(y, yr, P, Pr)
+
+
+def test_cnn_unet_fp32_rect(ctx):
+    y, yr, P, Pr = _cnn_case(ctx, 20_000, 4, 3, 2500, 16, 64, synth.ARCH_UNET4, (8, 16, 16, 32), 52)
+    _check_fp32_maps(y, yr, P, Pr)
+
+
+def test_budget_and_bad_args(ctx):
+    small = pg.Context(hbm_budget=1 << 20)
+    ph = synth.photons(100_000, 3, 60)
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_build_grid(small, torch.from_numpy(ph).cuda(), 100_000, LO, HI, 5, 0, 100)
+    assert e.value.status == 3
+    assert small.bytes_in_use() == 0
+    small.destroy()
+    with pytest.raises(pg.PgError) as e:
+        pg.pg_build_grid(ctx, torch.from_numpy(ph).cuda(), 100_000, LO, HI, 17, 0, 100)
+    assert e.value.status == 1
