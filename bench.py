@@ -259,7 +259,7 @@ def run_pg(args, wl, prec):
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves)
         out["gpu_launches"] = count_launches(wl, A)
-        print(json.dumps(out))
+        print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -337,7 +337,7 @@ def run_reference(args, wl):
                          "sample": "per step: grid+splat on all photons, CNN+CDF on 2 active leaves, sample+eval on "
                                    "65536 queries, scaled to the full step"},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }))
+    }), flush=True)
 
 
 def main():

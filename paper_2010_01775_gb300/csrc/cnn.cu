@@ -152,6 +152,14 @@ __global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
     store();
     __syncthreads();
     if (k0 + BK < K) load(k0 + BK);
+    // Blocked accumulation: each 16-term chunk is summed on its own and then
+    // added to the running total, which keeps FP32 rounding growth at about
+    // (K/16 + 16) ulps instead of K ulps over long reductions.
+    float part[8][TN];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) part[i][j] = 0.0f;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][tx * 4]);
@@ -171,8 +179,12 @@ __global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < TN; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] += part[i][j];
   }
 
   // Epilogue: bias + activation, channel-last store (optionally upsampled x2).
@@ -198,10 +210,12 @@ __global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
         float *p = ((float *)a.out) + ((size_t)(leaf * Ho + oy * reps + dy) * Wo + ox * reps + dx) * a.out_cs + a.out_co + nb;
         if constexpr (TN % 4 == 0) {
 #pragma unroll
-          for (int j = 0; j < TN; j += 4) *reinterpret_cast<float4 *>(p + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+          for (int j = 0; j < TN; j += 4)
+            if (nb + j < a.Cout) *reinterpret_cast<float4 *>(p + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
         } else {
 #pragma unroll
-          for (int j = 0; j < TN; ++j) p[j] = o[j];
+          for (int j = 0; j < TN; ++j)
+            if (nb + j < a.Cout) p[j] = o[j];
         }
       }
   }
@@ -245,18 +259,21 @@ void launch_f32(const ConvArgs &a, cudaStream_t st) {
 
 pg_status conv_f32(const ConvArgs &a, cudaStream_t st) {
   if (a.M == 0) return PG_OK;
+  // Channel counts must be multiples of 4 (16-byte vector access).
+  if (a.Cin % 4 || a.in_cs % 4 || a.in_co % 4 || (a.Cout != 1 && (a.Cout % 4 || a.out_cs % 4 || a.out_co % 4)))
+    return PG_ERR_UNSUPPORTED;
   if (a.Cout == 1) {
     k_conv_cout1<<<ceil_div(a.M, 256), 256, 0, st>>>(a);
-  } else if (a.Cout % 128 == 0) {
+  } else if (a.Cout >= 128) {
     launch_f32<128, 128, 8>(a, st);
-  } else if (a.Cout == 64) {
+  } else if (a.Cout > 32) {
     launch_f32<256, 64, 8>(a, st);
-  } else if (a.Cout == 32) {
+  } else if (a.Cout > 16) {
     launch_f32<256, 32, 4>(a, st);
-  } else if (a.Cout == 16) {
+  } else if (a.Cout > 8) {
     launch_f32<256, 16, 2>(a, st);
   } else {
-    return PG_ERR_UNSUPPORTED;
+    launch_f32<256, 8, 1>(a, st);
   }
   PG_CUDA(cudaGetLastError());
   return PG_OK;

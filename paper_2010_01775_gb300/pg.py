@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -103,10 +104,11 @@ def _ptr(x):
 
 
 class Handle:
-    """Owns one library handle; freed with pg_free."""
+    """Owns one library handle; freed with pg_free (before its context)."""
 
     def __init__(self, ctx, ptr, kind):
         self.ctx, self.ptr, self.kind = ctx, ptr, kind
+        ctx._handles.add(self)
 
     def info(self, what):
         v = ctypes.c_uint64()
@@ -120,9 +122,9 @@ class Handle:
         return out
 
     def free(self):
-        if self.ptr:
+        if self.ptr and self.ctx.ptr:
             _lib.pg_free(self.ptr)
-            self.ptr = None
+        self.ptr = None
 
     def __del__(self):
         try:
@@ -136,6 +138,8 @@ class Context:
 
     def __init__(self, stream=None, hbm_budget=0):
         load()
+        self.ptr = None
+        self._handles = weakref.WeakSet()
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -155,7 +159,10 @@ class Context:
         _check(_lib.pg_set_stream(self.ptr, ctypes.c_void_p(stream)), "pg_set_stream")
 
     def destroy(self):
+        """Frees every live handle of this context, then the context."""
         if self.ptr:
+            for h in list(self._handles):
+                h.free()
             _lib.pg_destroy(self.ptr)
             self.ptr = None
 

@@ -65,7 +65,13 @@ PRECISION = dataclasses.replace(
     SCALE, name="precision: 4M photons, 64 blobs, depth 10, split 2000, 128x128, U-Net BF16/FP8, 8M queries",
     H=128, W=128, seed=SEED_BASE + 2)
 
-WORKLOADS = {"tiny": TINY, "scale": SCALE, "precision": PRECISION}
+# A reduced copy of the scale workload for profiler captures (same kernels,
+# a few GB on the device).
+SCALE_SMALL = dataclasses.replace(
+    SCALE, name="scale-small: 262k photons, 16 blobs, depth 10, split 2000, 64x64, U-Net, 512k queries",
+    n_photons=262_144, n_blobs=16, n_queries=524_288, seed=SEED_BASE + 11)
+
+WORKLOADS = {"tiny": TINY, "scale": SCALE, "precision": PRECISION, "scale-small": SCALE_SMALL}
 
 
 def _unit(v):

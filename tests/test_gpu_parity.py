@@ -233,7 +233,14 @@ def test_sample_and_eval(ctx, tiny_scene, H, W, q, seed, stream_id):
     assert np.array_equal(leaf, s["leaf"])
     same = bins == s["bin"]
     assert same.mean() >= 1 - 1e-4
-    assert np.allclose(dirs[same], s["dir"][same], rtol=0, atol=2e-6)
+    # z = -1 + 2 (i + u2)/H is formed in FP32 (abs. error <= 2^-23); the
+    # in-plane part scales by sqrt(1 - z^2), whose error grows as 1/sin(theta)
+    # near the poles; the azimuth adds a few ulps of sincos.
+    st = np.sqrt(np.maximum(1e-12, 1.0 - s["dir"][:, 2] ** 2))
+    tol = 1e-6 + 2.4e-7 / st
+    err = np.abs(dirs.astype(np.float64) - s["dir"])
+    assert np.all(err[same, 2] <= 2.4e-7)
+    assert np.all(err[same, :2] <= tol[same, None])
     nz = same & (s["pdf"] > 0)
     assert np.max(np.abs(pdf[nz] - s["pdf"][nz]) / s["pdf"][nz], initial=0) <= 1e-5
     # Host buffers go through the same kernels.
@@ -254,8 +261,9 @@ def test_sample_and_eval(ctx, tiny_scene, H, W, q, seed, stream_id):
     ok = (leaf >> 31) == 0
     out = torch.empty(q, device="cuda")
     pg.pg_eval_pdf(ctx, g, t, torch.from_numpy(pos).cuda(), torch.from_numpy(dirs).cuda(), q, out)
-    agree = np.isclose(out.cpu().numpy()[ok], pdf[ok], rtol=1e-6)
-    assert agree.mean() >= 1 - 1e-3
+    if ok.any():
+        agree = np.isclose(out.cpu().numpy()[ok], pdf[ok], rtol=1e-6)
+        assert agree.mean() >= 1 - 1e-3
 
 
 # ------------------------------------------------------------------ a6-a7: CNN, FP32
