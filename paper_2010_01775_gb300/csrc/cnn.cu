@@ -295,8 +295,8 @@ pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision p
   const uint32_t A = h->A;
   if (A == 0) return PG_OK;
   const int H = h->H, W = h->W, HW = H * W;
-  const size_t elem = prec == PG_FP32 ? 4 : 2;
-  const size_t per_leaf = act_floats_per_leaf(net, H, W) * elem + 8 * (size_t)HW * 4;
+  const size_t per_leaf = 8 * (size_t)HW * 4 + (prec == PG_FP32 ? act_floats_per_leaf(net, H, W) * 4
+                                                                  : tc_bytes_per_leaf(net, prec, H, W));
   // Activation working set: leaves are processed in chunks of at most ~6 GB.
   uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(A, (6ull << 30) / per_leaf));
   size_t bytes = per_leaf * chunk + 4096;

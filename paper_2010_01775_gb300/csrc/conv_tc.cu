@@ -1,13 +1,732 @@
-// BF16 / FP8 convolutions on tcgen05 tensor cores.
+// a7 on tensor cores: BF16 (and FP8 E4M3) implicit-GEMM convolutions with
+// tcgen05 (5th-generation tensor cores, accumulators in TMEM), fed by TMA.
+//
+// GEMM view of one layer: M = leaves x output pixels (tiles of 128 pixels =
+// whole output rows of one or more leaves), N = output channels (the whole
+// layer, 16..256), K = taps x input channels.  One pipeline stage holds one
+// (tap, channel chunk): a 4-D TMA box {chunk, Wt, Ht, Lt} of the channel-last
+// activation tensor at the tap-shifted origin (out-of-range coordinates are
+// zero-filled by TMA, which implements the "same" zero padding; strided
+// layers use TMA element strides), and a 2-D TMA box of the K-major weights.
+// Both land in shared memory in the canonical K-major swizzled layout that
+// the MMA descriptors describe.
+//
+// Persistent, warp-specialised CTA (192 threads):
+//   warp 0   one thread issues TMA loads into a ring of stages
+//   warp 1   one thread issues tcgen05.mma (M=128, N=Cout) and commits each
+//            stage back to the producer; owns TMEM allocation
+//   warps 2-5 epilogue: tcgen05.ld the accumulator (one pixel row per thread),
+//            bias + ELU, convert, store channel-last (optionally upsampled x2)
+// The accumulator is double-buffered in TMEM so the epilogue of one tile
+// overlaps the main loop of the next.  Every mbarrier wait is bounded (2 s):
+// on expiry the CTA raises PG_ERR_TIMEOUT in the context status word, drains
+// what it issued and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "conv.cuh"
 
 namespace pgi {
 
-pg_status tc_prepare(pg_ctx *, Net *, pg_precision) { return PG_ERR_UNSUPPORTED; }
+namespace {
 
-pg_status forward_tc(pg_ctx *, const Net *, pg_precision, const float *, void *, uint32_t, int, int, float *,
-                     cudaStream_t) {
-  return PG_ERR_UNSUPPORTED;
+constexpr int kThreads = 192;
+constexpr int kBM = 128;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+struct TcArgs {
+  int k, stride, pad;
+  int Cin, chunk, cchunks;
+  int Hout, Wout, HWo;
+  long M;
+  int BN;
+  int Wt, Ht, Lt;
+  int num_tiles, kiters, stages;
+  uint32_t bytes_a, bytes_b;  // per stage
+  uint32_t idesc;
+  uint32_t sbo;
+  int swz;
+  int mma_per_stage, mma_kind;  // 0: kind::f16, 1: kind::f8f6f4
+  uint32_t tmem_cols;
+  // epilogue
+  void *out;
+  int out_cs, out_co, ups, act, out_fp8;
+  float out_mul;   // value multiplier before the output conversion (1/scale for FP8 outputs)
+  float acc_mul;   // accumulator multiplier (product of the FP8 operand scales, 1 otherwise)
+  const float *bias;
+  uint32_t *status;
+};
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.  Returns false when the
+// CTA is aborting (this wait timed out, or another role already gave up).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long limit_ns = kTimeoutNs) {
+  if (mbar_try(bar, parity)) return true;
+  unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > limit_ns) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_4d(const CUtensorMap *map, uint64_t *bar, void *dst, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+      "%6}], [%2];" ::"r"(saddr(dst)),
+      "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(saddr(dst)),
+      "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand in shared memory, rows of `row bytes` swizzled in groups of
+// 8 rows: start address, stride between 8-row groups (SBO), swizzle mode.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, int swz) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;  // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version
+  d |= (uint64_t)(swz & 7) << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Output-tile origin of M-tile t: first leaf, row and column of the tile.
+__device__ __forceinline__ void tile_origin(const TcArgs &a, int t, int &l0, int &y0, int &x0) {
+  long m0 = (long)t * kBM;
+  l0 = (int)(m0 / a.HWo);
+  int r = (int)(m0 % a.HWo);
+  y0 = r / a.Wout;
+  x0 = r % a.Wout;
+}
+
+__device__ __forceinline__ float elu(float v) { return v > 0.0f ? v : expm1f(v); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = smem;
+  uint8_t *sB = sA + (size_t)a.stages * a.bytes_a;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sB + (size_t)a.stages * a.bytes_b);
+  uint64_t *empty = full + a.stages;
+  uint64_t *acc_full = empty + a.stages;
+  uint64_t *acc_empty = acc_full + 2;
+  uint64_t *drain = acc_empty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < a.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"(a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      long issued = 0;
+      for (int t = blockIdx.x; t < a.num_tiles && !*abort_flag; t += gridDim.x) {
+        int l0, y0, x0;
+        tile_origin(a, t, l0, y0, x0);
+        for (int ki = 0; ki < a.kiters; ++ki) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) break;
+          int tap = ki / a.cchunks, cc = ki - tap * a.cchunks;
+          int ky = tap / a.k, kx = tap - ky * a.k;
+          mbar_expect_tx(&full[stage], a.bytes_a + a.bytes_b);
+          tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk, x0 * a.stride + kx - a.pad,
+                      y0 * a.stride + ky - a.pad, l0);
+          tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
+          ++issued;
+          if (++stage == a.stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (*abort_flag) {
+        // Drain: let the last stages' copies land before the CTA exits.
+        long back = issued < a.stages ? issued : a.stages;
+        for (long i = 0; i < back; ++i) {
+          if (--stage < 0) {
+            stage = a.stages - 1;
+            phase ^= 1u;
+          }
+          volatile int never = 0;
+          mbar_wait(&full[stage], phase, &never, 100000000ull);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      int stage = 0;
+      uint32_t phase = 0;
+      int i = 0;
+      const uint32_t a_base = saddr(sA), b_base = saddr(sB);
+      for (int t = blockIdx.x; t < a.num_tiles && !*abort_flag; t += gridDim.x, ++i) {
+        const int buf = i & 1;
+        const uint32_t use = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(&acc_empty[buf], use ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * a.BN);
+        bool ok = true;
+        for (int ki = 0; ki < a.kiters; ++ki) {
+          if (!mbar_wait(&full[stage], phase, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = a_base + (uint32_t)stage * a.bytes_a, sb = b_base + (uint32_t)stage * a.bytes_b;
+          for (int j = 0; j < a.mma_per_stage; ++j) {
+            uint64_t da = smem_desc(sa + 32u * j, a.sbo, a.swz), db = smem_desc(sb + 32u * j, a.sbo, a.swz);
+            uint32_t acc = (ki | j) ? 1u : 0u;
+            if (a.mma_kind == 0) mma_f16(d, da, db, a.idesc, acc);
+            else mma_f8(d, da, db, a.idesc, acc);
+          }
+          mma_commit(&empty[stage]);
+          if (++stage == a.stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[buf]);
+      }
+      // All issued MMAs complete before TMEM is released.
+      mma_commit(drain);
+      volatile int never = 0;
+      mbar_wait(drain, 0, &never, 200000000ull);
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5 own TMEM lane quarters 2,3,0,1
+    const int q = warp & 3;
+    const int m = q * 32 + lane;
+    int i = 0;
+    const int reps = a.ups ? 2 : 1;
+    const int Ho = a.Hout * reps, Wo = a.Wout * reps;
+    for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1) & 1u;
+      if (!mbar_wait(&acc_full[buf], use, abort_flag)) break;
+      tc_fence_after();
+      int l0, y0, x0;
+      tile_origin(a, t, l0, y0, x0);
+      const int xx = m % a.Wt, yy = (m / a.Wt) % a.Ht, ll = m / (a.Wt * a.Ht);
+      const int leaf = l0 + ll, y = y0 + yy, x = x0 + xx;
+      const bool valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.BN);
+      for (int c = 0; c < a.BN; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(trow + (uint32_t)c, r);
+        if (!valid) continue;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          float z = __uint_as_float(r[j]) * a.acc_mul + __ldg(a.bias + c + j);
+          v[j] = (a.act == 1 ? elu(z) : z) * a.out_mul;
+        }
+        for (int dy = 0; dy < reps; ++dy)
+          for (int dx = 0; dx < reps; ++dx) {
+            size_t pix = ((size_t)leaf * Ho + (size_t)(y * reps + dy)) * Wo + (size_t)(x * reps + dx);
+            if (a.out_fp8) {
+              uint8_t *o = (uint8_t *)a.out + pix * a.out_cs + a.out_co + c;
+              uint32_t w[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                __nv_fp8x4_e4m3 p(make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+                w[j] = *reinterpret_cast<uint32_t *>(&p);
+              }
+              *reinterpret_cast<uint4 *>(o) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+              __nv_bfloat16 *o = (__nv_bfloat16 *)a.out + pix * a.out_cs + a.out_co + c;
+              uint32_t w[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                w[j] = *reinterpret_cast<uint32_t *>(&p);
+              }
+              reinterpret_cast<uint4 *>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+              reinterpret_cast<uint4 *>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+          }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(a.status, ST_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- small SIMT kernels
+// First-layer im2col: x_col[m][tap*5 + c] (taps 3x3, 5 channels, zero padded
+// at the map border), columns 45..63 zero.  Input: the FP32 8-channel x0.
+template <typename T>
+__global__ void k_im2col0(const float *__restrict__ x0, long M, int H, int W, T *__restrict__ xcol, float mul) {
+  long m = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  int HW = H * W;
+  long leaf = m / HW;
+  int r = (int)(m % HW), y = r / W, x = r % W;
+  float v[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = 0.0f;
+#pragma unroll
+  for (int tap = 0; tap < 9; ++tap) {
+    int iy = y + tap / 3 - 1, ix = x + tap % 3 - 1;
+    if (iy < 0 || iy >= H || ix < 0 || ix >= W) continue;
+    const float4 *p = reinterpret_cast<const float4 *>(x0 + ((leaf * H + iy) * W + ix) * 8);
+    float4 a = __ldg(p), b = __ldg(p + 1);
+    v[tap * 5 + 0] = a.x;
+    v[tap * 5 + 1] = a.y;
+    v[tap * 5 + 2] = a.z;
+    v[tap * 5 + 3] = a.w;
+    v[tap * 5 + 4] = b.x;
+  }
+  T *o = xcol + m * 64;
+  if constexpr (sizeof(T) == 2) {
+    uint32_t w[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j] * mul, v[2 * j + 1] * mul);
+      w[j] = *reinterpret_cast<uint32_t *>(&p);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) reinterpret_cast<uint4 *>(o)[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+  } else {
+    uint32_t w[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      __nv_fp8x4_e4m3 p(make_float4(v[4 * j] * mul, v[4 * j + 1] * mul, v[4 * j + 2] * mul, v[4 * j + 3] * mul));
+      w[j] = *reinterpret_cast<uint32_t *>(&p);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) reinterpret_cast<uint4 *>(o)[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+  }
+}
+
+__device__ __forceinline__ float load_act(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float load_act(const __nv_fp8_e4m3 *p) { return float(*p); }
+
+// Single-output-channel conv (3x3 or 1x1) + softplus into the map y (FP32).
+template <typename T>
+__global__ void k_cout1_lp(const T *__restrict__ in, int in_cs, int H, int W, int Cin, int k, const float *__restrict__ w,
+                           const float *__restrict__ bias, float in_scale, long M, float *__restrict__ y) {
+  long mg = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (mg >= M) return;
+  int HW = H * W;
+  long leaf = mg / HW;
+  int r = (int)(mg % HW), oy = r / W, ox = r % W, pad = k / 2;
+  float acc = 0.0f;
+  for (int ky = 0; ky < k; ++ky) {
+    int iy = oy + ky - pad;
+    if (iy < 0 || iy >= H) continue;
+    for (int kx = 0; kx < k; ++kx) {
+      int ix = ox + kx - pad;
+      if (ix < 0 || ix >= W) continue;
+      const T *p = in + ((leaf * H + iy) * W + ix) * in_cs;
+      const float *wk = w + (size_t)(ky * k + kx) * Cin;
+      for (int c = 0; c < Cin; ++c) acc = fmaf(load_act(p + c), __ldg(wk + c), acc);
+    }
+  }
+  float v = acc * in_scale + __ldg(bias);
+  y[mg] = fmaxf(v, 0.0f) + log1pf(expf(-fabsf(v)));
+}
+
+// Per-tensor absolute maximum (FP8 activation scale calibration).
+__global__ void k_absmax(const float *__restrict__ x, size_t n, unsigned int *__restrict__ out) {
+  float m = 0.0f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+struct LpLayer {
+  const void *in;
+  int in_cs, in_co, Hin, Win, Cin;
+  void *out;
+  int out_cs, out_co, ups;
+  int Cout, k, stride, act;
+  const void *w;  // [Cout][k*k*Cin] reduced precision, K contiguous
+  const float *bias;
+  float acc_mul, out_mul;
+};
+
+pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStream_t st, uint32_t *status) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return PG_ERR_UNSUPPORTED;
+  const int Hout = L.Hin / L.stride, Wout = L.Win / L.stride, HWo = Hout * Wout;
+  const long M = (long)ns * HWo;
+  if (M == 0) return PG_OK;
+  if (L.Cout % 16 || L.Cout < 16 || L.Cout > 256) return PG_ERR_UNSUPPORTED;
+  // K chunk per stage: one swizzle row of 128, 64 or 32 bytes.
+  int cb = 0;
+  for (int c : {128, 64, 32})
+    if ((L.Cin * es) % c == 0) {
+      cb = c;
+      break;
+    }
+  if (!cb) return PG_ERR_UNSUPPORTED;
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.k = L.k;
+  a.stride = L.stride;
+  a.pad = L.k / 2;
+  a.Cin = L.Cin;
+  a.chunk = cb / es;
+  a.cchunks = L.Cin / a.chunk;
+  a.Hout = Hout;
+  a.Wout = Wout;
+  a.HWo = HWo;
+  a.M = M;
+  a.BN = L.Cout;
+  if (Wout >= kBM) {
+    a.Wt = kBM; a.Ht = 1; a.Lt = 1;
+  } else if (HWo >= kBM) {
+    a.Wt = Wout; a.Ht = kBM / Wout; a.Lt = 1;
+  } else {
+    a.Wt = Wout; a.Ht = Hout; a.Lt = kBM / HWo;
+  }
+  if (a.Wt * a.Ht * a.Lt != kBM || a.Wt * L.stride > 256 || a.Ht * L.stride > 256) return PG_ERR_UNSUPPORTED;
+  a.num_tiles = (int)((M + kBM - 1) / kBM);
+  a.kiters = L.k * L.k * a.cchunks;
+  a.bytes_a = (uint32_t)(kBM * cb);
+  a.bytes_b = (uint32_t)(L.Cout * cb);
+  a.sbo = 8u * (uint32_t)cb;
+  a.swz = cb == 128 ? 2 : (cb == 64 ? 4 : 6);
+  a.mma_per_stage = cb / 32;
+  a.mma_kind = es == 1 ? 1 : 0;
+  // Instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3
+  // (kind::f8f6f4), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+  a.idesc = (1u << 4) | ((es == 2 ? 1u : 0u) << 7) | ((es == 2 ? 1u : 0u) << 10) | ((uint32_t)(L.Cout >> 3) << 17) |
+            ((uint32_t)(kBM >> 4) << 24);
+  uint32_t cols = 32;
+  while (cols < 2u * (uint32_t)L.Cout) cols <<= 1;
+  a.tmem_cols = cols;
+  const int per_sm = cols <= 256 ? 2 : 1;
+  const size_t budget = per_sm == 2 ? 108 * 1024 : 200 * 1024;
+  const size_t stage_bytes = a.bytes_a + a.bytes_b;
+  a.stages = (int)std::min<size_t>(8, (budget - 2048) / stage_bytes);
+  if (a.stages < 2) return PG_ERR_UNSUPPORTED;
+  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16;
+  if (per_sm == 1) smem = std::max<size_t>(smem, 120 * 1024);  // keep one CTA per SM (TMEM > 256 columns)
+  a.out = L.out;
+  a.out_cs = L.out_cs;
+  a.out_co = L.out_co;
+  a.ups = L.ups;
+  a.act = L.act;
+  a.out_fp8 = fp8_out ? 1 : 0;
+  a.out_mul = L.out_mul;
+  a.acc_mul = L.acc_mul;
+  a.bias = L.bias;
+  a.status = status;
+
+  const CUtensorMapDataType dt = es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUtensorMapSwizzle sw =
+      cb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : (cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+  CUtensorMap mA, mB;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)L.Cin, (cuuint64_t)L.Win, (cuuint64_t)L.Hin, (cuuint64_t)ns};
+    cuuint64_t strides[3] = {(cuuint64_t)L.in_cs * es, (cuuint64_t)L.Win * L.in_cs * es,
+                             (cuuint64_t)L.Hin * L.Win * L.in_cs * es};
+    cuuint32_t box[4] = {(cuuint32_t)a.chunk, (cuuint32_t)(a.Wt * L.stride), (cuuint32_t)(a.Ht * L.stride),
+                         (cuuint32_t)a.Lt};
+    cuuint32_t estr[4] = {1, (cuuint32_t)L.stride, (cuuint32_t)L.stride, 1};
+    void *base = (uint8_t *)L.in + (size_t)L.in_co * es;
+    if (enc(&mA, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PG_ERR_UNSUPPORTED;
+  }
+  {
+    const int K = L.k * L.k * L.Cin;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)L.Cout};
+    cuuint64_t strides[1] = {(cuuint64_t)K * es};
+    cuuint32_t box[2] = {(cuuint32_t)a.chunk, (cuuint32_t)L.Cout};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&mB, dt, 2, const_cast<void *>(L.w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PG_ERR_UNSUPPORTED;
+  }
+  PG_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  const int grid = std::min(a.num_tiles, per_sm * num_sms());
+  k_conv_tc<<<grid, kThreads, smem, st>>>(mA, mB, a);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
+}  // namespace
+
+// Reduced-precision weight copies: [Cout][k*k*Cin] (K contiguous), the first
+// layer as [Cout][64] in im2col order (tap*5 + c).  FP8 weights carry one
+// per-tensor scale (amax / 448).
+pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
+  if (!encode_fn()) return PG_ERR_UNSUPPORTED;
+  for (int l = 0; l < net->n_layers; ++l) {
+    Layer &L = net->layers[l];
+    if (L.w_lp && L.w_lp_prec == (int)prec) continue;
+    if (L.w_lp) {
+      ctx_free(ctx, L.w_lp, L.w_lp_bytes);
+      L.w_lp = nullptr;
+    }
+    const int taps = L.k * L.k;
+    const size_t Kf = (size_t)taps * L.cin;  // rows of the FP32 [K][Cout] copy
+    std::vector<float> wf(Kf * L.cout);
+    PG_CUDA(cudaMemcpyAsync(wf.data(), L.w, wf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    PG_CUDA(cudaStreamSynchronize(ctx->stream));
+    const bool first = l == 0;
+    const size_t K = first ? 64 : Kf;
+    std::vector<float> wt((size_t)L.cout * K, 0.0f);
+    for (int o = 0; o < L.cout; ++o) {
+      if (first) {
+        for (int tap = 0; tap < taps; ++tap)
+          for (int c = 0; c < 5; ++c) wt[(size_t)o * K + tap * 5 + c] = wf[((size_t)tap * L.cin + c) * L.cout + o];
+      } else {
+        for (size_t kk = 0; kk < Kf; ++kk) wt[(size_t)o * K + kk] = wf[kk * L.cout + o];
+      }
+    }
+    const int es = prec == PG_FP8_E4M3 ? 1 : 2;
+    float scale = 1.0f;
+    std::vector<uint8_t> host(wt.size() * es);
+    if (es == 2) {
+      for (size_t i = 0; i < wt.size(); ++i) {
+        __nv_bfloat16 b = __float2bfloat16_rn(wt[i]);
+        memcpy(&host[2 * i], &b, 2);
+      }
+    } else {
+      float amax = 0.0f;
+      for (float v : wt) amax = std::max(amax, fabsf(v));
+      scale = amax > 0.0f ? amax / 448.0f : 1.0f;
+      for (size_t i = 0; i < wt.size(); ++i) {
+        __nv_fp8_e4m3 q(wt[i] / scale);
+        memcpy(&host[i], &q, 1);
+      }
+    }
+    void *p;
+    PG_TRY(ctx_alloc(ctx, host.size(), &p));
+    PG_CUDA(cudaMemcpyAsync(p, host.data(), host.size(), cudaMemcpyHostToDevice, ctx->stream));
+    PG_CUDA(cudaStreamSynchronize(ctx->stream));
+    L.w_lp = p;
+    L.w_lp_bytes = host.size();
+    L.w_lp_prec = (int)prec;
+    L.w_scale = scale;
+  }
+  return PG_OK;
+}
+
+pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float *x0, void *actv, uint32_t ns, int H,
+                     int W, float *y, cudaStream_t st) {
+  if (prec != PG_BF16) return PG_ERR_UNSUPPORTED;
+  const int es = 2;
+  typedef __nv_bfloat16 T;
+  const size_t HW = (size_t)H * W;
+  const long M0 = (long)ns * HW;
+  const Layer *Ls = net->layers;
+  uint8_t *act = (uint8_t *)actv;
+  T *xcol = (T *)act;
+  act += align256(M0 * 64 * es);
+  k_im2col0<T><<<ceil_div(M0, 128), 128, 0, st>>>(x0, M0, H, W, xcol, 1.0f);
+  PG_CUDA(cudaGetLastError());
+  auto conv = [&](int li, const void *in, int in_cs, int in_co, int Hin, int Win, int Cin, void *out, int out_cs,
+                  int out_co, int ups) -> pg_status {
+    const Layer &Lr = Ls[li];
+    LpLayer L;
+    L.in = in; L.in_cs = in_cs; L.in_co = in_co; L.Hin = Hin; L.Win = Win; L.Cin = Cin;
+    L.out = out; L.out_cs = out_cs; L.out_co = out_co; L.ups = ups;
+    L.Cout = Lr.cout; L.k = li == 0 ? 1 : Lr.k; L.stride = Lr.stride; L.act = Lr.act;
+    L.w = Lr.w_lp; L.bias = Lr.b; L.acc_mul = 1.0f; L.out_mul = 1.0f;
+    return launch_tc(L, ns, es, false, st, ctx->d_status);
+  };
+  auto head = [&](int li, const T *in, int in_cs, int Cin) -> pg_status {
+    const Layer &Lr = Ls[li];
+    k_cout1_lp<T><<<ceil_div(M0, 256), 256, 0, st>>>(in, in_cs, H, W, Cin, Lr.k, Lr.w, Lr.b, 1.0f, M0, y);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+  };
+  if (net->arch == 0) {
+    const int c = net->widths[0];
+    T *t0 = (T *)act, *t1 = t0 + M0 * c;
+    PG_TRY(conv(0, xcol, 64, 0, H, W, 64, t0, c, 0, 0));
+    PG_TRY(conv(1, t0, c, 0, H, W, c, t1, c, 0, 0));
+    return head(2, t1, c, c);
+  }
+  const int c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
+  const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4, H3 = H / 8, W3 = W / 8;
+  const int k0c = c1 + c0, k1c = c2 + c1, k2c = c3 + c2;
+  T *cat0 = (T *)act;
+  T *t0 = cat0 + ns * HW * k0c;
+  T *t0b = t0 + ns * HW * c0;
+  T *cat1 = t0b + ns * HW * c0;
+  T *t1 = cat1 + ns * HW / 4 * k1c;
+  T *cat2 = t1 + ns * HW / 4 * c1;
+  T *t2 = cat2 + ns * HW / 16 * k2c;
+  T *t3 = t2 + ns * HW / 16 * c2;
+  PG_TRY(conv(0, xcol, 64, 0, H, W, 64, t0, c0, 0, 0));
+  PG_TRY(conv(1, t0, c0, 0, H, W, c0, cat0, k0c, c1, 0));
+  PG_TRY(conv(2, cat0, k0c, c1, H, W, c0, t1, c1, 0, 0));
+  PG_TRY(conv(3, t1, c1, 0, H1, W1, c1, cat1, k1c, c2, 0));
+  PG_TRY(conv(4, cat1, k1c, c2, H1, W1, c1, t2, c2, 0, 0));
+  PG_TRY(conv(5, t2, c2, 0, H2, W2, c2, cat2, k2c, c3, 0));
+  PG_TRY(conv(6, cat2, k2c, c3, H2, W2, c2, t3, c3, 0, 0));
+  PG_TRY(conv(7, t3, c3, 0, H3, W3, c3, cat2, k2c, 0, 1));
+  PG_TRY(conv(8, cat2, k2c, 0, H2, W2, k2c, t2, c2, 0, 0));
+  PG_TRY(conv(9, t2, c2, 0, H2, W2, c2, cat1, k1c, 0, 1));
+  PG_TRY(conv(10, cat1, k1c, 0, H1, W1, k1c, t1, c1, 0, 0));
+  PG_TRY(conv(11, t1, c1, 0, H1, W1, c1, cat0, k0c, 0, 1));
+  PG_TRY(conv(12, cat0, k0c, 0, H, W, k0c, t0, c0, 0, 0));
+  PG_TRY(conv(13, t0, c0, 0, H, W, c0, t0b, c0, 0, 0));
+  return head(14, t0b, c0, c0);
+}
+
+size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W) {
+  const size_t es = prec == PG_FP8_E4M3 ? 1 : 2, HW = (size_t)H * W;
+  size_t n = HW * 64;  // first-layer im2col
+  if (net->arch == 0) return es * (n + 2 * HW * net->widths[0]) + 1024;
+  const size_t c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
+  n += HW * ((c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;
+  return es * n + 1024;
 }
 
 }  // namespace pgi

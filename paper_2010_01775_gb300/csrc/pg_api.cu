@@ -174,6 +174,15 @@ pg_status pg_create(pg_ctx **out, void *stream, size_t budget) {
   }
   c->stream = (cudaStream_t)stream;
   c->budget = budget;
+  // Handles and call scratch come from the device's default stream-ordered
+  // pool; keep freed blocks mapped so that repeated calls reuse them instead
+  // of returning memory to the driver at every synchronisation.
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(uint32_t)) != cudaSuccess) {
     delete c;

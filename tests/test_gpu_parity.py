@@ -335,3 +335,52 @@ def test_budget_and_bad_args(ctx):
     with pytest.raises(pg.PgError) as e:
         pg.pg_build_grid(ctx, torch.from_numpy(ph).cuda(), 100_000, LO, HI, 17, 0, 100)
     assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ a7 on tensor cores
+def _kl_l1(P, Pr):
+    """Per-leaf KL(P_oracle || P_gpu) and L1, the reduced-precision gates."""
+    kl, l1 = [], []
+    for a in range(P.shape[0]):
+        p, q = Pr[a].ravel(), np.maximum(P[a].ravel(), 1e-38)
+        nz = p > 0
+        kl.append(float(np.sum(p[nz] * np.log(p[nz] / q[nz]))))
+        l1.append(float(np.abs(p - P[a].ravel()).sum()))
+    return np.array(kl), np.array(l1)
+
+
+def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_leaves=16):
+    ph = synth.photons(n, blobs, seed)
+    d = torch.from_numpy(ph).cuda()
+    g = pg.pg_build_grid(ctx, d, n, LO, HI, D, 0, thr)
+    h = pg.pg_splat_photons(ctx, g, d, n, n // 2, H, W)
+    blob = synth.net_blob(arch, widths, seed + 1)
+    net = pg.pg_net_load(ctx, blob)
+    m = pg.pg_reconstruct(ctx, h, net, prec)
+    t = pg.pg_build_cdf(ctx, m)
+    tt = pg.export_tables(t)
+    ctx.sync()
+    ref = O.build_grid(ph, LO, HI, D, 0, thr)
+    act, _ = O.active_leaves(ref)
+    idx = np.linspace(0, act.size - 1, min(act.size, max_check_leaves)).astype(np.int64)
+    hr = O.hist_for_active(O.splat(ph, ref, n // 2, H, W), act)
+    hsub = {k: (v[idx] if isinstance(v, np.ndarray) else v) for k, v in hr.items()}
+    yr = O.cnn_forward(O.assemble_inputs(hsub), O.parse_net(blob))
+    Pr, _ = O.normalise(yr)
+    return tt["P"][idx].astype(np.float64), Pr, tt["valid"][idx]
+
+
+@pytest.mark.parametrize("arch,widths,H,W,n,D,thr", [
+    (synth.ARCH_TINY3, (16,), 32, 32, 100_000, 4, 1000),
+    (synth.ARCH_UNET4, (32, 64, 128, 256), 64, 64, 40_000, 5, 2000),
+    (synth.ARCH_UNET4, (32, 64, 128, 256), 32, 32, 20_000, 4, 1500),
+    (synth.ARCH_UNET4, (16, 32, 64, 128), 128, 128, 8_000, 3, 3000),
+])
+def test_cnn_bf16_kl(ctx, arch, widths, H, W, n, D, thr):
+    """BF16 tensor-core network: mean KL(P_oracle || P) <= 1e-3 over leaves."""
+    P, Pr, valid = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 70 + H, pg.PG_BF16)
+    assert np.all(valid == 1)
+    kl, l1 = _kl_l1(P, Pr)
+    print(f"bf16 {arch} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; L1 mean {l1.mean():.2e}")
+    assert kl.mean() <= 1e-3
+    assert np.all(np.isfinite(kl))
