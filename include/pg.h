@@ -227,6 +227,38 @@ void pg_free(void *handle);
 
 const char *pg_status_string(pg_status status);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* Largest photon count pg_sort_photons_noalloc accepts. */
+#define PG_NOALLOC_MAX_PHOTONS (1u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code that must not call cudaMalloc
+ * (for example a renderer plug-in whose host application owns every device
+ * allocation, or a thread that must not block on the driver's allocator).
+ * It computes the first two steps of pg_build_grid -- per-photon Morton codes
+ * (the pg_build_grid quantisation rule) and the stable sort permutation --
+ * without allocating anything: no cudaMalloc/cudaFree, no stream-ordered
+ * allocation, no library routine that allocates.  Its scratch is one static
+ * device array of about 20.3 MB compiled into libpg.so, present on every GPU
+ * that loads the library until the process exits.
+ *   d_photons  n photon records (device memory)
+ *   d_codes    [n] uint64 out, Morton code per original photon (device)
+ *   d_perm     [n] uint32 out, sorted slot -> original index (device)
+ *   cuda_stream  the cudaStream_t the work runs on (0 = legacy default)
+ * Results equal pg_export(PG_GRID_CODES / PG_GRID_PERM) of pg_build_grid on
+ * the same photons and parameters.  n > PG_NOALLOC_MAX_PHOTONS returns
+ * PG_ERR_UNSUPPORTED without touching the GPU.  The call waits for its work
+ * and returns PG_ERR_INVALID_INPUT if a position was not finite.
+ * The first call on a device looks up the scratch's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call uses the same scratch array, which keeps the previous call's
+ * contents (the status word is cleared at the start of each call): calls
+ * that overlap on the GPU -- from several host threads or streams -- race
+ * and must be serialised by the caller. */
+pg_status pg_sort_photons_noalloc(const pg_photon *d_photons, uint64_t n, const pg_grid_params *params,
+                                  uint64_t *d_codes, uint32_t *d_perm, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -503,3 +503,95 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
 }
 
 }  // namespace pgi
+
+// ---------------------------------------------------------------- allocation-free sort
+// Morton codes + stable radix sort with all scratch in one static device
+// array (no allocation by this library, the CUDA runtime or torch), for
+// callers that own every device allocation themselves.
+namespace pgi {
+namespace {
+
+constexpr uint64_t kNoAllocMax = PG_NOALLOC_MAX_PHOTONS;
+constexpr uint64_t kNoAllocTiles = (kNoAllocMax + kSortTile - 1) / kSortTile;
+constexpr size_t kNaKeys = 8 * kNoAllocMax;              // one ping-pong key buffer
+constexpr size_t kNaVals = 4 * kNoAllocMax;              // the spare value buffer
+constexpr size_t kNaHist = 4 * kRadix * (kNoAllocTiles + 1);
+constexpr size_t kNaBytes = 2 * kNaKeys + kNaVals + kNaHist + 4 * kRadix + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_ptr[kMaxDevices];
+
+}  // namespace
+}  // namespace pgi
+
+extern "C" pg_status pg_sort_photons_noalloc(const pg_photon *d_photons, uint64_t n, const pg_grid_params *p,
+                                             uint64_t *d_codes, uint32_t *d_perm, void *cuda_stream) {
+  using namespace pgi;
+  if (n > kNoAllocMax) return PG_ERR_UNSUPPORTED;
+  if (!p || (n && (!d_photons || !d_codes || !d_perm))) return PG_ERR_INVALID_ARG;
+  if (p->max_depth < 0 || p->max_depth > 16) return PG_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->lo[a]) || !isfinite(p->hi[a]) || !(p->hi[a] > p->lo[a])) return PG_ERR_INVALID_ARG;
+  int dev = 0;
+  PG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return PG_ERR_UNSUPPORTED;
+  // One-time set-up on this device: the device address of the static
+  // scratch (the symbol itself is only a host-side stand-in).
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    PG_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const uint32_t nn = (uint32_t)n;
+  uint8_t *q = (uint8_t *)g_noalloc_ptr[dev];
+  uint64_t *kA = (uint64_t *)q; q += kNaKeys;
+  uint64_t *kB = (uint64_t *)q; q += kNaKeys;
+  uint32_t *vT = (uint32_t *)q; q += kNaVals;
+  uint32_t *hist = (uint32_t *)q; q += kNaHist;
+  uint32_t *dtot = (uint32_t *)q; q += 4 * kRadix;
+  uint32_t *status = (uint32_t *)q;
+  PG_CUDA(cudaMemsetAsync(status, 0, 4, st));
+  if (n == 0) return PG_OK;
+  GridGeom gg;
+  for (int a = 0; a < 3; ++a) {
+    gg.lo[a] = p->lo[a];
+    gg.scale[a] = (float)(ldexp(1.0, p->max_depth) / ((double)p->hi[a] - (double)p->lo[a]));
+  }
+  gg.D = p->max_depth;
+  gg.top = (uint32_t)((1u << p->max_depth) - 1u);
+  const int TB = 256;
+  k_morton<<<ceil_div(nn, TB), TB, 0, st>>>(d_photons, nn, gg, d_codes, status);
+  const int passes = (3 * p->max_depth + 7) / 8;
+  if (passes == 0) {
+    k_iota<<<ceil_div(nn, TB), TB, 0, st>>>(d_perm, nn);
+  } else {
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    const uint32_t nblocks = ceil_div(nn, kSortTile);
+    const uint64_t *kin = d_codes;
+    const uint32_t *vin = nullptr;
+    for (int ps = 0; ps < passes; ++ps) {
+      uint64_t *kout = (ps & 1) ? kB : kA;
+      uint32_t *vout = ((passes - 1 - ps) & 1) ? vT : d_perm;
+      int shift = 8 * ps;
+      k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, nn, shift, hist, nblocks);
+      k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot);
+      if (ps == 0)
+        k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, nn, shift, hist, dtot,
+                                                                          nblocks);
+      else
+        k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, nn, shift, hist,
+                                                                           dtot, nblocks);
+      kin = kout;
+      vin = vout;
+    }
+  }
+  PG_CUDA(cudaGetLastError());
+  uint32_t hs = 0;
+  PG_CUDA(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaStreamSynchronize(st));
+  return (hs & ST_INVALID_INPUT) ? PG_ERR_INVALID_INPUT : PG_OK;
+}

@@ -32,7 +32,9 @@ STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_NOT_DEVICE_PTR", 3: "P
 
 EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_use", "pg_build_grid",
             "pg_splat_photons", "pg_net_load", "pg_reconstruct", "pg_map_import", "pg_build_cdf",
-            "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string"]
+            "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string",
+            "pg_sort_photons_noalloc"]
+PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
 class PgError(RuntimeError):
@@ -70,6 +72,7 @@ def load(path: str = LIB_PATH):
         "pg_sample_dirs": [P, P, P, P, u64, u64, u32, P, P, P, P],
         "pg_eval_pdf": [P, P, P, P, P, u64, P],
         "pg_info": [P, i32, ctypes.POINTER(u64)], "pg_export": [P, P, i32, P, sz],
+        "pg_sort_photons_noalloc": [P, u64, ctypes.POINTER(pg_grid_params), P, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -224,6 +227,15 @@ def pg_sample_dirs(ctx, grid, tables, pos, q, seed, stream_id, dirs, pdf, leaf, 
 
 def pg_eval_pdf(ctx, grid, tables, pos, dirs, q, pdf):
     _check(_lib.pg_eval_pdf(ctx.ptr, grid.ptr, tables.ptr, _ptr(pos), _ptr(dirs), q, _ptr(pdf)), "pg_eval_pdf")
+
+
+def pg_sort_photons_noalloc(photons, n, lo, hi, max_depth, codes, perm, stream=0):
+    """Morton codes and stable sort permutation with no device allocation
+    (scratch is a static device array; n <= PG_NOALLOC_MAX_PHOTONS)."""
+    load()
+    prm = pg_grid_params((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi), max_depth, 0, 0)
+    _check(_lib.pg_sort_photons_noalloc(_ptr(photons), n, ctypes.byref(prm), _ptr(codes), _ptr(perm),
+                                        ctypes.c_void_p(stream)), "pg_sort_photons_noalloc")
 
 
 def pg_sync(ctx):
