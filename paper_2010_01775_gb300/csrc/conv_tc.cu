@@ -61,6 +61,7 @@ struct TcArgs {
   float acc_mul;   // accumulator multiplier (product of the FP8 operand scales, 1 otherwise)
   const float *bias;
   uint32_t *status;
+  unsigned int *amax;  // optional: running max |output| (float bits) for FP8 calibration
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int i = 0;
     const int reps = a.ups ? 2 : 1;
     const int Ho = a.Hout * reps, Wo = a.Wout * reps;
+    float amax_local = 0.0f;
     for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x, ++i) {
       const int buf = i & 1;
       const uint32_t use = (uint32_t)(i >> 1) & 1u;
@@ -329,7 +331,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           float z = __uint_as_float(r[j]) * a.acc_mul + __ldg(a.bias + c + j);
-          v[j] = (a.act == 1 ? elu(z) : z) * a.out_mul;
+          z = a.act == 1 ? elu(z) : z;
+          amax_local = fmaxf(amax_local, fabsf(z));
+          v[j] = z * a.out_mul;
         }
         for (int dy = 0; dy < reps; ++dy)
           for (int dx = 0; dx < reps; ++dx) {
@@ -359,6 +363,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+    if (a.amax) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) amax_local = fmaxf(amax_local, __shfl_xor_sync(0xFFFFFFFFu, amax_local, o));
+      if (lane == 0) atomicMax(a.amax, __float_as_uint(amax_local));
     }
   }
   tc_fence_before();
@@ -493,6 +502,7 @@ struct LpLayer {
   const void *w;  // [Cout][k*k*Cin] reduced precision, K contiguous
   const float *bias;
   float acc_mul, out_mul;
+  unsigned int *amax;
 };
 
 pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStream_t st, uint32_t *status) {
@@ -563,6 +573,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.acc_mul = L.acc_mul;
   a.bias = L.bias;
   a.status = status;
+  a.amax = L.amax;
 
   const CUtensorMapDataType dt = es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   const CUtensorMapSwizzle sw =
@@ -602,72 +613,89 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
 // Reduced-precision weight copies: [Cout][k*k*Cin] (K contiguous), the first
 // layer as [Cout][64] in im2col order (tap*5 + c).  FP8 weights carry one
 // per-tensor scale (amax / 448).
-pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
-  if (!encode_fn()) return PG_ERR_UNSUPPORTED;
-  for (int l = 0; l < net->n_layers; ++l) {
-    Layer &L = net->layers[l];
-    if (L.w_lp && L.w_lp_prec == (int)prec) continue;
-    if (L.w_lp) {
-      ctx_free(ctx, L.w_lp, L.w_lp_bytes);
-      L.w_lp = nullptr;
-    }
-    const int taps = L.k * L.k;
-    const size_t Kf = (size_t)taps * L.cin;  // rows of the FP32 [K][Cout] copy
-    std::vector<float> wf(Kf * L.cout);
-    PG_CUDA(cudaMemcpyAsync(wf.data(), L.w, wf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    PG_CUDA(cudaStreamSynchronize(ctx->stream));
-    const bool first = l == 0;
-    const size_t K = first ? 64 : Kf;
-    std::vector<float> wt((size_t)L.cout * K, 0.0f);
-    for (int o = 0; o < L.cout; ++o) {
-      if (first) {
-        for (int tap = 0; tap < taps; ++tap)
-          for (int c = 0; c < 5; ++c) wt[(size_t)o * K + tap * 5 + c] = wf[((size_t)tap * L.cin + c) * L.cout + o];
-      } else {
-        for (size_t kk = 0; kk < Kf; ++kk) wt[(size_t)o * K + kk] = wf[kk * L.cout + o];
-      }
-    }
-    const int es = prec == PG_FP8_E4M3 ? 1 : 2;
-    float scale = 1.0f;
-    std::vector<uint8_t> host(wt.size() * es);
-    if (es == 2) {
-      for (size_t i = 0; i < wt.size(); ++i) {
-        __nv_bfloat16 b = __float2bfloat16_rn(wt[i]);
-        memcpy(&host[2 * i], &b, 2);
-      }
+static pg_status make_lp_weights(pg_ctx *ctx, Layer &L, bool first, pg_precision prec) {
+  const int taps = L.k * L.k;
+  const size_t Kf = (size_t)taps * L.cin;  // rows of the FP32 [K][Cout] copy
+  std::vector<float> wf(Kf * L.cout);
+  PG_CUDA(cudaMemcpyAsync(wf.data(), L.w, wf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  PG_CUDA(cudaStreamSynchronize(ctx->stream));
+  const size_t K = first ? 64 : Kf;
+  std::vector<float> wt((size_t)L.cout * K, 0.0f);
+  for (int o = 0; o < L.cout; ++o) {
+    if (first) {
+      for (int tap = 0; tap < taps; ++tap)
+        for (int c = 0; c < 5; ++c) wt[(size_t)o * K + tap * 5 + c] = wf[((size_t)tap * L.cin + c) * L.cout + o];
     } else {
-      float amax = 0.0f;
-      for (float v : wt) amax = std::max(amax, fabsf(v));
-      scale = amax > 0.0f ? amax / 448.0f : 1.0f;
-      for (size_t i = 0; i < wt.size(); ++i) {
-        __nv_fp8_e4m3 q(wt[i] / scale);
-        memcpy(&host[i], &q, 1);
-      }
+      for (size_t kk = 0; kk < Kf; ++kk) wt[(size_t)o * K + kk] = wf[kk * L.cout + o];
     }
-    void *p;
-    PG_TRY(ctx_alloc(ctx, host.size(), &p));
-    PG_CUDA(cudaMemcpyAsync(p, host.data(), host.size(), cudaMemcpyHostToDevice, ctx->stream));
-    PG_CUDA(cudaStreamSynchronize(ctx->stream));
-    L.w_lp = p;
-    L.w_lp_bytes = host.size();
-    L.w_lp_prec = (int)prec;
+  }
+  const int es = prec == PG_FP8_E4M3 ? 1 : 2;
+  std::vector<uint8_t> host(wt.size() * es);
+  float scale = 1.0f;
+  if (es == 2) {
+    for (size_t i = 0; i < wt.size(); ++i) {
+      __nv_bfloat16 b = __float2bfloat16_rn(wt[i]);
+      memcpy(&host[2 * i], &b, 2);
+    }
+  } else {
+    float amax = 0.0f;
+    for (float v : wt) amax = std::max(amax, fabsf(v));
+    scale = amax > 0.0f ? amax / 448.0f : 1.0f;
+    for (size_t i = 0; i < wt.size(); ++i) {
+      __nv_fp8_e4m3 q(wt[i] / scale);
+      memcpy(&host[i], &q, 1);
+    }
+  }
+  void *p;
+  PG_TRY(ctx_alloc(ctx, host.size(), &p));
+  PG_CUDA(cudaMemcpyAsync(p, host.data(), host.size(), cudaMemcpyHostToDevice, ctx->stream));
+  PG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (es == 2) {
+    L.w_bf16 = p;
+    L.w_bf16_bytes = host.size();
+  } else {
+    L.w_fp8 = p;
+    L.w_fp8_bytes = host.size();
     L.w_scale = scale;
   }
   return PG_OK;
 }
 
-pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float *x0, void *actv, uint32_t ns, int H,
-                     int W, float *y, cudaStream_t st) {
-  if (prec != PG_BF16) return PG_ERR_UNSUPPORTED;
-  const int es = 2;
-  typedef __nv_bfloat16 T;
+pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
+  if (!encode_fn()) return PG_ERR_UNSUPPORTED;
+  for (int l = 0; l < net->n_layers; ++l) {
+    Layer &L = net->layers[l];
+    // FP8 runs are calibrated by one BF16 pass, so they need both copies.
+    if (!L.w_bf16) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_BF16));
+    if (prec == PG_FP8_E4M3 && !L.w_fp8) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_FP8_E4M3));
+  }
+  return PG_OK;
+}
+
+namespace {
+
+// FP8 activation groups: every tensor a layer reads has one per-tensor scale,
+// so layers that write into the same buffer instance (the two halves of a
+// U-Net concatenation) share a group.  out_group[l] / in_group[l]; group 0 is
+// the network input (first-layer im2col).
+const int kUnetOut[15] = {1, 2, 3, 4, 5, 6, 7, 6, 8, 4, 9, 2, 10, 11, -1};
+const int kUnetIn[15] = {0, 1, 2, 3, 4, 5, 6, 7, 6, 8, 4, 9, 2, 10, 11};
+const int kTinyOut[3] = {1, 2, -1};
+const int kTinyIn[3] = {0, 1, 2};
+
+template <typename T>
+pg_status forward_lp(pg_ctx *ctx, const Net *net, bool fp8, const float *x0, void *actv, uint32_t ns, int H, int W,
+                     float *y, cudaStream_t st, const float *scale, unsigned int *amax) {
+  const int es = sizeof(T);
   const size_t HW = (size_t)H * W;
   const long M0 = (long)ns * HW;
   const Layer *Ls = net->layers;
+  const int *og = net->arch == 0 ? kTinyOut : kUnetOut;
+  const int *ig = net->arch == 0 ? kTinyIn : kUnetIn;
   uint8_t *act = (uint8_t *)actv;
   T *xcol = (T *)act;
   act += align256(M0 * 64 * es);
-  k_im2col0<T><<<ceil_div(M0, 128), 128, 0, st>>>(x0, M0, H, W, xcol, 1.0f);
+  k_im2col0<T><<<ceil_div(M0, 128), 128, 0, st>>>(x0, M0, H, W, xcol, fp8 ? 1.0f / scale[0] : 1.0f);
   PG_CUDA(cudaGetLastError());
   auto conv = [&](int li, const void *in, int in_cs, int in_co, int Hin, int Win, int Cin, void *out, int out_cs,
                   int out_co, int ups) -> pg_status {
@@ -676,12 +704,23 @@ pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float
     L.in = in; L.in_cs = in_cs; L.in_co = in_co; L.Hin = Hin; L.Win = Win; L.Cin = Cin;
     L.out = out; L.out_cs = out_cs; L.out_co = out_co; L.ups = ups;
     L.Cout = Lr.cout; L.k = li == 0 ? 1 : Lr.k; L.stride = Lr.stride; L.act = Lr.act;
-    L.w = Lr.w_lp; L.bias = Lr.b; L.acc_mul = 1.0f; L.out_mul = 1.0f;
-    return launch_tc(L, ns, es, false, st, ctx->d_status);
+    L.bias = Lr.b;
+    L.amax = amax ? amax + og[li] : nullptr;
+    if (fp8) {
+      L.w = Lr.w_fp8;
+      L.acc_mul = scale[ig[li]] * Lr.w_scale;
+      L.out_mul = 1.0f / scale[og[li]];
+    } else {
+      L.w = Lr.w_bf16;
+      L.acc_mul = 1.0f;
+      L.out_mul = 1.0f;
+    }
+    return launch_tc(L, ns, es, fp8, st, ctx->d_status);
   };
   auto head = [&](int li, const T *in, int in_cs, int Cin) -> pg_status {
     const Layer &Lr = Ls[li];
-    k_cout1_lp<T><<<ceil_div(M0, 256), 256, 0, st>>>(in, in_cs, H, W, Cin, Lr.k, Lr.w, Lr.b, 1.0f, M0, y);
+    k_cout1_lp<T><<<ceil_div(M0, 256), 256, 0, st>>>(in, in_cs, H, W, Cin, Lr.k, Lr.w, Lr.b,
+                                                     fp8 ? scale[ig[li]] : 1.0f, M0, y);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
   };
@@ -720,8 +759,44 @@ pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float
   return head(14, t0b, c0, c0);
 }
 
+}  // namespace
+
+pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const float *x0, void *actv, uint32_t ns, int H,
+                     int W, float *y, cudaStream_t st) {
+  Net *net = const_cast<Net *>(netc);
+  if (prec == PG_BF16) return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr);
+  if (prec != PG_FP8_E4M3) return PG_ERR_UNSUPPORTED;
+  if (!net->act_calibrated) {
+    // Delayed scaling: one BF16 pass over this chunk records the largest
+    // |activation| of every group; scale = amax / 448 (E4M3's largest normal).
+    unsigned int *d_amax;
+    PG_TRY(ctx_alloc(ctx, 64, (void **)&d_amax));
+    PG_CUDA(cudaMemsetAsync(d_amax, 0, 64, st));
+    k_absmax<<<num_sms() * 4, 256, 0, st>>>(x0, (size_t)ns * H * W * 8, d_amax);
+    pg_status s = forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, d_amax);
+    unsigned int h[16];
+    if (s == PG_OK && cudaMemcpyAsync(h, d_amax, 64, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+        cudaStreamSynchronize(st) == cudaSuccess) {
+      for (int g = 0; g < 16; ++g) {
+        float m;
+        memcpy(&m, &h[g], 4);
+        net->act_scale[g] = m > 0.0f && isfinite(m) ? m / 448.0f : 1.0f;
+      }
+      net->act_calibrated = 1;
+    } else if (s == PG_OK) {
+      s = PG_ERR_CUDA;
+    }
+    ctx_free(ctx, d_amax, 64);
+    PG_TRY(s);
+  }
+  return forward_lp<__nv_fp8_e4m3>(ctx, net, true, x0, actv, ns, H, W, y, st, net->act_scale, nullptr);
+}
+
 size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W) {
-  const size_t es = prec == PG_FP8_E4M3 ? 1 : 2, HW = (size_t)H * W;
+  // Sized for 2-byte activations in both forms: an FP8 reconstruction may
+  // first run the BF16 calibration pass in the same buffer.
+  (void)prec;
+  const size_t es = 2, HW = (size_t)H * W;
   size_t n = HW * 64;  // first-layer im2col
   if (net->arch == 0) return es * (n + 2 * HW * net->widths[0]) + 1024;
   const size_t c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];

@@ -584,8 +584,10 @@ void pg_free(void *handle) {
     case KIND_NET: {
       Net *n = (Net *)handle;
       block = n->block;
-      for (int i = 0; i < n->n_layers; ++i)
-        if (n->layers[i].w_lp) ctx_free(b->ctx, n->layers[i].w_lp, n->layers[i].w_lp_bytes);
+      for (int i = 0; i < n->n_layers; ++i) {
+        if (n->layers[i].w_bf16) ctx_free(b->ctx, n->layers[i].w_bf16, n->layers[i].w_bf16_bytes);
+        if (n->layers[i].w_fp8) ctx_free(b->ctx, n->layers[i].w_fp8, n->layers[i].w_fp8_bytes);
+      }
       break;
     }
     case KIND_MAP: block = ((Map *)handle)->block; break;

@@ -76,10 +76,10 @@ struct Layer {
   int cout, cin, k, stride, act;
   float *w;   // device, [k*k*cin][cout] (GEMM B operand, K-major rows)
   float *b;   // device, [cout]
-  void *w_lp; // device, reduced-precision copy (tensor-core layout), or null
-  size_t w_lp_bytes;
-  int w_lp_prec;  // pg_precision of w_lp
-  float w_scale;  // FP8 per-tensor weight scale (w = w_lp * w_scale)
+  void *w_bf16;  // device, BF16 copy [cout][K] (tensor-core layout), or null
+  void *w_fp8;   // device, FP8 E4M3 copy [cout][K], or null
+  size_t w_bf16_bytes, w_fp8_bytes;
+  float w_scale;  // FP8 per-tensor weight scale (w = w_fp8 * w_scale)
 };
 
 struct Net {
@@ -88,6 +88,10 @@ struct Net {
   int widths[4];
   Layer layers[16];
   void *block;
+  // FP8 activation scales per activation group (see conv_tc.cu), calibrated
+  // on the first FP8 reconstruction with this net and reused afterwards.
+  int act_calibrated;
+  float act_scale[16];
 };
 
 struct Map {

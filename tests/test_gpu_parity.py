@@ -349,7 +349,7 @@ def _kl_l1(P, Pr):
     return np.array(kl), np.array(l1)
 
 
-def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_leaves=16):
+def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_leaves=16, return_inputs=False):
     ph = synth.photons(n, blobs, seed)
     d = torch.from_numpy(ph).cuda()
     g = pg.pg_build_grid(ctx, d, n, LO, HI, D, 0, thr)
@@ -365,8 +365,12 @@ def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_le
     idx = np.linspace(0, act.size - 1, min(act.size, max_check_leaves)).astype(np.int64)
     hr = O.hist_for_active(O.splat(ph, ref, n // 2, H, W), act)
     hsub = {k: (v[idx] if isinstance(v, np.ndarray) else v) for k, v in hr.items()}
-    yr = O.cnn_forward(O.assemble_inputs(hsub), O.parse_net(blob))
+    x = O.assemble_inputs(hsub)
+    netp = O.parse_net(blob)
+    yr = O.cnn_forward(x, netp)
     Pr, _ = O.normalise(yr)
+    if return_inputs:
+        return tt["P"][idx].astype(np.float64), Pr, tt["valid"][idx], x, netp
     return tt["P"][idx].astype(np.float64), Pr, tt["valid"][idx]
 
 
@@ -383,4 +387,69 @@ def test_cnn_bf16_kl(ctx, arch, widths, H, W, n, D, thr):
     kl, l1 = _kl_l1(P, Pr)
     print(f"bf16 {arch} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; L1 mean {l1.mean():.2e}")
     assert kl.mean() <= 1e-3
+    assert np.all(np.isfinite(kl))
+
+
+def _e4m3_emulated_P(x, net):
+    """The same network in float64 with every conv input and weight cast to
+    E4M3 (torch.float8_e4m3fn) under a per-tensor amax/448 scale, the head's
+    weights kept FP32: what per-tensor FP8 quantisation alone does."""
+    F = torch.nn.functional
+
+    def q(t):
+        s = t.abs().max() / 448.0
+        s = s if s > 0 else torch.tensor(1.0, dtype=torch.float64)
+        return (t / s).to(torch.float8_e4m3fn).to(torch.float64) * s
+
+    Ls = net["layers"]
+    last = len(Ls) - 1
+
+    def c(h, i):
+        cout, cin, k, st, a, w, b = Ls[i]
+        wt = torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2)
+        h = F.conv2d(q(h), wt if i == last else q(wt), torch.from_numpy(b.astype(np.float64)), stride=st,
+                     padding=k // 2)
+        return F.elu(h) if a == O.ACT_ELU else (F.softplus(h) if a == O.ACT_SOFTPLUS else h)
+
+    t = torch.from_numpy(x).permute(0, 3, 1, 2)
+    if net["arch"] == O.ARCH_TINY3:
+        y = c(c(c(t, 0), 1), 2)
+    else:
+        up = lambda h: F.interpolate(h, scale_factor=2, mode="nearest")
+        e0 = c(c(t, 0), 1)
+        e1 = c(c(e0, 2), 3)
+        e2 = c(c(e1, 4), 5)
+        e3 = c(c(e2, 6), 7)
+        d2 = c(c(torch.cat([up(e3), e2], 1), 8), 9)
+        d1 = c(c(torch.cat([up(d2), e1], 1), 10), 11)
+        d0 = c(c(torch.cat([up(d1), e0], 1), 12), 13)
+        y = c(d0, 14)
+    P, _ = O.normalise(y[:, 0].numpy())
+    return P
+
+
+@pytest.mark.parametrize("arch,widths,H,W,n,D,thr", [
+    (synth.ARCH_UNET4, (32, 64, 128, 256), 64, 64, 40_000, 5, 2000),
+    (synth.ARCH_UNET4, (32, 64, 128, 256), 128, 128, 8_000, 3, 3000),
+    (synth.ARCH_TINY3, (32,), 32, 32, 100_000, 4, 1000),
+])
+def test_cnn_fp8_kl(ctx, arch, widths, H, W, n, D, thr):
+    """FP8 E4M3 network (per-tensor scales, FP32 accumulation).
+
+    E4M3 keeps 3 mantissa bits (relative rounding error up to 2^-4) at every
+    layer input and weight.  With seeded He-normal weights the head's
+    pre-activations span about -115..+250, so softplus turns that noise into
+    large relative changes of small bins: a float64 emulation of the same
+    network with E4M3 casts (torch.float8_e4m3fn, per-tensor amax scaling)
+    gives mean KL 0.021 on the 64x64 case, while BF16 gives 9e-5.  The gate
+    for FP8 is therefore relative to that emulation run on the same leaves:
+    mean KL <= 1.5 x the emulation's + 2e-3 (BF16 meets 1e-3 outright)."""
+    P, Pr, valid, x, net = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 80 + H, pg.PG_FP8_E4M3,
+                                    return_inputs=True)
+    assert np.all(valid == 1)
+    kl, l1 = _kl_l1(P, Pr)
+    kle, _ = _kl_l1(_e4m3_emulated_P(x, net), Pr)
+    print(f"fp8 {arch} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; L1 mean {l1.mean():.2e}; "
+          f"E4M3 emulation KL mean {kle.mean():.2e}")
+    assert kl.mean() <= 1.5 * kle.mean() + 2e-3
     assert np.all(np.isfinite(kl))
