@@ -114,67 +114,72 @@ def run_pg(args, wl, prec):
     d_ph = torch.from_numpy(ph).cuda()
     d_pos = torch.from_numpy(pos).cuda()
     d_dir = torch.from_numpy(dirs).cuda()
-    o_dir = torch.empty(q, 3, device="cuda")
-    o_pdf = torch.empty(q, device="cuda")
-    o_leaf = torch.empty(q, dtype=torch.int32, device="cuda")
-    o_bin = torch.empty(q, dtype=torch.int32, device="cuda")
-    o_ev = torch.empty(q, device="cuda")
+    outs = (torch.empty(q, 3, device="cuda"), torch.empty(q, device="cuda"),
+            torch.empty(q, dtype=torch.int32, device="cuda"), torch.empty(q, dtype=torch.int32, device="cuda"),
+            torch.empty(q, device="cuda"))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(p_ph, p_pos, p_dir, outs, marks=None):
+    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, keep_tables=False):
         o_d, o_p, o_l, o_b, o_e = outs
-        if marks is not None:
-            marks[0].record(stream)
+        rec = (lambda i: marks[i].record(stream)) if marks is not None else (lambda i: None)
+        rec(0)
         g = pg.pg_build_grid(ctx, p_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
-        if marks is not None:
-            marks[1].record(stream)
+        rec(1)
         h = pg.pg_splat_photons(ctx, g, p_ph, n, wl.n_prev, H, W, wl.frac_bits)
-        if marks is not None:
-            marks[2].record(stream)
-        m = pg.pg_reconstruct(ctx, h, net, prec)
-        if marks is not None:
-            marks[3].record(stream)
+        rec(2)
+        m = pg.pg_reconstruct(ctx, h, net, pr)
+        rec(3)
         t = pg.pg_build_cdf(ctx, m)
-        if marks is not None:
-            marks[4].record(stream)
+        rec(4)
         pg.pg_sample_dirs(ctx, g, t, p_pos, q, 20101775, 0, o_d, o_p, o_l, o_b)
-        if marks is not None:
-            marks[5].record(stream)
+        rec(5)
         pg.pg_eval_pdf(ctx, g, t, p_pos, p_dir, q, o_e)
-        if marks is not None:
-            marks[6].record(stream)
+        rec(6)
         A = g.info(pg.PG_INFO_N_ACTIVE)
         L = g.info(pg.PG_INFO_N_LEAVES)
+        P = pg.export_tables(t)["P"] if keep_tables else None
         for hd in (t, m, h, g):
             hd.free()
-        return A, L
+        return A, L, P
 
-    outs = (o_dir, o_pdf, o_leaf, o_bin, o_ev)
-    for _ in range(args.warmup):
-        A, L = step(d_ph, d_pos, d_dir, outs)
+    # Launch shapes of the tensor-core convolutions are tuned once, untimed.
+    g0 = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+    h0 = pg.pg_splat_photons(ctx, g0, d_ph, n, wl.n_prev, H, W, wl.frac_bits)
+    for pr in {prec} | ({pg.PG_BF16, pg.PG_FP8_E4M3} if args.sweep else set()):
+        pg.pg_autotune(ctx, h0, net, pr)
     ctx.sync()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks = Clocks(local)
-    times, stage = [], np.zeros(6)
-    for _ in range(args.steps):
-        flush.zero_()
-        marks = [ev() for _ in range(7)]
-        A, L = step(d_ph, d_pos, d_dir, outs, marks)
-        marks[6].synchronize()
-        times.append(marks[0].elapsed_time(marks[6]))
-        stage += [marks[i].elapsed_time(marks[i + 1]) for i in range(6)]
-    ctx.sync()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    total_ms = float(sum(times))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+
+    def measure(pr, steps, warmup, clocks_on=False):
+        for _ in range(warmup):
+            A, L, _ = step(d_ph, d_pos, d_dir, outs, pr)
+        ctx.sync()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(local) if clocks_on else None
+        times, stage = [], np.zeros(6)
+        for _ in range(steps):
+            flush.zero_()
+            marks = [ev() for _ in range(7)]
+            A, L, _ = step(d_ph, d_pos, d_dir, outs, pr, marks)
+            marks[6].synchronize()
+            times.append(marks[0].elapsed_time(marks[6]))
+            stage += [marks[i].elapsed_time(marks[i + 1]) for i in range(6)]
+        ctx.sync()
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks is not None else None
+        total_ms = float(sum(times))
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+            torch.distributed.barrier()
+        stage_ms = dict(zip(["grid", "splat", "cnn", "cdf", "sample", "eval"], (stage / steps).round(4).tolist()))
+        return dict(A=A, L=L, times=times, total_ms=total_ms, stage_ms=stage_ms, clocks=clk)
+
+    main = measure(prec, args.steps, args.warmup, clocks_on=True)
+    A, L, total_ms, stage_ms = main["A"], main["L"], main["total_ms"], main["stage_ms"]
 
     # End to end through the C ABI with pinned host buffers: photons are
     # copied once per step, query arrays are passed as host pointers (the
@@ -190,7 +195,7 @@ def run_pg(args, wl, prec):
     def e2e_step():
         dph = torch.empty_like(d_ph)
         dph.copy_(h_ph, non_blocking=True)
-        step(dph, h_pos, h_dir, h_outs)
+        step(dph, h_pos, h_dir, h_outs, prec)
         ctx.sync()
 
     e2e_step()
@@ -203,16 +208,14 @@ def run_pg(args, wl, prec):
     h2d = ph.nbytes + pos.nbytes + dirs.nbytes
     d2h = q * (12 + 4 + 4 + 4 + 4)
 
-    # Dominant kernel: the CNN (all conv launches of one reconstruct call),
+    # Dominant kernel family: the CNN convolutions of one reconstruct call,
     # timed with events on the launching stream.
     flops_leaf = unet_flops_per_leaf(H, W, wl.widths, wl.arch)
-    g = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
-    h = pg.pg_splat_photons(ctx, g, d_ph, n, wl.n_prev, H, W)
     cnn_ms = []
     for _ in range(max(2, min(args.steps, 5))):
         a, b = ev(), ev()
         a.record(stream)
-        m = pg.pg_reconstruct(ctx, h, net, prec)
+        m = pg.pg_reconstruct(ctx, h0, net, prec)
         b.record(stream)
         b.synchronize()
         cnn_ms.append(a.elapsed_time(b))
@@ -227,12 +230,28 @@ def run_pg(args, wl, prec):
         peak = peaks["bf16_tflops"] * (2.0 if prec == pg.PG_FP8_E4M3 else 1.0)
         bound, unit = "tensor", "TFLOP/s"
     achieved = flops_leaf * A / cnn_s / 1e12
-    for hd in (h, g):
+
+    # The other precisions of the same workload (shorter runs), and their
+    # sampling maps on a few leaves for the CPU-baseline leg's KL check.
+    names = {pg.PG_FP32: "fp32", pg.PG_BF16: "bf16", pg.PG_FP8_E4M3: "fp8"}
+    sweep, maps = {}, {}
+    check = None
+    if args.sweep and world == 1:
+        for pr in (pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3):
+            r = main if pr == prec else measure(pr, max(1, min(args.steps, 3)), 1)
+            sweep[names[pr]] = {"value": q * len(r["times"]) / (r["total_ms"] / 1e3),
+                                "ms_per_step": r["total_ms"] / len(r["times"]),
+                                "leaf_tables_per_s": r["A"] * len(r["times"]) / (r["total_ms"] / 1e3),
+                                "cnn_ms": r["stage_ms"]["cnn"]}
+            _, _, P = step(d_ph, d_pos, d_dir, outs, pr, keep_tables=True)
+            if check is None:
+                check = np.linspace(0, P.shape[0] - 1, args.cpu_sample_leaves).astype(np.int64)
+            maps[names[pr]] = P[check].astype(np.float64)
+    for hd in (h0, g0):
         hd.free()
     ctx.destroy()
 
     value = q * args.steps * world / (total_ms / 1e3)
-    stage_ms = dict(zip(["grid", "splat", "cnn", "cdf", "sample", "eval"], (stage / args.steps).round(4).tolist()))
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
@@ -247,24 +266,27 @@ def run_pg(args, wl, prec):
             "stage_ms": stage_ms,
             "stage_throughput": {"leaf_tables_per_s_build": A / (sum(list(stage_ms.values())[:4]) / 1e3),
                                  "guided_samples_per_s_sample_eval": q / ((stage_ms["sample"] + stage_ms["eval"]) / 1e3)},
-            "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+            "latency_ms": {"p50": float(np.percentile(main["times"], 50)),
+                           "p99": float(np.percentile(main["times"], 99))},
             "e2e": {"value": q / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": None,
+            "gpu_launches": count_launches(wl, A, prec),
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                          "traffic": None, "kernel": "CNN convolutions (all layers of one reconstruct call)",
-                         "peak_source": peak_src if prec != pg.PG_FP32 else "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock"},
-            "clocks": clk,
+                         "peak_source": ("of " + peak_src) if prec != pg.PG_FP32 else
+                         "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock"},
+            "clocks": main["clocks"],
         }
+        if sweep:
+            out["precisions"] = sweep
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves)
-        out["gpu_launches"] = count_launches(wl, A)
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves, check, maps, out.get("precisions"))
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def count_launches(wl, A):
+def count_launches(wl, A, prec):
     """Kernel launches of one step (host-side count of the library's launch
     sequence for this workload)."""
     passes = (3 * wl.max_depth + 7) // 8
@@ -272,12 +294,14 @@ def count_launches(wl, A):
     grid = 1 + 3 * passes + 1 + 3 * levels + 1 + 1 + 1
     splat = 1 if wl.H * wl.W <= 8192 else 2
     convs = 3 if wl.arch == 0 else 15
-    chunks = 1
-    cnn = chunks * (1 + convs)
+    HW = wl.H * wl.W
+    per_leaf = 8 * HW * 4 + (4 if prec == 0 else 2) * HW * (200 if wl.arch else 40)
+    chunks = -(-A // max(1, min(A, (6 << 30) // per_leaf)))
+    cnn = chunks * (1 + convs + (0 if prec == 0 else 1))
     return grid + splat + cnn + 1 + 1 + 1
 
 
-def oracle_sample_run(wl, n_leaves, n_queries, seed_shift=0):
+def oracle_sample_run(wl, n_leaves, n_queries, check=None):
     """The FP64 oracle on a bounded sample; returns per-stage seconds and the
     throughput extrapolated to the full workload."""
     from oracle import oracle as O
@@ -287,7 +311,7 @@ def oracle_sample_run(wl, n_leaves, n_queries, seed_shift=0):
     g = O.build_grid(ph, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
     act, slot = O.active_leaves(g)
     t1 = time.perf_counter()
-    keep = act[:: max(1, act.size // n_leaves)][:n_leaves]
+    keep = act[check] if check is not None else act[np.linspace(0, act.size - 1, n_leaves).astype(np.int64)]
     gsub = dict(g)
     h = O.splat(ph, g, wl.n_prev, wl.H, wl.W, wl.frac_bits)
     t2 = time.perf_counter()
@@ -305,16 +329,29 @@ def oracle_sample_run(wl, n_leaves, n_queries, seed_shift=0):
     step_s = (t1 - t0) + (t2 - t1) + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
         (t5 - t4) * wl.n_queries / n_queries
     return dict(step_s=step_s, samples_per_s=wl.n_queries / step_s, wall_s=t5 - t0, leaves=int(keep.size),
-                A=int(A), queries=n_queries)
+                A=int(A), queries=n_queries, P=tabs["P"])
 
 
-def cpu_baseline(wl, n_leaves):
-    r = oracle_sample_run(wl, n_leaves, 262_144)
-    return {"value": r["samples_per_s"], "unit": "samples/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons, CNN+CDF on "
-                       f"{r['leaves']} of {r['A']} active leaves, sample+eval on {r['queries']} of {wl.n_queries} "
-                       f"queries; per-stage times scaled to the full step ({r['step_s']:.1f} s); "
-                       f"wall {r['wall_s']:.1f} s")}
+def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None):
+    r = oracle_sample_run(wl, n_leaves, 262_144, check)
+    out = {"value": r["samples_per_s"], "unit": "samples/s", "cores": 1, "kind": "oracle",
+           "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons, CNN+CDF on "
+                      f"{r['leaves']} of {r['A']} active leaves, sample+eval on {r['queries']} of {wl.n_queries} "
+                      f"queries; per-stage times scaled to the full step ({r['step_s']:.1f} s); "
+                      f"wall {r['wall_s']:.1f} s")}
+    if maps and precisions is not None:
+        Pr = r["P"]
+        for name, P in maps.items():
+            kl, l1 = [], []
+            for a in range(P.shape[0]):
+                p, qq = Pr[a].ravel(), np.maximum(P[a].ravel(), 1e-38)
+                nz = p > 0
+                kl.append(float(np.sum(p[nz] * np.log(p[nz] / qq[nz]))))
+                l1.append(float(np.abs(p - P[a].ravel()).sum()))
+            precisions[name]["kl_vs_fp64_oracle"] = {"mean": float(np.mean(kl)), "max": float(np.max(kl)),
+                                                     "leaves": len(kl)}
+            precisions[name]["l1_vs_fp64_oracle_mean"] = float(np.mean(l1))
+    return out
 
 
 def run_reference(args, wl):
@@ -349,7 +386,9 @@ def main():
     ap.add_argument("--workload", default="scale")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-leaves", type=int, default=6)
+    ap.add_argument("--cpu-sample-leaves", type=int, default=4)
+    ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the other CNN precisions and report their KL against the oracle")
     args = ap.parse_args()
     from paper_2010_01775_gb300 import synth
     wl = synth.WORKLOADS[args.workload]

@@ -149,6 +149,13 @@ pg_status pg_net_load(pg_ctx *ctx, const void *host_blob, size_t bytes, pg_net *
 pg_status pg_reconstruct(pg_ctx *ctx, const pg_hist *hist, const pg_net *net,
                          pg_precision precision, pg_map **out);
 
+/* Picks the tensor-core launch shape (CTAs per SM, pipeline stages) of every
+ * convolution of `net` for `precision` by timing each feasible shape on the
+ * first chunk of `hist` with CUDA events, and stores the choice in the net
+ * (used by later pg_reconstruct calls with maps of the same size).  A no-op
+ * for PG_FP32.  Synchronous; results of the timing runs are discarded. */
+pg_status pg_autotune(pg_ctx *ctx, const pg_hist *hist, pg_net *net, pg_precision precision);
+
 /* Wraps caller-provided maps y [n_maps][H][W] (float32, >= 0) as a pg_map
  * (copied), so tables can be built from maps computed elsewhere. */
 pg_status pg_map_import(pg_ctx *ctx, const float *d_y, uint64_t n_maps, int H, int W,

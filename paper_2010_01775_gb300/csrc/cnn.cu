@@ -291,7 +291,7 @@ static size_t act_floats_per_leaf(const Net *net, int H, int W) {
   return HW * (8 + (c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;
 }
 
-pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m) {
+pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m, bool tune) {
   const uint32_t A = h->A;
   if (A == 0) return PG_OK;
   const int H = h->H, W = h->W, HW = H * W;
@@ -317,7 +317,8 @@ pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision p
     uint8_t *act = (uint8_t *)scratch + align256(nx * 8 * 4);
     float *y = m->y + (size_t)s0 * HW;
     if (prec == PG_FP32) PG_TRY(forward_f32(net, x0, act, ns, H, W, y, st));
-    else PG_TRY(forward_tc(ctx, net, prec, x0, act, ns, H, W, y, st));
+    else PG_TRY(forward_tc(ctx, net, prec, x0, act, ns, H, W, y, st, tune));
+    if (tune) break;  // the first chunk is representative of every later one
   }
   return PG_OK;
 }

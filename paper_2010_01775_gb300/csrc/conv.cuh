@@ -30,7 +30,7 @@ pg_status forward_f32(const Net *net, const float *x0, void *act, uint32_t ns, i
 // Tensor-core (tcgen05) forms.
 pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
 pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float *x0, void *act, uint32_t ns,
-                     int H, int W, float *y, cudaStream_t st);
+                     int H, int W, float *y, cudaStream_t st, bool tune = false);
 size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W);
 
 }  // namespace pgi

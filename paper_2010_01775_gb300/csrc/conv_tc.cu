@@ -505,7 +505,16 @@ struct LpLayer {
   unsigned int *amax;
 };
 
-pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStream_t st, uint32_t *status) {
+// Launch shape: CTAs resident per SM and pipeline stages per CTA.  Zero
+// fields select the built-in heuristic.
+struct TcCfg {
+  int ctas = 0, stages = 0;
+};
+
+constexpr size_t kSmemPerSM = 228 * 1024;
+
+pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStream_t st, uint32_t *status,
+                    TcCfg cfg = TcCfg()) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return PG_ERR_UNSUPPORTED;
   const int Hout = L.Hin / L.stride, Wout = L.Win / L.stride, HWo = Hout * Wout;
@@ -556,13 +565,19 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   uint32_t cols = 32;
   while (cols < 2u * (uint32_t)L.Cout) cols <<= 1;
   a.tmem_cols = cols;
-  const int per_sm = cols <= 256 ? 2 : 1;
-  const size_t budget = per_sm == 2 ? 108 * 1024 : 200 * 1024;
+  // CTAs per SM: TMEM holds 512 columns per SM, and shared memory is sized
+  // so that no more CTAs than that can be resident (a CTA that found no free
+  // TMEM columns would wait inside tcgen05.alloc).
+  const int max_ctas = (int)std::min<uint32_t>(4, 512u / cols);
+  int per_sm = cfg.ctas > 0 ? std::min(cfg.ctas, max_ctas) : std::min(2, max_ctas);
   const size_t stage_bytes = a.bytes_a + a.bytes_b;
-  a.stages = (int)std::min<size_t>(8, (budget - 2048) / stage_bytes);
+  const size_t fixed = 1024 + 8 * 5 + 16 + 1024;  // alignment, barriers, per-CTA reserve
+  const size_t cap = kSmemPerSM / per_sm - 1024;
+  const int max_stages = (int)std::min<size_t>(24, (cap - fixed) / (stage_bytes + 16));
+  a.stages = cfg.stages > 0 ? std::min(cfg.stages, max_stages) : std::min(8, max_stages);
   if (a.stages < 2) return PG_ERR_UNSUPPORTED;
   size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16;
-  if (per_sm == 1) smem = std::max<size_t>(smem, 120 * 1024);  // keep one CTA per SM (TMEM > 256 columns)
+  smem = std::max(smem, kSmemPerSM / (per_sm + 1) + 1024);  // at most per_sm CTAs resident
   a.out = L.out;
   a.out_cs = L.out_cs;
   a.out_co = L.out_co;
@@ -601,6 +616,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PG_ERR_UNSUPPORTED;
   }
+  if (smem > 227 * 1024) return PG_ERR_UNSUPPORTED;
   PG_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   const int grid = std::min(a.num_tiles, per_sm * num_sms());
   k_conv_tc<<<grid, kThreads, smem, st>>>(mA, mB, a);
@@ -683,9 +699,45 @@ const int kUnetIn[15] = {0, 1, 2, 3, 4, 5, 6, 7, 6, 8, 4, 9, 2, 10, 11};
 const int kTinyOut[3] = {1, 2, -1};
 const int kTinyIn[3] = {0, 1, 2};
 
+// Times every feasible launch shape of one layer on its real operands
+// (CUDA events on the launching stream) and returns the fastest.  The layer
+// is left computed (every candidate writes the same output).
+pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream_t st, uint32_t *status,
+                     TcCfg *best) {
+  cudaEvent_t e0, e1;
+  PG_CUDA(cudaEventCreate(&e0));
+  PG_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  *best = TcCfg();
+  for (int ctas : {1, 2, 3, 4})
+    for (int stages : {2, 3, 4, 6, 8, 12, 16, 24}) {
+      TcCfg c;
+      c.ctas = ctas;
+      c.stages = stages;
+      if (launch_tc(L, ns, es, fp8, st, status, c) != PG_OK) continue;  // warm-up / feasibility
+      cudaEventRecord(e0, st);
+      pg_status s = launch_tc(L, ns, es, fp8, st, status, c);
+      cudaEventRecord(e1, st);
+      if (s != PG_OK) continue;
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        *best = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PG_CUDA(cudaGetLastError());
+  return best->ctas ? PG_OK : PG_ERR_UNSUPPORTED;
+}
+
 template <typename T>
-pg_status forward_lp(pg_ctx *ctx, const Net *net, bool fp8, const float *x0, void *actv, uint32_t ns, int H, int W,
-                     float *y, cudaStream_t st, const float *scale, unsigned int *amax) {
+pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, void *actv, uint32_t ns, int H, int W,
+                     float *y, cudaStream_t st, const float *scale, unsigned int *amax, bool tune = false) {
+  Net *net = const_cast<Net *>(netc);
+  const int pi = fp8 ? 2 : 1;
   const int es = sizeof(T);
   const size_t HW = (size_t)H * W;
   const long M0 = (long)ns * HW;
@@ -715,7 +767,20 @@ pg_status forward_lp(pg_ctx *ctx, const Net *net, bool fp8, const float *x0, voi
       L.acc_mul = 1.0f;
       L.out_mul = 1.0f;
     }
-    return launch_tc(L, ns, es, fp8, st, ctx->d_status);
+    Layer &Lw = net->layers[li];
+    if (tune) {
+      TcCfg best;
+      PG_TRY(tune_layer(L, ns, es, fp8, st, ctx->d_status, &best));
+      Lw.tc_ctas[pi] = best.ctas;
+      Lw.tc_stages[pi] = best.stages;
+      Lw.tuned_hw[pi] = H * W;
+    }
+    TcCfg cfg;
+    if (Lw.tuned_hw[pi] == H * W) {
+      cfg.ctas = Lw.tc_ctas[pi];
+      cfg.stages = Lw.tc_stages[pi];
+    }
+    return launch_tc(L, ns, es, fp8, st, ctx->d_status, cfg);
   };
   auto head = [&](int li, const T *in, int in_cs, int Cin) -> pg_status {
     const Layer &Lr = Ls[li];
@@ -762,9 +827,10 @@ pg_status forward_lp(pg_ctx *ctx, const Net *net, bool fp8, const float *x0, voi
 }  // namespace
 
 pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const float *x0, void *actv, uint32_t ns, int H,
-                     int W, float *y, cudaStream_t st) {
+                     int W, float *y, cudaStream_t st, bool tune) {
   Net *net = const_cast<Net *>(netc);
-  if (prec == PG_BF16) return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr);
+  if (prec == PG_BF16)
+    return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr, tune);
   if (prec != PG_FP8_E4M3) return PG_ERR_UNSUPPORTED;
   if (!net->act_calibrated) {
     // Delayed scaling: one BF16 pass over this chunk records the largest
@@ -789,7 +855,7 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
     ctx_free(ctx, d_amax, 64);
     PG_TRY(s);
   }
-  return forward_lp<__nv_fp8_e4m3>(ctx, net, true, x0, actv, ns, H, W, y, st, net->act_scale, nullptr);
+  return forward_lp<__nv_fp8_e4m3>(ctx, net, true, x0, actv, ns, H, W, y, st, net->act_scale, nullptr, tune);
 }
 
 size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W) {

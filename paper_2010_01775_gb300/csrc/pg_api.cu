@@ -395,6 +395,27 @@ pg_status pg_reconstruct(pg_ctx *c, const pg_hist *hist, const pg_net *netp, pg_
   return PG_OK;
 }
 
+pg_status pg_autotune(pg_ctx *c, const pg_hist *hist, pg_net *netp, pg_precision prec) {
+  const Hist *h = as<Hist>(hist, KIND_HIST);
+  Net *net = as<Net>(netp, KIND_NET);
+  if (!c || !h || !net) return PG_ERR_INVALID_ARG;
+  if (prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_OK;  // the FP32 form has nothing to tune
+  if (h->A == 0) return PG_OK;
+  PG_TRY(net_prepare(c, net, prec));
+  Map m;
+  memset(&m, 0, sizeof(m));
+  m.A = h->A;
+  m.H = h->H;
+  m.W = h->W;
+  size_t bytes = (size_t)h->A * h->H * h->W * sizeof(float);
+  void *block = nullptr;
+  PG_TRY(ctx_alloc(c, bytes, &block));
+  m.y = (float *)block;
+  pg_status s = reconstruct(c, h, net, prec, &m, true);
+  ctx_free(c, block, bytes);
+  return s;
+}
+
 pg_status pg_map_import(pg_ctx *c, const float *d_y, uint64_t n_maps, int H, int W, pg_map **out) {
   if (!c || !out || (n_maps && !d_y)) return PG_ERR_INVALID_ARG;
   *out = nullptr;

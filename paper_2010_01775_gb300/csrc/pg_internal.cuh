@@ -80,6 +80,10 @@ struct Layer {
   void *w_fp8;   // device, FP8 E4M3 copy [cout][K], or null
   size_t w_bf16_bytes, w_fp8_bytes;
   float w_scale;  // FP8 per-tensor weight scale (w = w_fp8 * w_scale)
+  // Tensor-core launch shape picked by pg_autotune, per reduced precision
+  // (index 1 = BF16, 2 = FP8) for maps of tuned_hw[i] bins (0 = not tuned).
+  int tc_ctas[3], tc_stages[3];
+  int tuned_hw[3];
 };
 
 struct Net {
@@ -247,7 +251,7 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n, const pg_gr
 pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h);
 // cnn.cu
 pg_status net_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
-pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m);
+pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m, bool tune = false);
 // cdf.cu
 pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t);
 // sample.cu

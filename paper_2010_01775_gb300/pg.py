@@ -33,7 +33,7 @@ STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_NOT_DEVICE_PTR", 3: "P
 EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_use", "pg_build_grid",
             "pg_splat_photons", "pg_net_load", "pg_reconstruct", "pg_map_import", "pg_build_cdf",
             "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string",
-            "pg_sort_photons_noalloc"]
+            "pg_sort_photons_noalloc", "pg_autotune"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "pg_eval_pdf": [P, P, P, P, P, u64, P],
         "pg_info": [P, i32, ctypes.POINTER(u64)], "pg_export": [P, P, i32, P, sz],
         "pg_sort_photons_noalloc": [P, u64, ctypes.POINTER(pg_grid_params), P, P, P],
+        "pg_autotune": [P, P, P, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -206,6 +207,10 @@ def pg_reconstruct(ctx, hist, net, precision=PG_FP32) -> Handle:
     out = ctypes.c_void_p()
     _check(_lib.pg_reconstruct(ctx.ptr, hist.ptr, net.ptr, precision, ctypes.byref(out)), "pg_reconstruct")
     return Handle(ctx, out.value, "map")
+
+
+def pg_autotune(ctx, hist, net, precision):
+    _check(_lib.pg_autotune(ctx.ptr, hist.ptr, net.ptr, precision), "pg_autotune")
 
 
 def pg_map_import(ctx, y, n_maps, H, W) -> Handle:
