@@ -344,6 +344,15 @@ __global__ void __launch_bounds__(1024) k_active(Tree t, const uint32_t *__restr
   if (threadIdx.x == 0) t.counters[1] = carry;
 }
 
+// Coarse lookup table for query-side leaf location: for every cell of depth
+// lut_depth, the leaf containing its first code.
+__global__ void k_leaf_lut(const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ counters, int shift,
+                           uint32_t ncell, uint32_t *__restrict__ lut) {
+  uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  lut[c] = find_leaf(leaf_code, counters[0], (uint64_t)c << shift);
+}
+
 // ---------------------------------------------------------------- a4
 __global__ void k_leaf_assign(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ perm, uint32_t n,
                               const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ counters,
@@ -389,7 +398,10 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   // Handle block.
   size_t b_codes = align256(8ull * n), b_perm = align256(4ull * n), b_lo = align256(4ull * n);
   size_t b_lc = align256(8 * cap), b_l4 = align256(4 * cap);
-  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4;
+  g->lut_depth = D < 6 ? D : 6;
+  const uint32_t lut_cells = 1u << (3 * g->lut_depth);
+  size_t b_lut = align256(4ull * lut_cells);
+  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4 + b_lut;
   PG_TRY(ctx_alloc(ctx, g->h.bytes, &g->block));
   uint8_t *q = (uint8_t *)g->block;
   g->codes = (uint64_t *)q; q += b_codes;
@@ -400,7 +412,8 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   g->leaf_begin = (uint32_t *)q; q += b_l4;
   g->leaf_end = (uint32_t *)q; q += b_l4;
   g->active = (uint32_t *)q; q += b_l4;
-  g->slot_of_leaf = (int32_t *)q;
+  g->slot_of_leaf = (int32_t *)q; q += b_l4;
+  g->lut = (uint32_t *)q;
 
   // Scratch: sort ping-pong, digit histograms, cells.
   const int passes = (3 * D + 7) / 8;
@@ -485,6 +498,8 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   }
   // a4: leaf of every photon.
   if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of);
+  k_leaf_lut<<<ceil_div(lut_cells, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * (D - g->lut_depth), lut_cells,
+                                                      g->lut);
   PG_CUDA(cudaGetLastError());
 
   uint32_t hc[2];

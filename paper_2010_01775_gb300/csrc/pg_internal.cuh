@@ -59,6 +59,8 @@ struct Grid {
   uint32_t *leaf_end;    // [cap]
   uint32_t *active;      // [cap] active leaves (count > 0), ascending
   int32_t *slot_of_leaf; // [cap]
+  uint32_t *lut;         // [8^lut_depth] leaf containing the first code of each lut_depth cell
+  int lut_depth;
   void *block;           // single allocation holding the arrays above
 };
 
@@ -190,6 +192,25 @@ __device__ __forceinline__ uint32_t find_leaf(const uint64_t *__restrict__ leaf_
   return lo - 1;
 }
 
+// Leaf of a code through the coarse table: the leaves of a depth-`ld` cell
+// lie between the leaves holding its first code and the next cell's first
+// code, so the binary search covers only those.
+__device__ __forceinline__ uint32_t find_leaf_lut(const uint64_t *__restrict__ leaf_code, uint32_t L,
+                                                  const uint32_t *__restrict__ lut, uint32_t ncell, int shift,
+                                                  uint64_t code) {
+  const uint32_t c = (uint32_t)(code >> shift);
+  const uint32_t lo = __ldg(lut + c);
+  uint32_t hi = c + 1 < ncell ? __ldg(lut + c + 1) + 1 : L;  // exclusive bound
+  // Last l in [lo, hi) with leaf_code[l] <= code (holds at lo).
+  uint32_t a = lo + 1;
+  while (a < hi) {
+    uint32_t mid = a + ((hi - a) >> 1);
+    if (__ldg(leaf_code + mid) <= code) a = mid + 1;
+    else hi = mid;
+  }
+  return a - 1;
+}
+
 // Cylindrical-map row: clamp(floor(z * H/2) + H/2, 0, H-1).  z * H/2 is exact.
 __device__ __forceinline__ int dir_row(float z, int H) {
   int h2 = H >> 1;
@@ -199,15 +220,9 @@ __device__ __forceinline__ int dir_row(float z, int H) {
 }
 
 // Exact sign test "direction (x, y) is not clockwise of boundary ray (c, s)",
-// i.e. c*y - s*x >= 0.  A FP32 evaluation decides when its magnitude clears
-// the rounding error bound (4 ulp of |c y| + |s x|, with normal operands);
-// otherwise the products are formed exactly in FP64 (a float times a float
-// is exact in double) and the rounded difference has the exact sign.
-__device__ __forceinline__ bool not_clockwise(float c, float s, float x, float y) {
-  float a = __fmul_rn(c, y), b = __fmul_rn(s, x);
-  float d = __fsub_rn(a, b);
-  float mag = fabsf(a) + fabsf(b);
-  if (mag > 1e-30f && fabsf(d) > 4.8e-7f * mag) return d >= 0.0f;
+// i.e. c*y - s*x >= 0: the products of two floats are exact in FP64 and the
+// rounded FP64 difference keeps the exact sign.
+__device__ __forceinline__ bool not_clockwise_exact(float c, float s, float x, float y) {
   double dd = __dsub_rn(__dmul_rn((double)c, (double)y), __dmul_rn((double)s, (double)x));
   return dd >= 0.0;
 }
@@ -217,16 +232,35 @@ __device__ __forceinline__ bool not_clockwise(float c, float s, float x, float y
 // direction is not clockwise of, within the half plane of the direction
 // (upper: phi in [0, pi), rays 0..W/2-1; lower: phi in [pi, 2 pi), rays
 // W/2..W-1).  tab holds cos at [0, W) and sin at [W, 2W).
-__device__ __forceinline__ int dir_col(float x, float y, int W, const float *tab) {
-  if (x == 0.0f && y == 0.0f) return 0;
-  bool upper = (y > 0.0f) || (y == 0.0f && x >= 0.0f);
-  int lo = upper ? 0 : (W >> 1);
-  int hi = lo + (W >> 1) - 1;
+static __device__ __noinline__ int dir_col_exact(float x, float y, int W, const float *tab, int lo, int hi) {
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
-    if (not_clockwise(tab[mid], tab[W + mid], x, y)) lo = mid;
+    if (not_clockwise_exact(tab[mid], tab[W + mid], x, y)) lo = mid;
     else hi = mid - 1;
   }
+  return lo;
+}
+
+// The search runs in FP32; a step whose difference does not clear the
+// rounding bound (4 ulp of |c y| + |s x|, normal operands) marks the result
+// unsure, and only then is the search redone with the exact FP64 predicate
+// (kept out of line: GB300's FP64 rate is a small fraction of FP32's).
+__device__ __forceinline__ int dir_col(float x, float y, int W, const float *tab) {
+  if (x == 0.0f && y == 0.0f) return 0;
+  const bool upper = (y > 0.0f) || (y == 0.0f && x >= 0.0f);
+  const int lo0 = upper ? 0 : (W >> 1), hi0 = lo0 + (W >> 1) - 1;
+  int lo = lo0, hi = hi0;
+  bool unsure = false;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    float a = __fmul_rn(tab[mid], y), b = __fmul_rn(tab[W + mid], x);
+    float d = __fsub_rn(a, b);
+    float mag = fabsf(a) + fabsf(b);
+    unsure |= !(mag > 1e-30f && fabsf(d) > 4.8e-7f * mag);
+    if (d >= 0.0f) lo = mid;
+    else hi = mid - 1;
+  }
+  if (unsure) lo = dir_col_exact(x, y, W, tab, lo0, hi0);
   return lo;
 }
 

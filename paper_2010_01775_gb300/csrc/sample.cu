@@ -25,6 +25,9 @@ __device__ __forceinline__ int first_above(const float *__restrict__ F, int n, f
 
 struct Tab {
   const uint64_t *leaf_code;
+  const uint32_t *lut;
+  uint32_t lut_cells;
+  int lut_shift;
   const int32_t *slot_of_leaf;
   const float *P, *Fphi, *Fz;
   const uint8_t *valid;
@@ -42,7 +45,7 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, GridGeom g, 
   uint32_t bad = 0;
   uint64_t code = position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
   if (bad) atomicOr(status, ST_INVALID_INPUT);
-  uint32_t l = find_leaf(tb.leaf_code, tb.L, code);
+  uint32_t l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
   int32_t s = __ldg(tb.slot_of_leaf + l);
   uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), stream, 0u), key);
   const float k24 = 5.9604644775390625e-08f;  // 2^-24
@@ -82,7 +85,7 @@ __global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ 
   if (t >= q) return;
   uint32_t bad = 0;
   uint64_t code = position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
-  uint32_t l = find_leaf(tb.leaf_code, tb.L, code);
+  uint32_t l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
   int32_t s = __ldg(tb.slot_of_leaf + l);
   float p = tb.pdf_uniform;
   if (s >= 0 && __ldg(tb.valid + s)) {
@@ -103,6 +106,9 @@ __global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ 
 Tab make_tab(const Grid *g, const Tables *t) {
   Tab tb;
   tb.leaf_code = g->leaf_code;
+  tb.lut = g->lut;
+  tb.lut_cells = 1u << (3 * g->lut_depth);
+  tb.lut_shift = 3 * (g->D - g->lut_depth);
   tb.slot_of_leaf = g->slot_of_leaf;
   tb.P = t->P;
   tb.Fphi = t->cdf_phi;

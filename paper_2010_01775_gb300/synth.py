@@ -71,7 +71,14 @@ SCALE_SMALL = dataclasses.replace(
     SCALE, name="scale-small: 262k photons, 16 blobs, depth 10, split 2000, 64x64, U-Net, 512k queries",
     n_photons=262_144, n_blobs=16, n_queries=524_288, seed=SEED_BASE + 11)
 
-WORKLOADS = {"tiny": TINY, "scale": SCALE, "precision": PRECISION, "scale-small": SCALE_SMALL}
+# A mid-size copy for profiler captures of the memory-bound kernels (query
+# arrays and histograms larger than L2, a few GB on the device in BF16).
+SCALE_MID = dataclasses.replace(
+    SCALE, name="scale-mid: 1M photons, 32 blobs, depth 10, split 2000, 64x64, U-Net, 4M queries",
+    n_photons=1_048_576, n_blobs=32, n_queries=4_194_304, seed=SEED_BASE + 12)
+
+WORKLOADS = {"tiny": TINY, "scale": SCALE, "precision": PRECISION, "scale-small": SCALE_SMALL,
+             "scale-mid": SCALE_MID}
 
 
 def _unit(v):
