@@ -146,8 +146,9 @@ def run_pg(args, wl, prec):
     # Launch shapes of the tensor-core convolutions are tuned once, untimed.
     g0 = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
     h0 = pg.pg_splat_photons(ctx, g0, d_ph, n, wl.n_prev, H, W, wl.frac_bits)
-    for pr in {prec} | ({pg.PG_BF16, pg.PG_FP8_E4M3} if args.sweep else set()):
-        pg.pg_autotune(ctx, h0, net, pr)
+    if args.autotune:
+        for pr in {prec} | ({pg.PG_BF16, pg.PG_FP8_E4M3} if args.sweep else set()):
+            pg.pg_autotune(ctx, h0, net, pr)
     ctx.sync()
 
     def measure(pr, steps, warmup, clocks_on=False):
@@ -387,6 +388,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-leaves", type=int, default=4)
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="tune the tensor-core launch shapes before timing (untimed)")
     ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the other CNN precisions and report their KL against the oracle")
     args = ap.parse_args()

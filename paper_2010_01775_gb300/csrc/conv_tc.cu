@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -46,6 +48,9 @@ struct TcArgs {
   int Hout, Wout, HWo;
   long M;
   int BN;
+  int mt;           // 128-pixel M-subtiles per CTA tile (each its own accumulator)
+  int halo;         // 3x3 stride-1 layers: one stage = one channel chunk, all 9 taps
+  uint32_t bytes_ver;  // halo mode: bytes of one x-shifted input box (Ht + 2 rows)
   int Wt, Ht, Lt;
   int num_tiles, kiters, stages;
   uint32_t bytes_a, bytes_b;  // per stage
@@ -62,6 +67,7 @@ struct TcArgs {
   const float *bias;
   uint32_t *status;
   unsigned int *amax;  // optional: running max |output| (float bits) for FP8 calibration
+  unsigned long long *stats;  // optional: per-role cycle counters (diagnostics)
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -159,6 +165,22 @@ __device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint3
       : "memory");
 }
 
+// One MMA with descriptors given as (low, high) words.
+template <bool kFp8>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                          uint32_t idesc, uint32_t acc) {
+  if (kFp8)
+    asm volatile(
+        "{\n .reg .pred p;\n .reg .b64 da, db;\n mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n"
+        " setp.ne.b32 p, %6, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %5, p;\n}\n" ::"r"(d),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n .reg .b64 da, db;\n mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n"
+        " setp.ne.b32 p, %6, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(d),
+        "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
                : "memory");
@@ -174,17 +196,88 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Output-tile origin of M-tile t: first leaf, row and column of the tile.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Output-tile origin of tile t: first leaf, row and column of the tile.
 __device__ __forceinline__ void tile_origin(const TcArgs &a, int t, int &l0, int &y0, int &x0) {
-  long m0 = (long)t * kBM;
+  long m0 = (long)t * kBM * a.mt;
   l0 = (int)(m0 / a.HWo);
   int r = (int)(m0 % a.HWo);
   y0 = r / a.Wout;
   x0 = r % a.Wout;
 }
 
-__device__ __forceinline__ float elu(float v) { return v > 0.0f ? v : expm1f(v); }
+// ELU for the reduced-precision forms: exp(v) - 1 through the fast exponential
+// (its ~1e-7 absolute error is far below a BF16 or E4M3 output's rounding).
+__device__ __forceinline__ float elu_lp(float v) { return v > 0.0f ? v : __expf(v) - 1.0f; }
 
+// Bias + activation + conversion of 16 accumulator columns of one pixel and
+// their stores (four of them when the output is upsampled x2).
+template <bool kFp8Out, bool kCalib>
+__device__ __forceinline__ void epi16(const TcArgs &a, const uint32_t *r, const float *s_bias, int c, size_t pix0,
+                                      int Wo, int reps, float &amax) {
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; j += 4) {
+    const float4 b = *reinterpret_cast<const float4 *>(s_bias + c + j);
+    v[j] = fmaf(__uint_as_float(r[j]), a.acc_mul, b.x);
+    v[j + 1] = fmaf(__uint_as_float(r[j + 1]), a.acc_mul, b.y);
+    v[j + 2] = fmaf(__uint_as_float(r[j + 2]), a.acc_mul, b.z);
+    v[j + 3] = fmaf(__uint_as_float(r[j + 3]), a.acc_mul, b.w);
+  }
+  if (a.act == 1) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = elu_lp(v[j]);
+  }
+  if (kCalib) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) amax = fmaxf(amax, fabsf(v[j]));
+  }
+  uint4 w0, w1;
+  if (kFp8Out) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_fp8x4_e4m3 p(make_float4(v[4 * j] * a.out_mul, v[4 * j + 1] * a.out_mul, v[4 * j + 2] * a.out_mul,
+                                    v[4 * j + 3] * a.out_mul));
+      w[j] = *reinterpret_cast<uint32_t *>(&p);
+    }
+    w0 = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    uint32_t w[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      w[j] = *reinterpret_cast<uint32_t *>(&p);
+    }
+    w0 = make_uint4(w[0], w[1], w[2], w[3]);
+    w1 = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+  for (int dy = 0; dy < reps; ++dy)
+    for (int dx = 0; dx < reps; ++dx) {
+      const size_t pix = pix0 + (size_t)dy * Wo + dx;
+      if (kFp8Out) {
+        *reinterpret_cast<uint4 *>((uint8_t *)a.out + pix * a.out_cs + a.out_co + c) = w0;
+      } else {
+        uint4 *o = reinterpret_cast<uint4 *>((__nv_bfloat16 *)a.out + pix * a.out_cs + a.out_co + c);
+        o[0] = w0;
+        o[1] = w1;
+      }
+    }
+}
+
+template <bool kFp8Out, bool kCalib>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -198,6 +291,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *drain = acc_empty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  float *s_bias = reinterpret_cast<float *>(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // BN floats
+  for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_bias[k] = a.bias[k];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -227,40 +322,75 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    if (lane == 0) {
-      // ---------------- TMA producer
-      int stage = 0;
-      uint32_t phase = 0;
-      long issued = 0;
-      for (int t = blockIdx.x; t < a.num_tiles && !*abort_flag; t += gridDim.x) {
-        int l0, y0, x0;
-        tile_origin(a, t, l0, y0, x0);
-        for (int ki = 0; ki < a.kiters; ++ki) {
-          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) break;
-          int tap = ki / a.cchunks, cc = ki - tap * a.cchunks;
-          int ky = tap / a.k, kx = tap - ky * a.k;
-          mbar_expect_tx(&full[stage], a.bytes_a + a.bytes_b);
-          tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk, x0 * a.stride + kx - a.pad,
-                      y0 * a.stride + ky - a.pad, l0);
-          tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
-          ++issued;
-          if (++stage == a.stages) {
-            stage = 0;
-            phase ^= 1u;
+    // ---------------- TMA producer: lane 0 owns the ring; the copies of one
+    // stage are issued by separate lanes so they enter the TMA unit together.
+    int stage = 0;
+    uint32_t phase = 0;
+    long issued = 0;
+    bool ok = true;
+    long long prod_wait = 0;
+    const long long prod_t0 = clock64();
+    const int ntma = a.halo ? 12 : 2;
+    for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
+      int l0, y0, x0;
+      tile_origin(a, t, l0, y0, x0);
+      for (int ki = 0; ki < a.kiters; ++ki) {
+        int got = 1;
+        if (lane == 0) {
+          const long long c0 = clock64();
+          got = mbar_wait(&empty[stage], phase ^ 1u, abort_flag) ? 1 : 0;
+          prod_wait += clock64() - c0;
+          if (got) mbar_expect_tx(&full[stage], a.bytes_a + a.bytes_b);
+        }
+        got = __shfl_sync(0xFFFFFFFFu, got, 0);
+        if (!got) {
+          ok = false;
+          break;
+        }
+        __syncwarp();
+        if (lane < ntma) {
+          if (a.halo) {
+            // Three copies of the haloed input tile (rows y0-1 .. y0+Ht),
+            // shifted by kx - 1 columns; out-of-range columns and rows are
+            // zero-filled.  Tap (ky, kx) is then rows ky*Wt.. of copy kx.
+            const int cc = ki;
+            if (lane < 3)
+              tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a + (size_t)lane * a.bytes_ver,
+                          cc * a.chunk, x0 + lane - 1, y0 - 1, l0);
+            else
+              tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 3) * (a.bytes_b / 9),
+                          (lane - 3) * a.Cin + cc * a.chunk, 0);
+          } else {
+            int tap = ki / a.cchunks, cc = ki - tap * a.cchunks;
+            int ky = tap / a.k, kx = tap - ky * a.k;
+            if (lane == 0)
+              tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk,
+                          x0 * a.stride + kx - a.pad, y0 * a.stride + ky - a.pad, l0);
+            else
+              tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
           }
+        }
+        ++issued;
+        if (++stage == a.stages) {
+          stage = 0;
+          phase ^= 1u;
         }
       }
-      if (*abort_flag) {
-        // Drain: let the last stages' copies land before the CTA exits.
-        long back = issued < a.stages ? issued : a.stages;
-        for (long i = 0; i < back; ++i) {
-          if (--stage < 0) {
-            stage = a.stages - 1;
-            phase ^= 1u;
-          }
-          volatile int never = 0;
-          mbar_wait(&full[stage], phase, &never, 100000000ull);
+    }
+    if (lane == 0 && a.stats) {
+      atomicAdd(&a.stats[0], (unsigned long long)prod_wait);
+      atomicAdd(&a.stats[1], (unsigned long long)(clock64() - prod_t0));
+    }
+    if (lane == 0 && *abort_flag) {
+      // Drain: let the last stages' copies land before the CTA exits.
+      long back = issued < a.stages ? issued : a.stages;
+      for (long q = 0; q < back; ++q) {
+        if (--stage < 0) {
+          stage = a.stages - 1;
+          phase ^= 1u;
         }
+        volatile int never = 0;
+        mbar_wait(&full[stage], phase, &never, 100000000ull);
       }
     }
   } else if (warp == 1) {
@@ -270,25 +400,64 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       int i = 0;
       const uint32_t a_base = saddr(sA), b_base = saddr(sB);
+      // Descriptor words (see smem_desc): low = start address >> 4 | LBO,
+      // high = SBO >> 4 | version | swizzle mode.
+      const uint32_t desc_hi = ((a.sbo >> 4) & 0x3FFFu) | (1u << 14) | ((uint32_t)(a.swz & 7) << 29);
+      const uint32_t a_lo0 = ((a_base & 0x3FFFFu) >> 4) | (1u << 16), b_lo0 = ((b_base & 0x3FFFFu) >> 4) | (1u << 16);
+      const uint32_t row16 = a.sbo / 8 / 16;                 // one operand row, in 16-byte units
+      const uint32_t sub_step = (uint32_t)kBM * row16;       // next 128-row subtile
+      const uint32_t row_step = (uint32_t)a.Wt * row16;      // halo mode: next tap row
+      const uint32_t ver16 = a.bytes_ver >> 4;               // halo mode: next x-shifted copy
+      const uint32_t tap_b16 = (a.bytes_b / 9) >> 4;         // halo mode: next tap's weights
+      long long mma_wait_acc = 0, mma_wait_full = 0;
+      const long long mma_t0 = clock64();
       for (int t = blockIdx.x; t < a.num_tiles && !*abort_flag; t += gridDim.x, ++i) {
         const int buf = i & 1;
         const uint32_t use = (uint32_t)(i >> 1) & 1u;
+        long long c0 = clock64();
         if (!mbar_wait(&acc_empty[buf], use ^ 1u, abort_flag)) break;
+        mma_wait_acc += clock64() - c0;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * a.BN);
+        const uint32_t d = tmem + (uint32_t)(buf * a.mt * a.BN);
         bool ok = true;
         for (int ki = 0; ki < a.kiters; ++ki) {
+          c0 = clock64();
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-          const uint32_t sa = a_base + (uint32_t)stage * a.bytes_a, sb = b_base + (uint32_t)stage * a.bytes_b;
-          for (int j = 0; j < a.mma_per_stage; ++j) {
-            uint64_t da = smem_desc(sa + 32u * j, a.sbo, a.swz), db = smem_desc(sb + 32u * j, a.sbo, a.swz);
-            uint32_t acc = (ki | j) ? 1u : 0u;
-            if (a.mma_kind == 0) mma_f16(d, da, db, a.idesc, acc);
-            else mma_f8(d, da, db, a.idesc, acc);
+          mma_wait_full += clock64() - c0;
+          // No tcgen05 fence here: the TMA writes this stage's operands
+          // through the async proxy and the mbarrier's transaction count
+          // already orders them before the MMAs that read them.
+          // Descriptors move by adding (byte offset >> 4) to the 14-bit
+          // start-address field of the low word (shared memory < 256 KB, so
+          // the field never carries); the high word is fixed per launch.
+          const uint32_t alo_s = a_lo0 + (uint32_t)stage * (a.bytes_a >> 4);
+          const uint32_t blo_s = b_lo0 + (uint32_t)stage * (a.bytes_b >> 4);
+          const bool first = ki == 0;
+          if (!a.halo) {
+            for (int j = 0; j < a.mma_per_stage; ++j) {
+              const uint32_t acc = (first && j == 0) ? 0u : 1u;
+              for (int sub = 0; sub < a.mt; ++sub)
+                mma_issue<kFp8Out>(d + (uint32_t)(sub * a.BN), alo_s + (uint32_t)sub * sub_step + 2u * j, desc_hi,
+                                   blo_s + 2u * j, desc_hi, a.idesc, acc);
+            }
+          } else {
+            // Tap (ky, kx) reads copy kx of the haloed tile from row ky * Wt on.
+            uint32_t b_tap = blo_s;
+            for (int ky = 0; ky < 3; ++ky) {
+              for (int kx = 0; kx < 3; ++kx) {
+                const uint32_t a_tap = alo_s + (uint32_t)kx * ver16 + (uint32_t)ky * row_step;
+                for (int j = 0; j < a.mma_per_stage; ++j) {
+                  const uint32_t acc = (first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
+                  for (int sub = 0; sub < a.mt; ++sub)
+                    mma_issue<kFp8Out>(d + (uint32_t)(sub * a.BN), a_tap + (uint32_t)sub * sub_step + 2u * j, desc_hi,
+                                       b_tap + 2u * j, desc_hi, a.idesc, acc);
+                }
+                b_tap += tap_b16;
+              }
+            }
           }
           mma_commit(&empty[stage]);
           if (++stage == a.stages) {
@@ -298,6 +467,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
         mma_commit(&acc_full[buf]);
+      }
+      if (a.stats) {
+        atomicAdd(&a.stats[2], (unsigned long long)mma_wait_acc);
+        atomicAdd(&a.stats[3], (unsigned long long)mma_wait_full);
+        atomicAdd(&a.stats[4], (unsigned long long)(clock64() - mma_t0));
       }
       // All issued MMAs complete before TMEM is released.
       mma_commit(drain);
@@ -312,59 +486,51 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int reps = a.ups ? 2 : 1;
     const int Ho = a.Hout * reps, Wo = a.Wout * reps;
     float amax_local = 0.0f;
+    long long epi_wait = 0;
+    const long long epi_t0 = clock64();
     for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x, ++i) {
       const int buf = i & 1;
       const uint32_t use = (uint32_t)(i >> 1) & 1u;
+      const long long c0 = clock64();
       if (!mbar_wait(&acc_full[buf], use, abort_flag)) break;
+      epi_wait += clock64() - c0;
       tc_fence_after();
       int l0, y0, x0;
       tile_origin(a, t, l0, y0, x0);
-      const int xx = m % a.Wt, yy = (m / a.Wt) % a.Ht, ll = m / (a.Wt * a.Ht);
+      for (int sub = 0; sub < a.mt; ++sub) {
+      const int mm = sub * kBM + m;
+      const int xx = mm % a.Wt, yy = (mm / a.Wt) % a.Ht, ll = mm / (a.Wt * a.Ht);
       const int leaf = l0 + ll, y = y0 + yy, x = x0 + xx;
       const bool valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.BN);
-      for (int c = 0; c < a.BN; c += 16) {
-        uint32_t r[16];
-        tmem_ld16(trow + (uint32_t)c, r);
-        if (!valid) continue;
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          float z = __uint_as_float(r[j]) * a.acc_mul + __ldg(a.bias + c + j);
-          z = a.act == 1 ? elu(z) : z;
-          amax_local = fmaxf(amax_local, fabsf(z));
-          v[j] = z * a.out_mul;
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN);
+      const size_t pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
+      if (a.BN % 32 == 0) {
+        for (int c = 0; c < a.BN; c += 32) {
+          uint32_t r[32];
+          tmem_ld32(trow + (uint32_t)c, r);
+          if (!valid) continue;
+          epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
+          epi16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, pix0, Wo, reps, amax_local);
         }
-        for (int dy = 0; dy < reps; ++dy)
-          for (int dx = 0; dx < reps; ++dx) {
-            size_t pix = ((size_t)leaf * Ho + (size_t)(y * reps + dy)) * Wo + (size_t)(x * reps + dx);
-            if (a.out_fp8) {
-              uint8_t *o = (uint8_t *)a.out + pix * a.out_cs + a.out_co + c;
-              uint32_t w[4];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                __nv_fp8x4_e4m3 p(make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
-                w[j] = *reinterpret_cast<uint32_t *>(&p);
-              }
-              *reinterpret_cast<uint4 *>(o) = make_uint4(w[0], w[1], w[2], w[3]);
-            } else {
-              __nv_bfloat16 *o = (__nv_bfloat16 *)a.out + pix * a.out_cs + a.out_co + c;
-              uint32_t w[8];
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                w[j] = *reinterpret_cast<uint32_t *>(&p);
-              }
-              reinterpret_cast<uint4 *>(o)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-              reinterpret_cast<uint4 *>(o)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-            }
-          }
+      } else {
+        for (int c = 0; c < a.BN; c += 16) {
+          uint32_t r[16];
+          tmem_ld16(trow + (uint32_t)c, r);
+          if (!valid) continue;
+          epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
+        }
       }
+      }  // subtiles
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
-    if (a.amax) {
+    if (a.stats && lane == 0 && q == 2) {
+      atomicAdd(&a.stats[5], (unsigned long long)epi_wait);
+      atomicAdd(&a.stats[6], (unsigned long long)(clock64() - epi_t0));
+      atomicAdd(&a.stats[7], (unsigned long long)i);
+    }
+    if (kCalib) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) amax_local = fmaxf(amax_local, __shfl_xor_sync(0xFFFFFFFFu, amax_local, o));
       if (lane == 0) atomicMax(a.amax, __float_as_uint(amax_local));
@@ -508,7 +674,7 @@ struct LpLayer {
 // Launch shape: CTAs resident per SM and pipeline stages per CTA.  Zero
 // fields select the built-in heuristic.
 struct TcCfg {
-  int ctas = 0, stages = 0;
+  int ctas = 0, stages = 0, mt = 0, halo = 0, cb = 0;
 };
 
 constexpr size_t kSmemPerSM = 228 * 1024;
@@ -524,7 +690,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   // K chunk per stage: one swizzle row of 128, 64 or 32 bytes.
   int cb = 0;
   for (int c : {128, 64, 32})
-    if ((L.Cin * es) % c == 0) {
+    if ((L.Cin * es) % c == 0 && (cfg.cb == 0 || cfg.cb == c)) {
       cb = c;
       break;
     }
@@ -542,18 +708,24 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.HWo = HWo;
   a.M = M;
   a.BN = L.Cout;
-  if (Wout >= kBM) {
-    a.Wt = kBM; a.Ht = 1; a.Lt = 1;
-  } else if (HWo >= kBM) {
-    a.Wt = Wout; a.Ht = kBM / Wout; a.Lt = 1;
+  a.mt = cfg.mt > 0 ? cfg.mt : 1;
+  const int TP = kBM * a.mt;  // pixels per CTA tile
+  if (Wout >= TP) {
+    a.Wt = TP; a.Ht = 1; a.Lt = 1;
+  } else if (HWo >= TP) {
+    a.Wt = Wout; a.Ht = TP / Wout; a.Lt = 1;
   } else {
-    a.Wt = Wout; a.Ht = Hout; a.Lt = kBM / HWo;
+    a.Wt = Wout; a.Ht = Hout; a.Lt = TP / HWo;
   }
-  if (a.Wt * a.Ht * a.Lt != kBM || a.Wt * L.stride > 256 || a.Ht * L.stride > 256) return PG_ERR_UNSUPPORTED;
-  a.num_tiles = (int)((M + kBM - 1) / kBM);
-  a.kiters = L.k * L.k * a.cchunks;
-  a.bytes_a = (uint32_t)(kBM * cb);
-  a.bytes_b = (uint32_t)(L.Cout * cb);
+  if (a.Wt * a.Ht * a.Lt != TP || a.Wt * L.stride > 256 || a.Ht * L.stride > 256 || a.Lt > 256)
+    return PG_ERR_UNSUPPORTED;
+  a.num_tiles = (int)((M + TP - 1) / TP);
+  a.halo = cfg.halo;
+  if (a.halo && (L.k != 3 || L.stride != 1 || a.Lt != 1 || a.Ht + 2 > 256)) return PG_ERR_UNSUPPORTED;
+  a.kiters = a.halo ? a.cchunks : L.k * L.k * a.cchunks;
+  a.bytes_ver = (uint32_t)((a.Ht + 2) * a.Wt * cb);
+  a.bytes_a = a.halo ? 3u * a.bytes_ver : (uint32_t)(TP * cb);
+  a.bytes_b = (uint32_t)(L.Cout * cb) * (a.halo ? 9u : 1u);
   a.sbo = 8u * (uint32_t)cb;
   a.swz = cb == 128 ? 2 : (cb == 64 ? 4 : 6);
   a.mma_per_stage = cb / 32;
@@ -563,7 +735,8 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.idesc = (1u << 4) | ((es == 2 ? 1u : 0u) << 7) | ((es == 2 ? 1u : 0u) << 10) | ((uint32_t)(L.Cout >> 3) << 17) |
             ((uint32_t)(kBM >> 4) << 24);
   uint32_t cols = 32;
-  while (cols < 2u * (uint32_t)L.Cout) cols <<= 1;
+  while (cols < 2u * (uint32_t)(a.mt * L.Cout)) cols <<= 1;
+  if (cols > 512) return PG_ERR_UNSUPPORTED;
   a.tmem_cols = cols;
   // CTAs per SM: TMEM holds 512 columns per SM, and shared memory is sized
   // so that no more CTAs than that can be resident (a CTA that found no free
@@ -571,12 +744,12 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   const int max_ctas = (int)std::min<uint32_t>(4, 512u / cols);
   int per_sm = cfg.ctas > 0 ? std::min(cfg.ctas, max_ctas) : std::min(2, max_ctas);
   const size_t stage_bytes = a.bytes_a + a.bytes_b;
-  const size_t fixed = 1024 + 8 * 5 + 16 + 1024;  // alignment, barriers, per-CTA reserve
+  const size_t fixed = 1024 + 8 * 5 + 16 + 1024 + 1024;  // alignment, barriers, bias, per-CTA reserve
   const size_t cap = kSmemPerSM / per_sm - 1024;
   const int max_stages = (int)std::min<size_t>(24, (cap - fixed) / (stage_bytes + 16));
   a.stages = cfg.stages > 0 ? std::min(cfg.stages, max_stages) : std::min(8, max_stages);
   if (a.stages < 2) return PG_ERR_UNSUPPORTED;
-  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16;
+  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16 + 4 * 256;
   smem = std::max(smem, kSmemPerSM / (per_sm + 1) + 1024);  // at most per_sm CTAs resident
   a.out = L.out;
   a.out_cs = L.out_cs;
@@ -589,6 +762,14 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.bias = L.bias;
   a.status = status;
   a.amax = L.amax;
+  a.stats = nullptr;
+  static unsigned long long *d_stats = nullptr;
+  const bool want_stats = getenv("PG_TC_STATS") != nullptr;
+  if (want_stats) {
+    if (!d_stats) PG_CUDA(cudaMalloc(&d_stats, 8 * sizeof(unsigned long long)));
+    PG_CUDA(cudaMemsetAsync(d_stats, 0, 8 * sizeof(unsigned long long), st));
+    a.stats = d_stats;
+  }
 
   const CUtensorMapDataType dt = es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   const CUtensorMapSwizzle sw =
@@ -598,8 +779,8 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     cuuint64_t dims[4] = {(cuuint64_t)L.Cin, (cuuint64_t)L.Win, (cuuint64_t)L.Hin, (cuuint64_t)ns};
     cuuint64_t strides[3] = {(cuuint64_t)L.in_cs * es, (cuuint64_t)L.Win * L.in_cs * es,
                              (cuuint64_t)L.Hin * L.Win * L.in_cs * es};
-    cuuint32_t box[4] = {(cuuint32_t)a.chunk, (cuuint32_t)(a.Wt * L.stride), (cuuint32_t)(a.Ht * L.stride),
-                         (cuuint32_t)a.Lt};
+    cuuint32_t box[4] = {(cuuint32_t)a.chunk, (cuuint32_t)(a.Wt * L.stride),
+                         (cuuint32_t)(a.halo ? a.Ht + 2 : a.Ht * L.stride), (cuuint32_t)a.Lt};
     cuuint32_t estr[4] = {1, (cuuint32_t)L.stride, (cuuint32_t)L.stride, 1};
     void *base = (uint8_t *)L.in + (size_t)L.in_co * es;
     if (enc(&mA, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
@@ -617,9 +798,28 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
       return PG_ERR_UNSUPPORTED;
   }
   if (smem > 227 * 1024) return PG_ERR_UNSUPPORTED;
-  PG_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   const int grid = std::min(a.num_tiles, per_sm * num_sms());
-  k_conv_tc<<<grid, kThreads, smem, st>>>(mA, mB, a);
+  if (fp8_out) {
+    PG_CUDA(cudaFuncSetAttribute(k_conv_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    k_conv_tc<true, false><<<grid, kThreads, smem, st>>>(mA, mB, a);
+  } else if (a.amax) {
+    PG_CUDA(cudaFuncSetAttribute(k_conv_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    k_conv_tc<false, true><<<grid, kThreads, smem, st>>>(mA, mB, a);
+  } else {
+    PG_CUDA(cudaFuncSetAttribute(k_conv_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    k_conv_tc<false, false><<<grid, kThreads, smem, st>>>(mA, mB, a);
+  }
+  if (want_stats) {
+    unsigned long long h[8];
+    PG_CUDA(cudaMemcpyAsync(h, d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+    PG_CUDA(cudaStreamSynchronize(st));
+    const double g = (double)grid;
+    fprintf(stderr,
+            "pg_tc_stats: %dx%d cin %d cout %d halo %d cb %d mt %d ctas %d stages %d tiles %d | per CTA kcycles: "
+            "producer wait %.0f / %.0f, mma wait acc %.0f full %.0f / %.0f, epilogue wait %.0f / %.0f (tiles %.0f)\n",
+            L.Hin, L.Win, L.Cin, L.Cout, a.halo, cb, a.mt, per_sm, a.stages, a.num_tiles, h[0] / g / 1e3,
+            h[1] / g / 1e3, h[2] / g / 1e3, h[3] / g / 1e3, h[4] / g / 1e3, h[5] / g / 1e3, h[6] / g / 1e3, h[7] / g);
+  }
   PG_CUDA(cudaGetLastError());
   return PG_OK;
 }
@@ -703,17 +903,25 @@ const int kTinyIn[3] = {0, 1, 2};
 // (CUDA events on the launching stream) and returns the fastest.  The layer
 // is left computed (every candidate writes the same output).
 pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream_t st, uint32_t *status,
-                     TcCfg *best) {
+                     TcCfg *best, float *best_ms_out) {
   cudaEvent_t e0, e1;
   PG_CUDA(cudaEventCreate(&e0));
   PG_CUDA(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   *best = TcCfg();
+  for (int halo : {0, 1})
+  for (int cb : {128, 64, 32})
+  for (int mt : {1, 2})
   for (int ctas : {1, 2, 3, 4})
-    for (int stages : {2, 3, 4, 6, 8, 12, 16, 24}) {
+    for (int stages : {2, 3, 4, 6, 8, 12, 16}) {
+      if (halo && stages > 6) continue;
+      if (!halo && cb != 128 && stages < 3) continue;
       TcCfg c;
       c.ctas = ctas;
       c.stages = stages;
+      c.mt = mt;
+      c.halo = halo;
+      c.cb = cb;
       if (launch_tc(L, ns, es, fp8, st, status, c) != PG_OK) continue;  // warm-up / feasibility
       cudaEventRecord(e0, st);
       pg_status s = launch_tc(L, ns, es, fp8, st, status, c);
@@ -730,6 +938,7 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   PG_CUDA(cudaGetLastError());
+  *best_ms_out = best_ms;
   return best->ctas ? PG_OK : PG_ERR_UNSUPPORTED;
 }
 
@@ -770,15 +979,28 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
     Layer &Lw = net->layers[li];
     if (tune) {
       TcCfg best;
-      PG_TRY(tune_layer(L, ns, es, fp8, st, ctx->d_status, &best));
+      float best_ms = 0;
+      PG_TRY(tune_layer(L, ns, es, fp8, st, ctx->d_status, &best, &best_ms));
       Lw.tc_ctas[pi] = best.ctas;
       Lw.tc_stages[pi] = best.stages;
+      Lw.tc_mt[pi] = best.mt;
+      Lw.tc_halo[pi] = best.halo;
+      Lw.tc_cb[pi] = best.cb;
       Lw.tuned_hw[pi] = H * W;
+      if (getenv("PG_TC_LOG"))
+        fprintf(stderr,
+                "pg_autotune: layer %d %dx%d cin %d cout %d stride %d leaves %u -> halo %d chunk %dB mt %d ctas %d "
+                "stages %d: %.1f us\n",
+                li, Hin, Win, Cin, Lr.cout, Lr.stride, ns, best.halo, best.cb, best.mt, best.ctas, best.stages,
+                best_ms * 1e3f);
     }
     TcCfg cfg;
     if (Lw.tuned_hw[pi] == H * W) {
       cfg.ctas = Lw.tc_ctas[pi];
       cfg.stages = Lw.tc_stages[pi];
+      cfg.mt = Lw.tc_mt[pi];
+      cfg.halo = Lw.tc_halo[pi];
+      cfg.cb = Lw.tc_cb[pi];
     }
     return launch_tc(L, ns, es, fp8, st, ctx->d_status, cfg);
   };

@@ -84,7 +84,7 @@ struct Layer {
   float w_scale;  // FP8 per-tensor weight scale (w = w_fp8 * w_scale)
   // Tensor-core launch shape picked by pg_autotune, per reduced precision
   // (index 1 = BF16, 2 = FP8) for maps of tuned_hw[i] bins (0 = not tuned).
-  int tc_ctas[3], tc_stages[3];
+  int tc_ctas[3], tc_stages[3], tc_mt[3], tc_halo[3], tc_cb[3];
   int tuned_hw[3];
 };
 

@@ -349,13 +349,16 @@ def _kl_l1(P, Pr):
     return np.array(kl), np.array(l1)
 
 
-def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_leaves=16, return_inputs=False):
+def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_leaves=16, return_inputs=False,
+             tune=False):
     ph = synth.photons(n, blobs, seed)
     d = torch.from_numpy(ph).cuda()
     g = pg.pg_build_grid(ctx, d, n, LO, HI, D, 0, thr)
     h = pg.pg_splat_photons(ctx, g, d, n, n // 2, H, W)
     blob = synth.net_blob(arch, widths, seed + 1)
     net = pg.pg_net_load(ctx, blob)
+    if tune:
+        pg.pg_autotune(ctx, h, net, prec)  # the reconstruction below uses the tuned launch shapes
     m = pg.pg_reconstruct(ctx, h, net, prec)
     t = pg.pg_build_cdf(ctx, m)
     tt = pg.export_tables(t)
@@ -381,13 +384,15 @@ def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_le
     (synth.ARCH_UNET4, (16, 32, 64, 128), 128, 128, 8_000, 3, 3000),
 ])
 def test_cnn_bf16_kl(ctx, arch, widths, H, W, n, D, thr):
-    """BF16 tensor-core network: mean KL(P_oracle || P) <= 1e-3 over leaves."""
-    P, Pr, valid = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 70 + H, pg.PG_BF16)
-    assert np.all(valid == 1)
-    kl, l1 = _kl_l1(P, Pr)
-    print(f"bf16 {arch} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; L1 mean {l1.mean():.2e}")
-    assert kl.mean() <= 1e-3
-    assert np.all(np.isfinite(kl))
+    """BF16 tensor-core network: mean KL(P_oracle || P) <= 1e-3 over leaves,
+    with the default launch shapes and with autotuned ones."""
+    for tune in (False, True):
+        P, Pr, valid = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 70 + H, pg.PG_BF16, tune=tune)
+        assert np.all(valid == 1)
+        kl, l1 = _kl_l1(P, Pr)
+        print(f"bf16 tune={tune} {arch} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; L1 mean {l1.mean():.2e}")
+        assert kl.mean() <= 1e-3
+        assert np.all(np.isfinite(kl))
 
 
 def _e4m3_emulated_P(x, net):
