@@ -195,11 +195,47 @@ pg_status pg_sample_dirs(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tabl
 pg_status pg_eval_pdf(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables,
                       const float *d_pos, const float *d_dir, uint64_t q, float *d_pdf);
 
+/* ---- scene batches ------------------------------------------------------ */
+
+/* Many independent scenes in one call sequence (the batched form of the
+ * calls above).  Photons are grouped by scene: scene s owns photons
+ * [scene_begin[s], scene_begin[s+1]), scene_begin[0] = 0,
+ * scene_begin[S] = n, 1 <= S <= 4096.  params[s] gives scene s's domain;
+ * max_depth, min_depth and split_threshold must be equal across scenes
+ * (max_depth + ceil(log8 S) <= 18, min_depth + ceil(log8 S) <= 6).  The
+ * scene index becomes the top bits of every code (s << 3 max_depth), so one
+ * sort and one subdivision build every scene's tree exactly as it would be
+ * built alone; leaves are ordered by scene, then Morton order.  Leaf depths
+ * exported from a batched grid include the ceil(log8 S) scene levels. */
+pg_status pg_build_grid_batched(pg_ctx *ctx, const pg_photon *d_photons, uint64_t n,
+                                const uint32_t *d_scene_begin, uint32_t S,
+                                const pg_grid_params *params, pg_grid **out);
+/* pg_splat_photons for a batched grid: a photon of scene s counts in the
+ * previous-iteration planes when its index within the scene is below
+ * n_prev[s] (d_n_prev: S uint32). */
+pg_status pg_splat_photons_batched(pg_ctx *ctx, const pg_grid *grid, const pg_photon *d_photons,
+                                   uint64_t n, const uint32_t *d_n_prev, int H, int W,
+                                   int frac_bits, pg_hist **out);
+/* pg_sample_dirs over a batched grid: queries of scene s are
+ * [query_begin[s], query_begin[s+1]) (S+1 uint32, non-decreasing, last = q);
+ * a query's Philox counter uses its index within the scene and its stream is
+ * stream_ids[s], so a scene's samples are the same alone or in any batch.
+ * q < 2^32. */
+pg_status pg_sample_dirs_batched(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables,
+                                 const float *d_pos, const uint32_t *d_query_begin, uint64_t q,
+                                 uint64_t seed, const uint32_t *d_stream_ids, float *d_dir,
+                                 float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin);
+/* pg_eval_pdf over a batched grid, queries grouped as in
+ * pg_sample_dirs_batched. */
+pg_status pg_eval_pdf_batched(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables,
+                              const float *d_pos, const float *d_dir,
+                              const uint32_t *d_query_begin, uint64_t q, float *d_pdf);
+
 /* ---- inspection -------------------------------------------------------- */
 
 enum {
   PG_INFO_N_PHOTONS = 1, PG_INFO_N_LEAVES = 2, PG_INFO_N_ACTIVE = 3, PG_INFO_H = 4,
-  PG_INFO_W = 5, PG_INFO_BYTES = 6, PG_INFO_MAX_DEPTH = 7
+  PG_INFO_W = 5, PG_INFO_BYTES = 6, PG_INFO_MAX_DEPTH = 7, PG_INFO_N_SCENES = 8, PG_INFO_SCENE_LEVELS = 9
 };
 pg_status pg_info(const void *handle, int what, uint64_t *value);
 

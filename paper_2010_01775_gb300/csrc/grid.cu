@@ -83,6 +83,33 @@ __global__ void k_morton(const pg_photon *__restrict__ ph, uint32_t n, GridGeom 
   if (bad) atomicOr(status, ST_INVALID_INPUT);
 }
 
+// Scene batches: photon i belongs to the scene whose range holds i; its code
+// is the scene index above the scene's own Morton code.
+__global__ void k_morton_batched(const pg_photon *__restrict__ ph, uint32_t n, const uint32_t *__restrict__ begin,
+                                 uint32_t S, const float *__restrict__ geom, int D, uint64_t *__restrict__ codes,
+                                 uint32_t *status) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t lo = 0, hi = S;  // last s with begin[s] <= i
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(begin + mid) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const float *gs = geom + 6 * lo;
+  GridGeom gg;
+  for (int a = 0; a < 3; ++a) {
+    gg.lo[a] = __ldg(gs + a);
+    gg.scale[a] = __ldg(gs + 3 + a);
+  }
+  gg.D = D;
+  gg.top = (uint32_t)((1u << D) - 1u);
+  float4 a = __ldg(reinterpret_cast<const float4 *>(ph + i));
+  uint32_t bad = 0;
+  codes[i] = ((uint64_t)lo << (3 * D)) | position_code(gg, a.x, a.y, a.z, bad);
+  if (bad) atomicOr(status, ST_INVALID_INPUT);
+}
+
 // ---------------------------------------------------------------- a2: radix sort
 __global__ void __launch_bounds__(kSortThreads) k_sort_upsweep(const uint64_t *__restrict__ keys, uint32_t n,
                                                                int shift, uint32_t *__restrict__ hist,
@@ -367,19 +394,30 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_grid_params *p, Grid *g) {
+pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_grid_params *p, Grid *g,
+                     const SceneBatch *sb) {
   cudaStream_t st = ctx->stream;
   const uint32_t n = (uint32_t)n64;
-  const int D = p->max_depth, dmin = p->min_depth;
+  // A scene batch adds scene_levels octree levels above every scene's root
+  // (8^scene_levels >= S); those levels always split, so each scene keeps
+  // exactly the tree it would have alone.
+  const uint32_t S = sb ? sb->S : 1u;
+  int SL = 0;
+  while ((1ull << (3 * SL)) < S) ++SL;
+  const int Dsp = p->max_depth;  // spatial depth of every scene
+  const int D = Dsp + SL, dmin = p->min_depth + SL;
+  if (D > 18 || dmin > 6) return PG_ERR_UNSUPPORTED;
   const uint32_t thr = p->split_threshold;
   g->n = n;
-  g->D = D;
-  g->min_depth = dmin;
+  g->D = Dsp;
+  g->min_depth = p->min_depth;
   g->thr = thr;
+  g->n_scenes = S;
+  g->scene_levels = SL;
   for (int a = 0; a < 3; ++a) {
     g->lo[a] = p->lo[a];
     g->hi[a] = p->hi[a];
-    g->scale[a] = (float)(ldexp(1.0, D) / ((double)p->hi[a] - (double)p->lo[a]));
+    g->scale[a] = (float)(ldexp(1.0, Dsp) / ((double)p->hi[a] - (double)p->lo[a]));
   }
   // Cell capacity: split cells of one level are disjoint and hold > thr
   // photons each, so each level below min_depth adds at most 8 n/(thr+1).
@@ -401,7 +439,8 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   g->lut_depth = D < 6 ? D : 6;
   const uint32_t lut_cells = 1u << (3 * g->lut_depth);
   size_t b_lut = align256(4ull * lut_cells);
-  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4 + b_lut;
+  size_t b_sb = align256(4ull * (S + 1)), b_sg = align256(24ull * S);
+  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4 + b_lut + b_sb + b_sg;
   PG_TRY(ctx_alloc(ctx, g->h.bytes, &g->block));
   uint8_t *q = (uint8_t *)g->block;
   g->codes = (uint64_t *)q; q += b_codes;
@@ -413,7 +452,18 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   g->leaf_end = (uint32_t *)q; q += b_l4;
   g->active = (uint32_t *)q; q += b_l4;
   g->slot_of_leaf = (int32_t *)q; q += b_l4;
-  g->lut = (uint32_t *)q;
+  g->lut = (uint32_t *)q; q += b_lut;
+  g->scene_begin = (uint32_t *)q; q += b_sb;
+  g->scene_geom = (float *)q;
+  if (sb) {
+    PG_CUDA(cudaMemcpyAsync(g->scene_begin, sb->d_begin, 4ull * (S + 1), cudaMemcpyDefault, st));
+    PG_CUDA(cudaMemcpyAsync(g->scene_geom, sb->h_geom, 24ull * S, cudaMemcpyHostToDevice, st));
+  } else {
+    uint32_t hb[2] = {0u, n};
+    float hg[6] = {g->lo[0], g->lo[1], g->lo[2], g->scale[0], g->scale[1], g->scale[2]};
+    PG_CUDA(cudaMemcpyAsync(g->scene_begin, hb, 8, cudaMemcpyHostToDevice, st));
+    PG_CUDA(cudaMemcpyAsync(g->scene_geom, hg, 24, cudaMemcpyHostToDevice, st));
+  }
 
   // Scratch: sort ping-pong, digit histograms, cells.
   const int passes = (3 * D + 7) / 8;
@@ -449,7 +499,11 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
 
   GridGeom gg = geom_of(g);
   const int TB = 256;
-  if (n) k_morton<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, gg, g->codes, ctx->d_status);
+  if (n && sb)
+    k_morton_batched<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, g->scene_begin, S, g->scene_geom, Dsp, g->codes,
+                                                     ctx->d_status);
+  else if (n)
+    k_morton<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, gg, g->codes, ctx->d_status);
 
   // a2: stable LSD radix sort; the final permutation lands in g->perm.
   const uint64_t *sorted = g->codes;

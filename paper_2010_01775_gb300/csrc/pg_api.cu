@@ -253,6 +253,98 @@ pg_status pg_build_grid(pg_ctx *c, const pg_photon *d_ph, uint64_t n, const pg_g
   return PG_OK;
 }
 
+pg_status pg_build_grid_batched(pg_ctx *c, const pg_photon *d_ph, uint64_t n, const uint32_t *d_scene_begin,
+                                uint32_t S, const pg_grid_params *p, pg_grid **out) {
+  if (!c || !p || !out || !d_scene_begin || S == 0 || (n && !d_ph)) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n >= (1ull << 31) || S > 4096) return PG_ERR_UNSUPPORTED;
+  for (uint32_t s = 0; s < S; ++s) {
+    if (p[s].max_depth != p[0].max_depth || p[s].min_depth != p[0].min_depth ||
+        p[s].split_threshold != p[0].split_threshold)
+      return PG_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+      if (!isfinite(p[s].lo[a]) || !isfinite(p[s].hi[a]) || !(p[s].hi[a] > p[s].lo[a])) return PG_ERR_INVALID_ARG;
+  }
+  if (p[0].max_depth < 0 || p[0].max_depth > 16 || p[0].min_depth < 0 || p[0].min_depth > p[0].max_depth)
+    return PG_ERR_INVALID_ARG;
+  // Scene offsets: checked on the host (non-decreasing, 0 .. n).
+  uint32_t *hb = (uint32_t *)malloc(4ull * (S + 1));
+  if (!hb) return PG_ERR_OOM;
+  if (cudaMemcpy(hb, d_scene_begin, 4ull * (S + 1), cudaMemcpyDefault) != cudaSuccess) {
+    free(hb);
+    cudaGetLastError();
+    return PG_ERR_NOT_DEVICE_PTR;
+  }
+  bool okb = hb[0] == 0 && hb[S] == n;
+  for (uint32_t s = 0; s < S && okb; ++s) okb = hb[s] <= hb[s + 1];
+  float *geom = (float *)malloc(24ull * S);
+  if (!okb || !geom) {
+    free(hb);
+    free(geom);
+    return okb ? PG_ERR_OOM : PG_ERR_INVALID_ARG;
+  }
+  for (uint32_t s = 0; s < S; ++s)
+    for (int a = 0; a < 3; ++a) {
+      geom[6 * s + a] = p[s].lo[a];
+      geom[6 * s + 3 + a] = (float)(ldexp(1.0, p[0].max_depth) / ((double)p[s].hi[a] - (double)p[s].lo[a]));
+    }
+  Staged ph, sbeg;
+  pg_status s0 = PG_OK;
+  if (n) s0 = stage_in(c, d_ph, n * sizeof(pg_photon), ph);
+  if (s0 == PG_OK) s0 = stage_in(c, hb, 4ull * (S + 1), sbeg);
+  Grid *g = s0 == PG_OK ? new (std::nothrow) Grid() : nullptr;
+  if (!g) {
+    free(hb);
+    free(geom);
+    return s0 == PG_OK ? PG_ERR_OOM : s0;
+  }
+  memset(g, 0, sizeof(*g));
+  g->h.kind = KIND_GRID;
+  g->h.ctx = c;
+  SceneBatch sb;
+  sb.S = S;
+  sb.d_begin = (const uint32_t *)sbeg.dev;
+  sb.h_geom = geom;
+  pg_status st = build_grid(c, (const pg_photon *)ph.dev, n, &p[0], g, &sb);
+  free(hb);
+  free(geom);
+  if (st != PG_OK) {
+    if (g->block) ctx_free(c, g->block, g->h.bytes);
+    delete g;
+    return st;
+  }
+  *out = (pg_grid *)g;
+  return PG_OK;
+}
+
+pg_status pg_splat_photons_batched(pg_ctx *c, const pg_grid *grid, const pg_photon *d_ph, uint64_t n,
+                                   const uint32_t *d_n_prev, int H, int W, int F, pg_hist **out) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  if (!c || !g || !out || !d_n_prev || (n && !d_ph)) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n != g->n || F < 0 || F > 62) return PG_ERR_INVALID_ARG;
+  if (!pow2_in(H, 4, 256) || !pow2_in(W, 4, 256) || H * W > 16384) return PG_ERR_NOT_POW2;
+  Staged ph, np;
+  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
+  PG_TRY(stage_in(c, d_n_prev, 4ull * g->n_scenes, np));
+  Hist *h = new (std::nothrow) Hist();
+  if (!h) return PG_ERR_OOM;
+  memset(h, 0, sizeof(*h));
+  h->h.kind = KIND_HIST;
+  h->h.ctx = c;
+  h->A = g->A;
+  h->H = H;
+  h->W = W;
+  pg_status s = splat(c, g, (const pg_photon *)ph.dev, n, 0, F, h, (const uint32_t *)np.dev);
+  if (s != PG_OK) {
+    if (h->block) ctx_free(c, h->block, h->h.bytes);
+    delete h;
+    return s;
+  }
+  *out = (pg_hist *)h;
+  return PG_OK;
+}
+
 pg_status pg_splat_photons(pg_ctx *c, const pg_grid *grid, const pg_photon *d_ph, uint64_t n, uint64_t n_prev,
                            int H, int W, int F, pg_hist **out) {
   const Grid *g = as<Grid>(grid, KIND_GRID);
@@ -492,6 +584,57 @@ pg_status pg_sample_dirs(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, c
   return PG_OK;
 }
 
+pg_status pg_sample_dirs_batched(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const float *d_pos,
+                                 const uint32_t *d_query_begin, uint64_t q, uint64_t seed, const uint32_t *d_stream_ids,
+                                 float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  const Tables *t = as<Tables>(tab, KIND_TABLES);
+  if (!c || !g || !t || !d_query_begin || !d_stream_ids || (q && (!d_pos || !d_dir || !d_pdf || !d_leaf)))
+    return PG_ERR_INVALID_ARG;
+  if (t->A != g->A) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  if (q >= (1ull << 32)) return PG_ERR_UNSUPPORTED;
+  Staged pos, qb, sid, dir, pdf, leaf, bin;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_in(c, d_query_begin, 4ull * (g->n_scenes + 1), qb));
+  PG_TRY(stage_in(c, d_stream_ids, 4ull * g->n_scenes, sid));
+  PG_TRY(stage_out(c, d_dir, q * 12, dir));
+  PG_TRY(stage_out(c, d_pdf, q * 4, pdf));
+  PG_TRY(stage_out(c, d_leaf, q * 4, leaf));
+  if (d_bin) PG_TRY(stage_out(c, d_bin, q * 4, bin));
+  QueryScenes qs;
+  qs.d_qbegin = (const uint32_t *)qb.dev;
+  qs.d_streams = (const uint32_t *)sid.dev;
+  PG_TRY(sample(c, g, t, (const float *)pos.dev, q, seed, 0, (float *)dir.dev, (float *)pdf.dev,
+                (uint32_t *)leaf.dev, d_bin ? (uint32_t *)bin.dev : nullptr, qs));
+  PG_TRY(finish_out(dir));
+  PG_TRY(finish_out(pdf));
+  PG_TRY(finish_out(leaf));
+  if (d_bin) PG_TRY(finish_out(bin));
+  return PG_OK;
+}
+
+pg_status pg_eval_pdf_batched(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const float *d_pos,
+                              const float *d_dir, const uint32_t *d_query_begin, uint64_t q, float *d_pdf) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  const Tables *t = as<Tables>(tab, KIND_TABLES);
+  if (!c || !g || !t || !d_query_begin || (q && (!d_pos || !d_dir || !d_pdf))) return PG_ERR_INVALID_ARG;
+  if (t->A != g->A) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  if (q >= (1ull << 32)) return PG_ERR_UNSUPPORTED;
+  Staged pos, dir, qb, pdf;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_in(c, d_dir, q * 12, dir));
+  PG_TRY(stage_in(c, d_query_begin, 4ull * (g->n_scenes + 1), qb));
+  PG_TRY(stage_out(c, d_pdf, q * 4, pdf));
+  QueryScenes qs;
+  qs.d_qbegin = (const uint32_t *)qb.dev;
+  qs.d_streams = nullptr;
+  PG_TRY(eval_pdf(c, g, t, (const float *)pos.dev, (const float *)dir.dev, q, (float *)pdf.dev, qs));
+  PG_TRY(finish_out(pdf));
+  return PG_OK;
+}
+
 pg_status pg_eval_pdf(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const float *d_pos, const float *d_dir,
                       uint64_t q, float *d_pdf) {
   const Grid *g = as<Grid>(grid, KIND_GRID);
@@ -518,6 +661,8 @@ pg_status pg_info(const void *handle, int what, uint64_t *v) {
       else if (what == PG_INFO_N_LEAVES) *v = g->L;
       else if (what == PG_INFO_N_ACTIVE) *v = g->A;
       else if (what == PG_INFO_MAX_DEPTH) *v = (uint64_t)g->D;
+      else if (what == PG_INFO_N_SCENES) *v = g->n_scenes;
+      else if (what == PG_INFO_SCENE_LEVELS) *v = (uint64_t)g->scene_levels;
       else if (what == PG_INFO_BYTES) *v = b->bytes;
       else return PG_ERR_INVALID_ARG;
       return PG_OK;

@@ -61,7 +61,21 @@ struct Grid {
   int32_t *slot_of_leaf; // [cap]
   uint32_t *lut;         // [8^lut_depth] leaf containing the first code of each lut_depth cell
   int lut_depth;
+  // Scene batch: scene s occupies the top bits of the code (s << 3 D); the
+  // tree's first scene_levels levels enumerate scenes.  A single-scene grid
+  // has n_scenes = 1, scene_levels = 0.
+  uint32_t n_scenes;
+  int scene_levels;
+  uint32_t *scene_begin;  // [S+1] photon offsets per scene
+  float *scene_geom;      // [S][6] lo[3], scale[3] per scene (batched grids)
   void *block;           // single allocation holding the arrays above
+};
+
+// Host-side description of a scene batch for build_grid.
+struct SceneBatch {
+  uint32_t S;
+  const uint32_t *d_begin;  // device [S+1]
+  const float *h_geom;      // host [S][6]
 };
 
 struct Hist {
@@ -280,19 +294,28 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 // ---------------------------------------------------------------- launchers
 // grid.cu
-pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n, const pg_grid_params *p, Grid *g);
+pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n, const pg_grid_params *p, Grid *g,
+                     const SceneBatch *sb = nullptr);
 // splat.cu
-pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h);
+pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h,
+                const uint32_t *d_scene_nprev = nullptr);
 // cnn.cu
 pg_status net_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
 pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m, bool tune = false);
 // cdf.cu
 pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t);
 // sample.cu
+// Per-scene query ranges (device [S+1]) and Philox stream ids (device [S])
+// of a batched call; null for a single-scene call.
+struct QueryScenes {
+  const uint32_t *d_qbegin = nullptr;
+  const uint32_t *d_streams = nullptr;
+};
 pg_status sample(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, uint64_t q, uint64_t seed,
-                 uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin);
+                 uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin,
+                 QueryScenes qs = QueryScenes());
 pg_status eval_pdf(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, const float *d_dir,
-                   uint64_t q, float *d_pdf);
+                   uint64_t q, float *d_pdf, QueryScenes qs = QueryScenes());
 
 inline GridGeom geom_of(const Grid *g) {
   GridGeom gg;

@@ -37,17 +37,52 @@ struct Tab {
   float pdf_uniform;  // 1 / (4 pi)
 };
 
-__global__ void k_sample(const float *__restrict__ pos, uint64_t q, GridGeom g, Tab tb, uint2 key, uint32_t stream,
+// Scene of query t in a batched call: the range of qbegin holding t; its
+// local index restarts at 0 and its Philox stream is that scene's id, so a
+// scene's samples do not depend on the batch around it.
+struct QueryCtx {
+  GridGeom g0;            // single-scene geometry
+  const uint32_t *qbegin; // [S+1] or null
+  const uint32_t *streams;
+  const float *geom;      // [S][6]
+  uint32_t S;
+  int shift;              // 3 * spatial depth
+};
+
+__device__ __forceinline__ uint64_t query_code(const QueryCtx &qc, const float *pos, uint64_t t, uint64_t &local,
+                                               uint32_t &stream, uint32_t &bad) {
+  if (!qc.qbegin) {
+    local = t;
+    return position_code(qc.g0, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  }
+  uint32_t lo = 0, hi = qc.S;  // last s with qbegin[s] <= t
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(qc.qbegin + mid) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  local = t - __ldg(qc.qbegin + lo);
+  if (qc.streams) stream = __ldg(qc.streams + lo);
+  GridGeom g = qc.g0;
+  for (int a = 0; a < 3; ++a) {
+    g.lo[a] = __ldg(qc.geom + 6 * lo + a);
+    g.scale[a] = __ldg(qc.geom + 6 * lo + 3 + a);
+  }
+  return ((uint64_t)lo << qc.shift) | position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+}
+
+__global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc, Tab tb, uint2 key, uint32_t stream,
                          float *__restrict__ dir, float *__restrict__ pdf, uint32_t *__restrict__ leaf_out,
                          uint32_t *__restrict__ bin_out, uint32_t *status) {
   uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= q) return;
   uint32_t bad = 0;
-  uint64_t code = position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  uint64_t local;
+  uint64_t code = query_code(qc, pos, t, local, stream, bad);
   if (bad) atomicOr(status, ST_INVALID_INPUT);
   uint32_t l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
   int32_t s = __ldg(tb.slot_of_leaf + l);
-  uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), stream, 0u), key);
+  uint4 r = philox4x32_10(make_uint4((uint32_t)local, (uint32_t)(local >> 32), stream, 0u), key);
   const float k24 = 5.9604644775390625e-08f;  // 2^-24
   float u0 = (float)(r.x >> 8) * k24, u1 = (float)(r.y >> 8) * k24;
   float u2 = (float)(r.z >> 8) * k24, u3 = (float)(r.w >> 8) * k24;
@@ -79,12 +114,13 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, GridGeom g, 
   if (bin_out) bin_out[t] = bo;
 }
 
-__global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ dirs, uint64_t q, GridGeom g, Tab tb,
+__global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ dirs, uint64_t q, QueryCtx qc, Tab tb,
                        const float *__restrict__ phi_tab, float *__restrict__ pdf, uint32_t *status) {
   uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= q) return;
-  uint32_t bad = 0;
-  uint64_t code = position_code(g, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  uint32_t bad = 0, stream = 0;
+  uint64_t local;
+  uint64_t code = query_code(qc, pos, t, local, stream, bad);
   uint32_t l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
   int32_t s = __ldg(tb.slot_of_leaf + l);
   float p = tb.pdf_uniform;
@@ -103,12 +139,23 @@ __global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ 
   pdf[t] = p;
 }
 
+QueryCtx make_qc(const Grid *g, const QueryScenes &qs) {
+  QueryCtx qc;
+  qc.g0 = geom_of(g);
+  qc.qbegin = qs.d_qbegin;
+  qc.streams = qs.d_streams;
+  qc.geom = g->scene_geom;
+  qc.S = g->n_scenes;
+  qc.shift = 3 * g->D;
+  return qc;
+}
+
 Tab make_tab(const Grid *g, const Tables *t) {
   Tab tb;
   tb.leaf_code = g->leaf_code;
   tb.lut = g->lut;
   tb.lut_cells = 1u << (3 * g->lut_depth);
-  tb.lut_shift = 3 * (g->D - g->lut_depth);
+  tb.lut_shift = 3 * (g->D + g->scene_levels - g->lut_depth);
   tb.slot_of_leaf = g->slot_of_leaf;
   tb.P = t->P;
   tb.Fphi = t->cdf_phi;
@@ -125,19 +172,19 @@ Tab make_tab(const Grid *g, const Tables *t) {
 }  // namespace
 
 pg_status sample(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, uint64_t q, uint64_t seed,
-                 uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin) {
+                 uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin, QueryScenes qs) {
   uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  k_sample<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, q, geom_of(g), make_tab(g, t), key, stream_id, d_dir,
+  k_sample<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, q, make_qc(g, qs), make_tab(g, t), key, stream_id, d_dir,
                                                       d_pdf, d_leaf, d_bin, ctx->d_status);
   PG_CUDA(cudaGetLastError());
   return PG_OK;
 }
 
 pg_status eval_pdf(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, const float *d_dir, uint64_t q,
-                   float *d_pdf) {
+                   float *d_pdf, QueryScenes qs) {
   const float *tab;
   PG_TRY(phi_table(ctx, t->W, &tab));
-  k_eval<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, d_dir, q, geom_of(g), make_tab(g, t), tab, d_pdf,
+  k_eval<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, d_dir, q, make_qc(g, qs), make_tab(g, t), tab, d_pdf,
                                                     ctx->d_status);
   PG_CUDA(cudaGetLastError());
   return PG_OK;

@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
     const uint32_t *__restrict__ leaf_begin, const uint32_t *__restrict__ leaf_end, uint32_t n_prev, int H, int W,
     float two_f, uint64_t limit, const float *__restrict__ phi_tab, uint64_t *__restrict__ pow_cur,
     uint32_t *__restrict__ cnt_cur, uint64_t *__restrict__ pow_prev, uint32_t *__restrict__ cnt_prev,
-    uint64_t *__restrict__ tot_cur, uint64_t *__restrict__ tot_prev, uint32_t *status) {
+    uint64_t *__restrict__ tot_cur, uint64_t *__restrict__ tot_prev, uint32_t *status,
+    const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ sc_begin,
+    const uint32_t *__restrict__ sc_nprev, int sc_shift) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kPlanes = kMode == 0 ? 2 : 1;
   const int HW = H * W;
@@ -37,6 +39,14 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
   const uint32_t slot = blockIdx.x;
   const uint32_t leaf = active[slot];
   const uint32_t b = leaf_begin[leaf], e = leaf_end[leaf];
+  // "Previous iteration" photons: original index below n_prev, counted
+  // within the leaf's scene for a scene batch.
+  uint32_t prev_base = 0, prev_lim = n_prev;
+  if (sc_nprev) {
+    const uint32_t sc = (uint32_t)(leaf_code[leaf] >> sc_shift);
+    prev_base = sc_begin[sc];
+    prev_lim = sc_nprev[sc];
+  }
   const int tid = threadIdx.x, lane = tid & 31;
 
   {
@@ -81,7 +91,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
           }
         }
       }
-      prev = p < n_prev;
+      prev = p - prev_base < prev_lim;
       if (kMode == 2 && !prev) bin = -1;
     }
     // Combine photons of this warp that share a bin.
@@ -169,7 +179,8 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h) {
+pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h,
+                const uint32_t *d_scene_nprev) {
   const size_t A = g->A, HW = (size_t)h->H * h->W;
   size_t b64 = align256(8 * A * HW), b32 = align256(4 * A * HW), bt = align256(8 * A);
   h->h.bytes = 2 * b64 + 2 * b32 + 2 * bt;
@@ -192,17 +203,20 @@ pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, u
     PG_CUDA(cudaFuncSetAttribute(k_splat<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_splat<0><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
-        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status);
+        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
+        g->scene_begin, d_scene_nprev, 3 * g->D);
   } else {
     size_t smem = 12 * HW + 8 * (size_t)h->W;
     PG_CUDA(cudaFuncSetAttribute(k_splat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     PG_CUDA(cudaFuncSetAttribute(k_splat<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_splat<1><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
-        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status);
+        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
+        g->scene_begin, d_scene_nprev, 3 * g->D);
     k_splat<2><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
-        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status);
+        h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
+        g->scene_begin, d_scene_nprev, 3 * g->D);
   }
   PG_CUDA(cudaGetLastError());
   return PG_OK;

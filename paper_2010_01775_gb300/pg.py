@@ -20,6 +20,7 @@ PG_FP32, PG_BF16, PG_FP8_E4M3 = 0, 1, 2
 PRECISIONS = {"fp32": PG_FP32, "bf16": PG_BF16, "fp8": PG_FP8_E4M3}
 
 PG_INFO_N_PHOTONS, PG_INFO_N_LEAVES, PG_INFO_N_ACTIVE, PG_INFO_H, PG_INFO_W, PG_INFO_BYTES, PG_INFO_MAX_DEPTH = range(1, 8)
+PG_INFO_N_SCENES, PG_INFO_SCENE_LEVELS = 8, 9
 PG_GRID_CODES, PG_GRID_PERM, PG_GRID_LEAF_OF, PG_GRID_LEAF_CODE, PG_GRID_LEAF_DEPTH = 100, 101, 102, 103, 104
 PG_GRID_LEAF_BEGIN, PG_GRID_LEAF_END, PG_GRID_ACTIVE, PG_GRID_SLOT_OF_LEAF = 105, 106, 107, 108
 PG_HIST_POW_CUR, PG_HIST_CNT_CUR, PG_HIST_POW_PREV, PG_HIST_CNT_PREV = 200, 201, 202, 203
@@ -33,7 +34,8 @@ STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_NOT_DEVICE_PTR", 3: "P
 EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_use", "pg_build_grid",
             "pg_splat_photons", "pg_net_load", "pg_reconstruct", "pg_map_import", "pg_build_cdf",
             "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string",
-            "pg_sort_photons_noalloc", "pg_autotune"]
+            "pg_sort_photons_noalloc", "pg_autotune", "pg_build_grid_batched", "pg_splat_photons_batched",
+            "pg_sample_dirs_batched", "pg_eval_pdf_batched"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -74,6 +76,10 @@ def load(path: str = LIB_PATH):
         "pg_info": [P, i32, ctypes.POINTER(u64)], "pg_export": [P, P, i32, P, sz],
         "pg_sort_photons_noalloc": [P, u64, ctypes.POINTER(pg_grid_params), P, P, P],
         "pg_autotune": [P, P, P, i32],
+        "pg_build_grid_batched": [P, P, u64, P, u32, P, PP],
+        "pg_splat_photons_batched": [P, P, P, u64, P, i32, i32, i32, PP],
+        "pg_sample_dirs_batched": [P, P, P, P, P, u64, u64, P, P, P, P, P],
+        "pg_eval_pdf_batched": [P, P, P, P, P, P, u64, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -207,6 +213,38 @@ def pg_reconstruct(ctx, hist, net, precision=PG_FP32) -> Handle:
     out = ctypes.c_void_p()
     _check(_lib.pg_reconstruct(ctx.ptr, hist.ptr, net.ptr, precision, ctypes.byref(out)), "pg_reconstruct")
     return Handle(ctx, out.value, "map")
+
+
+def pg_build_grid_batched(ctx, photons, n, scene_begin, los, his, max_depth, min_depth, split_threshold) -> Handle:
+    """scene_begin: S+1 uint32 offsets (array or tensor); los/his: S x 3."""
+    S = len(los)
+    prm = (pg_grid_params * S)()
+    for s in range(S):
+        prm[s] = pg_grid_params((ctypes.c_float * 3)(*[float(v) for v in los[s]]),
+                                (ctypes.c_float * 3)(*[float(v) for v in his[s]]), max_depth, min_depth,
+                                split_threshold)
+    out = ctypes.c_void_p()
+    _check(_lib.pg_build_grid_batched(ctx.ptr, _ptr(photons), n, _ptr(scene_begin), S, prm, ctypes.byref(out)),
+           "pg_build_grid_batched")
+    return Handle(ctx, out.value, "grid")
+
+
+def pg_splat_photons_batched(ctx, grid, photons, n, n_prev, H, W, frac_bits=32) -> Handle:
+    out = ctypes.c_void_p()
+    _check(_lib.pg_splat_photons_batched(ctx.ptr, grid.ptr, _ptr(photons), n, _ptr(n_prev), H, W, frac_bits,
+                                         ctypes.byref(out)), "pg_splat_photons_batched")
+    return Handle(ctx, out.value, "hist")
+
+
+def pg_sample_dirs_batched(ctx, grid, tables, pos, query_begin, q, seed, stream_ids, dirs, pdf, leaf, bins=None):
+    _check(_lib.pg_sample_dirs_batched(ctx.ptr, grid.ptr, tables.ptr, _ptr(pos), _ptr(query_begin), q, seed,
+                                       _ptr(stream_ids), _ptr(dirs), _ptr(pdf), _ptr(leaf), _ptr(bins)),
+           "pg_sample_dirs_batched")
+
+
+def pg_eval_pdf_batched(ctx, grid, tables, pos, dirs, query_begin, q, pdf):
+    _check(_lib.pg_eval_pdf_batched(ctx.ptr, grid.ptr, tables.ptr, _ptr(pos), _ptr(dirs), _ptr(query_begin), q,
+                                    _ptr(pdf)), "pg_eval_pdf_batched")
 
 
 def pg_autotune(ctx, hist, net, precision):
