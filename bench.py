@@ -287,6 +287,193 @@ def run_pg(args, wl, prec):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args, bw, prec):
+    """Scene-batch workload: one batched grid build, then splat -> CNN -> CDF
+    -> sample -> eval over all scenes, the post-grid part captured once as a
+    CUDA graph and replayed."""
+    import torch
+
+    from paper_2010_01775_gb300 import pg, synth
+
+    torch.cuda.set_device(0)
+    ph, begin, pos, dirs, qbegin, blob = synth.batch_inputs(bw)
+    S, n, Q = bw.n_scenes, int(begin[-1]), int(qbegin[-1])
+    los, his = [[0.0, 0.0, 0.0]] * S, [[1.0, 1.0, 1.0]] * S
+    n_prev = ((begin[1:] - begin[:-1]) // 2).astype(np.uint32)
+    streams = np.arange(S, dtype=np.uint32)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = pg.Context(stream.cuda_stream)
+    net = pg.pg_net_load(ctx, blob)
+    d_ph = torch.from_numpy(ph).cuda()
+    d_pos = torch.from_numpy(pos).cuda()
+    d_dir = torch.from_numpy(dirs).cuda()
+    d_begin = torch.from_numpy(begin.view(np.int32)).cuda()
+    d_qbegin = torch.from_numpy(qbegin.view(np.int32)).cuda()
+    d_nprev = torch.from_numpy(n_prev.view(np.int32)).cuda()
+    d_streams = torch.from_numpy(streams.view(np.int32)).cuda()
+    o = (torch.empty(Q, 3, device="cuda"), torch.empty(Q, device="cuda"), torch.empty(Q, dtype=torch.int32, device="cuda"),
+         torch.empty(Q, dtype=torch.int32, device="cuda"), torch.empty(Q, device="cuda"))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def grid():
+        return pg.pg_build_grid_batched(ctx, d_ph, n, d_begin, los, his, bw.max_depth, bw.min_depth,
+                                        bw.split_threshold)
+
+    def post(g):
+        h = pg.pg_splat_photons_batched(ctx, g, d_ph, n, d_nprev, bw.H, bw.W, bw.frac_bits)
+        m = pg.pg_reconstruct(ctx, h, net, prec)
+        t = pg.pg_build_cdf(ctx, m)
+        pg.pg_sample_dirs_batched(ctx, g, t, d_pos, d_qbegin, Q, 20101775, d_streams, o[0], o[1], o[2], o[3])
+        pg.pg_eval_pdf_batched(ctx, g, t, d_pos, d_dir, d_qbegin, Q, o[4])
+        for hd in (t, m, h):
+            hd.free()
+
+    g = grid()
+    A, L = g.info(pg.PG_INFO_N_ACTIVE), g.info(pg.PG_INFO_N_LEAVES)
+    h0 = pg.pg_splat_photons_batched(ctx, g, d_ph, n, d_nprev, bw.H, bw.W, bw.frac_bits)
+    if args.autotune:
+        pg.pg_autotune(ctx, h0, net, prec)
+    h0.free()
+    for _ in range(args.warmup):
+        post(g)
+    ctx.sync()
+    # Eager steps: grid + post, events around each part.
+    eager, grid_ms = [], []
+    for _ in range(args.steps):
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        g2 = grid()
+        e1.record(stream)
+        post(g2)
+        e2.record(stream)
+        e2.synchronize()
+        grid_ms.append(e0.elapsed_time(e1))
+        eager.append(e0.elapsed_time(e2))
+        g2.free()
+    # CUDA graph of the post-grid pipeline (allocations become graph memory nodes).
+    graph = torch.cuda.CUDAGraph()
+    ctx.sync()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+        post(g)
+    replays = []
+    for _ in range(args.steps):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        replays.append(e0.elapsed_time(e1))
+    ctx.sync()
+    graph_ms = statistics.median(replays) + statistics.median(grid_ms)
+    eager_ms = statistics.median(eager)
+    out = {
+        "metric": METRIC, "value": Q / (graph_ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": graph_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec], "data": "synthetic",
+        "config": {"workload": bw.name, "scenes": S, "photons": n, "queries": Q, "leaves": L, "active_leaves": A,
+                   "H": bw.H, "W": bw.W, "precision": args.precision,
+                   "scene_photons_min_max": [int(np.min(np.diff(begin))), int(np.max(np.diff(begin)))]},
+        "leaf_tables_per_s": A / (graph_ms / 1e3),
+        "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms, "grid_ms": statistics.median(grid_ms),
+        "graph_replay_ms": statistics.median(replays),
+    }
+    graph.reset()
+    g.free()
+    ctx.destroy()
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args, tr):
+    """Serving loop: open-loop Poisson trace at the trace's rate and at a
+    sustainable rate, closed-loop capacity, and plain FP32 one-request-at-a-
+    time execution of the same requests for comparison."""
+    import torch
+
+    from paper_2010_01775_gb300 import pg, serve, synth
+
+    torch.cuda.set_device(0)
+    trace = synth.serve_trace(tr, duration=args.serve_seconds)
+    n_pool = max(max(r["n"] for r in trace), 1 << 20)
+    ph = torch.from_numpy(synth.photons(n_pool, 64, tr.seed)).pin_memory()
+    pmax = np.maximum.accumulate(ph[:, 6].numpy().astype(np.float64))
+    qpos = torch.from_numpy(synth.query_positions(tr.q_max, tr.seed)).pin_memory()
+    qdir = torch.from_numpy(synth.query_directions(tr.q_max, tr.seed)).pin_memory()
+    blob = synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), tr.seed + 77)
+
+    def make(spec, prec=None):
+        n, q, o = spec["n"], spec["q"], spec["q_offset"]
+        # Largest fixed-point scale (<= 2^32) that keeps every sum below 2^63.
+        frac = int(min(32, np.floor(np.log2(2.0 ** 63 / (n * max(pmax[n - 1], 1e-30)))) - 1))
+        return serve.Request(ph[:n], qpos[o:o + q], qdir[o:o + q], spec["H"], spec["W"],
+                             pg.PRECISIONS[prec or spec["precision"]], max_depth=tr.max_depth,
+                             split_threshold=tr.split_threshold, frac_bits=frac, stream_id=spec["stream_id"])
+
+    def warm_requests(precs):
+        return [serve.Request(ph[:1 << 20], qpos[:65536], qdir[:65536], s, s, pg.PRECISIONS[p], max_depth=tr.max_depth,
+                              split_threshold=tr.split_threshold, stream_id=1 << 30)
+                for p in precs for s in tr.sizes]
+
+    def replay(srv, specs, rate_scale=1.0, closed=False):
+        t0 = time.perf_counter()
+        rs = []
+        for spec in specs:
+            if not closed:
+                dt = t0 + spec["arrival"] * rate_scale - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            rs.append(srv.submit(make(spec, "fp32" if srv.fp32 else None)))
+        for r in rs:
+            r.wait()
+        return rs
+
+    out = {}
+    srv = serve.Server(blob, workers=args.serve_workers, hbm_budget=120 << 30)
+    srv.fp32 = False
+    t = time.perf_counter()
+    srv.warmup(warm_requests(tr.precisions), autotune=args.autotune)
+    warm_s = time.perf_counter() - t
+    k = min(args.serve_closed, len(trace))
+    replay(srv, trace[:8], closed=True)  # first touches of the pools and staging buffers
+    closed = serve.latency_summary(replay(srv, trace[:k], closed=True))
+    spec_rate = serve.latency_summary(replay(srv, trace))
+    sustain = 0.7 * closed["requests_per_s"]
+    scale = tr.rate / sustain
+    sub = [r for r in trace if r["arrival"] * scale <= args.serve_seconds]
+    sustained = serve.latency_summary(replay(srv, sub, rate_scale=scale))
+    srv.close()
+    # Plain FP32, one request at a time, no batching: the same first requests.
+    k32 = min(args.serve_fp32, k)
+    base = serve.Server(blob, workers=1, hbm_budget=120 << 30, batching=False)
+    base.fp32 = True
+    replay(base, trace[:2], closed=True)
+    fp32 = serve.latency_summary(replay(base, trace[:k32], closed=True))
+    base.close()
+    srv2 = serve.Server(blob, workers=args.serve_workers, hbm_budget=120 << 30)
+    srv2.fp32 = False
+    srv2.warmup(warm_requests(tr.precisions), autotune=args.autotune)
+    same = serve.latency_summary(replay(srv2, trace[:k32], closed=True))
+    srv2.close()
+    out = {
+        "metric": METRIC, "value": spec_rate["samples_per_s"], "unit": "samples/s", "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+fp8e4m3",
+        "data": "synthetic",
+        "config": {"workload": tr.name, "requests": len(trace), "rate_per_s": tr.rate,
+                   "arrival_seconds": args.serve_seconds, "workers": args.serve_workers, "hbm_budget_gb": 120,
+                   "batching": "continuous, same map size/precision, <=64 scenes, <=8M photons"},
+        "latency_ms": {"p50": spec_rate.get("p50_ms"), "p99": spec_rate.get("p99_ms")},
+        "open_loop_at_trace_rate": spec_rate,
+        "open_loop_at_70pct_capacity": dict(sustained, rate_per_s=sustain, requests=len(sub)),
+        "closed_loop_capacity": dict(closed, requests=k),
+        "fp32_one_at_a_time": dict(fp32, requests=k32),
+        "served_same_requests": dict(same, requests=k32),
+        "speedup_vs_fp32_one_at_a_time": same["samples_per_s"] / fp32["samples_per_s"],
+        "warmup_s": warm_s,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def count_launches(wl, A, prec):
     """Kernel launches of one step (host-side count of the library's launch
     sequence for this workload)."""
@@ -387,6 +574,10 @@ def main():
     ap.add_argument("--workload", default="scale")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving trace: seconds of arrivals")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-closed", type=int, default=64, help="requests in the closed-loop capacity run")
+    ap.add_argument("--serve-fp32", type=int, default=12, help="requests in the FP32 one-at-a-time run")
     ap.add_argument("--cpu-sample-leaves", type=int, default=4)
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="tune the tensor-core launch shapes before timing (untimed)")
@@ -394,6 +585,17 @@ def main():
                     help="also time the other CNN precisions and report their KL against the oracle")
     args = ap.parse_args()
     from paper_2010_01775_gb300 import synth
+    if args.workload in synth.SERVE_TRACES:
+        import __graft_entry__
+        __graft_entry__.build()
+        run_serve(args, synth.SERVE_TRACES[args.workload])
+        return
+    if args.workload in synth.BATCH_WORKLOADS:
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2010_01775_gb300 import pg
+        run_batch(args, synth.BATCH_WORKLOADS[args.workload], pg.PRECISIONS[args.precision])
+        return
     wl = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

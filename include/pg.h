@@ -95,6 +95,34 @@ pg_status pg_sync(pg_ctx *ctx);
 /* Bytes currently charged to the context's budget. */
 pg_status pg_bytes_in_use(const pg_ctx *ctx, uint64_t *bytes);
 
+/* ---- shared HBM budget (serving) ----------------------------------------
+ * One byte budget shared by several contexts, e.g. one context per serving
+ * stream on the same device.  The paper has no counterpart (it renders one
+ * scene at a time); this is the admission signal of a multi-request server.
+ * Every handle and call scratch of an attached context is charged to the
+ * shared budget as well as to the context's own hbm_budget; a call whose
+ * allocation would pass either cap fails with PG_ERR_OOM having allocated
+ * nothing (calls are all-or-nothing), so the caller can wait for a release
+ * and retry the same call.  Caller-owned device buffers (inputs, outputs)
+ * may be charged with pg_budget_charge / pg_budget_release.  All budget
+ * functions are thread-safe. */
+typedef struct pg_budget pg_budget;
+pg_status pg_budget_create(uint64_t capacity, pg_budget **out);
+/* PG_ERR_INVALID_ARG while a context is still attached. */
+pg_status pg_budget_destroy(pg_budget *b);
+/* Attaches ctx to b (NULL detaches).  The bytes ctx already holds move to
+ * the new budget (PG_ERR_OOM, and nothing changes, if they do not fit). */
+pg_status pg_ctx_attach_budget(pg_ctx *ctx, pg_budget *b);
+/* Charges `bytes` if they fit (PG_ERR_OOM otherwise, nothing charged). */
+pg_status pg_budget_charge(pg_budget *b, uint64_t bytes);
+pg_status pg_budget_release(pg_budget *b, uint64_t bytes);
+/* Blocks until `bytes` would fit or a release has happened after the
+ * release count *generation (as returned by pg_budget_query or by a
+ * previous wait), at most timeout_ms; PG_ERR_TIMEOUT if neither.  Updates
+ * *generation to the current release count. */
+pg_status pg_budget_wait(pg_budget *b, uint64_t bytes, uint64_t *generation, uint32_t timeout_ms);
+pg_status pg_budget_query(const pg_budget *b, uint64_t *in_use, uint64_t *capacity, uint64_t *generation);
+
 /* ---- a1-a4: grid ------------------------------------------------------- */
 
 /* Voxel location and adaptive subdivision (Algorithm 1 "Locate voxel j" and
@@ -212,7 +240,8 @@ pg_status pg_build_grid_batched(pg_ctx *ctx, const pg_photon *d_photons, uint64_
                                 const pg_grid_params *params, pg_grid **out);
 /* pg_splat_photons for a batched grid: a photon of scene s counts in the
  * previous-iteration planes when its index within the scene is below
- * n_prev[s] (d_n_prev: S uint32). */
+ * n_prev[s] (d_n_prev: S uint32), and the overflow bound of scene s is the
+ * one it has alone, (2^63-1) / (scene_begin[s+1] - scene_begin[s]). */
 pg_status pg_splat_photons_batched(pg_ctx *ctx, const pg_grid *grid, const pg_photon *d_photons,
                                    uint64_t n, const uint32_t *d_n_prev, int H, int W,
                                    int frac_bits, pg_hist **out);
@@ -251,6 +280,10 @@ enum {
   PG_GRID_LEAF_END = 106,   /* uint32 [L]  one past the last sorted slot */
   PG_GRID_ACTIVE = 107,     /* uint32 [A]  active leaves, ascending */
   PG_GRID_SLOT_OF_LEAF = 108, /* int32 [L] map slot or -1 */
+  PG_GRID_SCENE_LEAF_BEGIN = 109, /* uint32 [S+1] first leaf of each scene (leaves are
+                                     ordered by scene), L at S; a leaf id returned by
+                                     pg_sample_dirs_batched minus this is the id the
+                                     scene's leaf has in its grid alone */
   PG_HIST_POW_CUR = 200,    /* uint64 [A][H*W] */
   PG_HIST_CNT_CUR = 201,    /* uint32 [A][H*W] */
   PG_HIST_POW_PREV = 202,   /* uint64 [A][H*W] */

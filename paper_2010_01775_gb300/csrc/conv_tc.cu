@@ -18,7 +18,19 @@
 //   warps 2-5 epilogue: tcgen05.ld the accumulator (one pixel row per thread),
 //            bias + ELU, convert, store channel-last (optionally upsampled x2)
 // The accumulator is double-buffered in TMEM so the epilogue of one tile
-// overlaps the main loop of the next.  Every mbarrier wait is bounded (2 s):
+// overlaps the main loop of the next.
+//
+// Operand staging modes for the A (activation) tile of a 3x3 stride-1 layer:
+//   0  one box per (tap, channel chunk) at the tap-shifted origin;
+//   1  per channel chunk, three x-shifted boxes of the tile plus a one-row
+//      halo; tap (ky, kx) is rows ky*Wt.. of copy kx;
+//   2  per channel chunk, ONE box of whole zero-padded rows (P = W + 2
+//      pixels: x = -1 .. W) covering the tile and its halo.  Output pixels are
+//      indexed in the same padded row space (q = y * P + x), so tap (ky, kx)
+//      of output q is input row q + ky * P + kx of the box: every tap is the
+//      same box read from another starting row.  The two pad columns of each
+//      output row are computed and discarded (2 / (W + 2) extra MMA rows);
+//      the TMA moves each input pixel about once instead of 3 or 9 times.  Every mbarrier wait is bounded (2 s):
 // on expiry the CTA raises PG_ERR_TIMEOUT in the context status word, drains
 // what it issued and returns.
 #include <cuda.h>
@@ -52,8 +64,11 @@ struct TcArgs {
   int halo;         // 3x3 stride-1 layers: one stage = one channel chunk, all 9 taps
   uint32_t bytes_ver;  // halo mode: bytes of one x-shifted input box (Ht + 2 rows)
   int Wt, Ht, Lt;
+  int P, Hb, tpl;   // mode 2: padded row pitch, box rows, tiles per leaf
   int num_tiles, kiters, stages;
-  uint32_t bytes_a, bytes_b;  // per stage
+  uint32_t bytes_a, bytes_b;  // per stage (A rounded up to 1 KB in mode 2)
+  uint32_t tx_bytes;          // bytes the TMA copies of one stage deliver
+  int chunk_bytes;            // bytes of one operand row (the swizzle row)
   uint32_t idesc;
   uint32_t sbo;
   int swz;
@@ -138,32 +153,6 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *ba
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// K-major operand in shared memory, rows of `row bytes` swizzled in groups of
-// 8 rows: start address, stride between 8-row groups (SBO), swizzle mode.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, int swz) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;  // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version
-  d |= (uint64_t)(swz & 7) << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
 
 // One MMA with descriptors given as (low, high) words.
 template <bool kFp8>
@@ -277,6 +266,62 @@ __device__ __forceinline__ void epi16(const TcArgs &a, const uint32_t *r, const 
     }
 }
 
+// Descriptor words and offsets of one pipeline stage (see the MMA issuer).
+struct StageOps {
+  uint32_t d, BN, alo, blo, a_byte0;
+  int off0, P;
+  uint32_t cb, sub_step, row_step, ver16, tap_b16, desc_hi, idesc;
+  bool first;
+};
+
+// The MMAs of one stage as straight-line code: a tcgen05.mma stream issued
+// from a loop with run-time trip counts runs about 3x slower per
+// instruction than the same stream unrolled, so every (mode, subtiles,
+// K steps) combination gets its own fully unrolled sequence.  For each
+// accumulator the K order is (tap, K step), as in the loop form.
+template <bool kFp8, int kMode, int kMT, int kMPS>
+__device__ __forceinline__ void issue_stage(const StageOps &o) {
+  if constexpr (kMode == 0) {
+#pragma unroll
+    for (int j = 0; j < kMPS; ++j) {
+      const uint32_t acc = (o.first && j == 0) ? 0u : 1u;
+#pragma unroll
+      for (int sub = 0; sub < kMT; ++sub)
+        mma_issue<kFp8>(o.d + (uint32_t)sub * o.BN, o.alo + (uint32_t)sub * o.sub_step + 2u * j, o.desc_hi,
+                        o.blo + 2u * j, o.desc_hi, o.idesc, acc);
+    }
+  } else {
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const uint32_t b_tap = o.blo + (uint32_t)(ky * 3 + kx) * o.tap_b16;
+#pragma unroll
+        for (int sub = 0; sub < kMT; ++sub) {
+          uint32_t a_tap;
+          if constexpr (kMode == 1) {
+            // Copy kx of the haloed tile, from row ky * Wt on.
+            a_tap = o.alo + (uint32_t)kx * o.ver16 + (uint32_t)ky * o.row_step + (uint32_t)sub * o.sub_step;
+          } else {
+            // Padded row off0 + ky * P + kx of the box.  Any starting row
+            // works: the MMA, like the TMA that wrote the box, applies the
+            // swizzle to absolute shared-memory address bits of the
+            // 1-KB-aligned buffer (base offset 0).
+            const uint32_t addr = o.a_byte0 + ((uint32_t)(o.off0 + ky * o.P + kx) + (uint32_t)(sub * kBM)) * o.cb;
+            a_tap = ((addr & 0x3FFFFu) >> 4) | (1u << 16);
+          }
+#pragma unroll
+          for (int j = 0; j < kMPS; ++j) {
+            const uint32_t acc = (o.first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
+            mma_issue<kFp8>(o.d + (uint32_t)sub * o.BN, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi,
+                            o.idesc, acc);
+          }
+        }
+      }
+    }
+  }
+}
+
 template <bool kFp8Out, bool kCalib>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
@@ -330,17 +375,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     long long prod_wait = 0;
     const long long prod_t0 = clock64();
-    const int ntma = a.halo ? 12 : 2;
+    const int ntma = a.halo == 2 ? 10 : (a.halo ? 12 : 2);
     for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
       int l0, y0, x0;
-      tile_origin(a, t, l0, y0, x0);
+      if (a.halo == 2) {
+        // Leaf of the tile, and the first box row: the image row above the
+        // tile's first output row (row -1 and rows >= H are zero-filled).
+        l0 = t / a.tpl;
+        y0 = ((t - l0 * a.tpl) * kBM * a.mt) / a.P - 1;
+        x0 = -1;
+      } else {
+        tile_origin(a, t, l0, y0, x0);
+      }
       for (int ki = 0; ki < a.kiters; ++ki) {
         int got = 1;
         if (lane == 0) {
           const long long c0 = clock64();
           got = mbar_wait(&empty[stage], phase ^ 1u, abort_flag) ? 1 : 0;
           prod_wait += clock64() - c0;
-          if (got) mbar_expect_tx(&full[stage], a.bytes_a + a.bytes_b);
+          if (got) mbar_expect_tx(&full[stage], a.tx_bytes);
         }
         got = __shfl_sync(0xFFFFFFFFu, got, 0);
         if (!got) {
@@ -349,7 +402,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
         if (lane < ntma) {
-          if (a.halo) {
+          if (a.halo == 2) {
+            const int cc = ki;
+            if (lane == 0)
+              tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk, x0, y0, l0);
+            else
+              tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 1) * (a.bytes_b / 9),
+                          (lane - 1) * a.Cin + cc * a.chunk, 0);
+          } else if (a.halo) {
             // Three copies of the haloed input tile (rows y0-1 .. y0+Ht),
             // shifted by kx - 1 columns; out-of-range columns and rows are
             // zero-filled.  Tap (ky, kx) is then rows ky*Wt.. of copy kx.
@@ -419,6 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mma_wait_acc += clock64() - c0;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * a.mt * a.BN);
+        const int off0 = a.halo == 2 ? ((t % a.tpl) * kBM * a.mt) % a.P : 0;
         bool ok = true;
         for (int ki = 0; ki < a.kiters; ++ki) {
           c0 = clock64();
@@ -436,28 +497,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t alo_s = a_lo0 + (uint32_t)stage * (a.bytes_a >> 4);
           const uint32_t blo_s = b_lo0 + (uint32_t)stage * (a.bytes_b >> 4);
           const bool first = ki == 0;
-          if (!a.halo) {
-            for (int j = 0; j < a.mma_per_stage; ++j) {
-              const uint32_t acc = (first && j == 0) ? 0u : 1u;
-              for (int sub = 0; sub < a.mt; ++sub)
-                mma_issue<kFp8Out>(d + (uint32_t)(sub * a.BN), alo_s + (uint32_t)sub * sub_step + 2u * j, desc_hi,
-                                   blo_s + 2u * j, desc_hi, a.idesc, acc);
-            }
-          } else {
-            // Tap (ky, kx) reads copy kx of the haloed tile from row ky * Wt on.
-            uint32_t b_tap = blo_s;
-            for (int ky = 0; ky < 3; ++ky) {
-              for (int kx = 0; kx < 3; ++kx) {
-                const uint32_t a_tap = alo_s + (uint32_t)kx * ver16 + (uint32_t)ky * row_step;
-                for (int j = 0; j < a.mma_per_stage; ++j) {
-                  const uint32_t acc = (first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
-                  for (int sub = 0; sub < a.mt; ++sub)
-                    mma_issue<kFp8Out>(d + (uint32_t)(sub * a.BN), a_tap + (uint32_t)sub * sub_step + 2u * j, desc_hi,
-                                       b_tap + 2u * j, desc_hi, a.idesc, acc);
-                }
-                b_tap += tap_b16;
-              }
-            }
+          const StageOps so{d,         (uint32_t)a.BN, alo_s,        blo_s,   a_base + (uint32_t)stage * a.bytes_a,
+                            off0,      a.P,            (uint32_t)a.chunk_bytes, sub_step, row_step, ver16, tap_b16,
+                            desc_hi,   a.idesc,        first};
+          switch (a.halo * 16 + a.mt * 4 + (a.mma_per_stage >> 1)) {
+#define PG_STAGE_CASE(H, MT, MPS) \
+  case H * 16 + MT * 4 + (MPS >> 1): issue_stage<kFp8Out, H, MT, MPS>(so); break;
+            PG_STAGE_CASE(0, 1, 1) PG_STAGE_CASE(0, 1, 2) PG_STAGE_CASE(0, 1, 4)
+            PG_STAGE_CASE(0, 2, 1) PG_STAGE_CASE(0, 2, 2) PG_STAGE_CASE(0, 2, 4)
+            PG_STAGE_CASE(1, 1, 1) PG_STAGE_CASE(1, 1, 2) PG_STAGE_CASE(1, 1, 4)
+            PG_STAGE_CASE(1, 2, 1) PG_STAGE_CASE(1, 2, 2) PG_STAGE_CASE(1, 2, 4)
+            PG_STAGE_CASE(2, 1, 1) PG_STAGE_CASE(2, 1, 2) PG_STAGE_CASE(2, 1, 4)
+            PG_STAGE_CASE(2, 2, 1) PG_STAGE_CASE(2, 2, 2) PG_STAGE_CASE(2, 2, 4)
+#undef PG_STAGE_CASE
+            default: break;
           }
           mma_commit(&empty[stage]);
           if (++stage == a.stages) {
@@ -495,13 +548,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&acc_full[buf], use, abort_flag)) break;
       epi_wait += clock64() - c0;
       tc_fence_after();
-      int l0, y0, x0;
-      tile_origin(a, t, l0, y0, x0);
+      int l0 = 0, y0 = 0, x0 = 0, q0 = 0;
+      if (a.halo == 2) {
+        l0 = t / a.tpl;
+        q0 = (t - l0 * a.tpl) * kBM * a.mt;
+      } else {
+        tile_origin(a, t, l0, y0, x0);
+      }
       for (int sub = 0; sub < a.mt; ++sub) {
       const int mm = sub * kBM + m;
-      const int xx = mm % a.Wt, yy = (mm / a.Wt) % a.Ht, ll = mm / (a.Wt * a.Ht);
-      const int leaf = l0 + ll, y = y0 + yy, x = x0 + xx;
-      const bool valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
+      int leaf, y, x;
+      bool valid;
+      if (a.halo == 2) {
+        // Padded row space: q = y * P + x; the pad columns and rows past the
+        // map are discarded.
+        const int qq = q0 + mm;
+        leaf = l0;
+        y = qq / a.P;
+        x = qq - y * a.P;
+        valid = y < a.Hout && x < a.Wout;
+      } else {
+        const int xx = mm % a.Wt, yy = (mm / a.Wt) % a.Ht, ll = mm / (a.Wt * a.Ht);
+        leaf = l0 + ll;
+        y = y0 + yy;
+        x = x0 + xx;
+        valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
+      }
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN);
       const size_t pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
       if (a.BN % 32 == 0) {
@@ -635,27 +707,27 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
+  // Looked up once per process (thread-safe static initialisation).
+  static const EncodeTiledFn fn = [] {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    return (EncodeTiledFn) nullptr;
+  }();
   return fn;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 148;
+  }();
   return n;
 }
 
@@ -721,11 +793,27 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     return PG_ERR_UNSUPPORTED;
   a.num_tiles = (int)((M + TP - 1) / TP);
   a.halo = cfg.halo;
-  if (a.halo && (L.k != 3 || L.stride != 1 || a.Lt != 1 || a.Ht + 2 > 256)) return PG_ERR_UNSUPPORTED;
+  if (a.halo == 1 && (L.k != 3 || L.stride != 1 || a.Lt != 1 || a.Ht + 2 > 256)) return PG_ERR_UNSUPPORTED;
+  a.chunk_bytes = cb;
   a.kiters = a.halo ? a.cchunks : L.k * L.k * a.cchunks;
   a.bytes_ver = (uint32_t)((a.Ht + 2) * a.Wt * cb);
   a.bytes_a = a.halo ? 3u * a.bytes_ver : (uint32_t)(TP * cb);
   a.bytes_b = (uint32_t)(L.Cout * cb) * (a.halo ? 9u : 1u);
+  a.tx_bytes = a.bytes_a + a.bytes_b;
+  if (a.halo == 2) {
+    // One box of Hb padded rows per channel chunk: the tile's TP rows start
+    // anywhere in their first image row, and the taps read up to 2P + 2 rows
+    // further, so Hb = ceil((TP + 1) / P) + 3 image rows always cover them.
+    if (L.k != 3 || L.stride != 1 || HWo < TP || Wout + 2 > 256) return PG_ERR_UNSUPPORTED;
+    a.P = Wout + 2;
+    a.Hb = (TP + a.P) / a.P + 3;
+    if (a.Hb > 256) return PG_ERR_UNSUPPORTED;
+    a.tpl = (Hout * a.P + TP - 1) / TP;
+    a.num_tiles = (int)ns * a.tpl;
+    const uint32_t box = (uint32_t)(a.Hb * a.P * cb);
+    a.bytes_a = (box + 1023u) & ~1023u;
+    a.tx_bytes = box + a.bytes_b;
+  }
   a.sbo = 8u * (uint32_t)cb;
   a.swz = cb == 128 ? 2 : (cb == 64 ? 4 : 6);
   a.mma_per_stage = cb / 32;
@@ -781,6 +869,11 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
                              (cuuint64_t)L.Hin * L.Win * L.in_cs * es};
     cuuint32_t box[4] = {(cuuint32_t)a.chunk, (cuuint32_t)(a.Wt * L.stride),
                          (cuuint32_t)(a.halo ? a.Ht + 2 : a.Ht * L.stride), (cuuint32_t)a.Lt};
+    if (a.halo == 2) {
+      box[1] = (cuuint32_t)a.P;
+      box[2] = (cuuint32_t)a.Hb;
+      box[3] = 1;
+    }
     cuuint32_t estr[4] = {1, (cuuint32_t)L.stride, (cuuint32_t)L.stride, 1};
     void *base = (uint8_t *)L.in + (size_t)L.in_co * es;
     if (enc(&mA, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
@@ -879,6 +972,9 @@ static pg_status make_lp_weights(pg_ctx *ctx, Layer &L, bool first, pg_precision
 
 pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
   if (!encode_fn()) return PG_ERR_UNSUPPORTED;
+  // Weight copies belong to the net, so they are charged to the context that
+  // owns it (the one that frees them), whichever context runs the first call.
+  ctx = net->h.ctx;
   for (int l = 0; l < net->n_layers; ++l) {
     Layer &L = net->layers[l];
     // FP8 runs are calibrated by one BF16 pass, so they need both copies.
@@ -908,8 +1004,9 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   PG_CUDA(cudaEventCreate(&e0));
   PG_CUDA(cudaEventCreate(&e1));
   float best_ms = 1e30f;
+  pg_status last_err = PG_ERR_UNSUPPORTED;
   *best = TcCfg();
-  for (int halo : {0, 1})
+  for (int halo : {0, 1, 2})
   for (int cb : {128, 64, 32})
   for (int mt : {1, 2})
   for (int ctas : {1, 2, 3, 4})
@@ -922,7 +1019,11 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
       c.mt = mt;
       c.halo = halo;
       c.cb = cb;
-      if (launch_tc(L, ns, es, fp8, st, status, c) != PG_OK) continue;  // warm-up / feasibility
+      const pg_status w = launch_tc(L, ns, es, fp8, st, status, c);  // warm-up / feasibility
+      if (w != PG_OK) {
+        if (w != PG_ERR_UNSUPPORTED) last_err = w;
+        continue;
+      }
       cudaEventRecord(e0, st);
       pg_status s = launch_tc(L, ns, es, fp8, st, status, c);
       cudaEventRecord(e1, st);
@@ -939,7 +1040,7 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   cudaEventDestroy(e1);
   PG_CUDA(cudaGetLastError());
   *best_ms_out = best_ms;
-  return best->ctas ? PG_OK : PG_ERR_UNSUPPORTED;
+  return best->ctas ? PG_OK : last_err;
 }
 
 template <typename T>
@@ -1001,6 +1102,16 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       cfg.mt = Lw.tc_mt[pi];
       cfg.halo = Lw.tc_halo[pi];
       cfg.cb = Lw.tc_cb[pi];
+    }
+    // Diagnostics: PG_TC_FORCE=<mode>[,cb,mt,ctas,stages] runs every layer
+    // that supports it with that operand staging mode and launch shape (zero
+    // or missing fields: defaults); other layers run the default shape.
+    if (const char *force = getenv("PG_TC_FORCE")) {
+      TcCfg f;
+      sscanf(force, "%d,%d,%d,%d,%d", &f.halo, &f.cb, &f.mt, &f.ctas, &f.stages);
+      const pg_status s = launch_tc(L, ns, es, fp8, st, ctx->d_status, f);
+      if (s != PG_ERR_UNSUPPORTED) return s;
+      return launch_tc(L, ns, es, fp8, st, ctx->d_status, TcCfg());
     }
     return launch_tc(L, ns, es, fp8, st, ctx->d_status, cfg);
   };

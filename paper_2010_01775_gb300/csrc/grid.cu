@@ -380,6 +380,16 @@ __global__ void k_leaf_lut(const uint64_t *__restrict__ leaf_code, const uint32_
   lut[c] = find_leaf(leaf_code, counters[0], (uint64_t)c << shift);
 }
 
+// First leaf of every scene of a batch (leaves are ordered by scene), and L
+// at index S: slot s starts at code s << shift.
+__global__ void k_scene_leaves(const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ counters,
+                               int shift, uint32_t S, bool full, uint32_t *__restrict__ out) {
+  uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > S) return;
+  const uint32_t L = counters[0];
+  out[s] = (s == S && full) ? L : find_leaf(leaf_code, L, (uint64_t)s << shift);
+}
+
 // ---------------------------------------------------------------- a4
 __global__ void k_leaf_assign(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ perm, uint32_t n,
                               const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ counters,
@@ -440,7 +450,7 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   const uint32_t lut_cells = 1u << (3 * g->lut_depth);
   size_t b_lut = align256(4ull * lut_cells);
   size_t b_sb = align256(4ull * (S + 1)), b_sg = align256(24ull * S);
-  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4 + b_lut + b_sb + b_sg;
+  g->h.bytes = b_codes + b_perm + b_lo + b_lc + 5 * b_l4 + b_lut + 2 * b_sb + b_sg;
   PG_TRY(ctx_alloc(ctx, g->h.bytes, &g->block));
   uint8_t *q = (uint8_t *)g->block;
   g->codes = (uint64_t *)q; q += b_codes;
@@ -454,6 +464,7 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   g->slot_of_leaf = (int32_t *)q; q += b_l4;
   g->lut = (uint32_t *)q; q += b_lut;
   g->scene_begin = (uint32_t *)q; q += b_sb;
+  g->scene_leaf_begin = (uint32_t *)q; q += b_sb;
   g->scene_geom = (float *)q;
   if (sb) {
     PG_CUDA(cudaMemcpyAsync(g->scene_begin, sb->d_begin, 4ull * (S + 1), cudaMemcpyDefault, st));
@@ -554,16 +565,18 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of);
   k_leaf_lut<<<ceil_div(lut_cells, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * (D - g->lut_depth), lut_cells,
                                                       g->lut);
+  k_scene_leaves<<<ceil_div(S + 1, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * Dsp, S,
+                                                     S == (1u << (3 * SL)), g->scene_leaf_begin);
   PG_CUDA(cudaGetLastError());
 
-  uint32_t hc[2];
+  uint32_t hc[2], status = 0;
   PG_CUDA(cudaMemcpyAsync(hc, t.counters, 8, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
   PG_CUDA(cudaStreamSynchronize(st));
-  uint32_t status = 0;
-  PG_CUDA(cudaMemcpy(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost));
   if (status & ST_CAPACITY) return PG_ERR_UNSUPPORTED;
   if (status & ST_INVALID_INPUT) {
-    PG_CUDA(cudaMemset(ctx->d_status, 0, 4));
+    PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
+    PG_CUDA(cudaStreamSynchronize(st));
     return PG_ERR_INVALID_INPUT;
   }
   g->L = hc[0];

@@ -5,11 +5,45 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <new>
 
 #include "pg_internal.cuh"
 
+// Shared byte budget: charges are a compare-and-swap on in_use; releases
+// bump a generation counter and wake waiters.
+struct pg_budget {
+  uint64_t capacity;
+  std::atomic<uint64_t> in_use{0};
+  std::atomic<uint64_t> generation{0};
+  std::atomic<int> attached{0};
+  std::mutex mu;
+  std::condition_variable cv;
+};
+
 namespace pgi {
+
+bool budget_try_charge(pg_budget *b, size_t bytes) {
+  uint64_t cur = b->in_use.load(std::memory_order_relaxed);
+  do {
+    if (bytes > b->capacity || cur > b->capacity - bytes) return false;
+  } while (!b->in_use.compare_exchange_weak(cur, cur + bytes, std::memory_order_acq_rel));
+  return true;
+}
+
+void budget_release(pg_budget *b, size_t bytes) {
+  uint64_t cur = b->in_use.load(std::memory_order_relaxed);
+  while (!b->in_use.compare_exchange_weak(cur, cur >= bytes ? cur - bytes : 0, std::memory_order_acq_rel)) {
+  }
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->generation.fetch_add(1, std::memory_order_acq_rel);
+  }
+  b->cv.notify_all();
+}
 
 cudaError_t &last_cuda_error() {
   static thread_local cudaError_t e = cudaSuccess;
@@ -21,10 +55,12 @@ pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr) {
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~(size_t)255;
   if (ctx->budget && ctx->in_use + bytes > ctx->budget) return PG_ERR_OOM;
+  if (ctx->shared && !budget_try_charge(ctx->shared, bytes)) return PG_ERR_OOM;
   cudaError_t e = cudaMallocAsync(ptr, bytes, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *ptr = nullptr;
+    if (ctx->shared) budget_release(ctx->shared, bytes);
     return PG_ERR_OOM;
   }
   ctx->in_use += bytes;
@@ -37,6 +73,7 @@ void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   cudaFreeAsync(ptr, ctx->stream);
   ctx->in_use = ctx->in_use >= bytes ? ctx->in_use - bytes : 0;
+  if (ctx->shared) budget_release(ctx->shared, bytes);
 }
 
 // Boundary rays of the W phi sectors: (float cos, float sin) of 2 pi j / W,
@@ -195,6 +232,7 @@ pg_status pg_create(pg_ctx **out, void *stream, size_t budget) {
 pg_status pg_destroy(pg_ctx *c) {
   if (!c) return PG_OK;
   cudaStreamSynchronize(c->stream);
+  if (c->shared) pg_ctx_attach_budget(c, nullptr);
   for (int i = 0; i < 9; ++i)
     if (c->d_phi[i]) cudaFree(c->d_phi[i]);
   cudaFree(c->d_status);
@@ -210,10 +248,10 @@ pg_status pg_set_stream(pg_ctx *c, void *stream) {
 
 pg_status pg_sync(pg_ctx *c) {
   if (!c) return PG_ERR_INVALID_ARG;
-  PG_CUDA(cudaStreamSynchronize(c->stream));
   uint32_t st = 0;
-  PG_CUDA(cudaMemcpy(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
-  PG_CUDA(cudaMemset(c->d_status, 0, sizeof(uint32_t)));
+  PG_CUDA(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  PG_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
+  PG_CUDA(cudaStreamSynchronize(c->stream));
   if (st & ST_INVALID_INPUT) return PG_ERR_INVALID_INPUT;
   if (st & ST_OVERFLOW) return PG_ERR_OVERFLOW;
   if (st & ST_TIMEOUT) return PG_ERR_TIMEOUT;
@@ -224,6 +262,66 @@ pg_status pg_sync(pg_ctx *c) {
 pg_status pg_bytes_in_use(const pg_ctx *c, uint64_t *bytes) {
   if (!c || !bytes) return PG_ERR_INVALID_ARG;
   *bytes = c->in_use;
+  return PG_OK;
+}
+
+pg_status pg_budget_create(uint64_t capacity, pg_budget **out) {
+  if (!out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  pg_budget *b = new (std::nothrow) pg_budget();
+  if (!b) return PG_ERR_OOM;
+  b->capacity = capacity;
+  *out = b;
+  return PG_OK;
+}
+
+pg_status pg_budget_destroy(pg_budget *b) {
+  if (!b) return PG_OK;
+  if (b->attached.load() != 0) return PG_ERR_INVALID_ARG;
+  delete b;
+  return PG_OK;
+}
+
+pg_status pg_ctx_attach_budget(pg_ctx *c, pg_budget *b) {
+  if (!c) return PG_ERR_INVALID_ARG;
+  if (b == c->shared) return PG_OK;
+  if (b && !budget_try_charge(b, c->in_use)) return PG_ERR_OOM;
+  if (c->shared) {
+    budget_release(c->shared, c->in_use);
+    c->shared->attached.fetch_sub(1);
+  }
+  if (b) b->attached.fetch_add(1);
+  c->shared = b;
+  return PG_OK;
+}
+
+pg_status pg_budget_charge(pg_budget *b, uint64_t bytes) {
+  if (!b) return PG_ERR_INVALID_ARG;
+  return budget_try_charge(b, bytes) ? PG_OK : PG_ERR_OOM;
+}
+
+pg_status pg_budget_release(pg_budget *b, uint64_t bytes) {
+  if (!b) return PG_ERR_INVALID_ARG;
+  budget_release(b, bytes);
+  return PG_OK;
+}
+
+pg_status pg_budget_wait(pg_budget *b, uint64_t bytes, uint64_t *generation, uint32_t timeout_ms) {
+  if (!b || !generation) return PG_ERR_INVALID_ARG;
+  const uint64_t seen = *generation;
+  std::unique_lock<std::mutex> lk(b->mu);
+  bool ok = b->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+    return b->generation.load() != seen || b->in_use.load() + bytes <= b->capacity;
+  });
+  *generation = b->generation.load();
+  return ok ? PG_OK : PG_ERR_TIMEOUT;
+}
+
+pg_status pg_budget_query(const pg_budget *b, uint64_t *in_use, uint64_t *capacity, uint64_t *generation) {
+  if (!b) return PG_ERR_INVALID_ARG;
+  if (in_use) *in_use = b->in_use.load();
+  if (capacity) *capacity = b->capacity;
+  if (generation) *generation = b->generation.load();
   return PG_OK;
 }
 
@@ -270,7 +368,8 @@ pg_status pg_build_grid_batched(pg_ctx *c, const pg_photon *d_ph, uint64_t n, co
   // Scene offsets: checked on the host (non-decreasing, 0 .. n).
   uint32_t *hb = (uint32_t *)malloc(4ull * (S + 1));
   if (!hb) return PG_ERR_OOM;
-  if (cudaMemcpy(hb, d_scene_begin, 4ull * (S + 1), cudaMemcpyDefault) != cudaSuccess) {
+  if (cudaMemcpyAsync(hb, d_scene_begin, 4ull * (S + 1), cudaMemcpyDefault, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
     free(hb);
     cudaGetLastError();
     return PG_ERR_NOT_DEVICE_PTR;
@@ -703,6 +802,7 @@ pg_status pg_export(pg_ctx *c, const void *handle, int what, void *dst, size_t b
       case PG_GRID_LEAF_END: src = g->leaf_end; need = (size_t)g->L * 4; break;
       case PG_GRID_ACTIVE: src = g->active; need = (size_t)g->A * 4; break;
       case PG_GRID_SLOT_OF_LEAF: src = g->slot_of_leaf; need = (size_t)g->L * 4; break;
+      case PG_GRID_SCENE_LEAF_BEGIN: src = g->scene_leaf_begin; need = 4ull * (g->n_scenes + 1); break;
       default: return PG_ERR_INVALID_ARG;
     }
   } else if (b->kind == KIND_HIST) {

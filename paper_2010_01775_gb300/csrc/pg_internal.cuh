@@ -67,6 +67,7 @@ struct Grid {
   uint32_t n_scenes;
   int scene_levels;
   uint32_t *scene_begin;  // [S+1] photon offsets per scene
+  uint32_t *scene_leaf_begin;  // [S+1] first leaf per scene, L at S
   float *scene_geom;      // [S][6] lo[3], scale[3] per scene (batched grids)
   void *block;           // single allocation holding the arrays above
 };
@@ -139,6 +140,7 @@ struct pg_ctx {
   int device;
   cudaStream_t stream;
   size_t budget, in_use;
+  pg_budget *shared;   // optional budget shared with other contexts
   uint32_t *d_status;  // device status word (pgi::ST_* bits)
   float *d_phi[9];     // boundary-ray tables (cos, sin) per log2(W), W <= 256
 };
@@ -148,6 +150,8 @@ namespace pgi {
 // ---------------------------------------------------------------- memory
 pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr);
 void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes);
+bool budget_try_charge(pg_budget *b, size_t bytes);
+void budget_release(pg_budget *b, size_t bytes);
 // Device tables (cos, sin) of the W boundary rays, built once per W on the
 // host of the calling process and cached on the context.
 pg_status phi_table(pg_ctx *ctx, int W, const float **d_table);

@@ -41,11 +41,14 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
   const uint32_t b = leaf_begin[leaf], e = leaf_end[leaf];
   // "Previous iteration" photons: original index below n_prev, counted
   // within the leaf's scene for a scene batch.
+  // A scene of a batch has the overflow bound of the same scene alone,
+  // (2^63 - 1) / (its photon count).
   uint32_t prev_base = 0, prev_lim = n_prev;
   if (sc_nprev) {
     const uint32_t sc = (uint32_t)(leaf_code[leaf] >> sc_shift);
     prev_base = sc_begin[sc];
     prev_lim = sc_nprev[sc];
+    limit = (uint64_t)INT64_MAX / (uint64_t)(sc_begin[sc + 1] - prev_base);
   }
   const int tid = threadIdx.x, lane = tid & 31;
 

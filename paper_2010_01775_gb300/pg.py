@@ -23,6 +23,7 @@ PG_INFO_N_PHOTONS, PG_INFO_N_LEAVES, PG_INFO_N_ACTIVE, PG_INFO_H, PG_INFO_W, PG_
 PG_INFO_N_SCENES, PG_INFO_SCENE_LEVELS = 8, 9
 PG_GRID_CODES, PG_GRID_PERM, PG_GRID_LEAF_OF, PG_GRID_LEAF_CODE, PG_GRID_LEAF_DEPTH = 100, 101, 102, 103, 104
 PG_GRID_LEAF_BEGIN, PG_GRID_LEAF_END, PG_GRID_ACTIVE, PG_GRID_SLOT_OF_LEAF = 105, 106, 107, 108
+PG_GRID_SCENE_LEAF_BEGIN = 109
 PG_HIST_POW_CUR, PG_HIST_CNT_CUR, PG_HIST_POW_PREV, PG_HIST_CNT_PREV = 200, 201, 202, 203
 PG_MAP_Y = 300
 PG_TAB_P, PG_TAB_CDF_PHI, PG_TAB_CDF_Z, PG_TAB_VALID = 400, 401, 402, 403
@@ -35,7 +36,8 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_splat_photons", "pg_net_load", "pg_reconstruct", "pg_map_import", "pg_build_cdf",
             "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string",
             "pg_sort_photons_noalloc", "pg_autotune", "pg_build_grid_batched", "pg_splat_photons_batched",
-            "pg_sample_dirs_batched", "pg_eval_pdf_batched"]
+            "pg_sample_dirs_batched", "pg_eval_pdf_batched", "pg_budget_create", "pg_budget_destroy",
+            "pg_ctx_attach_budget", "pg_budget_charge", "pg_budget_release", "pg_budget_wait", "pg_budget_query"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -80,6 +82,10 @@ def load(path: str = LIB_PATH):
         "pg_splat_photons_batched": [P, P, P, u64, P, i32, i32, i32, PP],
         "pg_sample_dirs_batched": [P, P, P, P, P, u64, u64, P, P, P, P, P],
         "pg_eval_pdf_batched": [P, P, P, P, P, P, u64, P],
+        "pg_budget_create": [u64, PP], "pg_budget_destroy": [P], "pg_ctx_attach_budget": [P, P],
+        "pg_budget_charge": [P, u64], "pg_budget_release": [P, u64],
+        "pg_budget_wait": [P, u64, ctypes.POINTER(u64), u32],
+        "pg_budget_query": [P, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -181,6 +187,55 @@ class Context:
             self.destroy()
         except Exception:
             pass
+
+
+class Budget:
+    """A pg_budget: one HBM byte budget shared by several contexts."""
+
+    def __init__(self, capacity):
+        load()
+        p = ctypes.c_void_p()
+        _check(_lib.pg_budget_create(capacity, ctypes.byref(p)), "pg_budget_create")
+        self.ptr = p.value
+        self.capacity = capacity
+
+    def attach(self, ctx):
+        _check(_lib.pg_ctx_attach_budget(ctx.ptr, self.ptr), "pg_ctx_attach_budget")
+
+    @staticmethod
+    def detach(ctx):
+        _check(_lib.pg_ctx_attach_budget(ctx.ptr, None), "pg_ctx_attach_budget")
+
+    def charge(self, nbytes) -> bool:
+        """Charges nbytes if they fit; False (nothing charged) otherwise."""
+        st = _lib.pg_budget_charge(self.ptr, nbytes)
+        if st == 3:
+            return False
+        _check(st, "pg_budget_charge")
+        return True
+
+    def release(self, nbytes):
+        _check(_lib.pg_budget_release(self.ptr, nbytes), "pg_budget_release")
+
+    def query(self):
+        """(in_use, capacity, generation)."""
+        a, b, g = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(_lib.pg_budget_query(self.ptr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(g)), "pg_budget_query")
+        return a.value, b.value, g.value
+
+    def wait(self, nbytes, generation, timeout_ms) -> tuple:
+        """Blocks (GIL released) until nbytes fit or a release happened after
+        `generation`; returns (fits_or_released, new_generation)."""
+        g = ctypes.c_uint64(generation)
+        st = _lib.pg_budget_wait(self.ptr, nbytes, ctypes.byref(g), timeout_ms)
+        if st not in (0, 6):
+            _check(st, "pg_budget_wait")
+        return st == 0, g.value
+
+    def destroy(self):
+        if self.ptr:
+            _check(_lib.pg_budget_destroy(self.ptr), "pg_budget_destroy")
+            self.ptr = None
 
 
 def pg_create(stream=None, hbm_budget=0) -> Context:

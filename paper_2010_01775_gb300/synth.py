@@ -241,3 +241,110 @@ def workload_inputs(wl: Workload):
     dirs = query_directions(wl.n_queries, wl.seed)
     blob = net_blob(wl.arch, wl.widths, wl.seed + 77)
     return ph, pos, dirs, blob
+
+
+@dataclasses.dataclass(frozen=True)
+class BatchWorkload:
+    """Many independent scenes of uneven size processed as one batch."""
+
+    name: str
+    n_scenes: int
+    n_median: float
+    n_sigma: float
+    n_min: int
+    n_max: int
+    max_depth: int
+    split_threshold: int
+    H: int
+    W: int
+    arch: int
+    widths: tuple
+    n_queries: int
+    seed: int
+    min_depth: int = 0
+    frac_bits: int = 32
+
+
+BATCH64 = BatchWorkload(
+    "batch64: 64 scenes, photons per scene lognormal(ln 4e5, 1.5) clipped to [2e4, 8e6], depth 10, split 1000, "
+    "64x64, BF16 U-Net 32-64-128-256, 32M queries split by photon count",
+    64, 4e5, 1.5, 20_000, 8_000_000, 10, 1000, 64, 64, ARCH_UNET4, (32, 64, 128, 256), 33_554_432, SEED_BASE + 3)
+BATCH8 = dataclasses.replace(
+    BATCH64, name="batch8: 8 scenes, photons per scene lognormal(ln 1e5, 1.0) clipped to [2e4, 1e6], 2M queries",
+    n_scenes=8, n_median=1e5, n_sigma=1.0, n_max=1_000_000, n_queries=2_097_152, seed=SEED_BASE + 13)
+
+BATCH_WORKLOADS = {"batch64": BATCH64, "batch8": BATCH8}
+
+
+def batch_inputs(bw: BatchWorkload):
+    """Scene-grouped photons with offsets, scene-grouped query positions and
+    directions with offsets (queries split in proportion to photon counts),
+    and the network blob.  Every scene lives in [0, 1)^3."""
+    rng = np.random.Generator(np.random.PCG64(bw.seed))
+    sizes = np.clip(np.exp(rng.normal(np.log(bw.n_median), bw.n_sigma, bw.n_scenes)), bw.n_min, bw.n_max)
+    sizes = sizes.astype(np.int64)
+    phs = []
+    for s, n in enumerate(sizes):
+        blobs = int(np.clip(n // 62_500, 8, 64))
+        phs.append(photons(int(n), blobs, bw.seed * 1000 + s))
+    begin = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
+    q = np.floor(bw.n_queries * sizes / sizes.sum()).astype(np.int64)
+    q[0] += bw.n_queries - q.sum()
+    qbegin = np.concatenate([[0], np.cumsum(q)]).astype(np.uint32)
+    pos = query_positions(bw.n_queries, bw.seed)
+    dirs = query_directions(bw.n_queries, bw.seed)
+    blob = net_blob(bw.arch, bw.widths, bw.seed + 77)
+    return np.ascontiguousarray(np.concatenate(phs)), begin, pos, dirs, qbegin, blob
+
+
+@dataclasses.dataclass(frozen=True)
+class ServeTrace:
+    """A seeded open-loop request trace for the serving loop."""
+
+    name: str
+    rate: float  # Poisson arrivals per second
+    duration: float  # seconds of arrivals
+    n_min: int
+    n_max: int
+    q_min: int
+    q_max: int
+    sizes: tuple  # H = W choices
+    precisions: tuple  # cycled over requests
+    max_depth: int
+    split_threshold: int
+    seed: int
+
+
+SERVE = ServeTrace(
+    "serve: Poisson 200 req/s, photons log-uniform [1e4, 2e7], queries log-uniform [65536, 16777216], "
+    "H=W in {32, 64, 128}, split 2000, depth 10, BF16/FP8 alternating, U-Net 32-64-128-256",
+    200.0, 2.0, 10_000, 20_000_000, 65_536, 16_777_216, (32, 64, 128), ("bf16", "fp8"), 10, 2000, SEED_BASE + 4)
+SERVE_SMALL = dataclasses.replace(
+    SERVE, name="serve-small: Poisson 200 req/s, photons log-uniform [1e3, 1e5], queries log-uniform [1e3, 1e5], "
+    "H=W in {16, 32}", n_min=1_000, n_max=100_000, q_min=1_000, q_max=100_000, sizes=(16, 32), duration=0.2,
+    seed=SEED_BASE + 14)
+
+SERVE_TRACES = {"serve": SERVE, "serve-small": SERVE_SMALL}
+
+
+def serve_trace(tr: ServeTrace, rate: float | None = None, duration: float | None = None,
+                n_requests: int | None = None):
+    """Request descriptors: dicts with arrival (seconds from start), n, q,
+    H, W, precision, stream_id, q_offset (offset into a shared query pool of
+    q_max entries; a request's photons are the first n of a shared pool).
+    Exactly n_requests requests when given, else every arrival before
+    `duration`."""
+    rate = tr.rate if rate is None else rate
+    duration = tr.duration if duration is None else duration
+    rng = np.random.Generator(np.random.PCG64(tr.seed))
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if (n_requests is None and t >= duration) or (n_requests is not None and len(out) >= n_requests):
+            break
+        n = int(np.exp(rng.uniform(np.log(tr.n_min), np.log(tr.n_max))))
+        q = int(np.exp(rng.uniform(np.log(tr.q_min), np.log(tr.q_max))))
+        s = int(tr.sizes[rng.integers(len(tr.sizes))])
+        out.append(dict(arrival=t, n=n, q=q, H=s, W=s, precision=tr.precisions[len(out) % len(tr.precisions)],
+                        stream_id=len(out), q_offset=int(rng.integers(0, tr.q_max - q + 1))))
+    return out

@@ -82,7 +82,9 @@ def test_batched_grid_hist_maps_and_samples_match_single_scenes(ctx):
     shift = 3 * D
     mask = (1 << shift) - 1
     leaf0 = act0 = 0
+    scene_leaf0 = []
     for s in range(S):
+        scene_leaf0.append(leaf0)
         gs = pg.pg_build_grid(ctx, torch.from_numpy(phs[s]).cuda() if sizes[s] else 0, sizes[s], los[s], his[s],
                               D, 0, THR)
         G = pg.export_grid(gs)
@@ -127,6 +129,8 @@ def test_batched_grid_hist_maps_and_samples_match_single_scenes(ctx):
         act0 += A
     # Scene slots beyond S (8^SL > S) hold single empty leaves at the end.
     assert B["L"] == leaf0 + (8 ** SL - S)
+    lb = gb.export(pg.PG_GRID_SCENE_LEAF_BEGIN, np.uint32, S + 1)
+    assert lb.tolist() == scene_leaf0 + [leaf0]
     assert B["A"] == act0
 
 
@@ -141,3 +145,22 @@ def test_batched_argument_checks(ctx):
         pg.pg_build_grid_batched(ctx, d, 100, np.array([0, 50, 100], np.uint32), [[0, 0, 0]] * 2, [[1, 1, 1]] * 2,
                                  17, 0, 10)
     assert e.value.status in (1, 9)
+
+
+def test_batched_overflow_bound_is_per_scene(ctx):
+    # Two one-photon scenes of power 2^30: 2^62 in fixed point each, within
+    # (2^63-1)/1 for each scene alone, over (2^63-1)/2 for the two together.
+    ph = synth.photons(2, 1, 5)
+    ph[:, 6] = 2.0 ** 30
+    d = torch.from_numpy(ph).cuda()
+    begin = np.array([0, 1, 2], np.uint32)
+    g = pg.pg_build_grid_batched(ctx, d, 2, begin, [[0, 0, 0]] * 2, [[1, 1, 1]] * 2, 3, 0, 10)
+    h = pg.pg_splat_photons_batched(ctx, g, d, 2, np.zeros(2, np.uint32), 8, 8, 32)
+    ctx.sync()
+    hb = pg.export_hist(h)
+    assert hb["pow_cur"].sum(axis=1).tolist() == [1 << 62, 1 << 62]
+    g1 = pg.pg_build_grid(ctx, d, 2, [0, 0, 0], [1, 1, 1], 3, 0, 10)
+    pg.pg_splat_photons(ctx, g1, d, 2, 0, 8, 8, 32)
+    with pytest.raises(pg.PgError) as e:
+        ctx.sync()
+    assert e.value.status == 4

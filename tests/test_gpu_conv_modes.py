@@ -1,0 +1,69 @@
+"""Operand staging modes of the tensor-core convolutions.
+
+Modes 1 (three x-shifted haloed boxes) and 2 (one box of zero-padded rows,
+outputs in the padded row space, every tap a descriptor starting at another
+row of the same box) issue the same MMAs in the same K order (channel chunk,
+tap, K step) for every output pixel.  With the 3-layer net, whose one 3x3
+layer is eligible for both, the maps must be bit-identical.  In the U-Net
+the modes' eligibility differs per layer, and a layer that falls back to
+mode 0 sums its taps in another order, so there the maps agree to the
+accumulation order.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2010_01775_gb300 import pg, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+N = 300_000
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    c = pg.Context()
+    ph = torch.from_numpy(synth.photons(N, 16, 901)).cuda()
+    g = pg.pg_build_grid(c, ph, N, [0, 0, 0], [1, 1, 1], 8, 0, 4000)
+    yield c, ph, g
+    c.destroy()
+
+
+def _maps(ctx, net, h, prec, mode):
+    os.environ["PG_TC_FORCE"] = str(mode)
+    try:
+        m = pg.pg_reconstruct(ctx, h, net, prec)
+        ctx.sync()
+        return pg.export_map(m)
+    finally:
+        del os.environ["PG_TC_FORCE"]
+
+
+@pytest.mark.parametrize("size,prec", [(32, pg.PG_BF16), (64, pg.PG_BF16), (128, pg.PG_BF16),
+                                       (32, pg.PG_FP8_E4M3), (64, pg.PG_FP8_E4M3)])
+def test_padded_rows_equal_shifted_boxes_bit_for_bit(setup, size, prec):
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, size, size)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_TINY3, (32,), 902))
+    y1 = _maps(ctx, net, h, prec, 1)
+    y2 = _maps(ctx, net, h, prec, 2)
+    assert np.isfinite(y2).all() and (y2 >= 0).all()
+    assert np.array_equal(y1, y2)
+
+
+@pytest.mark.parametrize("size,prec", [(64, pg.PG_BF16), (128, pg.PG_BF16), (64, pg.PG_FP8_E4M3)])
+def test_unet_modes_agree(setup, size, prec):
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, size, size)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), 903))
+    y0 = _maps(ctx, net, h, prec, 0)
+    y1 = _maps(ctx, net, h, prec, 1)
+    y2 = _maps(ctx, net, h, prec, 2)
+    for y in (y1, y2):
+        assert np.abs(y - y0).sum() / np.abs(y0).sum() < 1e-3
