@@ -42,6 +42,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "conv.cuh"
@@ -50,7 +51,8 @@ namespace pgi {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // producer warp, MMA warp, 8 epilogue warps
+constexpr int kEpiWarps = 8;
 constexpr int kBM = 128;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
 
@@ -323,7 +325,7 @@ __device__ __forceinline__ void issue_stage(const StageOps &o) {
 }
 
 template <bool kFp8Out, bool kCalib>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);
+      mbar_init(&acc_empty[b], kEpiWarps);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -532,12 +534,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_wait(drain, 0, &never, 200000000ull);
     }
   } else {
-    // ---------------- epilogue: warps 2..5 own TMEM lane quarters 2,3,0,1
+    // ---------------- epilogue: warps 2..9; warp w reads TMEM lane quarter
+    // w % 4, and the two warps of a quarter split the tile's work items
+    // (subtile, column chunk) between them.
     const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     const int m = q * 32 + lane;
     int i = 0;
     const int reps = a.ups ? 2 : 1;
     const int Ho = a.Hout * reps, Wo = a.Wout * reps;
+    const int cw = (a.BN % 32 == 0 && a.mt * a.BN >= 64) ? 32 : 16;  // columns per work item
+    const int per_sub = a.BN / cw, items = a.mt * per_sub;
     float amax_local = 0.0f;
     long long epi_wait = 0;
     const long long epi_t0 = clock64();
@@ -555,7 +562,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       } else {
         tile_origin(a, t, l0, y0, x0);
       }
-      for (int sub = 0; sub < a.mt; ++sub) {
+      for (int it = h; it < items; it += 2) {
+      const int sub = it / per_sub, c = (it - sub * per_sub) * cw;
       const int mm = sub * kBM + m;
       int leaf, y, x;
       bool valid;
@@ -574,30 +582,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         x = x0 + xx;
         valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
       }
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN);
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN + c);
       const size_t pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
-      if (a.BN % 32 == 0) {
-        for (int c = 0; c < a.BN; c += 32) {
-          uint32_t r[32];
-          tmem_ld32(trow + (uint32_t)c, r);
-          if (!valid) continue;
+      if (cw == 32) {
+        uint32_t r[32];
+        tmem_ld32(trow, r);
+        if (valid) {
           epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
           epi16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, pix0, Wo, reps, amax_local);
         }
       } else {
-        for (int c = 0; c < a.BN; c += 16) {
-          uint32_t r[16];
-          tmem_ld16(trow + (uint32_t)c, r);
-          if (!valid) continue;
-          epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
-        }
+        uint32_t r[16];
+        tmem_ld16(trow, r);
+        if (valid) epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
       }
-      }  // subtiles
+      }  // work items
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
-    if (a.stats && lane == 0 && q == 2) {
+    if (a.stats && lane == 0 && warp == 2) {
       atomicAdd(&a.stats[5], (unsigned long long)epi_wait);
       atomicAdd(&a.stats[6], (unsigned long long)(clock64() - epi_t0));
       atomicAdd(&a.stats[7], (unsigned long long)i);
@@ -751,6 +755,21 @@ struct TcCfg {
 
 constexpr size_t kSmemPerSM = 228 * 1024;
 
+// CTAs per SM that the register file holds (65,536 registers per SM).
+int ctas_by_registers() {
+  static const int n = [] {
+    int regs = 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_conv_tc<false, false>) == cudaSuccess) regs = std::max(regs, fa.numRegs);
+    if (cudaFuncGetAttributes(&fa, k_conv_tc<false, true>) == cudaSuccess) regs = std::max(regs, fa.numRegs);
+    if (cudaFuncGetAttributes(&fa, k_conv_tc<true, false>) == cudaSuccess) regs = std::max(regs, fa.numRegs);
+    cudaGetLastError();
+    regs = (std::max(regs, 1) + 7) & ~7;
+    return std::max(1, 65536 / (regs * kThreads));
+  }();
+  return n;
+}
+
 pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStream_t st, uint32_t *status,
                     TcCfg cfg = TcCfg()) {
   EncodeTiledFn enc = encode_fn();
@@ -829,7 +848,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   // CTAs per SM: TMEM holds 512 columns per SM, and shared memory is sized
   // so that no more CTAs than that can be resident (a CTA that found no free
   // TMEM columns would wait inside tcgen05.alloc).
-  const int max_ctas = (int)std::min<uint32_t>(4, 512u / cols);
+  const int max_ctas = std::min((int)std::min<uint32_t>(4, 512u / cols), ctas_by_registers());
   int per_sm = cfg.ctas > 0 ? std::min(cfg.ctas, max_ctas) : std::min(2, max_ctas);
   const size_t stage_bytes = a.bytes_a + a.bytes_b;
   const size_t fixed = 1024 + 8 * 5 + 16 + 1024 + 1024;  // alignment, barriers, bias, per-CTA reserve
@@ -970,8 +989,16 @@ static pg_status make_lp_weights(pg_ctx *ctx, Layer &L, bool first, pg_precision
   return PG_OK;
 }
 
+// Serialises the one-time state changes of a net (reduced-precision weight
+// copies, FP8 activation calibration) between threads that share it.
+std::mutex &net_state_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
   if (!encode_fn()) return PG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(net_state_mutex());
   // Weight copies belong to the net, so they are charged to the context that
   // owns it (the one that frees them), whichever context runs the first call.
   ctx = net->h.ctx;
@@ -1165,6 +1192,7 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
   if (prec == PG_BF16)
     return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr, tune);
   if (prec != PG_FP8_E4M3) return PG_ERR_UNSUPPORTED;
+  std::unique_lock<std::mutex> lock(net_state_mutex());
   if (!net->act_calibrated) {
     // Delayed scaling: one BF16 pass over this chunk records the largest
     // |activation| of every group; scale = amax / 448 (E4M3's largest normal).
@@ -1188,6 +1216,7 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
     ctx_free(ctx, d_amax, 64);
     PG_TRY(s);
   }
+  lock.unlock();
   return forward_lp<__nv_fp8_e4m3>(ctx, net, true, x0, actv, ns, H, W, y, st, net->act_scale, nullptr, tune);
 }
 

@@ -239,25 +239,35 @@ class Executor:
         return b.charged
 
     def _retry(self, b: _Batch, fn, *args):
-        """Runs a library call, waiting for released memory on PG_ERR_OOM."""
+        """Runs a library call, waiting for released memory on PG_ERR_OOM.
+        Before giving its memory back the batch tries once more (memory may
+        have been released while it looked)."""
+        confirm = False
         while True:
-            gen = self.server.budget.query()[2]
             try:
                 return fn(*args)
             except pg.PgError as e:
                 if e.status != PG_ERR_OOM:
                     raise
-                self.server._wait_for_release(gen, self._t0, self.held(b))
+            v = self.server._wait_for_release(self._t0, self.held(b))
+            if v == "retry" or not confirm:
+                confirm = v != "retry"
+                continue
+            raise Evicted(final=v == "fail")
 
     def _charge(self, b: _Batch, nbytes):
         """Charges a new batch's buffers.  No new batch is admitted while a
         running one waits for memory (it has priority on what is released)."""
+        confirm = False
         while True:
-            gen = self.server.budget.query()[2]
             if not self.server._holder_waiting() and self.server.budget.charge(nbytes):
                 b.charged += nbytes
                 return
-            self.server._wait_for_release(gen, self._t0, self.held(b))
+            v = self.server._wait_for_release(self._t0, self.held(b))
+            if v == "retry" or not confirm:
+                confirm = v != "retry"
+                continue
+            raise Evicted(final=v == "fail")
 
     def close(self):
         pass
@@ -484,29 +494,37 @@ class Server:
         with self._lock:
             return any(h > 0 for k, (_, h) in self._stalled.items() if k != me)
 
-    def _wait_for_release(self, gen, t0, held) -> bool:
-        """After an allocation refusal: True once memory was released (retry).
-        When every busy worker is waiting, nothing will be released unless a
-        worker gives memory back: the youngest batch holding memory raises
-        Evicted; a worker that holds the only memory held (or none while no
-        one holds any) cannot fit its batch at all and raises Evicted(final)."""
+    def _wait_for_release(self, t0, held) -> str:
+        """After an allocation refusal: 'retry' once the bytes in use dropped
+        below what they were after the refusal (a failed call's own rollback
+        does not count, so two waiting workers cannot wake each other up
+        forever).  When every busy worker is waiting, nothing will be
+        released unless a worker gives memory back: the youngest batch holding
+        memory gets 'evict'; a worker that holds the only memory held (or none
+        while no one holds any) cannot fit its batch at all and gets 'fail'."""
         me = threading.get_ident()
+        used0, cap, gen = self.budget.query()
+        need = max(1, min(cap - used0 + 1, 1 << 63))  # fits iff in_use < used0
         with self._lock:
             self._stalled[me] = (t0, held)
         try:
             while True:
-                # Asking for more than the capacity: wakes on a release only.
-                ok, gen = self.budget.wait(min(self.budget.capacity + 1, 1 << 63), gen, self.stall_ms)
-                if ok:
-                    return True
+                end = time.monotonic() + self.stall_ms / 1000.0
+                while True:
+                    left = end - time.monotonic()
+                    if left <= 0:
+                        break
+                    _, gen = self.budget.wait(need, gen, max(1, int(left * 1000)))
+                    if self.budget.query()[0] < used0:
+                        return "retry"
                 with self._lock:
                     if self._busy - len(self._stalled) > 0:
                         continue
                     holders = [t for t, h in self._stalled.values() if h > 0]
                     if (held > 0 and len(holders) == 1) or not holders:
-                        raise Evicted(final=True)
+                        return "fail"
                     if held > 0 and t0 >= max(holders):
-                        raise Evicted(final=False)
+                        return "evict"
         finally:
             with self._lock:
                 del self._stalled[me]
@@ -569,7 +587,8 @@ def latency_summary(reqs) -> dict:
         return dict(done=0)
     t0 = min(r.arrival for r in reqs)
     t1 = max(r.t_done for r in done)
-    return dict(done=len(done), failed=sum(r.status == "failed" for r in reqs),
+    errors = sorted({f"{r.error_status}: {r.error}" for r in reqs if r.status == "failed"})[:4]
+    return dict(done=len(done), failed=sum(r.status == "failed" for r in reqs), errors=errors,
                 cancelled=sum(r.status == "cancelled" for r in reqs), p50_ms=float(np.percentile(lat, 50)),
                 p90_ms=float(np.percentile(lat, 90)), p99_ms=float(np.percentile(lat, 99)), max_ms=float(lat.max()),
                 makespan_s=t1 - t0, requests_per_s=len(done) / (t1 - t0),

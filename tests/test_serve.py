@@ -124,7 +124,13 @@ class FakeExecutor(serve.Executor):
         self.server = server
 
     def _fake_call(self, b, nbytes):
-        if not self.server.budget.charge(nbytes):
+        # Like a library call that allocates its output, then its scratch,
+        # and on refusal gives the output back before returning PG_ERR_OOM.
+        half = nbytes // 2
+        if not self.server.budget.charge(half):
+            raise pg.PgError(3, "fake")
+        if not self.server.budget.charge(nbytes - half):
+            self.server.budget.release(half)
             raise pg.PgError(3, "fake")
         b.charged += nbytes
 
