@@ -146,9 +146,13 @@ def run_pg(args, wl, prec):
     # Launch shapes of the tensor-core convolutions are tuned once, untimed.
     g0 = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
     h0 = pg.pg_splat_photons(ctx, g0, d_ph, n, wl.n_prev, H, W, wl.frac_bits)
-    if args.autotune:
+    if args.load_tuning:
+        pg.pg_net_set_tuning(net, np.load(args.load_tuning))
+    elif args.autotune:
         for pr in {prec} | ({pg.PG_BF16, pg.PG_FP8_E4M3} if args.sweep else set()):
             pg.pg_autotune(ctx, h0, net, pr)
+    if args.save_tuning:
+        np.save(args.save_tuning, pg.pg_net_get_tuning(net))
     ctx.sync()
 
     def measure(pr, steps, warmup, clocks_on=False):
@@ -159,6 +163,7 @@ def run_pg(args, wl, prec):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         clocks = Clocks(local) if clocks_on else None
+        launches0 = ctx.launch_count()
         times, stage = [], np.zeros(6)
         for _ in range(steps):
             flush.zero_()
@@ -169,6 +174,7 @@ def run_pg(args, wl, prec):
             stage += [marks[i].elapsed_time(marks[i + 1]) for i in range(6)]
         ctx.sync()
         torch.cuda.synchronize()
+        launches = (ctx.launch_count() - launches0) // steps
         clk = clocks.stop() if clocks is not None else None
         total_ms = float(sum(times))
         if world > 1:
@@ -177,7 +183,7 @@ def run_pg(args, wl, prec):
             total_ms = float(t.item())
             torch.distributed.barrier()
         stage_ms = dict(zip(["grid", "splat", "cnn", "cdf", "sample", "eval"], (stage / steps).round(4).tolist()))
-        return dict(A=A, L=L, times=times, total_ms=total_ms, stage_ms=stage_ms, clocks=clk)
+        return dict(A=A, L=L, times=times, total_ms=total_ms, stage_ms=stage_ms, clocks=clk, launches=launches)
 
     main = measure(prec, args.steps, args.warmup, clocks_on=True)
     A, L, total_ms, stage_ms = main["A"], main["L"], main["total_ms"], main["stage_ms"]
@@ -271,7 +277,7 @@ def run_pg(args, wl, prec):
                            "p99": float(np.percentile(main["times"], 99))},
             "e2e": {"value": q / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": count_launches(wl, A, prec),
+            "gpu_launches": main["launches"],
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                          "traffic": None, "kernel": "CNN convolutions (all layers of one reconstruct call)",
                          "peak_source": ("of " + peak_src) if prec != pg.PG_FP32 else
@@ -340,6 +346,7 @@ def run_batch(args, bw, prec):
     ctx.sync()
     # Eager steps: grid + post, events around each part.
     eager, grid_ms = [], []
+    launches0 = ctx.launch_count()
     for _ in range(args.steps):
         e0, e1, e2 = ev(), ev(), ev()
         e0.record(stream)
@@ -351,6 +358,7 @@ def run_batch(args, bw, prec):
         grid_ms.append(e0.elapsed_time(e1))
         eager.append(e0.elapsed_time(e2))
         g2.free()
+    launches = (ctx.launch_count() - launches0) // args.steps
     # CUDA graph of the post-grid pipeline (allocations become graph memory nodes).
     graph = torch.cuda.CUDAGraph()
     ctx.sync()
@@ -377,7 +385,7 @@ def run_batch(args, bw, prec):
                    "scene_photons_min_max": [int(np.min(np.diff(begin))), int(np.max(np.diff(begin)))]},
         "leaf_tables_per_s": A / (graph_ms / 1e3),
         "eager_ms_per_step": eager_ms, "graph_ms_per_step": graph_ms, "grid_ms": statistics.median(grid_ms),
-        "graph_replay_ms": statistics.median(replays),
+        "graph_replay_ms": statistics.median(replays), "gpu_launches": launches,
     }
     graph.reset()
     g.free()
@@ -474,21 +482,6 @@ def run_serve(args, tr):
     print(json.dumps(out), flush=True)
 
 
-def count_launches(wl, A, prec):
-    """Kernel launches of one step (host-side count of the library's launch
-    sequence for this workload)."""
-    passes = (3 * wl.max_depth + 7) // 8
-    levels = wl.max_depth - wl.min_depth + 1
-    grid = 1 + 3 * passes + 1 + 3 * levels + 1 + 1 + 1
-    splat = 1 if wl.H * wl.W <= 8192 else 2
-    convs = 3 if wl.arch == 0 else 15
-    HW = wl.H * wl.W
-    per_leaf = 8 * HW * 4 + (4 if prec == 0 else 2) * HW * (200 if wl.arch else 40)
-    chunks = -(-A // max(1, min(A, (6 << 30) // per_leaf)))
-    cnn = chunks * (1 + convs + (0 if prec == 0 else 1))
-    return grid + splat + cnn + 1 + 1 + 1
-
-
 def oracle_sample_run(wl, n_leaves, n_queries, check=None):
     """The FP64 oracle on a bounded sample; returns per-stage seconds and the
     throughput extrapolated to the full workload."""
@@ -572,8 +565,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pg", choices=["pg", "reference"])
     ap.add_argument("--workload", default="scale")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--save-tuning", default=None, help="write the autotuned launch shapes (.npy)")
+    ap.add_argument("--load-tuning", default=None, help="use launch shapes from --save-tuning instead of tuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving trace: seconds of arrivals")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-closed", type=int, default=64, help="requests in the closed-loop capacity run")

@@ -94,6 +94,10 @@ pg_status pg_set_stream(pg_ctx *ctx, void *cuda_stream);
 pg_status pg_sync(pg_ctx *ctx);
 /* Bytes currently charged to the context's budget. */
 pg_status pg_bytes_in_use(const pg_ctx *ctx, uint64_t *bytes);
+/* Kernels the library has launched for this context so far (autotuning
+ * candidates excluded); the difference across a region is the number of
+ * kernel launches that region made. */
+pg_status pg_launch_count(const pg_ctx *ctx, uint64_t *launches);
 
 /* ---- shared HBM budget (serving) ----------------------------------------
  * One byte budget shared by several contexts, e.g. one context per serving
@@ -183,6 +187,15 @@ pg_status pg_reconstruct(pg_ctx *ctx, const pg_hist *hist, const pg_net *net,
  * (used by later pg_reconstruct calls with maps of the same size).  A no-op
  * for PG_FP32.  Synchronous; results of the timing runs are discarded. */
 pg_status pg_autotune(pg_ctx *ctx, const pg_hist *hist, pg_net *net, pg_precision precision);
+/* The launch shapes pg_autotune chose for a net (7 int32 per layer and
+ * precision: CTAs per SM, stages, 128-row subtiles, operand staging mode,
+ * chunk bytes, map bins tuned for, staged output stores), so that another
+ * process can load them with pg_net_set_tuning instead of tuning again.
+ * pg_net_get_tuning writes *needed (the count) and, when out != NULL and
+ * n >= *needed, the values; pg_net_set_tuning checks the count and ranges
+ * (PG_ERR_INVALID_ARG). */
+pg_status pg_net_get_tuning(const pg_net *net, int32_t *out, size_t n, size_t *needed);
+pg_status pg_net_set_tuning(pg_net *net, const int32_t *in, size_t n);
 
 /* Wraps caller-provided maps y [n_maps][H][W] (float32, >= 0) as a pg_map
  * (copied), so tables can be built from maps computed elsewhere. */

@@ -189,10 +189,10 @@ pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t) {
   const unsigned A = m->A;
   cudaStream_t st = ctx->stream;
   switch (m->W >= 32 ? m->W / 32 : 1) {
-    case 1: k_cdf<1><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid); break;
-    case 2: k_cdf<2><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid); break;
-    case 4: k_cdf<4><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid); break;
-    case 8: k_cdf<8><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid); break;
+    case 1: k_cdf<1><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
+    case 2: k_cdf<2><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
+    case 4: k_cdf<4><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
+    case 8: k_cdf<8><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
     default: return PG_ERR_UNSUPPORTED;
   }
   PG_CUDA(cudaGetLastError());

@@ -250,30 +250,30 @@ __global__ void k_conv_cout1(ConvArgs a) {
 }
 
 template <int BM, int BN, int TN>
-void launch_f32(const ConvArgs &a, cudaStream_t st) {
+void launch_f32(pg_ctx *ctx, const ConvArgs &a, cudaStream_t st) {
   dim3 grid((unsigned)((a.M + BM - 1) / BM), (unsigned)((a.Cout + BN - 1) / BN));
-  k_conv_f32<BM, BN, TN><<<grid, 256, 0, st>>>(a);
+  k_conv_f32<BM, BN, TN><<<grid, 256, 0, st>>>(a), PG_COUNT(ctx);
 }
 
 }  // namespace
 
-pg_status conv_f32(const ConvArgs &a, cudaStream_t st) {
+pg_status conv_f32(pg_ctx *ctx, const ConvArgs &a, cudaStream_t st) {
   if (a.M == 0) return PG_OK;
   // Channel counts must be multiples of 4 (16-byte vector access).
   if (a.Cin % 4 || a.in_cs % 4 || a.in_co % 4 || (a.Cout != 1 && (a.Cout % 4 || a.out_cs % 4 || a.out_co % 4)))
     return PG_ERR_UNSUPPORTED;
   if (a.Cout == 1) {
-    k_conv_cout1<<<ceil_div(a.M, 256), 256, 0, st>>>(a);
+    k_conv_cout1<<<ceil_div(a.M, 256), 256, 0, st>>>(a), PG_COUNT(ctx);
   } else if (a.Cout >= 128) {
-    launch_f32<128, 128, 8>(a, st);
+    launch_f32<128, 128, 8>(ctx, a, st);
   } else if (a.Cout > 32) {
-    launch_f32<256, 64, 8>(a, st);
+    launch_f32<256, 64, 8>(ctx, a, st);
   } else if (a.Cout > 16) {
-    launch_f32<256, 32, 4>(a, st);
+    launch_f32<256, 32, 4>(ctx, a, st);
   } else if (a.Cout > 8) {
-    launch_f32<256, 16, 2>(a, st);
+    launch_f32<256, 16, 2>(ctx, a, st);
   } else {
-    launch_f32<256, 8, 1>(a, st);
+    launch_f32<256, 8, 1>(ctx, a, st);
   }
   PG_CUDA(cudaGetLastError());
   return PG_OK;
@@ -312,11 +312,11 @@ pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision p
     float *x0 = (float *)scratch;  // FP32 input, 8 channels
     size_t nx = (size_t)ns * HW;
     k_assemble<<<ceil_div(nx, 256), 256, 0, st>>>(h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur,
-                                                  h->tot_prev, s0, ns, HW, x0);
+                                                  h->tot_prev, s0, ns, HW, x0), PG_COUNT(ctx);
     PG_CUDA(cudaGetLastError());
     uint8_t *act = (uint8_t *)scratch + align256(nx * 8 * 4);
     float *y = m->y + (size_t)s0 * HW;
-    if (prec == PG_FP32) PG_TRY(forward_f32(net, x0, act, ns, H, W, y, st));
+    if (prec == PG_FP32) PG_TRY(forward_f32(ctx, net, x0, act, ns, H, W, y, st));
     else PG_TRY(forward_tc(ctx, net, prec, x0, act, ns, H, W, y, st, tune));
     if (tune) break;  // the first chunk is representative of every later one
   }
@@ -324,7 +324,7 @@ pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision p
 }
 
 // Plain FP32 forward of one chunk: activations carved from `act`.
-pg_status forward_f32(const Net *net, const float *x0, void *actv, uint32_t ns, int H, int W, float *y,
+pg_status forward_f32(pg_ctx *ctx, const Net *net, const float *x0, void *actv, uint32_t ns, int H, int W, float *y,
                       cudaStream_t st) {
   float *act = (float *)actv;
   const Layer *Ls = net->layers;
@@ -338,7 +338,7 @@ pg_status forward_f32(const Net *net, const float *x0, void *actv, uint32_t ns, 
     a.k = L.k; a.stride = L.stride; a.pad = L.k / 2;
     a.w = L.w; a.bias = L.b; a.act = L.act; a.ups = ups;
     a.M = (long)ns * a.Hout * a.Wout;
-    return conv_f32(a, st);
+    return conv_f32(ctx, a, st);
   };
   const size_t HW = (size_t)H * W;
   if (net->arch == 0) {

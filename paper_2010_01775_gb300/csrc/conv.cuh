@@ -24,8 +24,8 @@ struct ConvArgs {
   int ups;
 };
 
-pg_status conv_f32(const ConvArgs &a, cudaStream_t st);
-pg_status forward_f32(const Net *net, const float *x0, void *act, uint32_t ns, int H, int W, float *y,
+pg_status conv_f32(pg_ctx *ctx, const ConvArgs &a, cudaStream_t st);
+pg_status forward_f32(pg_ctx *ctx, const Net *net, const float *x0, void *act, uint32_t ns, int H, int W, float *y,
                       cudaStream_t st);
 // Tensor-core (tcgen05) forms.
 pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec);

@@ -71,6 +71,7 @@ struct TcArgs {
   uint32_t bytes_a, bytes_b;  // per stage (A rounded up to 1 KB in mode 2)
   uint32_t tx_bytes;          // bytes the TMA copies of one stage deliver
   int chunk_bytes;            // bytes of one operand row (the swizzle row)
+  int stage_out;              // epilogue stores staged through shared memory (coalesced)
   uint32_t idesc;
   uint32_t sbo;
   int swz;
@@ -85,6 +86,10 @@ struct TcArgs {
   uint32_t *status;
   unsigned int *amax;  // optional: running max |output| (float bits) for FP8 calibration
   unsigned long long *stats;  // optional: per-role cycle counters (diagnostics)
+  // Optional fused 1x1 head (Cout 1) + softplus: the epilogue writes the FP32
+  // map y instead of the layer's activations.
+  const float *head_w, *head_b;
+  float *head_y;
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -213,11 +218,11 @@ __device__ __forceinline__ void tile_origin(const TcArgs &a, int t, int &l0, int
 // (its ~1e-7 absolute error is far below a BF16 or E4M3 output's rounding).
 __device__ __forceinline__ float elu_lp(float v) { return v > 0.0f ? v : __expf(v) - 1.0f; }
 
-// Bias + activation + conversion of 16 accumulator columns of one pixel and
-// their stores (four of them when the output is upsampled x2).
+// Bias + activation + conversion of 16 accumulator columns of one pixel into
+// output bytes: one 16-byte chunk (E4M3) or two (BF16).
 template <bool kFp8Out, bool kCalib>
-__device__ __forceinline__ void epi16(const TcArgs &a, const uint32_t *r, const float *s_bias, int c, size_t pix0,
-                                      int Wo, int reps, float &amax) {
+__device__ __forceinline__ void epi_convert16(const TcArgs &a, const uint32_t *r, const float *s_bias, int c,
+                                              float &amax, uint4 *chunk) {
   float v[16];
 #pragma unroll
   for (int j = 0; j < 16; j += 4) {
@@ -235,7 +240,6 @@ __device__ __forceinline__ void epi16(const TcArgs &a, const uint32_t *r, const 
 #pragma unroll
     for (int j = 0; j < 16; ++j) amax = fmaxf(amax, fabsf(v[j]));
   }
-  uint4 w0, w1;
   if (kFp8Out) {
     uint32_t w[4];
 #pragma unroll
@@ -244,7 +248,7 @@ __device__ __forceinline__ void epi16(const TcArgs &a, const uint32_t *r, const 
                                     v[4 * j + 3] * a.out_mul));
       w[j] = *reinterpret_cast<uint32_t *>(&p);
     }
-    w0 = make_uint4(w[0], w[1], w[2], w[3]);
+    chunk[0] = make_uint4(w[0], w[1], w[2], w[3]);
   } else {
     uint32_t w[8];
 #pragma unroll
@@ -252,20 +256,60 @@ __device__ __forceinline__ void epi16(const TcArgs &a, const uint32_t *r, const 
       __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
       w[j] = *reinterpret_cast<uint32_t *>(&p);
     }
-    w0 = make_uint4(w[0], w[1], w[2], w[3]);
-    w1 = make_uint4(w[4], w[5], w[6], w[7]);
+    chunk[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    chunk[1] = make_uint4(w[4], w[5], w[6], w[7]);
   }
+}
+
+// Direct output of one work item: each lane stores its own pixel's chunks.
+__device__ __forceinline__ void store_direct(const TcArgs &a, const uint4 *chunk, int cpp, int c0, size_t pix0,
+                                             int Wo, int reps, int es) {
+  uint8_t *out = (uint8_t *)a.out;
   for (int dy = 0; dy < reps; ++dy)
     for (int dx = 0; dx < reps; ++dx) {
       const size_t pix = pix0 + (size_t)dy * Wo + dx;
-      if (kFp8Out) {
-        *reinterpret_cast<uint4 *>((uint8_t *)a.out + pix * a.out_cs + a.out_co + c) = w0;
-      } else {
-        uint4 *o = reinterpret_cast<uint4 *>((__nv_bfloat16 *)a.out + pix * a.out_cs + a.out_co + c);
-        o[0] = w0;
-        o[1] = w1;
-      }
+      uint4 *o = reinterpret_cast<uint4 *>(out + (pix * a.out_cs + a.out_co + c0) * es);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < cpp) o[k] = chunk[k];
     }
+}
+
+// Coalesced output of one work item: every lane holds `cpp` 16-byte chunks
+// of its own pixel (channels c0.. of the layer's output).  The chunks go
+// through a per-warp staging buffer (chunk slots XOR-swizzled by pixel so
+// that neither side conflicts on banks) and leave as runs of 16 * cpp
+// contiguous bytes per pixel, 32 / cpp pixels per store instruction,
+// instead of one scattered 16-byte store per lane.
+__device__ __forceinline__ void store_staged(const TcArgs &a, uint8_t *stg, const uint4 *chunk, int cpp, int c0,
+                                             size_t pix0, bool valid, int Wo, int reps, int lane, int es) {
+  const int sh = cpp == 4 ? 1 : 2;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k < cpp) {
+      const int slot = k ^ ((lane >> sh) & (cpp - 1));
+      *reinterpret_cast<uint4 *>(stg + (lane * cpp + slot) * 16) = chunk[k];
+    }
+  __syncwarp();
+  const int ppi = 32 / cpp;  // pixels per store instruction
+  const int c = lane & (cpp - 1);
+  uint8_t *out = (uint8_t *)a.out;
+  for (int it = 0; it < cpp; ++it) {
+    const int p = it * ppi + lane / cpp;
+    const uint32_t lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)pix0, p);
+    const uint32_t hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(pix0 >> 32), p);
+    const int ok = __shfl_sync(0xFFFFFFFFu, valid ? 1 : 0, p);
+    const uint4 v = *reinterpret_cast<const uint4 *>(stg + (p * cpp + (c ^ ((p >> sh) & (cpp - 1)))) * 16);
+    if (ok) {
+      const size_t px = ((size_t)hi << 32) | lo;
+      for (int dy = 0; dy < reps; ++dy)
+        for (int dx = 0; dx < reps; ++dx) {
+          const size_t pix = px + (size_t)dy * Wo + dx;
+          *reinterpret_cast<uint4 *>(out + (pix * a.out_cs + a.out_co + c0) * es + c * 16) = v;
+        }
+    }
+  }
+  __syncwarp();
 }
 
 // Descriptor words and offsets of one pipeline stage (see the MMA issuer).
@@ -274,50 +318,44 @@ struct StageOps {
   int off0, P;
   uint32_t cb, sub_step, row_step, ver16, tap_b16, desc_hi, idesc;
   bool first;
+  int sub;  // the 128-row subtile (and accumulator) this issuing lane owns
 };
 
-// The MMAs of one stage as straight-line code: a tcgen05.mma stream issued
-// from a loop with run-time trip counts runs about 3x slower per
-// instruction than the same stream unrolled, so every (mode, subtiles,
-// K steps) combination gets its own fully unrolled sequence.  For each
-// accumulator the K order is (tap, K step), as in the loop form.
-template <bool kFp8, int kMode, int kMT, int kMPS>
+// The MMAs of one stage for one subtile, as straight-line code: a
+// tcgen05.mma stream issued from a loop with run-time trip counts runs about
+// 3x slower per instruction than the same stream unrolled, so every (mode,
+// K steps) combination gets its own fully unrolled sequence.  The K order of
+// an accumulator is (tap, K step) in every mode.
+template <bool kFp8, int kMode, int kMPS>
 __device__ __forceinline__ void issue_stage(const StageOps &o) {
+  const uint32_t d = o.d + (uint32_t)o.sub * o.BN;
   if constexpr (kMode == 0) {
+    const uint32_t a0 = o.alo + (uint32_t)o.sub * o.sub_step;
 #pragma unroll
-    for (int j = 0; j < kMPS; ++j) {
-      const uint32_t acc = (o.first && j == 0) ? 0u : 1u;
-#pragma unroll
-      for (int sub = 0; sub < kMT; ++sub)
-        mma_issue<kFp8>(o.d + (uint32_t)sub * o.BN, o.alo + (uint32_t)sub * o.sub_step + 2u * j, o.desc_hi,
-                        o.blo + 2u * j, o.desc_hi, o.idesc, acc);
-    }
+    for (int j = 0; j < kMPS; ++j)
+      mma_issue<kFp8>(d, a0 + 2u * j, o.desc_hi, o.blo + 2u * j, o.desc_hi, o.idesc, (o.first && j == 0) ? 0u : 1u);
   } else {
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky) {
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx) {
         const uint32_t b_tap = o.blo + (uint32_t)(ky * 3 + kx) * o.tap_b16;
+        uint32_t a_tap;
+        if constexpr (kMode == 1) {
+          // Copy kx of the haloed tile, from row ky * Wt on.
+          a_tap = o.alo + (uint32_t)kx * o.ver16 + (uint32_t)ky * o.row_step + (uint32_t)o.sub * o.sub_step;
+        } else {
+          // Padded row off0 + ky * P + kx of the box.  Any starting row
+          // works: the MMA, like the TMA that wrote the box, applies the
+          // swizzle to absolute shared-memory address bits of the
+          // 1-KB-aligned buffer (base offset 0).
+          const uint32_t addr = o.a_byte0 + ((uint32_t)(o.off0 + ky * o.P + kx) + (uint32_t)(o.sub * kBM)) * o.cb;
+          a_tap = ((addr & 0x3FFFFu) >> 4) | (1u << 16);
+        }
 #pragma unroll
-        for (int sub = 0; sub < kMT; ++sub) {
-          uint32_t a_tap;
-          if constexpr (kMode == 1) {
-            // Copy kx of the haloed tile, from row ky * Wt on.
-            a_tap = o.alo + (uint32_t)kx * o.ver16 + (uint32_t)ky * o.row_step + (uint32_t)sub * o.sub_step;
-          } else {
-            // Padded row off0 + ky * P + kx of the box.  Any starting row
-            // works: the MMA, like the TMA that wrote the box, applies the
-            // swizzle to absolute shared-memory address bits of the
-            // 1-KB-aligned buffer (base offset 0).
-            const uint32_t addr = o.a_byte0 + ((uint32_t)(o.off0 + ky * o.P + kx) + (uint32_t)(sub * kBM)) * o.cb;
-            a_tap = ((addr & 0x3FFFFu) >> 4) | (1u << 16);
-          }
-#pragma unroll
-          for (int j = 0; j < kMPS; ++j) {
-            const uint32_t acc = (o.first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
-            mma_issue<kFp8>(o.d + (uint32_t)sub * o.BN, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi,
-                            o.idesc, acc);
-          }
+        for (int j = 0; j < kMPS; ++j) {
+          const uint32_t acc = (o.first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
+          mma_issue<kFp8>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi, o.idesc, acc);
         }
       }
     }
@@ -339,19 +377,25 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
   float *s_bias = reinterpret_cast<float *>(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // BN floats
+  float *s_head = s_bias + a.BN;                                                                   // BN + 1 floats
+  uint8_t *s_stage = reinterpret_cast<uint8_t *>(((uintptr_t)(s_head + a.BN + 1) + 15) & ~(uintptr_t)15);  // 8 x 2 KB
   for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_bias[k] = a.bias[k];
+  if (a.head_y) {
+    for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_head[k] = a.head_w[k];
+    if (threadIdx.x == 0) s_head[a.BN] = a.head_b[0];
+  }
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < a.stages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], a.mt);  // one commit per issuing lane
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_full[b], a.mt);
       mbar_init(&acc_empty[b], kEpiWarps);
     }
-    mbar_init(drain, 1);
+    mbar_init(drain, a.mt);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
@@ -456,8 +500,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
+    if (lane < a.mt) {
+      // ---------------- MMA issuers: lane s issues subtile s (the converged
+      // lanes issue their MMAs together).
       int stage = 0;
       uint32_t phase = 0;
       int i = 0;
@@ -501,16 +546,13 @@ __global__ void __launch_bounds__(kThreads, 2)
           const bool first = ki == 0;
           const StageOps so{d,         (uint32_t)a.BN, alo_s,        blo_s,   a_base + (uint32_t)stage * a.bytes_a,
                             off0,      a.P,            (uint32_t)a.chunk_bytes, sub_step, row_step, ver16, tap_b16,
-                            desc_hi,   a.idesc,        first};
-          switch (a.halo * 16 + a.mt * 4 + (a.mma_per_stage >> 1)) {
-#define PG_STAGE_CASE(H, MT, MPS) \
-  case H * 16 + MT * 4 + (MPS >> 1): issue_stage<kFp8Out, H, MT, MPS>(so); break;
-            PG_STAGE_CASE(0, 1, 1) PG_STAGE_CASE(0, 1, 2) PG_STAGE_CASE(0, 1, 4)
-            PG_STAGE_CASE(0, 2, 1) PG_STAGE_CASE(0, 2, 2) PG_STAGE_CASE(0, 2, 4)
-            PG_STAGE_CASE(1, 1, 1) PG_STAGE_CASE(1, 1, 2) PG_STAGE_CASE(1, 1, 4)
-            PG_STAGE_CASE(1, 2, 1) PG_STAGE_CASE(1, 2, 2) PG_STAGE_CASE(1, 2, 4)
-            PG_STAGE_CASE(2, 1, 1) PG_STAGE_CASE(2, 1, 2) PG_STAGE_CASE(2, 1, 4)
-            PG_STAGE_CASE(2, 2, 1) PG_STAGE_CASE(2, 2, 2) PG_STAGE_CASE(2, 2, 4)
+                            desc_hi,   a.idesc,        first,   lane};
+          switch (a.halo * 4 + (a.mma_per_stage >> 1)) {
+#define PG_STAGE_CASE(H, MPS) \
+  case H * 4 + (MPS >> 1): issue_stage<kFp8Out, H, MPS>(so); break;
+            PG_STAGE_CASE(0, 1) PG_STAGE_CASE(0, 2) PG_STAGE_CASE(0, 4)
+            PG_STAGE_CASE(1, 1) PG_STAGE_CASE(1, 2) PG_STAGE_CASE(1, 4)
+            PG_STAGE_CASE(2, 1) PG_STAGE_CASE(2, 2) PG_STAGE_CASE(2, 4)
 #undef PG_STAGE_CASE
             default: break;
           }
@@ -523,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (!ok) break;
         mma_commit(&acc_full[buf]);
       }
-      if (a.stats) {
+      if (a.stats && lane == 0) {
         atomicAdd(&a.stats[2], (unsigned long long)mma_wait_acc);
         atomicAdd(&a.stats[3], (unsigned long long)mma_wait_full);
         atomicAdd(&a.stats[4], (unsigned long long)(clock64() - mma_t0));
@@ -562,6 +604,49 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else {
         tile_origin(a, t, l0, y0, x0);
       }
+      if (a.head_y) {
+        // Fused head: each thread owns whole pixels (all BN channels), so
+        // the two warps of a lane quarter take alternate subtiles.
+        for (int sub = h; sub < a.mt; sub += 2) {
+          const int qq = q0 + sub * kBM + m;
+          int leaf, y, x;
+          bool valid;
+          if (a.halo == 2) {
+            leaf = l0;
+            y = qq / a.P;
+            x = qq - y * a.P;
+            valid = y < a.Hout && x < a.Wout;
+          } else {
+            const int mm = sub * kBM + m;
+            const int xx = mm % a.Wt, yy = (mm / a.Wt) % a.Ht, ll = mm / (a.Wt * a.Ht);
+            leaf = l0 + ll;
+            y = y0 + yy;
+            x = x0 + xx;
+            valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
+          }
+          const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN);
+          float hacc = 0.0f;
+          for (int c = 0; c < a.BN; c += 16) {
+            uint32_t r[16];
+            tmem_ld16(trow + (uint32_t)c, r);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float v = fmaf(__uint_as_float(r[j]), a.acc_mul, s_bias[c + j]);
+              if (a.act == 1) v = elu_lp(v);
+              if (kCalib) amax_local = fmaxf(amax_local, fabsf(v));
+              hacc = fmaf(s_head[c + j], v, hacc);
+            }
+          }
+          if (valid) {
+            const float v = hacc + s_head[a.BN];
+            a.head_y[((size_t)leaf * a.Hout + y) * a.Wout + x] = fmaxf(v, 0.0f) + log1pf(__expf(-fabsf(v)));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        continue;
+      }
       for (int it = h; it < items; it += 2) {
       const int sub = it / per_sub, c = (it - sub * per_sub) * cw;
       const int mm = sub * kBM + m;
@@ -584,18 +669,24 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN + c);
       const size_t pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
+      uint4 chunk[4];
+      int cpp;
       if (cw == 32) {
         uint32_t r[32];
         tmem_ld32(trow, r);
-        if (valid) {
-          epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
-          epi16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, pix0, Wo, reps, amax_local);
-        }
+        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk);
+        epi_convert16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, amax_local, chunk + (kFp8Out ? 1 : 2));
+        cpp = kFp8Out ? 2 : 4;
       } else {
         uint32_t r[16];
         tmem_ld16(trow, r);
-        if (valid) epi16<kFp8Out, kCalib>(a, r, s_bias, c, pix0, Wo, reps, amax_local);
+        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk);
+        cpp = kFp8Out ? 1 : 2;
       }
+      if (a.stage_out)
+        store_staged(a, s_stage + (warp - 2) * 2048, chunk, cpp, c, pix0, valid, Wo, reps, lane, kFp8Out ? 1 : 2);
+      else if (valid)
+        store_direct(a, chunk, cpp, c, pix0, Wo, reps, kFp8Out ? 1 : 2);
       }  // work items
       tc_fence_before();
       __syncwarp();
@@ -621,50 +712,28 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // ---------------------------------------------------------------- small SIMT kernels
-// First-layer im2col: x_col[m][tap*5 + c] (taps 3x3, 5 channels, zero padded
-// at the map border), columns 45..63 zero.  Input: the FP32 8-channel x0.
+// First-layer input in the tensor-core layout: the FP32 8-channel x0 as
+// 32-byte rows of T per pixel (16 BF16 or 32 E4M3 channels; channels 8.. are
+// zero), scaled by `mul`.  The first layer then runs as an ordinary 3x3
+// layer over it.
 template <typename T>
-__global__ void k_im2col0(const float *__restrict__ x0, long M, int H, int W, T *__restrict__ xcol, float mul) {
+__global__ void k_pack_x0(const float *__restrict__ x0, long M, T *__restrict__ out, float mul) {
   long m = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  int HW = H * W;
-  long leaf = m / HW;
-  int r = (int)(m % HW), y = r / W, x = r % W;
-  float v[64];
-#pragma unroll
-  for (int i = 0; i < 64; ++i) v[i] = 0.0f;
-#pragma unroll
-  for (int tap = 0; tap < 9; ++tap) {
-    int iy = y + tap / 3 - 1, ix = x + tap % 3 - 1;
-    if (iy < 0 || iy >= H || ix < 0 || ix >= W) continue;
-    const float4 *p = reinterpret_cast<const float4 *>(x0 + ((leaf * H + iy) * W + ix) * 8);
-    float4 a = __ldg(p), b = __ldg(p + 1);
-    v[tap * 5 + 0] = a.x;
-    v[tap * 5 + 1] = a.y;
-    v[tap * 5 + 2] = a.z;
-    v[tap * 5 + 3] = a.w;
-    v[tap * 5 + 4] = b.x;
-  }
-  T *o = xcol + m * 64;
+  const float4 *p = reinterpret_cast<const float4 *>(x0 + m * 8);
+  const float4 a = __ldg(p), b = __ldg(p + 1);
+  uint4 *o = reinterpret_cast<uint4 *>(out) + m * 2;
   if constexpr (sizeof(T) == 2) {
-    uint32_t w[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * j] * mul, v[2 * j + 1] * mul);
-      w[j] = *reinterpret_cast<uint32_t *>(&p);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) reinterpret_cast<uint4 *>(o)[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    __nv_bfloat162 q0 = __floats2bfloat162_rn(a.x * mul, a.y * mul), q1 = __floats2bfloat162_rn(a.z * mul, a.w * mul);
+    __nv_bfloat162 q2 = __floats2bfloat162_rn(b.x * mul, b.y * mul), q3 = __floats2bfloat162_rn(b.z * mul, b.w * mul);
+    o[0] = make_uint4(*reinterpret_cast<uint32_t *>(&q0), *reinterpret_cast<uint32_t *>(&q1),
+                      *reinterpret_cast<uint32_t *>(&q2), *reinterpret_cast<uint32_t *>(&q3));
   } else {
-    uint32_t w[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      __nv_fp8x4_e4m3 p(make_float4(v[4 * j] * mul, v[4 * j + 1] * mul, v[4 * j + 2] * mul, v[4 * j + 3] * mul));
-      w[j] = *reinterpret_cast<uint32_t *>(&p);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) reinterpret_cast<uint4 *>(o)[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    __nv_fp8x4_e4m3 q0(make_float4(a.x * mul, a.y * mul, a.z * mul, a.w * mul));
+    __nv_fp8x4_e4m3 q1(make_float4(b.x * mul, b.y * mul, b.z * mul, b.w * mul));
+    o[0] = make_uint4(*reinterpret_cast<uint32_t *>(&q0), *reinterpret_cast<uint32_t *>(&q1), 0u, 0u);
   }
+  o[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __device__ __forceinline__ float load_act(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
@@ -745,12 +814,14 @@ struct LpLayer {
   const float *bias;
   float acc_mul, out_mul;
   unsigned int *amax;
+  const float *head_w = nullptr, *head_b = nullptr;  // fused 1x1 head (see TcArgs)
+  float *head_y = nullptr;
 };
 
 // Launch shape: CTAs resident per SM and pipeline stages per CTA.  Zero
 // fields select the built-in heuristic.
 struct TcCfg {
-  int ctas = 0, stages = 0, mt = 0, halo = 0, cb = 0;
+  int ctas = 0, stages = 0, mt = 0, halo = 0, cb = 0, so = 0;
 };
 
 constexpr size_t kSmemPerSM = 228 * 1024;
@@ -851,12 +922,14 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   const int max_ctas = std::min((int)std::min<uint32_t>(4, 512u / cols), ctas_by_registers());
   int per_sm = cfg.ctas > 0 ? std::min(cfg.ctas, max_ctas) : std::min(2, max_ctas);
   const size_t stage_bytes = a.bytes_a + a.bytes_b;
-  const size_t fixed = 1024 + 8 * 5 + 16 + 1024 + 1024;  // alignment, barriers, bias, per-CTA reserve
+  a.stage_out = (cfg.so && !L.head_y) ? 1 : 0;
+  const size_t stage_smem = a.stage_out ? (size_t)kEpiWarps * 2048 : 0;
+  const size_t fixed = 1024 + 8 * 5 + 16 + 2048 + 32 + stage_smem + 1024;  // align, barriers, bias+head, staging, reserve
   const size_t cap = kSmemPerSM / per_sm - 1024;
   const int max_stages = (int)std::min<size_t>(24, (cap - fixed) / (stage_bytes + 16));
   a.stages = cfg.stages > 0 ? std::min(cfg.stages, max_stages) : std::min(8, max_stages);
   if (a.stages < 2) return PG_ERR_UNSUPPORTED;
-  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16 + 4 * 256;
+  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16 + 4 * (2 * 256 + 4) + 16 + stage_smem;
   smem = std::max(smem, kSmemPerSM / (per_sm + 1) + 1024);  // at most per_sm CTAs resident
   a.out = L.out;
   a.out_cs = L.out_cs;
@@ -869,6 +942,10 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.bias = L.bias;
   a.status = status;
   a.amax = L.amax;
+  a.head_w = L.head_w;
+  a.head_b = L.head_b;
+  a.head_y = L.head_y;
+  if (a.head_y && (L.ups || L.Cout % 16)) return PG_ERR_UNSUPPORTED;
   a.stats = nullptr;
   static unsigned long long *d_stats = nullptr;
   const bool want_stats = getenv("PG_TC_STATS") != nullptr;
@@ -938,25 +1015,22 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
 
 }  // namespace
 
-// Reduced-precision weight copies: [Cout][k*k*Cin] (K contiguous), the first
-// layer as [Cout][64] in im2col order (tap*5 + c).  FP8 weights carry one
-// per-tensor scale (amax / 448).
+// Reduced-precision weight copies: [Cout][k*k*Cin] (K contiguous); the first
+// layer's input channels are padded to the 32-byte rows of k_pack_x0 (16
+// BF16 or 32 E4M3 channels, zero weights past the net's own).  FP8 weights
+// carry one per-tensor scale (amax / 448).
 static pg_status make_lp_weights(pg_ctx *ctx, Layer &L, bool first, pg_precision prec) {
   const int taps = L.k * L.k;
   const size_t Kf = (size_t)taps * L.cin;  // rows of the FP32 [K][Cout] copy
   std::vector<float> wf(Kf * L.cout);
   PG_CUDA(cudaMemcpyAsync(wf.data(), L.w, wf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
   PG_CUDA(cudaStreamSynchronize(ctx->stream));
-  const size_t K = first ? 64 : Kf;
+  const int cp = first ? (prec == PG_FP8_E4M3 ? 32 : 16) : L.cin;
+  const size_t K = (size_t)taps * cp;
   std::vector<float> wt((size_t)L.cout * K, 0.0f);
-  for (int o = 0; o < L.cout; ++o) {
-    if (first) {
-      for (int tap = 0; tap < taps; ++tap)
-        for (int c = 0; c < 5; ++c) wt[(size_t)o * K + tap * 5 + c] = wf[((size_t)tap * L.cin + c) * L.cout + o];
-    } else {
-      for (size_t kk = 0; kk < Kf; ++kk) wt[(size_t)o * K + kk] = wf[kk * L.cout + o];
-    }
-  }
+  for (int o = 0; o < L.cout; ++o)
+    for (int tap = 0; tap < taps; ++tap)
+      for (int c = 0; c < L.cin; ++c) wt[(size_t)o * K + (size_t)tap * cp + c] = wf[((size_t)tap * L.cin + c) * L.cout + o];
   const int es = prec == PG_FP8_E4M3 ? 1 : 2;
   std::vector<uint8_t> host(wt.size() * es);
   float scale = 1.0f;
@@ -1016,7 +1090,7 @@ namespace {
 // FP8 activation groups: every tensor a layer reads has one per-tensor scale,
 // so layers that write into the same buffer instance (the two halves of a
 // U-Net concatenation) share a group.  out_group[l] / in_group[l]; group 0 is
-// the network input (first-layer im2col).
+// the network input (the packed first-layer input).
 const int kUnetOut[15] = {1, 2, 3, 4, 5, 6, 7, 6, 8, 4, 9, 2, 10, 11, -1};
 const int kUnetIn[15] = {0, 1, 2, 3, 4, 5, 6, 7, 6, 8, 4, 9, 2, 10, 11};
 const int kTinyOut[3] = {1, 2, -1};
@@ -1033,6 +1107,7 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   float best_ms = 1e30f;
   pg_status last_err = PG_ERR_UNSUPPORTED;
   *best = TcCfg();
+  for (int so : {0, 1})
   for (int halo : {0, 1, 2})
   for (int cb : {128, 64, 32})
   for (int mt : {1, 2})
@@ -1046,6 +1121,7 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
       c.mt = mt;
       c.halo = halo;
       c.cb = cb;
+      c.so = so;
       const pg_status w = launch_tc(L, ns, es, fp8, st, status, c);  // warm-up / feasibility
       if (w != PG_OK) {
         if (w != PG_ERR_UNSUPPORTED) last_err = w;
@@ -1082,17 +1158,24 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
   const int *og = net->arch == 0 ? kTinyOut : kUnetOut;
   const int *ig = net->arch == 0 ? kTinyIn : kUnetIn;
   uint8_t *act = (uint8_t *)actv;
+  const int cp = 32 / es;  // first-layer channels per pixel (32-byte rows)
   T *xcol = (T *)act;
-  act += align256(M0 * 64 * es);
-  k_im2col0<T><<<ceil_div(M0, 128), 128, 0, st>>>(x0, M0, H, W, xcol, fp8 ? 1.0f / scale[0] : 1.0f);
+  act += align256(M0 * 32);
+  k_pack_x0<T><<<ceil_div(M0, 256), 256, 0, st>>>(x0, M0, xcol, fp8 ? 1.0f / scale[0] : 1.0f);
+  PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
   auto conv = [&](int li, const void *in, int in_cs, int in_co, int Hin, int Win, int Cin, void *out, int out_cs,
-                  int out_co, int ups) -> pg_status {
+                  int out_co, int ups, const Layer *head = nullptr) -> pg_status {
     const Layer &Lr = Ls[li];
     LpLayer L;
+    if (head) {
+      L.head_w = head->w;
+      L.head_b = head->b;
+      L.head_y = y;
+    }
     L.in = in; L.in_cs = in_cs; L.in_co = in_co; L.Hin = Hin; L.Win = Win; L.Cin = Cin;
     L.out = out; L.out_cs = out_cs; L.out_co = out_co; L.ups = ups;
-    L.Cout = Lr.cout; L.k = li == 0 ? 1 : Lr.k; L.stride = Lr.stride; L.act = Lr.act;
+    L.Cout = Lr.cout; L.k = Lr.k; L.stride = Lr.stride; L.act = Lr.act;
     L.bias = Lr.b;
     L.amax = amax ? amax + og[li] : nullptr;
     if (fp8) {
@@ -1114,12 +1197,13 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       Lw.tc_mt[pi] = best.mt;
       Lw.tc_halo[pi] = best.halo;
       Lw.tc_cb[pi] = best.cb;
+      Lw.tc_so[pi] = best.so;
       Lw.tuned_hw[pi] = H * W;
       if (getenv("PG_TC_LOG"))
         fprintf(stderr,
                 "pg_autotune: layer %d %dx%d cin %d cout %d stride %d leaves %u -> halo %d chunk %dB mt %d ctas %d "
-                "stages %d: %.1f us\n",
-                li, Hin, Win, Cin, Lr.cout, Lr.stride, ns, best.halo, best.cb, best.mt, best.ctas, best.stages,
+                "stages %d staged-out %d: %.1f us\n",
+                li, Hin, Win, Cin, Lr.cout, Lr.stride, ns, best.halo, best.cb, best.mt, best.ctas, best.stages, best.so,
                 best_ms * 1e3f);
     }
     TcCfg cfg;
@@ -1129,30 +1213,34 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       cfg.mt = Lw.tc_mt[pi];
       cfg.halo = Lw.tc_halo[pi];
       cfg.cb = Lw.tc_cb[pi];
+      cfg.so = Lw.tc_so[pi];
     }
-    // Diagnostics: PG_TC_FORCE=<mode>[,cb,mt,ctas,stages] runs every layer
+    // Diagnostics: PG_TC_FORCE=<mode>[,cb,mt,ctas,stages,staged] runs every layer
     // that supports it with that operand staging mode and launch shape (zero
     // or missing fields: defaults); other layers run the default shape.
     if (const char *force = getenv("PG_TC_FORCE")) {
       TcCfg f;
-      sscanf(force, "%d,%d,%d,%d,%d", &f.halo, &f.cb, &f.mt, &f.ctas, &f.stages);
+      sscanf(force, "%d,%d,%d,%d,%d,%d", &f.halo, &f.cb, &f.mt, &f.ctas, &f.stages, &f.so);
+      PG_COUNT(ctx);
       const pg_status s = launch_tc(L, ns, es, fp8, st, ctx->d_status, f);
       if (s != PG_ERR_UNSUPPORTED) return s;
       return launch_tc(L, ns, es, fp8, st, ctx->d_status, TcCfg());
     }
+    PG_COUNT(ctx);
     return launch_tc(L, ns, es, fp8, st, ctx->d_status, cfg);
   };
   auto head = [&](int li, const T *in, int in_cs, int Cin) -> pg_status {
     const Layer &Lr = Ls[li];
     k_cout1_lp<T><<<ceil_div(M0, 256), 256, 0, st>>>(in, in_cs, H, W, Cin, Lr.k, Lr.w, Lr.b,
                                                      fp8 ? scale[ig[li]] : 1.0f, M0, y);
+    PG_COUNT(ctx);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
   };
   if (net->arch == 0) {
     const int c = net->widths[0];
     T *t0 = (T *)act, *t1 = t0 + M0 * c;
-    PG_TRY(conv(0, xcol, 64, 0, H, W, 64, t0, c, 0, 0));
+    PG_TRY(conv(0, xcol, cp, 0, H, W, cp, t0, c, 0, 0));
     PG_TRY(conv(1, t0, c, 0, H, W, c, t1, c, 0, 0));
     return head(2, t1, c, c);
   }
@@ -1167,7 +1255,7 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
   T *cat2 = t1 + ns * HW / 4 * c1;
   T *t2 = cat2 + ns * HW / 16 * k2c;
   T *t3 = t2 + ns * HW / 16 * c2;
-  PG_TRY(conv(0, xcol, 64, 0, H, W, 64, t0, c0, 0, 0));
+  PG_TRY(conv(0, xcol, cp, 0, H, W, cp, t0, c0, 0, 0));
   PG_TRY(conv(1, t0, c0, 0, H, W, c0, cat0, k0c, c1, 0));
   PG_TRY(conv(2, cat0, k0c, c1, H, W, c0, t1, c1, 0, 0));
   PG_TRY(conv(3, t1, c1, 0, H1, W1, c1, cat1, k1c, c2, 0));
@@ -1180,6 +1268,8 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
   PG_TRY(conv(10, cat1, k1c, 0, H1, W1, k1c, t1, c1, 0, 0));
   PG_TRY(conv(11, t1, c1, 0, H1, W1, c1, cat0, k0c, 0, 1));
   PG_TRY(conv(12, cat0, k0c, 0, H, W, k0c, t0, c0, 0, 0));
+  // The 1x1 head (Cout 1) + softplus runs in layer 13's epilogue.
+  if (Ls[14].k == 1 && Ls[14].cout == 1) return conv(13, t0, c0, 0, H, W, c0, t0b, c0, 0, 0, &Ls[14]);
   PG_TRY(conv(13, t0, c0, 0, H, W, c0, t0b, c0, 0, 0));
   return head(14, t0b, c0, c0);
 }
@@ -1200,6 +1290,7 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
     PG_TRY(ctx_alloc(ctx, 64, (void **)&d_amax));
     PG_CUDA(cudaMemsetAsync(d_amax, 0, 64, st));
     k_absmax<<<num_sms() * 4, 256, 0, st>>>(x0, (size_t)ns * H * W * 8, d_amax);
+    PG_COUNT(ctx);
     pg_status s = forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, d_amax);
     unsigned int h[16];
     if (s == PG_OK && cudaMemcpyAsync(h, d_amax, 64, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
@@ -1225,7 +1316,7 @@ size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W) {
   // first run the BF16 calibration pass in the same buffer.
   (void)prec;
   const size_t es = 2, HW = (size_t)H * W;
-  size_t n = HW * 64;  // first-layer im2col
+  size_t n = HW * 16;  // first-layer input, 32 bytes per pixel
   if (net->arch == 0) return es * (n + 2 * HW * net->widths[0]) + 1024;
   const size_t c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
   n += HW * ((c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;

@@ -512,14 +512,14 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   const int TB = 256;
   if (n && sb)
     k_morton_batched<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, g->scene_begin, S, g->scene_geom, Dsp, g->codes,
-                                                     ctx->d_status);
+                                                     ctx->d_status), PG_COUNT(ctx);
   else if (n)
-    k_morton<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, gg, g->codes, ctx->d_status);
+    k_morton<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, gg, g->codes, ctx->d_status), PG_COUNT(ctx);
 
   // a2: stable LSD radix sort; the final permutation lands in g->perm.
   const uint64_t *sorted = g->codes;
   if (n && passes == 0) {
-    k_iota<<<ceil_div(n, TB), TB, 0, st>>>(g->perm, n);
+    k_iota<<<ceil_div(n, TB), TB, 0, st>>>(g->perm, n), PG_COUNT(ctx);
   } else if (n) {
     PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
     PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
@@ -530,14 +530,14 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
       uint64_t *kout = (ps & 1) ? kB : kA;
       uint32_t *vout = ((passes - 1 - ps) & 1) ? vT : g->perm;
       int shift = 8 * ps;
-      k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks);
-      k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot);
+      k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
+      k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
       if (ps == 0)
         k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist, dtot,
-                                                                          nblocks);
+                                                                          nblocks), PG_COUNT(ctx);
       else
         k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
-                                                                           dtot, nblocks);
+                                                                           dtot, nblocks), PG_COUNT(ctx);
       kin = kout;
       vin = vout;
     }
@@ -547,26 +547,26 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   // a3: tree, level by level.
   {
     uint32_t ncell0 = 1u << (3 * dmin);
-    k_tree_init<<<ceil_div(ncell0, TB), TB, 0, st>>>(sorted, n, D, dmin, t);
+    k_tree_init<<<ceil_div(ncell0, TB), TB, 0, st>>>(sorted, n, D, dmin, t), PG_COUNT(ctx);
     // Levels whose cell bound is zero cannot hold cells (no launch).
     for (int d = dmin; d <= D && bound[d]; ++d) {
       uint64_t threads = 8 * bound[d];
-      k_tree_split<<<ceil_div(threads, TB), TB, 0, st>>>(sorted, D, d, thr, t, ctx->d_status);
+      k_tree_split<<<ceil_div(threads, TB), TB, 0, st>>>(sorted, D, d, thr, t, ctx->d_status), PG_COUNT(ctx);
     }
     for (int d = D; d >= dmin; --d)
-      if (bound[d]) k_tree_count<<<ceil_div(bound[d], TB), TB, 0, st>>>(d, t);
-    k_tree_root_offsets<<<1, 1024, 0, st>>>(dmin, t);
+      if (bound[d]) k_tree_count<<<ceil_div(bound[d], TB), TB, 0, st>>>(d, t), PG_COUNT(ctx);
+    k_tree_root_offsets<<<1, 1024, 0, st>>>(dmin, t), PG_COUNT(ctx);
     for (int d = dmin; d <= D && bound[d]; ++d)
       k_tree_offsets<<<ceil_div(bound[d], TB), TB, 0, st>>>(D, d, t, g->leaf_code, g->leaf_depth, g->leaf_begin,
-                                                             g->leaf_end);
-    k_active<<<1, 1024, 0, st>>>(t, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf);
+                                                             g->leaf_end), PG_COUNT(ctx);
+    k_active<<<1, 1024, 0, st>>>(t, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf), PG_COUNT(ctx);
   }
   // a4: leaf of every photon.
-  if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of);
+  if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of), PG_COUNT(ctx);
   k_leaf_lut<<<ceil_div(lut_cells, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * (D - g->lut_depth), lut_cells,
-                                                      g->lut);
+                                                      g->lut), PG_COUNT(ctx);
   k_scene_leaves<<<ceil_div(S + 1, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * Dsp, S,
-                                                     S == (1u << (3 * SL)), g->scene_leaf_begin);
+                                                     S == (1u << (3 * SL)), g->scene_leaf_begin), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
 
   uint32_t hc[2], status = 0;

@@ -259,6 +259,47 @@ pg_status pg_sync(pg_ctx *c) {
   return PG_OK;
 }
 
+pg_status pg_net_get_tuning(const pg_net *netp, int32_t *out, size_t n, size_t *needed) {
+  const Net *net = as<Net>(netp, KIND_NET);
+  if (!net) return PG_ERR_INVALID_ARG;
+  const size_t need = (size_t)net->n_layers * 3 * 7;
+  if (needed) *needed = need;
+  if (!out) return PG_OK;
+  if (n < need) return PG_ERR_INVALID_ARG;
+  for (int l = 0; l < net->n_layers; ++l)
+    for (int p = 0; p < 3; ++p) {
+      const Layer &L = net->layers[l];
+      int32_t *o = out + ((size_t)l * 3 + p) * 7;
+      o[0] = L.tc_ctas[p]; o[1] = L.tc_stages[p]; o[2] = L.tc_mt[p];
+      o[3] = L.tc_halo[p]; o[4] = L.tc_cb[p]; o[5] = L.tuned_hw[p]; o[6] = L.tc_so[p];
+    }
+  return PG_OK;
+}
+
+pg_status pg_net_set_tuning(pg_net *netp, const int32_t *in, size_t n) {
+  Net *net = as<Net>(netp, KIND_NET);
+  if (!net || !in || n != (size_t)net->n_layers * 3 * 7) return PG_ERR_INVALID_ARG;
+  for (size_t i = 0; i < n; i += 7)
+    if (in[i] < 0 || in[i] > 4 || in[i + 1] < 0 || in[i + 1] > 24 || in[i + 2] < 0 || in[i + 2] > 2 ||
+        in[i + 3] < 0 || in[i + 3] > 2 || (in[i + 4] != 0 && in[i + 4] != 32 && in[i + 4] != 64 && in[i + 4] != 128) ||
+        in[i + 5] < 0 || in[i + 6] < 0 || in[i + 6] > 1)
+      return PG_ERR_INVALID_ARG;
+  for (int l = 0; l < net->n_layers; ++l)
+    for (int p = 0; p < 3; ++p) {
+      Layer &L = net->layers[l];
+      const int32_t *v = in + ((size_t)l * 3 + p) * 7;
+      L.tc_ctas[p] = v[0]; L.tc_stages[p] = v[1]; L.tc_mt[p] = v[2];
+      L.tc_halo[p] = v[3]; L.tc_cb[p] = v[4]; L.tuned_hw[p] = v[5]; L.tc_so[p] = v[6];
+    }
+  return PG_OK;
+}
+
+pg_status pg_launch_count(const pg_ctx *c, uint64_t *launches) {
+  if (!c || !launches) return PG_ERR_INVALID_ARG;
+  *launches = c->launches;
+  return PG_OK;
+}
+
 pg_status pg_bytes_in_use(const pg_ctx *c, uint64_t *bytes) {
   if (!c || !bytes) return PG_ERR_INVALID_ARG;
   *bytes = c->in_use;

@@ -99,7 +99,7 @@ struct Layer {
   float w_scale;  // FP8 per-tensor weight scale (w = w_fp8 * w_scale)
   // Tensor-core launch shape picked by pg_autotune, per reduced precision
   // (index 1 = BF16, 2 = FP8) for maps of tuned_hw[i] bins (0 = not tuned).
-  int tc_ctas[3], tc_stages[3], tc_mt[3], tc_halo[3], tc_cb[3];
+  int tc_ctas[3], tc_stages[3], tc_mt[3], tc_halo[3], tc_cb[3], tc_so[3];
   int tuned_hw[3];
 };
 
@@ -141,9 +141,13 @@ struct pg_ctx {
   cudaStream_t stream;
   size_t budget, in_use;
   pg_budget *shared;   // optional budget shared with other contexts
+  uint64_t launches;   // kernels launched for this context (pg_launch_count)
   uint32_t *d_status;  // device status word (pgi::ST_* bits)
   float *d_phi[9];     // boundary-ray tables (cos, sin) per log2(W), W <= 256
 };
+
+// Counts one kernel launch made for a context.
+#define PG_COUNT(ctx) (++(ctx)->launches)
 
 namespace pgi {
 

@@ -175,7 +175,7 @@ pg_status sample(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos
                  uint32_t stream_id, float *d_dir, float *d_pdf, uint32_t *d_leaf, uint32_t *d_bin, QueryScenes qs) {
   uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
   k_sample<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, q, make_qc(g, qs), make_tab(g, t), key, stream_id, d_dir,
-                                                      d_pdf, d_leaf, d_bin, ctx->d_status);
+                                                      d_pdf, d_leaf, d_bin, ctx->d_status), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
   return PG_OK;
 }
@@ -185,7 +185,7 @@ pg_status eval_pdf(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_p
   const float *tab;
   PG_TRY(phi_table(ctx, t->W, &tab));
   k_eval<<<ceil_div(q, 256), 256, 0, ctx->stream>>>(d_pos, d_dir, q, make_qc(g, qs), make_tab(g, t), tab, d_pdf,
-                                                    ctx->d_status);
+                                                    ctx->d_status), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
   return PG_OK;
 }

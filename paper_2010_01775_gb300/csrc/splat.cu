@@ -207,7 +207,7 @@ pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, u
     k_splat<0><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
         h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
-        g->scene_begin, d_scene_nprev, 3 * g->D);
+        g->scene_begin, d_scene_nprev, 3 * g->D), PG_COUNT(ctx);
   } else {
     size_t smem = 12 * HW + 8 * (size_t)h->W;
     PG_CUDA(cudaFuncSetAttribute(k_splat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -215,11 +215,11 @@ pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, u
     k_splat<1><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
         h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
-        g->scene_begin, d_scene_nprev, 3 * g->D);
+        g->scene_begin, d_scene_nprev, 3 * g->D), PG_COUNT(ctx);
     k_splat<2><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
         h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
-        g->scene_begin, d_scene_nprev, 3 * g->D);
+        g->scene_begin, d_scene_nprev, 3 * g->D), PG_COUNT(ctx);
   }
   PG_CUDA(cudaGetLastError());
   return PG_OK;

@@ -37,7 +37,8 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_sample_dirs", "pg_eval_pdf", "pg_info", "pg_export", "pg_free", "pg_status_string",
             "pg_sort_photons_noalloc", "pg_autotune", "pg_build_grid_batched", "pg_splat_photons_batched",
             "pg_sample_dirs_batched", "pg_eval_pdf_batched", "pg_budget_create", "pg_budget_destroy",
-            "pg_ctx_attach_budget", "pg_budget_charge", "pg_budget_release", "pg_budget_wait", "pg_budget_query"]
+            "pg_ctx_attach_budget", "pg_budget_charge", "pg_budget_release", "pg_budget_wait", "pg_budget_query",
+            "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -82,6 +83,8 @@ def load(path: str = LIB_PATH):
         "pg_splat_photons_batched": [P, P, P, u64, P, i32, i32, i32, PP],
         "pg_sample_dirs_batched": [P, P, P, P, P, u64, u64, P, P, P, P, P],
         "pg_eval_pdf_batched": [P, P, P, P, P, P, u64, P],
+        "pg_launch_count": [P, ctypes.POINTER(u64)],
+        "pg_net_get_tuning": [P, P, sz, ctypes.POINTER(sz)], "pg_net_set_tuning": [P, P, sz],
         "pg_budget_create": [u64, PP], "pg_budget_destroy": [P], "pg_ctx_attach_budget": [P, P],
         "pg_budget_charge": [P, u64], "pg_budget_release": [P, u64],
         "pg_budget_wait": [P, u64, ctypes.POINTER(u64), u32],
@@ -169,6 +172,11 @@ class Context:
     def bytes_in_use(self):
         v = ctypes.c_uint64()
         _check(_lib.pg_bytes_in_use(self.ptr, ctypes.byref(v)), "pg_bytes_in_use")
+        return v.value
+
+    def launch_count(self):
+        v = ctypes.c_uint64()
+        _check(_lib.pg_launch_count(self.ptr, ctypes.byref(v)), "pg_launch_count")
         return v.value
 
     def set_stream(self, stream):
@@ -304,6 +312,19 @@ def pg_eval_pdf_batched(ctx, grid, tables, pos, dirs, query_begin, q, pdf):
 
 def pg_autotune(ctx, hist, net, precision):
     _check(_lib.pg_autotune(ctx.ptr, hist.ptr, net.ptr, precision), "pg_autotune")
+
+
+def pg_net_get_tuning(net) -> np.ndarray:
+    need = ctypes.c_size_t()
+    _check(_lib.pg_net_get_tuning(net.ptr, None, 0, ctypes.byref(need)), "pg_net_get_tuning")
+    out = np.zeros(need.value, np.int32)
+    _check(_lib.pg_net_get_tuning(net.ptr, out.ctypes.data, out.size, ctypes.byref(need)), "pg_net_get_tuning")
+    return out
+
+
+def pg_net_set_tuning(net, values):
+    v = np.ascontiguousarray(values, dtype=np.int32)
+    _check(_lib.pg_net_set_tuning(net.ptr, v.ctypes.data, v.size), "pg_net_set_tuning")
 
 
 def pg_map_import(ctx, y, n_maps, H, W) -> Handle:

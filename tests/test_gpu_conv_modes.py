@@ -67,3 +67,38 @@ def test_unet_modes_agree(setup, size, prec):
     y2 = _maps(ctx, net, h, prec, 2)
     for y in (y1, y2):
         assert np.abs(y - y0).sum() / np.abs(y0).sum() < 1e-3
+
+
+def test_staged_and_direct_output_stores_agree(setup):
+    # The epilogue's two store paths write the same bytes: staged through
+    # shared memory (coalesced) or each lane straight to its pixel.
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, 64, 64)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), 905))
+    for prec in (pg.PG_BF16, pg.PG_FP8_E4M3):
+        for mode, mt in ((0, 2), (2, 2), (2, 1)):
+            # One CTA per SM and two stages: both store paths fit in shared memory.
+            ys = [_maps(ctx, net, h, prec, f"{mode},0,{mt},1,2,{so}") for so in (0, 1)]
+            assert np.array_equal(ys[0], ys[1]), (prec, mode, mt)
+
+
+def test_tuning_round_trip(setup):
+    # Launch shapes chosen by the autotuner load into a fresh copy of the net
+    # and reproduce its maps bit for bit.
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, 64, 64)
+    blob = synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), 904)
+    a = pg.pg_net_load(ctx, blob)
+    pg.pg_autotune(ctx, h, a, pg.PG_BF16)
+    tun = pg.pg_net_get_tuning(a)
+    assert tun.size == 15 * 3 * 7 and (tun.reshape(15, 3, 7)[:14, 1, 5] == 64 * 64).all()
+    b = pg.pg_net_load(ctx, blob)
+    pg.pg_net_set_tuning(b, tun)
+    assert np.array_equal(pg.pg_net_get_tuning(b), tun)
+    ya = pg.export_map(pg.pg_reconstruct(ctx, h, a, pg.PG_BF16))
+    yb = pg.export_map(pg.pg_reconstruct(ctx, h, b, pg.PG_BF16))
+    assert np.array_equal(ya, yb)
+    bad = tun.copy()
+    bad[3] = 7  # no such staging mode
+    with pytest.raises(pg.PgError):
+        pg.pg_net_set_tuning(b, bad)
