@@ -32,6 +32,12 @@ sys.path.insert(0, ROOT)
 METRIC = "guided samples/s + leaf tables/s, FP32 vs BF16/FP8 at KL≤1e-3; p50/p99 latency"
 LO, HI = [0.0, 0.0, 0.0], [1.0, 1.0, 1.0]
 
+# DRAM bytes (read + write) of one reconstruct call per active leaf, from one
+# ncu capture of every kernel of a reconstruct (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/k_conv_tc_scale-mid.md), keyed by (H, W,
+# precision).  The traffic of a reconstruct grows in proportion to its leaves.
+CNN_DRAM_BYTES_PER_LEAF = {(64, 64, "bf16"): 7437.1e6 / 1322}
+
 
 def unet_flops_per_leaf(H, W, widths, arch):
     """2 * MACs of the network per map (zero padding counted as work)."""
@@ -279,7 +285,9 @@ def run_pg(args, wl, prec):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": main["launches"],
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                         "traffic": None, "kernel": "CNN convolutions (all layers of one reconstruct call)",
+                         "traffic": (CNN_DRAM_BYTES_PER_LEAF[(H, W, args.precision)] * A
+                                     if (H, W, args.precision) in CNN_DRAM_BYTES_PER_LEAF else None),
+                         "kernel": "CNN convolutions (all layers of one reconstruct call)",
                          "peak_source": ("of " + peak_src) if prec != pg.PG_FP32 else
                          "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock"},
             "clocks": main["clocks"],
