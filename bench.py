@@ -182,11 +182,8 @@ def run_pg(args, wl, prec):
         torch.cuda.synchronize()
         launches = (ctx.launch_count() - launches0) // steps
         clk = clocks.stop() if clocks is not None else None
-        total_ms = float(sum(times))
+        total_ms = max_over_ranks(float(sum(times)), world)
         if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
             torch.distributed.barrier()
         stage_ms = dict(zip(["grid", "splat", "cnn", "cdf", "sample", "eval"], (stage / steps).round(4).tolist()))
         return dict(A=A, L=L, times=times, total_ms=total_ms, stage_ms=stage_ms, clocks=clk, launches=launches)
@@ -264,7 +261,7 @@ def run_pg(args, wl, prec):
         hd.free()
     ctx.destroy()
 
-    value = q * args.steps * world / (total_ms / 1e3)
+    value = whole_job_rate(q, args.steps, world, total_ms)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
@@ -541,6 +538,22 @@ def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None):
                                                      "leaves": len(kl)}
             precisions[name]["l1_vs_fp64_oracle_mean"] = float(np.mean(l1))
     return out
+
+
+def max_over_ranks(ms, world, device="cuda"):
+    """Time of a step replicated over `world` ranks: the slowest rank's time,
+    returned on every rank (one all-reduce; no data-path collective)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, job_ms):
+    """Units all ranks processed per second of job time (weak scaling)."""
+    return units_per_rank_step * steps * world / (job_ms / 1e3)
 
 
 def run_reference(args, wl):

@@ -18,6 +18,14 @@ namespace {
 
 constexpr int kSplatThreads = 512;
 
+// Bulk asynchronous copy shared -> global (16-byte aligned, size a multiple
+// of 16 bytes), completion tracked by the issuing thread's bulk group.
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+               "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+               : "memory");
+}
+
 // kMode 0: all four planes; 1: current planes only; 2: previous planes only.
 template <int kMode>
 __global__ void __launch_bounds__(kSplatThreads) k_splat(
@@ -139,23 +147,29 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
   if (bad) atomicOr(status, bad);
   __syncthreads();
 
-  // Flush: coalesced 16-byte stores, per-leaf totals by block reduction.
+  // Flush: the finished planes leave shared memory as bulk asynchronous
+  // copies issued by one thread, so the CTA can retire (and the next leaf's
+  // CTA start on this SM) while its histogram drains to HBM; the per-leaf
+  // totals come from a block reduction over the shared planes.
   const size_t o = (size_t)slot * HW;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // atomics above -> bulk-copy reads below
   unsigned long long t_cur = 0, t_prev = 0;
-  for (int k = 2 * tid; k < HW; k += 2 * kSplatThreads) {
+  const int P = kMode == 0 ? HW : 0;
+  for (int k = tid; k < HW; k += kSplatThreads) {
+    if (kMode != 2) t_cur += s_pow[k];
+    if (kMode != 1) t_prev += s_pow[P + k];
+  }
+  __syncthreads();
+  if (tid == 0) {
     if (kMode != 2) {
-      ulonglong2 v = make_ulonglong2(s_pow[k], s_pow[k + 1]);
-      *reinterpret_cast<ulonglong2 *>(pow_cur + o + k) = v;
-      *reinterpret_cast<uint2 *>(cnt_cur + o + k) = make_uint2(s_cnt[k], s_cnt[k + 1]);
-      t_cur += v.x + v.y;
+      bulk_store(pow_cur + o, s_pow, 8u * HW);
+      bulk_store(cnt_cur + o, s_cnt, 4u * HW);
     }
     if (kMode != 1) {
-      const int P = kMode == 0 ? HW : 0;
-      ulonglong2 v = make_ulonglong2(s_pow[P + k], s_pow[P + k + 1]);
-      *reinterpret_cast<ulonglong2 *>(pow_prev + o + k) = v;
-      *reinterpret_cast<uint2 *>(cnt_prev + o + k) = make_uint2(s_cnt[P + k], s_cnt[P + k + 1]);
-      t_prev += v.x + v.y;
+      bulk_store(pow_prev + o, s_pow + P, 8u * HW);
+      bulk_store(cnt_prev + o, s_cnt + P, 4u * HW);
     }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   }
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
@@ -175,6 +189,8 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
     }
     if (kMode != 2) tot_cur[slot] = a;
     if (kMode != 1) tot_prev[slot] = c;
+    // Shared memory must outlive the copies' reads of it (not their writes).
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
   }
 }
 
