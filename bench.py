@@ -117,6 +117,15 @@ def run_pg(args, wl, prec):
     torch.cuda.set_stream(stream)
     ctx = pg.Context(stream.cuda_stream)
     net = pg.pg_net_load(ctx, blob)
+    # Optional mixture of experts (Sec. 8): experts 1.. are the same
+    # architecture with other seeded weights.
+    experts = [net] + [pg.pg_net_load(ctx, synth.net_blob(wl.arch, wl.widths, wl.seed + 1000 + e))
+                       for e in range(1, args.experts)] if args.experts > 1 else []
+
+    def recon(h, pr):
+        if experts:
+            return pg.pg_reconstruct_experts(ctx, h, experts, synth.EXPERT_BOUNDS[:len(experts) - 1], pr)
+        return pg.pg_reconstruct(ctx, h, net, pr)
     d_ph = torch.from_numpy(ph).cuda()
     d_pos = torch.from_numpy(pos).cuda()
     d_dir = torch.from_numpy(dirs).cuda()
@@ -134,7 +143,7 @@ def run_pg(args, wl, prec):
         rec(1)
         h = pg.pg_splat_photons(ctx, g, p_ph, n, wl.n_prev, H, W, wl.frac_bits)
         rec(2)
-        m = pg.pg_reconstruct(ctx, h, net, pr)
+        m = recon(h, pr)
         rec(3)
         t = pg.pg_build_cdf(ctx, m)
         rec(4)
@@ -157,6 +166,8 @@ def run_pg(args, wl, prec):
     elif args.autotune:
         for pr in {prec} | ({pg.PG_BF16, pg.PG_FP8_E4M3} if args.sweep else set()):
             pg.pg_autotune(ctx, h0, net, pr)
+    for ex in experts[1:]:  # same layer shapes: the first net's launch shapes fit every expert
+        pg.pg_net_set_tuning(ex, pg.pg_net_get_tuning(net))
     if args.save_tuning:
         np.save(args.save_tuning, pg.pg_net_get_tuning(net))
     ctx.sync()
@@ -225,7 +236,7 @@ def run_pg(args, wl, prec):
     for _ in range(max(2, min(args.steps, 5))):
         a, b = ev(), ev()
         a.record(stream)
-        m = pg.pg_reconstruct(ctx, h0, net, prec)
+        m = recon(h0, prec)
         b.record(stream)
         b.synchronize()
         cnn_ms.append(a.elapsed_time(b))
@@ -256,7 +267,8 @@ def run_pg(args, wl, prec):
             _, _, P = step(d_ph, d_pos, d_dir, outs, pr, keep_tables=True)
             if check is None:
                 check = np.linspace(0, P.shape[0] - 1, args.cpu_sample_leaves).astype(np.int64)
-            maps[names[pr]] = P[check].astype(np.float64)
+            if not experts:  # the oracle leg runs the single net
+                maps[names[pr]] = P[check].astype(np.float64)
     for hd in (h0, g0):
         hd.free()
     ctx.destroy()
@@ -271,6 +283,7 @@ def run_pg(args, wl, prec):
             "config": {"workload": wl.name, "photons": n, "queries": q, "H": H, "W": W, "max_depth": wl.max_depth,
                        "split_threshold": wl.split_threshold, "leaves": L, "active_leaves": A,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "experts": args.experts or 1,
                        "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
             "leaf_tables_per_s": A * args.steps * world / (total_ms / 1e3),
             "stage_ms": stage_ms,
@@ -588,6 +601,8 @@ def main():
     ap.add_argument("--workload", default="scale")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--experts", type=int, default=0,
+                    help="reconstruct with a mixture of this many experts routed by leaf photon count (Sec. 8)")
     ap.add_argument("--save-tuning", default=None, help="write the autotuned launch shapes (.npy)")
     ap.add_argument("--load-tuning", default=None, help="use launch shapes from --save-tuning instead of tuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving trace: seconds of arrivals")

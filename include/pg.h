@@ -180,6 +180,17 @@ pg_status pg_net_load(pg_ctx *ctx, const void *host_blob, size_t bytes, pg_net *
  * `precision` with FP32 accumulation. */
 pg_status pg_reconstruct(pg_ctx *ctx, const pg_hist *hist, const pg_net *net,
                          pg_precision precision, pg_map **out);
+/* The mixture of experts of Sec. 8 (one network per range of voxel photon
+ * counts, [0,100), [100,500), [500,1000), [1000,5000), [5000,inf) in the
+ * paper): the map of every active leaf comes from nets[e], where e is the
+ * number of count_bounds (n_experts - 1 ascending uint32 values, host
+ * memory) that are <= the leaf's photon count (the sum of its current count
+ * plane).  A leaf's map is the one pg_reconstruct gives it with its expert's
+ * net alone.  Each expert with leaves runs once over its leaves; the call
+ * reads the counts back to the host (it returns after a stream
+ * synchronisation).  1 <= n_experts <= 16. */
+pg_status pg_reconstruct_experts(pg_ctx *ctx, const pg_hist *hist, const pg_net *const *nets, int n_experts,
+                                 const uint32_t *count_bounds, pg_precision precision, pg_map **out);
 
 /* Picks the tensor-core launch shape (CTAs per SM, pipeline stages) of every
  * convolution of `net` for `precision` by timing each feasible shape on the

@@ -274,6 +274,36 @@ def cnn_forward(x, net):
     return run(d0, 14)[..., 0]
 
 
+# Sec. 8 (implementation): five networks, each trained for the voxels whose
+# photon count falls in one range, [0,100), [100,500), [500,1000),
+# [1000,5000) and [5000, inf).
+PAPER_EXPERT_BOUNDS = (100, 500, 1000, 5000)
+
+
+def expert_of(counts, bounds=PAPER_EXPERT_BOUNDS):
+    """Index of the count range each voxel's photon count falls in."""
+    counts = np.asarray(counts, np.int64)
+    e = np.zeros(counts.shape, np.int64)
+    for b in bounds:
+        e += counts >= b
+    return e
+
+
+def cnn_forward_experts(x, counts, nets, bounds=PAPER_EXPERT_BOUNDS):
+    """Map of every voxel from the network of its photon-count range."""
+    e = expert_of(counts, bounds)
+    y = None
+    for k, net in enumerate(nets):
+        sel = np.nonzero(e == k)[0]
+        if sel.size == 0:
+            continue
+        yk = cnn_forward(x[sel], net)
+        if y is None:
+            y = np.zeros((x.shape[0],) + yk.shape[1:], np.float64)
+        y[sel] = yk
+    return y
+
+
 # --------------------------------------------------------------------------
 # a8-a9: sampling map and its CDFs (Eq. energy_target; Sec. 7.3 "CDF built
 # via a cumulative sum over pixels, like sampling an environment map").

@@ -30,11 +30,14 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 __global__ void k_assemble(const uint64_t *__restrict__ pow_cur, const uint32_t *__restrict__ cnt_cur,
                            const uint64_t *__restrict__ pow_prev, const uint32_t *__restrict__ cnt_prev,
                            const uint64_t *__restrict__ tot_cur, const uint64_t *__restrict__ tot_prev,
-                           uint32_t slot0, uint32_t nslots, int HW, float *__restrict__ x) {
+                           const uint32_t *__restrict__ perm, uint32_t slot0, uint32_t nslots, int HW,
+                           float *__restrict__ x) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)nslots * HW) return;
-  uint32_t s = slot0 + (uint32_t)(i / HW);
-  size_t g = (size_t)slot0 * HW + i;
+  // Position slot0 + i / HW of the order `perm` (the identity when null).
+  const uint32_t pos = slot0 + (uint32_t)(i / HW);
+  const uint32_t s = perm ? perm[pos] : pos;
+  size_t g = (size_t)s * HW + i % HW;
   uint64_t tc = tot_cur[s], tp = tot_prev[s];
   float ic = tc ? (float)HW / __ull2float_rn(tc) : 0.0f;
   float ip = tp ? (float)HW / __ull2float_rn(tp) : 0.0f;
@@ -291,8 +294,54 @@ static size_t act_floats_per_leaf(const Net *net, int H, int W) {
   return HW * (8 + (c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;
 }
 
+// Per-leaf photon count: the sum of the leaf's current count plane.
+__global__ void k_leaf_counts(const uint32_t *__restrict__ cnt, int HW, uint32_t *__restrict__ out) {
+  __shared__ uint32_t part[8];
+  const uint32_t *row = cnt + (size_t)blockIdx.x * HW;
+  uint32_t v = 0;
+  for (int k = threadIdx.x; k < HW; k += blockDim.x) v += row[k];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < 8; ++w) t += part[w];
+    out[blockIdx.x] = t;
+  }
+}
+
+// y[perm[k]] = yp[k] for rows of HW floats.
+__global__ void k_scatter_rows(const float *__restrict__ yp, const uint32_t *__restrict__ perm, uint32_t A, int HW,
+                               float *__restrict__ y) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)A * HW / 4) return;
+  const size_t k = (4 * i) / HW, c = (4 * i) % HW;
+  *reinterpret_cast<float4 *>(y + (size_t)perm[k] * HW + c) = *reinterpret_cast<const float4 *>(yp + 4 * i);
+}
+
+pg_status leaf_counts(pg_ctx *ctx, const Hist *h, uint32_t *d_counts) {
+  if (h->A == 0) return PG_OK;
+  k_leaf_counts<<<h->A, 256, 0, ctx->stream>>>(h->cnt_cur, h->H * h->W, d_counts), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
+pg_status scatter_rows(pg_ctx *ctx, const float *yp, const uint32_t *d_perm, uint32_t A, int HW, float *y) {
+  if (A == 0) return PG_OK;
+  const size_t n4 = (size_t)A * HW / 4;
+  k_scatter_rows<<<ceil_div(n4, 256), 256, 0, ctx->stream>>>(yp, d_perm, A, HW, y), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
+
 pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m, bool tune) {
-  const uint32_t A = h->A;
+  return reconstruct_range(ctx, h, net, prec, m->y, nullptr, 0, h->A, tune);
+}
+
+pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, float *y_out,
+                            const uint32_t *d_perm, uint32_t first, uint32_t count, bool tune) {
+  const uint32_t A = count;
   if (A == 0) return PG_OK;
   const int H = h->H, W = h->W, HW = H * W;
   const size_t per_leaf = 8 * (size_t)HW * 4 + (prec == PG_FP32 ? act_floats_per_leaf(net, H, W) * 4
@@ -312,10 +361,10 @@ pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision p
     float *x0 = (float *)scratch;  // FP32 input, 8 channels
     size_t nx = (size_t)ns * HW;
     k_assemble<<<ceil_div(nx, 256), 256, 0, st>>>(h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur,
-                                                  h->tot_prev, s0, ns, HW, x0), PG_COUNT(ctx);
+                                                  h->tot_prev, d_perm, first + s0, ns, HW, x0), PG_COUNT(ctx);
     PG_CUDA(cudaGetLastError());
     uint8_t *act = (uint8_t *)scratch + align256(nx * 8 * 4);
-    float *y = m->y + (size_t)s0 * HW;
+    float *y = y_out + (size_t)s0 * HW;
     if (prec == PG_FP32) PG_TRY(forward_f32(ctx, net, x0, act, ns, H, W, y, st));
     else PG_TRY(forward_tc(ctx, net, prec, x0, act, ns, H, W, y, st, tune));
     if (tune) break;  // the first chunk is representative of every later one

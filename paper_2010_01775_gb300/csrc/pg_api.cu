@@ -10,6 +10,7 @@
 #include <condition_variable>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "pg_internal.cuh"
 
@@ -617,6 +618,93 @@ pg_status pg_reconstruct(pg_ctx *c, const pg_hist *hist, const pg_net *netp, pg_
   if (s == PG_OK) {
     m->y = (float *)m->block;
     s = reconstruct(c, h, net, prec, m);
+  }
+  if (s != PG_OK) {
+    if (m->block) ctx_free(c, m->block, m->h.bytes);
+    delete m;
+    return s;
+  }
+  *out = (pg_map *)m;
+  return PG_OK;
+}
+
+pg_status pg_reconstruct_experts(pg_ctx *c, const pg_hist *hist, const pg_net *const *nets, int n_experts,
+                                 const uint32_t *count_bounds, pg_precision prec, pg_map **out) {
+  const Hist *h = as<Hist>(hist, KIND_HIST);
+  if (!c || !h || !nets || !out || n_experts < 1 || n_experts > 16 || (n_experts > 1 && !count_bounds))
+    return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
+  Net *ns[16];
+  for (int e = 0; e < n_experts; ++e) {
+    ns[e] = as<Net>(nets[e], KIND_NET);
+    if (!ns[e]) return PG_ERR_INVALID_ARG;
+    if (ns[e]->arch == 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
+    if (e + 1 < n_experts && e > 0 && count_bounds[e] <= count_bounds[e - 1]) return PG_ERR_INVALID_ARG;
+  }
+  const uint32_t A = h->A;
+  const size_t HW = (size_t)h->H * h->W;
+  // Photon count of every leaf -> expert (the number of bounds <= count),
+  // and the leaves grouped by expert, each group in slot order.
+  std::vector<uint32_t> cnt(A), perm(A);
+  std::vector<uint32_t> first(n_experts + 1, 0);
+  if (A) {
+    uint32_t *d_cnt;
+    PG_TRY(ctx_alloc(c, 4ull * A, (void **)&d_cnt));
+    pg_status s = leaf_counts(c, h, d_cnt);
+    if (s == PG_OK && (cudaMemcpyAsync(cnt.data(), d_cnt, 4ull * A, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                       cudaStreamSynchronize(c->stream) != cudaSuccess))
+      s = PG_ERR_CUDA;
+    ctx_free(c, d_cnt, 4ull * A);
+    PG_TRY(s);
+    std::vector<int> ex(A);
+    for (uint32_t k = 0; k < A; ++k) {
+      int e = 0;
+      while (e + 1 < n_experts && cnt[k] >= count_bounds[e]) ++e;
+      ex[k] = e;
+      ++first[e + 1];
+    }
+    for (int e = 0; e < n_experts; ++e) first[e + 1] += first[e];
+    std::vector<uint32_t> at(first.begin(), first.end() - 1);
+    for (uint32_t k = 0; k < A; ++k) perm[at[ex[k]]++] = k;
+  }
+  for (int e = 0; e < n_experts; ++e)
+    if (first[e + 1] > first[e]) PG_TRY(net_prepare(c, ns[e], prec));
+  Map *m = new (std::nothrow) Map();
+  if (!m) return PG_ERR_OOM;
+  memset(m, 0, sizeof(*m));
+  m->h.kind = KIND_MAP;
+  m->h.ctx = c;
+  m->A = A;
+  m->H = h->H;
+  m->W = h->W;
+  m->h.bytes = (size_t)A * HW * sizeof(float);
+  pg_status s = ctx_alloc(c, m->h.bytes, &m->block);
+  if (s == PG_OK) m->y = (float *)m->block;
+  int used = 0;
+  for (int e = 0; e < n_experts; ++e) used += first[e + 1] > first[e] ? 1 : 0;
+  if (s == PG_OK && used <= 1) {
+    // One expert (or none) has leaves: it runs over all of them in place.
+    int e = 0;
+    while (e + 1 < n_experts && first[e + 1] == first[e]) ++e;
+    s = reconstruct(c, h, ns[e], prec, m);
+  } else if (s == PG_OK) {
+    // Each expert runs over its leaves (contiguous positions of `perm`) into
+    // a position-ordered map, which one scatter returns to slot order.
+    uint32_t *d_perm = nullptr;
+    float *yp = nullptr;
+    const size_t yb = (size_t)A * HW * sizeof(float);
+    s = ctx_alloc(c, 4ull * A, (void **)&d_perm);
+    if (s == PG_OK) s = ctx_alloc(c, yb, (void **)&yp);
+    if (s == PG_OK && cudaMemcpyAsync(d_perm, perm.data(), 4ull * A, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      s = PG_ERR_CUDA;
+    for (int e = 0; e < n_experts && s == PG_OK; ++e)
+      if (first[e + 1] > first[e])
+        s = reconstruct_range(c, h, ns[e], prec, yp + (size_t)first[e] * HW, d_perm, first[e], first[e + 1] - first[e]);
+    if (s == PG_OK) s = scatter_rows(c, yp, d_perm, A, (int)HW, m->y);
+    if (s == PG_OK) s = cudaStreamSynchronize(c->stream) == cudaSuccess ? PG_OK : PG_ERR_CUDA;  // perm is host memory
+    if (yp) ctx_free(c, yp, yb);
+    if (d_perm) ctx_free(c, d_perm, 4ull * A);
   }
   if (s != PG_OK) {
     if (m->block) ctx_free(c, m->block, m->h.bytes);

@@ -310,6 +310,14 @@ pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, u
 // cnn.cu
 pg_status net_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
 pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m, bool tune = false);
+// Maps of the leaves at positions [first, first + count) of the slot order
+// d_perm (the identity when null), written to y_out in that position order.
+pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, float *y_out,
+                            const uint32_t *d_perm, uint32_t first, uint32_t count, bool tune = false);
+// Photon count of every active leaf (sum of its current count plane).
+pg_status leaf_counts(pg_ctx *ctx, const Hist *h, uint32_t *d_counts);
+// y[perm[k]] = yp[k], rows of HW floats (HW a multiple of 4).
+pg_status scatter_rows(pg_ctx *ctx, const float *yp, const uint32_t *d_perm, uint32_t A, int HW, float *y);
 // cdf.cu
 pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t);
 // sample.cu

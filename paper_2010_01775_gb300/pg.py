@@ -38,7 +38,8 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_sort_photons_noalloc", "pg_autotune", "pg_build_grid_batched", "pg_splat_photons_batched",
             "pg_sample_dirs_batched", "pg_eval_pdf_batched", "pg_budget_create", "pg_budget_destroy",
             "pg_ctx_attach_budget", "pg_budget_charge", "pg_budget_release", "pg_budget_wait", "pg_budget_query",
-            "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning"]
+            "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning",
+            "pg_reconstruct_experts"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
         "pg_sample_dirs_batched": [P, P, P, P, P, u64, u64, P, P, P, P, P],
         "pg_eval_pdf_batched": [P, P, P, P, P, P, u64, P],
         "pg_launch_count": [P, ctypes.POINTER(u64)],
+        "pg_reconstruct_experts": [P, P, P, i32, P, i32, PP],
         "pg_net_get_tuning": [P, P, sz, ctypes.POINTER(sz)], "pg_net_set_tuning": [P, P, sz],
         "pg_budget_create": [u64, PP], "pg_budget_destroy": [P], "pg_ctx_attach_budget": [P, P],
         "pg_budget_charge": [P, u64], "pg_budget_release": [P, u64],
@@ -308,6 +310,20 @@ def pg_sample_dirs_batched(ctx, grid, tables, pos, query_begin, q, seed, stream_
 def pg_eval_pdf_batched(ctx, grid, tables, pos, dirs, query_begin, q, pdf):
     _check(_lib.pg_eval_pdf_batched(ctx.ptr, grid.ptr, tables.ptr, _ptr(pos), _ptr(dirs), _ptr(query_begin), q,
                                     _ptr(pdf)), "pg_eval_pdf_batched")
+
+
+PAPER_EXPERT_BOUNDS = (100, 500, 1000, 5000)  # photon-count ranges of the 5 experts (Sec. 8)
+
+
+def pg_reconstruct_experts(ctx, hist, nets, count_bounds=PAPER_EXPERT_BOUNDS, precision=PG_FP32) -> Handle:
+    """Map of every leaf from the net of its photon-count range (len(nets)
+    experts, len(nets) - 1 ascending bounds)."""
+    arr = (ctypes.c_void_p * len(nets))(*[n.ptr for n in nets])
+    b = np.ascontiguousarray(np.asarray(count_bounds, dtype=np.uint32))
+    out = ctypes.c_void_p()
+    _check(_lib.pg_reconstruct_experts(ctx.ptr, hist.ptr, arr, len(nets), b.ctypes.data if b.size else None,
+                                       precision, ctypes.byref(out)), "pg_reconstruct_experts")
+    return Handle(ctx, out.value, "map")
 
 
 def pg_autotune(ctx, hist, net, precision):

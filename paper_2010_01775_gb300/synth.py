@@ -57,6 +57,9 @@ class Workload:
 
 SEED_BASE = 20101775
 
+# Photon-count bounds of the paper's five expert networks (Sec. 8).
+EXPERT_BOUNDS = (100, 500, 1000, 5000)
+
 TINY = Workload("tiny: 100k photons, 8 blobs, depth 4, split 1000, 32x32, 3-layer 16-ch CNN, 64k queries",
                 100_000, 8, 4, 1000, 32, 32, ARCH_TINY3, (16,), 65_536, SEED_BASE + 0)
 SCALE = Workload("scale: 4M photons, 64 blobs, depth 10, split 2000, 64x64, U-Net 32-64-128-256, 8M queries",

@@ -457,3 +457,21 @@ def test_uniform_fallback_for_leaves_without_map():
     assert np.allclose(s["pdf"][empty], 1 / (4 * np.pi))
     assert np.allclose(s["pdf"][~empty], 1 / (4 * np.pi))  # a constant map is the uniform pdf
     assert np.all(s["bin"][empty] == 0xFFFFFFFF)
+
+
+def test_expert_ranges_follow_the_papers_count_table():
+    # Sec. 8: [0,100), [100,500), [500,1000), [1000,5000), [5000,inf).
+    counts = [0, 1, 99, 100, 499, 500, 999, 1000, 4999, 5000, 10 ** 7]
+    assert O.expert_of(counts).tolist() == [0, 0, 0, 1, 1, 2, 2, 3, 3, 4, 4]
+    assert O.expert_of([5, 6], bounds=()).tolist() == [0, 0]
+
+
+def test_experts_forward_routes_each_leaf_to_its_net():
+    # With two experts the mixture equals each net on its own leaves.
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((4, 8, 8, 5))
+    nets = [O.parse_net(synth.net_blob(synth.ARCH_TINY3, (4,), s)) for s in (1, 2)]
+    counts = np.array([10, 700, 3, 100])
+    y = O.cnn_forward_experts(x, counts, nets, bounds=(100,))
+    for k, e in enumerate(O.expert_of(counts, (100,))):
+        assert np.array_equal(y[k], O.cnn_forward(x[k:k + 1], nets[e])[0])
