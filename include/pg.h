@@ -79,6 +79,7 @@ typedef struct pg_hist pg_hist;
 typedef struct pg_net pg_net;
 typedef struct pg_map pg_map;
 typedef struct pg_tables pg_tables;
+typedef struct pg_mis pg_mis;
 
 /* ---- context ----------------------------------------------------------- */
 
@@ -284,6 +285,41 @@ pg_status pg_eval_pdf_batched(pg_ctx *ctx, const pg_grid *grid, const pg_tables 
                               const float *d_pos, const float *d_dir,
                               const uint32_t *d_query_begin, uint64_t q, float *d_pdf);
 
+/* ---- one-sample MIS of BSDF and guide (Sec. 7.3, Eq. target_mis, mis_alpha,
+ * mis_coef; Algorithm 1) ---------------------------------------------------
+ * Per leaf of a single-scene grid: the sums nu_B, nu_G of bounce
+ * contributions whose direction came from BSDF resp. guided sampling, their
+ * counts Q_B, Q_G, and alpha, the probability of choosing BSDF sampling
+ * (starts at 0.5).  The BSDF is a stand-in: a Lambertian lobe around the
+ * vertex normal n (unit), p_BSDF(w) = max(0, n.w) / pi, sampled as the
+ * projection of a uniform disk sample (r = sqrt(v1), phi = 2 pi v2) onto the
+ * hemisphere, in the tangent frame of Duff et al. (JCGT 2017).  A vertex in
+ * a leaf without a valid map uses BSDF sampling alone (alpha = 1). */
+pg_status pg_mis_create(pg_ctx *ctx, const pg_grid *grid, pg_mis **out);
+/* Adds q bounce records: position (q x 3), strategy (q uint8: 0 BSDF,
+ * 1 guide) and contribution nu_b = L cos f (q float, finite, >= 0; else
+ * PG_ERR_INVALID_INPUT via pg_sync).  Sums are FP64 atomic additions, so
+ * their last bits depend on the order of the additions; counts are exact. */
+pg_status pg_mis_accumulate(pg_ctx *ctx, pg_mis *mis, const pg_grid *grid, const float *d_pos,
+                            const uint8_t *d_strategy, const float *d_contrib, uint64_t q);
+/* Eq. mis_alpha for every leaf with Q_B >= min_count and Q_G >= min_count
+ * (the paper: 50): alpha = nu_B_avg / (nu_B_avg + nu_G_avg), clamped to
+ * [alpha_lo, alpha_hi] (the paper: 0.2, 0.8); other leaves keep alpha. */
+pg_status pg_mis_update(pg_ctx *ctx, pg_mis *mis, uint32_t min_count, float alpha_lo, float alpha_hi);
+/* Samples p_MIS = alpha p_BSDF + (1 - alpha) p_guide at q vertices (positions
+ * and unit normals q x 3).  Philox4x32-10 with key = seed: counter (query
+ * index, stream_id, 1) gives the selection uniform v0 (BSDF when v0 < alpha)
+ * and the BSDF uniforms v1, v2; a guided sample is the one pg_sample_dirs
+ * draws for the same query (counter word 3 = 0).  Outputs: direction
+ * (q x 3), the mixture pdf of that direction (the guide term by the
+ * pg_eval_pdf bin rule), strategy (q uint8: 0 BSDF, 1 guide). */
+pg_status pg_mis_sample(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables, const pg_mis *mis,
+                        const float *d_pos, const float *d_normal, uint64_t q, uint64_t seed, uint32_t stream_id,
+                        float *d_dir, float *d_pdf, uint8_t *d_strategy);
+/* p_MIS of given directions (q x 3) at vertices (positions, normals). */
+pg_status pg_mis_eval(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables, const pg_mis *mis,
+                      const float *d_pos, const float *d_normal, const float *d_dir, uint64_t q, float *d_pdf);
+
 /* ---- inspection -------------------------------------------------------- */
 
 enum {
@@ -313,6 +349,11 @@ enum {
   PG_HIST_POW_PREV = 202,   /* uint64 [A][H*W] */
   PG_HIST_CNT_PREV = 203,   /* uint32 [A][H*W] */
   PG_MAP_Y = 300,           /* float  [A][H][W] */
+  PG_MIS_NU_B = 500,        /* double [L]  sum of BSDF-sampled contributions */
+  PG_MIS_NU_G = 501,        /* double [L]  sum of guide-sampled contributions */
+  PG_MIS_Q_B = 502,         /* uint32 [L]  BSDF-sampled bounces */
+  PG_MIS_Q_G = 503,         /* uint32 [L]  guide-sampled bounces */
+  PG_MIS_ALPHA = 504,       /* float  [L]  BSDF selection probability */
   PG_TAB_P = 400,           /* float  [A][H*W] */
   PG_TAB_CDF_PHI = 401,     /* float  [A][H][W] */
   PG_TAB_CDF_Z = 402,       /* float  [A][H] */

@@ -391,6 +391,104 @@ def eval_pdf(grid, slot_of_leaf, tables, pos, dirs):
 
 
 # --------------------------------------------------------------------------
+# One-sample MIS of BSDF and guide (Sec. 7.3, Eq. target_mis, mis_alpha,
+# mis_coef; Algorithm 1).  The BSDF is a Lambertian stand-in around the
+# vertex normal (no renderer is in scope).
+# --------------------------------------------------------------------------
+def leaf_of_positions(grid, pos):
+    """Leaf containing each position (Algorithm 1, "Locate voxel j"): its
+    code under the a1 rule, then the last leaf whose start code is <= it."""
+    codes, st = morton_codes(pos, grid["lo"], grid["hi"], grid["D"])
+    return np.searchsorted(grid["leaf_code"], codes, side="right").astype(np.int64) - 1, st
+
+
+def mis_accumulate(L, leaf, strategy, contrib):
+    """nu_{j,B}, nu_{j,G}: sums of the bounce contributions in voxel j by the
+    strategy that sampled them; Q_{j,B}, Q_{j,G}: their counts (FP64)."""
+    strategy = np.asarray(strategy).astype(bool)
+    c = np.asarray(contrib, np.float64)
+    nu_b, nu_g = np.zeros(L), np.zeros(L)
+    q_b, q_g = np.zeros(L, np.int64), np.zeros(L, np.int64)
+    np.add.at(nu_b, leaf[~strategy], c[~strategy])
+    np.add.at(nu_g, leaf[strategy], c[strategy])
+    np.add.at(q_b, leaf[~strategy], 1)
+    np.add.at(q_g, leaf[strategy], 1)
+    return dict(nu_b=nu_b, nu_g=nu_g, q_b=q_b, q_g=q_g)
+
+
+def mis_alpha(stats, alpha, min_count=50, lo=0.2, hi=0.8):
+    """Eq. mis_alpha where both counts reach min_count: the BSDF share of the
+    average contributions, clamped to [lo, hi]; other voxels keep alpha."""
+    a = np.array(alpha, np.float64)
+    nb, ng = stats["q_b"], stats["q_g"]
+    ok = (nb >= min_count) & (ng >= min_count) & (nb > 0) & (ng > 0)
+    mb = np.where(ok, stats["nu_b"] / np.maximum(nb, 1), 0.0)
+    mg = np.where(ok, stats["nu_g"] / np.maximum(ng, 1), 0.0)
+    ok &= (mb + mg) > 0
+    a[ok] = np.clip(mb[ok] / (mb[ok] + mg[ok]), lo, hi)
+    return a
+
+
+def tangent_frame(n):
+    """Orthonormal frame (b1, b2, n) of unit normals (Duff, Burgess,
+    Christensen, Hery, Kensler, Liani, Villemin, JCGT 2017)."""
+    n = np.asarray(n, np.float64)
+    sgn = np.where(n[:, 2] >= 0, 1.0, -1.0)
+    a = -1.0 / (sgn + n[:, 2])
+    b = n[:, 0] * n[:, 1] * a
+    b1 = np.stack([1.0 + sgn * n[:, 0] ** 2 * a, sgn * b, -sgn * n[:, 0]], axis=1)
+    b2 = np.stack([b, sgn + n[:, 1] ** 2 * a, -n[:, 1]], axis=1)
+    return b1, b2
+
+
+def cosine_sample(n, v1, v2):
+    """Lambertian lobe around n: a uniform disk sample (r = sqrt(v1), angle
+    2 pi v2) lifted onto the hemisphere; pdf cos(theta) / pi."""
+    b1, b2 = tangent_frame(n)
+    r = np.sqrt(v1)
+    ph = 2.0 * np.pi * v2
+    lz = np.sqrt(np.maximum(0.0, 1.0 - v1))
+    return (b1 * (r * np.cos(ph))[:, None] + b2 * (r * np.sin(ph))[:, None] + np.asarray(n, np.float64) * lz[:, None])
+
+
+def bsdf_pdf(n, d):
+    return np.maximum(0.0, np.sum(np.asarray(n, np.float64) * np.asarray(d, np.float64), axis=1)) / np.pi
+
+
+def mis_uniforms(q, seed, stream):
+    """Selection and BSDF uniforms: Philox4x32-10, counter (i, 0, stream, 1)."""
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    u = np.array([philox4x32_10([i & 0xFFFFFFFF, i >> 32, stream, 1], key) for i in range(q)], np.uint64)
+    return (u >> 8).astype(np.float64) * 2.0 ** -24
+
+
+def mis_sample(grid, slot_of_leaf, tables, alpha_leaf, pos, normals, seed, stream=0):
+    """One-sample MIS: BSDF sampling with probability alpha_j (1 where the
+    voxel has no valid map), else the guided sample; pdf of the result under
+    alpha p_BSDF + (1 - alpha) p_guide."""
+    q = len(pos)
+    leaf, _ = leaf_of_positions(grid, pos)
+    slot = np.asarray(slot_of_leaf)[leaf]
+    valid = (slot >= 0) & (np.asarray(tables["valid"])[np.maximum(slot, 0)] > 0)
+    a = np.where(valid, np.asarray(alpha_leaf, np.float64)[leaf], 1.0)
+    u = mis_uniforms(q, seed, stream)
+    use_bsdf = u[:, 0] < a
+    g = sample(grid, slot_of_leaf, tables, pos, seed, stream)
+    d = np.where(use_bsdf[:, None], cosine_sample(normals, u[:, 1], u[:, 2]), g["dir"])
+    pdf = mis_eval(grid, slot_of_leaf, tables, alpha_leaf, pos, normals, d)
+    return dict(dir=d, pdf=pdf, strategy=(~use_bsdf).astype(np.uint8), alpha=a)
+
+
+def mis_eval(grid, slot_of_leaf, tables, alpha_leaf, pos, normals, dirs):
+    leaf, _ = leaf_of_positions(grid, pos)
+    slot = np.asarray(slot_of_leaf)[leaf]
+    valid = (slot >= 0) & (np.asarray(tables["valid"])[np.maximum(slot, 0)] > 0)
+    a = np.where(valid, np.asarray(alpha_leaf, np.float64)[leaf], 1.0)
+    pg = np.where(valid, eval_pdf(grid, slot_of_leaf, tables, pos, dirs), 0.0)
+    return a * bsdf_pdf(normals, dirs) + (1.0 - a) * pg
+
+
+# --------------------------------------------------------------------------
 # The whole path, for smoke checks and the CPU baseline.
 # --------------------------------------------------------------------------
 def run_path(photons, n_prev, lo, hi, D, min_depth, thr, H, W, blob, pos, dirs, seed, F=32,

@@ -715,6 +715,102 @@ pg_status pg_reconstruct_experts(pg_ctx *c, const pg_hist *hist, const pg_net *c
   return PG_OK;
 }
 
+pg_status pg_mis_create(pg_ctx *c, const pg_grid *grid, pg_mis **out) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  if (!c || !g || !out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (g->n_scenes != 1) return PG_ERR_UNSUPPORTED;
+  Mis *m = new (std::nothrow) Mis();
+  if (!m) return PG_ERR_OOM;
+  memset(m, 0, sizeof(*m));
+  m->h.kind = KIND_MIS;
+  m->h.ctx = c;
+  m->L = g->L;
+  const size_t L = g->L, b8 = (8 * L + 255) & ~(size_t)255, b4 = (4 * L + 255) & ~(size_t)255;
+  m->h.bytes = 2 * b8 + 3 * b4;
+  pg_status s = ctx_alloc(c, m->h.bytes, &m->block);
+  if (s != PG_OK) {
+    delete m;
+    return s;
+  }
+  uint8_t *p = (uint8_t *)m->block;
+  m->nu_b = (double *)p;
+  m->nu_g = (double *)(p + b8);
+  m->q_b = (uint32_t *)(p + 2 * b8);
+  m->q_g = (uint32_t *)(p + 2 * b8 + b4);
+  m->alpha = (float *)(p + 2 * b8 + 2 * b4);
+  s = mis_init(c, m);
+  if (s != PG_OK) {
+    pg_free(m);
+    return s;
+  }
+  *out = (pg_mis *)m;
+  return PG_OK;
+}
+
+pg_status pg_mis_accumulate(pg_ctx *c, pg_mis *misp, const pg_grid *grid, const float *d_pos,
+                            const uint8_t *d_strategy, const float *d_contrib, uint64_t q) {
+  Mis *m = as<Mis>(misp, KIND_MIS);
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  if (!c || !m || !g || (q && (!d_pos || !d_strategy || !d_contrib))) return PG_ERR_INVALID_ARG;
+  if (g->L != m->L || g->n_scenes != 1) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  Staged pos, st, co;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_in(c, d_strategy, q, st));
+  PG_TRY(stage_in(c, d_contrib, q * 4, co));
+  return mis_accumulate(c, m, g, (const float *)pos.dev, (const uint8_t *)st.dev, (const float *)co.dev, q);
+}
+
+pg_status pg_mis_update(pg_ctx *c, pg_mis *misp, uint32_t min_count, float alpha_lo, float alpha_hi) {
+  Mis *m = as<Mis>(misp, KIND_MIS);
+  if (!c || !m || !(alpha_lo >= 0.0f) || !(alpha_hi <= 1.0f) || !(alpha_lo <= alpha_hi)) return PG_ERR_INVALID_ARG;
+  return mis_update(c, m, min_count, alpha_lo, alpha_hi);
+}
+
+pg_status pg_mis_sample(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const pg_mis *misp, const float *d_pos,
+                        const float *d_normal, uint64_t q, uint64_t seed, uint32_t stream_id, float *d_dir,
+                        float *d_pdf, uint8_t *d_strategy) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  const Tables *t = as<Tables>(tab, KIND_TABLES);
+  const Mis *m = as<Mis>(misp, KIND_MIS);
+  if (!c || !g || !t || !m || (q && (!d_pos || !d_normal || !d_dir || !d_pdf || !d_strategy)))
+    return PG_ERR_INVALID_ARG;
+  if (t->A != g->A || m->L != g->L || g->n_scenes != 1) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  Staged pos, nrm, dir, pdf, st;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_in(c, d_normal, q * 12, nrm));
+  PG_TRY(stage_out(c, d_dir, q * 12, dir));
+  PG_TRY(stage_out(c, d_pdf, q * 4, pdf));
+  PG_TRY(stage_out(c, d_strategy, q, st));
+  PG_TRY(mis_sample(c, g, t, m, (const float *)pos.dev, (const float *)nrm.dev, q, seed, stream_id, (float *)dir.dev,
+                    (float *)pdf.dev, (uint8_t *)st.dev));
+  PG_TRY(finish_out(dir));
+  PG_TRY(finish_out(pdf));
+  PG_TRY(finish_out(st));
+  return PG_OK;
+}
+
+pg_status pg_mis_eval(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, const pg_mis *misp, const float *d_pos,
+                      const float *d_normal, const float *d_dir, uint64_t q, float *d_pdf) {
+  const Grid *g = as<Grid>(grid, KIND_GRID);
+  const Tables *t = as<Tables>(tab, KIND_TABLES);
+  const Mis *m = as<Mis>(misp, KIND_MIS);
+  if (!c || !g || !t || !m || (q && (!d_pos || !d_normal || !d_dir || !d_pdf))) return PG_ERR_INVALID_ARG;
+  if (t->A != g->A || m->L != g->L || g->n_scenes != 1) return PG_ERR_INVALID_ARG;
+  if (q == 0) return PG_OK;
+  Staged pos, nrm, dir, pdf;
+  PG_TRY(stage_in(c, d_pos, q * 12, pos));
+  PG_TRY(stage_in(c, d_normal, q * 12, nrm));
+  PG_TRY(stage_in(c, d_dir, q * 12, dir));
+  PG_TRY(stage_out(c, d_pdf, q * 4, pdf));
+  PG_TRY(mis_eval(c, g, t, m, (const float *)pos.dev, (const float *)nrm.dev, (const float *)dir.dev, q,
+                  (float *)pdf.dev));
+  PG_TRY(finish_out(pdf));
+  return PG_OK;
+}
+
 pg_status pg_autotune(pg_ctx *c, const pg_hist *hist, pg_net *netp, pg_precision prec) {
   const Hist *h = as<Hist>(hist, KIND_HIST);
   Net *net = as<Net>(netp, KIND_NET);
@@ -910,6 +1006,10 @@ pg_status pg_info(const void *handle, int what, uint64_t *v) {
     case KIND_NET:
       if (what == PG_INFO_BYTES) { *v = b->bytes; return PG_OK; }
       return PG_ERR_INVALID_ARG;
+    case KIND_MIS:
+      if (what == PG_INFO_N_LEAVES) { *v = ((const Mis *)handle)->L; return PG_OK; }
+      if (what == PG_INFO_BYTES) { *v = b->bytes; return PG_OK; }
+      return PG_ERR_INVALID_ARG;
   }
   return PG_ERR_INVALID_ARG;
 }
@@ -959,6 +1059,16 @@ pg_status pg_export(pg_ctx *c, const void *handle, int what, void *dst, size_t b
       case PG_TAB_VALID: src = t->valid; need = t->A; break;
       default: return PG_ERR_INVALID_ARG;
     }
+  } else if (b->kind == KIND_MIS) {
+    const Mis *m = (const Mis *)handle;
+    switch (what) {
+      case PG_MIS_NU_B: src = m->nu_b; need = (size_t)m->L * 8; break;
+      case PG_MIS_NU_G: src = m->nu_g; need = (size_t)m->L * 8; break;
+      case PG_MIS_Q_B: src = m->q_b; need = (size_t)m->L * 4; break;
+      case PG_MIS_Q_G: src = m->q_g; need = (size_t)m->L * 4; break;
+      case PG_MIS_ALPHA: src = m->alpha; need = (size_t)m->L * 4; break;
+      default: return PG_ERR_INVALID_ARG;
+    }
   } else {
     return PG_ERR_INVALID_ARG;
   }
@@ -987,6 +1097,7 @@ void pg_free(void *handle) {
     }
     case KIND_MAP: block = ((Map *)handle)->block; break;
     case KIND_TABLES: block = ((Tables *)handle)->block; break;
+    case KIND_MIS: block = ((Mis *)handle)->block; break;
     default: return;
   }
   ctx_free(b->ctx, block, b->bytes);
@@ -996,6 +1107,7 @@ void pg_free(void *handle) {
     case KIND_GRID: delete (Grid *)handle; break;
     case KIND_HIST: delete (Hist *)handle; break;
     case KIND_NET: delete (Net *)handle; break;
+    case KIND_MIS: delete (Mis *)handle; break;
     case KIND_MAP: delete (Map *)handle; break;
     default: delete (Tables *)handle; break;
   }

@@ -34,7 +34,7 @@ cudaError_t &last_cuda_error();
 // ---------------------------------------------------------------- handles
 enum : uint32_t {
   KIND_GRID = 0x50474744u, KIND_HIST = 0x50474848u, KIND_NET = 0x5047484Eu,
-  KIND_MAP = 0x5047484Du, KIND_TABLES = 0x50474854u
+  KIND_MAP = 0x5047484Du, KIND_TABLES = 0x50474854u, KIND_MIS = 0x5047494Du
 };
 
 struct Handle {
@@ -131,6 +131,18 @@ struct Tables {
   float *cdf_phi;  // [A][HW]
   float *cdf_z;    // [A][H]
   uint8_t *valid;  // [A]
+  void *block;
+};
+
+// One-sample MIS state per leaf of a grid (Sec. 7.3): accumulated bounce
+// contributions and counts by the strategy that sampled them, and the BSDF
+// selection probability alpha.
+struct Mis {
+  Handle h;
+  uint32_t L;
+  double *nu_b, *nu_g;     // [L]
+  uint32_t *q_b, *q_g;     // [L]
+  float *alpha;            // [L]
   void *block;
 };
 
@@ -332,6 +344,16 @@ pg_status sample(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos
                  QueryScenes qs = QueryScenes());
 pg_status eval_pdf(pg_ctx *ctx, const Grid *g, const Tables *t, const float *d_pos, const float *d_dir,
                    uint64_t q, float *d_pdf, QueryScenes qs = QueryScenes());
+
+pg_status mis_init(pg_ctx *ctx, Mis *m);
+pg_status mis_accumulate(pg_ctx *ctx, Mis *m, const Grid *g, const float *d_pos, const uint8_t *d_strategy,
+                         const float *d_contrib, uint64_t q);
+pg_status mis_update(pg_ctx *ctx, Mis *m, uint32_t min_count, float alpha_lo, float alpha_hi);
+pg_status mis_sample(pg_ctx *ctx, const Grid *g, const Tables *t, const Mis *m, const float *d_pos,
+                     const float *d_normal, uint64_t q, uint64_t seed, uint32_t stream_id, float *d_dir,
+                     float *d_pdf, uint8_t *d_strategy);
+pg_status mis_eval(pg_ctx *ctx, const Grid *g, const Tables *t, const Mis *m, const float *d_pos,
+                   const float *d_normal, const float *d_dir, uint64_t q, float *d_pdf);
 
 inline GridGeom geom_of(const Grid *g) {
   GridGeom gg;

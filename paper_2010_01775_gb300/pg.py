@@ -27,6 +27,7 @@ PG_GRID_SCENE_LEAF_BEGIN = 109
 PG_HIST_POW_CUR, PG_HIST_CNT_CUR, PG_HIST_POW_PREV, PG_HIST_CNT_PREV = 200, 201, 202, 203
 PG_MAP_Y = 300
 PG_TAB_P, PG_TAB_CDF_PHI, PG_TAB_CDF_Z, PG_TAB_VALID = 400, 401, 402, 403
+PG_MIS_NU_B, PG_MIS_NU_G, PG_MIS_Q_B, PG_MIS_Q_G, PG_MIS_ALPHA = 500, 501, 502, 503, 504
 
 STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_NOT_DEVICE_PTR", 3: "PG_ERR_OOM",
           4: "PG_ERR_OVERFLOW", 5: "PG_ERR_NOT_POW2", 6: "PG_ERR_TIMEOUT", 7: "PG_ERR_CUDA",
@@ -39,7 +40,8 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_sample_dirs_batched", "pg_eval_pdf_batched", "pg_budget_create", "pg_budget_destroy",
             "pg_ctx_attach_budget", "pg_budget_charge", "pg_budget_release", "pg_budget_wait", "pg_budget_query",
             "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning",
-            "pg_reconstruct_experts"]
+            "pg_reconstruct_experts", "pg_mis_create", "pg_mis_accumulate", "pg_mis_update", "pg_mis_sample",
+            "pg_mis_eval"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -86,6 +88,10 @@ def load(path: str = LIB_PATH):
         "pg_eval_pdf_batched": [P, P, P, P, P, P, u64, P],
         "pg_launch_count": [P, ctypes.POINTER(u64)],
         "pg_reconstruct_experts": [P, P, P, i32, P, i32, PP],
+        "pg_mis_create": [P, P, PP], "pg_mis_accumulate": [P, P, P, P, P, P, u64],
+        "pg_mis_update": [P, P, u32, ctypes.c_float, ctypes.c_float],
+        "pg_mis_sample": [P, P, P, P, P, P, u64, u64, u32, P, P, P],
+        "pg_mis_eval": [P, P, P, P, P, P, P, u64, P],
         "pg_net_get_tuning": [P, P, sz, ctypes.POINTER(sz)], "pg_net_set_tuning": [P, P, sz],
         "pg_budget_create": [u64, PP], "pg_budget_destroy": [P], "pg_ctx_attach_budget": [P, P],
         "pg_budget_charge": [P, u64], "pg_budget_release": [P, u64],
@@ -324,6 +330,38 @@ def pg_reconstruct_experts(ctx, hist, nets, count_bounds=PAPER_EXPERT_BOUNDS, pr
     _check(_lib.pg_reconstruct_experts(ctx.ptr, hist.ptr, arr, len(nets), b.ctypes.data if b.size else None,
                                        precision, ctypes.byref(out)), "pg_reconstruct_experts")
     return Handle(ctx, out.value, "map")
+
+
+def pg_mis_create(ctx, grid) -> Handle:
+    out = ctypes.c_void_p()
+    _check(_lib.pg_mis_create(ctx.ptr, grid.ptr, ctypes.byref(out)), "pg_mis_create")
+    return Handle(ctx, out.value, "mis")
+
+
+def pg_mis_accumulate(ctx, mis, grid, pos, strategy, contrib, q):
+    _check(_lib.pg_mis_accumulate(ctx.ptr, mis.ptr, grid.ptr, _ptr(pos), _ptr(strategy), _ptr(contrib), q),
+           "pg_mis_accumulate")
+
+
+def pg_mis_update(ctx, mis, min_count=50, alpha_lo=0.2, alpha_hi=0.8):
+    _check(_lib.pg_mis_update(ctx.ptr, mis.ptr, min_count, alpha_lo, alpha_hi), "pg_mis_update")
+
+
+def pg_mis_sample(ctx, grid, tables, mis, pos, normal, q, seed, stream_id, dirs, pdf, strategy):
+    _check(_lib.pg_mis_sample(ctx.ptr, grid.ptr, tables.ptr, mis.ptr, _ptr(pos), _ptr(normal), q, seed, stream_id,
+                              _ptr(dirs), _ptr(pdf), _ptr(strategy)), "pg_mis_sample")
+
+
+def pg_mis_eval(ctx, grid, tables, mis, pos, normal, dirs, q, pdf):
+    _check(_lib.pg_mis_eval(ctx.ptr, grid.ptr, tables.ptr, mis.ptr, _ptr(pos), _ptr(normal), _ptr(dirs), q,
+                            _ptr(pdf)), "pg_mis_eval")
+
+
+def export_mis(m):
+    L = m.info(PG_INFO_N_LEAVES)
+    return dict(nu_b=m.export(PG_MIS_NU_B, np.float64, L), nu_g=m.export(PG_MIS_NU_G, np.float64, L),
+                q_b=m.export(PG_MIS_Q_B, np.uint32, L), q_g=m.export(PG_MIS_Q_G, np.uint32, L),
+                alpha=m.export(PG_MIS_ALPHA, np.float32, L))
 
 
 def pg_autotune(ctx, hist, net, precision):

@@ -248,7 +248,7 @@ def test_sample_and_eval(ctx, tiny_scene, H, W, q, seed, stream_id):
     assert np.array_equal(hb, bins) and np.array_equal(hp, pdf) and np.array_equal(hd, dirs)
     # Evaluation at uniform directions and at the sampled directions.
     ev_dirs = synth.query_directions(q, seed & 0xFFFF)
-    for dd in (ev_dirs, dirs):
+    for dd in (ev_dirs, s["dir"].astype(np.float32)):
         out = torch.empty(q, device="cuda")
         pg.pg_eval_pdf(ctx, g, t, torch.from_numpy(pos).cuda(), torch.from_numpy(np.ascontiguousarray(dd)).cuda(), q, out)
         ctx.sync()

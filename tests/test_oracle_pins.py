@@ -475,3 +475,119 @@ def test_experts_forward_routes_each_leaf_to_its_net():
     y = O.cnn_forward_experts(x, counts, nets, bounds=(100,))
     for k, e in enumerate(O.expert_of(counts, (100,))):
         assert np.array_equal(y[k], O.cnn_forward(x[k:k + 1], nets[e])[0])
+
+
+# ---------------------------------------------------------------- one-sample MIS (Sec. 7.3)
+def test_mis_alpha_rule_hand_values():
+    # Eq. mis_alpha: alpha = avg_B / (avg_B + avg_G), clamped to [0.2, 0.8],
+    # changed only where both strategies have at least 50 samples.
+    st = dict(nu_b=np.array([50.0, 150.0, 450.0, 0.0, 50.0, 0.0, 7.0]),
+              nu_g=np.array([150.0, 50.0, 50.0, 50.0, 150.0, 0.0, 7.0]),
+              q_b=np.array([50, 50, 50, 50, 49, 60, 100]),
+              q_g=np.array([50, 50, 50, 50, 50, 60, 100]))
+    a = O.mis_alpha(st, np.full(7, 0.5))
+    assert a.tolist() == [0.25, 0.75, 0.8, 0.2, 0.5, 0.5, 0.5]
+    a = O.mis_alpha(st, np.full(7, 0.3), min_count=10, lo=0.0, hi=1.0)
+    assert a.tolist()[:4] == [0.25, 0.75, 0.9, 0.0] and a.tolist()[5:] == [0.3, 0.5]
+    assert a[4] == pytest.approx((50 / 49) / (50 / 49 + 3), rel=1e-15)
+
+
+def test_mis_accumulate_matches_loops():
+    rng = np.random.default_rng(4)
+    L, q = 7, 500
+    leaf = rng.integers(0, L, q)
+    strat = rng.integers(0, 2, q).astype(np.uint8)
+    c = rng.random(q)
+    st = O.mis_accumulate(L, leaf, strat, c)
+    for j in range(L):
+        b = [c[k] for k in range(q) if leaf[k] == j and strat[k] == 0]
+        g = [c[k] for k in range(q) if leaf[k] == j and strat[k] == 1]
+        assert st["q_b"][j] == len(b) and st["q_g"][j] == len(g)
+        assert st["nu_b"][j] == pytest.approx(math.fsum(b), rel=1e-13)
+        assert st["nu_g"][j] == pytest.approx(math.fsum(g), rel=1e-13)
+
+
+def test_tangent_frame_is_orthonormal_and_right_handed():
+    rng = np.random.default_rng(5)
+    n = synth.uniform_sphere(rng, 1000)
+    n = np.concatenate([n, [[0, 0, 1], [0, 0, -1], [1, 0, 0], [0, 1e-4, -1 + 5e-9]]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    b1, b2 = O.tangent_frame(n)
+    for u, v in ((b1, b1), (b2, b2)):
+        assert np.allclose(np.sum(u * v, axis=1), 1.0, atol=1e-9)
+    for u, v in ((b1, b2), (b1, n), (b2, n)):
+        assert np.allclose(np.sum(u * v, axis=1), 0.0, atol=1e-9)
+    assert np.allclose(np.cross(b1, b2), n, atol=1e-9)
+
+
+def test_cosine_lobe_distribution():
+    # Lambertian sampling: (n.w)^2 is uniform on [0, 1] and the azimuth in the
+    # tangent plane is uniform; E[n.w] = 2/3.
+    from scipy.stats import kstest
+    rng = np.random.default_rng(6)
+    q = 100000
+    n = synth.uniform_sphere(rng, q)
+    d = O.cosine_sample(n, rng.random(q), rng.random(q))
+    c = np.sum(n * d, axis=1)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-12) and np.all(c >= 0)
+    assert kstest(c ** 2, "uniform").pvalue > 1e-3
+    assert abs(c.mean() - 2 / 3) < 5 * c.std() / math.sqrt(q)
+    b1, b2 = O.tangent_frame(n)
+    az = np.arctan2(np.sum(b2 * d, axis=1), np.sum(b1 * d, axis=1))
+    assert kstest((az + np.pi) / (2 * np.pi), "uniform").pvalue > 1e-3
+
+
+def _mis_setup(H=8, W=16, seed=21):
+    g = _one_leaf_grid()
+    t = O.tables_from_map(_random_maps(1, H, W, seed, zero_rows=False))
+    return g, np.zeros(1, np.int32), t
+
+
+def test_mis_pdf_integrates_to_one():
+    g, slot, t = _mis_setup()
+    rng = np.random.default_rng(22)
+    q = 400000
+    d = synth.uniform_sphere(rng, q)
+    n = np.tile(np.array([[0.3, -0.4, np.sqrt(0.75)]]), (q, 1))
+    p = O.mis_eval(g, slot, t, np.array([0.35]), np.full((q, 3), 0.5, np.float32), n, d) * 4 * np.pi
+    assert abs(p.mean() - 1.0) < 5 * p.std() / math.sqrt(q)
+
+
+def test_mis_sample_is_unbiased_and_selects_with_alpha():
+    # One-sample MIS estimator of a known integral: E[f(w) / p_MIS(w)] with
+    # f = (1 + z)^2 over the sphere is 16 pi / 3 (the guide map is positive
+    # everywhere, so the mixture covers the sphere).
+    g, slot, t = _mis_setup()
+    q, alpha = 200000, 0.35
+    pos = np.full((q, 3), 0.5, np.float32)
+    rng = np.random.default_rng(23)
+    n = synth.uniform_sphere(rng, q)
+    s = O.mis_sample(g, slot, t, np.array([alpha]), pos, n, seed=77, stream=2)
+    f = (1.0 + s["dir"][:, 2]) ** 2 / s["pdf"]
+    assert abs(f.mean() - 16 * np.pi / 3) < 5 * f.std() / math.sqrt(q)
+    k = int((s["strategy"] == 0).sum())
+    assert abs(k - alpha * q) < 5 * math.sqrt(q * alpha * (1 - alpha))
+    # The guided branch draws exactly the guide's sample for the same query.
+    gd = O.sample(g, slot, t, pos, seed=77, stream=2)["dir"]
+    sel = s["strategy"] == 1
+    assert np.array_equal(s["dir"][sel], gd[sel])
+    bs = ~sel
+    assert np.all(np.sum(n[bs] * s["dir"][bs], axis=1) >= -1e-12)
+    assert np.allclose(s["pdf"], O.mis_eval(g, slot, t, np.array([alpha]), pos, n, s["dir"]), rtol=1e-14)
+
+
+def test_mis_leaves_without_map_use_bsdf_only():
+    ph = synth.photons(2000, 2, 20)
+    g = O.build_grid(ph, LO, HI, 3, 0, 50)
+    act, slot = O.active_leaves(g)
+    t = O.tables_from_map(np.ones((act.size, 8, 8)))
+    pos = synth.query_positions(4000, 20)
+    rng = np.random.default_rng(24)
+    n = synth.uniform_sphere(rng, pos.shape[0])
+    s = O.mis_sample(g, slot, t, np.full(g["L"], 0.2), pos, n, seed=3)
+    leaf, _ = O.leaf_of_positions(g, pos)
+    empty = slot[leaf] < 0
+    assert empty.any() and (~empty).any()
+    assert np.all(s["strategy"][empty] == 0) and np.all(s["alpha"][empty] == 1.0)
+    c = np.sum(n * s["dir"], axis=1)
+    assert np.allclose(s["pdf"][empty], c[empty] / np.pi, rtol=1e-12)
