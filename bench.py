@@ -131,12 +131,17 @@ def run_pg(args, wl, prec):
     d_dir = torch.from_numpy(dirs).cuda()
     outs = (torch.empty(q, 3, device="cuda"), torch.empty(q, device="cuda"),
             torch.empty(q, dtype=torch.int32, device="cuda"), torch.empty(q, dtype=torch.int32, device="cuda"),
-            torch.empty(q, device="cuda"))
+            torch.empty(q, device="cuda"), torch.empty(q, dtype=torch.uint8, device="cuda"))
+    # One-sample MIS (Sec. 7.3): vertex normals and bounce contributions.
+    nrm, con = synth.vertex_records(q, wl.seed) if args.mis else (None, None)
+    d_vtx = (torch.from_numpy(nrm).cuda(), torch.from_numpy(con).cuda()) if args.mis else None
+    mis = None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, keep_tables=False):
-        o_d, o_p, o_l, o_b, o_e = outs
+    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, keep_tables=False, vtx=None):
+        o_d, o_p, o_l, o_b, o_e, o_s = outs
+        vtx = vtx if vtx is not None else d_vtx
         rec = (lambda i: marks[i].record(stream)) if marks is not None else (lambda i: None)
         rec(0)
         g = pg.pg_build_grid(ctx, p_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
@@ -147,9 +152,18 @@ def run_pg(args, wl, prec):
         rec(3)
         t = pg.pg_build_cdf(ctx, m)
         rec(4)
-        pg.pg_sample_dirs(ctx, g, t, p_pos, q, 20101775, 0, o_d, o_p, o_l, o_b)
-        rec(5)
-        pg.pg_eval_pdf(ctx, g, t, p_pos, p_dir, q, o_e)
+        if mis is None:
+            pg.pg_sample_dirs(ctx, g, t, p_pos, q, 20101775, 0, o_d, o_p, o_l, o_b)
+            rec(5)
+            pg.pg_eval_pdf(ctx, g, t, p_pos, p_dir, q, o_e)
+        else:
+            # Sample and evaluate the mixture, then fold this pass's bounces
+            # into the statistics and update alpha for the next pass.
+            pg.pg_mis_sample(ctx, g, t, mis, p_pos, vtx[0], q, 20101775, 0, o_d, o_p, o_s)
+            rec(5)
+            pg.pg_mis_eval(ctx, g, t, mis, p_pos, vtx[0], p_dir, q, o_e)
+            pg.pg_mis_accumulate(ctx, mis, g, p_pos, o_s, vtx[1], q)
+            pg.pg_mis_update(ctx, mis)
         rec(6)
         A = g.info(pg.PG_INFO_N_ACTIVE)
         L = g.info(pg.PG_INFO_N_LEAVES)
@@ -170,6 +184,8 @@ def run_pg(args, wl, prec):
         pg.pg_net_set_tuning(ex, pg.pg_net_get_tuning(net))
     if args.save_tuning:
         np.save(args.save_tuning, pg.pg_net_get_tuning(net))
+    if args.mis:  # the grid is rebuilt from the same photons each step: same leaves
+        mis = pg.pg_mis_create(ctx, g0)
     ctx.sync()
 
     def measure(pr, steps, warmup, clocks_on=False):
@@ -210,13 +226,14 @@ def run_pg(args, wl, prec):
     h_dir = torch.from_numpy(dirs).pin_memory()
     h_outs = (torch.empty(q, 3).pin_memory(), torch.empty(q).pin_memory(),
               torch.empty(q, dtype=torch.int32).pin_memory(), torch.empty(q, dtype=torch.int32).pin_memory(),
-              torch.empty(q).pin_memory())
+              torch.empty(q).pin_memory(), torch.empty(q, dtype=torch.uint8).pin_memory())
+    h_vtx = (torch.from_numpy(nrm).pin_memory(), torch.from_numpy(con).pin_memory()) if args.mis else None
     e2e_steps = max(1, min(args.steps, 3))
 
     def e2e_step():
         dph = torch.empty_like(d_ph)
         dph.copy_(h_ph, non_blocking=True)
-        step(dph, h_pos, h_dir, h_outs, prec)
+        step(dph, h_pos, h_dir, h_outs, prec, vtx=h_vtx)
         ctx.sync()
 
     e2e_step()
@@ -226,8 +243,12 @@ def run_pg(args, wl, prec):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = ph.nbytes + pos.nbytes + dirs.nbytes
-    d2h = q * (12 + 4 + 4 + 4 + 4)
+    if args.mis:  # positions, normals, eval directions, contributions in; dirs, pdfs, strategies out
+        h2d = ph.nbytes + pos.nbytes + dirs.nbytes + nrm.nbytes + con.nbytes
+        d2h = q * (12 + 4 + 4 + 1)
+    else:
+        h2d = ph.nbytes + pos.nbytes + dirs.nbytes
+        d2h = q * (12 + 4 + 4 + 4 + 4)
 
     # Dominant kernel family: the CNN convolutions of one reconstruct call,
     # timed with events on the launching stream.
@@ -269,6 +290,12 @@ def run_pg(args, wl, prec):
                 check = np.linspace(0, P.shape[0] - 1, args.cpu_sample_leaves).astype(np.int64)
             if not experts:  # the oracle leg runs the single net
                 maps[names[pr]] = P[check].astype(np.float64)
+    mis_alpha = None
+    if mis is not None:
+        e = pg.export_mis(mis)
+        mis_alpha = {"mean": float(e["alpha"].mean()), "updated_leaves": int(np.sum(e["alpha"] != 0.5)),
+                     "leaves": int(e["alpha"].size)}
+        mis.free()
     for hd in (h0, g0):
         hd.free()
     ctx.destroy()
@@ -284,6 +311,8 @@ def run_pg(args, wl, prec):
                        "split_threshold": wl.split_threshold, "leaves": L, "active_leaves": A,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "experts": args.experts or 1,
+                       "sampling": ("one-sample MIS: Lambertian BSDF stand-in + guide, per-leaf alpha"
+                                    if args.mis else "guide"),
                        "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
             "leaf_tables_per_s": A * args.steps * world / (total_ms / 1e3),
             "stage_ms": stage_ms,
@@ -304,8 +333,11 @@ def run_pg(args, wl, prec):
         }
         if sweep:
             out["precisions"] = sweep
+        if mis_alpha is not None:
+            out["mis_alpha"] = mis_alpha
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves, check, maps, out.get("precisions"))
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves, check, maps, out.get("precisions"),
+                                               mis=args.mis)
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -500,7 +532,7 @@ def run_serve(args, tr):
     print(json.dumps(out), flush=True)
 
 
-def oracle_sample_run(wl, n_leaves, n_queries, check=None):
+def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False):
     """The FP64 oracle on a bounded sample; returns per-stage seconds and the
     throughput extrapolated to the full workload."""
     from oracle import oracle as O
@@ -521,8 +553,17 @@ def oracle_sample_run(wl, n_leaves, n_queries, check=None):
     t4 = time.perf_counter()
     slot2 = np.full(g["L"], -1, np.int32)
     slot2[keep] = np.arange(keep.size, dtype=np.int32)
-    s = O.sample(gsub, slot2, tabs, pos[:n_queries], 20101775)
-    O.eval_pdf(gsub, slot2, tabs, pos[:n_queries], dirs[:n_queries])
+    if mis:
+        nrm, con = synth.vertex_records(wl.n_queries, wl.seed)
+        p, nq = pos[:n_queries], nrm[:n_queries].astype(np.float64)
+        alpha = np.full(g["L"], 0.5)
+        s = O.mis_sample(gsub, slot2, tabs, alpha, p, nq, 20101775)
+        O.mis_eval(gsub, slot2, tabs, alpha, p, nq, dirs[:n_queries])
+        leaf, _ = O.leaf_of_positions(gsub, p)
+        O.mis_alpha(O.mis_accumulate(g["L"], leaf, s["strategy"], con[:n_queries].astype(np.float64)), alpha)
+    else:
+        s = O.sample(gsub, slot2, tabs, pos[:n_queries], 20101775)
+        O.eval_pdf(gsub, slot2, tabs, pos[:n_queries], dirs[:n_queries])
     t5 = time.perf_counter()
     A = act.size
     step_s = (t1 - t0) + (t2 - t1) + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
@@ -531,11 +572,12 @@ def oracle_sample_run(wl, n_leaves, n_queries, check=None):
                 A=int(A), queries=n_queries, P=tabs["P"])
 
 
-def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None):
-    r = oracle_sample_run(wl, n_leaves, 262_144, check)
+def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None, mis=False):
+    r = oracle_sample_run(wl, n_leaves, 65_536 if mis else 262_144, check, mis)
     out = {"value": r["samples_per_s"], "unit": "samples/s", "cores": 1, "kind": "oracle",
            "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons, CNN+CDF on "
-                      f"{r['leaves']} of {r['A']} active leaves, sample+eval on {r['queries']} of {wl.n_queries} "
+                      f"{r['leaves']} of {r['A']} active leaves, {'MIS ' if mis else ''}sample+eval on "
+                      f"{r['queries']} of {wl.n_queries} "
                       f"queries; per-stage times scaled to the full step ({r['step_s']:.1f} s); "
                       f"wall {r['wall_s']:.1f} s")}
     if maps and precisions is not None:
@@ -603,6 +645,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--experts", type=int, default=0,
                     help="reconstruct with a mixture of this many experts routed by leaf photon count (Sec. 8)")
+    ap.add_argument("--mis", action="store_true",
+                    help="sample and evaluate one-sample MIS of a Lambertian BSDF and the guide (Sec. 7.3), "
+                         "with the per-leaf statistics and alpha update in every step")
     ap.add_argument("--save-tuning", default=None, help="write the autotuned launch shapes (.npy)")
     ap.add_argument("--load-tuning", default=None, help="use launch shapes from --save-tuning instead of tuning")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serving trace: seconds of arrivals")

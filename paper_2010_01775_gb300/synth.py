@@ -195,6 +195,16 @@ def query_directions(q: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(_unit(uniform_sphere(rng, q)).astype(np.float32))
 
 
+def vertex_records(q: int, seed: int):
+    """Path-vertex records for one-sample MIS: (q, 3) float32 unit normals
+    (uniform on the sphere) and (q,) float32 bounce contributions (lognormal,
+    sigma 1), the values a renderer would report for each sampled bounce."""
+    rng = np.random.Generator(np.random.PCG64(seed ^ 0x3A15))
+    n = np.ascontiguousarray(_unit(uniform_sphere(rng, q)).astype(np.float32))
+    c = np.ascontiguousarray(rng.lognormal(0.0, 1.0, q).astype(np.float32))
+    return n, c
+
+
 def net_layers(arch: int, widths) -> list:
     """Layer descriptors (cout, cin, k, stride, act) in blob order."""
     if arch == ARCH_TINY3:
