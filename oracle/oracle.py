@@ -23,6 +23,7 @@ against any number from the paper.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import struct
 import subprocess
@@ -162,14 +163,16 @@ def dir_bins(dirs, H, W):
 # --------------------------------------------------------------------------
 # a5: photon energy and count maps, Eq. (photon), Sec. 5 input buffers.
 # --------------------------------------------------------------------------
-def splat(photons, grid, n_prev, H, W, F=32):
+def splat(photons, grid, n_prev, H, W, F=32, n_bound=None):
+    """n_bound: the photon count of the fixed-point bound (default: this call's)."""
     ph = _f32(photons)
     L, HW = grid["L"], H * W
     pc = np.zeros((L, HW), np.uint64)
     pp = np.zeros((L, HW), np.uint64)
     cc = np.zeros((L, HW), np.uint32)
     cp = np.zeros((L, HW), np.uint32)
-    st = lib().or_splat(_p(ph), ph.shape[0], n_prev, _p(grid["perm"]), L, _p(grid["leaf_begin"]),
+    n = ph.shape[0] if n_bound is None else n_bound
+    st = lib().or_splat(_p(ph), n, n_prev, _p(grid["perm"]), L, _p(grid["leaf_begin"]),
                         _p(grid["leaf_end"]), H, W, F, _p(pc), _p(cc), _p(pp), _p(cp))
     return dict(pow_cur=pc, cnt_cur=cc, pow_prev=pp, cnt_prev=cp, H=H, W=W, status=st)
 
@@ -486,6 +489,91 @@ def mis_eval(grid, slot_of_leaf, tables, alpha_leaf, pos, normals, dirs):
     a = np.where(valid, np.asarray(alpha_leaf, np.float64)[leaf], 1.0)
     pg = np.where(valid, eval_pdf(grid, slot_of_leaf, tables, pos, dirs), 0.0)
     return a * bsdf_pdf(normals, dirs) + (1.0 - a) * pg
+
+
+# --------------------------------------------------------------------------
+# Progressive iterations (Sec. 7.1 "Voxel subdivision", Sec. 7.2; Algorithm 1,
+# the photon and reconstruction blocks; Sec. 8: M_thr = c sqrt(2^t), c = 500,
+# subdivision in the first two iterations).
+# --------------------------------------------------------------------------
+def split_threshold(t, c=500.0):
+    """M_thr of iteration t; photon counts are integers, so a count exceeds
+    c sqrt(2^t) exactly when it exceeds its floor."""
+    return int(math.floor(c * math.sqrt(2.0 ** t)))
+
+
+def bin_batch(grid, photons, H, W, F=32, n_bound=None):
+    """A batch binned into the fixed leaves of grid: (L, HW) energy and count
+    sums (Algorithm 1: locate voxel j and solid angle k, add the power)."""
+    ph = _f32(photons)
+    leaf, st = leaf_of_positions(grid, ph[:, :3])
+    counts = np.bincount(leaf, minlength=grid["L"]).astype(np.int64)
+    end = np.cumsum(counts)
+    view = dict(grid, perm=np.argsort(leaf, kind="stable").astype(np.uint32),
+                leaf_begin=(end - counts).astype(np.uint32), leaf_end=end.astype(np.uint32))
+    h = splat(ph, view, 0, H, W, F, n_bound=n_bound)
+    h["status"] |= st
+    return h
+
+
+class Progressive:
+    """Per-leaf energy and count maps over iterations.  Refining iterations
+    (t < refine_iterations) keep their photons and rebuild the grid from all
+    of them with threshold M_thr(t); every leaf with photons is then updated,
+    its previous planes being the sums over the earlier iterations.  Later
+    batches are binned into the fixed leaves: a leaf that receives photons
+    first copies its sums into its previous planes, then adds the batch.
+    Maps are reconstructed for the updated leaves only; the others keep
+    theirs (zero for a leaf never reconstructed)."""
+
+    def __init__(self, lo, hi, max_depth, min_depth, H, W, max_photons, split_c=500.0, refine_iterations=2, F=32):
+        self.lo, self.hi = _f32(lo), _f32(hi)
+        self.D, self.min_depth, self.H, self.W, self.F = max_depth, min_depth, H, W, F
+        self.c, self.refine, self.max_photons = split_c, refine_iterations, max_photons
+        self.t = 0
+        self.status = 0
+        self.stored = np.zeros((0, 8), np.float32)
+        self.grid = None
+        self.updated = np.zeros(0, np.int64)
+        if refine_iterations == 0:
+            self._regrid(0, 2 ** 32 - 1)
+
+    def _regrid(self, n_prev, thr):
+        self.grid = build_grid(self.stored, self.lo, self.hi, self.D, self.min_depth, thr)
+        h = splat(self.stored, self.grid, n_prev, self.H, self.W, self.F, n_bound=self.max_photons)
+        self.status = h["status"]
+        self.pow_cur, self.cnt_cur = h["pow_cur"], h["cnt_cur"]
+        self.pow_prev, self.cnt_prev = h["pow_prev"], h["cnt_prev"]
+        self.updated = active_leaves(self.grid)[0].astype(np.int64)
+        self.maps = np.zeros((self.grid["L"], self.H, self.W))
+
+    def add_photons(self, photons):
+        ph = _f32(photons)
+        if self.t < self.refine:
+            n_prev = self.stored.shape[0]
+            self.stored = np.concatenate([self.stored, ph])
+            self._regrid(n_prev, split_threshold(self.t, self.c))
+            if self.t + 1 == self.refine:
+                self.stored = np.zeros((0, 8), np.float32)
+        else:
+            b = bin_batch(self.grid, ph, self.H, self.W, self.F, n_bound=self.max_photons)
+            self.status = b["status"]
+            touched = np.nonzero(b["cnt_cur"].sum(axis=1) > 0)[0]
+            self.pow_prev[touched] = self.pow_cur[touched]
+            self.cnt_prev[touched] = self.cnt_cur[touched]
+            self.pow_cur[touched] += b["pow_cur"][touched]
+            self.cnt_cur[touched] += b["cnt_cur"][touched]
+            self.updated = touched.astype(np.int64)
+        self.t += 1
+
+    def planes(self, leaves):
+        return dict(pow_cur=self.pow_cur[leaves], cnt_cur=self.cnt_cur[leaves], pow_prev=self.pow_prev[leaves],
+                    cnt_prev=self.cnt_prev[leaves], H=self.H, W=self.W)
+
+    def reconstruct(self, net):
+        if self.updated.size:
+            self.maps[self.updated] = cnn_forward(assemble_inputs(self.planes(self.updated)), net)
+        return tables_from_map(self.maps)
 
 
 # --------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -176,6 +177,111 @@ static T *as(const void *h, uint32_t kind) {
   if (!h) return nullptr;
   const Handle *b = static_cast<const Handle *>(h);
   return b->kind == kind ? (T *)h : nullptr;
+}
+
+// ---------------------------------------------------------------- progressive iterations
+// Frees a handle that a progress state owns (and lends out).
+static void release_owned(void *h) {
+  if (!h) return;
+  ((Handle *)h)->borrowed = 0;
+  pg_free(h);
+}
+
+static void free_progress(Progress *s) {
+  pg_ctx *c = s->h.ctx;
+  release_owned(s->grid);
+  release_owned(s->cum);
+  release_owned(s->map);
+  release_owned(s->tab);
+  ctx_free(c, s->stored, s->cap_stored * sizeof(pg_photon));
+  ctx_free(c, s->updated, 4ull * s->cap_updated);
+  s->h.kind = 0;
+  delete s;
+}
+
+static pg_status progress_updated(pg_ctx *c, Progress *s, const uint32_t *d_leaves, uint32_t A) {
+  if (A > s->cap_updated) {
+    void *b;
+    PG_TRY(ctx_alloc(c, 4ull * A, &b));
+    ctx_free(c, s->updated, 4ull * s->cap_updated);
+    s->updated = (uint32_t *)b;
+    s->cap_updated = A;
+  }
+  if (A) PG_CUDA(cudaMemcpyAsync(s->updated, d_leaves, 4ull * A, cudaMemcpyDeviceToDevice, c->stream));
+  s->n_updated = A;
+  return PG_OK;
+}
+
+// A refining iteration: the grid is rebuilt from every photon kept so far
+// (split threshold thr), and all its leaves' planes are recomputed; photons
+// with index < n_prev are the earlier iterations'.
+static pg_status progress_regrid(pg_ctx *c, Progress *s, uint64_t n_prev, uint32_t thr) {
+  const pg_progress_params &p = s->p;
+  pg_grid_params gp;
+  for (int a = 0; a < 3; ++a) {
+    gp.lo[a] = p.lo[a];
+    gp.hi[a] = p.hi[a];
+  }
+  gp.max_depth = p.max_depth;
+  gp.min_depth = p.min_depth;
+  gp.split_threshold = thr;
+  Grid *g = new (std::nothrow) Grid();
+  Hist *cum = new (std::nothrow) Hist();
+  Map *m = new (std::nothrow) Map();
+  if (!g || !cum || !m) {
+    delete g;
+    delete cum;
+    delete m;
+    return PG_ERR_OOM;
+  }
+  memset(g, 0, sizeof(*g));
+  memset(cum, 0, sizeof(*cum));
+  memset(m, 0, sizeof(*m));
+  g->h.kind = KIND_GRID;
+  cum->h.kind = KIND_HIST;
+  m->h.kind = KIND_MAP;
+  g->h.ctx = cum->h.ctx = m->h.ctx = c;
+  g->h.borrowed = cum->h.borrowed = m->h.borrowed = 1;
+  Hist slot;
+  memset(&slot, 0, sizeof(slot));
+  slot.H = p.H;
+  slot.W = p.W;
+  pg_status st = build_grid(c, s->stored, s->n_stored, &gp, g);
+  if (st == PG_OK && g->A) {
+    slot.A = g->A;
+    st = splat(c, g, s->stored, p.max_photons, n_prev, p.frac_bits, &slot);
+  }
+  if (st == PG_OK) st = hist_alloc(c, cum, g->L, p.H, p.W);
+  if (st == PG_OK && g->A) st = rows_to_leaves(c, &slot, g->active, cum);
+  if (st == PG_OK) st = progress_updated(c, s, g->active, g->A);
+  if (st == PG_OK) st = identity_slots(c, g);
+  if (st == PG_OK) {
+    m->A = g->L;
+    m->H = p.H;
+    m->W = p.W;
+    m->h.bytes = (size_t)g->L * p.H * p.W * sizeof(float);
+    st = ctx_alloc(c, m->h.bytes, &m->block);
+    if (st == PG_OK) {
+      m->y = (float *)m->block;
+      st = cudaMemsetAsync(m->block, 0, m->h.bytes, c->stream) == cudaSuccess ? PG_OK : PG_ERR_CUDA;
+    }
+  }
+  ctx_free(c, slot.block, slot.h.bytes);
+  if (st != PG_OK) {
+    release_owned(g);
+    release_owned(cum);
+    release_owned(m);
+    return st;
+  }
+  release_owned(s->grid);
+  release_owned(s->cum);
+  release_owned(s->map);
+  release_owned(s->tab);
+  s->tab = nullptr;
+  s->grid = g;
+  s->cum = cum;
+  s->map = m;
+  return PG_OK;
 }
 
 }  // namespace pgi
@@ -975,6 +1081,131 @@ pg_status pg_eval_pdf(pg_ctx *c, const pg_grid *grid, const pg_tables *tab, cons
   return PG_OK;
 }
 
+pg_status pg_progress_create(pg_ctx *c, const pg_progress_params *p, pg_progress **out) {
+  if (!c || !p || !out) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (p->max_depth < 0 || p->max_depth > 16 || p->min_depth < 0 || p->min_depth > 6 ||
+      p->min_depth > p->max_depth)
+    return PG_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->lo[a]) || !isfinite(p->hi[a]) || !(p->hi[a] > p->lo[a])) return PG_ERR_INVALID_ARG;
+  if (!isfinite(p->split_c) || !(p->split_c >= 0.0) || p->refine_iterations < 0 || p->refine_iterations > 31 ||
+      p->frac_bits < 0 || p->frac_bits > 62 || p->max_photons == 0 || p->max_photons >= (1ull << 31))
+    return PG_ERR_INVALID_ARG;
+  if (!pow2_in(p->H, 4, 256) || !pow2_in(p->W, 4, 256) || p->H * p->W > 16384) return PG_ERR_NOT_POW2;
+  Progress *s = new (std::nothrow) Progress();
+  if (!s) return PG_ERR_OOM;
+  memset(s, 0, sizeof(*s));
+  s->h.kind = KIND_PROGRESS;
+  s->h.ctx = c;
+  s->p = *p;
+  if (p->refine_iterations == 0) {  // the regular grid of depth min_depth, for good
+    pg_status st = progress_regrid(c, s, 0, 0xFFFFFFFFu);
+    if (st != PG_OK) {
+      free_progress(s);
+      return st;
+    }
+  }
+  *out = (pg_progress *)s;
+  return PG_OK;
+}
+
+pg_status pg_progress_add_photons(pg_ctx *c, pg_progress *sp, const pg_photon *d_ph, uint64_t n) {
+  Progress *s = as<Progress>(sp, KIND_PROGRESS);
+  if (!c || !s || (n && !d_ph)) return PG_ERR_INVALID_ARG;
+  if (n > s->p.max_photons || s->total + n > s->p.max_photons) return PG_ERR_INVALID_ARG;
+  Staged ph;
+  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
+  const uint32_t t = s->t;
+  if ((int64_t)t < s->p.refine_iterations) {
+    if (s->n_stored + n > s->cap_stored) {
+      const uint64_t cap = std::max<uint64_t>(2 * s->cap_stored, s->n_stored + n);
+      void *b;
+      PG_TRY(ctx_alloc(c, cap * sizeof(pg_photon), &b));
+      if (s->n_stored)
+        PG_CUDA(cudaMemcpyAsync(b, s->stored, s->n_stored * sizeof(pg_photon), cudaMemcpyDeviceToDevice, c->stream));
+      ctx_free(c, s->stored, s->cap_stored * sizeof(pg_photon));
+      s->stored = (pg_photon *)b;
+      s->cap_stored = cap;
+    }
+    if (n)
+      PG_CUDA(cudaMemcpyAsync(s->stored + s->n_stored, ph.dev, n * sizeof(pg_photon), cudaMemcpyDeviceToDevice,
+                              c->stream));
+    const uint64_t n_prev = s->n_stored;
+    s->n_stored += n;
+    // M_thr = c sqrt(2^t); counts are integers, so count > M_thr <=> count > floor(M_thr).
+    const double m_thr = floor(s->p.split_c * sqrt(ldexp(1.0, (int)t)));
+    const uint32_t thr = m_thr >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)m_thr;
+    pg_status st = progress_regrid(c, s, n_prev, thr);
+    if (st != PG_OK) {
+      s->n_stored = n_prev;
+      return st;
+    }
+    if ((int64_t)t + 1 == s->p.refine_iterations) {  // the grid is fixed from here on
+      ctx_free(c, s->stored, s->cap_stored * sizeof(pg_photon));
+      s->stored = nullptr;
+      s->n_stored = s->cap_stored = 0;
+    }
+  } else {
+    Grid view;
+    void *scr = nullptr;
+    size_t sb = 0;
+    Hist batch;
+    memset(&batch, 0, sizeof(batch));
+    batch.H = s->p.H;
+    batch.W = s->p.W;
+    pg_status st = bin_into_grid(c, s->grid, (const pg_photon *)ph.dev, n, &view, &scr, &sb);
+    if (st == PG_OK && view.A) {
+      batch.A = view.A;
+      st = splat(c, &view, (const pg_photon *)ph.dev, s->p.max_photons, 0, s->p.frac_bits, &batch);
+      if (st == PG_OK) st = merge_batch(c, &batch, view.active, s->cum);
+    }
+    if (st == PG_OK) st = progress_updated(c, s, view.active, view.A);
+    ctx_free(c, batch.block, batch.h.bytes);
+    ctx_free(c, scr, sb);
+    if (st != PG_OK) return st;
+  }
+  s->t = t + 1;
+  s->total += n;
+  return PG_OK;
+}
+
+pg_status pg_progress_reconstruct(pg_ctx *c, pg_progress *sp, const pg_net *netp, pg_precision prec) {
+  Progress *s = as<Progress>(sp, KIND_PROGRESS);
+  Net *net = as<Net>(netp, KIND_NET);
+  if (!c || !s || !net || !s->grid) return PG_ERR_INVALID_ARG;
+  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
+  if (net->arch == 1 && (s->p.H < 8 || s->p.W < 8)) return PG_ERR_UNSUPPORTED;
+  PG_TRY(net_prepare(c, net, prec));
+  const uint32_t A = s->n_updated;
+  const int HW = s->p.H * s->p.W;
+  if (A) {
+    void *yp;
+    PG_TRY(ctx_alloc(c, (size_t)A * HW * sizeof(float), &yp));
+    pg_status st = reconstruct_range(c, s->cum, net, prec, (float *)yp, s->updated, 0, A);
+    if (st == PG_OK) st = scatter_rows(c, (const float *)yp, s->updated, A, HW, s->map->y);
+    ctx_free(c, yp, (size_t)A * HW * sizeof(float));
+    if (st != PG_OK) return st;
+  }
+  pg_tables *t = nullptr;
+  PG_TRY(pg_build_cdf(c, (const pg_map *)s->map, &t));
+  ((Handle *)t)->borrowed = 1;
+  release_owned(s->tab);
+  s->tab = (Tables *)t;
+  return PG_OK;
+}
+
+pg_status pg_progress_view(const pg_progress *sp, const pg_grid **grid, const pg_hist **planes, const pg_map **map,
+                           const pg_tables **tables) {
+  const Progress *s = as<Progress>(sp, KIND_PROGRESS);
+  if (!s) return PG_ERR_INVALID_ARG;
+  if (grid) *grid = (const pg_grid *)s->grid;
+  if (planes) *planes = (const pg_hist *)s->cum;
+  if (map) *map = (const pg_map *)s->map;
+  if (tables) *tables = (const pg_tables *)s->tab;
+  return PG_OK;
+}
+
 pg_status pg_info(const void *handle, int what, uint64_t *v) {
   if (!handle || !v) return PG_ERR_INVALID_ARG;
   const Handle *b = (const Handle *)handle;
@@ -1010,6 +1241,17 @@ pg_status pg_info(const void *handle, int what, uint64_t *v) {
       if (what == PG_INFO_N_LEAVES) { *v = ((const Mis *)handle)->L; return PG_OK; }
       if (what == PG_INFO_BYTES) { *v = b->bytes; return PG_OK; }
       return PG_ERR_INVALID_ARG;
+    case KIND_PROGRESS: {
+      const Progress *s = (const Progress *)handle;
+      if (what == PG_INFO_ITERATION) *v = s->t;
+      else if (what == PG_INFO_N_UPDATED) *v = s->n_updated;
+      else if (what == PG_INFO_N_PHOTONS) *v = s->total;
+      else if (what == PG_INFO_N_LEAVES) *v = s->grid ? s->grid->L : 0;
+      else if (what == PG_INFO_H) *v = (uint64_t)s->p.H;
+      else if (what == PG_INFO_W) *v = (uint64_t)s->p.W;
+      else return PG_ERR_INVALID_ARG;
+      return PG_OK;
+    }
   }
   return PG_ERR_INVALID_ARG;
 }
@@ -1069,6 +1311,11 @@ pg_status pg_export(pg_ctx *c, const void *handle, int what, void *dst, size_t b
       case PG_MIS_ALPHA: src = m->alpha; need = (size_t)m->L * 4; break;
       default: return PG_ERR_INVALID_ARG;
     }
+  } else if (b->kind == KIND_PROGRESS) {
+    const Progress *s = (const Progress *)handle;
+    if (what != PG_PROGRESS_UPDATED) return PG_ERR_INVALID_ARG;
+    src = s->updated;
+    need = 4ull * s->n_updated;
   } else {
     return PG_ERR_INVALID_ARG;
   }
@@ -1082,6 +1329,11 @@ pg_status pg_export(pg_ctx *c, const void *handle, int what, void *dst, size_t b
 void pg_free(void *handle) {
   if (!handle) return;
   Handle *b = (Handle *)handle;
+  if (b->borrowed) return;
+  if (b->kind == KIND_PROGRESS) {
+    free_progress((Progress *)handle);
+    return;
+  }
   void *block = nullptr;
   switch (b->kind) {
     case KIND_GRID: block = ((Grid *)handle)->block; break;

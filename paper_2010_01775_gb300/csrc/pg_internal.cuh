@@ -34,11 +34,12 @@ cudaError_t &last_cuda_error();
 // ---------------------------------------------------------------- handles
 enum : uint32_t {
   KIND_GRID = 0x50474744u, KIND_HIST = 0x50474848u, KIND_NET = 0x5047484Eu,
-  KIND_MAP = 0x5047484Du, KIND_TABLES = 0x50474854u, KIND_MIS = 0x5047494Du
+  KIND_MAP = 0x5047484Du, KIND_TABLES = 0x50474854u, KIND_MIS = 0x5047494Du, KIND_PROGRESS = 0x50475052u
 };
 
 struct Handle {
   uint32_t kind;
+  uint32_t borrowed;  // owned by another handle: pg_free leaves it alone
   pg_ctx *ctx;
   size_t bytes;  // charged to the context budget
 };
@@ -144,6 +145,24 @@ struct Mis {
   uint32_t *q_b, *q_g;     // [L]
   float *alpha;            // [L]
   void *block;
+};
+
+// Progressive iterations (Sec. 7.1, 7.2; Algorithm 1).  The grid, the
+// leaf-indexed planes, maps and tables are handles of their own kinds, lent
+// to the caller (borrowed) and replaced as iterations go on.
+struct Progress {
+  Handle h;
+  pg_progress_params p;
+  uint32_t t;               // iterations added so far
+  uint64_t total;           // photons added so far
+  Grid *grid;               // leaf table; slot_of_leaf is the identity (A = L)
+  Hist *cum;                // [L][HW] planes: sums over all iterations, and before the leaf's last update
+  Map *map;                 // [L][H][W]; zero rows for leaves never reconstructed
+  Tables *tab;              // tables of map, or null before the first reconstruct
+  pg_photon *stored;        // refining iterations keep their photons (the grid is rebuilt)
+  uint64_t n_stored, cap_stored;
+  uint32_t *updated;        // leaves whose planes changed in the last add, ascending
+  uint32_t n_updated, cap_updated;
 };
 
 }  // namespace pgi
@@ -316,6 +335,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // grid.cu
 pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n, const pg_grid_params *p, Grid *g,
                      const SceneBatch *sb = nullptr);
+// A batch of photons binned into the fixed leaves of g (single scene): *view
+// is g with this batch's sort permutation, per-leaf ranges and the leaves
+// holding its photons (A of them); its arrays live in *scratch (bytes in
+// *scratch_bytes, freed by the caller with ctx_free).
+pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, Grid *view, void **scratch,
+                        size_t *scratch_bytes);
+// progress.cu
+pg_status hist_alloc(pg_ctx *ctx, Hist *h, uint32_t A, int H, int W);  // zeroed planes
+// dst[d_active[a]] = src[a] (all planes); dst is leaf-indexed.
+pg_status rows_to_leaves(pg_ctx *ctx, const Hist *src, const uint32_t *d_active, Hist *dst);
+// For a = 0..batch->A-1, leaf l = d_active[a]: prev[l] = cur[l]; cur[l] += batch[a].
+pg_status merge_batch(pg_ctx *ctx, const Hist *batch, const uint32_t *d_active, Hist *cum);
+pg_status identity_slots(pg_ctx *ctx, Grid *g);  // slot_of_leaf[l] = active[l] = l, A = L
 // splat.cu
 pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h,
                 const uint32_t *d_scene_nprev = nullptr);

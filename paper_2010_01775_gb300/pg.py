@@ -21,6 +21,7 @@ PRECISIONS = {"fp32": PG_FP32, "bf16": PG_BF16, "fp8": PG_FP8_E4M3}
 
 PG_INFO_N_PHOTONS, PG_INFO_N_LEAVES, PG_INFO_N_ACTIVE, PG_INFO_H, PG_INFO_W, PG_INFO_BYTES, PG_INFO_MAX_DEPTH = range(1, 8)
 PG_INFO_N_SCENES, PG_INFO_SCENE_LEVELS = 8, 9
+PG_INFO_ITERATION, PG_INFO_N_UPDATED = 10, 11
 PG_GRID_CODES, PG_GRID_PERM, PG_GRID_LEAF_OF, PG_GRID_LEAF_CODE, PG_GRID_LEAF_DEPTH = 100, 101, 102, 103, 104
 PG_GRID_LEAF_BEGIN, PG_GRID_LEAF_END, PG_GRID_ACTIVE, PG_GRID_SLOT_OF_LEAF = 105, 106, 107, 108
 PG_GRID_SCENE_LEAF_BEGIN = 109
@@ -28,6 +29,7 @@ PG_HIST_POW_CUR, PG_HIST_CNT_CUR, PG_HIST_POW_PREV, PG_HIST_CNT_PREV = 200, 201,
 PG_MAP_Y = 300
 PG_TAB_P, PG_TAB_CDF_PHI, PG_TAB_CDF_Z, PG_TAB_VALID = 400, 401, 402, 403
 PG_MIS_NU_B, PG_MIS_NU_G, PG_MIS_Q_B, PG_MIS_Q_G, PG_MIS_ALPHA = 500, 501, 502, 503, 504
+PG_PROGRESS_UPDATED = 600
 
 STATUS = {0: "PG_OK", 1: "PG_ERR_INVALID_ARG", 2: "PG_ERR_NOT_DEVICE_PTR", 3: "PG_ERR_OOM",
           4: "PG_ERR_OVERFLOW", 5: "PG_ERR_NOT_POW2", 6: "PG_ERR_TIMEOUT", 7: "PG_ERR_CUDA",
@@ -41,7 +43,8 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_ctx_attach_budget", "pg_budget_charge", "pg_budget_release", "pg_budget_wait", "pg_budget_query",
             "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning",
             "pg_reconstruct_experts", "pg_mis_create", "pg_mis_accumulate", "pg_mis_update", "pg_mis_sample",
-            "pg_mis_eval"]
+            "pg_mis_eval", "pg_progress_create", "pg_progress_add_photons", "pg_progress_reconstruct",
+            "pg_progress_view"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -55,6 +58,13 @@ class PgError(RuntimeError):
 class pg_grid_params(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("max_depth", ctypes.c_int32),
                 ("min_depth", ctypes.c_int32), ("split_threshold", ctypes.c_uint32)]
+
+
+class pg_progress_params(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("max_depth", ctypes.c_int32),
+                ("min_depth", ctypes.c_int32), ("split_c", ctypes.c_double), ("refine_iterations", ctypes.c_int32),
+                ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("frac_bits", ctypes.c_int32),
+                ("max_photons", ctypes.c_uint64)]
 
 
 _lib = None
@@ -92,6 +102,9 @@ def load(path: str = LIB_PATH):
         "pg_mis_update": [P, P, u32, ctypes.c_float, ctypes.c_float],
         "pg_mis_sample": [P, P, P, P, P, P, u64, u64, u32, P, P, P],
         "pg_mis_eval": [P, P, P, P, P, P, P, u64, P],
+        "pg_progress_create": [P, ctypes.POINTER(pg_progress_params), PP],
+        "pg_progress_add_photons": [P, P, P, u64], "pg_progress_reconstruct": [P, P, P, i32],
+        "pg_progress_view": [P, PP, PP, PP, PP],
         "pg_net_get_tuning": [P, P, sz, ctypes.POINTER(sz)], "pg_net_set_tuning": [P, P, sz],
         "pg_budget_create": [u64, PP], "pg_budget_destroy": [P], "pg_ctx_attach_budget": [P, P],
         "pg_budget_charge": [P, u64], "pg_budget_release": [P, u64],
@@ -158,6 +171,17 @@ class Handle:
             self.free()
         except Exception:
             pass
+
+
+class Borrowed(Handle):
+    """A handle lent by another handle (a progress state's grid, planes, maps,
+    tables): never freed here, and it keeps its owner alive."""
+
+    def __init__(self, ctx, ptr, kind, owner):
+        self.ctx, self.ptr, self.kind, self.owner = ctx, ptr, kind, owner
+
+    def free(self):
+        self.ptr = None
 
 
 class Context:
@@ -452,3 +476,34 @@ def export_tables(t):
                 cdf_phi=t.export(PG_TAB_CDF_PHI, np.float32, A * H * W).reshape(A, H, W),
                 cdf_z=t.export(PG_TAB_CDF_Z, np.float32, A * H).reshape(A, H),
                 valid=t.export(PG_TAB_VALID, np.uint8, A), H=H, W=W)
+
+
+# ---------------------------------------------------------------- progressive iterations
+def pg_progress_create(ctx, lo, hi, max_depth, min_depth, H, W, max_photons, split_c=500.0, refine_iterations=2,
+                       frac_bits=32) -> Handle:
+    p = pg_progress_params((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi), max_depth, min_depth, split_c,
+                           refine_iterations, H, W, frac_bits, max_photons)
+    out = ctypes.c_void_p()
+    _check(_lib.pg_progress_create(ctx.ptr, ctypes.byref(p), ctypes.byref(out)), "pg_progress_create")
+    return Handle(ctx, out.value, "progress")
+
+
+def pg_progress_add_photons(ctx, state, photons, n):
+    _check(_lib.pg_progress_add_photons(ctx.ptr, state.ptr, _ptr(photons), n), "pg_progress_add_photons")
+
+
+def pg_progress_reconstruct(ctx, state, net, precision):
+    _check(_lib.pg_progress_reconstruct(ctx.ptr, state.ptr, net.ptr, precision), "pg_progress_reconstruct")
+
+
+def pg_progress_view(state):
+    """(grid, planes, maps, tables) borrowed from the state (tables is None
+    before the first reconstruct); valid until the state's next call."""
+    ptrs = [ctypes.c_void_p() for _ in range(4)]
+    _check(_lib.pg_progress_view(state.ptr, *[ctypes.byref(p) for p in ptrs]), "pg_progress_view")
+    kinds = ("grid", "hist", "map", "tables")
+    return tuple(Borrowed(state.ctx, p.value, k, state) if p.value else None for p, k in zip(ptrs, kinds))
+
+
+def export_progress_updated(state) -> np.ndarray:
+    return state.export(PG_PROGRESS_UPDATED, np.uint32, state.info(PG_INFO_N_UPDATED))

@@ -591,3 +591,119 @@ def test_mis_leaves_without_map_use_bsdf_only():
     assert np.all(s["strategy"][empty] == 0) and np.all(s["alpha"][empty] == 1.0)
     c = np.sum(n * s["dir"], axis=1)
     assert np.allclose(s["pdf"][empty], c[empty] / np.pi, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- progressive iterations (Sec. 7.1, 7.2)
+def test_split_threshold_schedule_hand_values():
+    # Sec. 8: M_thr = c sqrt(2^t) with c = 500.
+    assert [O.split_threshold(t) for t in range(5)] == [500, 707, 1000, 1414, 2000]
+    assert [O.split_threshold(t, 400.0) for t in range(3)] == [400, 565, 800]
+
+
+def _leaf_by_range(g, codes):
+    """Leaf of each code by direct range membership: leaf l holds the codes
+    [start_l, start_l + 8^(D - depth_l))."""
+    D = g["D"]
+    out = np.full(len(codes), -1)
+    for l in range(g["L"]):
+        a = int(g["leaf_code"][l])
+        b = a + 8 ** (D - int(g["leaf_depth"][l]))
+        for i, c in enumerate(codes):
+            if a <= int(c) < b:
+                assert out[i] == -1
+                out[i] = l
+    assert np.all(out >= 0)
+    return out
+
+
+def _batches(sizes, seed):
+    ph = synth.photons(sum(sizes), 3, seed)
+    ends = np.cumsum(sizes)
+    return [ph[e - n:e] for n, e in zip(sizes, ends)]
+
+
+def test_progressive_refinement_rebuilds_from_all_photons():
+    # Two refining iterations (c = 20: thresholds 20 then 28) on 150 + 300 photons.
+    b = _batches([150, 300], 31)
+    pr = O.Progressive(LO, HI, 3, 0, 4, 8, 450, split_c=20.0, refine_iterations=2)
+    pr.add_photons(b[0])
+    pr.add_photons(b[1])
+    allp = np.concatenate(b)
+    g = pr.grid
+    q = [_deinterleave(c, 3) for c in O.morton_codes(allp, LO, HI, 3)[0]]
+    leaves = _brute_grid(q, 3, 0, 28)
+    assert g["L"] == len(leaves) and pr.t == 2
+    for l, (c, d, idx) in enumerate(leaves):
+        assert g["leaf_depth"][l] == d
+    # Current planes: every photon; previous planes: the first iteration's.
+    pc, cc, pp, cp, _ = _brute_splat(allp, g, 150, 4, 8, 32)
+    assert pr.pow_cur.tolist() == pc and pr.cnt_cur.tolist() == cc
+    assert pr.pow_prev.tolist() == pp and pr.cnt_prev.tolist() == cp
+    assert pr.updated.tolist() == [l for l in range(g["L"]) if sum(cc[l]) > 0]
+    assert pr.stored.shape[0] == 0 and pr.status == 0  # the grid is fixed from here on
+
+
+def test_progressive_accumulation_matches_recount():
+    # One refining iteration, then three batches binned into the fixed leaves.
+    H, W, F = 4, 8, 32
+    b = _batches([400, 200, 400, 800], 32)
+    pr = O.Progressive(LO, HI, 4, 1, H, W, 1800, split_c=30.0, refine_iterations=1)
+    seen = []
+    for t, ph in enumerate(b):
+        before = (pr.pow_cur.copy(), pr.cnt_cur.copy()) if t else None
+        pr.add_photons(ph)
+        seen.append(ph)
+        g = pr.grid
+        allp = np.concatenate(seen)
+        it = np.concatenate([np.full(len(x), k) for k, x in enumerate(seen)])
+        leaf = _leaf_by_range(g, O.morton_codes(allp, LO, HI, 4)[0])
+        rows, cols, _ = O.dir_bins(allp[:, 3:6], H, W)
+        pfx = [int(v) for v in np.rint(allp[:, 6].astype(np.float64) * 2.0 ** F)]
+        L = g["L"]
+        cur = [[0] * (H * W) for _ in range(L)]
+        cnt = [[0] * (H * W) for _ in range(L)]
+        prev = [[0] * (H * W) for _ in range(L)]
+        cprev = [[0] * (H * W) for _ in range(L)]
+        last = [max([int(it[i]) for i in range(len(allp)) if leaf[i] == l], default=-1) for l in range(L)]
+        for i in range(len(allp)):
+            l, k = int(leaf[i]), int(rows[i] * W + cols[i])
+            cur[l][k] += pfx[i]
+            cnt[l][k] += 1
+            if t == 0 or it[i] < last[l]:  # before the leaf's last update (all earlier for the refine)
+                if t > 0 or it[i] < 0:
+                    prev[l][k] += pfx[i]
+                    cprev[l][k] += 1
+        assert pr.status == 0
+        assert pr.pow_cur.tolist() == cur and pr.cnt_cur.tolist() == cnt
+        if t > 0:
+            assert pr.pow_prev.tolist() == prev and pr.cnt_prev.tolist() == cprev
+            assert pr.updated.tolist() == sorted({int(leaf[i]) for i in range(len(allp)) if it[i] == t})
+            untouched = np.setdiff1d(np.arange(L), pr.updated)
+            assert np.array_equal(pr.pow_cur[untouched], before[0][untouched])
+        # Eq. (photon): the maps hold every photon's power, exactly.
+        assert sum(int(v) for v in pr.pow_cur.ravel()) == sum(pfx)
+
+
+def test_progressive_maps_change_only_where_photons_arrive():
+    H, W = 8, 8
+    net = O.parse_net(synth.net_blob(synth.ARCH_TINY3, (4,), 5))
+    b = _batches([500, 100, 1000], 33)
+    pr = O.Progressive(LO, HI, 3, 1, H, W, 1600, split_c=40.0, refine_iterations=1)
+    pr.add_photons(b[0])
+    t0 = pr.reconstruct(net)
+    m0 = pr.maps.copy()
+    assert np.all(t0["valid"][pr.updated] == 1)
+    pr.add_photons(b[1])
+    pr.reconstruct(net)
+    other = np.setdiff1d(np.arange(pr.grid["L"]), pr.updated)
+    assert other.size and pr.updated.size
+    assert np.array_equal(pr.maps[other], m0[other])
+    assert not np.array_equal(pr.maps[pr.updated], m0[pr.updated])
+
+
+def test_progressive_without_refinement_uses_the_regular_grid():
+    pr = O.Progressive(LO, HI, 5, 2, 4, 4, 900, refine_iterations=0)
+    assert pr.grid["L"] == 64 and np.all(pr.grid["leaf_depth"] == 2)
+    for ph in _batches([300, 600], 34):
+        pr.add_photons(ph)
+    assert int(pr.cnt_cur.sum()) == 900 and pr.grid["L"] == 64
