@@ -5,7 +5,10 @@ codes, radix sort, adaptive split, leaf assignment) -> splat -> CNN
 reconstruction -> normalisation + CDFs -> guided sampling of Q queries -> pdf
 evaluation of Q (position, direction) pairs.  Default workload: 4,194,304
 photons (64 blobs), depth 10, split threshold 2000, 64x64 maps, U-Net
-32-64-128-256, FP32, 8,388,608 queries.
+32-64-128-256, BF16 tensor-core CNN, 8,388,608 queries.  `--progressive`
+times instead one later iteration of the progressive form (a photon batch
+binned into the fixed grid, maps rebuilt where photons arrived, tables,
+sampling, evaluation); `--mis` samples and evaluates the BSDF/guide mixture.
 
 Prints one JSON line.  `value` = guided samples per second over whole steps
 (Q x steps / device time of the steps, inputs resident in HBM); `e2e` = the
@@ -532,6 +535,196 @@ def run_serve(args, tr):
     print(json.dumps(out), flush=True)
 
 
+PROGRESS_FRAC_BITS = 24  # fixed point of the progressive sums: room for ~60M photons of power <= 500
+
+
+def run_progressive(args, wl, prec):
+    """One step = one later iteration of the progressive form (Sec. 7.2;
+    Algorithm 1): a batch of wl.n_photons photons binned into the fixed grid
+    and merged, the maps of the leaves that received photons reconstructed,
+    the tables rebuilt, then Q guided samples and Q pdf evaluations.  The
+    grid is refined beforehand, untimed, by two iterations of N_p and 2 N_p
+    photons (N_p = wl.n_photons / 4, so that the timed batch is iteration
+    2's, 2^2 N_p) with threshold 500 sqrt(2^t) (Sec. 8)."""
+    import torch
+
+    from paper_2010_01775_gb300 import pg, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n, q, H, W = wl.n_photons, wl.n_queries, wl.H, wl.W
+    n_p = n // 4
+    pool = synth.photons(3 * n_p + 2 * n, wl.n_blobs, wl.seed)
+    refine = [pool[:n_p], pool[n_p:3 * n_p]]
+    batches = [pool[3 * n_p:3 * n_p + n], pool[3 * n_p + n:]]  # timed steps alternate between two batches
+    _, pos, dirs, blob = synth.workload_inputs(wl)
+    steps_total = args.warmup + args.steps + 8
+    max_photons = 3 * n_p + n * steps_total
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = pg.Context(stream.cuda_stream)
+    net = pg.pg_net_load(ctx, blob)
+    st = pg.pg_progress_create(ctx, LO, HI, wl.max_depth, wl.min_depth, H, W, max_photons, split_c=500.0,
+                               refine_iterations=2, frac_bits=PROGRESS_FRAC_BITS)
+    for b in refine:
+        pg.pg_progress_add_photons(ctx, st, torch.from_numpy(b).cuda(), len(b))
+    d_b = [torch.from_numpy(b).cuda() for b in batches]
+    d_pos = torch.from_numpy(pos).cuda()
+    d_dir = torch.from_numpy(dirs).cuda()
+    o_d, o_p = torch.empty(q, 3, device="cuda"), torch.empty(q, device="cuda")
+    o_l, o_e = torch.empty(q, dtype=torch.int32, device="cuda"), torch.empty(q, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    _, h0, _, _ = pg.pg_progress_view(st)
+    if args.load_tuning:
+        pg.pg_net_set_tuning(net, np.load(args.load_tuning))
+    elif args.autotune:
+        pg.pg_autotune(ctx, h0, net, prec)
+    pg.pg_progress_reconstruct(ctx, st, net, prec)
+    ctx.sync()
+    counter = [0]
+
+    def step(marks=None, batch=None, p_pos=d_pos, p_dir=d_dir, outs=(o_d, o_p, o_l, o_e)):
+        rec = (lambda i: marks[i].record(stream)) if marks is not None else (lambda i: None)
+        b = batch if batch is not None else d_b[counter[0] % 2]
+        counter[0] += 1
+        rec(0)
+        pg.pg_progress_add_photons(ctx, st, b, n)
+        rec(1)
+        pg.pg_progress_reconstruct(ctx, st, net, prec)
+        rec(2)
+        g, _, _, t = pg.pg_progress_view(st)
+        pg.pg_sample_dirs(ctx, g, t, p_pos, q, 20101775, 0, outs[0], outs[1], outs[2])
+        rec(3)
+        pg.pg_eval_pdf(ctx, g, t, p_pos, p_dir, q, outs[3])
+        rec(4)
+        return st.info(pg.PG_INFO_N_UPDATED), g.info(pg.PG_INFO_N_LEAVES)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    launches0 = ctx.launch_count()
+    times, stage, upd = [], np.zeros(4), []
+    for _ in range(args.steps):
+        flush.zero_()
+        marks = [ev() for _ in range(5)]
+        A, L = step(marks)
+        marks[4].synchronize()
+        times.append(marks[0].elapsed_time(marks[4]))
+        stage += [marks[i].elapsed_time(marks[i + 1]) for i in range(4)]
+        upd.append(A)
+    ctx.sync()
+    torch.cuda.synchronize()
+    launches = (ctx.launch_count() - launches0) // args.steps
+    clk = clocks.stop()
+    total_ms = max_over_ranks(float(sum(times)), world)
+    if world > 1:
+        torch.distributed.barrier()
+    stage_ms = dict(zip(["bin_merge", "reconstruct_cdf", "sample", "eval"], (stage / args.steps).round(4).tolist()))
+
+    # End to end: the batch and the queries from pinned host memory, results back.
+    h_b = torch.from_numpy(batches[0]).pin_memory()
+    h_pos, h_dir = torch.from_numpy(pos).pin_memory(), torch.from_numpy(dirs).pin_memory()
+    h_outs = (torch.empty(q, 3).pin_memory(), torch.empty(q).pin_memory(),
+              torch.empty(q, dtype=torch.int32).pin_memory(), torch.empty(q).pin_memory())
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step(batch=h_b, p_pos=h_pos, p_dir=h_dir, outs=h_outs)
+        ctx.sync()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+
+    # Dominant kernels: the CNN of one reconstruct of the updated leaves.
+    flops_leaf = unet_flops_per_leaf(H, W, wl.widths, wl.arch)
+    peaks, peak_src = load_peaks()
+    A_mean = float(np.mean(upd))
+    cnn_ms = stage_ms["reconstruct_cdf"]
+    peak = peaks["bf16_tflops"] * (2.0 if prec == pg.PG_FP8_E4M3 else 1.0)
+    achieved = flops_leaf * A_mean / (cnn_ms / 1e3) / 1e12
+    st.free()
+    ctx.destroy()
+    value = whole_job_rate(q, args.steps, world, total_ms)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec],
+            "data": "synthetic (seeded photon blobs on room walls, vMF directions, lognormal power; random He-init U-Net)",
+            "config": {"workload": "progressive iteration, " + wl.name, "photons_per_iteration": n,
+                       "refine": f"2 iterations of {n_p} and {2 * n_p} photons, threshold 500 sqrt(2^t)",
+                       "queries": q, "H": H, "W": W, "max_depth": wl.max_depth, "leaves": L,
+                       "updated_leaves_per_step": A_mean, "frac_bits": PROGRESS_FRAC_BITS,
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
+            "leaf_tables_per_s": A_mean * args.steps * world / (total_ms / 1e3),
+            "stage_ms": stage_ms,
+            "e2e": {"value": q / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(batches[0].nbytes + pos.nbytes + dirs.nbytes),
+                    "d2h_bytes_per_step": int(q * (12 + 4 + 4 + 4))},
+            "gpu_launches": launches,
+            "roofline": {"bound": "tensor" if prec != pg.PG_FP32 else "alu", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "CNN convolutions + CDF of one progressive reconstruct (stage time)",
+                         "peak_source": "of " + peak_src},
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = progressive_cpu_baseline(wl, args.cpu_sample_leaves)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def progressive_cpu_baseline(wl, n_leaves, n_batch=262_144, n_queries=262_144):
+    """The oracle's later iteration on a bounded sample: refinement on the
+    same N_p and 2 N_p photons (untimed), then a batch of n_batch photons
+    binned and merged, n_leaves of the updated leaves reconstructed, the
+    tables built, n_queries sampled and evaluated; per-stage times scaled to
+    the full step."""
+    from oracle import oracle as O
+    from paper_2010_01775_gb300 import synth
+    n = wl.n_photons
+    n_p = n // 4
+    n_batch, n_queries = min(n_batch, n), min(n_queries, wl.n_queries)
+    pool = synth.photons(3 * n_p + 2 * n, wl.n_blobs, wl.seed)
+    _, pos, dirs, blob = synth.workload_inputs(wl)
+    pr = O.Progressive(LO, HI, wl.max_depth, wl.min_depth, wl.H, wl.W, 3 * n_p + n, split_c=500.0,
+                       refine_iterations=2, F=PROGRESS_FRAC_BITS)
+    pr.add_photons(pool[:n_p])
+    pr.add_photons(pool[n_p:3 * n_p])
+    net = O.parse_net(blob)
+    t0 = time.perf_counter()
+    pr.add_photons(pool[3 * n_p:3 * n_p + n_batch])
+    t1 = time.perf_counter()
+    upd = pr.updated
+    keep = upd[np.linspace(0, upd.size - 1, n_leaves).astype(np.int64)]
+    y = O.cnn_forward(O.assemble_inputs(pr.planes(keep)), net)
+    t2 = time.perf_counter()
+    tabs = O.tables_from_map(y)
+    t3 = time.perf_counter()
+    slot = np.full(pr.grid["L"], -1, np.int32)
+    slot[keep] = np.arange(keep.size, dtype=np.int32)
+    O.sample(pr.grid, slot, tabs, pos[:n_queries], 20101775)
+    O.eval_pdf(pr.grid, slot, tabs, pos[:n_queries], dirs[:n_queries])
+    t4 = time.perf_counter()
+    full_leaf, _ = O.leaf_of_positions(pr.grid, pool[3 * n_p:3 * n_p + n, :3])
+    A_full = np.unique(full_leaf).size  # leaves a full batch updates
+    step_s = (t1 - t0) * n / n_batch + (t3 - t1) * A_full / keep.size + (t4 - t3) * wl.n_queries / n_queries
+    return {"value": wl.n_queries / step_s, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle, single thread, progressive later iteration: {n_batch} of {n} photons binned "
+                       f"and merged, CNN+CDF on {keep.size} of ~{int(A_full)} updated leaves, sample+eval on "
+                       f"{n_queries} of {wl.n_queries} queries; per-stage times scaled to the full step "
+                       f"({step_s:.1f} s); wall {t4 - t0:.1f} s")}
+
+
 def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False):
     """The FP64 oracle on a bounded sample; returns per-stage seconds and the
     throughput extrapolated to the full workload."""
@@ -645,6 +838,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--experts", type=int, default=0,
                     help="reconstruct with a mixture of this many experts routed by leaf photon count (Sec. 8)")
+    ap.add_argument("--progressive", action="store_true",
+                    help="time one later iteration of the progressive form (Sec. 7.2) instead of a single-shot step")
     ap.add_argument("--mis", action="store_true",
                     help="sample and evaluate one-sample MIS of a Lambertian BSDF and the guide (Sec. 7.3), "
                          "with the per-leaf statistics and alpha update in every step")
@@ -679,7 +874,10 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2010_01775_gb300 import pg
-    run_pg(args, wl, pg.PRECISIONS[args.precision])
+    if args.progressive:
+        run_progressive(args, wl, pg.PRECISIONS[args.precision])
+    else:
+        run_pg(args, wl, pg.PRECISIONS[args.precision])
 
 
 if __name__ == "__main__":
