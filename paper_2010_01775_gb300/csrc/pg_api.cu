@@ -1150,18 +1150,9 @@ pg_status pg_progress_add_photons(pg_ctx *c, pg_progress *sp, const pg_photon *d
     Grid view;
     void *scr = nullptr;
     size_t sb = 0;
-    Hist batch;
-    memset(&batch, 0, sizeof(batch));
-    batch.H = s->p.H;
-    batch.W = s->p.W;
     pg_status st = bin_into_grid(c, s->grid, (const pg_photon *)ph.dev, n, &view, &scr, &sb);
-    if (st == PG_OK && view.A) {
-      batch.A = view.A;
-      st = splat(c, &view, (const pg_photon *)ph.dev, s->p.max_photons, 0, s->p.frac_bits, &batch);
-      if (st == PG_OK) st = merge_batch(c, &batch, view.active, s->cum);
-    }
+    if (st == PG_OK) st = splat_merge(c, &view, (const pg_photon *)ph.dev, s->p.max_photons, s->p.frac_bits, s->cum);
     if (st == PG_OK) st = progress_updated(c, s, view.active, view.A);
-    ctx_free(c, batch.block, batch.h.bytes);
     ctx_free(c, scr, sb);
     if (st != PG_OK) return st;
   }

@@ -345,10 +345,13 @@ pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint6
 pg_status hist_alloc(pg_ctx *ctx, Hist *h, uint32_t A, int H, int W);  // zeroed planes
 // dst[d_active[a]] = src[a] (all planes); dst is leaf-indexed.
 pg_status rows_to_leaves(pg_ctx *ctx, const Hist *src, const uint32_t *d_active, Hist *dst);
-// For a = 0..batch->A-1, leaf l = d_active[a]: prev[l] = cur[l]; cur[l] += batch[a].
-pg_status merge_batch(pg_ctx *ctx, const Hist *batch, const uint32_t *d_active, Hist *cum);
 pg_status identity_slots(pg_ctx *ctx, Grid *g);  // slot_of_leaf[l] = active[l] = l, A = L
 // splat.cu
+// A batch binned into a fixed grid (view from bin_into_grid) and merged into
+// leaf-indexed sums: for every leaf l of the view's active list, prev[l] =
+// cur[l], then cur[l] += the leaf's batch histogram (planes and totals).
+// n_bound sets the fixed-point bound (2^63 - 1) / n_bound.
+pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint64_t n_bound, int F, Hist *cum);
 pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h,
                 const uint32_t *d_scene_nprev = nullptr);
 // cnn.cu

@@ -2,8 +2,10 @@
 // doubling size arrive one iteration at a time.  Every leaf keeps its energy
 // and count maps summed over all iterations so far and, for the network's
 // previous-iteration channels, the sums as they stood before the last
-// iteration that brought it photons.  These kernels move those leaf-indexed
-// planes; the iteration logic is in the C ABI layer.
+// iteration that brought it photons.  These kernels lay out those
+// leaf-indexed planes after a refining iteration (the merge of a later batch
+// is the splat kernel's merge mode); the iteration logic is in the C ABI
+// layer.
 #include "pg_internal.cuh"
 
 namespace pgi {
@@ -31,30 +33,6 @@ __global__ void k_rows_to_leaves(const uint64_t *__restrict__ spc, const uint32_
   if (threadIdx.x == 0) {
     dtc[l] = stc[a];
     dtp[l] = stp[a];
-  }
-}
-
-// A later iteration's batch, binned per leaf (rows in the order of active):
-// the leaf's previous planes become its current sums, then the batch is
-// added to the current sums.
-__global__ void k_merge_batch(const uint64_t *__restrict__ bpow, const uint32_t *__restrict__ bcnt,
-                              const uint64_t *__restrict__ btot, const uint32_t *__restrict__ active, int HW,
-                              uint64_t *__restrict__ pc, uint32_t *__restrict__ cc, uint64_t *__restrict__ pp,
-                              uint32_t *__restrict__ cp, uint64_t *__restrict__ tc, uint64_t *__restrict__ tp) {
-  const uint32_t a = blockIdx.x, l = active[a];
-  const size_t s0 = (size_t)a * HW, d0 = (size_t)l * HW;
-  for (int k = threadIdx.x; k < HW; k += blockDim.x) {
-    const uint64_t p = pc[d0 + k];
-    const uint32_t c = cc[d0 + k];
-    pp[d0 + k] = p;
-    cp[d0 + k] = c;
-    pc[d0 + k] = p + bpow[s0 + k];
-    cc[d0 + k] = c + bcnt[s0 + k];
-  }
-  if (threadIdx.x == 0) {
-    const uint64_t t = tc[l];
-    tp[l] = t;
-    tc[l] = t + btot[a];
   }
 }
 
@@ -92,15 +70,6 @@ pg_status rows_to_leaves(pg_ctx *ctx, const Hist *src, const uint32_t *d_active,
                                                     src->tot_cur, src->tot_prev, d_active, src->H * src->W,
                                                     dst->pow_cur, dst->cnt_cur, dst->pow_prev, dst->cnt_prev,
                                                     dst->tot_cur, dst->tot_prev), PG_COUNT(ctx);
-  PG_CUDA(cudaGetLastError());
-  return PG_OK;
-}
-
-pg_status merge_batch(pg_ctx *ctx, const Hist *batch, const uint32_t *d_active, Hist *cum) {
-  if (batch->A == 0) return PG_OK;
-  k_merge_batch<<<batch->A, 256, 0, ctx->stream>>>(batch->pow_cur, batch->cnt_cur, batch->tot_cur, d_active,
-                                                   batch->H * batch->W, cum->pow_cur, cum->cnt_cur, cum->pow_prev,
-                                                   cum->cnt_prev, cum->tot_cur, cum->tot_prev), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
   return PG_OK;
 }

@@ -26,7 +26,10 @@ __device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, uint32_
                : "memory");
 }
 
-// kMode 0: all four planes; 1: current planes only; 2: previous planes only.
+// kMode 0: all four planes; 1: current planes only; 2: previous planes only;
+// 3: merge into leaf-indexed running sums (progressive iterations): the
+// leaf's previous planes take its current sums, and the current planes add
+// this batch.
 template <int kMode>
 __global__ void __launch_bounds__(kSplatThreads) k_splat(
     const pg_photon *__restrict__ ph, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ active,
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
           atomicAdd(&s_pow[HW + bin], gsum_p);
           atomicAdd(&s_cnt[HW + bin], gsum_p_cnt);
         }
-      } else if (kMode == 1) {
+      } else if (kMode == 1 || kMode == 3) {
         atomicAdd(&s_pow[bin], gsum);
         atomicAdd(&s_cnt[bin], gcnt);
       } else {
@@ -146,6 +149,34 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
   }
   if (bad) atomicOr(status, bad);
   __syncthreads();
+
+  if (kMode == 3) {
+    // Read-modify-write of the leaf's rows, coalesced; totals likewise.
+    const size_t o = (size_t)leaf * HW;
+    unsigned long long t_add = 0;
+    for (int k = tid; k < HW; k += kSplatThreads) {
+      const unsigned long long add = s_pow[k];
+      const unsigned long long p0 = pow_cur[o + k];
+      const uint32_t c0 = cnt_cur[o + k];
+      pow_prev[o + k] = p0;
+      cnt_prev[o + k] = c0;
+      pow_cur[o + k] = p0 + add;
+      cnt_cur[o + k] = c0 + s_cnt[k];
+      t_add += add;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) t_add += __shfl_xor_sync(0xFFFFFFFFu, t_add, off);
+    if (lane == 0) s_tot[0][tid >> 5] = t_add;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long a = 0;
+      for (int w = 0; w < kSplatThreads / 32; ++w) a += s_tot[0][w];
+      const unsigned long long t0 = tot_cur[leaf];
+      tot_prev[leaf] = t0;
+      tot_cur[leaf] = t0 + a;
+    }
+    return;
+  }
 
   // Flush: the finished planes leave shared memory as bulk asynchronous
   // copies issued by one thread, so the CTA can retire (and the next leaf's
@@ -197,6 +228,23 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
+
+pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint64_t n_bound, int F, Hist *cum) {
+  if (view->A == 0) return PG_OK;
+  const size_t HW = (size_t)cum->H * cum->W;
+  const float *tab;
+  PG_TRY(phi_table(ctx, cum->W, &tab));
+  const float two_f = ldexpf(1.0f, F);
+  const uint64_t limit = n_bound ? (uint64_t)INT64_MAX / n_bound : 0;
+  const size_t smem = 12 * HW + 8 * (size_t)cum->W;
+  PG_CUDA(cudaFuncSetAttribute(k_splat<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_splat<3><<<(unsigned)view->A, kSplatThreads, smem, ctx->stream>>>(
+      d_ph, view->perm, view->active, view->leaf_begin, view->leaf_end, 0u, cum->H, cum->W, two_f, limit, tab,
+      cum->pow_cur, cum->cnt_cur, cum->pow_prev, cum->cnt_prev, cum->tot_cur, cum->tot_prev, ctx->d_status,
+      view->leaf_code, view->scene_begin, nullptr, 3 * view->D), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
+}
 
 pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h,
                 const uint32_t *d_scene_nprev) {
