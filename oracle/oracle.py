@@ -79,6 +79,8 @@ def lib():
         L.or_sample.argtypes = [P, i64, P, P, i32, P, i64, P, i32, i32, P, P, P, P, u64, u32,
                                 P, P, P, P]
         L.or_eval_pdf.argtypes = [P, P, i64, P, P, i32, P, i64, P, i32, i32, P, P, P]
+        L.or_sample_leaves.argtypes = [P, i64, P, i32, i32, P, P, P, P, u64, u32, P, P, P, P]
+        L.or_eval_pdf_leaves.argtypes = [P, P, i64, P, i32, i32, P, P, P]
     return _lib
 
 
@@ -139,6 +141,151 @@ def active_leaves(grid):
     slot = np.full(grid["L"], -1, np.int32)
     slot[act] = np.arange(act.size, dtype=np.int32)
     return act, slot
+
+
+# --------------------------------------------------------------------------
+# The paper's grid rule (Sec. 7.1 "An initial regular grid" and "Voxel
+# subdivision"; Sec. 8: a 100^3 regular grid, local binary trees of depth at
+# most 8, V_thr = 0.5): every voxel of a regular R^3 grid holds a binary tree
+# whose nodes split at the median photon position along one axis while the
+# node has more than M_thr photons or its normal variance exceeds V_thr.
+# --------------------------------------------------------------------------
+KD_NORMAL_BITS = 20  # normals enter the variance as round_half_even(n * 2^20)
+
+
+def kd_scale(lo, hi, R):
+    """Cells per unit length, fl32(R / (hi - lo)) formed in double."""
+    return np.array([np.float32(R / (float(hi[a]) - float(lo[a]))) for a in range(3)], np.float32)
+
+
+def kd_cells(pos, lo, hi, R):
+    """Voxel of each position: per axis q = clamp(floor(fl32(fl32(x - lo) *
+    s)), 0, R - 1) (the a1 rule with R cells), cell = qx + R (qy + R qz).
+    Returns (cells int64, invalid-input flag)."""
+    pos = _f32(pos)
+    lo32 = _f32(lo)
+    t = (pos - lo32) * kd_scale(lo, hi, R)  # two IEEE FP32 roundings
+    bad = ~np.isfinite(pos).all(axis=1)
+    q = np.floor(np.where(np.isfinite(t), t, 0.0)).clip(0, R - 1).astype(np.int64)
+    q[bad] = 0
+    return q[:, 0] + R * (q[:, 1] + R * q[:, 2]), bool(bad.any())
+
+
+def kd_normal_variance(S, m):
+    """V = 1 - |mean normal|^2 from fixed-point sums S (Python ints) of m unit
+    normals, in double with this exact operation order."""
+    a, b, c = float(S[0]), float(S[1]), float(S[2])
+    r = (a * a + b * b) + c * c
+    mm = (float(m) * float(m)) * 2.0 ** (2 * KD_NORMAL_BITS)
+    return 1.0 - r / mm
+
+
+def build_kd_grid(photons, normals, lo, hi, R, max_depth, thr, vthr):
+    """Regular grid + one binary tree per voxel, built level by level.
+
+    A node of m photons at depth d splits when d < max_depth, m >= 2, its
+    photons are not all at one coordinate along the axis of largest spread
+    (max - min in FP32, first axis on ties), and m > thr or V > vthr (V = 0
+    without normals).  Split value: the floor(m/2)-th smallest coordinate s
+    (0-based); the left child holds x < tau with tau = s, or tau = the next
+    float above s when no coordinate is below s.  Children keep the photons'
+    order (a stable partition).
+
+    Node numbering: nodes 0 .. R^3-1 are the voxels' roots; each level's
+    children follow, two per splitting node in the order of their parents.
+    Leaves are numbered depth-first (left first) in voxel order, so their
+    photon ranges in `perm` ascend.  node_link is the left child's index
+    (right = left + 1) for an internal node and ~leaf for a leaf."""
+    ph = _f32(photons)
+    n = ph.shape[0]
+    cells, bad = kd_cells(ph[:, :3], lo, hi, R)
+    if bad:
+        raise ValueError("non-finite photon position")
+    nfx = None
+    if normals is not None:
+        nfx = np.rint(_f32(normals).astype(np.float64) * 2.0 ** KD_NORMAL_BITS).astype(np.int64)
+    perm = np.argsort(cells, kind="stable").astype(np.int64)
+    C = R ** 3
+    cnt = np.bincount(cells, minlength=C)
+    end = np.cumsum(cnt)
+    begin = [int(v) for v in end - cnt]
+    end = [int(v) for v in end]
+    axis = [0] * C
+    tau = [0.0] * C
+    link = [-1] * C
+    depth = [0] * C
+    level = list(range(C))
+    d = 0
+    while level:
+        nxt = []
+        for v in level:
+            b, e = begin[v], end[v]
+            m = e - b
+            if d >= max_depth or m < 2:
+                continue
+            idx = perm[b:e]
+            P = ph[idx, :3]
+            spread = P.max(axis=0) - P.min(axis=0)  # FP32
+            a = int(np.argmax(spread))
+            if not spread[a] > 0:
+                continue
+            V = kd_normal_variance(nfx[idx].sum(axis=0).tolist(), m) if nfx is not None else 0.0
+            if not (m > thr or V > vthr):
+                continue
+            x = P[:, a]
+            s = np.sort(x)[m // 2]
+            t = s if (x < s).any() else np.nextafter(s, np.float32(np.inf))
+            left = x < t
+            perm[b:e] = np.concatenate([idx[left], idx[~left]])
+            nl = int(left.sum())
+            child = len(begin)
+            axis[v], tau[v], link[v] = a, float(t), child
+            begin += [b, b + nl]
+            end += [b + nl, e]
+            axis += [0, 0]
+            tau += [0.0, 0.0]
+            link += [-1, -1]
+            depth += [d + 1, d + 1]
+            nxt += [child, child + 1]
+        level = nxt
+        d += 1
+    # Leaves depth-first, left first, voxel by voxel.
+    leaf_cell, leaf_depth, leaf_begin, leaf_end = [], [], [], []
+    for c in range(C):
+        stack = [c]
+        while stack:
+            v = stack.pop()
+            if link[v] >= 0:
+                stack += [link[v] + 1, link[v]]
+            else:
+                link[v] = ~len(leaf_cell)
+                leaf_cell.append(c)
+                leaf_depth.append(depth[v])
+                leaf_begin.append(begin[v])
+                leaf_end.append(end[v])
+    L = len(leaf_cell)
+    leaf_of = np.zeros(n, np.uint32)
+    for l in range(L):
+        leaf_of[perm[leaf_begin[l]:leaf_end[l]]] = l
+    return dict(kd=True, R=R, lo=_f32(lo), hi=_f32(hi), n=n, cells=cells, perm=perm.astype(np.uint32),
+                leaf_of=leaf_of, L=L, leaf_cell=np.array(leaf_cell, np.uint32),
+                leaf_depth=np.array(leaf_depth, np.int32), leaf_begin=np.array(leaf_begin, np.uint32),
+                leaf_end=np.array(leaf_end, np.uint32), node_axis=np.array(axis, np.uint8),
+                node_tau=np.array(tau, np.float32), node_link=np.array(link, np.int32))
+
+
+def kd_locate(grid, pos):
+    """Leaf of each position: its voxel's root, then left when x[axis] < tau."""
+    pos = _f32(pos)
+    cells, bad = kd_cells(pos, grid["lo"], grid["hi"], grid["R"])
+    link, ax, tau = grid["node_link"], grid["node_axis"], grid["node_tau"]
+    out = np.zeros(pos.shape[0], np.int64)
+    for i in range(pos.shape[0]):
+        v = int(cells[i])
+        while link[v] >= 0:
+            v = int(link[v]) + (0 if pos[i, ax[v]] < tau[v] else 1)
+        out[i] = ~int(link[v])
+    return out, bad
 
 
 # --------------------------------------------------------------------------
@@ -374,6 +521,12 @@ def sample(grid, slot_of_leaf, tables, pos, seed, stream=0):
     leaf = np.zeros(q, np.uint32)
     binv = np.zeros(q, np.uint32)
     slot = np.ascontiguousarray(slot_of_leaf, np.int32)
+    if grid.get("kd"):
+        lq = np.ascontiguousarray(kd_locate(grid, pos)[0], np.int64)
+        lib().or_sample_leaves(_p(lq), q, _p(slot), tables["H"], tables["W"], _p(tables["P"]), _p(tables["fz"]),
+                               _p(tables["fphi"]), _p(tables["valid"]), seed, stream, _p(dirs), _p(pdf), _p(leaf),
+                               _p(binv))
+        return dict(dir=dirs, pdf=pdf, leaf=leaf, bin=binv)
     lib().or_sample(_p(pos), q, _p(grid["lo"]), _p(grid["hi"]), grid["D"], _p(grid["leaf_code"]),
                     grid["L"], _p(slot), tables["H"], tables["W"], _p(tables["P"]), _p(tables["fz"]),
                     _p(tables["fphi"]), _p(tables["valid"]), seed, stream, _p(dirs), _p(pdf),
@@ -387,6 +540,11 @@ def eval_pdf(grid, slot_of_leaf, tables, pos, dirs):
     q = pos.shape[0]
     pdf = np.zeros(q, np.float64)
     slot = np.ascontiguousarray(slot_of_leaf, np.int32)
+    if grid.get("kd"):
+        lq = np.ascontiguousarray(kd_locate(grid, pos)[0], np.int64)
+        lib().or_eval_pdf_leaves(_p(lq), _p(d), q, _p(slot), tables["H"], tables["W"], _p(tables["P"]),
+                                 _p(tables["valid"]), _p(pdf))
+        return pdf
     lib().or_eval_pdf(_p(pos), _p(d), q, _p(grid["lo"]), _p(grid["hi"]), grid["D"],
                       _p(grid["leaf_code"]), grid["L"], _p(slot), tables["H"], tables["W"],
                       _p(tables["P"]), _p(tables["valid"]), _p(pdf))

@@ -355,50 +355,76 @@ static int64_t leaf_of_code(const uint64_t *leaf_code, int64_t L, uint64_t code)
   return lo - 1;
 }
 
+/* Query t in leaf `leaf`: the guided sample of its map, or the uniform
+ * fallback when the leaf has no valid map. */
+static void sample_one(int64_t t, int64_t leaf, const int32_t *slot_of_leaf, int H, int W, const double *P,
+                       const float *Fz, const float *Fphi, const uint8_t *valid, uint64_t seed, uint32_t stream,
+                       double *dir, double *pdf, uint32_t *leaf_out, uint32_t *bin_out) {
+  const double inv24 = ldexp(1.0, -24);
+  int64_t HW = (int64_t)H * W;
+  int32_t slot = slot_of_leaf[leaf];
+  uint32_t ctr[4] = {(uint32_t)t, (uint32_t)((uint64_t)t >> 32), stream, 0};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  or_philox4x32_10(ctr, key, r);
+  double u[4];
+  for (int k = 0; k < 4; ++k) u[k] = (double)(r[k] >> 8) * inv24;
+  double z, phi;
+  if (slot < 0 || !valid[slot]) {
+    z = 1.0 - 2.0 * u[0];
+    phi = 2.0 * M_PI * u[1];
+    pdf[t] = 1.0 / (4.0 * M_PI);
+    leaf_out[t] = (uint32_t)leaf | 0x80000000u;
+    bin_out[t] = 0xFFFFFFFFu;
+  } else {
+    const float *fz = Fz + (int64_t)slot * H;
+    int i = 0;
+    while (i < H - 1 && !((float)u[0] < fz[i])) ++i;
+    const float *fp = Fphi + (int64_t)slot * HW + (int64_t)i * W;
+    int j = 0;
+    while (j < W - 1 && !((float)u[1] < fp[j])) ++j;
+    z = -1.0 + 2.0 * ((double)i + u[2]) / (double)H;
+    phi = 2.0 * M_PI * ((double)j + u[3]) / (double)W;
+    pdf[t] = P[(int64_t)slot * HW + (int64_t)i * W + j] * (double)HW / (4.0 * M_PI);
+    leaf_out[t] = (uint32_t)leaf;
+    bin_out[t] = (uint32_t)(i * W + j);
+  }
+  double st = sqrt(fmax(0.0, 1.0 - z * z));
+  dir[3 * t + 0] = st * cos(phi);
+  dir[3 * t + 1] = st * sin(phi);
+  dir[3 * t + 2] = z;
+}
+
 void or_sample(const float *pos, int64_t q, const float lo[3], const float hi[3], int D,
                const uint64_t *leaf_code, int64_t L, const int32_t *slot_of_leaf, int H, int W,
                const double *P, const float *Fz, const float *Fphi, const uint8_t *valid, uint64_t seed,
                uint32_t stream, double *dir, double *pdf, uint32_t *leaf_out, uint32_t *bin_out) {
   float s[3];
   or_axis_scale(lo, hi, D, s);
-  const double inv24 = ldexp(1.0, -24);
-  int64_t HW = (int64_t)H * W;
   for (int64_t t = 0; t < q; ++t) {
     uint32_t qq[3];
     for (int a = 0; a < 3; ++a) quantise(pos[3 * t + a], lo[a], s[a], D, &qq[a]);
     int64_t leaf = leaf_of_code(leaf_code, L, or_morton3(qq[0], qq[1], qq[2], D));
-    int32_t slot = slot_of_leaf[leaf];
-    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)((uint64_t)t >> 32), stream, 0};
-    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    uint32_t r[4];
-    or_philox4x32_10(ctr, key, r);
-    double u[4];
-    for (int k = 0; k < 4; ++k) u[k] = (double)(r[k] >> 8) * inv24;
-    double z, phi;
-    if (slot < 0 || !valid[slot]) {
-      z = 1.0 - 2.0 * u[0];
-      phi = 2.0 * M_PI * u[1];
-      pdf[t] = 1.0 / (4.0 * M_PI);
-      leaf_out[t] = (uint32_t)leaf | 0x80000000u;
-      bin_out[t] = 0xFFFFFFFFu;
-    } else {
-      const float *fz = Fz + (int64_t)slot * H;
-      int i = 0;
-      while (i < H - 1 && !((float)u[0] < fz[i])) ++i;
-      const float *fp = Fphi + (int64_t)slot * HW + (int64_t)i * W;
-      int j = 0;
-      while (j < W - 1 && !((float)u[1] < fp[j])) ++j;
-      z = -1.0 + 2.0 * ((double)i + u[2]) / (double)H;
-      phi = 2.0 * M_PI * ((double)j + u[3]) / (double)W;
-      pdf[t] = P[(int64_t)slot * HW + (int64_t)i * W + j] * (double)HW / (4.0 * M_PI);
-      leaf_out[t] = (uint32_t)leaf;
-      bin_out[t] = (uint32_t)(i * W + j);
-    }
-    double st = sqrt(fmax(0.0, 1.0 - z * z));
-    dir[3 * t + 0] = st * cos(phi);
-    dir[3 * t + 1] = st * sin(phi);
-    dir[3 * t + 2] = z;
+    sample_one(t, leaf, slot_of_leaf, H, W, P, Fz, Fphi, valid, seed, stream, dir, pdf, leaf_out, bin_out);
   }
+}
+
+/* The same for queries whose leaves are given (any grid form). */
+void or_sample_leaves(const int64_t *leaf, int64_t q, const int32_t *slot_of_leaf, int H, int W, const double *P,
+                      const float *Fz, const float *Fphi, const uint8_t *valid, uint64_t seed, uint32_t stream,
+                      double *dir, double *pdf, uint32_t *leaf_out, uint32_t *bin_out) {
+  for (int64_t t = 0; t < q; ++t)
+    sample_one(t, leaf[t], slot_of_leaf, H, W, P, Fz, Fphi, valid, seed, stream, dir, pdf, leaf_out, bin_out);
+}
+
+/* p_guide of direction t in leaf `leaf` (1/4pi without a valid map). */
+static double eval_one(int64_t leaf, const float *d, const int32_t *slot_of_leaf, int H, int W, const double *P,
+                       const uint8_t *valid, const float *c, const float *sn) {
+  int32_t slot = slot_of_leaf[leaf];
+  if (slot < 0 || !valid[slot]) return 1.0 / (4.0 * M_PI);
+  int row, col;
+  or_dir_bin(d[0], d[1], d[2], H, W, c, sn, &row, &col);
+  return P[(int64_t)slot * H * W + (int64_t)row * W + col] * (double)H * W / (4.0 * M_PI);
 }
 
 void or_eval_pdf(const float *pos, const float *dirs, int64_t q, const float lo[3], const float hi[3],
@@ -408,17 +434,21 @@ void or_eval_pdf(const float *pos, const float *dirs, int64_t q, const float lo[
   or_axis_scale(lo, hi, D, s);
   float *c = (float *)malloc(sizeof(float) * W), *sn = (float *)malloc(sizeof(float) * W);
   or_phi_table(W, c, sn);
-  int64_t HW = (int64_t)H * W;
   for (int64_t t = 0; t < q; ++t) {
     uint32_t qq[3];
     for (int a = 0; a < 3; ++a) quantise(pos[3 * t + a], lo[a], s[a], D, &qq[a]);
     int64_t leaf = leaf_of_code(leaf_code, L, or_morton3(qq[0], qq[1], qq[2], D));
-    int32_t slot = slot_of_leaf[leaf];
-    if (slot < 0 || !valid[slot]) { pdf[t] = 1.0 / (4.0 * M_PI); continue; }
-    int row, col;
-    or_dir_bin(dirs[3 * t], dirs[3 * t + 1], dirs[3 * t + 2], H, W, c, sn, &row, &col);
-    pdf[t] = P[(int64_t)slot * HW + (int64_t)row * W + col] * (double)HW / (4.0 * M_PI);
+    pdf[t] = eval_one(leaf, dirs + 3 * t, slot_of_leaf, H, W, P, valid, c, sn);
   }
+  free(c);
+  free(sn);
+}
+
+void or_eval_pdf_leaves(const int64_t *leaf, const float *dirs, int64_t q, const int32_t *slot_of_leaf, int H,
+                        int W, const double *P, const uint8_t *valid, double *pdf) {
+  float *c = (float *)malloc(sizeof(float) * W), *sn = (float *)malloc(sizeof(float) * W);
+  or_phi_table(W, c, sn);
+  for (int64_t t = 0; t < q; ++t) pdf[t] = eval_one(leaf[t], dirs + 3 * t, slot_of_leaf, H, W, P, valid, c, sn);
   free(c);
   free(sn);
 }

@@ -707,3 +707,116 @@ def test_progressive_without_refinement_uses_the_regular_grid():
     for ph in _batches([300, 600], 34):
         pr.add_photons(ph)
     assert int(pr.cnt_cur.sum()) == 900 and pr.grid["L"] == 64
+
+
+# ---------------------------------------------------------------- the paper's grid rule (Sec. 7.1)
+def _kd_photons(xyz):
+    ph = np.zeros((len(xyz), 8), np.float32)
+    ph[:, :3] = xyz
+    ph[:, 5] = 1.0
+    ph[:, 6] = 1.0
+    return ph
+
+
+def test_kd_median_splits_hand_example():
+    ph = _kd_photons([[0.4, 0.5, 0.5], [0.1, 0.5, 0.5], [0.3, 0.5, 0.5], [0.2, 0.5, 0.5]])
+    g = O.build_kd_grid(ph, None, LO, HI, 1, 2, 1, 1.0)
+    # Root splits at the 2nd smallest x (0.3), each child at its 1st (0.2 and 0.4).
+    assert g["node_link"].tolist() == [1, 3, 5, ~0, ~1, ~2, ~3]
+    assert g["node_tau"][:3].tolist() == [np.float32(0.3), np.float32(0.2), np.float32(0.4)]
+    assert g["node_axis"][:3].tolist() == [0, 0, 0]
+    assert g["L"] == 4 and g["leaf_depth"].tolist() == [2, 2, 2, 2]
+    assert g["perm"].tolist() == [1, 3, 2, 0]  # leaves in x order
+    assert g["leaf_of"].tolist() == [3, 0, 2, 1]
+
+
+def test_kd_ties_go_left_and_flat_nodes_stay_leaves():
+    ph = _kd_photons([[0.2, 0.5, 0.5], [0.7, 0.5, 0.5], [0.2, 0.5, 0.5], [0.2, 0.5, 0.5]])
+    g = O.build_kd_grid(ph, None, LO, HI, 1, 8, 1, 1.0)
+    # The median (0.2) is the minimum: tau is the next float, so x <= 0.2 goes left.
+    assert g["node_tau"][0] == np.nextafter(np.float32(0.2), np.float32(1.0))
+    assert g["L"] == 2 and (g["leaf_end"] - g["leaf_begin"]).tolist() == [3, 1]
+
+
+def test_kd_normal_variance_hand_values():
+    u = 2 ** O.KD_NORMAL_BITS
+    assert O.kd_normal_variance([u, u, 0], 2) == 0.5
+    assert O.kd_normal_variance([u, u, u], 3) == pytest.approx(2 / 3, rel=1e-15)
+    assert O.kd_normal_variance([5 * u, 0, 0], 5) == 0.0
+    # Two photons on perpendicular walls: V = 0.5, not above V_thr = 0.5.
+    ph = _kd_photons([[0.2, 0.3, 0.5], [0.6, 0.7, 0.5]])
+    nrm = np.array([[1, 0, 0], [0, 1, 0]], np.float32)
+    assert O.build_kd_grid(ph, nrm, LO, HI, 1, 8, 100, 0.5)["L"] == 1
+    # Three photons on three perpendicular walls: V = 2/3 > 0.5 splits.
+    ph = _kd_photons([[0.2, 0.3, 0.5], [0.6, 0.7, 0.5], [0.9, 0.1, 0.5]])
+    nrm = np.eye(3, dtype=np.float32)
+    g = O.build_kd_grid(ph, nrm, LO, HI, 1, 8, 100, 0.5)
+    assert g["L"] > 1 and g["node_link"][0] >= 0
+
+
+def test_kd_without_splits_is_the_regular_grid():
+    R = 5
+    ph = synth.photons(3000, 4, 41)
+    g = O.build_kd_grid(ph, None, LO, HI, R, 8, 10 ** 9, 2.0)
+    assert g["L"] == R ** 3 and g["leaf_cell"].tolist() == list(range(R ** 3))
+    t = ph[:, :3].astype(np.float64) * R
+    far = np.all(np.abs(t - np.round(t)) > 1e-4, axis=1)
+    q = np.floor(t).astype(np.int64)
+    cell = q[:, 0] + R * (q[:, 1] + R * q[:, 2])
+    assert np.array_equal(g["leaf_of"][far], cell[far])
+
+
+def _kd_node_range(g, v):
+    link = int(g["node_link"][v])
+    if link < 0:
+        return int(g["leaf_begin"][~link]), int(g["leaf_end"][~link])
+    return _kd_node_range(g, link)[0], _kd_node_range(g, link + 1)[1]
+
+
+@pytest.mark.parametrize("n,R,depth,thr,normals,seed", [(4000, 3, 8, 40, False, 42), (3000, 2, 5, 60, True, 43),
+                                                         (2000, 4, 3, 10, True, 44)])
+def test_kd_grid_brute_properties(n, R, depth, thr, normals, seed):
+    ph = synth.photons(n, 6, seed)
+    nrm = None
+    if normals:  # a unit normal per photon, from a few directions
+        rng = np.random.default_rng(seed)
+        nrm = synth.uniform_sphere(rng, 5)[rng.integers(0, 5, n)].astype(np.float32)
+    g = O.build_kd_grid(ph, nrm, LO, HI, R, depth, thr, 0.5)
+    L = g["L"]
+    # Leaves partition the photons, in ascending ranges.
+    assert g["leaf_begin"][0] == 0 and g["leaf_end"][-1] == n
+    assert np.array_equal(g["leaf_begin"][1:], g["leaf_end"][:-1])
+    assert sorted(g["perm"].tolist()) == list(range(n))
+    # Locating a photon by descent finds the leaf that holds it.
+    loc, _ = O.kd_locate(g, ph[:, :3])
+    assert np.array_equal(loc, g["leaf_of"].astype(np.int64))
+    for l in range(L):
+        assert np.all(g["leaf_of"][g["perm"][g["leaf_begin"][l]:g["leaf_end"][l]]] == l)
+    # Every node against its photons: the split rule, the axis, the median.
+    u = 2 ** O.KD_NORMAL_BITS
+    nfx = np.rint(nrm.astype(np.float64) * u).astype(np.int64) if normals else None
+    stack = [(c, 0) for c in range(R ** 3)]
+    while stack:
+        v, d = stack.pop()
+        b, e = _kd_node_range(g, v)
+        idx = g["perm"][b:e]
+        P = ph[idx, :3]
+        m = e - b
+        spread = (P.max(axis=0) - P.min(axis=0)) if m else np.zeros(3, np.float32)
+        V = O.kd_normal_variance(nfx[idx].sum(axis=0).tolist(), m) if (normals and m) else 0.0
+        want = d < depth and m >= 2 and spread.max() > 0 and (m > thr or V > 0.5)
+        link = int(g["node_link"][v])
+        assert (link >= 0) == want, (v, d, m)
+        if link < 0:
+            continue
+        a = int(g["node_axis"][v])
+        assert spread[a] == spread.max() and np.all(spread[:a] < spread[a])
+        x = np.sort(P[:, a])
+        s = x[m // 2]
+        tau = g["node_tau"][v]
+        assert tau == (s if x[0] < s else np.nextafter(s, np.float32(np.inf)))
+        nl = int((P[:, a] < tau).sum())
+        assert 0 < nl < m and _kd_node_range(g, link) == (b, b + nl)
+        # The left part keeps the photons' order (a stable partition).
+        assert np.all(np.diff(np.nonzero(np.isin(g["perm"][b:e], idx[P[:, a] < tau]))[0]) == 1)
+        stack += [(link, d + 1), (link + 1, d + 1)]
