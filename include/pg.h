@@ -148,6 +148,39 @@ pg_status pg_budget_query(const pg_budget *b, uint64_t *in_use, uint64_t *capaci
 pg_status pg_build_grid(pg_ctx *ctx, const pg_photon *d_photons, uint64_t n,
                         const pg_grid_params *params, pg_grid **out);
 
+/* The paper's own grid rule (Sec. 7.1 "An initial regular grid" and "Voxel
+ * subdivision"; Sec. 8: R = 100, trees of depth <= 8, V_thr = 0.5).  The
+ * domain is cut into R^3 voxels (cell index per axis by the rule above with
+ * R cells, voxel = qx + R (qy + R qz)), and every voxel holds a binary tree:
+ * a node of m photons at depth d < max_depth splits when m >= 2, its photons
+ * do not all share one coordinate along the axis of largest spread (max - min
+ * in FP32, first axis on ties), and m > split_threshold or the normal
+ * variance V = 1 - |mean n|^2 exceeds normal_variance_threshold.  V is
+ * formed in double, as 1 - ((Sx^2 + Sy^2) + Sz^2) / ((m^2) 2^40), from the
+ * integer sums S of round_half_even(n * 2^20) over the node's unit normals;
+ * without normals (d_normals NULL) V = 0.  The split value is the
+ * floor(m/2)-th smallest coordinate s (0-based) along that axis: the left
+ * child takes x < tau, tau = s, or tau = the next float above s when no
+ * coordinate is below s; children keep the photons' order.  Nodes are
+ * numbered level by level (voxel roots first, then two children per
+ * splitting node in parent order) and leaves depth-first, left first, voxel
+ * by voxel, so leaf photon ranges ascend.  d_normals: n x 3 float (device or
+ * host) or NULL.  The grid serves pg_splat_photons, pg_sample_dirs,
+ * pg_eval_pdf and pg_mis_*; queries find their leaf by walking their voxel's
+ * tree.  For such a grid PG_GRID_CODES and PG_GRID_LEAF_CODE give voxel
+ * indices, and the tree is exported by PG_GRID_KD_*.  Batched scenes and
+ * progressive states use the octree form only. */
+typedef struct {
+  float lo[3], hi[3];
+  int32_t resolution;               /* R voxels per axis, R^3 <= 2^27 */
+  int32_t max_depth;                /* deepest split inside a voxel, <= 16 */
+  uint32_t split_threshold;         /* M_thr */
+  float normal_variance_threshold;  /* V_thr */
+} pg_kd_params;
+
+pg_status pg_build_grid_kd(pg_ctx *ctx, const pg_photon *d_photons, const float *d_normals, uint64_t n,
+                           const pg_kd_params *params, pg_grid **out);
+
 /* ---- a5: splat --------------------------------------------------------- */
 
 /* Photon energy and count maps, Eq. (photon) and the input buffers of
@@ -384,7 +417,8 @@ enum {
   PG_INFO_N_PHOTONS = 1, PG_INFO_N_LEAVES = 2, PG_INFO_N_ACTIVE = 3, PG_INFO_H = 4,
   PG_INFO_W = 5, PG_INFO_BYTES = 6, PG_INFO_MAX_DEPTH = 7, PG_INFO_N_SCENES = 8, PG_INFO_SCENE_LEVELS = 9,
   PG_INFO_ITERATION = 10,  /* progress: iterations added so far */
-  PG_INFO_N_UPDATED = 11   /* progress: leaves updated by the last add */
+  PG_INFO_N_UPDATED = 11,  /* progress: leaves updated by the last add */
+  PG_INFO_KD_NODES = 12    /* grid of the paper's form: tree nodes, voxel roots included */
 };
 pg_status pg_info(const void *handle, int what, uint64_t *value);
 
@@ -404,6 +438,9 @@ enum {
                                      ordered by scene), L at S; a leaf id returned by
                                      pg_sample_dirs_batched minus this is the id the
                                      scene's leaf has in its grid alone */
+  PG_GRID_KD_AXIS = 110,    /* uint8 [nodes] split axis (0 x, 1 y, 2 z) */
+  PG_GRID_KD_TAU = 111,     /* float [nodes] split value: left holds x[axis] < tau */
+  PG_GRID_KD_LINK = 112,    /* int32 [nodes] left child, or ~leaf */
   PG_HIST_POW_CUR = 200,    /* uint64 [A][H*W] */
   PG_HIST_CNT_CUR = 201,    /* uint32 [A][H*W] */
   PG_HIST_POW_PREV = 202,   /* uint64 [A][H*W] */

@@ -584,6 +584,546 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   return PG_OK;
 }
 
+// ---------------------------------------------------------------- the paper's grid rule
+// Regular R^3 voxels, each refined by a binary tree (Sec. 7.1, Sec. 8).
+// Photons are sorted by voxel; the trees then grow level by level: a warp
+// per node gathers the node's statistics (coordinate extent, fixed-point
+// normal sums) and decides the split, and a CTA per splitting node finds the
+// median by a four-pass radix select over order-preserving keys and
+// partitions the node's slice of the permutation stably.  Leaves are
+// numbered depth-first through bottom-up leaf counts and top-down offsets.
+namespace {
+
+constexpr int kKdNormalBits = 20;
+constexpr int kKdSplitThreads = 256;
+
+__device__ __forceinline__ uint32_t kd_key(float x) {
+  const uint32_t u = __float_as_uint(__fadd_rn(x, 0.0f));  // -0 -> +0
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float kd_unkey(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__device__ __forceinline__ float kd_coord(const pg_photon *__restrict__ ph, uint32_t p, int a) {
+  return __ldg(reinterpret_cast<const float *>(ph + p) + a);
+}
+
+__global__ void k_kd_cells(const pg_photon *__restrict__ ph, uint32_t n, KdView kv, uint64_t *__restrict__ cells,
+                           uint32_t *status) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(ph + i));
+  uint32_t bad = 0;
+  const uint32_t qx = quantise(a.x, kv.lo[0], kv.scale[0], kv.R - 1, bad);
+  const uint32_t qy = quantise(a.y, kv.lo[1], kv.scale[1], kv.R - 1, bad);
+  const uint32_t qz = quantise(a.z, kv.lo[2], kv.scale[2], kv.R - 1, bad);
+  cells[i] = (uint64_t)qx + (uint64_t)kv.R * ((uint64_t)qy + (uint64_t)kv.R * qz);
+  if (bad) atomicOr(status, ST_INVALID_INPUT);
+}
+
+__global__ void k_kd_roots(const uint64_t *__restrict__ sorted, uint32_t n, uint32_t C, uint32_t *__restrict__ nb,
+                           uint32_t *__restrict__ ne) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  nb[c] = lower_bound_u64(sorted, n, c);
+  ne[c] = c + 1 == C ? n : lower_bound_u64(sorted, n, (uint64_t)c + 1);
+}
+
+// One warp per node of a level: extent and normal sums, then the decision.
+__global__ void k_kd_stats(const pg_photon *__restrict__ ph, const float *__restrict__ nrm,
+                           const uint32_t *__restrict__ perm, uint32_t N, const uint32_t *__restrict__ nb,
+                           const uint32_t *__restrict__ ne, int depth, int max_depth, uint32_t thr, double vthr,
+                           uint32_t *__restrict__ flag, uint8_t *__restrict__ axis, uint32_t *status) {
+  const uint32_t v = (uint32_t)((((uint64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (v >= N) return;
+  const uint32_t b = nb[v], e = ne[v], m = e - b;
+  if (depth >= max_depth || m < 2) {
+    if (lane == 0) {
+      flag[v] = 0;
+      axis[v] = 0;
+    }
+    return;
+  }
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  long long sn[3] = {0, 0, 0};
+  for (uint32_t i = b + lane; i < e; i += 32) {
+    const uint32_t p = __ldg(perm + i);
+    const float4 r = __ldg(reinterpret_cast<const float4 *>(ph + p));
+    lo[0] = fminf(lo[0], r.x); hi[0] = fmaxf(hi[0], r.x);
+    lo[1] = fminf(lo[1], r.y); hi[1] = fmaxf(hi[1], r.y);
+    lo[2] = fminf(lo[2], r.z); hi[2] = fmaxf(hi[2], r.z);
+    if (nrm) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float c = __ldg(nrm + 3 * (size_t)p + a);
+        if (!(fabsf(c) <= 1.0f)) atomicOr(status, ST_INVALID_INPUT);  // unit normals only
+        else sn[a] += __float2ll_rn(__fmul_rn(c, (float)(1 << kKdNormalBits)));
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xFFFFFFFFu, lo[a], off));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xFFFFFFFFu, hi[a], off));
+      sn[a] += __shfl_xor_sync(0xFFFFFFFFu, sn[a], off);
+    }
+  }
+  if (lane) return;
+  int a = 0;
+  float best = __fsub_rn(hi[0], lo[0]);
+  for (int k = 1; k < 3; ++k) {
+    const float sp = __fsub_rn(hi[k], lo[k]);
+    if (sp > best) {
+      best = sp;
+      a = k;
+    }
+  }
+  bool split = false;
+  if (best > 0.0f) {
+    double V = 0.0;
+    if (nrm) {
+      const double x = (double)sn[0], y = (double)sn[1], z = (double)sn[2];
+      const double r = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+      const double mm = __dmul_rn(__dmul_rn((double)m, (double)m), 1099511627776.0);  // 2^40
+      V = __dsub_rn(1.0, __ddiv_rn(r, mm));
+    }
+    split = m > thr || V > vthr;
+  }
+  flag[v] = split ? 1u : 0u;
+  axis[v] = (uint8_t)a;
+}
+
+// Exclusive ranks of the splitting nodes of a level, their list, and the count.
+__global__ void __launch_bounds__(1024) k_kd_rank(uint32_t N, const uint32_t *__restrict__ flag,
+                                                  uint32_t *__restrict__ rank, uint32_t *__restrict__ list,
+                                                  uint32_t *__restrict__ count) {
+  __shared__ uint32_t sh[32];
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < N; base += blockDim.x) {
+    const uint32_t v = base + threadIdx.x;
+    uint32_t tot;
+    const uint32_t f = v < N ? flag[v] : 0u;
+    const uint32_t p = block_excl_scan(f, &tot, sh);
+    if (v < N) rank[v] = carry + p;
+    if (f) list[carry + p] = v;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *count = carry;
+}
+
+__device__ __forceinline__ uint32_t block_sum(uint32_t x, uint32_t *sh) {
+  uint32_t tot;
+  block_excl_scan(x, &tot, sh);
+  return tot;
+}
+
+// One CTA per splitting node: median by radix select, then a stable partition.
+__global__ void __launch_bounds__(kKdSplitThreads) k_kd_split(
+    const pg_photon *__restrict__ ph, uint32_t *__restrict__ perm, uint32_t *__restrict__ tmp,
+    const uint32_t *__restrict__ list, const uint32_t *__restrict__ nb, const uint32_t *__restrict__ ne,
+    const uint8_t *__restrict__ axis, const uint32_t *__restrict__ rank, uint32_t next_base,
+    float *__restrict__ tau, int32_t *__restrict__ link, uint32_t *__restrict__ cnb, uint32_t *__restrict__ cne) {
+  __shared__ uint32_t hist[256];
+  __shared__ uint32_t sh[32];
+  __shared__ uint32_t s_prefix, s_mask, s_k;
+  const uint32_t v = list[blockIdx.x];
+  const uint32_t b = nb[v], e = ne[v], m = e - b;
+  const int a = axis[v];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_prefix = 0;
+    s_mask = 0;
+    s_k = m / 2;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    hist[tid] = 0;  // 256 threads, 256 bins
+    __syncthreads();
+    const uint32_t prefix = s_prefix, mask = s_mask;
+    for (uint32_t i = b + tid; i < e; i += kKdSplitThreads) {
+      const uint32_t key = kd_key(kd_coord(ph, perm[i], a));
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t k = s_k, cum = 0;
+      int dg = 0;
+      for (; dg < 255; ++dg) {
+        if (k < cum + hist[dg]) break;
+        cum += hist[dg];
+      }
+      s_k = k - cum;
+      s_prefix = prefix | ((uint32_t)dg << shift);
+      s_mask = mask | (255u << shift);
+    }
+    __syncthreads();
+  }
+  const float sv = kd_unkey(s_prefix);
+  uint32_t below = 0;
+  for (uint32_t i = b + tid; i < e; i += kKdSplitThreads) below += kd_coord(ph, perm[i], a) < sv ? 1u : 0u;
+  below = block_sum(below, sh);
+  const float t = below ? sv : nextafterf(sv, INFINITY);
+  uint32_t nl = below;
+  if (!below) {
+    uint32_t c = 0;
+    for (uint32_t i = b + tid; i < e; i += kKdSplitThreads) c += kd_coord(ph, perm[i], a) < t ? 1u : 0u;
+    nl = block_sum(c, sh);
+  }
+  // Stable partition into tmp[b, e), then back into perm.
+  uint32_t carry_l = 0, carry_r = 0;
+  for (uint32_t base = b; base < e; base += kKdSplitThreads) {
+    const uint32_t i = base + tid;
+    const bool live = i < e;
+    uint32_t p = 0;
+    uint32_t f = 0;
+    if (live) {
+      p = perm[i];
+      f = kd_coord(ph, p, a) < t ? 1u : 0u;
+    }
+    uint32_t tot_l;
+    const uint32_t pl = block_excl_scan(f, &tot_l, sh);
+    if (live) {
+      const uint32_t pr = (uint32_t)tid - pl;  // live lanes are a prefix of the chunk
+      tmp[f ? b + carry_l + pl : b + nl + carry_r + pr] = p;
+    }
+    const uint32_t nlive = min((uint32_t)kKdSplitThreads, e - base);
+    carry_l += tot_l;
+    carry_r += nlive - tot_l;
+  }
+  __syncthreads();
+  for (uint32_t i = b + tid; i < e; i += kKdSplitThreads) perm[i] = tmp[i];
+  if (tid == 0) {
+    const uint32_t c = 2 * rank[v];
+    tau[v] = t;
+    link[v] = (int32_t)(next_base + c);
+    cnb[c] = b;
+    cne[c] = b + nl;
+    cnb[c + 1] = b + nl;
+    cne[c + 1] = e;
+  }
+}
+
+// Bottom-up leaf counts of one level (children of level d are level d + 1).
+__global__ void k_kd_nleaf(uint32_t N, const uint32_t *__restrict__ flag, const uint32_t *__restrict__ rank,
+                           const uint32_t *__restrict__ child_nleaf, uint32_t *__restrict__ nleaf) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  nleaf[v] = flag[v] ? child_nleaf[2 * rank[v]] + child_nleaf[2 * rank[v] + 1] : 1u;
+}
+
+// Exclusive scan of the voxel roots' leaf counts (single block).
+__global__ void __launch_bounds__(1024) k_kd_root_offsets(uint32_t C, const uint32_t *__restrict__ nleaf,
+                                                          uint32_t *__restrict__ off, uint32_t *__restrict__ total) {
+  __shared__ uint32_t sh[32];
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < C; base += blockDim.x) {
+    const uint32_t c = base + threadIdx.x;
+    uint32_t tot;
+    const uint32_t x = c < C ? nleaf[c] : 0u;
+    const uint32_t p = block_excl_scan(x, &tot, sh);
+    if (c < C) off[c] = carry + p;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Top-down: children inherit offsets and voxels; leaves get their ids.
+__global__ void k_kd_offsets(uint32_t N, int depth, const uint32_t *__restrict__ flag,
+                             const uint32_t *__restrict__ rank, const uint32_t *__restrict__ nb,
+                             const uint32_t *__restrict__ ne, const uint32_t *__restrict__ off,
+                             const uint32_t *__restrict__ cell, const uint32_t *__restrict__ child_nleaf,
+                             uint32_t *__restrict__ child_off, uint32_t *__restrict__ child_cell,
+                             int32_t *__restrict__ link, uint64_t *__restrict__ leaf_cell,
+                             int32_t *__restrict__ leaf_depth, uint32_t *__restrict__ leaf_begin,
+                             uint32_t *__restrict__ leaf_end) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const uint32_t o = off[v], c = cell ? cell[v] : v;
+  if (flag[v]) {
+    const uint32_t k = 2 * rank[v];
+    child_off[k] = o;
+    child_off[k + 1] = o + child_nleaf[k];
+    child_cell[k] = c;
+    child_cell[k + 1] = c;
+  } else {
+    link[v] = ~(int32_t)o;
+    leaf_cell[o] = c;
+    leaf_depth[o] = depth;
+    leaf_begin[o] = nb[v];
+    leaf_end[o] = ne[v];
+  }
+}
+
+// leaf_of per photon: the first leaf whose range ends beyond its slot.
+__global__ void k_kd_leaf_of(const uint32_t *__restrict__ perm, uint32_t n, const uint32_t *__restrict__ leaf_end,
+                             uint32_t L, uint32_t *__restrict__ leaf_of) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t lo = 0, hi = L;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (leaf_end[mid] > i) hi = mid;
+    else lo = mid + 1;
+  }
+  leaf_of[perm[i]] = lo;
+}
+
+// Active leaves (>= 1 photon) get consecutive map slots in leaf order.
+__global__ void __launch_bounds__(1024) k_kd_active(uint32_t L, const uint32_t *__restrict__ leaf_begin,
+                                                    const uint32_t *__restrict__ leaf_end,
+                                                    uint32_t *__restrict__ active, int32_t *__restrict__ slot_of_leaf,
+                                                    uint32_t *__restrict__ count) {
+  __shared__ uint32_t sh[32];
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < L; base += blockDim.x) {
+    const uint32_t l = base + threadIdx.x;
+    uint32_t tot;
+    const uint32_t f = (l < L && leaf_end[l] > leaf_begin[l]) ? 1u : 0u;
+    const uint32_t p = block_excl_scan(f, &tot, sh);
+    if (l < L) {
+      slot_of_leaf[l] = f ? (int32_t)(carry + p) : -1;
+      if (f) active[carry + p] = l;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *count = carry;
+}
+
+// Per-level node arrays of the build (device), freed at the end.
+struct KdLevel {
+  uint32_t N = 0, S = 0;
+  uint32_t *nb = nullptr, *ne = nullptr, *flag = nullptr, *rank = nullptr, *list = nullptr;
+  uint32_t *nleaf = nullptr, *off = nullptr, *cell = nullptr;
+  uint8_t *axis = nullptr;
+  float *tau = nullptr;
+  int32_t *link = nullptr;
+  void *block = nullptr;
+  size_t bytes = 0;
+};
+
+pg_status kd_level_alloc(pg_ctx *ctx, KdLevel &lv, uint32_t N) {
+  lv.N = N;
+  const size_t b4 = align256(4ull * N), b1 = align256(N);
+  lv.bytes = 10 * b4 + b1;
+  PG_TRY(ctx_alloc(ctx, lv.bytes, &lv.block));
+  uint8_t *q = (uint8_t *)lv.block;
+  lv.nb = (uint32_t *)q; q += b4;
+  lv.ne = (uint32_t *)q; q += b4;
+  lv.flag = (uint32_t *)q; q += b4;
+  lv.rank = (uint32_t *)q; q += b4;
+  lv.list = (uint32_t *)q; q += b4;
+  lv.nleaf = (uint32_t *)q; q += b4;
+  lv.off = (uint32_t *)q; q += b4;
+  lv.cell = (uint32_t *)q; q += b4;
+  lv.tau = (float *)q; q += b4;
+  lv.link = (int32_t *)q; q += b4;
+  lv.axis = q;
+  PG_CUDA(cudaMemsetAsync(lv.tau, 0, 4ull * N, ctx->stream));
+  PG_CUDA(cudaMemsetAsync(lv.link, 0xFF, 4ull * N, ctx->stream));
+  return PG_OK;
+}
+
+}  // namespace
+
+pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, uint64_t n64, const pg_kd_params *p,
+                        Grid *g) {
+  cudaStream_t st = ctx->stream;
+  const uint32_t n = (uint32_t)n64, R = (uint32_t)p->resolution, C = R * R * R;
+  const int maxd = p->max_depth;
+  g->kd = 1;
+  g->kd_R = R;
+  g->n = n;
+  g->D = maxd;
+  g->min_depth = 0;
+  g->thr = p->split_threshold;
+  g->n_scenes = 1;
+  g->scene_levels = 0;
+  g->lut = nullptr;
+  g->lut_depth = 0;
+  for (int a = 0; a < 3; ++a) {
+    g->lo[a] = p->lo[a];
+    g->hi[a] = p->hi[a];
+    g->scale[a] = (float)((double)R / ((double)p->hi[a] - (double)p->lo[a]));
+  }
+  KdView kv;
+  memset(&kv, 0, sizeof(kv));
+  for (int a = 0; a < 3; ++a) {
+    kv.lo[a] = g->lo[a];
+    kv.scale[a] = g->scale[a];
+  }
+  kv.R = R;
+
+  // Scratch: voxel codes (ping-pong), sort values and histograms, the partition buffer.
+  int bits = 0;
+  while ((1ull << bits) < C) ++bits;
+  const int passes = (bits + 7) / 8;
+  const uint32_t nblocks = n ? ceil_div(n, kSortTile) : 0;
+  const size_t s_k = align256(8ull * n), s_v = align256(4ull * n), s_h = align256(4ull * kRadix * (nblocks + 1));
+  const size_t s_dt = align256(4 * kRadix), s_c = 256;
+  const size_t scratch_bytes = 3 * s_k + 3 * s_v + s_h + s_dt + s_c;
+  void *scratch = nullptr;
+  PG_TRY(ctx_alloc(ctx, scratch_bytes, &scratch));
+  std::vector<KdLevel> levels;
+  struct Guard {
+    pg_ctx *c; void *p; size_t b; std::vector<KdLevel> *lv;
+    ~Guard() {
+      ctx_free(c, p, b);
+      for (auto &l : *lv) ctx_free(c, l.block, l.bytes);
+    }
+  } guard{ctx, scratch, scratch_bytes, &levels};
+  uint8_t *q = (uint8_t *)scratch;
+  uint64_t *codes = (uint64_t *)q; q += s_k;
+  uint64_t *kA = (uint64_t *)q; q += s_k;
+  uint64_t *kB = (uint64_t *)q; q += s_k;
+  uint32_t *perm = (uint32_t *)q; q += s_v;
+  uint32_t *vT = (uint32_t *)q; q += s_v;
+  uint32_t *tmp = (uint32_t *)q; q += s_v;
+  uint32_t *hist = (uint32_t *)q; q += s_h;
+  uint32_t *dtot = (uint32_t *)q; q += s_dt;
+  uint32_t *count = (uint32_t *)q;
+
+  const int TB = 256;
+  const uint64_t *sorted = codes;
+  if (n) {
+    k_kd_cells<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, kv, codes, ctx->d_status), PG_COUNT(ctx);
+    if (passes == 0) {
+      k_iota<<<ceil_div(n, TB), TB, 0, st>>>(perm, n), PG_COUNT(ctx);
+    } else {
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kScatterSmem));
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kScatterSmem));
+      const uint64_t *kin = codes;
+      const uint32_t *vin = nullptr;
+      for (int ps = 0; ps < passes; ++ps) {
+        uint64_t *kout = (ps & 1) ? kB : kA;
+        uint32_t *vout = ((passes - 1 - ps) & 1) ? vT : perm;
+        const int shift = 8 * ps;
+        k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
+        k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
+        if (ps == 0)
+          k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                            dtot, nblocks), PG_COUNT(ctx);
+        else
+          k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                             dtot, nblocks), PG_COUNT(ctx);
+        kin = kout;
+        vin = vout;
+      }
+      sorted = kin;
+    }
+  }
+
+  // Level 0: the voxel roots.
+  levels.emplace_back();
+  PG_TRY(kd_level_alloc(ctx, levels[0], C));
+  k_kd_roots<<<ceil_div(C, TB), TB, 0, st>>>(sorted, n, C, levels[0].nb, levels[0].ne), PG_COUNT(ctx);
+  uint32_t node_total = C;
+  for (int d = 0;; ++d) {
+    KdLevel &lv = levels[d];
+    k_kd_stats<<<ceil_div((uint64_t)lv.N * 32, TB), TB, 0, st>>>(d_ph, d_nrm, perm, lv.N, lv.nb, lv.ne, d, maxd,
+                                                                 p->split_threshold,
+                                                                 (double)p->normal_variance_threshold, lv.flag,
+                                                                 lv.axis, ctx->d_status), PG_COUNT(ctx);
+    k_kd_rank<<<1, 1024, 0, st>>>(lv.N, lv.flag, lv.rank, lv.list, count), PG_COUNT(ctx);
+    uint32_t S = 0, status = 0;
+    PG_CUDA(cudaMemcpyAsync(&S, count, 4, cudaMemcpyDeviceToHost, st));
+    PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
+    PG_CUDA(cudaStreamSynchronize(st));
+    if (status & ST_INVALID_INPUT) {
+      PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
+      PG_CUDA(cudaStreamSynchronize(st));
+      return PG_ERR_INVALID_INPUT;
+    }
+    lv.S = S;
+    if (S == 0) break;
+    if ((uint64_t)node_total + 2ull * S >= (1ull << 31)) return PG_ERR_UNSUPPORTED;
+    levels.emplace_back();
+    KdLevel &nx = levels[d + 1];
+    KdLevel &cur = levels[d];  // emplace_back may have moved the vector
+    PG_TRY(kd_level_alloc(ctx, nx, 2 * S));
+    k_kd_split<<<S, kKdSplitThreads, 0, st>>>(d_ph, perm, tmp, cur.list, cur.nb, cur.ne, cur.axis, cur.rank,
+                                              node_total, cur.tau, cur.link, nx.nb, nx.ne), PG_COUNT(ctx);
+    node_total += 2 * S;
+  }
+  const int nlev = (int)levels.size();
+  // Bottom-up leaf counts, root offsets, top-down offsets.
+  for (int d = nlev - 1; d >= 0; --d) {
+    KdLevel &lv = levels[d];
+    k_kd_nleaf<<<ceil_div(lv.N, TB), TB, 0, st>>>(lv.N, lv.flag, lv.rank, d + 1 < nlev ? levels[d + 1].nleaf : nullptr,
+                                                  lv.nleaf), PG_COUNT(ctx);
+  }
+  k_kd_root_offsets<<<1, 1024, 0, st>>>(C, levels[0].nleaf, levels[0].off, count), PG_COUNT(ctx);
+  uint32_t L = 0;
+  PG_CUDA(cudaMemcpyAsync(&L, count, 4, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaStreamSynchronize(st));
+
+  // The handle block.
+  const size_t b_codes = align256(8ull * n), b_n4 = align256(4ull * n), b_l8 = align256(8ull * L),
+               b_l4 = align256(4ull * L), b_t4 = align256(4ull * node_total), b_t1 = align256(node_total),
+               b_sb = 256, b_sg = 256;
+  g->h.bytes = b_codes + 2 * b_n4 + b_l8 + 5 * b_l4 + 2 * b_t4 + b_t1 + 2 * b_sb + b_sg;
+  PG_TRY(ctx_alloc(ctx, g->h.bytes, &g->block));
+  q = (uint8_t *)g->block;
+  g->codes = (uint64_t *)q; q += b_codes;
+  g->perm = (uint32_t *)q; q += b_n4;
+  g->leaf_of = (uint32_t *)q; q += b_n4;
+  g->leaf_code = (uint64_t *)q; q += b_l8;
+  g->leaf_depth = (int32_t *)q; q += b_l4;
+  g->leaf_begin = (uint32_t *)q; q += b_l4;
+  g->leaf_end = (uint32_t *)q; q += b_l4;
+  g->active = (uint32_t *)q; q += b_l4;
+  g->slot_of_leaf = (int32_t *)q; q += b_l4;
+  g->kd_link = (int32_t *)q; q += b_t4;
+  g->kd_tau = (float *)q; q += b_t4;
+  g->kd_axis = q; q += b_t1;
+  g->scene_begin = (uint32_t *)q; q += b_sb;
+  g->scene_leaf_begin = (uint32_t *)q; q += b_sb;
+  g->scene_geom = (float *)q;
+  g->kd_nodes = node_total;
+  g->L = L;
+  for (int d = 0; d < nlev; ++d) {
+    KdLevel &lv = levels[d];
+    uint32_t *coff = d + 1 < nlev ? levels[d + 1].off : nullptr;
+    uint32_t *ccell = d + 1 < nlev ? levels[d + 1].cell : nullptr;
+    const uint32_t *cnl = d + 1 < nlev ? levels[d + 1].nleaf : nullptr;
+    k_kd_offsets<<<ceil_div(lv.N, TB), TB, 0, st>>>(lv.N, d, lv.flag, lv.rank, lv.nb, lv.ne, lv.off,
+                                                    d ? lv.cell : nullptr, cnl, coff, ccell, lv.link, g->leaf_code,
+                                                    g->leaf_depth, g->leaf_begin, g->leaf_end), PG_COUNT(ctx);
+  }
+  uint32_t base = 0;
+  for (int d = 0; d < nlev; ++d) {
+    KdLevel &lv = levels[d];
+    PG_CUDA(cudaMemcpyAsync(g->kd_link + base, lv.link, 4ull * lv.N, cudaMemcpyDeviceToDevice, st));
+    PG_CUDA(cudaMemcpyAsync(g->kd_tau + base, lv.tau, 4ull * lv.N, cudaMemcpyDeviceToDevice, st));
+    PG_CUDA(cudaMemcpyAsync(g->kd_axis + base, lv.axis, lv.N, cudaMemcpyDeviceToDevice, st));
+    base += lv.N;
+  }
+  if (n) {
+    PG_CUDA(cudaMemcpyAsync(g->codes, codes, 8ull * n, cudaMemcpyDeviceToDevice, st));
+    PG_CUDA(cudaMemcpyAsync(g->perm, perm, 4ull * n, cudaMemcpyDeviceToDevice, st));
+    k_kd_leaf_of<<<ceil_div(n, TB), TB, 0, st>>>(g->perm, n, g->leaf_end, L, g->leaf_of), PG_COUNT(ctx);
+  }
+  k_kd_active<<<1, 1024, 0, st>>>(L, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf, count), PG_COUNT(ctx);
+  uint32_t hb[2] = {0u, n}, hl[2] = {0u, L};
+  float hg[6] = {g->lo[0], g->lo[1], g->lo[2], g->scale[0], g->scale[1], g->scale[2]};
+  PG_CUDA(cudaMemcpyAsync(g->scene_begin, hb, 8, cudaMemcpyHostToDevice, st));
+  PG_CUDA(cudaMemcpyAsync(g->scene_leaf_begin, hl, 8, cudaMemcpyHostToDevice, st));
+  PG_CUDA(cudaMemcpyAsync(g->scene_geom, hg, 24, cudaMemcpyHostToDevice, st));
+  PG_CUDA(cudaGetLastError());
+  uint32_t A = 0;
+  PG_CUDA(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaStreamSynchronize(st));
+  g->A = A;
+  return PG_OK;
+}
+
 // ---------------------------------------------------------------- fixed leaf table
 // Progressive iterations bin later photon batches into a grid that no longer
 // splits: the batch is sorted by code like the build does, and each leaf's

@@ -52,9 +52,11 @@ struct MisTab {
   const float *alpha;
   int H, W;
   float pdf_scale;  // HW / (4 pi)
+  KdView kd;        // grid of the paper's form (link null otherwise)
 };
 
 __device__ __forceinline__ uint32_t leaf_of(const MisTab &tb, float x, float y, float z, uint32_t &bad) {
+  if (tb.kd.link) return kd_locate(tb.kd, x, y, z, bad);
   const uint64_t code = position_code(tb.geom, x, y, z, bad);
   return find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
 }
@@ -206,6 +208,7 @@ MisTab make_mis_tab(const Grid *g, const Tables *t, const Mis *m, const float *p
   tb.H = t ? t->H : 0;
   tb.W = t ? t->W : 0;
   tb.pdf_scale = t ? (float)((double)t->H * t->W / (4.0 * 3.14159265358979323846)) : 0.0f;
+  tb.kd = kd_view_of(g);
   return tb;
 }
 

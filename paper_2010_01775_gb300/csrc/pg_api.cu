@@ -499,6 +499,34 @@ pg_status pg_build_grid(pg_ctx *c, const pg_photon *d_ph, uint64_t n, const pg_g
   return PG_OK;
 }
 
+pg_status pg_build_grid_kd(pg_ctx *c, const pg_photon *d_ph, const float *d_normals, uint64_t n,
+                           const pg_kd_params *p, pg_grid **out) {
+  if (!c || !p || !out || (n && !d_ph)) return PG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n >= (1ull << 31)) return PG_ERR_UNSUPPORTED;
+  if (p->resolution < 1 || (uint64_t)p->resolution * p->resolution * p->resolution > (1ull << 27) ||
+      p->max_depth < 0 || p->max_depth > 16 || !(p->normal_variance_threshold == p->normal_variance_threshold))
+    return PG_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!isfinite(p->lo[a]) || !isfinite(p->hi[a]) || !(p->hi[a] > p->lo[a])) return PG_ERR_INVALID_ARG;
+  Staged ph, nr;
+  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
+  if (n && d_normals) PG_TRY(stage_in(c, d_normals, n * 3 * sizeof(float), nr));
+  Grid *g = new (std::nothrow) Grid();
+  if (!g) return PG_ERR_OOM;
+  memset(g, 0, sizeof(*g));
+  g->h.kind = KIND_GRID;
+  g->h.ctx = c;
+  pg_status s = build_grid_kd(c, (const pg_photon *)ph.dev, d_normals ? (const float *)nr.dev : nullptr, n, p, g);
+  if (s != PG_OK) {
+    if (g->block) ctx_free(c, g->block, g->h.bytes);
+    delete g;
+    return s;
+  }
+  *out = (pg_grid *)g;
+  return PG_OK;
+}
+
 pg_status pg_build_grid_batched(pg_ctx *c, const pg_photon *d_ph, uint64_t n, const uint32_t *d_scene_begin,
                                 uint32_t S, const pg_grid_params *p, pg_grid **out) {
   if (!c || !p || !out || !d_scene_begin || S == 0 || (n && !d_ph)) return PG_ERR_INVALID_ARG;
@@ -569,6 +597,7 @@ pg_status pg_splat_photons_batched(pg_ctx *c, const pg_grid *grid, const pg_phot
   const Grid *g = as<Grid>(grid, KIND_GRID);
   if (!c || !g || !out || !d_n_prev || (n && !d_ph)) return PG_ERR_INVALID_ARG;
   *out = nullptr;
+  if (g->kd) return PG_ERR_UNSUPPORTED;
   if (n != g->n || F < 0 || F > 62) return PG_ERR_INVALID_ARG;
   if (!pow2_in(H, 4, 256) || !pow2_in(W, 4, 256) || H * W > 16384) return PG_ERR_NOT_POW2;
   Staged ph, np;
@@ -1022,6 +1051,7 @@ pg_status pg_sample_dirs_batched(pg_ctx *c, const pg_grid *grid, const pg_tables
   if (!c || !g || !t || !d_query_begin || !d_stream_ids || (q && (!d_pos || !d_dir || !d_pdf || !d_leaf)))
     return PG_ERR_INVALID_ARG;
   if (t->A != g->A) return PG_ERR_INVALID_ARG;
+  if (g->kd) return PG_ERR_UNSUPPORTED;  // scene batches are octree grids
   if (q == 0) return PG_OK;
   if (q >= (1ull << 32)) return PG_ERR_UNSUPPORTED;
   Staged pos, qb, sid, dir, pdf, leaf, bin;
@@ -1050,6 +1080,7 @@ pg_status pg_eval_pdf_batched(pg_ctx *c, const pg_grid *grid, const pg_tables *t
   const Tables *t = as<Tables>(tab, KIND_TABLES);
   if (!c || !g || !t || !d_query_begin || (q && (!d_pos || !d_dir || !d_pdf))) return PG_ERR_INVALID_ARG;
   if (t->A != g->A) return PG_ERR_INVALID_ARG;
+  if (g->kd) return PG_ERR_UNSUPPORTED;  // scene batches are octree grids
   if (q == 0) return PG_OK;
   if (q >= (1ull << 32)) return PG_ERR_UNSUPPORTED;
   Staged pos, dir, qb, pdf;
@@ -1209,6 +1240,7 @@ pg_status pg_info(const void *handle, int what, uint64_t *v) {
       else if (what == PG_INFO_MAX_DEPTH) *v = (uint64_t)g->D;
       else if (what == PG_INFO_N_SCENES) *v = g->n_scenes;
       else if (what == PG_INFO_SCENE_LEVELS) *v = (uint64_t)g->scene_levels;
+      else if (what == PG_INFO_KD_NODES && g->kd) *v = g->kd_nodes;
       else if (what == PG_INFO_BYTES) *v = b->bytes;
       else return PG_ERR_INVALID_ARG;
       return PG_OK;
@@ -1265,6 +1297,9 @@ pg_status pg_export(pg_ctx *c, const void *handle, int what, void *dst, size_t b
       case PG_GRID_ACTIVE: src = g->active; need = (size_t)g->A * 4; break;
       case PG_GRID_SLOT_OF_LEAF: src = g->slot_of_leaf; need = (size_t)g->L * 4; break;
       case PG_GRID_SCENE_LEAF_BEGIN: src = g->scene_leaf_begin; need = 4ull * (g->n_scenes + 1); break;
+      case PG_GRID_KD_AXIS: src = g->kd ? (const void *)g->kd_axis : nullptr; need = g->kd ? g->kd_nodes : 0; break;
+      case PG_GRID_KD_TAU: src = g->kd ? (const void *)g->kd_tau : nullptr; need = g->kd ? 4ull * g->kd_nodes : 0; break;
+      case PG_GRID_KD_LINK: src = g->kd ? (const void *)g->kd_link : nullptr; need = g->kd ? 4ull * g->kd_nodes : 0; break;
       default: return PG_ERR_INVALID_ARG;
     }
   } else if (b->kind == KIND_HIST) {

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "pg.h"
 
@@ -70,6 +71,16 @@ struct Grid {
   uint32_t *scene_begin;  // [S+1] photon offsets per scene
   uint32_t *scene_leaf_begin;  // [S+1] first leaf per scene, L at S
   float *scene_geom;      // [S][6] lo[3], scale[3] per scene (batched grids)
+  // The paper's grid rule (pg_build_grid_kd): R^3 voxels, each a binary tree.
+  // Nodes 0 .. R^3-1 are the voxels' roots; kd_link >= 0 is a node's left
+  // child (right = left + 1), < 0 is ~leaf.  leaf_code then holds each
+  // leaf's voxel, codes each photon's voxel, D the deepest split, and
+  // scale R / (hi - lo).
+  int kd;
+  uint32_t kd_R, kd_nodes;
+  int32_t *kd_link;      // [kd_nodes]
+  float *kd_tau;         // [kd_nodes] left holds x[axis] < tau
+  uint8_t *kd_axis;      // [kd_nodes]
   void *block;           // single allocation holding the arrays above
 };
 
@@ -234,6 +245,32 @@ __device__ __forceinline__ uint64_t position_code(const GridGeom &g, float x, fl
   return morton3(qx, qy, qz);
 }
 
+// Leaf of a position in a grid of the paper's form: its voxel's root, then
+// left while x[axis] < tau.  Children always have larger indices than their
+// parent, and depth is at most 16, so the walk ends; the bound guards it.
+struct KdView {
+  const int32_t *link;
+  const float *tau;
+  const uint8_t *axis;
+  float lo[3], scale[3];
+  uint32_t R;
+};
+
+__device__ __forceinline__ uint32_t kd_locate(const KdView &k, float x, float y, float z, uint32_t &bad) {
+  const uint32_t qx = quantise(x, k.lo[0], k.scale[0], k.R - 1, bad);
+  const uint32_t qy = quantise(y, k.lo[1], k.scale[1], k.R - 1, bad);
+  const uint32_t qz = quantise(z, k.lo[2], k.scale[2], k.R - 1, bad);
+  int32_t v = (int32_t)(qx + k.R * (qy + k.R * qz));
+  int32_t ln = __ldg(k.link + v);
+  for (int it = 0; ln >= 0 && it < 64; ++it) {
+    const int a = __ldg(k.axis + v);
+    const float p = a == 0 ? x : (a == 1 ? y : z);
+    v = ln + (p < __ldg(k.tau + v) ? 0 : 1);
+    ln = __ldg(k.link + v);
+  }
+  return ln < 0 ? (uint32_t)~ln : 0u;
+}
+
 // Last leaf whose start code is <= code (leaf start codes ascend).
 __device__ __forceinline__ uint32_t find_leaf(const uint64_t *__restrict__ leaf_code, uint32_t L, uint64_t code) {
   uint32_t lo = 0, hi = L;
@@ -346,6 +383,9 @@ pg_status hist_alloc(pg_ctx *ctx, Hist *h, uint32_t A, int H, int W);  // zeroed
 // dst[d_active[a]] = src[a] (all planes); dst is leaf-indexed.
 pg_status rows_to_leaves(pg_ctx *ctx, const Hist *src, const uint32_t *d_active, Hist *dst);
 pg_status identity_slots(pg_ctx *ctx, Grid *g);  // slot_of_leaf[l] = active[l] = l, A = L
+// The paper's grid rule: R^3 voxels refined by binary trees (grid.cu).
+pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_normals, uint64_t n,
+                        const pg_kd_params *p, Grid *g);
 // splat.cu
 // A batch binned into a fixed grid (view from bin_into_grid) and merged into
 // leaf-indexed sums: for every leaf l of the view's active list, prev[l] =
@@ -402,5 +442,21 @@ inline GridGeom geom_of(const Grid *g) {
 }
 
 inline unsigned ceil_div(uint64_t a, uint64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Query-side view of a grid of the paper's form (link null for an octree grid).
+inline KdView kd_view_of(const Grid *g) {
+  KdView k;
+  memset(&k, 0, sizeof(k));
+  if (!g->kd) return k;
+  k.link = g->kd_link;
+  k.tau = g->kd_tau;
+  k.axis = g->kd_axis;
+  for (int a = 0; a < 3; ++a) {
+    k.lo[a] = g->lo[a];
+    k.scale[a] = g->scale[a];
+  }
+  k.R = g->kd_R;
+  return k;
+}
 
 }  // namespace pgi

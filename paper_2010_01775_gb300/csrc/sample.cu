@@ -2,7 +2,8 @@
 // (Sec. 7.3; the p_guide term of Eq. target_mis / mis_coef).
 //
 // One thread per query: voxel location (the a1 rule), binary search of the
-// leaf start codes, Philox4x32-10 uniforms, then an inverse-CDF search of the
+// leaf start codes (or, for a grid of the paper's form, a walk down the
+// voxel's binary tree), Philox4x32-10 uniforms, then an inverse-CDF search of the
 // marginal (rows) and the conditional (columns) tables; the direction is
 // uniform in (z, phi) inside the chosen bin, i.e. uniform in solid angle on
 // the equal-area cylindrical map, and its pdf is P_ij * HW / (4 pi).
@@ -47,6 +48,7 @@ struct QueryCtx {
   const float *geom;      // [S][6]
   uint32_t S;
   int shift;              // 3 * spatial depth
+  KdView kd;              // grid of the paper's form (link null otherwise)
 };
 
 __device__ __forceinline__ uint64_t query_code(const QueryCtx &qc, const float *pos, uint64_t t, uint64_t &local,
@@ -77,10 +79,15 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc,
   uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= q) return;
   uint32_t bad = 0;
-  uint64_t local;
-  uint64_t code = query_code(qc, pos, t, local, stream, bad);
+  uint64_t local = t;
+  uint32_t l;
+  if (qc.kd.link) {
+    l = kd_locate(qc.kd, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  } else {
+    const uint64_t code = query_code(qc, pos, t, local, stream, bad);
+    l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
+  }
   if (bad) atomicOr(status, ST_INVALID_INPUT);
-  uint32_t l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
   int32_t s = __ldg(tb.slot_of_leaf + l);
   uint4 r = philox4x32_10(make_uint4((uint32_t)local, (uint32_t)(local >> 32), stream, 0u), key);
   const float k24 = 5.9604644775390625e-08f;  // 2^-24
@@ -120,8 +127,13 @@ __global__ void k_eval(const float *__restrict__ pos, const float *__restrict__ 
   if (t >= q) return;
   uint32_t bad = 0, stream = 0;
   uint64_t local;
-  uint64_t code = query_code(qc, pos, t, local, stream, bad);
-  uint32_t l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
+  uint32_t l;
+  if (qc.kd.link) {
+    l = kd_locate(qc.kd, pos[3 * t], pos[3 * t + 1], pos[3 * t + 2], bad);
+  } else {
+    const uint64_t code = query_code(qc, pos, t, local, stream, bad);
+    l = find_leaf_lut(tb.leaf_code, tb.L, tb.lut, tb.lut_cells, tb.lut_shift, code);
+  }
   int32_t s = __ldg(tb.slot_of_leaf + l);
   float p = tb.pdf_uniform;
   if (s >= 0 && __ldg(tb.valid + s)) {
@@ -147,6 +159,7 @@ QueryCtx make_qc(const Grid *g, const QueryScenes &qs) {
   qc.geom = g->scene_geom;
   qc.S = g->n_scenes;
   qc.shift = 3 * g->D;
+  qc.kd = kd_view_of(g);
   return qc;
 }
 

@@ -21,10 +21,11 @@ PRECISIONS = {"fp32": PG_FP32, "bf16": PG_BF16, "fp8": PG_FP8_E4M3}
 
 PG_INFO_N_PHOTONS, PG_INFO_N_LEAVES, PG_INFO_N_ACTIVE, PG_INFO_H, PG_INFO_W, PG_INFO_BYTES, PG_INFO_MAX_DEPTH = range(1, 8)
 PG_INFO_N_SCENES, PG_INFO_SCENE_LEVELS = 8, 9
-PG_INFO_ITERATION, PG_INFO_N_UPDATED = 10, 11
+PG_INFO_ITERATION, PG_INFO_N_UPDATED, PG_INFO_KD_NODES = 10, 11, 12
 PG_GRID_CODES, PG_GRID_PERM, PG_GRID_LEAF_OF, PG_GRID_LEAF_CODE, PG_GRID_LEAF_DEPTH = 100, 101, 102, 103, 104
 PG_GRID_LEAF_BEGIN, PG_GRID_LEAF_END, PG_GRID_ACTIVE, PG_GRID_SLOT_OF_LEAF = 105, 106, 107, 108
 PG_GRID_SCENE_LEAF_BEGIN = 109
+PG_GRID_KD_AXIS, PG_GRID_KD_TAU, PG_GRID_KD_LINK = 110, 111, 112
 PG_HIST_POW_CUR, PG_HIST_CNT_CUR, PG_HIST_POW_PREV, PG_HIST_CNT_PREV = 200, 201, 202, 203
 PG_MAP_Y = 300
 PG_TAB_P, PG_TAB_CDF_PHI, PG_TAB_CDF_Z, PG_TAB_VALID = 400, 401, 402, 403
@@ -44,7 +45,7 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning",
             "pg_reconstruct_experts", "pg_mis_create", "pg_mis_accumulate", "pg_mis_update", "pg_mis_sample",
             "pg_mis_eval", "pg_progress_create", "pg_progress_add_photons", "pg_progress_reconstruct",
-            "pg_progress_view"]
+            "pg_progress_view", "pg_build_grid_kd"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -58,6 +59,12 @@ class PgError(RuntimeError):
 class pg_grid_params(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("max_depth", ctypes.c_int32),
                 ("min_depth", ctypes.c_int32), ("split_threshold", ctypes.c_uint32)]
+
+
+class pg_kd_params(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("resolution", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32), ("split_threshold", ctypes.c_uint32),
+                ("normal_variance_threshold", ctypes.c_float)]
 
 
 class pg_progress_params(ctypes.Structure):
@@ -105,6 +112,7 @@ def load(path: str = LIB_PATH):
         "pg_progress_create": [P, ctypes.POINTER(pg_progress_params), PP],
         "pg_progress_add_photons": [P, P, P, u64], "pg_progress_reconstruct": [P, P, P, i32],
         "pg_progress_view": [P, PP, PP, PP, PP],
+        "pg_build_grid_kd": [P, P, P, u64, ctypes.POINTER(pg_kd_params), PP],
         "pg_net_get_tuning": [P, P, sz, ctypes.POINTER(sz)], "pg_net_set_tuning": [P, P, sz],
         "pg_budget_create": [u64, PP], "pg_budget_destroy": [P], "pg_ctx_attach_budget": [P, P],
         "pg_budget_charge": [P, u64], "pg_budget_release": [P, u64],
@@ -507,3 +515,26 @@ def pg_progress_view(state):
 
 def export_progress_updated(state) -> np.ndarray:
     return state.export(PG_PROGRESS_UPDATED, np.uint32, state.info(PG_INFO_N_UPDATED))
+
+
+# ---------------------------------------------------------------- the paper's grid rule
+def pg_build_grid_kd(ctx, photons, normals, n, lo, hi, resolution=100, max_depth=8, split_threshold=500,
+                     normal_variance_threshold=0.5) -> Handle:
+    p = pg_kd_params((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi), resolution, max_depth, split_threshold,
+                     normal_variance_threshold)
+    out = ctypes.c_void_p()
+    _check(_lib.pg_build_grid_kd(ctx.ptr, _ptr(photons), _ptr(normals), n, ctypes.byref(p), ctypes.byref(out)),
+           "pg_build_grid_kd")
+    return Handle(ctx, out.value, "grid")
+
+
+def export_kd(g):
+    """Leaf table and tree of a grid of the paper's form."""
+    n, L, N = g.info(PG_INFO_N_PHOTONS), g.info(PG_INFO_N_LEAVES), g.info(PG_INFO_KD_NODES)
+    return dict(cells=g.export(PG_GRID_CODES, np.uint64, n), perm=g.export(PG_GRID_PERM, np.uint32, n),
+                leaf_of=g.export(PG_GRID_LEAF_OF, np.uint32, n), leaf_cell=g.export(PG_GRID_LEAF_CODE, np.uint64, L),
+                leaf_depth=g.export(PG_GRID_LEAF_DEPTH, np.int32, L),
+                leaf_begin=g.export(PG_GRID_LEAF_BEGIN, np.uint32, L),
+                leaf_end=g.export(PG_GRID_LEAF_END, np.uint32, L),
+                node_axis=g.export(PG_GRID_KD_AXIS, np.uint8, N), node_tau=g.export(PG_GRID_KD_TAU, np.float32, N),
+                node_link=g.export(PG_GRID_KD_LINK, np.int32, N), L=L, A=g.info(PG_INFO_N_ACTIVE))

@@ -195,6 +195,17 @@ def query_directions(q: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(_unit(uniform_sphere(rng, q)).astype(np.float32))
 
 
+def wall_normals(ph: np.ndarray) -> np.ndarray:
+    """(n, 3) float32 unit normals of the walls the photons of `photons()`
+    lie on (a photon on the wall at ROOM_LO of axis a faces +e_a, at ROOM_HI
+    -e_a): the surface normals at the photon hit points."""
+    n = np.zeros((ph.shape[0], 3), np.float32)
+    for a in range(3):
+        n[ph[:, a] == np.float32(ROOM_LO), a] = 1.0
+        n[ph[:, a] == np.float32(ROOM_HI), a] = -1.0
+    return n
+
+
 def vertex_records(q: int, seed: int):
     """Path-vertex records for one-sample MIS: (q, 3) float32 unit normals
     (uniform on the sphere) and (q,) float32 bounce contributions (lognormal,
