@@ -135,6 +135,9 @@ def run_pg(args, wl, prec):
     outs = (torch.empty(q, 3, device="cuda"), torch.empty(q, device="cuda"),
             torch.empty(q, dtype=torch.int32, device="cuda"), torch.empty(q, dtype=torch.int32, device="cuda"),
             torch.empty(q, device="cuda"), torch.empty(q, dtype=torch.uint8, device="cuda"))
+    # The paper's grid rule needs the surface normal at every photon.
+    ph_nrm = synth.wall_normals(ph) if args.grid == "kd" else None
+    d_nrm = torch.from_numpy(ph_nrm).cuda() if ph_nrm is not None else None
     # One-sample MIS (Sec. 7.3): vertex normals and bounce contributions.
     nrm, con = synth.vertex_records(q, wl.seed) if args.mis else (None, None)
     d_vtx = (torch.from_numpy(nrm).cuda(), torch.from_numpy(con).cuda()) if args.mis else None
@@ -142,12 +145,18 @@ def run_pg(args, wl, prec):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, keep_tables=False, vtx=None):
+    def build_grid(p_ph, p_nrm=None):
+        if args.grid == "kd":  # the paper's rule: 100^3 voxels, trees of depth 8, M_thr = 500, V_thr = 0.5
+            return pg.pg_build_grid_kd(ctx, p_ph, p_nrm if p_nrm is not None else d_nrm, n, LO, HI, KD_R, KD_DEPTH,
+                                       KD_THR, KD_VTHR)
+        return pg.pg_build_grid(ctx, p_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+
+    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, keep_tables=False, vtx=None, p_nrm=None):
         o_d, o_p, o_l, o_b, o_e, o_s = outs
         vtx = vtx if vtx is not None else d_vtx
         rec = (lambda i: marks[i].record(stream)) if marks is not None else (lambda i: None)
         rec(0)
-        g = pg.pg_build_grid(ctx, p_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+        g = build_grid(p_ph, p_nrm)
         rec(1)
         h = pg.pg_splat_photons(ctx, g, p_ph, n, wl.n_prev, H, W, wl.frac_bits)
         rec(2)
@@ -176,7 +185,7 @@ def run_pg(args, wl, prec):
         return A, L, P
 
     # Launch shapes of the tensor-core convolutions are tuned once, untimed.
-    g0 = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+    g0 = build_grid(d_ph)
     h0 = pg.pg_splat_photons(ctx, g0, d_ph, n, wl.n_prev, H, W, wl.frac_bits)
     if args.load_tuning:
         pg.pg_net_set_tuning(net, np.load(args.load_tuning))
@@ -231,12 +240,13 @@ def run_pg(args, wl, prec):
               torch.empty(q, dtype=torch.int32).pin_memory(), torch.empty(q, dtype=torch.int32).pin_memory(),
               torch.empty(q).pin_memory(), torch.empty(q, dtype=torch.uint8).pin_memory())
     h_vtx = (torch.from_numpy(nrm).pin_memory(), torch.from_numpy(con).pin_memory()) if args.mis else None
+    h_nrm = torch.from_numpy(ph_nrm).pin_memory() if ph_nrm is not None else None
     e2e_steps = max(1, min(args.steps, 3))
 
     def e2e_step():
         dph = torch.empty_like(d_ph)
         dph.copy_(h_ph, non_blocking=True)
-        step(dph, h_pos, h_dir, h_outs, prec, vtx=h_vtx)
+        step(dph, h_pos, h_dir, h_outs, prec, vtx=h_vtx, p_nrm=h_nrm)
         ctx.sync()
 
     e2e_step()
@@ -252,6 +262,8 @@ def run_pg(args, wl, prec):
     else:
         h2d = ph.nbytes + pos.nbytes + dirs.nbytes
         d2h = q * (12 + 4 + 4 + 4 + 4)
+    if ph_nrm is not None:
+        h2d += ph_nrm.nbytes
 
     # Dominant kernel family: the CNN convolutions of one reconstruct call,
     # timed with events on the launching stream.
@@ -310,12 +322,18 @@ def run_pg(args, wl, prec):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec],
             "data": "synthetic (seeded photon blobs on room walls, vMF directions, lognormal power; random He-init U-Net)",
-            "config": {"workload": wl.name, "photons": n, "queries": q, "H": H, "W": W, "max_depth": wl.max_depth,
-                       "split_threshold": wl.split_threshold, "leaves": L, "active_leaves": A,
+            "config": {"workload": wl.name + (" (paper's grid rule)" if args.grid == "kd" else ""), "photons": n,
+                       "queries": q, "H": H, "W": W,
+                       "max_depth": KD_DEPTH if args.grid == "kd" else wl.max_depth,
+                       "split_threshold": KD_THR if args.grid == "kd" else wl.split_threshold,
+                       "leaves": L, "active_leaves": A,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "experts": args.experts or 1,
                        "sampling": ("one-sample MIS: Lambertian BSDF stand-in + guide, per-leaf alpha"
                                     if args.mis else "guide"),
+                       "grid": (f"paper's rule: {KD_R}^3 voxels, binary trees of depth <= {KD_DEPTH}, "
+                                f"M_thr {KD_THR}, V_thr {KD_VTHR}, wall normals" if args.grid == "kd"
+                                else f"octree, depth {wl.max_depth}, split {wl.split_threshold}"),
                        "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
             "leaf_tables_per_s": A * args.steps * world / (total_ms / 1e3),
             "stage_ms": stage_ms,
@@ -340,7 +358,7 @@ def run_pg(args, wl, prec):
             out["mis_alpha"] = mis_alpha
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves, check, maps, out.get("precisions"),
-                                               mis=args.mis)
+                                               mis=args.mis, kd=args.grid == "kd")
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -535,6 +553,7 @@ def run_serve(args, tr):
     print(json.dumps(out), flush=True)
 
 
+KD_R, KD_DEPTH, KD_THR, KD_VTHR = 100, 8, 500, 0.5  # Sec. 8 (M_thr = c sqrt(2^t) at t = 0, c = 500)
 PROGRESS_FRAC_BITS = 24  # fixed point of the progressive sums: room for ~60M photons of power <= 500
 
 
@@ -725,21 +744,33 @@ def progressive_cpu_baseline(wl, n_leaves, n_batch=262_144, n_queries=262_144):
                        f"({step_s:.1f} s); wall {t4 - t0:.1f} s")}
 
 
-def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False):
+def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False, kd=False):
     """The FP64 oracle on a bounded sample; returns per-stage seconds and the
     throughput extrapolated to the full workload."""
     from oracle import oracle as O
     from paper_2010_01775_gb300 import synth
     ph, pos, dirs, blob = synth.workload_inputs(wl)
     t0 = time.perf_counter()
-    g = O.build_grid(ph, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+    if kd:
+        g = O.build_kd_grid(ph, synth.wall_normals(ph), LO, HI, KD_R, KD_DEPTH, KD_THR, KD_VTHR)
+    else:
+        g = O.build_grid(ph, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
     act, slot = O.active_leaves(g)
     t1 = time.perf_counter()
     keep = act[check] if check is not None else act[np.linspace(0, act.size - 1, n_leaves).astype(np.int64)]
     gsub = dict(g)
-    h = O.splat(ph, g, wl.n_prev, wl.H, wl.W, wl.frac_bits)
-    t2 = time.perf_counter()
-    hs = O.hist_for_active(h, keep)
+    if kd:  # ~10^6 leaves: splat the kept leaves only and scale by their share of the photons
+        sub = dict(g, L=keep.size, leaf_begin=g["leaf_begin"][keep], leaf_end=g["leaf_end"][keep])
+        hs = O.splat(ph, sub, wl.n_prev, wl.H, wl.W, wl.frac_bits)
+        hs = {k: v for k, v in hs.items() if k != "status"}
+        share = float((g["leaf_end"][keep] - g["leaf_begin"][keep]).sum()) / max(1, ph.shape[0])
+        t2 = time.perf_counter()
+        splat_s = (t2 - t1) / max(share, 1e-9)
+    else:
+        h = O.splat(ph, g, wl.n_prev, wl.H, wl.W, wl.frac_bits)
+        t2 = time.perf_counter()
+        splat_s = t2 - t1
+        hs = O.hist_for_active(h, keep)
     y = O.cnn_forward(O.assemble_inputs(hs), O.parse_net(blob))
     t3 = time.perf_counter()
     tabs = O.tables_from_map(y)
@@ -759,16 +790,17 @@ def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False):
         O.eval_pdf(gsub, slot2, tabs, pos[:n_queries], dirs[:n_queries])
     t5 = time.perf_counter()
     A = act.size
-    step_s = (t1 - t0) + (t2 - t1) + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
+    step_s = (t1 - t0) + splat_s + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
         (t5 - t4) * wl.n_queries / n_queries
     return dict(step_s=step_s, samples_per_s=wl.n_queries / step_s, wall_s=t5 - t0, leaves=int(keep.size),
                 A=int(A), queries=n_queries, P=tabs["P"])
 
 
-def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None, mis=False):
-    r = oracle_sample_run(wl, n_leaves, 65_536 if mis else 262_144, check, mis)
+def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None, mis=False, kd=False):
+    r = oracle_sample_run(wl, n_leaves, 65_536 if mis else 262_144, check, mis, kd)
     out = {"value": r["samples_per_s"], "unit": "samples/s", "cores": 1, "kind": "oracle",
-           "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons, CNN+CDF on "
+           "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons"
+                      f"{' (the splat on the sampled leaves, scaled by their photon share)' if kd else ''}, CNN+CDF on "
                       f"{r['leaves']} of {r['A']} active leaves, {'MIS ' if mis else ''}sample+eval on "
                       f"{r['queries']} of {wl.n_queries} "
                       f"queries; per-stage times scaled to the full step ({r['step_s']:.1f} s); "
@@ -838,6 +870,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--experts", type=int, default=0,
                     help="reconstruct with a mixture of this many experts routed by leaf photon count (Sec. 8)")
+    ap.add_argument("--grid", default="octree", choices=["octree", "kd"],
+                    help="octree grid, or the paper's rule (100^3 voxels refined by binary trees)")
     ap.add_argument("--progressive", action="store_true",
                     help="time one later iteration of the progressive form (Sec. 7.2) instead of a single-shot step")
     ap.add_argument("--mis", action="store_true",
