@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "conv.cuh"
 
 namespace pgi {
@@ -48,6 +50,31 @@ __global__ void k_assemble(const uint64_t *__restrict__ pow_cur, const uint32_t 
   float4 *o = reinterpret_cast<float4 *>(x + i * 8);
   o[0] = a;
   o[1] = b;
+}
+
+// k_assemble fused with the tensor-core first-layer packing for BF16: the
+// same five channels, rounded to BF16, in a 32-byte row per pixel (channels
+// 5..15 zero).  Bit-identical to k_assemble followed by k_pack_x0.
+__global__ void k_assemble_bf16(const uint64_t *__restrict__ pow_cur, const uint32_t *__restrict__ cnt_cur,
+                                const uint64_t *__restrict__ pow_prev, const uint32_t *__restrict__ cnt_prev,
+                                const uint64_t *__restrict__ tot_cur, const uint64_t *__restrict__ tot_prev,
+                                const uint32_t *__restrict__ perm, uint32_t slot0, uint32_t nslots, int HW,
+                                uint4 *__restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)nslots * HW) return;
+  const uint32_t pos = slot0 + (uint32_t)(i / HW);
+  const uint32_t s = perm ? perm[pos] : pos;
+  size_t g = (size_t)s * HW + i % HW;
+  uint64_t tc = tot_cur[s], tp = tot_prev[s];
+  float ic = tc ? (float)HW / __ull2float_rn(tc) : 0.0f;
+  float ip = tp ? (float)HW / __ull2float_rn(tp) : 0.0f;
+  uint32_t c = cnt_cur[g], cp = cnt_prev[g];
+  __nv_bfloat162 q0 = __floats2bfloat162_rn(__ull2float_rn(pow_cur[g]) * ic, __ull2float_rn(pow_prev[g]) * ip);
+  __nv_bfloat162 q1 = __floats2bfloat162_rn(log1pf((float)c), log1pf((float)cp));
+  __nv_bfloat162 q2 = __floats2bfloat162_rn(c ? 1.0f : 0.0f, 0.0f);
+  out[2 * i] = make_uint4(*reinterpret_cast<uint32_t *>(&q0), *reinterpret_cast<uint32_t *>(&q1),
+                          *reinterpret_cast<uint32_t *>(&q2), 0u);
+  out[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 __device__ __forceinline__ float activate(float v, int act) {
@@ -344,8 +371,11 @@ pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_preci
   const uint32_t A = count;
   if (A == 0) return PG_OK;
   const int H = h->H, W = h->W, HW = H * W;
-  const size_t per_leaf = 8 * (size_t)HW * 4 + (prec == PG_FP32 ? act_floats_per_leaf(net, H, W) * 4
-                                                                  : tc_bytes_per_leaf(net, prec, H, W));
+  // BF16 assembles straight into the packed first-layer input (no FP32 x0).
+  const bool packed = prec == PG_BF16;
+  const size_t x0_per_leaf = packed ? 0 : 8 * (size_t)HW * 4;
+  const size_t per_leaf = x0_per_leaf + (prec == PG_FP32 ? act_floats_per_leaf(net, H, W) * 4
+                                                         : tc_bytes_per_leaf(net, prec, H, W));
   // Activation working set: leaves are processed in chunks of at most ~6 GB.
   uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(A, (6ull << 30) / per_leaf));
   size_t bytes = per_leaf * chunk + 4096;
@@ -358,13 +388,23 @@ pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_preci
   cudaStream_t st = ctx->stream;
   for (uint32_t s0 = 0; s0 < A; s0 += chunk) {
     uint32_t ns = std::min(chunk, A - s0);
-    float *x0 = (float *)scratch;  // FP32 input, 8 channels
     size_t nx = (size_t)ns * HW;
+    float *y = y_out + (size_t)s0 * HW;
+    if (packed) {
+      // The packed input is the first region of the activation buffer.
+      k_assemble_bf16<<<ceil_div(nx, 256), 256, 0, st>>>(h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev,
+                                                         h->tot_cur, h->tot_prev, d_perm, first + s0, ns, HW,
+                                                         (uint4 *)scratch), PG_COUNT(ctx);
+      PG_CUDA(cudaGetLastError());
+      PG_TRY(forward_tc(ctx, net, prec, nullptr, scratch, ns, H, W, y, st, tune));
+      if (tune) break;
+      continue;
+    }
+    float *x0 = (float *)scratch;  // FP32 input, 8 channels
     k_assemble<<<ceil_div(nx, 256), 256, 0, st>>>(h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur,
                                                   h->tot_prev, d_perm, first + s0, ns, HW, x0), PG_COUNT(ctx);
     PG_CUDA(cudaGetLastError());
     uint8_t *act = (uint8_t *)scratch + align256(nx * 8 * 4);
-    float *y = y_out + (size_t)s0 * HW;
     if (prec == PG_FP32) PG_TRY(forward_f32(ctx, net, x0, act, ns, H, W, y, st));
     else PG_TRY(forward_tc(ctx, net, prec, x0, act, ns, H, W, y, st, tune));
     if (tune) break;  // the first chunk is representative of every later one

@@ -1161,9 +1161,11 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
   const int cp = 32 / es;  // first-layer channels per pixel (32-byte rows)
   T *xcol = (T *)act;
   act += align256(M0 * 32);
-  k_pack_x0<T><<<ceil_div(M0, 256), 256, 0, st>>>(x0, M0, xcol, fp8 ? 1.0f / scale[0] : 1.0f);
-  PG_COUNT(ctx);
-  PG_CUDA(cudaGetLastError());
+  if (x0) {  // null: the caller assembled the packed input into xcol already
+    k_pack_x0<T><<<ceil_div(M0, 256), 256, 0, st>>>(x0, M0, xcol, fp8 ? 1.0f / scale[0] : 1.0f);
+    PG_COUNT(ctx);
+    PG_CUDA(cudaGetLastError());
+  }
   auto conv = [&](int li, const void *in, int in_cs, int in_co, int Hin, int Win, int Cin, void *out, int out_cs,
                   int out_co, int ups, const Layer *head = nullptr) -> pg_status {
     const Layer &Lr = Ls[li];
