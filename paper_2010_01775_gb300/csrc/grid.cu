@@ -698,24 +698,6 @@ __global__ void k_kd_stats(const pg_photon *__restrict__ ph, const float *__rest
   axis[v] = (uint8_t)a;
 }
 
-// Exclusive ranks of the splitting nodes of a level, their list, and the count.
-__global__ void __launch_bounds__(1024) k_kd_rank(uint32_t N, const uint32_t *__restrict__ flag,
-                                                  uint32_t *__restrict__ rank, uint32_t *__restrict__ list,
-                                                  uint32_t *__restrict__ count) {
-  __shared__ uint32_t sh[32];
-  uint32_t carry = 0;
-  for (uint32_t base = 0; base < N; base += blockDim.x) {
-    const uint32_t v = base + threadIdx.x;
-    uint32_t tot;
-    const uint32_t f = v < N ? flag[v] : 0u;
-    const uint32_t p = block_excl_scan(f, &tot, sh);
-    if (v < N) rank[v] = carry + p;
-    if (f) list[carry + p] = v;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) *count = carry;
-}
-
 __device__ __forceinline__ uint32_t block_sum(uint32_t x, uint32_t *sh) {
   uint32_t tot;
   block_excl_scan(x, &tot, sh);
@@ -817,22 +799,6 @@ __global__ void k_kd_nleaf(uint32_t N, const uint32_t *__restrict__ flag, const 
   nleaf[v] = flag[v] ? child_nleaf[2 * rank[v]] + child_nleaf[2 * rank[v] + 1] : 1u;
 }
 
-// Exclusive scan of the voxel roots' leaf counts (single block).
-__global__ void __launch_bounds__(1024) k_kd_root_offsets(uint32_t C, const uint32_t *__restrict__ nleaf,
-                                                          uint32_t *__restrict__ off, uint32_t *__restrict__ total) {
-  __shared__ uint32_t sh[32];
-  uint32_t carry = 0;
-  for (uint32_t base = 0; base < C; base += blockDim.x) {
-    const uint32_t c = base + threadIdx.x;
-    uint32_t tot;
-    const uint32_t x = c < C ? nleaf[c] : 0u;
-    const uint32_t p = block_excl_scan(x, &tot, sh);
-    if (c < C) off[c] = carry + p;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) *total = carry;
-}
-
 // Top-down: children inherit offsets and voxels; leaves get their ids.
 __global__ void k_kd_offsets(uint32_t N, int depth, const uint32_t *__restrict__ flag,
                              const uint32_t *__restrict__ rank, const uint32_t *__restrict__ nb,
@@ -874,25 +840,100 @@ __global__ void k_kd_leaf_of(const uint32_t *__restrict__ perm, uint32_t n, cons
   leaf_of[perm[i]] = lo;
 }
 
-// Active leaves (>= 1 photon) get consecutive map slots in leaf order.
-__global__ void __launch_bounds__(1024) k_kd_active(uint32_t L, const uint32_t *__restrict__ leaf_begin,
-                                                    const uint32_t *__restrict__ leaf_end,
-                                                    uint32_t *__restrict__ active, int32_t *__restrict__ slot_of_leaf,
-                                                    uint32_t *__restrict__ count) {
+// Device-wide exclusive scans of the build: tile sums, one block over the
+// tile sums, then each tile rescanned with its offset and the result handed
+// to an emitter.  A tile is 4096 values (1024 threads x 4).
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+
+template <class Val>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint32_t N, Val f, uint32_t *__restrict__ partial) {
+  __shared__ uint32_t sh[32];
+  const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) s += base + j < N ? f(base + j) : 0u;
+  uint32_t tot;
+  block_excl_scan(s, &tot, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t nt, uint32_t *__restrict__ partial,
+                                                        uint32_t *__restrict__ total) {
   __shared__ uint32_t sh[32];
   uint32_t carry = 0;
-  for (uint32_t base = 0; base < L; base += blockDim.x) {
-    const uint32_t l = base + threadIdx.x;
+  for (uint32_t b0 = 0; b0 < nt; b0 += blockDim.x) {
+    const uint32_t b = b0 + threadIdx.x;
     uint32_t tot;
-    const uint32_t f = (l < L && leaf_end[l] > leaf_begin[l]) ? 1u : 0u;
-    const uint32_t p = block_excl_scan(f, &tot, sh);
-    if (l < L) {
-      slot_of_leaf[l] = f ? (int32_t)(carry + p) : -1;
-      if (f) active[carry + p] = l;
-    }
+    const uint32_t x = b < nt ? partial[b] : 0u;
+    const uint32_t p = block_excl_scan(x, &tot, sh);
+    if (b < nt) partial[b] = carry + p;
     carry += tot;
   }
-  if (threadIdx.x == 0) *count = carry;
+  if (threadIdx.x == 0) *total = carry;
+}
+
+template <class Val, class Emit>
+__global__ void __launch_bounds__(kScanThreads) k_scan_emit(uint32_t N, Val f, const uint32_t *__restrict__ partial,
+                                                           Emit e) {
+  __shared__ uint32_t sh[32];
+  const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = base + j < N ? f(base + j) : 0u;
+    s += v[j];
+  }
+  uint32_t tot;
+  uint32_t p = partial[blockIdx.x] + block_excl_scan(s, &tot, sh);
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < N) e(base + j, p, v[j]);
+    p += v[j];
+  }
+}
+
+struct FlagVal {
+  const uint32_t *flag;
+  __device__ uint32_t operator()(uint32_t i) const { return flag[i]; }
+};
+struct RankEmit {  // rank of every node, and the list of splitting nodes
+  uint32_t *rank, *list;
+  __device__ void operator()(uint32_t i, uint32_t p, uint32_t v) const {
+    rank[i] = p;
+    if (v) list[p] = i;
+  }
+};
+struct OffEmit {
+  uint32_t *off;
+  __device__ void operator()(uint32_t i, uint32_t p, uint32_t) const { off[i] = p; }
+};
+struct NonEmptyVal {
+  const uint32_t *b, *e;
+  __device__ uint32_t operator()(uint32_t i) const { return e[i] > b[i] ? 1u : 0u; }
+};
+struct SlotEmit {  // map slots of the leaves with photons
+  uint32_t *active;
+  int32_t *slot;
+  __device__ void operator()(uint32_t i, uint32_t p, uint32_t v) const {
+    slot[i] = v ? (int32_t)p : -1;
+    if (v) active[p] = i;
+  }
+};
+
+// partial: ceil(N / kScanTile) words of scratch; *total gets the sum.
+template <class Val, class Emit>
+pg_status scan_emit(pg_ctx *ctx, uint32_t N, Val f, Emit e, uint32_t *partial, uint32_t *total) {
+  cudaStream_t st = ctx->stream;
+  if (N == 0) {
+    PG_CUDA(cudaMemsetAsync(total, 0, 4, st));
+    return PG_OK;
+  }
+  const uint32_t nt = ceil_div(N, kScanTile);
+  k_scan_tiles<<<nt, kScanThreads, 0, st>>>(N, f, partial), PG_COUNT(ctx);
+  k_scan_partials<<<1, 1024, 0, st>>>(nt, partial, total), PG_COUNT(ctx);
+  k_scan_emit<<<nt, kScanThreads, 0, st>>>(N, f, partial, e), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
+  return PG_OK;
 }
 
 // Per-level node arrays of the build (device), freed at the end.
@@ -966,7 +1007,9 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
   const uint32_t nblocks = n ? ceil_div(n, kSortTile) : 0;
   const size_t s_k = align256(8ull * n), s_v = align256(4ull * n), s_h = align256(4ull * kRadix * (nblocks + 1));
   const size_t s_dt = align256(4 * kRadix), s_c = 256;
-  const size_t scratch_bytes = 3 * s_k + 3 * s_v + s_h + s_dt + s_c;
+  // Scan tile sums: a scan covers at most 2^31 values (nodes or leaves).
+  const size_t s_p = align256(4ull * ((1ull << 31) / kScanTile + 1));
+  const size_t scratch_bytes = 3 * s_k + 3 * s_v + s_h + s_dt + s_c + s_p;
   void *scratch = nullptr;
   PG_TRY(ctx_alloc(ctx, scratch_bytes, &scratch));
   std::vector<KdLevel> levels;
@@ -986,6 +1029,7 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
   uint32_t *tmp = (uint32_t *)q; q += s_v;
   uint32_t *hist = (uint32_t *)q; q += s_h;
   uint32_t *dtot = (uint32_t *)q; q += s_dt;
+  uint32_t *partial = (uint32_t *)q; q += s_p;
   uint32_t *count = (uint32_t *)q;
 
   const int TB = 256;
@@ -1031,7 +1075,7 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
                                                                  p->split_threshold,
                                                                  (double)p->normal_variance_threshold, lv.flag,
                                                                  lv.axis, ctx->d_status), PG_COUNT(ctx);
-    k_kd_rank<<<1, 1024, 0, st>>>(lv.N, lv.flag, lv.rank, lv.list, count), PG_COUNT(ctx);
+    PG_TRY(scan_emit(ctx, lv.N, FlagVal{lv.flag}, RankEmit{lv.rank, lv.list}, partial, count));
     uint32_t S = 0, status = 0;
     PG_CUDA(cudaMemcpyAsync(&S, count, 4, cudaMemcpyDeviceToHost, st));
     PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
@@ -1059,7 +1103,7 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
     k_kd_nleaf<<<ceil_div(lv.N, TB), TB, 0, st>>>(lv.N, lv.flag, lv.rank, d + 1 < nlev ? levels[d + 1].nleaf : nullptr,
                                                   lv.nleaf), PG_COUNT(ctx);
   }
-  k_kd_root_offsets<<<1, 1024, 0, st>>>(C, levels[0].nleaf, levels[0].off, count), PG_COUNT(ctx);
+  PG_TRY(scan_emit(ctx, C, FlagVal{levels[0].nleaf}, OffEmit{levels[0].off}, partial, count));
   uint32_t L = 0;
   PG_CUDA(cudaMemcpyAsync(&L, count, 4, cudaMemcpyDeviceToHost, st));
   PG_CUDA(cudaStreamSynchronize(st));
@@ -1110,7 +1154,8 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
     PG_CUDA(cudaMemcpyAsync(g->perm, perm, 4ull * n, cudaMemcpyDeviceToDevice, st));
     k_kd_leaf_of<<<ceil_div(n, TB), TB, 0, st>>>(g->perm, n, g->leaf_end, L, g->leaf_of), PG_COUNT(ctx);
   }
-  k_kd_active<<<1, 1024, 0, st>>>(L, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf, count), PG_COUNT(ctx);
+  PG_TRY(scan_emit(ctx, L, NonEmptyVal{g->leaf_begin, g->leaf_end}, SlotEmit{g->active, g->slot_of_leaf}, partial,
+                   count));
   uint32_t hb[2] = {0u, n}, hl[2] = {0u, L};
   float hg[6] = {g->lo[0], g->lo[1], g->lo[2], g->scale[0], g->scale[1], g->scale[2]};
   PG_CUDA(cudaMemcpyAsync(g->scene_begin, hb, 8, cudaMemcpyHostToDevice, st));
