@@ -40,6 +40,7 @@ ERR_INVALID_INPUT = 8
 
 ARCH_TINY3 = 0
 ARCH_UNET4 = 1
+ARCH_PAPER = 2
 ACT_NONE, ACT_ELU, ACT_SOFTPLUS = 0, 1, 2
 NET_MAGIC = 0x314E4750
 
@@ -79,6 +80,7 @@ def lib():
         L.or_sample.argtypes = [P, i64, P, P, i32, P, i64, P, i32, i32, P, P, P, P, u64, u32,
                                 P, P, P, P]
         L.or_eval_pdf.argtypes = [P, P, i64, P, P, i32, P, i64, P, i32, i32, P, P, P]
+        L.or_conv2d_dilated.argtypes = [P, i64, i32, i32, i32, P, P, i32, i32, i32, i32, P]
         L.or_sample_leaves.argtypes = [P, i64, P, i32, i32, P, P, P, P, u64, u32, P, P, P, P]
         L.or_eval_pdf_leaves.argtypes = [P, P, i64, P, i32, i32, P, P, P]
     return _lib
@@ -344,32 +346,65 @@ def assemble_inputs(hist):
 
 
 def parse_net(blob: bytes):
-    """Layer list [(cout, cin, k, stride, act, w[cout][k][k][cin], b[cout])]."""
+    """Layer list [(cout, cin, k, stride, act, w[cout][k][k][cin], b[cout])];
+    the per-layer tap spacing (dilation, 1 unless stored) is in "dil"."""
     magic, arch, cin0, nl, w0, w1, w2, w3, seed = struct.unpack_from("<IIII4IQ", blob, 0)
     if magic != NET_MAGIC:
         raise ValueError("bad net blob")
     off = struct.calcsize("<IIII4IQ")
-    layers = []
+    layers, dil = [], []
     for _ in range(nl):
-        cout, cin, k, stride, act, _z = struct.unpack_from("<6I", blob, off)
+        cout, cin, k, stride, act, d = struct.unpack_from("<6I", blob, off)
+        dil.append(max(1, d))
         off += 24
         w = np.frombuffer(blob, np.float32, cout * k * k * cin, off).reshape(cout, k, k, cin)
         off += 4 * w.size
         b = np.frombuffer(blob, np.float32, cout, off)
         off += 4 * cout
         layers.append((cout, cin, k, stride, act, np.ascontiguousarray(w), np.ascontiguousarray(b)))
-    return dict(arch=arch, widths=(w0, w1, w2, w3), layers=layers, seed=seed)
+    return dict(arch=arch, widths=(w0, w1, w2, w3), layers=layers, dil=dil, seed=seed)
 
 
-def conv2d(x, w, b, stride):
-    """One conv layer, 'same' zero padding, channel-last FP64 (plain loops in C)."""
+def conv2d(x, w, b, stride, dil=1):
+    """One conv layer, 'same' zero padding, channel-last FP64 (plain loops in
+    C); dil spreads the taps dil pixels apart (dilated convolution)."""
     x = np.ascontiguousarray(x, np.float64)
     A, Hin, Win, Cin = x.shape
     cout, k, _, cin = w.shape
     assert cin == Cin
     out = np.zeros((A, Hin // stride, Win // stride, cout), np.float64)
-    lib().or_conv2d(_p(x), A, Hin, Win, Cin, _p(_f32(w)), _p(_f32(b)), cout, k, stride, _p(out))
+    if dil == 1:
+        lib().or_conv2d(_p(x), A, Hin, Win, Cin, _p(_f32(w)), _p(_f32(b)), cout, k, stride, _p(out))
+    else:
+        lib().or_conv2d_dilated(_p(x), A, Hin, Win, Cin, _p(_f32(w)), _p(_f32(b)), cout, k, stride, dil, _p(out))
     return out
+
+
+def pconv_mask(m, k, stride, dil):
+    """Mask update of a partial (masked) convolution (Sec. 5.1, the masked
+    convolutions of Liu et al. 2018): for every output pixel the number c of
+    valid input pixels under its k x k window (taps dil apart, zero outside
+    the map).  Returns (scale, m_out): scale = k^2 / c where c > 0, else 0;
+    m_out = c > 0.  m: [A][H][W] of 0/1."""
+    ones = np.ones((1, k, k, 1), np.float32)
+    c = conv2d(np.asarray(m, np.float64)[..., None], ones, np.zeros(1, np.float32), stride, dil)[..., 0]
+    scale = np.where(c > 0, (k * k) / np.maximum(c, 1.0), 0.0)
+    return scale, (c > 0).astype(np.float64)
+
+
+def pconv(x, m, w, b, stride, dil, act, residual=None):
+    """Partial convolution: W (x * m) renormalised by k^2 / (valid pixels
+    under the window), plus the bias, where any input pixel is valid, else 0;
+    then the activation, then the residual link.  The activations are zero
+    wherever their mask is, so x * m = x.  Returns (y, m_out)."""
+    cout, k, _, cin = w.shape
+    scale, m_out = pconv_mask(m, k, stride, dil)
+    y = conv2d(x, w, np.zeros(cout, np.float32), stride, dil)
+    y = np.where(scale[..., None] > 0, y * scale[..., None] + np.asarray(b, np.float64), 0.0)
+    y = _act(y, act)
+    if residual is not None:
+        y = y + residual
+    return y, m_out
 
 
 def elu(x):
@@ -403,6 +438,8 @@ def cnn_forward(x, net):
     deeper output (nearest x2), concatenate [upsampled, skip] and apply two
     3x3 convs, then a 1x1 head with softplus."""
     layers = net["layers"]
+    if net["arch"] == ARCH_PAPER:
+        return cnn_forward_paper(x, net)
     if net["arch"] == ARCH_TINY3:
         h = x
         for cout, cin, k, stride, act, w, b in layers:
@@ -422,6 +459,39 @@ def cnn_forward(x, net):
     d1 = run(run(np.concatenate([upsample2(d2), e1], axis=3), 10), 11)
     d0 = run(run(np.concatenate([upsample2(d1), e0], axis=3), 12), 13)
     return run(d0, 14)[..., 0]
+
+
+def cnn_forward_paper(x, net):
+    """The compact masked U-Net of Sec. 5.1 as read here (the paper's layer
+    list is in a figure absent from the text): partial convolutions with ELU
+    and residual links, two stride-2 levels, a bottleneck of dilated
+    convolutions (taps 2 and 4 apart), decoder levels that upsample (nearest
+    x2) and concatenate [upsampled, skip], at most 64 channels, and a 1x1
+    head with softplus.  The input mask is the B channel (bins with photons);
+    a concatenation's mask is the union of its parts' masks."""
+    L, dil = net["layers"], net["dil"]
+    assert len(L) == 12
+
+    def run(h, m, i, res=None):
+        cout, cin, k, stride, act, w, b = L[i]
+        return pconv(h, m, w, b, stride, dil[i], act, res)
+
+    m0 = x[..., 4]
+    a0, m1 = run(x[..., :5], m0, 0)
+    e0, me0 = run(a0, m1, 1, a0)
+    a1, m3 = run(e0, me0, 2)
+    e1, me1 = run(a1, m3, 3, a1)
+    b0, m5 = run(e1, me1, 4)
+    b1, m6 = run(b0, m5, 5, b0)
+    b2, m7 = run(b1, m6, 6, b1)
+    c1 = np.concatenate([upsample2(b2), e1], axis=3)
+    d1, md1 = run(c1, np.maximum(upsample2(m7[..., None])[..., 0], me1), 7)
+    d1b, md1b = run(d1, md1, 8, d1)
+    c0 = np.concatenate([upsample2(d1b), e0], axis=3)
+    d0, md0 = run(c0, np.maximum(upsample2(md1b[..., None])[..., 0], me0), 9)
+    d0b, _ = run(d0, md0, 10, d0)
+    cout, cin, k, stride, act, w, b = L[11]
+    return _act(conv2d(d0b, w, b, stride), act)[..., 0]
 
 
 # Sec. 8 (implementation): five networks, each trained for the voxels whose

@@ -289,6 +289,32 @@ void or_assemble_inputs(int64_t A, int64_t HW, const uint64_t *pow_cur, const ui
 /* in[l, y*stride + ky - k/2, x*stride + kx - k/2, i], zero outside the map. */
 /* Channel-last activations, weights [Cout][k][k][Cin].                       */
 /* ------------------------------------------------------------------------ */
+/* A convolution with its taps spread `dil` pixels apart (dilated, Sec. 5.1's
+ * bottleneck): output (y, x) reads input (y*stride + (ky - k/2)*dil,
+ * x*stride + (kx - k/2)*dil), zero outside the map. */
+void or_conv2d_dilated(const double *in, int64_t L, int Hin, int Win, int Cin, const float *w, const float *b,
+                       int Cout, int k, int stride, int dil, double *out) {
+  int Hout = Hin / stride, Wout = Win / stride, r = k / 2;
+  for (int64_t l = 0; l < L; ++l)
+    for (int y = 0; y < Hout; ++y)
+      for (int x = 0; x < Wout; ++x)
+        for (int o = 0; o < Cout; ++o) {
+          double acc = (double)b[o];
+          for (int ky = 0; ky < k; ++ky) {
+            int iy = y * stride + (ky - r) * dil;
+            if (iy < 0 || iy >= Hin) continue;
+            for (int kx = 0; kx < k; ++kx) {
+              int ix = x * stride + (kx - r) * dil;
+              if (ix < 0 || ix >= Win) continue;
+              const double *src = in + (((l * Hin + iy) * Win + ix) * (int64_t)Cin);
+              const float *wk = w + (((int64_t)o * k + ky) * k + kx) * Cin;
+              for (int i = 0; i < Cin; ++i) acc += (double)wk[i] * src[i];
+            }
+          }
+          out[((l * Hout + y) * Wout + x) * (int64_t)Cout + o] = acc;
+        }
+}
+
 void or_conv2d(const double *in, int64_t L, int Hin, int Win, int Cin, const float *w, const float *b,
                int Cout, int k, int stride, double *out) {
   int Hout = Hin / stride, Wout = Win / stride, pad = k / 2;

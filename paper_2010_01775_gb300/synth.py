@@ -25,6 +25,7 @@ ROOM_HI = 0.98
 # Network architectures understood by the weight blob (both sides parse it).
 ARCH_TINY3 = 0
 ARCH_UNET4 = 1
+ARCH_PAPER = 2  # compact masked U-Net with residual links and a dilated bottleneck
 ACT_NONE, ACT_ELU, ACT_SOFTPLUS = 0, 1, 2
 NET_MAGIC = 0x314E4750  # "PGN1"
 IN_CHANNELS = 5
@@ -216,6 +217,13 @@ def vertex_records(q: int, seed: int):
     return n, c
 
 
+def net_dilations(arch: int) -> list:
+    """Tap spacing of every layer (1 except the paper-style bottleneck)."""
+    if arch == ARCH_PAPER:
+        return [1, 1, 1, 1, 1, 2, 4, 1, 1, 1, 1, 1]
+    return [1] * len(net_layers(arch, (1, 1, 1, 1)))
+
+
 def net_layers(arch: int, widths) -> list:
     """Layer descriptors (cout, cin, k, stride, act) in blob order."""
     if arch == ARCH_TINY3:
@@ -233,6 +241,16 @@ def net_layers(arch: int, widths) -> list:
             (c0, c1 + c0, 3, 1, ACT_ELU), (c0, c0, 3, 1, ACT_ELU),
             (1, c0, 1, 1, ACT_SOFTPLUS),
         ]
+    if arch == ARCH_PAPER:
+        c0, c1 = widths[0], widths[1]
+        return [
+            (c0, IN_CHANNELS, 3, 1, ACT_ELU), (c0, c0, 3, 1, ACT_ELU),      # level 0 (+ residual)
+            (c1, c0, 3, 2, ACT_ELU), (c1, c1, 3, 1, ACT_ELU),               # level 1 (+ residual)
+            (c1, c1, 3, 2, ACT_ELU), (c1, c1, 3, 1, ACT_ELU), (c1, c1, 3, 1, ACT_ELU),  # dilated bottleneck
+            (c1, 2 * c1, 3, 1, ACT_ELU), (c1, c1, 3, 1, ACT_ELU),           # decoder level 1
+            (c0, c1 + c0, 3, 1, ACT_ELU), (c0, c0, 3, 1, ACT_ELU),          # decoder level 0
+            (1, c0, 1, 1, ACT_SOFTPLUS),
+        ]
     raise ValueError(f"unknown arch {arch}")
 
 
@@ -241,18 +259,19 @@ def net_blob(arch: int, widths, seed: int) -> bytes:
 
     Blob layout (little endian): u32 magic, u32 arch, u32 in_channels,
     u32 n_layers, u32 widths[4], u64 seed; then per layer u32
-    {cout, cin, k, stride, act, 0} followed by float32 weights in
-    [cout][k][k][cin] order and float32 bias[cout].
+    {cout, cin, k, stride, act, dilation (0 = 1)} followed by float32
+    weights in [cout][k][k][cin] order and float32 bias[cout].
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     layers = net_layers(arch, widths)
+    dil = net_dilations(arch)
     w4 = list(widths) + [0] * (4 - len(widths))
     parts = [struct.pack("<IIII4IQ", NET_MAGIC, arch, IN_CHANNELS, len(layers), *w4, seed)]
-    for cout, cin, k, stride, act in layers:
+    for (cout, cin, k, stride, act), d in zip(layers, dil):
         fan_in = k * k * cin
         w = (rng.standard_normal((cout, k, k, cin)) * np.sqrt(2.0 / fan_in)).astype(np.float32)
         b = (rng.standard_normal(cout) * 0.01).astype(np.float32)
-        parts.append(struct.pack("<6I", cout, cin, k, stride, act, 0))
+        parts.append(struct.pack("<6I", cout, cin, k, stride, act, d if d > 1 else 0))
         parts.append(w.tobytes())
         parts.append(b.tobytes())
     return b"".join(parts)

@@ -820,3 +820,79 @@ def test_kd_grid_brute_properties(n, R, depth, thr, normals, seed):
         # The left part keeps the photons' order (a stable partition).
         assert np.all(np.diff(np.nonzero(np.isin(g["perm"][b:e], idx[P[:, a] < tau]))[0]) == 1)
         stack += [(link, d + 1), (link + 1, d + 1)]
+
+
+# ---------------------------------------------------------------- the paper-style network (Sec. 5.1)
+@pytest.mark.parametrize("dil,stride", [(2, 1), (4, 1), (2, 2)])
+def test_dilated_conv_matches_torch(dil, stride):
+    rng = np.random.default_rng(50 + dil)
+    x = rng.standard_normal((2, 12, 16, 5))
+    w = rng.standard_normal((4, 3, 3, 5)).astype(np.float32)
+    b = rng.standard_normal(4).astype(np.float32)
+    y = O.conv2d(x, w, b, stride, dil)
+    ref = Fnn.conv2d(torch.from_numpy(x).permute(0, 3, 1, 2), torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                     torch.from_numpy(b.astype(np.float64)), stride=stride, padding=dil, dilation=dil)
+    assert np.allclose(y, ref.permute(0, 2, 3, 1).numpy(), rtol=1e-12, atol=1e-12)
+
+
+def test_partial_conv_mask_hand_values():
+    m = np.zeros((1, 5, 5))
+    m[0, 2, 2] = 1.0
+    scale, mo = O.pconv_mask(m, 3, 1, 1)
+    want = np.zeros((5, 5))
+    want[1:4, 1:4] = 9.0  # one valid pixel under each of these windows
+    assert np.array_equal(scale[0], want) and np.array_equal(mo[0], (want > 0).astype(float))
+    scale, _ = O.pconv_mask(m, 3, 1, 2)
+    want = np.zeros((5, 5))
+    for y in (0, 2, 4):
+        for x in (0, 2, 4):
+            want[y, x] = 9.0
+    assert np.array_equal(scale[0], want)
+    full, _ = O.pconv_mask(np.ones((1, 4, 4)), 3, 1, 1)
+    assert full[0, 1, 1] == 1.0 and full[0, 0, 0] == 9 / 4 and full[0, 0, 1] == 9 / 6
+
+
+def test_partial_conv_matches_the_definition():
+    """W^T (X * M) * sum(1) / sum(M) + b over each window (Liu et al. 2018),
+    written as plain loops."""
+    rng = np.random.default_rng(53)
+    A, H, W, C, O_ = 2, 6, 7, 3, 2
+    m = (rng.random((A, H, W)) < 0.4).astype(float)
+    x = rng.standard_normal((A, H, W, C)) * m[..., None]
+    w = rng.standard_normal((O_, 3, 3, C)).astype(np.float32)
+    b = rng.standard_normal(O_).astype(np.float32)
+    y, mo = O.pconv(x, m, w, b, 1, 2, 0)
+    for a in range(A):
+        for i in range(H):
+            for j in range(W):
+                acc, cnt = np.zeros(O_), 0.0
+                for ky in range(3):
+                    for kx in range(3):
+                        yy, xx = i + 2 * (ky - 1), j + 2 * (kx - 1)
+                        if 0 <= yy < H and 0 <= xx < W and m[a, yy, xx]:
+                            cnt += 1
+                            acc += w[:, ky, kx, :].astype(np.float64) @ x[a, yy, xx]
+                want = acc * 9.0 / cnt + b if cnt else np.zeros(O_)
+                assert np.allclose(y[a, i, j], want, rtol=1e-12, atol=1e-12)
+                assert mo[a, i, j] == (cnt > 0)
+
+
+def test_residual_link_and_masked_zeros():
+    rng = np.random.default_rng(54)
+    m = (rng.random((1, 8, 8)) < 0.3).astype(float)
+    r = rng.standard_normal((1, 8, 8, 4)) * m[..., None]
+    y, _ = O.pconv(r, m, np.zeros((4, 3, 3, 4), np.float32), np.zeros(4, np.float32), 1, 1, O.ACT_ELU, r)
+    assert np.array_equal(y, r)  # ELU(0) + r
+    # Through the whole network: every layer's output vanishes outside its mask;
+    # with every bin valid the first layer is an ordinary conv away from the border.
+    net = O.parse_net(synth.net_blob(synth.ARCH_PAPER, (8, 16), 55))
+    x = rng.random((2, 16, 16, 5))
+    x[..., 4] = 1.0
+    cout, cin, k, stride, act, w, b = net["layers"][0]
+    y0, _ = O.pconv(x, x[..., 4], w, b, 1, 1, act)
+    plain = O.elu(O.conv2d(x, w, b, 1))
+    assert np.allclose(y0[:, 1:-1, 1:-1], plain[:, 1:-1, 1:-1], rtol=1e-12, atol=1e-12)
+    x[..., 4] = (rng.random((2, 16, 16)) < 0.05)
+    x[..., :4] *= x[..., 4:5]
+    out = O.cnn_forward(x, net)
+    assert out.shape == (2, 16, 16) and np.all(np.isfinite(out)) and np.all(out >= 0)
