@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
       int leaf = (int)(mg / HWo), r = (int)(mg % HWo);
       int oy = r / a.Wout, ox = r % a.Wout;
       a_iy[v] = oy * a.stride - a.pad;
-      a_ix[v] = ox * a.stride - a.pad;
+      a_ix[v] = ox * a.stride - a.pad;  // pad = dil * (k / 2)
       a_base[v] = leaf * a.Hin;
     } else {
       a_iy[v] = -100000;
@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
   auto load = [&](int k0) {
     int kk = k0 + a_kq * 4;
     int tap = kk / a.Cin, c = kk - tap * a.Cin;
-    int ky = tap / a.k, kx = tap - ky * a.k;
+    const int dl = a.dil > 1 ? a.dil : 1;
+    int ky = (tap / a.k) * dl, kx = (tap - (tap / a.k) * a.k) * dl;
 #pragma unroll
     for (int v = 0; v < A_VEC; ++v) {
       int iy = a_iy[v] + ky, ix = a_ix[v] + kx;
@@ -226,13 +227,22 @@ __global__ void __launch_bounds__(256) k_conv_f32(ConvArgs a) {
     int leaf = (int)(mg / HWo), r = (int)(mg % HWo);
     int oy = r / a.Wout, ox = r % a.Wout;
     float o[TN];
+    const float ps = a.scale ? __ldg(a.scale + mg) : 1.0f;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       int n = n0 + ty * TN + j;
-      o[j] = n < a.Cout ? activate(acc[i][j] + __ldg(a.bias + n), a.act) : 0.0f;
+      const float bn = n < a.Cout ? __ldg(a.bias + n) : 0.0f;
+      const float v = a.scale ? (ps > 0.0f ? acc[i][j] * ps + bn : 0.0f) : acc[i][j] + bn;
+      o[j] = n < a.Cout ? activate(v, a.act) : 0.0f;
     }
     int nb = n0 + ty * TN;
     if (nb >= a.Cout) continue;
+    if (a.res) {
+      const float *rp = ((const float *)a.res) + (size_t)mg * a.res_cs + a.res_co + nb;
+#pragma unroll
+      for (int j = 0; j < TN; ++j)
+        if (nb + j < a.Cout) o[j] += __ldg(rp + j);
+    }
     int reps = a.ups ? 2 : 1;
     int Ho = a.Hout * reps, Wo = a.Wout * reps;
     for (int dy = 0; dy < reps; ++dy)
@@ -317,8 +327,85 @@ pg_status net_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
 static size_t act_floats_per_leaf(const Net *net, int H, int W) {
   size_t HW = (size_t)H * W;
   if (net->arch == 0) return HW * (8 + 2 * (size_t)net->widths[0]);
+  if (net->arch == 2) {
+    const size_t c0 = net->widths[0], c1 = net->widths[1];
+    return HW * (c0 + (c1 + c0) + 2 * c0) + HW / 4 * (c1 + 2 * c1 + 2 * c1) + HW / 16 * 2 * c1 +
+           paper_mask_floats_per_leaf(H, W);
+  }
   size_t c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
   return HW * (8 + (c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;
+}
+
+// ---------------------------------------------------------------- paper-style net (arch 2)
+// Partial-convolution masks (Liu et al. 2018, the masked convolutions of
+// Sec. 5.1): for each output pixel the number c of valid input pixels under
+// its 3x3 window (taps dil apart, stride, zero outside the map); scale =
+// 9 / c where c > 0, else 0; the output mask is c > 0.
+__global__ void k_pconv_mask(const float *__restrict__ m_in, int in_cs, int Hin, int Win, int stride, int dil,
+                             long M, int Hout, int Wout, float *__restrict__ scale, float *__restrict__ m_out) {
+  const long mg = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (mg >= M) return;
+  const int HWo = Hout * Wout;
+  const int leaf = (int)(mg / HWo), r = (int)(mg % HWo), oy = r / Wout, ox = r % Wout;
+  int c = 0;
+  for (int ky = -1; ky <= 1; ++ky)
+    for (int kx = -1; kx <= 1; ++kx) {
+      const int iy = oy * stride + ky * dil, ix = ox * stride + kx * dil;
+      if (iy >= 0 && iy < Hin && ix >= 0 && ix < Win)
+        c += m_in[((size_t)(leaf * Hin + iy) * Win + ix) * in_cs] > 0.0f ? 1 : 0;
+    }
+  scale[mg] = c ? 9.0f / (float)c : 0.0f;
+  if (m_out) m_out[mg] = c ? 1.0f : 0.0f;
+}
+
+// Mask of a decoder concatenation: the union of the upsampled (nearest x2)
+// deeper mask and the skip's mask.
+__global__ void k_mask_union_up(const float *__restrict__ deep, const float *__restrict__ skip, long M, int H, int W,
+                                float *__restrict__ out) {
+  const long mg = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (mg >= M) return;
+  const int HW = H * W, leaf = (int)(mg / HW), r = (int)(mg % HW), y = r / W, x = r % W;
+  const float d = deep[((size_t)leaf * (H / 2) + y / 2) * (W / 2) + x / 2];
+  out[mg] = fmaxf(d, skip[mg]);
+}
+
+size_t paper_mask_floats_per_leaf(int H, int W) {
+  const size_t HW = (size_t)H * W;
+  // 11 scales and 11 masks: 4 + 4 at full resolution, 4 + 4 at half, 3 + 3 at quarter; 2 unions.
+  return 8 * HW + 8 * HW / 4 + 6 * HW / 16 + HW + HW / 4;
+}
+
+pg_status paper_masks(pg_ctx *ctx, const float *x0, uint32_t ns, int H, int W, float *buf, PaperMasks *pm,
+                      cudaStream_t st) {
+  const long M0 = (long)ns * H * W, M1 = M0 / 4, M2 = M0 / 16;
+  float *q = buf;
+  auto take = [&](long n) { float *p = q; q += n; return p; };
+  float *s[12] = {}, *m[12] = {};
+  const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
+  auto mask = [&](int l, const float *in, int in_cs, int Hin, int Win, int stride, int dil, long M, int Ho, int Wo) {
+    s[l] = take(M);
+    m[l] = take(M);
+    k_pconv_mask<<<ceil_div(M, 256), 256, 0, st>>>(in, in_cs, Hin, Win, stride, dil, M, Ho, Wo, s[l], m[l]),
+        PG_COUNT(ctx);
+  };
+  mask(0, x0 + 4, 8, H, W, 1, 1, M0, H, W);        // input mask: the B channel
+  mask(1, m[0], 1, H, W, 1, 1, M0, H, W);          // e0
+  mask(2, m[1], 1, H, W, 2, 1, M1, H1, W1);
+  mask(3, m[2], 1, H1, W1, 1, 1, M1, H1, W1);      // e1
+  mask(4, m[3], 1, H1, W1, 2, 1, M2, H2, W2);
+  mask(5, m[4], 1, H2, W2, 1, 2, M2, H2, W2);
+  mask(6, m[5], 1, H2, W2, 1, 4, M2, H2, W2);
+  float *u7 = take(M1);
+  k_mask_union_up<<<ceil_div(M1, 256), 256, 0, st>>>(m[6], m[3], M1, H1, W1, u7), PG_COUNT(ctx);
+  mask(7, u7, 1, H1, W1, 1, 1, M1, H1, W1);
+  mask(8, m[7], 1, H1, W1, 1, 1, M1, H1, W1);
+  float *u9 = take(M0);
+  k_mask_union_up<<<ceil_div(M0, 256), 256, 0, st>>>(m[8], m[1], M0, H, W, u9), PG_COUNT(ctx);
+  mask(9, u9, 1, H, W, 1, 1, M0, H, W);
+  mask(10, m[9], 1, H, W, 1, 1, M0, H, W);
+  PG_CUDA(cudaGetLastError());
+  for (int l = 0; l < 12; ++l) pm->scale[l] = s[l];
+  return PG_OK;
 }
 
 // Per-leaf photon count: the sum of the leaf's current count plane.
@@ -418,18 +505,53 @@ pg_status forward_f32(pg_ctx *ctx, const Net *net, const float *x0, void *actv, 
   float *act = (float *)actv;
   const Layer *Ls = net->layers;
   auto conv = [&](const Layer &L, const float *in, int in_cs, int in_co, int Hin, int Win, float *out, int out_cs,
-                  int out_co, int ups) -> pg_status {
+                  int out_co, int ups, const float *scale = nullptr, const float *res = nullptr, int res_cs = 0,
+                  int res_co = 0) -> pg_status {
     ConvArgs a;
     memset(&a, 0, sizeof(a));
     a.in = in; a.in_cs = in_cs; a.in_co = in_co; a.Hin = Hin; a.Win = Win; a.Cin = L.cin;
     a.out = out; a.out_cs = out_cs; a.out_co = out_co;
     a.Hout = Hin / L.stride; a.Wout = Win / L.stride; a.Cout = L.cout;
-    a.k = L.k; a.stride = L.stride; a.pad = L.k / 2;
+    a.dil = L.dil > 1 ? L.dil : 1;
+    a.k = L.k; a.stride = L.stride; a.pad = a.dil * (L.k / 2);
     a.w = L.w; a.bias = L.b; a.act = L.act; a.ups = ups;
+    a.scale = scale;
+    a.res = res; a.res_cs = res_cs; a.res_co = res_co;
     a.M = (long)ns * a.Hout * a.Wout;
     return conv_f32(ctx, a, st);
   };
   const size_t HW = (size_t)H * W;
+  if (net->arch == 2) {
+    const int c0 = net->widths[0], c1 = net->widths[1];
+    const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
+    const int k0c = c1 + c0, k1c = 2 * c1;
+    float *a0 = act;                               // [ns][H][W][c0]
+    float *cat0 = a0 + ns * HW * c0;               // [ns][H][W][c1+c0]   up(d1b) | e0
+    float *d0 = cat0 + ns * HW * k0c;              // [ns][H][W][c0]
+    float *d0b = d0 + ns * HW * c0;                // [ns][H][W][c0]
+    float *a1 = d0b + ns * HW * c0;                // [ns][H1][W1][c1]
+    float *cat1 = a1 + ns * HW / 4 * c1;           // [ns][H1][W1][2c1]   up(b2) | e1
+    float *d1 = cat1 + ns * HW / 4 * k1c;          // [ns][H1][W1][c1]
+    float *b0 = d1 + ns * HW / 4 * c1;             // [ns][H2][W2][c1]
+    float *b1 = b0 + ns * HW / 16 * c1;            // [ns][H2][W2][c1]
+    float *mbuf = b1 + ns * HW / 16 * c1;
+    PaperMasks pm;
+    PG_TRY(paper_masks(ctx, x0, ns, H, W, mbuf, &pm, st));
+    // Encoder (residual links within a level), dilated bottleneck, decoder.
+    PG_TRY(conv(Ls[0], x0, 8, 0, H, W, a0, c0, 0, 0, pm.scale[0]));
+    PG_TRY(conv(Ls[1], a0, c0, 0, H, W, cat0, k0c, c1, 0, pm.scale[1], a0, c0, 0));            // e0
+    PG_TRY(conv(Ls[2], cat0, k0c, c1, H, W, a1, c1, 0, 0, pm.scale[2]));
+    PG_TRY(conv(Ls[3], a1, c1, 0, H1, W1, cat1, k1c, c1, 0, pm.scale[3], a1, c1, 0));          // e1
+    PG_TRY(conv(Ls[4], cat1, k1c, c1, H1, W1, b0, c1, 0, 0, pm.scale[4]));
+    PG_TRY(conv(Ls[5], b0, c1, 0, H2, W2, b1, c1, 0, 0, pm.scale[5], b0, c1, 0));              // dilation 2
+    PG_TRY(conv(Ls[6], b1, c1, 0, H2, W2, cat1, k1c, 0, 1, pm.scale[6], b1, c1, 0));           // dilation 4, up
+    PG_TRY(conv(Ls[7], cat1, k1c, 0, H1, W1, d1, c1, 0, 0, pm.scale[7]));
+    PG_TRY(conv(Ls[8], d1, c1, 0, H1, W1, cat0, k0c, 0, 1, pm.scale[8], d1, c1, 0));           // up
+    PG_TRY(conv(Ls[9], cat0, k0c, 0, H, W, d0, c0, 0, 0, pm.scale[9]));
+    PG_TRY(conv(Ls[10], d0, c0, 0, H, W, d0b, c0, 0, 0, pm.scale[10], d0, c0, 0));
+    PG_TRY(conv(Ls[11], d0b, c0, 0, H, W, y, 1, 0, 0));                                          // 1x1 head
+    return PG_OK;
+  }
   if (net->arch == 0) {
     int c = net->widths[0];
     float *t0 = act, *t1 = act + ns * HW * c;

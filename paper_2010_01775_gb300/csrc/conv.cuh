@@ -22,6 +22,14 @@ struct ConvArgs {
   long M;             // leaves x Hout x Wout
   int act;            // 0 none, 1 ELU, 2 softplus
   int ups;
+  int dil;            // tap spacing (dilated convolution); 0 means 1
+  // Partial convolution: per output pixel [M] scale k^2 / (valid inputs under
+  // the window), 0 where none is valid (output act(0)); null for a plain layer.
+  const float *scale;
+  // Residual link: added after the activation, same pixel indexing as the
+  // output (no upsampling), channel stride res_cs, first channel res_co.
+  const void *res;
+  int res_cs, res_co;
 };
 
 pg_status conv_f32(pg_ctx *ctx, const ConvArgs &a, cudaStream_t st);
@@ -32,5 +40,15 @@ pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
 pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float *x0, void *act, uint32_t ns,
                      int H, int W, float *y, cudaStream_t st, bool tune = false);
 size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W);
+
+// Masks and partial-convolution scales of the paper-style network (arch 2),
+// computed once per chunk from the input mask (the B channel): scale[l] is
+// the [ns][Hout][Wout] map of layer l (null for the head).
+struct PaperMasks {
+  const float *scale[12];
+};
+size_t paper_mask_floats_per_leaf(int H, int W);
+pg_status paper_masks(pg_ctx *ctx, const float *x0, uint32_t ns, int H, int W, float *buf, PaperMasks *pm,
+                      cudaStream_t st);
 
 }  // namespace pgi

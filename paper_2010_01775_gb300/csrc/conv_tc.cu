@@ -1281,6 +1281,7 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
 pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const float *x0, void *actv, uint32_t ns, int H,
                      int W, float *y, cudaStream_t st, bool tune) {
   Net *net = const_cast<Net *>(netc);
+  if (net->arch == 2) return PG_ERR_UNSUPPORTED;
   if (prec == PG_BF16)
     return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr, tune);
   if (prec != PG_FP8_E4M3) return PG_ERR_UNSUPPORTED;

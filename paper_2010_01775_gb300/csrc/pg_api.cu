@@ -657,8 +657,8 @@ pg_status pg_net_load(pg_ctx *c, const void *blob, size_t bytes, pg_net **out) {
   memcpy(hdr, b, 32);
   if (hdr[0] != 0x314E4750u || hdr[2] != 5u) return PG_ERR_INVALID_ARG;
   uint32_t arch = hdr[1], nl = hdr[3];
-  static const int expect_layers[2] = {3, 15};
-  if (arch > 1 || nl != (uint32_t)expect_layers[arch]) return PG_ERR_UNSUPPORTED;
+  static const int expect_layers[3] = {3, 15, 12};
+  if (arch > 2 || nl != (uint32_t)expect_layers[arch]) return PG_ERR_UNSUPPORTED;
   Net *net = new (std::nothrow) Net();
   if (!net) return PG_ERR_OOM;
   memset(net, 0, sizeof(*net));
@@ -676,7 +676,9 @@ pg_status pg_net_load(pg_ctx *c, const void *blob, size_t bytes, pg_net **out) {
     off += 24;
     Layer &L = net->layers[l];
     L.cout = (int)d[0]; L.cin = (int)d[1]; L.k = (int)d[2]; L.stride = (int)d[3]; L.act = (int)d[4];
-    if (L.cout <= 0 || L.cin <= 0 || (L.k != 1 && L.k != 3) || (L.stride != 1 && L.stride != 2) || L.act > 2) {
+    L.dil = d[5] ? (int)d[5] : 1;
+    if (L.cout <= 0 || L.cin <= 0 || (L.k != 1 && L.k != 3) || (L.stride != 1 && L.stride != 2) || L.act > 2 ||
+        (L.dil != 1 && L.dil != 2 && L.dil != 4 && L.dil != 8) || (L.dil > 1 && (L.k != 3 || L.stride != 1))) {
       delete net;
       return PG_ERR_INVALID_ARG;
     }
@@ -738,7 +740,7 @@ pg_status pg_reconstruct(pg_ctx *c, const pg_hist *hist, const pg_net *netp, pg_
   if (!c || !h || !net || !out) return PG_ERR_INVALID_ARG;
   *out = nullptr;
   if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
-  if (net->arch == 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
+  if (net->arch >= 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
   PG_TRY(net_prepare(c, net, prec));
   Map *m = new (std::nothrow) Map();
   if (!m) return PG_ERR_OOM;
@@ -774,7 +776,7 @@ pg_status pg_reconstruct_experts(pg_ctx *c, const pg_hist *hist, const pg_net *c
   for (int e = 0; e < n_experts; ++e) {
     ns[e] = as<Net>(nets[e], KIND_NET);
     if (!ns[e]) return PG_ERR_INVALID_ARG;
-    if (ns[e]->arch == 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
+    if (ns[e]->arch >= 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
     if (e + 1 < n_experts && e > 0 && count_bounds[e] <= count_bounds[e - 1]) return PG_ERR_INVALID_ARG;
   }
   const uint32_t A = h->A;
@@ -1197,7 +1199,7 @@ pg_status pg_progress_reconstruct(pg_ctx *c, pg_progress *sp, const pg_net *netp
   Net *net = as<Net>(netp, KIND_NET);
   if (!c || !s || !net || !s->grid) return PG_ERR_INVALID_ARG;
   if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
-  if (net->arch == 1 && (s->p.H < 8 || s->p.W < 8)) return PG_ERR_UNSUPPORTED;
+  if (net->arch >= 1 && (s->p.H < 8 || s->p.W < 8)) return PG_ERR_UNSUPPORTED;
   PG_TRY(net_prepare(c, net, prec));
   const uint32_t A = s->n_updated;
   const int HW = s->p.H * s->p.W;

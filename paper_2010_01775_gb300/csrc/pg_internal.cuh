@@ -103,6 +103,7 @@ struct Hist {
 
 struct Layer {
   int cout, cin, k, stride, act;
+  int dil;    // tap spacing (1 except dilated layers)
   float *w;   // device, [k*k*cin][cout] (GEMM B operand, K-major rows)
   float *b;   // device, [cout]
   void *w_bf16;  // device, BF16 copy [cout][K] (tensor-core layout), or null
