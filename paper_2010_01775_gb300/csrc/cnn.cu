@@ -459,7 +459,7 @@ pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_preci
   if (A == 0) return PG_OK;
   const int H = h->H, W = h->W, HW = H * W;
   // BF16 assembles straight into the packed first-layer input (no FP32 x0).
-  const bool packed = prec == PG_BF16;
+  const bool packed = prec == PG_BF16 && net->arch != 2;  // the paper-style net reads its mask from x0
   const size_t x0_per_leaf = packed ? 0 : 8 * (size_t)HW * 4;
   const size_t per_leaf = x0_per_leaf + (prec == PG_FP32 ? act_floats_per_leaf(net, H, W) * 4
                                                          : tc_bytes_per_leaf(net, prec, H, W));

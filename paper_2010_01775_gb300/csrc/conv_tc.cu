@@ -90,6 +90,14 @@ struct TcArgs {
   // map y instead of the layer's activations.
   const float *head_w, *head_b;
   float *head_y;
+  // Paper-style layers: taps dil apart (operand mode 0 only); per output
+  // pixel partial-convolution scale (null: plain layer; 0: output act(0));
+  // residual link (BF16, same pixel indexing as the output) added after the
+  // activation.
+  int dil;
+  const float *pscale;
+  const void *res;
+  int res_cs, res_co;
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -222,19 +230,38 @@ __device__ __forceinline__ float elu_lp(float v) { return v > 0.0f ? v : __expf(
 // output bytes: one 16-byte chunk (E4M3) or two (BF16).
 template <bool kFp8Out, bool kCalib>
 __device__ __forceinline__ void epi_convert16(const TcArgs &a, const uint32_t *r, const float *s_bias, int c,
-                                              float &amax, uint4 *chunk) {
+                                              float &amax, uint4 *chunk, float ps = 1.0f,
+                                              const __nv_bfloat16 *resp = nullptr) {
   float v[16];
+  if (a.pscale) {
+    // Partial convolution: acc * scale + bias where a valid input lies under
+    // the window, else 0 (before the activation).
 #pragma unroll
-  for (int j = 0; j < 16; j += 4) {
-    const float4 b = *reinterpret_cast<const float4 *>(s_bias + c + j);
-    v[j] = fmaf(__uint_as_float(r[j]), a.acc_mul, b.x);
-    v[j + 1] = fmaf(__uint_as_float(r[j + 1]), a.acc_mul, b.y);
-    v[j + 2] = fmaf(__uint_as_float(r[j + 2]), a.acc_mul, b.z);
-    v[j + 3] = fmaf(__uint_as_float(r[j + 3]), a.acc_mul, b.w);
+    for (int j = 0; j < 16; ++j)
+      v[j] = ps > 0.0f ? fmaf(__uint_as_float(r[j]) * a.acc_mul, ps, s_bias[c + j]) : 0.0f;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) {
+      const float4 b = *reinterpret_cast<const float4 *>(s_bias + c + j);
+      v[j] = fmaf(__uint_as_float(r[j]), a.acc_mul, b.x);
+      v[j + 1] = fmaf(__uint_as_float(r[j + 1]), a.acc_mul, b.y);
+      v[j + 2] = fmaf(__uint_as_float(r[j + 2]), a.acc_mul, b.z);
+      v[j + 3] = fmaf(__uint_as_float(r[j + 3]), a.acc_mul, b.w);
+    }
   }
   if (a.act == 1) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = elu_lp(v[j]);
+  }
+  if (resp) {
+    const uint4 q0 = *reinterpret_cast<const uint4 *>(resp), q1 = *reinterpret_cast<const uint4 *>(resp + 8);
+    const uint32_t qw[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&qw[j]));
+      v[2 * j] += f.x;
+      v[2 * j + 1] += f.y;
+    }
   }
   if (kCalib) {
 #pragma unroll
@@ -471,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             int ky = tap / a.k, kx = tap - ky * a.k;
             if (lane == 0)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk,
-                          x0 * a.stride + kx - a.pad, y0 * a.stride + ky - a.pad, l0);
+                          x0 * a.stride + kx * a.dil - a.pad, y0 * a.stride + ky * a.dil - a.pad, l0);
             else
               tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
           }
@@ -625,14 +652,20 @@ __global__ void __launch_bounds__(kThreads, 2)
             valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
           }
           const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN);
+          const size_t hpix = ((size_t)leaf * a.Hout + y) * a.Wout + x;
+          const float hps = (a.pscale && valid) ? a.pscale[hpix] : 0.0f;
+          const __nv_bfloat16 *hres =
+              (a.res && valid) ? (const __nv_bfloat16 *)a.res + hpix * a.res_cs + a.res_co : nullptr;
           float hacc = 0.0f;
           for (int c = 0; c < a.BN; c += 16) {
             uint32_t r[16];
             tmem_ld16(trow + (uint32_t)c, r);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              float v = fmaf(__uint_as_float(r[j]), a.acc_mul, s_bias[c + j]);
+              float v = a.pscale ? (hps > 0.0f ? fmaf(__uint_as_float(r[j]) * a.acc_mul, hps, s_bias[c + j]) : 0.0f)
+                                 : fmaf(__uint_as_float(r[j]), a.acc_mul, s_bias[c + j]);
               if (a.act == 1) v = elu_lp(v);
+              if (hres) v += __bfloat162float(hres[c + j]);
               if (kCalib) amax_local = fmaxf(amax_local, fabsf(v));
               hacc = fmaf(s_head[c + j], v, hacc);
             }
@@ -669,18 +702,23 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN + c);
       const size_t pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
+      const size_t opix = ((size_t)leaf * a.Hout + y) * a.Wout + x;  // before the x2 upsampled store
+      const float ps = (a.pscale && valid) ? a.pscale[opix] : 0.0f;
+      const __nv_bfloat16 *resp =
+          (a.res && valid) ? (const __nv_bfloat16 *)a.res + opix * a.res_cs + a.res_co + c : nullptr;
       uint4 chunk[4];
       int cpp;
       if (cw == 32) {
         uint32_t r[32];
         tmem_ld32(trow, r);
-        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk);
-        epi_convert16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, amax_local, chunk + (kFp8Out ? 1 : 2));
+        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk, ps, resp);
+        epi_convert16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, amax_local, chunk + (kFp8Out ? 1 : 2), ps,
+                                       resp ? resp + 16 : nullptr);
         cpp = kFp8Out ? 2 : 4;
       } else {
         uint32_t r[16];
         tmem_ld16(trow, r);
-        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk);
+        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk, ps, resp);
         cpp = kFp8Out ? 1 : 2;
       }
       if (a.stage_out)
@@ -816,6 +854,10 @@ struct LpLayer {
   unsigned int *amax;
   const float *head_w = nullptr, *head_b = nullptr;  // fused 1x1 head (see TcArgs)
   float *head_y = nullptr;
+  int dil = 1;                                         // paper-style layers (see TcArgs)
+  const float *pscale = nullptr;
+  const void *res = nullptr;
+  int res_cs = 0, res_co = 0;
 };
 
 // Launch shape: CTAs resident per SM and pipeline stages per CTA.  Zero
@@ -861,7 +903,8 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   memset(&a, 0, sizeof(a));
   a.k = L.k;
   a.stride = L.stride;
-  a.pad = L.k / 2;
+  a.dil = L.dil > 1 ? L.dil : 1;
+  a.pad = a.dil * (L.k / 2);
   a.Cin = L.Cin;
   a.chunk = cb / es;
   a.cchunks = L.Cin / a.chunk;
@@ -883,6 +926,8 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     return PG_ERR_UNSUPPORTED;
   a.num_tiles = (int)((M + TP - 1) / TP);
   a.halo = cfg.halo;
+  if (a.dil > 1 && a.halo) return PG_ERR_UNSUPPORTED;  // haloed operand modes assume adjacent taps
+  if ((L.pscale || L.res) && fp8_out) return PG_ERR_UNSUPPORTED;  // paper-style layers run in BF16
   if (a.halo == 1 && (L.k != 3 || L.stride != 1 || a.Lt != 1 || a.Ht + 2 > 256)) return PG_ERR_UNSUPPORTED;
   a.chunk_bytes = cb;
   a.kiters = a.halo ? a.cchunks : L.k * L.k * a.cchunks;
@@ -945,6 +990,10 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.head_w = L.head_w;
   a.head_b = L.head_b;
   a.head_y = L.head_y;
+  a.pscale = L.pscale;
+  a.res = L.res;
+  a.res_cs = L.res_cs;
+  a.res_co = L.res_co;
   if (a.head_y && (L.ups || L.Cout % 16)) return PG_ERR_UNSUPPORTED;
   a.stats = nullptr;
   static unsigned long long *d_stats = nullptr;
@@ -1167,7 +1216,8 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
     PG_CUDA(cudaGetLastError());
   }
   auto conv = [&](int li, const void *in, int in_cs, int in_co, int Hin, int Win, int Cin, void *out, int out_cs,
-                  int out_co, int ups, const Layer *head = nullptr) -> pg_status {
+                  int out_co, int ups, const Layer *head = nullptr, const float *pscale = nullptr,
+                  const void *res = nullptr, int res_cs = 0, int res_co = 0) -> pg_status {
     const Layer &Lr = Ls[li];
     LpLayer L;
     if (head) {
@@ -1175,6 +1225,11 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       L.head_b = head->b;
       L.head_y = y;
     }
+    L.dil = Lr.dil;
+    L.pscale = pscale;
+    L.res = res;
+    L.res_cs = res_cs;
+    L.res_co = res_co;
     L.in = in; L.in_cs = in_cs; L.in_co = in_co; L.Hin = Hin; L.Win = Win; L.Cin = Cin;
     L.out = out; L.out_cs = out_cs; L.out_co = out_co; L.ups = ups;
     L.Cout = Lr.cout; L.k = Lr.k; L.stride = Lr.stride; L.act = Lr.act;
@@ -1239,6 +1294,38 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
     PG_CUDA(cudaGetLastError());
     return PG_OK;
   };
+  if (net->arch == 2) {
+    // The paper-style network (BF16 only): partial convolutions with the
+    // FP32 scale maps of the mask pyramid, residual links, dilated
+    // bottleneck; the 1x1 head runs in layer 10's epilogue.
+    if (fp8 || !x0) return PG_ERR_UNSUPPORTED;
+    const int c0 = net->widths[0], c1 = net->widths[1];
+    const int H1 = H / 2, W1 = W / 2, H2 = H / 4, W2 = W / 4;
+    const int k0c = c1 + c0, k1c = 2 * c1;
+    T *a0 = (T *)act;
+    T *cat0 = a0 + ns * HW * c0;
+    T *d0 = cat0 + ns * HW * k0c;
+    T *d0b = d0 + ns * HW * c0;
+    T *a1 = d0b + ns * HW * c0;
+    T *cat1 = a1 + ns * HW / 4 * c1;
+    T *d1 = cat1 + ns * HW / 4 * k1c;
+    T *b0 = d1 + ns * HW / 4 * c1;
+    T *b1 = b0 + ns * HW / 16 * c1;
+    float *mbuf = (float *)(b1 + ns * HW / 16 * c1);
+    PaperMasks pm;
+    PG_TRY(paper_masks(ctx, x0, ns, H, W, mbuf, &pm, st));
+    PG_TRY(conv(0, xcol, cp, 0, H, W, cp, a0, c0, 0, 0, nullptr, pm.scale[0]));
+    PG_TRY(conv(1, a0, c0, 0, H, W, c0, cat0, k0c, c1, 0, nullptr, pm.scale[1], a0, c0, 0));        // e0
+    PG_TRY(conv(2, cat0, k0c, c1, H, W, c0, a1, c1, 0, 0, nullptr, pm.scale[2]));
+    PG_TRY(conv(3, a1, c1, 0, H1, W1, c1, cat1, k1c, c1, 0, nullptr, pm.scale[3], a1, c1, 0));      // e1
+    PG_TRY(conv(4, cat1, k1c, c1, H1, W1, c1, b0, c1, 0, 0, nullptr, pm.scale[4]));
+    PG_TRY(conv(5, b0, c1, 0, H2, W2, c1, b1, c1, 0, 0, nullptr, pm.scale[5], b0, c1, 0));          // dilation 2
+    PG_TRY(conv(6, b1, c1, 0, H2, W2, c1, cat1, k1c, 0, 1, nullptr, pm.scale[6], b1, c1, 0));       // dilation 4, up
+    PG_TRY(conv(7, cat1, k1c, 0, H1, W1, k1c, d1, c1, 0, 0, nullptr, pm.scale[7]));
+    PG_TRY(conv(8, d1, c1, 0, H1, W1, c1, cat0, k0c, 0, 1, nullptr, pm.scale[8], d1, c1, 0));       // up
+    PG_TRY(conv(9, cat0, k0c, 0, H, W, k0c, d0, c0, 0, 0, nullptr, pm.scale[9]));
+    return conv(10, d0, c0, 0, H, W, c0, d0b, c0, 0, 0, &Ls[11], pm.scale[10], d0, c0, 0);
+  }
   if (net->arch == 0) {
     const int c = net->widths[0];
     T *t0 = (T *)act, *t1 = t0 + M0 * c;
@@ -1281,7 +1368,7 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
 pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const float *x0, void *actv, uint32_t ns, int H,
                      int W, float *y, cudaStream_t st, bool tune) {
   Net *net = const_cast<Net *>(netc);
-  if (net->arch == 2) return PG_ERR_UNSUPPORTED;
+  if (net->arch == 2 && prec != PG_BF16) return PG_ERR_UNSUPPORTED;
   if (prec == PG_BF16)
     return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr, tune);
   if (prec != PG_FP8_E4M3) return PG_ERR_UNSUPPORTED;
@@ -1321,6 +1408,11 @@ size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W) {
   const size_t es = 2, HW = (size_t)H * W;
   size_t n = HW * 16;  // first-layer input, 32 bytes per pixel
   if (net->arch == 0) return es * (n + 2 * HW * net->widths[0]) + 1024;
+  if (net->arch == 2) {
+    const size_t c0 = net->widths[0], c1 = net->widths[1];
+    n += HW * (c0 + (c1 + c0) + 2 * c0) + HW / 4 * (c1 + 2 * c1 + c1) + HW / 16 * 2 * c1;
+    return es * n + 4 * paper_mask_floats_per_leaf(H, W) + 1024;
+  }
   const size_t c0 = net->widths[0], c1 = net->widths[1], c2 = net->widths[2], c3 = net->widths[3];
   n += HW * ((c1 + c0) + 2 * c0) + HW / 4 * ((c2 + c1) + c1) + HW / 16 * ((c3 + c2) + c2) + HW / 64 * c3;
   return es * n + 1024;

@@ -81,3 +81,42 @@ def test_paper_net_rejects_small_maps_and_fp8(ctx):
     with pytest.raises(pg.PgError) as e:
         pg.pg_reconstruct(ctx, h, net, pg.PG_FP32)
     assert e.value.status == 9
+
+
+def _kl(P, Pr):
+    out = []
+    for a in range(P.shape[0]):
+        p, q = Pr[a].ravel(), np.maximum(P[a].ravel(), 1e-30)
+        nz = p > 0
+        out.append(float(np.sum(p[nz] * np.log(p[nz] / q[nz]))))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n,H,W,widths,seed", [(60_000, 32, 32, (32, 64), 91), (40_000, 64, 64, (32, 64), 92)])
+def test_paper_net_bf16_kl(ctx, n, H, W, widths, seed):
+    """The tensor-core BF16 form within the reduced-precision gate (KL <= 1e-3)."""
+    ph = synth.photons(n, 8, seed)
+    d = torch.from_numpy(ph).cuda()
+    g = pg.pg_build_grid(ctx, d, n, LO, HI, 4, 0, 800)
+    h = pg.pg_splat_photons(ctx, g, d, n, n // 2, H, W)
+    blob = synth.net_blob(synth.ARCH_PAPER, widths, seed + 1)
+    net = pg.pg_net_load(ctx, blob)
+    P = pg.export_tables(pg.pg_build_cdf(ctx, pg.pg_reconstruct(ctx, h, net, pg.PG_BF16)))["P"]
+    P32 = pg.export_tables(pg.pg_build_cdf(ctx, pg.pg_reconstruct(ctx, h, net, pg.PG_FP32)))["P"]
+    ref = O.build_grid(ph, LO, HI, 4, 0, 800)
+    act, _ = O.active_leaves(ref)
+    hr = O.hist_for_active(O.splat(ph, ref, n // 2, H, W), act)
+    idx = np.linspace(0, act.size - 1, min(8, act.size)).astype(np.int64)
+    hsub = {k: (v[idx] if isinstance(v, np.ndarray) else v) for k, v in hr.items()}
+    Pr, _ = O.normalise(O.cnn_forward(O.assemble_inputs(hsub), O.parse_net(blob)))
+    kl = _kl(P[idx].astype(np.float64), Pr)
+    assert kl.mean() <= 1e-3, kl
+    # Every leaf: BF16 against the FP32 form of the same kernels.
+    kl_all = _kl(P.astype(np.float64), P32.astype(np.float64))
+    assert np.median(kl_all) <= 1e-3 and np.isfinite(kl_all).all()
+    # Autotuned launch shapes (other operand modes sum K in another order, so
+    # BF16 activations may round differently) stay within the same gate.
+    pg.pg_autotune(ctx, h, net, pg.PG_BF16)
+    Pt = pg.export_tables(pg.pg_build_cdf(ctx, pg.pg_reconstruct(ctx, h, net, pg.PG_BF16)))["P"]
+    kl_t = _kl(Pt.astype(np.float64), P32.astype(np.float64))
+    assert np.median(kl_t) <= 1e-3 and _kl(Pt[idx].astype(np.float64), Pr).mean() <= 1e-3
