@@ -50,6 +50,10 @@ def unet_flops_per_leaf(H, W, widths, arch):
     res = {0: (H, W)}
     if arch == synth.ARCH_TINY3:
         return sum(2 * H * W * k * k * cin * cout for cout, cin, k, s, a in layers)
+    if arch == synth.ARCH_PAPER:
+        sizes = [(H, W), (H, W), (H // 2, W // 2), (H // 2, W // 2), (H // 4, W // 4), (H // 4, W // 4),
+                 (H // 4, W // 4), (H // 2, W // 2), (H // 2, W // 2), (H, W), (H, W), (H, W)]
+        return sum(2 * ho * wo * k * k * cin * cout for (cout, cin, k, s, a), (ho, wo) in zip(layers, sizes))
     sizes = [(H, W), (H, W), (H // 2, W // 2), (H // 2, W // 2), (H // 4, W // 4), (H // 4, W // 4),
              (H // 8, W // 8), (H // 8, W // 8), (H // 4, W // 4), (H // 4, W // 4), (H // 2, W // 2),
              (H // 2, W // 2), (H, W), (H, W), (H, W)]
@@ -190,7 +194,8 @@ def run_pg(args, wl, prec):
     if args.load_tuning:
         pg.pg_net_set_tuning(net, np.load(args.load_tuning))
     elif args.autotune:
-        for pr in {prec} | ({pg.PG_BF16, pg.PG_FP8_E4M3} if args.sweep else set()):
+        lp = {pg.PG_BF16, pg.PG_FP8_E4M3} if args.arch == "unet" else {pg.PG_BF16}  # the paper-style net: BF16
+        for pr in {prec} | (lp if args.sweep else set()):
             pg.pg_autotune(ctx, h0, net, pr)
     for ex in experts[1:]:  # same layer shapes: the first net's launch shapes fit every expert
         pg.pg_net_set_tuning(ex, pg.pg_net_get_tuning(net))
@@ -350,7 +355,7 @@ def run_pg(args, wl, prec):
     sweep, maps = {}, {}
     check = None
     if args.sweep and world == 1:
-        for pr in (pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3):
+        for pr in (pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3) if args.arch == "unet" else (pg.PG_FP32, pg.PG_BF16):
             r = main if pr == prec else measure(pr, max(1, min(args.steps, 3)), 1)
             sweep[names[pr]] = {"value": q * len(r["times"]) / (r["total_ms"] / 1e3),
                                 "ms_per_step": r["total_ms"] / len(r["times"]),
@@ -407,7 +412,8 @@ def run_pg(args, wl, prec):
             "gpu_launches": main["launches"],
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                          "traffic": (CNN_DRAM_BYTES_PER_LEAF[(H, W, args.precision)] * A
-                                     if (H, W, args.precision) in CNN_DRAM_BYTES_PER_LEAF else None),
+                                     if (H, W, args.precision) in CNN_DRAM_BYTES_PER_LEAF and args.arch == "unet"
+                                     else None),
                          "kernel": "CNN convolutions (all layers of one reconstruct call)",
                          "peak_source": ("of " + peak_src) if prec != pg.PG_FP32 else
                          "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock"},
@@ -931,6 +937,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--experts", type=int, default=0,
                     help="reconstruct with a mixture of this many experts routed by leaf photon count (Sec. 8)")
+    ap.add_argument("--arch", default="unet", choices=["unet", "paper"],
+                    help="the workload's U-Net, or the paper-style masked U-Net (partial convolutions, residual "
+                         "links, dilated bottleneck, 32-64 channels; BF16 or FP32)")
     ap.add_argument("--grid", default="octree", choices=["octree", "kd"],
                     help="octree grid, or the paper's rule (100^3 voxels refined by binary trees)")
     ap.add_argument("--progressive", action="store_true",
@@ -963,6 +972,10 @@ def main():
         run_batch(args, synth.BATCH_WORKLOADS[args.workload], pg.PRECISIONS[args.precision])
         return
     wl = synth.WORKLOADS[args.workload]
+    if args.arch == "paper":
+        import dataclasses
+        wl = dataclasses.replace(wl, arch=synth.ARCH_PAPER, widths=(32, 64),
+                                 name=wl.name + " (paper-style masked U-Net 32-64)")
     if args.impl == "reference":
         run_reference(args, wl)
         return
