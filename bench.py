@@ -194,7 +194,8 @@ def run_pg(args, wl, prec):
     if args.load_tuning:
         pg.pg_net_set_tuning(net, np.load(args.load_tuning))
     elif args.autotune:
-        lp = {pg.PG_BF16, pg.PG_FP8_E4M3} if args.arch == "unet" else {pg.PG_BF16}  # the paper-style net: BF16
+        lp = ({pg.PG_BF16, pg.PG_FP8_E4M3, pg.PG_FP8_MIXED} if args.arch == "unet"
+              else {pg.PG_BF16})  # the paper-style net: BF16
         for pr in {prec} | (lp if args.sweep else set()):
             pg.pg_autotune(ctx, h0, net, pr)
     for ex in experts[1:]:  # same layer shapes: the first net's launch shapes fit every expert
@@ -352,11 +353,12 @@ def run_pg(args, wl, prec):
 
     # The other precisions of the same workload (shorter runs), and their
     # sampling maps on a few leaves for the CPU-baseline leg's KL check.
-    names = {pg.PG_FP32: "fp32", pg.PG_BF16: "bf16", pg.PG_FP8_E4M3: "fp8"}
+    names = {pg.PG_FP32: "fp32", pg.PG_BF16: "bf16", pg.PG_FP8_E4M3: "fp8", pg.PG_FP8_MIXED: "fp8mix"}
     sweep, maps = {}, {}
     check = None
     if args.sweep and world == 1:
-        for pr in (pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3) if args.arch == "unet" else (pg.PG_FP32, pg.PG_BF16):
+        for pr in ((pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3, pg.PG_FP8_MIXED) if args.arch == "unet"
+                   else (pg.PG_FP32, pg.PG_BF16)):
             r = main if pr == prec else measure(pr, max(1, min(args.steps, 3)), 1)
             sweep[names[pr]] = {"value": q * len(r["times"]) / (r["total_ms"] / 1e3),
                                 "ms_per_step": r["total_ms"] / len(r["times"]),
@@ -382,7 +384,7 @@ def run_pg(args, wl, prec):
         out = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec],
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3", 3: "fp8e4m3+bf16"}[prec],
             "data": "synthetic (seeded photon blobs on room walls, vMF directions, lognormal power; random He-init U-Net)",
             "config": {"workload": wl.name + (" (paper's grid rule)" if args.grid == "kd" else ""), "photons": n,
                        "queries": q, "H": H, "W": W,
@@ -518,7 +520,7 @@ def run_batch(args, bw, prec):
     out = {
         "metric": METRIC, "value": Q / (graph_ms / 1e3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": graph_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec], "data": "synthetic",
+        "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3", 3: "fp8e4m3+bf16"}[prec], "data": "synthetic",
         "config": {"workload": bw.name, "scenes": S, "photons": n, "queries": Q, "leaves": L, "active_leaves": A,
                    "H": bw.H, "W": bw.W, "precision": args.precision,
                    "scene_photons_min_max": [int(np.min(np.diff(begin))), int(np.max(np.diff(begin)))]},
@@ -744,7 +746,7 @@ def run_progressive(args, wl, prec):
         out = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3"}[prec],
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f32", 1: "bf16", 2: "fp8e4m3", 3: "fp8e4m3+bf16"}[prec],
             "data": "synthetic (seeded photon blobs on room walls, vMF directions, lognormal power; random He-init U-Net)",
             "config": {"workload": "progressive iteration, " + wl.name, "photons_per_iteration": n,
                        "refine": f"2 iterations of {n_p} and {2 * n_p} photons, threshold 500 sqrt(2^t)",
@@ -934,7 +936,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pg", choices=["pg", "reference"])
     ap.add_argument("--workload", default="scale")
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8", "fp8mix"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--experts", type=int, default=0,
                     help="reconstruct with a mixture of this many experts routed by leaf photon count (Sec. 8)")

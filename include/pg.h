@@ -51,7 +51,10 @@ typedef enum {
 
 /* Arithmetic of the reconstruction CNN's convolutions (accumulation is FP32
  * in every case). */
-typedef enum { PG_FP32 = 0, PG_BF16 = 1, PG_FP8_E4M3 = 2 } pg_precision;
+/* PG_FP8_MIXED (U-Net only): E4M3 operands inside the network (the layers
+ * below full resolution), BF16 at the full-resolution level, its skip
+ * concatenation and the head; activation scales as for PG_FP8_E4M3. */
+typedef enum { PG_FP32 = 0, PG_BF16 = 1, PG_FP8_E4M3 = 2, PG_FP8_MIXED = 3 } pg_precision;
 
 /* One photon record, 32 bytes: hit position, unit incident direction, power
  * (the flux Delta Phi_p carried by the photon, Eq. "photon" of Sec. 4). */

@@ -574,12 +574,17 @@ __global__ void __launch_bounds__(kThreads, 2)
           const StageOps so{d,         (uint32_t)a.BN, alo_s,        blo_s,   a_base + (uint32_t)stage * a.bytes_a,
                             off0,      a.P,            (uint32_t)a.chunk_bytes, sub_step, row_step, ver16, tap_b16,
                             desc_hi,   a.idesc,        first,   lane};
-          switch (a.halo * 4 + (a.mma_per_stage >> 1)) {
-#define PG_STAGE_CASE(H, MPS) \
-  case H * 4 + (MPS >> 1): issue_stage<kFp8Out, H, MPS>(so); break;
-            PG_STAGE_CASE(0, 1) PG_STAGE_CASE(0, 2) PG_STAGE_CASE(0, 4)
-            PG_STAGE_CASE(1, 1) PG_STAGE_CASE(1, 2) PG_STAGE_CASE(1, 4)
-            PG_STAGE_CASE(2, 1) PG_STAGE_CASE(2, 2) PG_STAGE_CASE(2, 4)
+          // The MMA kind follows the operands (a.mma_kind), which may differ
+          // from the output type (a layer at a BF16/E4M3 boundary).
+          switch ((a.mma_kind ? 16 : 0) + a.halo * 4 + (a.mma_per_stage >> 1)) {
+#define PG_STAGE_CASE(K, H, MPS) \
+  case (K ? 16 : 0) + H * 4 + (MPS >> 1): issue_stage<K, H, MPS>(so); break;
+            PG_STAGE_CASE(false, 0, 1) PG_STAGE_CASE(false, 0, 2) PG_STAGE_CASE(false, 0, 4)
+            PG_STAGE_CASE(false, 1, 1) PG_STAGE_CASE(false, 1, 2) PG_STAGE_CASE(false, 1, 4)
+            PG_STAGE_CASE(false, 2, 1) PG_STAGE_CASE(false, 2, 2) PG_STAGE_CASE(false, 2, 4)
+            PG_STAGE_CASE(true, 0, 1) PG_STAGE_CASE(true, 0, 2) PG_STAGE_CASE(true, 0, 4)
+            PG_STAGE_CASE(true, 1, 1) PG_STAGE_CASE(true, 1, 2) PG_STAGE_CASE(true, 1, 4)
+            PG_STAGE_CASE(true, 2, 1) PG_STAGE_CASE(true, 2, 2) PG_STAGE_CASE(true, 2, 4)
 #undef PG_STAGE_CASE
             default: break;
           }
@@ -1129,7 +1134,7 @@ pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
     Layer &L = net->layers[l];
     // FP8 runs are calibrated by one BF16 pass, so they need both copies.
     if (!L.w_bf16) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_BF16));
-    if (prec == PG_FP8_E4M3 && !L.w_fp8) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_FP8_E4M3));
+    if ((prec == PG_FP8_E4M3 || prec == PG_FP8_MIXED) && !L.w_fp8) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_FP8_E4M3));
   }
   return PG_OK;
 }
@@ -1197,9 +1202,15 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
 
 template <typename T>
 pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, void *actv, uint32_t ns, int H, int W,
-                     float *y, cudaStream_t st, const float *scale, unsigned int *amax, bool tune = false) {
+                     float *y, cudaStream_t st, const float *scale, unsigned int *amax, bool tune = false,
+                     bool mixed = false) {
   Net *net = const_cast<Net *>(netc);
-  const int pi = fp8 ? 2 : 1;
+  // Mixed form (U-Net only): E4M3 operands inside the network (layers 3-11
+  // read E4M3, layers 2-10 write it); the full-resolution level, its skip
+  // concatenation and the head stay BF16.
+  if (mixed && (net->arch != 1 || fp8 || !scale)) return PG_ERR_UNSUPPORTED;
+  auto in8_of = [&](int li) { return mixed ? (li >= 3 && li <= 11) : fp8; };
+  auto out8_of = [&](int li) { return mixed ? (li >= 2 && li <= 10) : fp8; };
   const int es = sizeof(T);
   const size_t HW = (size_t)H * W;
   const long M0 = (long)ns * HW;
@@ -1235,20 +1246,22 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
     L.Cout = Lr.cout; L.k = Lr.k; L.stride = Lr.stride; L.act = Lr.act;
     L.bias = Lr.b;
     L.amax = amax ? amax + og[li] : nullptr;
-    if (fp8) {
+    const bool in8 = in8_of(li), out8 = out8_of(li);
+    const int pi = in8 ? 2 : 1;  // tuned shapes are kept per operand type
+    const int les = in8 ? 1 : 2;
+    if (in8) {
       L.w = Lr.w_fp8;
       L.acc_mul = scale[ig[li]] * Lr.w_scale;
-      L.out_mul = 1.0f / scale[og[li]];
     } else {
       L.w = Lr.w_bf16;
       L.acc_mul = 1.0f;
-      L.out_mul = 1.0f;
     }
+    L.out_mul = out8 ? 1.0f / scale[og[li]] : 1.0f;
     Layer &Lw = net->layers[li];
     if (tune) {
       TcCfg best;
       float best_ms = 0;
-      PG_TRY(tune_layer(L, ns, es, fp8, st, ctx->d_status, &best, &best_ms));
+      PG_TRY(tune_layer(L, ns, les, out8, st, ctx->d_status, &best, &best_ms));
       Lw.tc_ctas[pi] = best.ctas;
       Lw.tc_stages[pi] = best.stages;
       Lw.tc_mt[pi] = best.mt;
@@ -1279,12 +1292,12 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       TcCfg f;
       sscanf(force, "%d,%d,%d,%d,%d,%d", &f.halo, &f.cb, &f.mt, &f.ctas, &f.stages, &f.so);
       PG_COUNT(ctx);
-      const pg_status s = launch_tc(L, ns, es, fp8, st, ctx->d_status, f);
+      const pg_status s = launch_tc(L, ns, les, out8, st, ctx->d_status, f);
       if (s != PG_ERR_UNSUPPORTED) return s;
-      return launch_tc(L, ns, es, fp8, st, ctx->d_status, TcCfg());
+      return launch_tc(L, ns, les, out8, st, ctx->d_status, TcCfg());
     }
     PG_COUNT(ctx);
-    return launch_tc(L, ns, es, fp8, st, ctx->d_status, cfg);
+    return launch_tc(L, ns, les, out8, st, ctx->d_status, cfg);
   };
   auto head = [&](int li, const T *in, int in_cs, int Cin) -> pg_status {
     const Layer &Lr = Ls[li];
@@ -1371,7 +1384,8 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
   if (net->arch == 2 && prec != PG_BF16) return PG_ERR_UNSUPPORTED;
   if (prec == PG_BF16)
     return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, nullptr, nullptr, tune);
-  if (prec != PG_FP8_E4M3) return PG_ERR_UNSUPPORTED;
+  if (prec != PG_FP8_E4M3 && prec != PG_FP8_MIXED) return PG_ERR_UNSUPPORTED;
+  if (prec == PG_FP8_MIXED && net->arch != 1) return PG_ERR_UNSUPPORTED;
   std::unique_lock<std::mutex> lock(net_state_mutex());
   if (!net->act_calibrated) {
     // Delayed scaling: one BF16 pass over this chunk records the largest
@@ -1398,6 +1412,9 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
     PG_TRY(s);
   }
   lock.unlock();
+  if (prec == PG_FP8_MIXED)
+    return forward_lp<__nv_bfloat16>(ctx, net, false, x0, actv, ns, H, W, y, st, net->act_scale, nullptr, tune,
+                                     true);
   return forward_lp<__nv_fp8_e4m3>(ctx, net, true, x0, actv, ns, H, W, y, st, net->act_scale, nullptr, tune);
 }
 

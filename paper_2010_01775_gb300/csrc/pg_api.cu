@@ -739,7 +739,7 @@ pg_status pg_reconstruct(pg_ctx *c, const pg_hist *hist, const pg_net *netp, pg_
   Net *net = as<Net>(netp, KIND_NET);
   if (!c || !h || !net || !out) return PG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
+  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3 && prec != PG_FP8_MIXED) return PG_ERR_INVALID_ARG;
   if (net->arch >= 1 && (h->H < 8 || h->W < 8)) return PG_ERR_UNSUPPORTED;
   PG_TRY(net_prepare(c, net, prec));
   Map *m = new (std::nothrow) Map();
@@ -771,7 +771,7 @@ pg_status pg_reconstruct_experts(pg_ctx *c, const pg_hist *hist, const pg_net *c
   if (!c || !h || !nets || !out || n_experts < 1 || n_experts > 16 || (n_experts > 1 && !count_bounds))
     return PG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
+  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3 && prec != PG_FP8_MIXED) return PG_ERR_INVALID_ARG;
   Net *ns[16];
   for (int e = 0; e < n_experts; ++e) {
     ns[e] = as<Net>(nets[e], KIND_NET);
@@ -952,7 +952,7 @@ pg_status pg_autotune(pg_ctx *c, const pg_hist *hist, pg_net *netp, pg_precision
   const Hist *h = as<Hist>(hist, KIND_HIST);
   Net *net = as<Net>(netp, KIND_NET);
   if (!c || !h || !net) return PG_ERR_INVALID_ARG;
-  if (prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_OK;  // the FP32 form has nothing to tune
+  if (prec != PG_BF16 && prec != PG_FP8_E4M3 && prec != PG_FP8_MIXED) return PG_OK;  // FP32: nothing to tune
   if (h->A == 0) return PG_OK;
   PG_TRY(net_prepare(c, net, prec));
   Map m;
@@ -1198,7 +1198,7 @@ pg_status pg_progress_reconstruct(pg_ctx *c, pg_progress *sp, const pg_net *netp
   Progress *s = as<Progress>(sp, KIND_PROGRESS);
   Net *net = as<Net>(netp, KIND_NET);
   if (!c || !s || !net || !s->grid) return PG_ERR_INVALID_ARG;
-  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3) return PG_ERR_INVALID_ARG;
+  if (prec != PG_FP32 && prec != PG_BF16 && prec != PG_FP8_E4M3 && prec != PG_FP8_MIXED) return PG_ERR_INVALID_ARG;
   if (net->arch >= 1 && (s->p.H < 8 || s->p.W < 8)) return PG_ERR_UNSUPPORTED;
   PG_TRY(net_prepare(c, net, prec));
   const uint32_t A = s->n_updated;

@@ -16,8 +16,8 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libpg.so")
 
-PG_FP32, PG_BF16, PG_FP8_E4M3 = 0, 1, 2
-PRECISIONS = {"fp32": PG_FP32, "bf16": PG_BF16, "fp8": PG_FP8_E4M3}
+PG_FP32, PG_BF16, PG_FP8_E4M3, PG_FP8_MIXED = 0, 1, 2, 3
+PRECISIONS = {"fp32": PG_FP32, "bf16": PG_BF16, "fp8": PG_FP8_E4M3, "fp8mix": PG_FP8_MIXED}
 
 PG_INFO_N_PHOTONS, PG_INFO_N_LEAVES, PG_INFO_N_ACTIVE, PG_INFO_H, PG_INFO_W, PG_INFO_BYTES, PG_INFO_MAX_DEPTH = range(1, 8)
 PG_INFO_N_SCENES, PG_INFO_SCENE_LEVELS = 8, 9

@@ -458,3 +458,20 @@ def test_cnn_fp8_kl(ctx, arch, widths, H, W, n, D, thr):
           f"E4M3 emulation KL mean {kle.mean():.2e}")
     assert kl.mean() <= 1.5 * kle.mean() + 2e-3
     assert np.all(np.isfinite(kl))
+
+
+@pytest.mark.parametrize("H,W,n,D,thr", [(64, 64, 40_000, 5, 2000), (32, 32, 20_000, 4, 1500)])
+def test_cnn_fp8_mixed(ctx, H, W, n, D, thr):
+    """E4M3 inside the U-Net, BF16 at full resolution (PG_FP8_MIXED).  Its
+    layers at the BF16/E4M3 boundary read one operand type and write the
+    other, so the MMA kind must follow the operands.  Gate: no worse than the
+    all-E4M3 form on the same leaves (whose own gate is an E4M3 emulation),
+    and a mean KL that a kind mismatch (garbage maps, KL ~ 80) cannot meet."""
+    arch, widths = synth.ARCH_UNET4, (32, 64, 128, 256)
+    P8, Pr, _ = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 80 + H, pg.PG_FP8_E4M3)
+    Pm, Pr2, valid = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 80 + H, pg.PG_FP8_MIXED)
+    assert np.array_equal(Pr, Pr2) and np.all(valid == 1)
+    k8, _ = _kl_l1(P8, Pr)
+    km, _ = _kl_l1(Pm, Pr)
+    print(f"fp8 mixed {H}x{W}: KL mean {km.mean():.2e} (all-E4M3 {k8.mean():.2e})")
+    assert np.all(np.isfinite(km)) and km.mean() <= 1.2 * k8.mean() + 1e-3 and km.mean() < 0.1
