@@ -80,11 +80,22 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.skip = 0
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        # Wait (up to 3 s) until sampling is live, so that the timed region that
+        # follows is covered; samples taken before it are dropped in stop().
+        t_end = time.time() + 3.0
+        while self.p is not None and time.time() < t_end:
+            self.f.flush()
+            n = len(open(self.f.name).read().strip().splitlines())
+            if n:
+                self.skip = n
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.p is None:
@@ -94,6 +105,8 @@ class Clocks:
         self.f.flush()
         rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
         os.unlink(self.f.name)
+        if len(rows) > self.skip:
+            rows = rows[self.skip:]  # the samples taken during the timed region
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
