@@ -628,7 +628,11 @@ def eval_pdf(grid, slot_of_leaf, tables, pos, dirs):
 # --------------------------------------------------------------------------
 def leaf_of_positions(grid, pos):
     """Leaf containing each position (Algorithm 1, "Locate voxel j"): its
-    code under the a1 rule, then the last leaf whose start code is <= it."""
+    code under the a1 rule, then the last leaf whose start code is <= it (a
+    walk down the voxel's tree for a grid of the paper's form)."""
+    if grid.get("kd"):
+        leaf, bad = kd_locate(grid, pos)
+        return leaf, (ERR_INVALID_INPUT if bad else 0)
     codes, st = morton_codes(pos, grid["lo"], grid["hi"], grid["D"])
     return np.searchsorted(grid["leaf_code"], codes, side="right").astype(np.int64) - 1, st
 
@@ -752,37 +756,60 @@ class Progressive:
     batches are binned into the fixed leaves: a leaf that receives photons
     first copies its sums into its previous planes, then adds the batch.
     Maps are reconstructed for the updated leaves only; the others keep
-    theirs (zero for a leaf never reconstructed)."""
+    theirs (zero for a leaf never reconstructed).
 
-    def __init__(self, lo, hi, max_depth, min_depth, H, W, max_photons, split_c=500.0, refine_iterations=2, F=32):
+    grid_rule "octree" refines by the octree rule of build_grid, "kd" by the
+    paper's rule (build_kd_grid: R^3 voxels, median splits, normal variance
+    threshold vthr; normals per photon, or none).
+
+    Map slots: after a refinement the leaves with photons take slots 0.. in
+    leaf order; a leaf that first receives photons later takes the next slot
+    (new leaves of one batch in leaf order).  slot_of_leaf / slot_leaf hold
+    the map; planes here stay leaf-indexed."""
+
+    def __init__(self, lo, hi, max_depth, min_depth, H, W, max_photons, split_c=500.0, refine_iterations=2, F=32,
+                 grid_rule="octree", R=None, vthr=0.5):
         self.lo, self.hi = _f32(lo), _f32(hi)
         self.D, self.min_depth, self.H, self.W, self.F = max_depth, min_depth, H, W, F
         self.c, self.refine, self.max_photons = split_c, refine_iterations, max_photons
+        self.rule, self.R, self.vthr = grid_rule, R, vthr
         self.t = 0
         self.status = 0
         self.stored = np.zeros((0, 8), np.float32)
+        self.stored_n = None
         self.grid = None
         self.updated = np.zeros(0, np.int64)
         if refine_iterations == 0:
             self._regrid(0, 2 ** 32 - 1)
 
     def _regrid(self, n_prev, thr):
-        self.grid = build_grid(self.stored, self.lo, self.hi, self.D, self.min_depth, thr)
+        if self.rule == "kd":
+            self.grid = build_kd_grid(self.stored, self.stored_n, self.lo, self.hi, self.R, self.D, thr, self.vthr)
+        else:
+            self.grid = build_grid(self.stored, self.lo, self.hi, self.D, self.min_depth, thr)
         h = splat(self.stored, self.grid, n_prev, self.H, self.W, self.F, n_bound=self.max_photons)
         self.status = h["status"]
         self.pow_cur, self.cnt_cur = h["pow_cur"], h["cnt_cur"]
         self.pow_prev, self.cnt_prev = h["pow_prev"], h["cnt_prev"]
-        self.updated = active_leaves(self.grid)[0].astype(np.int64)
+        act, slot = active_leaves(self.grid)
+        self.updated = act.astype(np.int64)
+        self.slot_of_leaf = slot.astype(np.int64)
+        self.slot_leaf = list(act.astype(np.int64))
         self.maps = np.zeros((self.grid["L"], self.H, self.W))
 
-    def add_photons(self, photons):
+    def add_photons(self, photons, normals=None):
         ph = _f32(photons)
         if self.t < self.refine:
             n_prev = self.stored.shape[0]
             self.stored = np.concatenate([self.stored, ph])
+            if normals is not None or self.stored_n is not None:
+                prev_n = self.stored_n if self.stored_n is not None else np.zeros((n_prev, 3), np.float32)
+                new_n = _f32(normals) if normals is not None else np.zeros((ph.shape[0], 3), np.float32)
+                self.stored_n = np.concatenate([prev_n, new_n])
             self._regrid(n_prev, split_threshold(self.t, self.c))
             if self.t + 1 == self.refine:
                 self.stored = np.zeros((0, 8), np.float32)
+                self.stored_n = None
         else:
             b = bin_batch(self.grid, ph, self.H, self.W, self.F, n_bound=self.max_photons)
             self.status = b["status"]
@@ -791,8 +818,16 @@ class Progressive:
             self.cnt_prev[touched] = self.cnt_cur[touched]
             self.pow_cur[touched] += b["pow_cur"][touched]
             self.cnt_cur[touched] += b["cnt_cur"][touched]
+            for l in touched:
+                if self.slot_of_leaf[l] < 0:
+                    self.slot_of_leaf[l] = len(self.slot_leaf)
+                    self.slot_leaf.append(int(l))
             self.updated = touched.astype(np.int64)
         self.t += 1
+
+    @property
+    def updated_slots(self):
+        return self.slot_of_leaf[self.updated]
 
     def planes(self, leaves):
         return dict(pow_cur=self.pow_cur[leaves], cnt_cur=self.cnt_cur[leaves], pow_prev=self.pow_prev[leaves],

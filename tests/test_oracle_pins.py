@@ -896,3 +896,35 @@ def test_residual_link_and_masked_zeros():
     x[..., :4] *= x[..., 4:5]
     out = O.cnn_forward(x, net)
     assert out.shape == (2, 16, 16) and np.all(np.isfinite(out)) and np.all(out >= 0)
+
+
+def test_progressive_with_the_papers_grid_rule_and_slots():
+    """Refinement by the paper's rule (two iterations, normals), then batches
+    binned by walking the voxels' trees; map slots: refined leaves in leaf
+    order, later newcomers appended in leaf order."""
+    H, W = 4, 8
+    b = _batches([300, 600, 900, 900], 35)
+    nrm = [synth.wall_normals(x) for x in b]
+    pr = O.Progressive(LO, HI, 6, 0, H, W, 2700, split_c=40.0, refine_iterations=2, grid_rule="kd", R=4, vthr=0.5)
+    pr.add_photons(b[0], nrm[0])
+    pr.add_photons(b[1], nrm[1])
+    ref = O.build_kd_grid(np.concatenate(b[:2]), np.concatenate(nrm[:2]), LO, HI, 4, 6, O.split_threshold(1, 40.0),
+                          0.5)
+    for k in ("leaf_cell", "leaf_depth", "node_link", "node_tau"):
+        assert np.array_equal(pr.grid[k], ref[k]), k
+    act, _ = O.active_leaves(ref)
+    assert pr.slot_leaf == list(act) and np.array_equal(pr.updated_slots, np.arange(act.size))
+    total = O.bin_batch(ref, np.concatenate(b[:2]), H, W, 32, n_bound=2700)
+    assert np.array_equal(pr.pow_cur, total["pow_cur"]) and np.array_equal(pr.cnt_cur, total["cnt_cur"])
+    A = len(pr.slot_leaf)
+    seen = list(b[:2])
+    for t in (2, 3):
+        pr.add_photons(b[t], nrm[t])
+        seen.append(b[t])
+        total = O.bin_batch(ref, np.concatenate(seen), H, W, 32, n_bound=2700)
+        assert np.array_equal(pr.pow_cur, total["pow_cur"]) and np.array_equal(pr.cnt_cur, total["cnt_cur"])
+        leaf, _ = O.leaf_of_positions(ref, b[t][:, :3])
+        assert pr.updated.tolist() == sorted(set(leaf.tolist()))
+        new = [l for l in pr.updated if l not in pr.slot_leaf[:A]]
+        assert pr.slot_leaf[A:] == new and list(pr.updated_slots) == [pr.slot_leaf.index(l) for l in pr.updated]
+        A = len(pr.slot_leaf)
