@@ -364,51 +364,66 @@ pg_status pg_mis_eval(pg_ctx *ctx, const pg_grid *grid, const pg_tables *tables,
  * batch of photons (the paper doubles the batch each iteration).
  *
  * Iterations t < refine_iterations (the paper: 2) refine the grid: their
- * photons are kept, and the grid is rebuilt from all photons so far with the
- * split threshold floor(split_c * sqrt(2^t)) (the paper: c = 500), so a
- * voxel splits on its photon count through the iterations.  The grid is
- * fixed from then on, and later batches are binned into its leaves and
- * dropped.
+ * photons (and normals) are kept, and the grid is rebuilt from all photons
+ * so far with the split threshold floor(split_c * sqrt(2^t)) (the paper:
+ * c = 500), so a voxel splits on its photon count through the iterations.
+ * grid_rule 0 refines by the octree rule of pg_build_grid (max_depth,
+ * min_depth); grid_rule 1 by the paper's rule of pg_build_grid_kd
+ * (resolution R, trees of depth max_depth, normal_variance_threshold; the
+ * normals come with the batches).  The grid is fixed from then on, and later
+ * batches are binned into its leaves (the a1 rule or the voxel's tree walk)
+ * and dropped.
  *
- * Every leaf keeps its energy and count maps summed over all iterations so
- * far (the current planes), and, as the previous planes, those sums as they
- * stood before the last iteration that brought the leaf photons.  In a
- * refining iteration every leaf with photons counts as updated, and its
+ * Every leaf with photons owns a map slot.  After a refinement the leaves
+ * with photons take slots 0.. in leaf order; a leaf that first receives
+ * photons later takes the next free slot (the newcomers of one batch in leaf
+ * order).  Each slot keeps the leaf's energy and count maps summed over all
+ * iterations so far (the current planes), and, as the previous planes,
+ * those sums as they stood before the last iteration that brought the leaf
+ * photons.  In a refining iteration every slot counts as updated, and its
  * previous planes are the sums over the earlier iterations' photons.  The
  * fixed-point bound of pg_splat_photons applies with n = max_photons, the
  * photon total over all iterations.
  *
- * With refine_iterations = 0 the grid is the regular grid of depth
- * min_depth from the start.  The renderer's valid-voxel marking is not
- * modelled: every leaf accumulates. */
+ * With refine_iterations = 0 the grid is the unrefined grid from the start
+ * (the regular grid of depth min_depth, or R^3 voxels).  The renderer's
+ * valid-voxel marking is not modelled: every leaf accumulates. */
 typedef struct {
   float lo[3], hi[3];
-  int32_t max_depth;          /* deepest split, <= 16 */
-  int32_t min_depth;          /* the initial regular grid, <= 6 */
+  int32_t max_depth;          /* deepest split (octree or tree), <= 16 */
+  int32_t min_depth;          /* octree: the initial regular grid, <= 6 */
   double split_c;             /* split threshold floor(split_c * sqrt(2^t)) */
   int32_t refine_iterations;  /* iterations that rebuild the grid */
   int32_t H, W, frac_bits;    /* as for pg_splat_photons */
   uint64_t max_photons;       /* photons over all iterations, < 2^31 */
+  int32_t grid_rule;          /* 0 octree, 1 the paper's rule (pg_build_grid_kd) */
+  int32_t resolution;         /* grid_rule 1: R voxels per axis, R^3 <= 2^27 */
+  float normal_variance_threshold;  /* grid_rule 1: V_thr */
 } pg_progress_params;
 
 pg_status pg_progress_create(pg_ctx *ctx, const pg_progress_params *params, pg_progress **out);
 /* Adds iteration t's batch (n records, device or host) and advances t.
  * PG_ERR_INVALID_ARG if the photon total would pass max_photons; invalid
  * positions or powers give PG_ERR_INVALID_INPUT or PG_ERR_OVERFLOW (now or
- * via pg_sync) as in pg_build_grid / pg_splat_photons.  The updated leaves
+ * via pg_sync) as in pg_build_grid / pg_splat_photons.  The updated slots
  * can be read with pg_export(PG_PROGRESS_UPDATED). */
 pg_status pg_progress_add_photons(pg_ctx *ctx, pg_progress *state, const pg_photon *d_photons, uint64_t n);
-/* Reconstructs the maps of the leaves updated by the last pg_progress_add_photons
- * (Sec. 7.2: "valid voxels that have new photons"), from their current and
- * previous planes as pg_reconstruct would; the other leaves keep their maps
- * (zero for a leaf never reconstructed, i.e. no valid map).  Then rebuilds
- * the tables of every leaf's map as pg_build_cdf does. */
+/* The same with the unit surface normals at the photons (n x 3 float,
+ * device or host, or NULL), used by grid_rule 1 while the grid is refined:
+ * either every refining batch brings normals or none does
+ * (PG_ERR_INVALID_ARG otherwise). */
+pg_status pg_progress_add_photons_normals(pg_ctx *ctx, pg_progress *state, const pg_photon *d_photons,
+                                          const float *d_normals, uint64_t n);
+/* Reconstructs the maps of the slots updated by the last add (Sec. 7.2:
+ * "valid voxels that have new photons"), from their current and previous
+ * planes as pg_reconstruct would; the other slots keep their maps.  Then
+ * rebuilds the tables of every slot's map as pg_build_cdf does. */
 pg_status pg_progress_reconstruct(pg_ctx *ctx, pg_progress *state, const pg_net *net, pg_precision precision);
 /* Borrowed handles of the state (any pointer may be NULL), valid until the
- * state's next add or reconstruct call: the grid (its slot_of_leaf is the
- * identity and its active count is L, so that the tables, one row per leaf,
+ * state's next add or reconstruct call: the grid (its slot_of_leaf and
+ * active list are the state's slots, so that the tables, one row per slot,
  * serve pg_sample_dirs, pg_eval_pdf and pg_mis_*; its photon arrays describe
- * the last refining iteration's photons), the leaf-indexed planes ([L][H*W];
+ * the last refining iteration's photons), the slot planes ([slots][H*W];
  * pg_autotune and pg_reconstruct accept them), the maps and the tables (NULL
  * before the first reconstruct).  pg_free ignores borrowed handles. */
 pg_status pg_progress_view(const pg_progress *state, const pg_grid **grid, const pg_hist **planes,
@@ -420,7 +435,7 @@ enum {
   PG_INFO_N_PHOTONS = 1, PG_INFO_N_LEAVES = 2, PG_INFO_N_ACTIVE = 3, PG_INFO_H = 4,
   PG_INFO_W = 5, PG_INFO_BYTES = 6, PG_INFO_MAX_DEPTH = 7, PG_INFO_N_SCENES = 8, PG_INFO_SCENE_LEVELS = 9,
   PG_INFO_ITERATION = 10,  /* progress: iterations added so far */
-  PG_INFO_N_UPDATED = 11,  /* progress: leaves updated by the last add */
+  PG_INFO_N_UPDATED = 11,  /* progress: slots updated by the last add */
   PG_INFO_KD_NODES = 12    /* grid of the paper's form: tree nodes, voxel roots included */
 };
 pg_status pg_info(const void *handle, int what, uint64_t *value);
@@ -454,7 +469,7 @@ enum {
   PG_MIS_Q_B = 502,         /* uint32 [L]  BSDF-sampled bounces */
   PG_MIS_Q_G = 503,         /* uint32 [L]  guide-sampled bounces */
   PG_MIS_ALPHA = 504,       /* float  [L]  BSDF selection probability */
-  PG_PROGRESS_UPDATED = 600, /* uint32 [N_UPDATED] leaves updated by the last add, ascending */
+  PG_PROGRESS_UPDATED = 600, /* uint32 [N_UPDATED] slots updated by the last add (in leaf order) */
   PG_TAB_P = 400,           /* float  [A][H*W] */
   PG_TAB_CDF_PHI = 401,     /* float  [A][H][W] */
   PG_TAB_CDF_Z = 402,       /* float  [A][H] */

@@ -1292,6 +1292,123 @@ pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint6
   return PG_OK;
 }
 
+// A batch binned into a grid of the paper's form: each photon walks its
+// voxel's tree to its leaf, the batch is sorted by leaf id, and each leaf's
+// range is found by binary search of its id.
+namespace {
+
+__global__ void k_kd_batch_leaf(const pg_photon *__restrict__ ph, uint32_t n, KdView kv, uint64_t *__restrict__ keys,
+                                uint32_t *status) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(ph + i));
+  uint32_t bad = 0;
+  keys[i] = kd_locate(kv, a.x, a.y, a.z, bad);
+  if (bad) atomicOr(status, ST_INVALID_INPUT);
+}
+
+__global__ void k_leaf_ranges_ids(const uint64_t *__restrict__ sorted, uint32_t n, uint32_t L,
+                                  uint32_t *__restrict__ leaf_begin, uint32_t *__restrict__ leaf_end) {
+  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  leaf_begin[l] = lower_bound_u64(sorted, n, l);
+  leaf_end[l] = lower_bound_u64(sorted, n, (uint64_t)l + 1);
+}
+
+}  // namespace
+
+pg_status bin_into_grid_kd(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n64, Grid *view,
+                           void **scratch, size_t *scratch_bytes) {
+  *scratch = nullptr;
+  *scratch_bytes = 0;
+  if (!g->kd || n64 >= (1ull << 31)) return PG_ERR_UNSUPPORTED;
+  cudaStream_t st = ctx->stream;
+  const uint32_t n = (uint32_t)n64, L = g->L;
+  int bits = 0;
+  while ((1ull << bits) < (uint64_t)L) ++bits;
+  const int passes = (bits + 7) / 8;
+  const uint32_t nblocks = n ? ceil_div(n, kSortTile) : 0;
+  const size_t s_k = align256(8ull * n), s_v = align256(4ull * n), s_h = align256(4ull * kRadix * (nblocks + 1));
+  const size_t s_dt = align256(4 * kRadix), s_l = align256(4ull * L), s_c = 256;
+  const size_t bytes = 3 * s_k + 2 * s_v + s_h + s_dt + 3 * s_l + s_c;
+  void *blk;
+  PG_TRY(ctx_alloc(ctx, bytes, &blk));
+  *scratch = blk;
+  *scratch_bytes = bytes;
+  uint8_t *q = (uint8_t *)blk;
+  uint64_t *keys = (uint64_t *)q; q += s_k;
+  uint64_t *kA = (uint64_t *)q; q += s_k;
+  uint64_t *kB = (uint64_t *)q; q += s_k;
+  uint32_t *perm = (uint32_t *)q; q += s_v;
+  uint32_t *vT = (uint32_t *)q; q += s_v;
+  uint32_t *hist = (uint32_t *)q; q += s_h;
+  uint32_t *dtot = (uint32_t *)q; q += s_dt;
+  uint32_t *lb = (uint32_t *)q; q += s_l;
+  uint32_t *le = (uint32_t *)q; q += s_l;
+  uint32_t *act = (uint32_t *)q; q += s_l;
+  uint32_t *count = (uint32_t *)q;
+
+  const int TB = 256;
+  const uint64_t *sorted = keys;
+  if (n) {
+    k_kd_batch_leaf<<<ceil_div(n, TB), TB, 0, st>>>(d_ph, n, kd_view_of(g), keys, ctx->d_status), PG_COUNT(ctx);
+    if (passes == 0) {
+      k_iota<<<ceil_div(n, TB), TB, 0, st>>>(perm, n), PG_COUNT(ctx);
+    } else {
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kScatterSmem));
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kScatterSmem));
+      const uint64_t *kin = keys;
+      const uint32_t *vin = nullptr;
+      for (int ps = 0; ps < passes; ++ps) {
+        uint64_t *kout = (ps & 1) ? kB : kA;
+        uint32_t *vout = ((passes - 1 - ps) & 1) ? vT : perm;
+        const int shift = 8 * ps;
+        k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
+        k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
+        if (ps == 0)
+          k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                            dtot, nblocks), PG_COUNT(ctx);
+        else
+          k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+                                                                             dtot, nblocks), PG_COUNT(ctx);
+        kin = kout;
+        vin = vout;
+      }
+      sorted = kin;
+    }
+  }
+  if (L) {
+    k_leaf_ranges_ids<<<ceil_div(L, TB), TB, 0, st>>>(sorted, n, L, lb, le), PG_COUNT(ctx);
+    k_batch_active<<<1, 1024, 0, st>>>(L, lb, le, act, count), PG_COUNT(ctx);
+  } else {
+    PG_CUDA(cudaMemsetAsync(count, 0, 4, st));
+  }
+  PG_CUDA(cudaGetLastError());
+  uint32_t A = 0, status = 0;
+  PG_CUDA(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
+  PG_CUDA(cudaStreamSynchronize(st));
+  if (status & ST_INVALID_INPUT) {
+    PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
+    PG_CUDA(cudaStreamSynchronize(st));
+    return PG_ERR_INVALID_INPUT;
+  }
+  *view = *g;
+  view->h.kind = 0;
+  view->n = n;
+  view->A = A;
+  view->codes = keys;
+  view->perm = perm;
+  view->leaf_of = nullptr;
+  view->leaf_begin = lb;
+  view->leaf_end = le;
+  view->active = act;
+  view->block = nullptr;
+  return PG_OK;
+}
+
 }  // namespace pgi
 
 // ---------------------------------------------------------------- allocation-free sort

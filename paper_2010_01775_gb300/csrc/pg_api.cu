@@ -194,12 +194,13 @@ static void free_progress(Progress *s) {
   release_owned(s->map);
   release_owned(s->tab);
   ctx_free(c, s->stored, s->cap_stored * sizeof(pg_photon));
+  ctx_free(c, s->stored_n, s->cap_stored * 3 * sizeof(float));
   ctx_free(c, s->updated, 4ull * s->cap_updated);
   s->h.kind = 0;
   delete s;
 }
 
-static pg_status progress_updated(pg_ctx *c, Progress *s, const uint32_t *d_leaves, uint32_t A) {
+static pg_status progress_reserve_updated(pg_ctx *c, Progress *s, uint32_t A) {
   if (A > s->cap_updated) {
     void *b;
     PG_TRY(ctx_alloc(c, 4ull * A, &b));
@@ -207,24 +208,15 @@ static pg_status progress_updated(pg_ctx *c, Progress *s, const uint32_t *d_leav
     s->updated = (uint32_t *)b;
     s->cap_updated = A;
   }
-  if (A) PG_CUDA(cudaMemcpyAsync(s->updated, d_leaves, 4ull * A, cudaMemcpyDeviceToDevice, c->stream));
-  s->n_updated = A;
   return PG_OK;
 }
 
 // A refining iteration: the grid is rebuilt from every photon kept so far
 // (split threshold thr), and all its leaves' planes are recomputed; photons
-// with index < n_prev are the earlier iterations'.
+// with index < n_prev are the earlier iterations'.  The leaves with photons
+// take slots 0.. in leaf order (the grid's own active list).
 static pg_status progress_regrid(pg_ctx *c, Progress *s, uint64_t n_prev, uint32_t thr) {
   const pg_progress_params &p = s->p;
-  pg_grid_params gp;
-  for (int a = 0; a < 3; ++a) {
-    gp.lo[a] = p.lo[a];
-    gp.hi[a] = p.hi[a];
-  }
-  gp.max_depth = p.max_depth;
-  gp.min_depth = p.min_depth;
-  gp.split_threshold = thr;
   Grid *g = new (std::nothrow) Grid();
   Hist *cum = new (std::nothrow) Hist();
   Map *m = new (std::nothrow) Map();
@@ -242,31 +234,48 @@ static pg_status progress_regrid(pg_ctx *c, Progress *s, uint64_t n_prev, uint32
   m->h.kind = KIND_MAP;
   g->h.ctx = cum->h.ctx = m->h.ctx = c;
   g->h.borrowed = cum->h.borrowed = m->h.borrowed = 1;
-  Hist slot;
-  memset(&slot, 0, sizeof(slot));
-  slot.H = p.H;
-  slot.W = p.W;
-  pg_status st = build_grid(c, s->stored, s->n_stored, &gp, g);
-  if (st == PG_OK && g->A) {
-    slot.A = g->A;
-    st = splat(c, g, s->stored, p.max_photons, n_prev, p.frac_bits, &slot);
+  pg_status st;
+  if (p.grid_rule == 1) {
+    pg_kd_params kp;
+    for (int a = 0; a < 3; ++a) {
+      kp.lo[a] = p.lo[a];
+      kp.hi[a] = p.hi[a];
+    }
+    kp.resolution = p.resolution;
+    kp.max_depth = p.max_depth;
+    kp.split_threshold = thr;
+    kp.normal_variance_threshold = p.normal_variance_threshold;
+    st = build_grid_kd(c, s->stored, s->normals == 1 ? s->stored_n : nullptr, s->n_stored, &kp, g);
+  } else {
+    pg_grid_params gp;
+    for (int a = 0; a < 3; ++a) {
+      gp.lo[a] = p.lo[a];
+      gp.hi[a] = p.hi[a];
+    }
+    gp.max_depth = p.max_depth;
+    gp.min_depth = p.min_depth;
+    gp.split_threshold = thr;
+    st = build_grid(c, s->stored, s->n_stored, &gp, g);
   }
-  if (st == PG_OK) st = hist_alloc(c, cum, g->L, p.H, p.W);
-  if (st == PG_OK && g->A) st = rows_to_leaves(c, &slot, g->active, cum);
-  if (st == PG_OK) st = progress_updated(c, s, g->active, g->A);
-  if (st == PG_OK) st = identity_slots(c, g);
   if (st == PG_OK) {
-    m->A = g->L;
+    cum->H = p.H;
+    cum->W = p.W;
+    cum->A = g->A;
+    st = splat(c, g, s->stored, p.max_photons, n_prev, p.frac_bits, cum);  // slot-indexed by the active list
+  }
+  if (st == PG_OK) st = progress_reserve_updated(c, s, g->A);
+  if (st == PG_OK) st = iota_slots(c, g->A, s->updated);
+  if (st == PG_OK) {
+    m->A = g->A;
     m->H = p.H;
     m->W = p.W;
-    m->h.bytes = (size_t)g->L * p.H * p.W * sizeof(float);
+    m->h.bytes = (size_t)std::max<uint32_t>(g->A, 1) * p.H * p.W * sizeof(float);
     st = ctx_alloc(c, m->h.bytes, &m->block);
     if (st == PG_OK) {
       m->y = (float *)m->block;
       st = cudaMemsetAsync(m->block, 0, m->h.bytes, c->stream) == cudaSuccess ? PG_OK : PG_ERR_CUDA;
     }
   }
-  ctx_free(c, slot.block, slot.h.bytes);
   if (st != PG_OK) {
     release_owned(g);
     release_owned(cum);
@@ -281,6 +290,8 @@ static pg_status progress_regrid(pg_ctx *c, Progress *s, uint64_t n_prev, uint32
   s->grid = g;
   s->cum = cum;
   s->map = m;
+  s->cap_slots = g->A;  // rows of cum (the map holds at least as many)
+  s->n_updated = g->A;
   return PG_OK;
 }
 
@@ -1125,6 +1136,11 @@ pg_status pg_progress_create(pg_ctx *c, const pg_progress_params *p, pg_progress
   if (!isfinite(p->split_c) || !(p->split_c >= 0.0) || p->refine_iterations < 0 || p->refine_iterations > 31 ||
       p->frac_bits < 0 || p->frac_bits > 62 || p->max_photons == 0 || p->max_photons >= (1ull << 31))
     return PG_ERR_INVALID_ARG;
+  if (p->grid_rule != 0 && p->grid_rule != 1) return PG_ERR_INVALID_ARG;
+  if (p->grid_rule == 1 &&
+      (p->resolution < 1 || (uint64_t)p->resolution * p->resolution * p->resolution > (1ull << 27) ||
+       !(p->normal_variance_threshold == p->normal_variance_threshold)))
+    return PG_ERR_INVALID_ARG;
   if (!pow2_in(p->H, 4, 256) || !pow2_in(p->W, 4, 256) || p->H * p->W > 16384) return PG_ERR_NOT_POW2;
   Progress *s = new (std::nothrow) Progress();
   if (!s) return PG_ERR_OOM;
@@ -1132,7 +1148,8 @@ pg_status pg_progress_create(pg_ctx *c, const pg_progress_params *p, pg_progress
   s->h.kind = KIND_PROGRESS;
   s->h.ctx = c;
   s->p = *p;
-  if (p->refine_iterations == 0) {  // the regular grid of depth min_depth, for good
+  s->normals = -1;
+  if (p->refine_iterations == 0) {  // the unrefined grid, for good
     pg_status st = progress_regrid(c, s, 0, 0xFFFFFFFFu);
     if (st != PG_OK) {
       free_progress(s);
@@ -1144,26 +1161,54 @@ pg_status pg_progress_create(pg_ctx *c, const pg_progress_params *p, pg_progress
 }
 
 pg_status pg_progress_add_photons(pg_ctx *c, pg_progress *sp, const pg_photon *d_ph, uint64_t n) {
+  return pg_progress_add_photons_normals(c, sp, d_ph, nullptr, n);
+}
+
+pg_status pg_progress_add_photons_normals(pg_ctx *c, pg_progress *sp, const pg_photon *d_ph, const float *d_nrm,
+                                          uint64_t n) {
   Progress *s = as<Progress>(sp, KIND_PROGRESS);
   if (!c || !s || (n && !d_ph)) return PG_ERR_INVALID_ARG;
   if (n > s->p.max_photons || s->total + n > s->p.max_photons) return PG_ERR_INVALID_ARG;
-  Staged ph;
-  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
   const uint32_t t = s->t;
-  if ((int64_t)t < s->p.refine_iterations) {
+  const bool refining = (int64_t)t < s->p.refine_iterations;
+  const int with_n = d_nrm ? 1 : 0;
+  if (refining && s->p.grid_rule == 1 && s->normals >= 0 && s->normals != with_n) return PG_ERR_INVALID_ARG;
+  Staged ph, nr;
+  if (n) PG_TRY(stage_in(c, d_ph, n * sizeof(pg_photon), ph));
+  const bool keep_n = refining && s->p.grid_rule == 1 && with_n;
+  if (n && keep_n) PG_TRY(stage_in(c, d_nrm, n * 3 * sizeof(float), nr));
+  if (refining) {
     if (s->n_stored + n > s->cap_stored) {
       const uint64_t cap = std::max<uint64_t>(2 * s->cap_stored, s->n_stored + n);
-      void *b;
+      void *b, *bn = nullptr;
       PG_TRY(ctx_alloc(c, cap * sizeof(pg_photon), &b));
-      if (s->n_stored)
+      if (keep_n) {
+        pg_status sa = ctx_alloc(c, cap * 3 * sizeof(float), &bn);
+        if (sa != PG_OK) {
+          ctx_free(c, b, cap * sizeof(pg_photon));
+          return sa;
+        }
+      }
+      if (s->n_stored) {
         PG_CUDA(cudaMemcpyAsync(b, s->stored, s->n_stored * sizeof(pg_photon), cudaMemcpyDeviceToDevice, c->stream));
+        if (keep_n && s->stored_n)
+          PG_CUDA(cudaMemcpyAsync(bn, s->stored_n, s->n_stored * 3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  c->stream));
+      }
       ctx_free(c, s->stored, s->cap_stored * sizeof(pg_photon));
+      ctx_free(c, s->stored_n, s->cap_stored * 3 * sizeof(float));
       s->stored = (pg_photon *)b;
+      s->stored_n = (float *)bn;
       s->cap_stored = cap;
     }
-    if (n)
+    if (n) {
       PG_CUDA(cudaMemcpyAsync(s->stored + s->n_stored, ph.dev, n * sizeof(pg_photon), cudaMemcpyDeviceToDevice,
                               c->stream));
+      if (keep_n)
+        PG_CUDA(cudaMemcpyAsync(s->stored_n + 3 * s->n_stored, nr.dev, n * 3 * sizeof(float),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (s->p.grid_rule == 1) s->normals = with_n;
     const uint64_t n_prev = s->n_stored;
     s->n_stored += n;
     // M_thr = c sqrt(2^t); counts are integers, so count > M_thr <=> count > floor(M_thr).
@@ -1176,16 +1221,38 @@ pg_status pg_progress_add_photons(pg_ctx *c, pg_progress *sp, const pg_photon *d
     }
     if ((int64_t)t + 1 == s->p.refine_iterations) {  // the grid is fixed from here on
       ctx_free(c, s->stored, s->cap_stored * sizeof(pg_photon));
+      ctx_free(c, s->stored_n, s->cap_stored * 3 * sizeof(float));
       s->stored = nullptr;
+      s->stored_n = nullptr;
       s->n_stored = s->cap_stored = 0;
     }
   } else {
     Grid view;
     void *scr = nullptr;
     size_t sb = 0;
-    pg_status st = bin_into_grid(c, s->grid, (const pg_photon *)ph.dev, n, &view, &scr, &sb);
-    if (st == PG_OK) st = splat_merge(c, &view, (const pg_photon *)ph.dev, s->p.max_photons, s->p.frac_bits, s->cum);
-    if (st == PG_OK) st = progress_updated(c, s, view.active, view.A);
+    Grid *g = s->grid;
+    pg_status st = g->kd ? bin_into_grid_kd(c, g, (const pg_photon *)ph.dev, n, &view, &scr, &sb)
+                         : bin_into_grid(c, g, (const pg_photon *)ph.dev, n, &view, &scr, &sb);
+    // Leaves that receive their first photons take the next slots.
+    uint32_t fresh = 0;
+    if (st == PG_OK) st = assign_slots(c, view.A, view.active, g, &fresh);
+    const uint32_t A0 = g->A, A1 = A0 + fresh;
+    if (st == PG_OK && A1 > s->cap_slots) {
+      const uint32_t cap = std::max<uint32_t>(2 * s->cap_slots, A1);
+      st = hist_grow(c, s->cum, A0, cap);
+      if (st == PG_OK) st = map_grow(c, s->map, A0, cap);
+      if (st == PG_OK) s->cap_slots = cap;
+    }
+    if (st == PG_OK) {
+      g->A = A1;
+      s->cum->A = A1;
+      s->map->A = A1;
+      st = splat_merge(c, &view, (const pg_photon *)ph.dev, s->p.max_photons, s->p.frac_bits, g->slot_of_leaf,
+                       s->cum);
+    }
+    if (st == PG_OK) st = progress_reserve_updated(c, s, view.A);
+    if (st == PG_OK) st = slots_of(c, view.A, view.active, g, s->updated);
+    if (st == PG_OK) s->n_updated = view.A;
     ctx_free(c, scr, sb);
     if (st != PG_OK) return st;
   }

@@ -167,13 +167,16 @@ struct Progress {
   pg_progress_params p;
   uint32_t t;               // iterations added so far
   uint64_t total;           // photons added so far
-  Grid *grid;               // leaf table; slot_of_leaf is the identity (A = L)
-  Hist *cum;                // [L][HW] planes: sums over all iterations, and before the leaf's last update
-  Map *map;                 // [L][H][W]; zero rows for leaves never reconstructed
+  Grid *grid;               // leaf table; slot_of_leaf / active are the state's map slots (A = slots)
+  Hist *cum;                // [slots][HW] planes: sums over all iterations, and before the leaf's last update
+  Map *map;                 // [slots][H][W]
   Tables *tab;              // tables of map, or null before the first reconstruct
   pg_photon *stored;        // refining iterations keep their photons (the grid is rebuilt)
+  float *stored_n;          // and their normals (grid_rule 1), or null
+  int normals;              // -1 not yet known, 0 batches without normals, 1 with
   uint64_t n_stored, cap_stored;
-  uint32_t *updated;        // leaves whose planes changed in the last add, ascending
+  uint32_t cap_slots;       // rows allocated in cum and map (cum->A = map->A = slots in use)
+  uint32_t *updated;        // slots whose planes changed in the last add (in leaf order)
   uint32_t n_updated, cap_updated;
 };
 
@@ -379,20 +382,32 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n, const pg_gr
 // *scratch_bytes, freed by the caller with ctx_free).
 pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, Grid *view, void **scratch,
                         size_t *scratch_bytes);
-// progress.cu
-pg_status hist_alloc(pg_ctx *ctx, Hist *h, uint32_t A, int H, int W);  // zeroed planes
-// dst[d_active[a]] = src[a] (all planes); dst is leaf-indexed.
-pg_status rows_to_leaves(pg_ctx *ctx, const Hist *src, const uint32_t *d_active, Hist *dst);
-pg_status identity_slots(pg_ctx *ctx, Grid *g);  // slot_of_leaf[l] = active[l] = l, A = L
 // The paper's grid rule: R^3 voxels refined by binary trees (grid.cu).
 pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_normals, uint64_t n,
                         const pg_kd_params *p, Grid *g);
+// progress.cu
+pg_status hist_alloc(pg_ctx *ctx, Hist *h, uint32_t A, int H, int W);  // zeroed planes
+// Reallocates to cap rows (zeroed), keeping the first `rows`; A becomes rows.
+pg_status hist_grow(pg_ctx *ctx, Hist *h, uint32_t rows, uint32_t cap);
+pg_status map_grow(pg_ctx *ctx, Map *m, uint32_t rows, uint32_t cap);
+// Leaves in d_leaves (ascending) without a slot take slots g->A, g->A+1, ...
+// (slot_of_leaf and the active list of g updated); *new_slots gets their
+// number (one synchronisation).
+pg_status assign_slots(pg_ctx *ctx, uint32_t nA, const uint32_t *d_leaves, Grid *g, uint32_t *new_slots);
+pg_status slots_of(pg_ctx *ctx, uint32_t nA, const uint32_t *d_leaves, const Grid *g, uint32_t *d_out);
+pg_status iota_slots(pg_ctx *ctx, uint32_t n, uint32_t *d_out);
+// A batch binned into the fixed leaves of a grid of the paper's form (tree
+// walk per photon, then a sort by leaf); as bin_into_grid otherwise.
+pg_status bin_into_grid_kd(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, Grid *view, void **scratch,
+                           size_t *scratch_bytes);
 // splat.cu
 // A batch binned into a fixed grid (view from bin_into_grid) and merged into
-// leaf-indexed sums: for every leaf l of the view's active list, prev[l] =
-// cur[l], then cur[l] += the leaf's batch histogram (planes and totals).
-// n_bound sets the fixed-point bound (2^63 - 1) / n_bound.
-pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint64_t n_bound, int F, Hist *cum);
+// slot-indexed sums: for every leaf l of the view's active list, with slot
+// s = slot_of_leaf[l]: prev[s] = cur[s], then cur[s] += the leaf's batch
+// histogram (planes and totals).  n_bound sets the fixed-point bound
+// (2^63 - 1) / n_bound.
+pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint64_t n_bound, int F,
+                      const int32_t *d_slot_of_leaf, Hist *cum);
 pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, uint64_t n_prev, int F, Hist *h,
                 const uint32_t *d_scene_nprev = nullptr);
 // cnn.cu

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
     uint32_t *__restrict__ cnt_cur, uint64_t *__restrict__ pow_prev, uint32_t *__restrict__ cnt_prev,
     uint64_t *__restrict__ tot_cur, uint64_t *__restrict__ tot_prev, uint32_t *status,
     const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ sc_begin,
-    const uint32_t *__restrict__ sc_nprev, int sc_shift) {
+    const uint32_t *__restrict__ sc_nprev, int sc_shift, const int32_t *__restrict__ merge_slot) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int kPlanes = kMode == 0 ? 2 : 1;
   const int HW = H * W;
@@ -151,8 +151,9 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
   __syncthreads();
 
   if (kMode == 3) {
-    // Read-modify-write of the leaf's rows, coalesced; totals likewise.
-    const size_t o = (size_t)leaf * HW;
+    // Read-modify-write of the leaf's slot rows, coalesced; totals likewise.
+    const uint32_t row = (uint32_t)merge_slot[leaf];
+    const size_t o = (size_t)row * HW;
     unsigned long long t_add = 0;
     for (int k = tid; k < HW; k += kSplatThreads) {
       const unsigned long long add = s_pow[k];
@@ -171,9 +172,9 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
     if (tid == 0) {
       unsigned long long a = 0;
       for (int w = 0; w < kSplatThreads / 32; ++w) a += s_tot[0][w];
-      const unsigned long long t0 = tot_cur[leaf];
-      tot_prev[leaf] = t0;
-      tot_cur[leaf] = t0 + a;
+      const unsigned long long t0 = tot_cur[row];
+      tot_prev[row] = t0;
+      tot_cur[row] = t0 + a;
     }
     return;
   }
@@ -229,7 +230,8 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 }  // namespace
 
-pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint64_t n_bound, int F, Hist *cum) {
+pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint64_t n_bound, int F,
+                      const int32_t *d_slot_of_leaf, Hist *cum) {
   if (view->A == 0) return PG_OK;
   const size_t HW = (size_t)cum->H * cum->W;
   const float *tab;
@@ -241,7 +243,7 @@ pg_status splat_merge(pg_ctx *ctx, const Grid *view, const pg_photon *d_ph, uint
   k_splat<3><<<(unsigned)view->A, kSplatThreads, smem, ctx->stream>>>(
       d_ph, view->perm, view->active, view->leaf_begin, view->leaf_end, 0u, cum->H, cum->W, two_f, limit, tab,
       cum->pow_cur, cum->cnt_cur, cum->pow_prev, cum->cnt_prev, cum->tot_cur, cum->tot_prev, ctx->d_status,
-      view->leaf_code, view->scene_begin, nullptr, 3 * view->D), PG_COUNT(ctx);
+      view->leaf_code, view->scene_begin, nullptr, 3 * view->D, d_slot_of_leaf), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
   return PG_OK;
 }
@@ -271,7 +273,7 @@ pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, u
     k_splat<0><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
         h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
-        g->scene_begin, d_scene_nprev, 3 * g->D), PG_COUNT(ctx);
+        g->scene_begin, d_scene_nprev, 3 * g->D, nullptr), PG_COUNT(ctx);
   } else {
     size_t smem = 12 * HW + 8 * (size_t)h->W;
     PG_CUDA(cudaFuncSetAttribute(k_splat<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -279,11 +281,11 @@ pg_status splat(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint64_t n, u
     k_splat<1><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
         h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
-        g->scene_begin, d_scene_nprev, 3 * g->D), PG_COUNT(ctx);
+        g->scene_begin, d_scene_nprev, 3 * g->D, nullptr), PG_COUNT(ctx);
     k_splat<2><<<(unsigned)A, kSplatThreads, smem, ctx->stream>>>(
         d_ph, g->perm, g->active, g->leaf_begin, g->leaf_end, (uint32_t)n_prev, h->H, h->W, two_f, limit, tab,
         h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur, h->tot_prev, ctx->d_status, g->leaf_code,
-        g->scene_begin, d_scene_nprev, 3 * g->D), PG_COUNT(ctx);
+        g->scene_begin, d_scene_nprev, 3 * g->D, nullptr), PG_COUNT(ctx);
   }
   PG_CUDA(cudaGetLastError());
   return PG_OK;

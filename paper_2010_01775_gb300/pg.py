@@ -45,7 +45,7 @@ EXPORTED = ["pg_create", "pg_destroy", "pg_set_stream", "pg_sync", "pg_bytes_in_
             "pg_launch_count", "pg_net_get_tuning", "pg_net_set_tuning",
             "pg_reconstruct_experts", "pg_mis_create", "pg_mis_accumulate", "pg_mis_update", "pg_mis_sample",
             "pg_mis_eval", "pg_progress_create", "pg_progress_add_photons", "pg_progress_reconstruct",
-            "pg_progress_view", "pg_build_grid_kd"]
+            "pg_progress_view", "pg_build_grid_kd", "pg_progress_add_photons_normals"]
 PG_NOALLOC_MAX_PHOTONS = 1 << 20
 
 
@@ -71,7 +71,8 @@ class pg_progress_params(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_float * 3), ("hi", ctypes.c_float * 3), ("max_depth", ctypes.c_int32),
                 ("min_depth", ctypes.c_int32), ("split_c", ctypes.c_double), ("refine_iterations", ctypes.c_int32),
                 ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("frac_bits", ctypes.c_int32),
-                ("max_photons", ctypes.c_uint64)]
+                ("max_photons", ctypes.c_uint64), ("grid_rule", ctypes.c_int32), ("resolution", ctypes.c_int32),
+                ("normal_variance_threshold", ctypes.c_float)]
 
 
 _lib = None
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
         "pg_mis_eval": [P, P, P, P, P, P, P, u64, P],
         "pg_progress_create": [P, ctypes.POINTER(pg_progress_params), PP],
         "pg_progress_add_photons": [P, P, P, u64], "pg_progress_reconstruct": [P, P, P, i32],
+        "pg_progress_add_photons_normals": [P, P, P, P, u64],
         "pg_progress_view": [P, PP, PP, PP, PP],
         "pg_build_grid_kd": [P, P, P, u64, ctypes.POINTER(pg_kd_params), PP],
         "pg_net_get_tuning": [P, P, sz, ctypes.POINTER(sz)], "pg_net_set_tuning": [P, P, sz],
@@ -488,16 +490,21 @@ def export_tables(t):
 
 # ---------------------------------------------------------------- progressive iterations
 def pg_progress_create(ctx, lo, hi, max_depth, min_depth, H, W, max_photons, split_c=500.0, refine_iterations=2,
-                       frac_bits=32) -> Handle:
+                       frac_bits=32, grid_rule=0, resolution=100, normal_variance_threshold=0.5) -> Handle:
     p = pg_progress_params((ctypes.c_float * 3)(*lo), (ctypes.c_float * 3)(*hi), max_depth, min_depth, split_c,
-                           refine_iterations, H, W, frac_bits, max_photons)
+                           refine_iterations, H, W, frac_bits, max_photons, grid_rule, resolution,
+                           normal_variance_threshold)
     out = ctypes.c_void_p()
     _check(_lib.pg_progress_create(ctx.ptr, ctypes.byref(p), ctypes.byref(out)), "pg_progress_create")
     return Handle(ctx, out.value, "progress")
 
 
-def pg_progress_add_photons(ctx, state, photons, n):
-    _check(_lib.pg_progress_add_photons(ctx.ptr, state.ptr, _ptr(photons), n), "pg_progress_add_photons")
+def pg_progress_add_photons(ctx, state, photons, n, normals=None):
+    if normals is None:
+        _check(_lib.pg_progress_add_photons(ctx.ptr, state.ptr, _ptr(photons), n), "pg_progress_add_photons")
+    else:
+        _check(_lib.pg_progress_add_photons_normals(ctx.ptr, state.ptr, _ptr(photons), _ptr(normals), n),
+               "pg_progress_add_photons_normals")
 
 
 def pg_progress_reconstruct(ctx, state, net, precision):
