@@ -669,10 +669,13 @@ def run_progressive(args, wl, prec):
     torch.cuda.set_stream(stream)
     ctx = pg.Context(stream.cuda_stream)
     net = pg.pg_net_load(ctx, blob)
-    st = pg.pg_progress_create(ctx, LO, HI, wl.max_depth, wl.min_depth, H, W, max_photons, split_c=500.0,
-                               refine_iterations=2, frac_bits=PROGRESS_FRAC_BITS)
+    kd = args.grid == "kd"  # refinement by the paper's rule (100^3 voxels, trees of depth 8, wall normals)
+    st = pg.pg_progress_create(ctx, LO, HI, KD_DEPTH if kd else wl.max_depth, wl.min_depth, H, W, max_photons,
+                               split_c=500.0, refine_iterations=2, frac_bits=PROGRESS_FRAC_BITS,
+                               grid_rule=1 if kd else 0, resolution=KD_R, normal_variance_threshold=KD_VTHR)
     for b in refine:
-        pg.pg_progress_add_photons(ctx, st, torch.from_numpy(b).cuda(), len(b))
+        pg.pg_progress_add_photons(ctx, st, torch.from_numpy(b).cuda(), len(b),
+                                   torch.from_numpy(synth.wall_normals(b)).cuda() if kd else None)
     d_b = [torch.from_numpy(b).cuda() for b in batches]
     d_pos = torch.from_numpy(pos).cuda()
     d_dir = torch.from_numpy(dirs).cuda()
@@ -763,7 +766,9 @@ def run_progressive(args, wl, prec):
             "data": "synthetic (seeded photon blobs on room walls, vMF directions, lognormal power; random He-init U-Net)",
             "config": {"workload": "progressive iteration, " + wl.name, "photons_per_iteration": n,
                        "refine": f"2 iterations of {n_p} and {2 * n_p} photons, threshold 500 sqrt(2^t)",
-                       "queries": q, "H": H, "W": W, "max_depth": wl.max_depth, "leaves": L,
+                       "grid": (f"paper's rule: {KD_R}^3 voxels, trees of depth <= {KD_DEPTH}, V_thr {KD_VTHR}, "
+                                "wall normals" if kd else f"octree, depth {wl.max_depth}"),
+                       "queries": q, "H": H, "W": W, "max_depth": KD_DEPTH if kd else wl.max_depth, "leaves": L,
                        "updated_leaves_per_step": A_mean, "frac_bits": PROGRESS_FRAC_BITS,
                        "precision": args.precision, "parallelism": f"replicas x{world}",
                        "l2": "flushed between steps (256 MB write); inputs also exceed L2"},
@@ -778,7 +783,12 @@ def run_progressive(args, wl, prec):
                          "peak_source": "of " + peak_src},
             "clocks": clk,
         }
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and kd:
+            # The oracle keeps leaf-indexed planes: 10^6 leaves x 4096 bins do not fit host memory.
+            out["cpu_baseline"] = {"value": None, "unit": "samples/s", "kind": "oracle", "cores": 1,
+                                   "sample": "not run: the oracle's progressive form holds leaf-indexed planes, "
+                                             "about 100 GB for a 100^3-voxel grid of 64x64 maps"}
+        elif world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = progressive_cpu_baseline(wl, args.cpu_sample_leaves)
         print(json.dumps(out), flush=True)
     if world > 1:
