@@ -415,7 +415,7 @@ pg_status pg_progress_add_photons(pg_ctx *ctx, pg_progress *state, const pg_phot
 pg_status pg_progress_add_photons_normals(pg_ctx *ctx, pg_progress *state, const pg_photon *d_photons,
                                           const float *d_normals, uint64_t n);
 /* Reconstructs the maps of the slots updated by the last add (Sec. 7.2:
- * "valid voxels that have new photons"), from their current and previous
+ * only voxels that received photons in this batch), from their current and previous
  * planes as pg_reconstruct would; the other slots keep their maps.  Then
  * rebuilds the tables of every slot's map as pg_build_cdf does. */
 pg_status pg_progress_reconstruct(pg_ctx *ctx, pg_progress *state, const pg_net *net, pg_precision precision);

@@ -361,8 +361,9 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
 }
 
 /* ------------------------------------------------------------------------ */
-/* a10-a12. Guided sampling "just like sampling an environment map"          */
-/* (Sec. 7.3) and pdf evaluation p_guide (Eq. target_mis / mis_coef terms).  */
+/* a10-a12. Guided sampling by inverse CDFs over the map, as for an         */
+/* environment map (Sec. 7.3), and pdf evaluation p_guide (Eq. target_mis / */
+/* mis_coef terms).                                                         */
 /* For query q: leaf = last leaf whose start code <= code(position); the     */
 /* four uniforms are (philox(ctr=(q_lo, q_hi, stream, 0), key=seed) >> 8) *  */
 /* 2^-24.  Row i = first i with u0 < Fz[i], column j = first j with          */

@@ -1,11 +1,13 @@
-// a8-a9: sampling map and CDFs (Eq. energy_target; Sec. 7.3, a CDF built by
-// a cumulative sum over the map "like sampling an environment map").
+// a8-a9: sampling map and CDFs (Eq. energy_target; Sec. 7.3: the CDF is a
+// cumulative sum over the map pixels, as for an environment map).
 //
-// One CTA per map.  Each warp owns rows: every lane holds W/32 consecutive
-// bins (one vector load), forms their running sum, and one warp scan joins
-// the lanes; the conditional CDF of the row is prefix / row sum (1 in the
+// One CTA per map.  Each row is split over T consecutive lanes, N bins per
+// lane: a lane sums its bins in sequence, a T-lane shuffle scan joins the
+// segments, and the conditional CDF of the row is prefix / row sum (1 in the
 // last bin, uniform for an empty row).  Warp 0 then scans the row sums into
-// the marginal CDF, and all threads write P = y / sum y.
+// the marginal CDF, and all threads write P = y / sum y.  Sequential sums in
+// each lane keep the pair arithmetic below to about a third of what a
+// 32-lane scan per row costs.
 //
 // Sums, prefixes and quotients carry ~48 significant bits without FP64:
 // each value is an unevaluated pair (hi, lo) of FP32 numbers combined with
@@ -86,99 +88,126 @@ __device__ __forceinline__ df warp_incl_scan_df(df x) {
   return x;
 }
 
-template <int E>
+template <int N>
+__device__ __forceinline__ void load_seg(const float *__restrict__ p, float (&v)[N]) {
+#pragma unroll
+  for (int e = 0; e < N; e += 4) {
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p + e));
+    v[e] = t.x; v[e + 1] = t.y; v[e + 2] = t.z; v[e + 3] = t.w;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_seg(float *__restrict__ p, const float (&v)[N]) {
+#pragma unroll
+  for (int e = 0; e < N; e += 4) *reinterpret_cast<float4 *>(p + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+}
+
+// Warp 0: the marginal CDF over the row sums and the map total.
+__device__ __forceinline__ void marginal_cdf(int H, const float *mrow_hi, const float *mrow_lo, float *__restrict__ cz,
+                                             uint8_t *__restrict__ valid, df *s_total) {
+  const int lane = threadIdx.x & 31;
+  const int EH = (H + 31) >> 5;
+  df pref[8], run = {0.0f, 0.0f};
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    int i = lane * EH + e;
+    if (e < EH && i < H) run = df_add(run, df{mrow_hi[i], mrow_lo[i]});
+    pref[e] = run;
+  }
+  df incl = warp_incl_scan_df(run);
+  df off = {__shfl_up_sync(0xFFFFFFFFu, incl.hi, 1), __shfl_up_sync(0xFFFFFFFFu, incl.lo, 1)};
+  if (lane == 0) off = {0.0f, 0.0f};
+  df total = {__shfl_sync(0xFFFFFFFFu, incl.hi, 31), __shfl_sync(0xFFFFFFFFu, incl.lo, 31)};
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    int i = lane * EH + e;
+    if (e < EH && i < H)
+      cz[(size_t)blockIdx.x * H + i] =
+          i == H - 1 ? 1.0f : (total.hi > 0.0f ? df_div_to_f32(df_add(off, pref[e]), total) : 0.0f);
+  }
+  if (lane == 0) {
+    *s_total = total;
+    valid[blockIdx.x] = total.hi > 0.0f ? 1 : 0;
+  }
+}
+
+// One CTA (256 threads) per map.  A row of W = N*T bins belongs to T
+// consecutive lanes, each holding N consecutive bins (N = min(W, 16)), so a
+// pass covers 256/T rows: a 64x64 map is one pass with every bin loaded
+// once.  A lane sums its N bins in sequence, a T-lane shuffle scan gives its
+// offset and the row sum, and a second sweep of its bins forms the prefixes.
+// When the map fits one pass the bins stay in registers for P = y / sum y;
+// taller maps re-read them.
+template <int N, int T>
 __global__ void __launch_bounds__(256) k_cdf(const float *__restrict__ y, int H, int W, float *__restrict__ P,
                                              float *__restrict__ cphi, float *__restrict__ cz,
                                              uint8_t *__restrict__ valid) {
+  constexpr int RP = 256 / T;
   __shared__ float mrow_hi[256], mrow_lo[256];
   __shared__ df s_total;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x;
+  const int q = tid % T;  // = lane % T: the T lanes of a row are one shuffle segment
   const size_t HW = (size_t)H * W, base = (size_t)blockIdx.x * HW;
-  for (int i = warp; i < H; i += 8) {
-    const float *row = y + base + (size_t)i * W;
-    float v[E];
-    if (E >= 4) {
+  float v[N];
+  int i = 0;
+  for (int r0 = 0; r0 < H; r0 += RP) {
+    i = r0 + tid / T;
+    const bool has = i < H;  // lanes past the last row still join the shuffles
+    const size_t o = base + (size_t)i * W + q * N;
+    if (has) load_seg<N>(y + o, v);
+    else
 #pragma unroll
-      for (int e = 0; e < E; e += 4) {
-        float4 t = __ldg(reinterpret_cast<const float4 *>(row + lane * E + e));
-        v[e] = t.x; v[e + 1] = t.y; v[e + 2] = t.z; v[e + 3] = t.w;
-      }
-    } else if (E == 2) {
-      float2 t = __ldg(reinterpret_cast<const float2 *>(row + lane * 2));
-      v[0] = t.x;
-      v[1] = t.y;
-    } else {
-      v[0] = lane < W ? __ldg(row + lane) : 0.0f;
-    }
-    df pref[E], run = {0.0f, 0.0f};
+      for (int e = 0; e < N; ++e) v[e] = 0.0f;
+    df tot = {0.0f, 0.0f};
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      run = df_add(run, df_from(v[e]));
-      pref[e] = run;
+    for (int e = 0; e < N; ++e) tot = df_add(tot, df_from(v[e]));
+    df incl = tot;
+#pragma unroll
+    for (int s = 1; s < T; s <<= 1) {
+      df u = {__shfl_up_sync(0xFFFFFFFFu, incl.hi, s, T), __shfl_up_sync(0xFFFFFFFFu, incl.lo, s, T)};
+      if (q >= s) incl = df_add(incl, u);
     }
-    df incl = warp_incl_scan_df(run);
-    df off = {__shfl_up_sync(0xFFFFFFFFu, incl.hi, 1), __shfl_up_sync(0xFFFFFFFFu, incl.lo, 1)};
-    if (lane == 0) off = {0.0f, 0.0f};
-    df m = {__shfl_sync(0xFFFFFFFFu, incl.hi, 31), __shfl_sync(0xFFFFFFFFu, incl.lo, 31)};
-    if (lane == 0) {
+    df off = {__shfl_up_sync(0xFFFFFFFFu, incl.hi, 1, T), __shfl_up_sync(0xFFFFFFFFu, incl.lo, 1, T)};
+    if (q == 0) off = {0.0f, 0.0f};
+    const df m = {__shfl_sync(0xFFFFFFFFu, incl.hi, T - 1, T), __shfl_sync(0xFFFFFFFFu, incl.lo, T - 1, T)};
+    if (!has) continue;
+    if (q == 0) {
       mrow_hi[i] = m.hi;
       mrow_lo[i] = m.lo;
     }
-    float out[E];
-    const df rm = m.hi > 0.0f ? df_recip(m) : df{0.0f, 0.0f};
+    float out[N];
+    if (m.hi > 0.0f) {
+      const df rm = df_recip(m);
+      df run = off;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-      int j = lane * E + e;
-      if (m.hi > 0.0f) out[e] = j == W - 1 ? 1.0f : df_mul_to_f32(df_add(off, pref[e]), rm);
-      else out[e] = (float)(j + 1) / (float)W;
-    }
-    float *o = cphi + base + (size_t)i * W + lane * E;
-    if (E >= 4) {
+      for (int e = 0; e < N; ++e) {
+        run = df_add(run, df_from(v[e]));
+        out[e] = q * N + e == W - 1 ? 1.0f : df_mul_to_f32(run, rm);
+      }
+    } else {
 #pragma unroll
-      for (int e = 0; e < E; e += 4) *reinterpret_cast<float4 *>(o + e) = make_float4(out[e], out[e + 1], out[e + 2], out[e + 3]);
-    } else if (E == 2) {
-      *reinterpret_cast<float2 *>(o) = make_float2(out[0], out[1]);
-    } else if (lane < W) {
-      o[0] = out[0];
+      for (int e = 0; e < N; ++e) out[e] = (float)(q * N + e + 1) / (float)W;
     }
+    store_seg<N>(cphi + o, out);
   }
   __syncthreads();
-  if (warp == 0) {
-    const int EH = (H + 31) >> 5;
-    df pref[8], run = {0.0f, 0.0f};
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      int i = lane * EH + e;
-      if (e < EH && i < H) run = df_add(run, df{mrow_hi[i], mrow_lo[i]});
-      pref[e] = run;
-    }
-    df incl = warp_incl_scan_df(run);
-    df off = {__shfl_up_sync(0xFFFFFFFFu, incl.hi, 1), __shfl_up_sync(0xFFFFFFFFu, incl.lo, 1)};
-    if (lane == 0) off = {0.0f, 0.0f};
-    df total = {__shfl_sync(0xFFFFFFFFu, incl.hi, 31), __shfl_sync(0xFFFFFFFFu, incl.lo, 31)};
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      int i = lane * EH + e;
-      if (e < EH && i < H)
-        cz[(size_t)blockIdx.x * H + i] =
-            i == H - 1 ? 1.0f : (total.hi > 0.0f ? df_div_to_f32(df_add(off, pref[e]), total) : 0.0f);
-    }
-    if (lane == 0) {
-      s_total = total;
-      valid[blockIdx.x] = total.hi > 0.0f ? 1 : 0;
-    }
-  }
+  if (tid < 32) marginal_cdf(H, mrow_hi, mrow_lo, cz, valid, &s_total);
   __syncthreads();
   const df total = s_total;
-  if (total.hi > 0.0f) {
-    const float inv = df_div_to_f32(df{1.0f, 0.0f}, total);
-    for (size_t k = 4 * threadIdx.x; k < HW; k += 4 * blockDim.x) {
-      float4 t = __ldg(reinterpret_cast<const float4 *>(y + base + k));
-      *reinterpret_cast<float4 *>(P + base + k) = make_float4(t.x * inv, t.y * inv, t.z * inv, t.w * inv);
+  const float inv = total.hi > 0.0f ? df_div_to_f32(df{1.0f, 0.0f}, total) : 0.0f;
+  if (H <= RP) {
+    if (i < H) {
+      float out[N];
+#pragma unroll
+      for (int e = 0; e < N; ++e) out[e] = total.hi > 0.0f ? v[e] * inv : 0.0f;
+      store_seg<N>(P + base + (size_t)i * W + q * N, out);
     }
   } else {
-    for (size_t k = 4 * threadIdx.x; k < HW; k += 4 * blockDim.x)
-      *reinterpret_cast<float4 *>(P + base + k) = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (size_t k = 4 * tid; k < HW; k += 4 * blockDim.x) {
+      float4 t = total.hi > 0.0f ? __ldg(reinterpret_cast<const float4 *>(y + base + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4 *>(P + base + k) = make_float4(t.x * inv, t.y * inv, t.z * inv, t.w * inv);
+    }
   }
 }
 
@@ -188,11 +217,17 @@ pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t) {
   if (m->A == 0) return PG_OK;
   const unsigned A = m->A;
   cudaStream_t st = ctx->stream;
-  switch (m->W >= 32 ? m->W / 32 : 1) {
-    case 1: k_cdf<1><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
-    case 2: k_cdf<2><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
-    case 4: k_cdf<4><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
-    case 8: k_cdf<8><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
+  switch (m->W) {
+#define PG_CDF_CASE(Wc, Nc, Tc) \
+  case Wc: k_cdf<Nc, Tc><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
+    PG_CDF_CASE(4, 4, 1)
+    PG_CDF_CASE(8, 8, 1)
+    PG_CDF_CASE(16, 16, 1)
+    PG_CDF_CASE(32, 16, 2)
+    PG_CDF_CASE(64, 16, 4)
+    PG_CDF_CASE(128, 16, 8)
+    PG_CDF_CASE(256, 16, 16)
+#undef PG_CDF_CASE
     default: return PG_ERR_UNSUPPORTED;
   }
   PG_CUDA(cudaGetLastError());

@@ -174,7 +174,9 @@ def tiny_scene(ctx):
     return dict(ph=ph, d=d, g=g, ref=ref, act=act, slot=slot, wl=wl)
 
 
-@pytest.mark.parametrize("H,W", [(32, 32), (64, 64), (16, 128), (128, 128), (4, 4)])
+# Maps of at most 64 rows and 128 columns keep their rows in registers; the
+# others (128x128, 64x256) stream them.
+@pytest.mark.parametrize("H,W", [(32, 32), (64, 64), (16, 128), (128, 128), (4, 4), (8, 16), (64, 256)])
 def test_cdf_tables(ctx, tiny_scene, H, W):
     A = tiny_scene["g"].info(pg.PG_INFO_N_ACTIVE)
     y = _maps(A, H, W, H * 1000 + W)
