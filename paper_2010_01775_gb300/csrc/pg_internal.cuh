@@ -322,8 +322,8 @@ __device__ __forceinline__ bool not_clockwise_exact(float c, float s, float x, f
 }
 
 // Cylindrical-map column: the phi sector of (x, y) among W equal sectors,
-// phi = atan2(y, x) in [0, 2 pi).  Binary search of the last boundary ray the
-// direction is not clockwise of, within the half plane of the direction
+// phi = atan2(y, x) in [0, 2 pi): the last boundary ray the direction is not
+// clockwise of, within the half plane of the direction
 // (upper: phi in [0, pi), rays 0..W/2-1; lower: phi in [pi, 2 pi), rays
 // W/2..W-1).  tab holds cos at [0, W) and sin at [W, 2W).
 static __device__ __noinline__ int dir_col_exact(float x, float y, int W, const float *tab, int lo, int hi) {
@@ -335,27 +335,43 @@ static __device__ __noinline__ int dir_col_exact(float x, float y, int W, const 
   return lo;
 }
 
-// The search runs in FP32; a step whose difference does not clear the
-// rounding bound (4 ulp of |c y| + |s x|, normal operands) marks the result
-// unsure, and only then is the search redone with the exact FP64 predicate
-// (kept out of line: GB300's FP64 rate is a small fraction of FP32's).
+// FP32 form of the same test; `unsure` is set when the difference does not
+// clear its rounding bound (4 ulp of |c y| + |s x|, normal operands).
+__device__ __forceinline__ bool not_clockwise_f32(float c, float s, float x, float y, bool &unsure) {
+  float a = __fmul_rn(c, y), b = __fmul_rn(s, x);
+  float d = __fsub_rn(a, b);
+  float mag = fabsf(a) + fabsf(b);
+  unsure |= !(mag > 1e-30f && fabsf(d) > 4.8e-7f * mag);
+  return d >= 0.0f;
+}
+
+// The answer is the last ray of the half plane that the direction is not
+// clockwise of: the first ray always is, and the test holds up to the answer
+// and fails after it.  A guess from atan2 is checked against its own ray and
+// the next one (one round of table reads, usually the last), and walked from
+// there if either test disagrees, so any guess gives the same column.  Any
+// unsure FP32 test redoes the search with the exact FP64 test (kept out of
+// line: GB300's FP64 rate is a small fraction of FP32's).
 __device__ __forceinline__ int dir_col(float x, float y, int W, const float *tab) {
   if (x == 0.0f && y == 0.0f) return 0;
   const bool upper = (y > 0.0f) || (y == 0.0f && x >= 0.0f);
   const int lo0 = upper ? 0 : (W >> 1), hi0 = lo0 + (W >> 1) - 1;
-  int lo = lo0, hi = hi0;
+  float phi = atan2f(y, x);
+  if (phi < 0.0f) phi += 6.2831853071795865f;
+  int a = (int)(phi * ((float)W * 0.15915494309189535f));
+  a = min(max(a, lo0), hi0);
+  const int b = a < hi0 ? a + 1 : a;
+  const float c0 = tab[a], s0 = tab[W + a], c1 = tab[b], s1 = tab[W + b];
   bool unsure = false;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    float a = __fmul_rn(tab[mid], y), b = __fmul_rn(tab[W + mid], x);
-    float d = __fsub_rn(a, b);
-    float mag = fabsf(a) + fabsf(b);
-    unsure |= !(mag > 1e-30f && fabsf(d) > 4.8e-7f * mag);
-    if (d >= 0.0f) lo = mid;
-    else hi = mid - 1;
+  if (a > lo0 && !not_clockwise_f32(c0, s0, x, y, unsure)) {
+    --a;
+    while (a > lo0 && !not_clockwise_f32(tab[a], tab[W + a], x, y, unsure)) --a;
+  } else if (a < hi0 && not_clockwise_f32(c1, s1, x, y, unsure)) {
+    ++a;
+    while (a < hi0 && not_clockwise_f32(tab[a + 1], tab[W + a + 1], x, y, unsure)) ++a;
   }
-  if (unsure) lo = dir_col_exact(x, y, W, tab, lo0, hi0);
-  return lo;
+  if (unsure) a = dir_col_exact(x, y, W, tab, lo0, hi0);
+  return a;
 }
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds, Weyl key schedule.
