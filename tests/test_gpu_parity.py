@@ -109,16 +109,21 @@ def test_splat_bit_exact(ctx, n, D, thr, H, W, n_prev):
     g.free()
 
 
-def test_splat_axis_and_seam_directions(ctx):
-    """Directions on bin edges and the phi seam: the exact rule on both sides."""
-    H, W = 16, 32
+@pytest.mark.parametrize("W", [32, 256])
+def test_splat_axis_and_seam_directions(ctx, W):
+    """Directions on bin edges and the phi seam: the exact rule on both sides.
+    Also just either side of every edge (rotated by 1e-7 and 1e-6 rad) and
+    edges scaled down, where an angle-based first guess of the column is
+    most often off by one."""
+    H = 16
     dirs = [[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1e-30, 0],
             [1, -1e-30, 0], [-1, -1e-30, 0], [-1, 1e-38, 0], [0.7071068, 0.7071068, 0]]
     rng = np.random.default_rng(41)
     th = 2 * np.pi * np.arange(W) / W
     edge = np.stack([np.cos(th), np.sin(th), np.zeros(W)], 1)  # exactly on rounded boundary rays
+    near = [np.stack([np.cos(th + e), np.sin(th + e), np.zeros(W)], 1) for e in (-1e-6, -1e-7, 1e-7, 1e-6)]
     rand = synth.uniform_sphere(rng, 5000)
-    D = np.concatenate([np.array(dirs, np.float64), edge, rand]).astype(np.float32)
+    D = np.concatenate([np.array(dirs, np.float64), edge, edge * 1e-3, *near, rand]).astype(np.float32)
     n = D.shape[0]
     ph = np.zeros((n, 8), np.float32)
     ph[:, :3] = 0.5
