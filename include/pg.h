@@ -134,8 +134,8 @@ pg_status pg_budget_query(const pg_budget *b, uint64_t *in_use, uint64_t *capaci
 
 /* ---- a1-a4: grid ------------------------------------------------------- */
 
-/* Voxel location and adaptive subdivision (Algorithm 1 "Locate voxel j" and
- * "Subdivide voxel j"; Sec. 7.1 "Voxel subdivision"), octree form:
+/* Voxel location and adaptive subdivision (Algorithm 1; Sec. 7.1, voxel
+ * subdivision), octree form:
  *   cell index per axis  q = clamp(floor(fl32(fl32(x - lo) * s)), 0, 2^D-1),
  *                        s = fl32(2^D / (hi - lo)) computed in double;
  *   Morton code          bits (3b, 3b+1, 3b+2) = bit b of (qx, qy, qz);

@@ -97,7 +97,7 @@ def _f32(x):
 
 # --------------------------------------------------------------------------
 # a1-a4: voxel location and the adaptive hierarchical grid (Sec. 7.1,
-# Algorithm 1 "Locate voxel j" and "Subdivide voxel j").
+# Algorithm 1: locating a position's voxel and subdividing voxels).
 # --------------------------------------------------------------------------
 def morton_codes(pos, lo, hi, D):
     pos = _f32(pos)
@@ -627,7 +627,7 @@ def eval_pdf(grid, slot_of_leaf, tables, pos, dirs):
 # vertex normal (no renderer is in scope).
 # --------------------------------------------------------------------------
 def leaf_of_positions(grid, pos):
-    """Leaf containing each position (Algorithm 1, "Locate voxel j"): its
+    """Leaf containing each position (Algorithm 1, voxel location): its
     code under the a1 rule, then the last leaf whose start code is <= it (a
     walk down the voxel's tree for a grid of the paper's form)."""
     if grid.get("kd"):

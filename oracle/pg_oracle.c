@@ -22,7 +22,7 @@
 enum { OR_OK = 0, OR_ERR_OVERFLOW = 4, OR_ERR_INVALID_INPUT = 8, OR_ERR_CAPACITY = 9 };
 
 /* ------------------------------------------------------------------------ */
-/* a1. Voxel location (Algorithm 1 "Locate voxel j", Sec. 7.1 grid).         */
+/* a1. Voxel location (Algorithm 1, Sec. 7.1 grid).                          */
 /* Per-axis cell index at depth D: t = x - lo, u = t * s in FP32 with        */
 /* s = float(2^D / (hi - lo)), q = clamp(floor(u), 0, 2^D - 1).              */
 /* ------------------------------------------------------------------------ */

@@ -1,5 +1,5 @@
 // a1-a4: voxel location and the adaptive hierarchical grid (Sec. 7.1,
-// Algorithm 1 "Locate voxel j" / "Subdivide voxel j"), octree form.
+// Algorithm 1: locating a position's voxel and subdividing voxels), octree form.
 //
 //   k_morton        per photon: FP32 quantisation + Morton code (a1)
 //   k_sort_*        stable LSD radix sort of (code, index), 8-bit digits (a2):

@@ -207,7 +207,7 @@ void budget_release(pg_budget *b, size_t bytes);
 pg_status phi_table(pg_ctx *ctx, int W, const float **d_table);
 
 // ---------------------------------------------------------------- device rules
-// Voxel quantisation (Algorithm 1 "Locate voxel j"): q = clamp(floor(fl32(
+// Voxel quantisation (Algorithm 1, voxel location): q = clamp(floor(fl32(
 // fl32(x - lo) * s)), 0, top) with IEEE round-to-nearest FP32 operations
 // (the __f*_rn intrinsics are never contracted into FMAs).
 __device__ __forceinline__ uint32_t quantise(float x, float lo, float s, uint32_t top, uint32_t &bad) {
