@@ -66,7 +66,7 @@ typedef struct {
 } pg_photon;
 
 /* Spatial grid parameters (Sec. 7.1).  The domain [lo, hi) is cut into a
- * regular 2^min_depth grid per axis (the "initial regular grid"); a cell
+ * regular 2^min_depth grid per axis (the paper's initial regular grid); a cell
  * holding more than split_threshold photons is split into its 8 children
  * until max_depth.  0 <= min_depth <= max_depth <= 16, min_depth <= 6. */
 typedef struct {
@@ -253,12 +253,14 @@ pg_status pg_map_import(pg_ctx *ctx, const float *d_y, uint64_t n_maps, int H, i
 
 /* ---- a8-a9: normalisation and CDFs ------------------------------------- */
 
-/* Sampling map and CDFs (Eq. energy_target; Sec. 7.3, a CDF "like sampling
- * an environment map"): P = y / sum y per map; marginal CDF over rows
- * Fz[i] = sum_{i'<=i} m_i' / sum m with m_i = sum_j y_ij; conditional CDF
- * Fphi[i][j] = sum_{j'<=j} y_ij' / m_i ((j+1)/W for an empty row).  Sums and
- * prefixes in FP64, stored float32 with the last entry of every CDF exactly
- * 1.  A map with sum 0 is marked invalid (uniform fallback when sampled). */
+/* Sampling map and CDFs (Eq. energy_target; Sec. 7.3: CDFs over the map
+ * pixels, sampled as an environment map is): P = y / sum y per map; marginal
+ * CDF over rows Fz[i] = sum_{i'<=i} m_i' / sum m with m_i = sum_j y_ij;
+ * conditional CDF Fphi[i][j] = sum_{j'<=j} y_ij' / m_i ((j+1)/W for an empty
+ * row).  Sums, prefixes and quotients carry about 48 significant bits (pairs
+ * of float32 joined by error-free transformations), stored float32 with the
+ * last entry of every CDF exactly 1.  A map with sum 0 is marked invalid
+ * (uniform fallback when sampled). */
 pg_status pg_build_cdf(pg_ctx *ctx, const pg_map *map, pg_tables **out);
 
 /* ---- a10-a12: guided sampling and pdf evaluation ----------------------- */

@@ -525,8 +525,8 @@ def cnn_forward_experts(x, counts, nets, bounds=PAPER_EXPERT_BOUNDS):
 
 
 # --------------------------------------------------------------------------
-# a8-a9: sampling map and its CDFs (Eq. energy_target; Sec. 7.3 "CDF built
-# via a cumulative sum over pixels, like sampling an environment map").
+# a8-a9: sampling map and its CDFs (Eq. energy_target; Sec. 7.3: the CDF is a
+# cumulative sum over the map pixels, sampled as an environment map is).
 # --------------------------------------------------------------------------
 def normalise(y):
     """P_k = y_k / sum_k y (FP64).  A map whose sum is zero is invalid."""
