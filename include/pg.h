@@ -9,6 +9,10 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Every call returns a pg_status; nothing throws across the ABI.
+ *  - A NULL context, handle or required pointer gives PG_ERR_INVALID_ARG
+ *    before any CUDA call, so argument errors cost no device work.
+ *    pg_destroy(NULL), pg_budget_destroy(NULL) and pg_free(NULL) are no-ops
+ *    (PG_OK).
  *  - Work is asynchronous on the context's CUDA stream (pg_create).  A call
  *    returns once its work is enqueued; results are ready after pg_sync() or
  *    any later stream-ordered operation.  The exceptions are pg_build_grid

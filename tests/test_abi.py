@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(lib):
             "pg_eval_pdf"} <= declared
     for name in declared:
         assert hasattr(lib, name), name
-    assert declared <= set(pg.EXPORTED) | declared
+    assert declared == set(pg.EXPORTED)  # the binding covers exactly the declared entry points
 
 
 def test_status_strings(lib):
@@ -49,3 +49,21 @@ def test_null_arguments_rejected_without_gpu(lib):
     v = ctypes.c_uint64()
     assert lib.pg_info(None, 1, ctypes.byref(v)) == 1
     lib.pg_free(None)
+
+
+def test_every_entry_point_rejects_null_handles_without_gpu(lib):
+    """The convention at the top of include/pg.h: NULL contexts, handles and
+    required pointers give PG_ERR_INVALID_ARG before any CUDA call (this
+    machine has no GPU, so a call that reached CUDA would report
+    PG_ERR_CUDA instead); destroying NULL is a no-op."""
+    pointer = (ctypes.c_void_p, ctypes._Pointer)
+    checked = 0
+    for name in pg.EXPORTED:
+        if name in ("pg_free", "pg_status_string"):
+            continue
+        f = getattr(lib, name)
+        args = [None if isinstance(a, type) and issubclass(a, pointer) else 0 for a in f.argtypes]
+        want = 0 if name in ("pg_destroy", "pg_budget_destroy") else 1
+        assert f(*args) == want, name
+        checked += 1
+    assert checked == len(pg.EXPORTED) - 2
