@@ -429,6 +429,28 @@ def test_sampling_chi_square_and_bins_and_pdf():
     assert np.allclose(s["pdf"], P[s["bin"]] * H * W / (4 * np.pi), rtol=1e-14)
 
 
+def test_one_leaf_grids_of_both_forms_sample_alike():
+    """A one-voxel grid of the paper's form (R = 1, no split) and a one-cell
+    octree are the same single leaf: sampling and evaluation through the
+    tree-walk path give what the code-search path gives, value for value."""
+    H, W = 8, 16
+    ph = synth.photons(500, 2, 21)
+    g_oct = _one_leaf_grid()
+    g_kd = O.build_kd_grid(ph, None, LO, HI, 1, 8, 10 ** 6, 0.5)
+    assert g_kd["L"] == 1 and g_kd["kd"]
+    y = _random_maps(1, H, W, 22, zero_rows=False)
+    y[0, 3, :] = 0.0  # an empty row
+    t = O.tables_from_map(y)
+    pos = synth.query_positions(20000, 21)
+    one = np.zeros(1, np.int32)
+    a = O.sample(g_oct, one, t, pos, seed=31, stream=4)
+    b = O.sample(g_kd, one, t, pos, seed=31, stream=4)
+    for k in ("leaf", "bin", "dir", "pdf"):
+        assert np.array_equal(a[k], b[k]), k
+    d = synth.query_directions(20000, 21)
+    assert np.array_equal(O.eval_pdf(g_oct, one, t, pos, d), O.eval_pdf(g_kd, one, t, pos, d))
+
+
 def test_pdf_monte_carlo_mean_is_one():
     """E over uniform directions of p(w) * 4pi equals the integral of p: 1."""
     H, W = 16, 16
