@@ -67,3 +67,29 @@ def test_every_entry_point_rejects_null_handles_without_gpu(lib):
         assert f(*args) == want, name
         checked += 1
     assert checked == len(pg.EXPORTED) - 2
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/pg.h compiles as strict C99 and as C++11, and a C program that
+    takes the address of every declared entry point links against libpg.so
+    and runs (no entry point is called)."""
+    import shutil
+    import subprocess
+    gcc, gxx = shutil.which("gcc"), shutil.which("g++")
+    if not gcc or not gxx:
+        pytest.skip("no host C compiler")
+    names = sorted(_declared())
+    src = tmp_path / "uses_pg.c"
+    src.write_text('#include "pg.h"\n#include <stddef.h>\ntypedef void (*fn)(void);\n'
+                   "static const fn entry[] = {\n" + "".join(f"  (fn){n},\n" for n in names) + "};\n"
+                   "int main(void) {\n  size_t i, n = sizeof entry / sizeof entry[0];\n"
+                   "  for (i = 0; i < n; ++i) if (!entry[i]) return 1;\n"
+                   f"  return n == {len(names)} ? 0 : 2;\n}}\n")
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(pg.LIB_PATH)
+    exe = tmp_path / "uses_pg"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src), "-o", str(exe),
+                    "-L", libdir, "-lpg", f"-Wl,-rpath,{libdir}"], check=True, capture_output=True)
+    subprocess.run([gxx, "-std=c++11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, "-x", "c++", "-c",
+                    str(src), "-o", str(tmp_path / "uses_pg_cxx.o")], check=True, capture_output=True)
+    assert subprocess.run([str(exe)]).returncode == 0
