@@ -920,6 +920,118 @@ def test_residual_link_and_masked_zeros():
     assert out.shape == (2, 16, 16) and np.all(np.isfinite(out)) and np.all(out >= 0)
 
 
+def _torch_paper_net(x, net):
+    """The paper-style masked U-Net wired from its layer table with
+    torch.nn.functional in float64 (library pin of the wiring).
+
+    Partial convolution (Liu et al. 2018): conv2d of the masked input, scaled
+    by 9 / (valid pixels under the window) counted by conv2d of the mask with
+    a ones kernel, plus the bias where that count is positive, else 0.  The
+    output mask is a 3x3 max-pool of the input mask (same stride, spacing and
+    padding as the layer).  Residual links are explicit adds after the ELU;
+    decoder levels concatenate [nearest x2 upsample, skip] along channels, and
+    their mask is the elementwise max (union) of the two parts' masks."""
+    Ls, dil = net["layers"], net["dil"]
+    t = torch.from_numpy(x).permute(0, 3, 1, 2).contiguous()
+
+    def pconv(h, m, i, res=None):
+        cout, cin, k, stride, act, w, b = Ls[i]
+        d = dil[i]
+        wt = torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2)
+        y = Fnn.conv2d(h * m, wt, None, stride=stride, padding=d * (k // 2), dilation=d)
+        cnt = Fnn.conv2d(m, torch.ones(1, 1, k, k, dtype=torch.float64), None, stride=stride,
+                         padding=d * (k // 2), dilation=d)
+        bias = torch.from_numpy(b.astype(np.float64)).view(1, -1, 1, 1)
+        y = torch.where(cnt > 0, y * (k * k) / cnt.clamp(min=1.0) + bias, torch.zeros_like(y))
+        y = Fnn.elu(y)
+        if res is not None:
+            y = y + res
+        pad = d * (k // 2)  # masks are >= 0, so zero padding leaves the max unchanged
+        m_out = Fnn.max_pool2d(Fnn.pad(m, (pad, pad, pad, pad)), k, stride=stride, dilation=d)
+        return y, m_out
+
+    up = lambda h: Fnn.interpolate(h, scale_factor=2, mode="nearest")
+    m = t[:, 4:5]
+    a0, m = pconv(t, m, 0)
+    e0, me0 = pconv(a0, m, 1, a0)
+    a1, m = pconv(e0, me0, 2)
+    e1, me1 = pconv(a1, m, 3, a1)
+    b0, m = pconv(e1, me1, 4)
+    b1, m = pconv(b0, m, 5, b0)
+    b2, m = pconv(b1, m, 6, b1)
+    d1, m = pconv(torch.cat([up(b2), e1], 1), torch.maximum(up(m), me1), 7)
+    d1, m = pconv(d1, m, 8, d1)
+    d0, m = pconv(torch.cat([up(d1), e0], 1), torch.maximum(up(m), me0), 9)
+    d0, _ = pconv(d0, m, 10, d0)
+    cout, cin, k, stride, act, w, b = Ls[11]
+    y = Fnn.conv2d(d0, torch.from_numpy(w.astype(np.float64)).permute(0, 3, 1, 2),
+                   torch.from_numpy(b.astype(np.float64)))
+    return Fnn.softplus(y)[:, 0].numpy()
+
+
+@pytest.mark.parametrize("H,W,density", [(16, 16, 0.15), (32, 16, 0.05), (32, 32, 0.6)])
+def test_paper_net_matches_torch_wiring(H, W, density):
+    """The whole paper-style network as wired, on sparse masks: a slip in the
+    oracle's skip order, mask union, mask pyramid or residual positions moves
+    bins that this independent torch build does not."""
+    net = O.parse_net(synth.net_blob(synth.ARCH_PAPER, (8, 16), 56))
+    rng = np.random.default_rng(57 + H + W)
+    A = 3
+    mask = (rng.random((A, H, W)) < density).astype(np.float64)
+    x = rng.random((A, H, W, 5)) * 2.0
+    x[..., 4] = mask
+    x[..., :4] *= mask[..., None]
+    got = O.cnn_forward(x, net)
+    ref = _torch_paper_net(x, net)
+    assert got.shape == ref.shape == (A, H, W) and np.all(ref > 0)
+    # Compared in log space: for a logit v << 0 softplus(v) ~ e^v, so an FP64
+    # rounding of v from another summation order becomes a relative error of
+    # |v| * 2^-52 on the map (about 1e-10 at v = -73 in the dense case).
+    assert np.allclose(np.log(got), np.log(ref), rtol=0, atol=1e-9)
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-300)
+
+
+def test_paper_net_torch_pin_detects_wiring_slips():
+    """The torch build above tells the oracle's wiring from plausible slips:
+    the skip halves swapped, the concatenation's mask taken from the skip
+    alone, or a residual dropped, each changes the map."""
+    net = O.parse_net(synth.net_blob(synth.ARCH_PAPER, (8, 16), 58))
+    rng = np.random.default_rng(59)
+    mask = np.zeros((2, 32, 32))
+    mask[0, 3, 5] = mask[0, 20, 25] = mask[1, 10, 10] = mask[1, 11, 12] = 1.0  # masks stay sparse down the levels
+    x = rng.random((2, 32, 32, 5))
+    x[..., 4] = mask
+    x[..., :4] *= mask[..., None]
+    ref = _torch_paper_net(x, net)
+    L = net["layers"]
+
+    def variant(swap_skip=False, skip_mask_only=False, drop_res=False):
+        def run(h, m, i, res=None):
+            cout, cin, k, stride, act, w, b = L[i]
+            return O.pconv(h, m, w, b, stride, net["dil"][i], act, None if drop_res and i == 8 else res)
+        m0 = x[..., 4]
+        a0, m1 = run(x[..., :5], m0, 0)
+        e0, me0 = run(a0, m1, 1, a0)
+        a1, m3 = run(e0, me0, 2)
+        e1, me1 = run(a1, m3, 3, a1)
+        b0, m5 = run(e1, me1, 4)
+        b1, m6 = run(b0, m5, 5, b0)
+        b2, m7 = run(b1, m6, 6, b1)
+        parts = [e1, O.upsample2(b2)] if swap_skip else [O.upsample2(b2), e1]
+        mk = me1 if skip_mask_only else np.maximum(O.upsample2(m7[..., None])[..., 0], me1)
+        d1, md1 = run(np.concatenate(parts, axis=3), mk, 7)  # both halves are c1 wide here
+        d1b, md1b = run(d1, md1, 8, d1)
+        c0 = np.concatenate([O.upsample2(d1b), e0], axis=3)
+        d0, md0 = run(c0, np.maximum(O.upsample2(md1b[..., None])[..., 0], me0), 9)
+        d0b, _ = run(d0, md0, 10, d0)
+        cout, cin, k, stride, act, w, b = L[11]
+        return O._act(O.conv2d(d0b, w, b, stride), act)[..., 0]
+
+    assert np.allclose(variant(), ref, rtol=1e-9, atol=1e-300)
+    for kw in ({"swap_skip": True}, {"skip_mask_only": True}, {"drop_res": True}):
+        assert not np.allclose(variant(**kw), ref, rtol=1e-6, atol=0), kw
+
+
 def test_progressive_with_the_papers_grid_rule_and_slots():
     """Refinement by the paper's rule (two iterations, normals), then batches
     binned by walking the voxels' trees; map slots: refined leaves in leaf
