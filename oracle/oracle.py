@@ -46,11 +46,12 @@ NET_MAGIC = 0x314E4750
 
 
 def build(force: bool = False) -> str:
-    """Compile pg_oracle.c with gcc (IEEE, no FMA contraction, no fast math)."""
+    """Compile pg_oracle.c with gcc (IEEE, no FMA contraction, no fast math;
+    OpenMP for the per-output loops, which does not change any result)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
                                "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -83,7 +84,15 @@ def lib():
         L.or_conv2d_dilated.argtypes = [P, i64, i32, i32, i32, P, P, i32, i32, i32, i32, P]
         L.or_sample_leaves.argtypes = [P, i64, P, i32, i32, P, P, P, P, u64, u32, P, P, P, P]
         L.or_eval_pdf_leaves.argtypes = [P, P, i64, P, i32, i32, P, P, P]
+        L.or_set_threads.restype = i32
+        L.or_set_threads.argtypes = [i32]
     return _lib
+
+
+def set_threads(n: int = 0) -> int:
+    """Host threads of the convolution, sampling and evaluation loops (0: all
+    cores); returns the count used.  Outputs are identical for every count."""
+    return int(lib().or_set_threads(n))
 
 
 def _p(a: np.ndarray):

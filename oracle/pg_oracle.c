@@ -13,13 +13,27 @@
  * no contraction; this file is compiled with -ffp-contract=off).
  *
  * Every function cites the passage of the paper it follows.
+ *
+ * The convolution loops (one (leaf, output row) per iteration) and the
+ * per-query sampling and evaluation loops are spread over host threads with
+ * OpenMP: every output value is still the same sequential computation in the
+ * same order, so results do not depend on the thread count (or_set_threads;
+ * default: all cores).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 enum { OR_OK = 0, OR_ERR_OVERFLOW = 4, OR_ERR_INVALID_INPUT = 8, OR_ERR_CAPACITY = 9 };
+
+/* Host threads of the parallel loops (n <= 0: all cores); returns the
+ * count the next parallel loop will use. */
+int or_set_threads(int n) {
+  omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+  return omp_get_max_threads();
+}
 
 /* ------------------------------------------------------------------------ */
 /* a1. Voxel location (Algorithm 1, Sec. 7.1 grid).                          */
@@ -295,6 +309,7 @@ void or_assemble_inputs(int64_t A, int64_t HW, const uint64_t *pow_cur, const ui
 void or_conv2d_dilated(const double *in, int64_t L, int Hin, int Win, int Cin, const float *w, const float *b,
                        int Cout, int k, int stride, int dil, double *out) {
   int Hout = Hin / stride, Wout = Win / stride, r = k / 2;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t l = 0; l < L; ++l)
     for (int y = 0; y < Hout; ++y)
       for (int x = 0; x < Wout; ++x)
@@ -318,6 +333,7 @@ void or_conv2d_dilated(const double *in, int64_t L, int Hin, int Win, int Cin, c
 void or_conv2d(const double *in, int64_t L, int Hin, int Win, int Cin, const float *w, const float *b,
                int Cout, int k, int stride, double *out) {
   int Hout = Hin / stride, Wout = Win / stride, pad = k / 2;
+#pragma omp parallel for collapse(2) schedule(static)
   for (int64_t l = 0; l < L; ++l)
     for (int y = 0; y < Hout; ++y)
       for (int x = 0; x < Wout; ++x)
@@ -428,6 +444,7 @@ void or_sample(const float *pos, int64_t q, const float lo[3], const float hi[3]
                uint32_t stream, double *dir, double *pdf, uint32_t *leaf_out, uint32_t *bin_out) {
   float s[3];
   or_axis_scale(lo, hi, D, s);
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < q; ++t) {
     uint32_t qq[3];
     for (int a = 0; a < 3; ++a) quantise(pos[3 * t + a], lo[a], s[a], D, &qq[a]);
@@ -440,6 +457,7 @@ void or_sample(const float *pos, int64_t q, const float lo[3], const float hi[3]
 void or_sample_leaves(const int64_t *leaf, int64_t q, const int32_t *slot_of_leaf, int H, int W, const double *P,
                       const float *Fz, const float *Fphi, const uint8_t *valid, uint64_t seed, uint32_t stream,
                       double *dir, double *pdf, uint32_t *leaf_out, uint32_t *bin_out) {
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < q; ++t)
     sample_one(t, leaf[t], slot_of_leaf, H, W, P, Fz, Fphi, valid, seed, stream, dir, pdf, leaf_out, bin_out);
 }
@@ -461,6 +479,7 @@ void or_eval_pdf(const float *pos, const float *dirs, int64_t q, const float lo[
   or_axis_scale(lo, hi, D, s);
   float *c = (float *)malloc(sizeof(float) * W), *sn = (float *)malloc(sizeof(float) * W);
   or_phi_table(W, c, sn);
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < q; ++t) {
     uint32_t qq[3];
     for (int a = 0; a < 3; ++a) quantise(pos[3 * t + a], lo[a], s[a], D, &qq[a]);
@@ -475,6 +494,7 @@ void or_eval_pdf_leaves(const int64_t *leaf, const float *dirs, int64_t q, const
                         int W, const double *P, const uint8_t *valid, double *pdf) {
   float *c = (float *)malloc(sizeof(float) * W), *sn = (float *)malloc(sizeof(float) * W);
   or_phi_table(W, c, sn);
+#pragma omp parallel for schedule(static)
   for (int64_t t = 0; t < q; ++t) pdf[t] = eval_one(leaf[t], dirs + 3 * t, slot_of_leaf, H, W, P, valid, c, sn);
   free(c);
   free(sn);

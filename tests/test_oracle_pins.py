@@ -293,6 +293,33 @@ def test_conv2d_matches_torch(A, H, W, Cin, Cout, k, stride):
     assert np.allclose(got, ref.permute(0, 2, 3, 1).numpy(), rtol=1e-12, atol=1e-12)
 
 
+def test_oracle_results_do_not_depend_on_thread_count():
+    """The parallel loops compute every output by the same sequential sum:
+    one host thread and all of them give identical bits."""
+    rng = np.random.default_rng(16)
+    x = rng.standard_normal((3, 16, 16, 8))
+    w = rng.standard_normal((8, 3, 3, 8)).astype(np.float32)
+    b = rng.standard_normal(8).astype(np.float32)
+    ph = synth.photons(20_000, 4, 16)
+    g = O.build_grid(ph, LO, HI, 4, 0, 500)
+    act, slot = O.active_leaves(g)
+    h = O.hist_for_active(O.splat(ph, g, 10_000, 8, 16), act)
+    t = O.tables_from_map(np.exp(O.assemble_inputs(h)[..., 2]))
+    pos = synth.query_positions(5000, 16)
+    d = synth.query_directions(5000, 16)
+    out = []
+    try:
+        for n in (1, 0):
+            O.set_threads(n)
+            s = O.sample(g, slot, t, pos, 7)
+            out.append((O.conv2d(x, w, b, 1), O.conv2d(x, w, b, 2, 2), s["dir"], s["pdf"], s["bin"],
+                        O.eval_pdf(g, slot, t, pos, d)))
+    finally:
+        O.set_threads(0)
+    for a, c in zip(*out):
+        assert np.array_equal(a, c)
+
+
 def test_conv2d_delta_kernel_is_identity():
     rng = np.random.default_rng(14)
     x = rng.standard_normal((2, 8, 8, 3))
