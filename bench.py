@@ -168,7 +168,7 @@ def run_pg(args, wl, prec):
                                        KD_THR, KD_VTHR)
         return pg.pg_build_grid(ctx, p_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
 
-    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, keep_tables=False, vtx=None, p_nrm=None):
+    def step(p_ph, p_pos, p_dir, outs, pr, marks=None, probe=None, vtx=None, p_nrm=None):
         o_d, o_p, o_l, o_b, o_e, o_s = outs
         vtx = vtx if vtx is not None else d_vtx
         rec = (lambda i: marks[i].record(stream)) if marks is not None else (lambda i: None)
@@ -196,10 +196,10 @@ def run_pg(args, wl, prec):
         rec(6)
         A = g.info(pg.PG_INFO_N_ACTIVE)
         L = g.info(pg.PG_INFO_N_LEAVES)
-        P = pg.export_tables(t)["P"] if keep_tables else None
+        got = probe(g, t) if probe is not None else None
         for hd in (t, m, h, g):
             hd.free()
-        return A, L, P
+        return A, L, got
 
     # Launch shapes of the tensor-core convolutions are tuned once, untimed.
     g0 = build_grid(d_ph)
@@ -364,12 +364,16 @@ def run_pg(args, wl, prec):
         bound, unit = "tensor", "TFLOP/s"
     achieved = flops_leaf * A / cnn_s / 1e12
 
-    # The other precisions of the same workload (shorter runs), and their
-    # sampling maps on a few leaves for the CPU-baseline leg's KL check.
+    # The other precisions of the same workload (shorter runs).  For the
+    # reduced-precision check each one's sampling map is kept on the leaves
+    # the oracle recomputes (stratified by photon count), and guided samples
+    # drawn at the centres of a few of them for the chi-square test.
     names = {pg.PG_FP32: "fp32", pg.PG_BF16: "bf16", pg.PG_FP8_E4M3: "fp8", pg.PG_FP8_MIXED: "fp8mix"}
-    sweep, maps = {}, {}
-    check = None
+    sweep, maps, chi_bins = {}, {}, {}
+    ocheck = None
     if args.sweep and world == 1:
+        ocheck = OracleCheck(wl) if (not args.no_cpu_baseline and not experts and args.grid == "octree") else None
+        probe = ocheck.gpu_probe(ctx, pg, torch) if ocheck is not None else None
         for pr in ((pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3, pg.PG_FP8_MIXED) if args.arch == "unet"
                    else (pg.PG_FP32, pg.PG_BF16)):
             r = main if pr == prec else measure(pr, max(1, min(args.steps, 3)), 1)
@@ -377,11 +381,9 @@ def run_pg(args, wl, prec):
                                 "ms_per_step": r["total_ms"] / len(r["times"]),
                                 "leaf_tables_per_s": r["A"] * len(r["times"]) / (r["total_ms"] / 1e3),
                                 "cnn_ms": r["stage_ms"]["cnn"]}
-            _, _, P = step(d_ph, d_pos, d_dir, outs, pr, keep_tables=True)
-            if check is None:
-                check = np.linspace(0, P.shape[0] - 1, args.cpu_sample_leaves).astype(np.int64)
-            if not experts:  # the oracle leg runs the single net
-                maps[names[pr]] = P[check].astype(np.float64)
+            if probe is not None:
+                _, _, got = step(d_ph, d_pos, d_dir, outs, pr, probe=probe)
+                maps[names[pr]], chi_bins[names[pr]] = got
     mis_alpha = None
     if mis is not None:
         e = pg.export_mis(mis)
@@ -391,6 +393,14 @@ def run_pg(args, wl, prec):
     for hd in (h0, g0):
         hd.free()
     ctx.destroy()
+    # The precision workload (128x128 maps, the same photons, U-Net and
+    # queries) as its own table: every form's step rate and its check
+    # against the oracle.
+    prec_block, ocheck3, maps3, chi3 = None, None, None, None
+    if (args.precision_config and world == 1 and args.sweep and args.arch == "unet" and not experts
+            and args.grid == "octree" and not args.mis and wl.H == 64 and wl.n_photons == synth.SCALE.n_photons):
+        prec_block, ocheck3, maps3, chi3 = run_precision_config(args, synth.PRECISION,
+                                                                with_oracle=not args.no_cpu_baseline)
 
     value = whole_job_rate(q, args.steps, world, total_ms)
     if rank == 0:
@@ -439,12 +449,99 @@ def run_pg(args, wl, prec):
             out["precisions"] = sweep
         if mis_alpha is not None:
             out["mis_alpha"] = mis_alpha
+        if prec_block is not None:
+            out["configs"] = {"precision": prec_block}
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves, check, maps, out.get("precisions"),
-                                               mis=args.mis, kd=args.grid == "kd")
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_leaves, ocheck, maps, chi_bins,
+                                               out.get("precisions"), mis=args.mis, kd=args.grid == "kd")
+        if prec_block is not None and ocheck3 is not None:
+            t0 = time.perf_counter()
+            tm = ocheck3.run(threads=0)
+            ocheck3.attach(prec_block["precisions"], maps3, chi3)
+            prec_block["oracle"] = {"threads": tm["threads"], "leaves": int(len(ocheck3.slots)),
+                                    "wall_s": round(time.perf_counter() - t0 + ocheck3.grid_s, 1),
+                                    "what": "FP64 grid + splat of all photons, CNN + tables of the checked leaves"}
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_precision_config(args, wl, with_oracle=True):
+    """Every CNN form (FP32, BF16, FP8 E4M3, FP8 inside / BF16 outside) on
+    the precision workload (128x128 maps): the whole step timed as in the
+    main line, and each form's sampling map on the checked leaves plus guided
+    samples for the chi-square, kept for the comparison with the FP64
+    oracle."""
+    import torch
+
+    from paper_2010_01775_gb300 import pg, synth
+    ph, pos, dirs, blob = synth.workload_inputs(wl)
+    n, q, H, W = wl.n_photons, wl.n_queries, wl.H, wl.W
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = pg.Context(stream.cuda_stream)
+    net = pg.pg_net_load(ctx, blob)
+    d_ph, d_pos, d_dir = (torch.from_numpy(a).cuda() for a in (ph, pos, dirs))
+    o_d, o_p = torch.empty(q, 3, device="cuda"), torch.empty(q, device="cuda")
+    o_l, o_b = torch.empty(q, dtype=torch.int32, device="cuda"), torch.empty(q, dtype=torch.int32, device="cuda")
+    o_e = torch.empty(q, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ocheck = OracleCheck(wl) if with_oracle else None
+    probe = ocheck.gpu_probe(ctx, pg, torch) if ocheck is not None else None
+
+    def step(pr, marks=None, probe=None):
+        rec = (lambda i: marks[i].record(stream)) if marks is not None else (lambda i: None)
+        rec(0)
+        g = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+        h = pg.pg_splat_photons(ctx, g, d_ph, n, wl.n_prev, H, W, wl.frac_bits)
+        rec(1)
+        m = pg.pg_reconstruct(ctx, h, net, pr)
+        rec(2)
+        t = pg.pg_build_cdf(ctx, m)
+        pg.pg_sample_dirs(ctx, g, t, d_pos, q, 20101775, 0, o_d, o_p, o_l, o_b)
+        pg.pg_eval_pdf(ctx, g, t, d_pos, d_dir, q, o_e)
+        rec(3)
+        A = g.info(pg.PG_INFO_N_ACTIVE)
+        got = probe(g, t) if probe is not None else None
+        for hd in (t, m, h, g):
+            hd.free()
+        return A, got
+
+    g0 = pg.pg_build_grid(ctx, d_ph, n, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+    h0 = pg.pg_splat_photons(ctx, g0, d_ph, n, wl.n_prev, H, W, wl.frac_bits)
+    if args.autotune:
+        for pr in (pg.PG_BF16, pg.PG_FP8_E4M3, pg.PG_FP8_MIXED):
+            pg.pg_autotune(ctx, h0, net, pr)
+    h0.free()
+    g0.free()
+    names = {pg.PG_FP32: "fp32", pg.PG_BF16: "bf16", pg.PG_FP8_E4M3: "fp8", pg.PG_FP8_MIXED: "fp8mix"}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    table, maps, bins = {}, {}, {}
+    A = 0
+    for pr in (pg.PG_FP32, pg.PG_BF16, pg.PG_FP8_E4M3, pg.PG_FP8_MIXED):
+        steps = 2 if pr == pg.PG_FP32 else max(2, min(args.steps, 5))
+        step(pr)
+        ctx.sync()
+        times, cnn = [], []
+        for _ in range(steps):
+            flush.zero_()
+            marks = [ev() for _ in range(4)]
+            A, _ = step(pr, marks)
+            marks[3].synchronize()
+            times.append(marks[0].elapsed_time(marks[3]))
+            cnn.append(marks[1].elapsed_time(marks[2]))
+        ms = float(np.mean(times))
+        flops = unet_flops_per_leaf(H, W, wl.widths, wl.arch) * A
+        table[names[pr]] = {"ms_per_step": ms, "value": q / (ms / 1e3), "unit": "samples/s",
+                            "leaf_tables_per_s": A / (ms / 1e3), "cnn_ms": float(np.mean(cnn)),
+                            "cnn_tflops": flops / (float(np.mean(cnn)) / 1e3) / 1e12}
+        if probe is not None:
+            _, got = step(pr, probe=probe)
+            maps[names[pr]], bins[names[pr]] = got
+    ctx.destroy()
+    block = {"workload": wl.name, "H": H, "W": W, "active_leaves": int(A), "queries": q,
+             "l2": "flushed between steps (256 MB write)", "precisions": table}
+    return block, ocheck, maps, bins
 
 
 def run_batch(args, bw, prec):
@@ -837,20 +934,194 @@ def progressive_cpu_baseline(wl, n_leaves, n_batch=262_144, n_queries=262_144):
                        f"({step_s:.1f} s); wall {t4 - t0:.1f} s")}
 
 
-def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False, kd=False):
+N_CHECK_LEAVES = 64    # leaves of the reduced-precision KL / L1 check, stratified by photon count
+N_CHI_LEAVES = 8       # leaves of the sample chi-square check (a stratified subset of those)
+CHI_SAMPLES = 65_536   # guided samples per chi-square leaf
+KL_GATE = 1e-3         # mean-over-leaves KL(P_oracle || P_gpu) a reduced-precision form must meet
+CHI_SEED = 20101775 ^ 0xC1
+
+
+def host_cpu():
+    """Core count and CPU model of this host (for the oracle's timings)."""
+    model = None
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def stratified(counts, n):
+    """n indices spread evenly over the ascending order of counts (every
+    photon-count stratum from the emptiest leaf to the fullest)."""
+    order = np.argsort(np.asarray(counts), kind="stable")
+    k = np.unique(np.linspace(0, len(order) - 1, min(n, len(order))).round().astype(np.int64))
+    return np.sort(order[k])
+
+
+def leaf_centres(g, leaves):
+    """Centre of each octree leaf: its first cell at full depth D (the Morton
+    code's de-interleaved bits) plus half the leaf's edge, in the domain."""
+    D = g["D"]
+    codes = g["leaf_code"][leaves].astype(np.uint64)
+    q = np.zeros((len(leaves), 3))
+    for b in range(D):
+        for a in range(3):
+            q[:, a] += ((codes >> np.uint64(3 * b + a)) & np.uint64(1)).astype(np.float64) * float(1 << b)
+    edge = 2.0 ** (D - g["leaf_depth"][leaves].astype(np.float64))
+    lo, hi = np.asarray(g["lo"], np.float64), np.asarray(g["hi"], np.float64)
+    return ((q + edge[:, None] / 2.0) / 2.0 ** D * (hi - lo) + lo).astype(np.float32)
+
+
+def kl_l1(P_ref, P):
+    """Per leaf KL(P_ref || P) and L1 = sum |P_ref - P| of maps [n][HW]."""
+    kl, l1 = [], []
+    for a in range(P_ref.shape[0]):
+        p, qq = P_ref[a].ravel(), P[a].ravel().astype(np.float64)
+        nz = p > 0
+        kl.append(float(np.sum(p[nz] * np.log(p[nz] / np.maximum(qq[nz], 1e-300)))))
+        l1.append(float(np.abs(p - qq).sum()))
+    return np.array(kl), np.array(l1)
+
+
+def chi_square(bins, P_ref, n_per_leaf):
+    """Pearson chi-square of guided-sample bins against the oracle's map, per
+    leaf: expected counts n P_k, bins with expectation below 5 pooled into one
+    cell; returns (chi2 / dof per leaf, p-values)."""
+    from scipy.stats import chi2 as chi2_dist
+    red, pv = [], []
+    for a in range(P_ref.shape[0]):
+        b = bins[a * n_per_leaf:(a + 1) * n_per_leaf].astype(np.int64)
+        obs = np.bincount(b[(b >= 0) & (b < P_ref.shape[1])], minlength=P_ref.shape[1]).astype(np.float64)
+        exp = n_per_leaf * P_ref[a].ravel()
+        big = exp >= 5.0
+        o = np.append(obs[big], obs[~big].sum())
+        e = np.append(exp[big], exp[~big].sum())
+        keep = e > 0
+        o, e = o[keep], e[keep]
+        c2, dof = float(np.sum((o - e) ** 2 / e)), max(1, int(keep.sum()) - 1)
+        red.append(c2 / dof)
+        pv.append(float(chi2_dist.sf(c2, dof)))
+    return np.array(red), np.array(pv)
+
+
+class OracleCheck:
+    """The FP64 oracle's sampling maps on leaves stratified by photon count,
+    for the reduced-precision check of every GPU form: KL and L1 of its map
+    against the oracle's (mean, p99, max over the leaves) and a chi-square of
+    its guided samples, drawn at the centres of a subset of the leaves,
+    against the oracle's pdf.  Which leaves are checked is decided here, from
+    the oracle's own grid (bit-identical to the GPU's)."""
+
+    def __init__(self, wl, n_leaves=N_CHECK_LEAVES, n_chi=N_CHI_LEAVES):
+        from oracle import oracle as O
+        from paper_2010_01775_gb300 import synth
+        self.O, self.wl = O, wl
+        self.ph, _, _, self.blob = _inputs(wl)
+        t0 = time.perf_counter()
+        self.g = O.build_grid(self.ph, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
+        self.grid_s = time.perf_counter() - t0
+        self.act, _ = O.active_leaves(self.g)
+        counts = (self.g["leaf_end"].astype(np.int64) - self.g["leaf_begin"])[self.act]
+        self.slots = stratified(counts, n_leaves)
+        self.chi_idx = stratified(counts[self.slots], n_chi)  # rows of self.slots
+        self.counts = counts[self.slots]
+        self.chi_pos = np.ascontiguousarray(np.repeat(leaf_centres(self.g, self.act[self.slots[self.chi_idx]]),
+                                                      CHI_SAMPLES, axis=0))
+        self.P = None
+        self.times = {}
+
+    def gpu_probe(self, ctx, pg, torch):
+        """A step hook: the GPU map on the checked leaves (slots) and the bins
+        of CHI_SAMPLES guided samples at each chi-square leaf's centre."""
+        d_pos = torch.from_numpy(self.chi_pos).cuda()
+        qn = self.chi_pos.shape[0]
+        o = (torch.empty(qn, 3, device="cuda"), torch.empty(qn, device="cuda"),
+             torch.empty(qn, dtype=torch.int32, device="cuda"), torch.empty(qn, dtype=torch.int32, device="cuda"))
+        slots = self.slots
+
+        def probe(g, t):
+            A, H, W = t.info(pg.PG_INFO_N_ACTIVE), t.info(pg.PG_INFO_H), t.info(pg.PG_INFO_W)
+            P = t.export(pg.PG_TAB_P, np.float32, A * H * W).reshape(A, H * W)
+            pg.pg_sample_dirs(ctx, g, t, d_pos, qn, CHI_SEED, 0, o[0], o[1], o[2], o[3])
+            ctx.sync()
+            return np.ascontiguousarray(P[slots]), o[3].cpu().numpy()
+        return probe
+
+    def run(self, threads=0):
+        """The oracle's splat of every photon, then CNN and tables on the
+        checked leaves; stage seconds in self.times."""
+        O, wl = self.O, self.wl
+        used = O.set_threads(threads)
+        t0 = time.perf_counter()
+        h = O.splat(self.ph, self.g, wl.n_prev, wl.H, wl.W, wl.frac_bits)
+        t1 = time.perf_counter()
+        y = O.cnn_forward(O.assemble_inputs(O.hist_for_active(h, self.act[self.slots])), O.parse_net(self.blob))
+        t2 = time.perf_counter()
+        self.P = O.tables_from_map(y)["P"].reshape(len(self.slots), -1)
+        t3 = time.perf_counter()
+        O.set_threads(0)
+        self.times = dict(grid=self.grid_s, splat=t1 - t0, cnn=t2 - t1, cdf=t3 - t2, threads=used)
+        return self.times
+
+    def stats(self, P_gpu, bins=None):
+        kl, l1 = kl_l1(self.P, P_gpu)
+        out = {"kl_vs_fp64_oracle": {"mean": float(kl.mean()), "p99": float(np.percentile(kl, 99)),
+                                     "max": float(kl.max()), "leaves": int(kl.size),
+                                     "leaf_photons": [int(self.counts.min()), int(self.counts.max())],
+                                     "selection": "stratified by leaf photon count"},
+               "l1_vs_fp64_oracle": {"mean": float(l1.mean()), "p99": float(np.percentile(l1, 99)),
+                                     "max": float(l1.max())},
+               "kl_gate": KL_GATE, "meets_kl_gate": bool(kl.mean() <= KL_GATE)}
+        if bins is not None:
+            red, pv = chi_square(bins, self.P[self.chi_idx], CHI_SAMPLES)
+            out["sample_chi2_vs_fp64_oracle"] = {
+                "chi2_per_dof_mean": float(red.mean()), "chi2_per_dof_max": float(red.max()),
+                "p_min": float(pv.min()), "leaves_p_above_0.01": int(np.sum(pv > 0.01)), "leaves": int(pv.size),
+                "samples_per_leaf": CHI_SAMPLES}
+        return out
+
+    def attach(self, precisions, maps, bins):
+        """Adds each form's check to its entry of the precision table."""
+        for name, P in maps.items():
+            precisions[name].update(self.stats(P, bins.get(name)))
+
+
+_INPUTS = {}
+
+
+def _inputs(wl):
+    """The workload's seeded inputs, generated once per process (input
+    generation is not part of any timed oracle stage)."""
+    from paper_2010_01775_gb300 import synth
+    if wl.name not in _INPUTS:
+        _INPUTS[wl.name] = synth.workload_inputs(wl)
+    return _INPUTS[wl.name]
+
+
+def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False, kd=False, threads=0):
     """The FP64 oracle on a bounded sample; returns per-stage seconds and the
-    throughput extrapolated to the full workload."""
+    throughput extrapolated to the full workload.  check: an OracleCheck whose
+    grid and leaves are reused (its maps are computed here)."""
     from oracle import oracle as O
     from paper_2010_01775_gb300 import synth
-    ph, pos, dirs, blob = synth.workload_inputs(wl)
+    used = O.set_threads(threads)
+    ph, pos, dirs, blob = _inputs(wl)
     t0 = time.perf_counter()
-    if kd:
+    if check is not None:
+        g, grid_s = check.g, check.grid_s
+    elif kd:
         g = O.build_kd_grid(ph, synth.wall_normals(ph), LO, HI, KD_R, KD_DEPTH, KD_THR, KD_VTHR)
     else:
         g = O.build_grid(ph, LO, HI, wl.max_depth, wl.min_depth, wl.split_threshold)
     act, slot = O.active_leaves(g)
     t1 = time.perf_counter()
-    keep = act[check] if check is not None else act[np.linspace(0, act.size - 1, n_leaves).astype(np.int64)]
+    if check is None:
+        grid_s = t1 - t0
+    keep = act[check.slots] if check is not None else act[np.linspace(0, act.size - 1, n_leaves).astype(np.int64)]
     gsub = dict(g)
     if kd:  # ~10^6 leaves: splat the kept leaves only and scale by their share of the photons
         sub = dict(g, L=keep.size, leaf_begin=g["leaf_begin"][keep], leaf_end=g["leaf_end"][keep])
@@ -868,6 +1139,8 @@ def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False, kd=False):
     t3 = time.perf_counter()
     tabs = O.tables_from_map(y)
     t4 = time.perf_counter()
+    if check is not None:
+        check.P = tabs["P"].reshape(keep.size, -1)
     slot2 = np.full(g["L"], -1, np.int32)
     slot2[keep] = np.arange(keep.size, dtype=np.int32)
     if mis:
@@ -882,34 +1155,39 @@ def oracle_sample_run(wl, n_leaves, n_queries, check=None, mis=False, kd=False):
         s = O.sample(gsub, slot2, tabs, pos[:n_queries], 20101775)
         O.eval_pdf(gsub, slot2, tabs, pos[:n_queries], dirs[:n_queries])
     t5 = time.perf_counter()
+    O.set_threads(0)
     A = act.size
-    step_s = (t1 - t0) + splat_s + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
+    step_s = grid_s + splat_s + (t3 - t2) * A / keep.size + (t4 - t3) * A / keep.size + \
         (t5 - t4) * wl.n_queries / n_queries
-    return dict(step_s=step_s, samples_per_s=wl.n_queries / step_s, wall_s=t5 - t0, leaves=int(keep.size),
-                A=int(A), queries=n_queries, P=tabs["P"])
+    return dict(step_s=step_s, samples_per_s=wl.n_queries / step_s, wall_s=t5 - t0 + (grid_s if check else 0.0),
+                leaves=int(keep.size), A=int(A), queries=n_queries, P=tabs["P"], threads=used,
+                stage_s=dict(grid=grid_s, splat=splat_s, cnn=(t3 - t2) * A / keep.size,
+                             cdf=(t4 - t3) * A / keep.size, sample_eval=(t5 - t4) * wl.n_queries / n_queries))
 
 
-def cpu_baseline(wl, n_leaves, check=None, maps=None, precisions=None, mis=False, kd=False):
-    r = oracle_sample_run(wl, n_leaves, 65_536 if mis else 262_144, check, mis, kd)
-    out = {"value": r["samples_per_s"], "unit": "samples/s", "cores": 1, "kind": "oracle",
-           "sample": (f"FP64 oracle, single thread: grid+splat on all {wl.n_photons} photons"
+def cpu_baseline(wl, n_leaves, check=None, maps=None, bins=None, precisions=None, mis=False, kd=False):
+    """The oracle timed on this host: single-threaded on a small sample, and
+    on all cores (OpenMP over the convolution, sampling and evaluation loops;
+    the grid and the splat stay sequential) on the checked leaves, whose maps
+    then serve the reduced-precision check."""
+    cores, model = host_cpu()
+    nq = 65_536 if mis else 262_144
+    r1 = oracle_sample_run(wl, n_leaves, nq, None, mis, kd, threads=1)
+    rN = oracle_sample_run(wl, n_leaves, nq, check, mis, kd, threads=0)
+    out = {"value": rN["samples_per_s"], "unit": "samples/s", "cores": rN["threads"], "kind": "oracle",
+           "cpu": model, "nproc": cores,
+           "value_1_thread": r1["samples_per_s"],
+           "stage_s_full_step": {k: round(v, 3) for k, v in rN["stage_s"].items()},
+           "sample": (f"FP64 oracle on {rN['threads']} threads (OpenMP over the convolution, sampling and "
+                      f"evaluation loops; grid and splat sequential): grid+splat on all {wl.n_photons} photons"
                       f"{' (the splat on the sampled leaves, scaled by their photon share)' if kd else ''}, CNN+CDF on "
-                      f"{r['leaves']} of {r['A']} active leaves, {'MIS ' if mis else ''}sample+eval on "
-                      f"{r['queries']} of {wl.n_queries} "
-                      f"queries; per-stage times scaled to the full step ({r['step_s']:.1f} s); "
-                      f"wall {r['wall_s']:.1f} s")}
-    if maps and precisions is not None:
-        Pr = r["P"]
-        for name, P in maps.items():
-            kl, l1 = [], []
-            for a in range(P.shape[0]):
-                p, qq = Pr[a].ravel(), np.maximum(P[a].ravel(), 1e-38)
-                nz = p > 0
-                kl.append(float(np.sum(p[nz] * np.log(p[nz] / qq[nz]))))
-                l1.append(float(np.abs(p - P[a].ravel()).sum()))
-            precisions[name]["kl_vs_fp64_oracle"] = {"mean": float(np.mean(kl)), "max": float(np.max(kl)),
-                                                     "leaves": len(kl)}
-            precisions[name]["l1_vs_fp64_oracle_mean"] = float(np.mean(l1))
+                      f"{rN['leaves']} of {rN['A']} active leaves"
+                      f"{' (stratified by photon count)' if check is not None else ''}, "
+                      f"{'MIS ' if mis else ''}sample+eval on {rN['queries']} of {wl.n_queries} queries; per-stage "
+                      f"times scaled to the full step ({rN['step_s']:.1f} s; {r1['step_s']:.1f} s on one thread, "
+                      f"from {r1['leaves']} leaves); wall {rN['wall_s'] + r1['wall_s']:.1f} s")}
+    if check is not None and maps and precisions is not None:
+        check.attach(precisions, maps, bins or {})
     return out
 
 
@@ -930,26 +1208,39 @@ def whole_job_rate(units_per_rank_step, steps, world, job_ms):
 
 
 def run_reference(args, wl):
+    """The oracle as it stands (FP64, this host's cores) on the main line's
+    workload: every step is one bounded sample of it (grid + splat of every
+    photon, CNN + tables on a few leaves, sample + eval on a slice of the
+    queries), timed for real; `value` is the full step's rate extrapolated
+    from that step's per-stage times."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    steps = []
+    cores, model = host_cpu()
+    runs = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample_run(wl, 2, 65_536)
+        r = oracle_sample_run(wl, REF_LEAVES, REF_QUERIES, threads=0)
+        r["wall"] = r["wall_s"]  # the oracle's own stages, inputs already generated
         if i >= args.warmup:
-            steps.append(r)
-    step_s = statistics.mean(r["step_s"] for r in steps)
-    value = wl.n_queries / step_s
+            runs.append(r)
+    value = wl.n_queries / statistics.mean(r["step_s"] for r in runs)
+    wall_ms = statistics.mean(r["wall"] for r in runs) * 1e3
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "precision": "fp64 oracle"},
-        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": 1, "kind": "oracle",
-                         "sample": "per step: grid+splat on all photons, CNN+CDF on 2 active leaves, sample+eval on "
-                                   "65536 queries, scaled to the full step"},
+        "cpu_baseline": {"value": value, "unit": "samples/s", "cores": runs[0]["threads"], "kind": "oracle",
+                         "cpu": model, "nproc": cores,
+                         "sample": (f"per step (ms_per_step is its wall time): grid+splat on all {wl.n_photons} "
+                                    f"photons (sequential), CNN+CDF on {REF_LEAVES} active leaves and sample+eval on "
+                                    f"{REF_QUERIES} queries (OpenMP, {runs[0]['threads']} threads); value = "
+                                    f"{wl.n_queries} queries / the full step extrapolated from the per-stage times")},
         "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+REF_LEAVES, REF_QUERIES = 8, 65_536
 
 
 def main():
@@ -979,7 +1270,10 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-closed", type=int, default=64, help="requests in the closed-loop capacity run")
     ap.add_argument("--serve-fp32", type=int, default=12, help="requests in the FP32 one-at-a-time run")
-    ap.add_argument("--cpu-sample-leaves", type=int, default=4)
+    ap.add_argument("--cpu-sample-leaves", type=int, default=4,
+                    help="leaves of the single-thread oracle timing sample")
+    ap.add_argument("--precision-config", action=argparse.BooleanOptionalAction, default=True,
+                    help="also run every CNN form on the precision workload (128x128 maps) with its oracle check")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="tune the tensor-core launch shapes before timing (untimed)")
     ap.add_argument("--sweep", action=argparse.BooleanOptionalAction, default=True,
