@@ -515,7 +515,10 @@ const char *pg_status_string(pg_status status);
  * PG_ERR_UNSUPPORTED without touching the GPU.  The call waits for its work
  * and returns PG_ERR_INVALID_INPUT if a position was not finite.
  * The first call on a device looks up the scratch's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it with the id of the current CUDA context;
+ * the first call from any other context on that device (for example a new
+ * primary context after cudaDeviceReset) looks it up again.  Make such a
+ * first call before any stream capture.
  * Every call uses the same scratch array, which keeps the previous call's
  * contents (the status word is cleared at the start of each call): calls
  * that overlap on the GPU -- from several host threads or streams -- race

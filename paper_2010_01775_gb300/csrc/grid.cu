@@ -13,8 +13,11 @@
 //                   bottom-up leaf counts and top-down offsets put the leaves
 //                   in Morton order without sorting them
 //   k_leaf_assign   per photon: leaf id by binary search of leaf start codes (a4)
+#include <cuda.h>
 #include <math.h>
 #include <string.h>
+
+#include <mutex>
 
 #include <vector>
 
@@ -1429,6 +1432,42 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 constexpr int kMaxDevices = 64;
 static void *g_noalloc_ptr[kMaxDevices];
+static unsigned long long g_noalloc_ctx[kMaxDevices];  // context the address belongs to (0: none yet)
+
+// The unique id of the calling thread's current CUDA context (0 if none),
+// through the driver entry points the runtime exposes (no link to libcuda).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+pg_status current_context_id(unsigned long long *id) {
+  static const CtxGetCurrentFn get_current = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? (CtxGetCurrentFn)f
+               : (CtxGetCurrentFn) nullptr;
+  }();
+  static const CtxGetIdFn get_id = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    return cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+                   q == cudaDriverEntryPointSuccess
+               ? (CtxGetIdFn)f
+               : (CtxGetIdFn) nullptr;
+  }();
+  *id = 0;
+  if (!get_current || !get_id) return PG_ERR_UNSUPPORTED;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS) return PG_ERR_CUDA;
+  if (c && get_id(c, id) != CUDA_SUCCESS) return PG_ERR_CUDA;
+  return PG_OK;
+}
+
+std::mutex &noalloc_mutex() {
+  static std::mutex mu;
+  return mu;
+}
 
 }  // namespace
 }  // namespace pgi
@@ -1444,16 +1483,29 @@ extern "C" pg_status pg_sort_photons_noalloc(const pg_photon *d_photons, uint64_
   int dev = 0;
   PG_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return PG_ERR_UNSUPPORTED;
-  // One-time set-up on this device: the device address of the static
-  // scratch (the symbol itself is only a host-side stand-in).
-  if (!g_noalloc_ptr[dev]) {
-    void *ptr = nullptr;
-    PG_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = ptr;
+  // Set-up, once per device and context: the device address of the static
+  // scratch (the symbol itself is only a host-side stand-in).  The address
+  // is kept with the id of the context it was looked up in; a call from
+  // another context (a new primary context after cudaDeviceReset, say)
+  // looks it up again instead of using a dead address.
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(noalloc_mutex());
+    unsigned long long cid = 0;
+    PG_TRY(current_context_id(&cid));
+    if (!g_noalloc_ptr[dev] || cid == 0 || g_noalloc_ctx[dev] != cid) {
+      void *ptr = nullptr;
+      PG_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));  // makes the device's context current if none was
+      PG_TRY(current_context_id(&cid));
+      if (cid == 0) return PG_ERR_CUDA;
+      g_noalloc_ptr[dev] = ptr;
+      g_noalloc_ctx[dev] = cid;
+    }
+    base = g_noalloc_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const uint32_t nn = (uint32_t)n;
-  uint8_t *q = (uint8_t *)g_noalloc_ptr[dev];
+  uint8_t *q = (uint8_t *)base;
   uint64_t *kA = (uint64_t *)q; q += kNaKeys;
   uint64_t *kB = (uint64_t *)q; q += kNaKeys;
   uint32_t *vT = (uint32_t *)q; q += kNaVals;

@@ -32,10 +32,15 @@ def test_noalloc_sort_matches_build_grid_twice():
     torch.cuda.set_device(0)
     ctx = pg.Context()
     stream = torch.cuda.current_stream().cuda_stream
-    # Two different inputs in a row: a large one (several sort tiles, ragged
-    # tail, 4 radix passes), then a smaller one with a different depth, so
-    # stale scratch from the first call would show up in the second.
-    for n, D, seed in [(300_001, 10, 901), (77_777, 6, 902)]:
+    # Different inputs in a row: a large one (several sort tiles, ragged
+    # tail, 4 radix passes), a smaller one with a different depth (3
+    # passes), an empty call, and depth 16 at the size limit (48-bit codes,
+    # 6 passes: the largest use of the scratch), so stale scratch from one
+    # call would show up in the next.
+    for n, D, seed in [(300_001, 10, 901), (77_777, 6, 902), (0, 10, 903), (pg.PG_NOALLOC_MAX_PHOTONS, 16, 904)]:
+        if n == 0:
+            pg.pg_sort_photons_noalloc(0, 0, LO, HI, D, 0, 0, stream)  # nothing to do, no pointers needed
+            continue
         ph = synth.photons(n, 7, seed)
         d_ph = torch.from_numpy(ph).cuda()
         codes = torch.empty(n, dtype=torch.int64, device="cuda")
