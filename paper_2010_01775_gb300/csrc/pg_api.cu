@@ -52,10 +52,55 @@ cudaError_t &last_cuda_error() {
   return e;
 }
 
+// Frees are stream-ordered: cudaFreeAsync returns at once, and the block
+// stays live until the stream reaches it.  The shared budget gets the bytes
+// back only then: each free records an event, and the bytes of completed
+// events are released when the context next allocates, synchronises or is
+// destroyed (in stream order, so the queue is reaped from its head).
+struct PendingFrees {
+  std::mutex mu;
+  std::vector<cudaEvent_t> spare;                          // reusable events
+  std::vector<std::pair<cudaEvent_t, size_t>> queue;       // in stream order
+  size_t head = 0;
+};
+
+void ctx_reap_frees(pg_ctx *ctx, bool all) {
+  PendingFrees *pf = ctx->pending;
+  if (!pf) return;
+  if (all) cudaStreamSynchronize(ctx->stream);
+  std::lock_guard<std::mutex> lk(pf->mu);
+  size_t released = 0;
+  while (pf->head < pf->queue.size()) {
+    auto &e = pf->queue[pf->head];
+    const cudaError_t q = all ? cudaEventSynchronize(e.first) : cudaEventQuery(e.first);
+    if (q == cudaErrorNotReady) break;
+    released += e.second;
+    pf->spare.push_back(e.first);
+    ++pf->head;
+  }
+  cudaGetLastError();
+  if (pf->head == pf->queue.size()) {
+    pf->queue.clear();
+    pf->head = 0;
+  }
+  if (released && ctx->shared) budget_release(ctx->shared, released);
+}
+
+// Bytes still charged to the shared budget for frees that have not run.
+static size_t pending_bytes(pg_ctx *ctx) {
+  PendingFrees *pf = ctx->pending;
+  if (!pf) return 0;
+  std::lock_guard<std::mutex> lk(pf->mu);
+  size_t b = 0;
+  for (size_t i = pf->head; i < pf->queue.size(); ++i) b += pf->queue[i].second;
+  return b;
+}
+
 pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 256;
   bytes = (bytes + 255) & ~(size_t)255;
+  if (ctx->shared) ctx_reap_frees(ctx, false);
   if (ctx->budget && ctx->in_use + bytes > ctx->budget) return PG_ERR_OOM;
   if (ctx->shared && !budget_try_charge(ctx->shared, bytes)) return PG_ERR_OOM;
   cudaError_t e = cudaMallocAsync(ptr, bytes, ctx->stream);
@@ -75,7 +120,37 @@ void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
   cudaFreeAsync(ptr, ctx->stream);
   ctx->in_use = ctx->in_use >= bytes ? ctx->in_use - bytes : 0;
-  if (ctx->shared) budget_release(ctx->shared, bytes);
+  if (!ctx->shared) return;
+  // A free captured into a CUDA graph is a graph node, not work on the
+  // stream: its bytes go back at once, as the capture's allocations were
+  // charged at capture time.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (!ctx->pending || cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    budget_release(ctx->shared, bytes);
+    return;
+  }
+  PendingFrees *pf = ctx->pending;
+  cudaEvent_t ev = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(pf->mu);
+    if (!pf->spare.empty()) {
+      ev = pf->spare.back();
+      pf->spare.pop_back();
+    }
+  }
+  if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
+  if (!ev || cudaEventRecord(ev, ctx->stream) != cudaSuccess) {
+    // No event: wait for the stream, after which the free has run.
+    cudaGetLastError();
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamSynchronize(ctx->stream);
+    budget_release(ctx->shared, bytes);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(pf->mu);
+  pf->queue.emplace_back(ev, bytes);
 }
 
 // Boundary rays of the W phi sectors: (float cos, float sin) of 2 pi j / W,
@@ -343,6 +418,12 @@ pg_status pg_create(pg_ctx **out, void *stream, size_t budget) {
     delete c;
     return PG_ERR_CUDA;
   }
+  c->pending = new (std::nothrow) PendingFrees();
+  if (!c->pending) {
+    cudaFree(c->d_status);
+    delete c;
+    return PG_ERR_OOM;
+  }
   *out = c;
   return PG_OK;
 }
@@ -350,10 +431,13 @@ pg_status pg_create(pg_ctx **out, void *stream, size_t budget) {
 pg_status pg_destroy(pg_ctx *c) {
   if (!c) return PG_OK;
   cudaStreamSynchronize(c->stream);
+  ctx_reap_frees(c, true);
   if (c->shared) pg_ctx_attach_budget(c, nullptr);
   for (int i = 0; i < 9; ++i)
     if (c->d_phi[i]) cudaFree(c->d_phi[i]);
   cudaFree(c->d_status);
+  for (cudaEvent_t e : c->pending->spare) cudaEventDestroy(e);
+  delete c->pending;
   delete c;
   return PG_OK;
 }
@@ -370,6 +454,7 @@ pg_status pg_sync(pg_ctx *c) {
   PG_CUDA(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   PG_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
   PG_CUDA(cudaStreamSynchronize(c->stream));
+  ctx_reap_frees(c, false);  // every free enqueued so far has run
   if (st & ST_INVALID_INPUT) return PG_ERR_INVALID_INPUT;
   if (st & ST_OVERFLOW) return PG_ERR_OVERFLOW;
   if (st & ST_TIMEOUT) return PG_ERR_TIMEOUT;
@@ -444,6 +529,7 @@ pg_status pg_budget_destroy(pg_budget *b) {
 pg_status pg_ctx_attach_budget(pg_ctx *c, pg_budget *b) {
   if (!c) return PG_ERR_INVALID_ARG;
   if (b == c->shared) return PG_OK;
+  if (c->shared && pending_bytes(c)) ctx_reap_frees(c, true);  // the old budget gets its bytes back first
   if (b && !budget_try_charge(b, c->in_use)) return PG_ERR_OOM;
   if (c->shared) {
     budget_release(c->shared, c->in_use);

@@ -182,11 +182,16 @@ struct Progress {
 
 }  // namespace pgi
 
+namespace pgi {
+struct PendingFrees;  // shared-budget bytes whose stream-ordered frees have not run yet
+}
+
 struct pg_ctx {
   int device;
   cudaStream_t stream;
   size_t budget, in_use;
   pg_budget *shared;   // optional budget shared with other contexts
+  pgi::PendingFrees *pending;
   uint64_t launches;   // kernels launched for this context (pg_launch_count)
   uint32_t *d_status;  // device status word (pgi::ST_* bits)
   float *d_phi[9];     // boundary-ray tables (cos, sin) per log2(W), W <= 256
@@ -200,6 +205,9 @@ namespace pgi {
 // ---------------------------------------------------------------- memory
 pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr);
 void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes);
+// Returns to the shared budget the bytes of every free that has run on the
+// GPU (all of them when `all`, which waits for the context's stream).
+void ctx_reap_frees(pg_ctx *ctx, bool all);
 bool budget_try_charge(pg_budget *b, size_t bytes);
 void budget_release(pg_budget *b, size_t bytes);
 // Device tables (cos, sin) of the W boundary rays, built once per W on the

@@ -299,6 +299,12 @@ class GpuExecutor(Executor):
         for h in reversed(b.handles):
             h.free()
         b.handles.clear()
+        # The library returns a freed block's bytes to the shared budget once
+        # the stream has run the free; synchronising the context does that now.
+        try:
+            self.ctx.sync()
+        except pg.PgError:
+            pass  # a device-side error of the failed batch, already reported
         if b.tensors:
             self.stream.synchronize()
             b.tensors.clear()

@@ -1,14 +1,17 @@
 """Serving loop on the GPU: every request's results are the same served in a
 mix (several workers, scene batches, BF16 and FP8 interleaved) as computed
-alone through the single-scene calls; a malformed request fails alone; a
-request over the HBM budget fails with PG_ERR_OOM while the rest are
-served; a waiting request can be cancelled.
+alone through the single-scene calls; a served BF16 request's maps meet the
+reduced-precision gate against the FP64 oracle; a malformed request fails
+alone; a request over the HBM budget fails with PG_ERR_OOM while the rest
+are served; a waiting request can be cancelled; the shared budget gets a
+freed block's bytes back only once the stream has run the free.
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import oracle as O  # noqa: E402
 from paper_2010_01775_gb300 import pg, serve, synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -158,3 +161,77 @@ def test_cancel_waiting_request(pools):
         assert all(r.status == "done" for r in rs[:-1])
     finally:
         srv.close()
+
+
+def test_served_bf16_request_meets_the_gate_against_the_oracle(pools):
+    """A BF16 request served in a mix: its results equal the request alone
+    (whose tables decide every sample), and the maps of the request alone
+    meet the reduced-precision gate, mean KL(P_oracle || P) <= 1e-3 over its
+    leaves, against the FP64 oracle's path on the same photons."""
+    srv = serve.Server(NET, workers=2, hbm_budget=8 << 30, keep_results=True)
+    try:
+        srv.warmup(_warm(pools)[:2])
+        rs = _requests(pools, 500, 6, 9)
+        for r in rs:
+            r.precision = pg.PG_BF16
+        rs = [srv.submit(r) for r in rs]
+        for r in rs:
+            assert r.wait(120)
+        assert all(r.status == "done" for r in rs), [r.error for r in rs]
+        r = max(rs, key=lambda x: x.n)
+        ctx = pg.Context()
+        ref = _alone(ctx, srv.net, srv.seed, r)
+        for k in ("dirs", "pdf", "leaf", "bin", "eval_pdf"):
+            assert np.array_equal(r.result[k], ref[k]), k
+        ph = r.photons.numpy()
+        g = pg.pg_build_grid(ctx, r.photons.cuda(), r.n, r.lo, r.hi, r.max_depth, r.min_depth, r.split_threshold)
+        h = pg.pg_splat_photons(ctx, g, r.photons.cuda(), r.n, r.n // 2, r.H, r.W, r.frac_bits)
+        m = pg.pg_reconstruct(ctx, h, srv.net, pg.PG_BF16)
+        t = pg.pg_build_cdf(ctx, m)
+        ctx.sync()
+        P = pg.export_tables(t)["P"].reshape(-1, r.H * r.W).astype(np.float64)
+        for x in (t, m, h, g):
+            x.free()
+        ctx.destroy()
+        og = O.build_grid(ph, r.lo, r.hi, r.max_depth, r.min_depth, r.split_threshold)
+        act, _ = O.active_leaves(og)
+        oh = O.hist_for_active(O.splat(ph, og, r.n // 2, r.H, r.W, r.frac_bits), act)
+        Po = O.tables_from_map(O.cnn_forward(O.assemble_inputs(oh), O.parse_net(NET)))["P"].reshape(-1, r.H * r.W)
+        assert Po.shape == P.shape and act.size > 3
+        kl = [float(np.sum(p[p > 0] * np.log(p[p > 0] / np.maximum(q[p > 0], 1e-300)))) for p, q in zip(Po, P)]
+        assert np.mean(kl) <= 1e-3, (np.mean(kl), np.max(kl))
+    finally:
+        srv.close()
+
+
+def test_shared_budget_released_after_the_free_runs():
+    """A handle freed behind queued GPU work stays charged to the shared
+    budget until the stream has run its free; synchronising the context
+    returns the bytes."""
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    st = torch.cuda.Stream()
+    ctx = pg.Context(st.cuda_stream)
+    b = pg.Budget(1 << 34)
+    b.attach(ctx)
+    try:
+        ph = synth.photons(200_000, 8, 830)
+        d = torch.from_numpy(ph).cuda()
+        torch.cuda.synchronize()
+        g = pg.pg_build_grid(ctx, d, 200_000, [0, 0, 0], [1, 1, 1], 8, 0, 500)
+        ctx.sync()
+        charged = b.query()[0]
+        gbytes = g.info(pg.PG_INFO_BYTES)
+        assert charged >= gbytes > 0 and charged == ctx.bytes_in_use()
+        with torch.cuda.stream(st):
+            torch.cuda._sleep(400_000_000)  # about 0.2 s of GPU time ahead of the free
+        g.free()
+        assert b.query()[0] == charged  # the free has not run yet
+        ctx.sync()
+        assert b.query()[0] <= charged - gbytes
+        assert b.query()[0] == ctx.bytes_in_use()
+    finally:
+        b.detach(ctx)
+        ctx.destroy()
+        b.destroy()
