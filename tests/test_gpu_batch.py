@@ -1,14 +1,16 @@
 """Scene batches: every scene of a batched call matches the same scene alone.
 
-The single-scene path is checked against the oracle elsewhere; here each
-scene's grid, histograms, BF16 maps and guided samples inside a batch are
-compared bit for bit with the scene processed on its own.
+Each scene's grid, histograms, BF16 maps and guided samples inside a batch
+are compared bit for bit with the scene processed on its own, and two of the
+scenes inside the batch are compared with the FP64 oracle directly (grid,
+histograms and sampling bit for bit, pdfs within the FP32 bound).
 """
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import oracle as O  # noqa: E402
 from paper_2010_01775_gb300 import pg, synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -132,6 +134,92 @@ def test_batched_grid_hist_maps_and_samples_match_single_scenes(ctx):
     lb = gb.export(pg.PG_GRID_SCENE_LEAF_BEGIN, np.uint32, S + 1)
     assert lb.tolist() == scene_leaf0 + [leaf0]
     assert B["A"] == act0
+
+
+def test_batched_scenes_against_the_oracle(ctx):
+    """Scenes 0 and 3 of the batch (20,000 and 9,001 photons, different
+    domains) against the oracle run on each scene alone: the scene's leaves,
+    permutation and leaf assignment, all four histogram planes, and the guided
+    samples and pdf evaluations of the scene's queries on the batch's own
+    maps (bins identical for >= 1 - 1e-4 of the queries, FP32 pdfs within
+    1e-5 relative)."""
+    sizes, los, his, phs = _scenes()
+    S = len(sizes)
+    begin = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
+    n = int(begin[-1])
+    d_all = torch.from_numpy(np.ascontiguousarray(np.concatenate(phs))).cuda()
+    gb = pg.pg_build_grid_batched(ctx, d_all, n, begin, los, his, D, 0, THR)
+    SL = gb.info(pg.PG_INFO_SCENE_LEVELS)
+    B = pg.export_grid(gb)
+    n_prev = np.array([sz // 2 for sz in sizes], np.uint32)
+    hb = pg.pg_splat_photons_batched(ctx, gb, d_all, n, n_prev, H, W)
+    HB = pg.export_hist(hb)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_TINY3, (16,), 602))
+    mb = pg.pg_reconstruct(ctx, hb, net, pg.PG_BF16)
+    tb = pg.pg_build_cdf(ctx, mb)
+    YB = pg.export_map(mb).astype(np.float64)
+    qs = [3000, 0, 0, 2000, 0]
+    qbeg = np.concatenate([[0], np.cumsum(qs)]).astype(np.uint32)
+    pos = []
+    for s_, q in enumerate(qs):
+        p = synth.query_positions(q, 710 + s_)
+        lo, hi = np.array(los[s_], np.float32), np.array(his[s_], np.float32)
+        pos.append((lo + p * (hi - lo)).astype(np.float32))
+    pos_all = np.ascontiguousarray(np.concatenate(pos))
+    streams = np.array([5, 6, 7, 8, 9], np.uint32)
+    Q = int(qbeg[-1])
+    dirs = torch.empty(Q, 3, device="cuda")
+    pdf = torch.empty(Q, device="cuda")
+    leaf = torch.empty(Q, dtype=torch.int32, device="cuda")
+    bins = torch.empty(Q, dtype=torch.int32, device="cuda")
+    d_pos = torch.from_numpy(pos_all).cuda()
+    pg.pg_sample_dirs_batched(ctx, gb, tb, d_pos, qbeg, Q, 77, streams, dirs, pdf, leaf, bins)
+    ev_dirs = np.ascontiguousarray(np.concatenate([synth.query_directions(q, 720 + s_) for s_, q in enumerate(qs)]))
+    ev = torch.empty(Q, device="cuda")
+    pg.pg_eval_pdf_batched(ctx, gb, tb, d_pos, torch.from_numpy(ev_dirs).cuda(), qbeg, Q, ev)
+    ctx.sync()
+    dirs, pdf, leaf, bins, ev = (dirs.cpu().numpy(), pdf.cpu().numpy(), leaf.cpu().numpy().view(np.uint32),
+                                 bins.cpu().numpy().view(np.uint32), ev.cpu().numpy().astype(np.float64))
+    shift = np.uint64(3 * D)
+    scene_of_leaf = (B["leaf_code"] >> shift).astype(np.int64)
+    active = np.zeros(B["L"], bool)
+    active[B["active"]] = True
+    for s_ in (0, 3):
+        ref = O.build_grid(phs[s_], los[s_], his[s_], D, 0, THR)
+        leaf0 = int(np.argmax(scene_of_leaf == s_))
+        L = ref["L"]
+        sel = slice(leaf0, leaf0 + L)
+        assert np.all(scene_of_leaf[sel] == s_)
+        assert np.array_equal(B["leaf_code"][sel] & np.uint64((1 << (3 * D)) - 1), ref["leaf_code"])
+        assert np.array_equal(B["leaf_depth"][sel] - SL, ref["leaf_depth"])
+        assert np.array_equal(B["leaf_begin"][sel] - begin[s_], ref["leaf_begin"])
+        assert np.array_equal(B["leaf_end"][sel] - begin[s_], ref["leaf_end"])
+        assert np.array_equal(B["perm"][begin[s_]:begin[s_ + 1]] - begin[s_], ref["perm"])
+        assert np.array_equal(B["leaf_of"][begin[s_]:begin[s_ + 1]] - leaf0, ref["leaf_of"])
+        act, slot = O.active_leaves(ref)
+        act0 = int(active[:leaf0].sum())
+        A = act.size
+        assert np.array_equal(np.nonzero(active[sel])[0], act)
+        h = O.hist_for_active(O.splat(phs[s_], ref, int(n_prev[s_]), H, W), act)
+        for k in ("pow_cur", "cnt_cur", "pow_prev", "cnt_prev"):
+            assert np.array_equal(HB[k][act0:act0 + A], h[k]), (s_, k)
+        # Sampling and evaluation of the scene's queries on the batch's maps.
+        tabs = O.tables_from_map(YB[act0:act0 + A])
+        r = slice(qbeg[s_], qbeg[s_ + 1])
+        o = O.sample(ref, slot, tabs, pos[s_], 77, int(streams[s_]))
+        lb = leaf[r]
+        assert np.array_equal(lb >> 31, o["leaf"] >> 31)
+        assert np.array_equal((lb & 0x7FFFFFFF) - leaf0, o["leaf"] & 0x7FFFFFFF)
+        same = bins[r] == o["bin"]
+        assert same.mean() >= 1 - 1e-4
+        nz = same & (o["pdf"] > 0)
+        assert np.max(np.abs(pdf[r][nz] - o["pdf"][nz]) / o["pdf"][nz], initial=0) <= 1e-5
+        e = O.eval_pdf(ref, slot, tabs, pos[s_], ev_dirs[r])
+        nz = e > 0
+        assert np.all(ev[r][~nz] == 0)
+        assert np.max(np.abs(ev[r][nz] - e[nz]) / e[nz], initial=0) <= 1e-5
+    for hd in (tb, mb, hb, gb, net):
+        hd.free()
 
 
 def test_batched_argument_checks(ctx):
