@@ -142,7 +142,7 @@ def test_batched_scenes_against_the_oracle(ctx):
     permutation and leaf assignment, all four histogram planes, and the guided
     samples and pdf evaluations of the scene's queries on the batch's own
     maps (bins identical for >= 1 - 1e-4 of the queries, FP32 pdfs within
-    1e-5 relative)."""
+    1e-5 relative above FP32's normal range)."""
     sizes, los, his, phs = _scenes()
     S = len(sizes)
     begin = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint32)
@@ -212,12 +212,13 @@ def test_batched_scenes_against_the_oracle(ctx):
         assert np.array_equal((lb & 0x7FFFFFFF) - leaf0, o["leaf"] & 0x7FFFFFFF)
         same = bins[r] == o["bin"]
         assert same.mean() >= 1 - 1e-4
+        # FP32 pdfs within 1e-5 relative; maps of this random net reach P below
+        # FP32's normal range (1.2e-38) on some bins, where an FP32 value keeps
+        # only its absolute spacing, hence the 1e-35 floor (HW / 4 pi = 81.5).
         nz = same & (o["pdf"] > 0)
-        assert np.max(np.abs(pdf[r][nz] - o["pdf"][nz]) / o["pdf"][nz], initial=0) <= 1e-5
+        assert np.all(np.abs(pdf[r][nz] - o["pdf"][nz]) <= 1e-5 * o["pdf"][nz] + 1e-35)
         e = O.eval_pdf(ref, slot, tabs, pos[s_], ev_dirs[r])
-        nz = e > 0
-        assert np.all(ev[r][~nz] == 0)
-        assert np.max(np.abs(ev[r][nz] - e[nz]) / e[nz], initial=0) <= 1e-5
+        assert np.all(np.abs(ev[r] - e) <= 1e-5 * e + 1e-35)
     for hd in (tb, mb, hb, gb, net):
         hd.free()
 
