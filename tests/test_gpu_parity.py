@@ -6,6 +6,8 @@ within the tolerances derived in each test.
 """
 import math
 
+import os
+
 import numpy as np
 import pytest
 
@@ -357,7 +359,9 @@ def _kl_l1(P, Pr):
 
 
 def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_leaves=16, return_inputs=False,
-             tune=False):
+             tune=False, force=None):
+    """force: a PG_TC_FORCE launch shape for every tensor-core layer that
+    supports it (e.g. "3", the tap-stacked operand mode)."""
     ph = synth.photons(n, blobs, seed)
     d = torch.from_numpy(ph).cuda()
     g = pg.pg_build_grid(ctx, d, n, LO, HI, D, 0, thr)
@@ -366,7 +370,13 @@ def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_le
     net = pg.pg_net_load(ctx, blob)
     if tune:
         pg.pg_autotune(ctx, h, net, prec)  # the reconstruction below uses the tuned launch shapes
-    m = pg.pg_reconstruct(ctx, h, net, prec)
+    if force is not None:
+        os.environ["PG_TC_FORCE"] = force
+    try:
+        m = pg.pg_reconstruct(ctx, h, net, prec)
+        ctx.sync()
+    finally:
+        os.environ.pop("PG_TC_FORCE", None)
     t = pg.pg_build_cdf(ctx, m)
     tt = pg.export_tables(t)
     ctx.sync()
@@ -386,18 +396,21 @@ def _lp_case(ctx, n, blobs, D, thr, H, W, arch, widths, seed, prec, max_check_le
 
 @pytest.mark.parametrize("arch,widths,H,W,n,D,thr", [
     (synth.ARCH_TINY3, (16,), 32, 32, 100_000, 4, 1000),
+    (synth.ARCH_TINY3, (32,), 64, 64, 100_000, 4, 1000),
     (synth.ARCH_UNET4, (32, 64, 128, 256), 64, 64, 40_000, 5, 2000),
     (synth.ARCH_UNET4, (32, 64, 128, 256), 32, 32, 20_000, 4, 1500),
     (synth.ARCH_UNET4, (16, 32, 64, 128), 128, 128, 8_000, 3, 3000),
+    (synth.ARCH_UNET4, (32, 64, 128, 256), 128, 128, 8_000, 3, 3000),  # the precision workload's net and maps
 ])
 def test_cnn_bf16_kl(ctx, arch, widths, H, W, n, D, thr):
     """BF16 tensor-core network: mean KL(P_oracle || P) <= 1e-3 over leaves,
     with the default launch shapes and with autotuned ones."""
-    for tune in (False, True):
-        P, Pr, valid = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 70 + H, pg.PG_BF16, tune=tune)
+    for tune, force in ((False, None), (True, None)):
+        P, Pr, valid = _lp_case(ctx, n, 6, D, thr, H, W, arch, widths, 70 + H, pg.PG_BF16, tune=tune, force=force)
         assert np.all(valid == 1)
         kl, l1 = _kl_l1(P, Pr)
-        print(f"bf16 tune={tune} {arch} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; L1 mean {l1.mean():.2e}")
+        print(f"bf16 tune={tune} force={force} {arch} {widths} {H}x{W}: KL mean {kl.mean():.2e} max {kl.max():.2e}; "
+              f"L1 mean {l1.mean():.2e}")
         assert kl.mean() <= 1e-3
         assert np.all(np.isfinite(kl))
 
