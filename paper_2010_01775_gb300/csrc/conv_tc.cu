@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int cw = (a.BN % 32 == 0 && a.mt * a.BN >= 64) ? 32 : 16;  // columns per work item
     const int per_sub = a.BN / cw, items = a.mt * per_sub;
     float amax_local = 0.0f;
-    long long epi_wait = 0, epi_ld = 0, epi_cvt = 0, epi_st = 0;
+    long long epi_wait = 0;
     const long long epi_t0 = clock64();
     for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x, ++i) {
       const int buf = i & 1;
@@ -713,11 +713,9 @@ __global__ void __launch_bounds__(kThreads, 2)
           (a.res && valid) ? (const __nv_bfloat16 *)a.res + opix * a.res_cs + a.res_co + c : nullptr;
       uint4 chunk[4];
       int cpp;
-      long long p0 = a.stats ? clock64() : 0, p1 = 0, p2 = 0;
       if (cw == 32) {
         uint32_t r[32];
         tmem_ld32(trow, r);
-        if (a.stats) p1 = clock64();
         epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk, ps, resp);
         epi_convert16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, amax_local, chunk + (kFp8Out ? 1 : 2), ps,
                                        resp ? resp + 16 : nullptr);
@@ -725,20 +723,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else {
         uint32_t r[16];
         tmem_ld16(trow, r);
-        if (a.stats) p1 = clock64();
         epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk, ps, resp);
         cpp = kFp8Out ? 1 : 2;
       }
-      if (a.stats) p2 = clock64();
       if (a.stage_out)
         store_staged(a, s_stage + (warp - 2) * 2048, chunk, cpp, c, pix0, valid, Wo, reps, lane, kFp8Out ? 1 : 2);
       else if (valid)
         store_direct(a, chunk, cpp, c, pix0, Wo, reps, kFp8Out ? 1 : 2);
-      if (a.stats) {
-        epi_ld += p1 - p0;
-        epi_cvt += p2 - p1;
-        epi_st += clock64() - p2;
-      }
       }  // work items
       tc_fence_before();
       __syncwarp();
@@ -748,9 +739,6 @@ __global__ void __launch_bounds__(kThreads, 2)
       atomicAdd(&a.stats[5], (unsigned long long)epi_wait);
       atomicAdd(&a.stats[6], (unsigned long long)(clock64() - epi_t0));
       atomicAdd(&a.stats[7], (unsigned long long)i);
-      atomicAdd(&a.stats[8], (unsigned long long)epi_ld);
-      atomicAdd(&a.stats[9], (unsigned long long)epi_cvt);
-      atomicAdd(&a.stats[10], (unsigned long long)epi_st);
     }
     if (kCalib) {
 #pragma unroll
@@ -1016,8 +1004,8 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   static unsigned long long *d_stats = nullptr;
   const bool want_stats = getenv("PG_TC_STATS") != nullptr;
   if (want_stats) {
-    if (!d_stats) PG_CUDA(cudaMalloc(&d_stats, 12 * sizeof(unsigned long long)));
-    PG_CUDA(cudaMemsetAsync(d_stats, 0, 12 * sizeof(unsigned long long), st));
+    if (!d_stats) PG_CUDA(cudaMalloc(&d_stats, 8 * sizeof(unsigned long long)));
+    PG_CUDA(cudaMemsetAsync(d_stats, 0, 8 * sizeof(unsigned long long), st));
     a.stats = d_stats;
   }
 
@@ -1065,17 +1053,15 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     k_conv_tc<false, false><<<grid, kThreads, smem, st>>>(mA, mB, a);
   }
   if (want_stats) {
-    unsigned long long h[12];
+    unsigned long long h[8];
     PG_CUDA(cudaMemcpyAsync(h, d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
     PG_CUDA(cudaStreamSynchronize(st));
     const double g = (double)grid;
     fprintf(stderr,
             "pg_tc_stats: %dx%d cin %d cout %d halo %d cb %d mt %d ctas %d stages %d tiles %d | per CTA kcycles: "
-            "producer wait %.0f / %.0f, mma wait acc %.0f full %.0f / %.0f, epilogue wait %.0f / %.0f (tiles %.0f; "
-            "one warp's items: tmem load %.0f, convert %.0f, store %.0f)\n",
+            "producer wait %.0f / %.0f, mma wait acc %.0f full %.0f / %.0f, epilogue wait %.0f / %.0f (tiles %.0f)\n",
             L.Hin, L.Win, L.Cin, L.Cout, a.halo, cb, a.mt, per_sm, a.stages, a.num_tiles, h[0] / g / 1e3,
-            h[1] / g / 1e3, h[2] / g / 1e3, h[3] / g / 1e3, h[4] / g / 1e3, h[5] / g / 1e3, h[6] / g / 1e3, h[7] / g,
-            h[8] / g / 1e3, h[9] / g / 1e3, h[10] / g / 1e3);
+            h[1] / g / 1e3, h[2] / g / 1e3, h[3] / g / 1e3, h[4] / g / 1e3, h[5] / g / 1e3, h[6] / g / 1e3, h[7] / g);
   }
   PG_CUDA(cudaGetLastError());
   return PG_OK;
