@@ -7,7 +7,8 @@
 // last bin, uniform for an empty row).  Warp 0 then scans the row sums into
 // the marginal CDF, and all threads write P = y / sum y.  Sequential sums in
 // each lane keep the pair arithmetic below to about a third of what a
-// 32-lane scan per row costs.
+// 32-lane scan per row costs.  Every 8th CDF entry is also written to a
+// segment summary that the samplers search first.
 //
 // Sums, prefixes and quotients carry ~48 significant bits without FP64:
 // each value is an unevaluated pair (hi, lo) of FP32 numbers combined with
@@ -105,7 +106,7 @@ __device__ __forceinline__ void store_seg(float *__restrict__ p, const float (&v
 
 // Warp 0: the marginal CDF over the row sums and the map total.
 __device__ __forceinline__ void marginal_cdf(int H, const float *mrow_hi, const float *mrow_lo, float *__restrict__ cz,
-                                             uint8_t *__restrict__ valid, df *s_total) {
+                                             float *__restrict__ sz, uint8_t *__restrict__ valid, df *s_total) {
   const int lane = threadIdx.x & 31;
   const int EH = (H + 31) >> 5;
   df pref[8], run = {0.0f, 0.0f};
@@ -122,9 +123,11 @@ __device__ __forceinline__ void marginal_cdf(int H, const float *mrow_hi, const 
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     int i = lane * EH + e;
-    if (e < EH && i < H)
-      cz[(size_t)blockIdx.x * H + i] =
-          i == H - 1 ? 1.0f : (total.hi > 0.0f ? df_div_to_f32(df_add(off, pref[e]), total) : 0.0f);
+    if (e < EH && i < H) {
+      const float f = i == H - 1 ? 1.0f : (total.hi > 0.0f ? df_div_to_f32(df_add(off, pref[e]), total) : 0.0f);
+      cz[(size_t)blockIdx.x * H + i] = f;
+      if (sz && (i & 7) == 7) sz[(size_t)blockIdx.x * (H >> 3) + (i >> 3)] = f;  // segment summary
+    }
   }
   if (lane == 0) {
     *s_total = total;
@@ -139,9 +142,12 @@ __device__ __forceinline__ void marginal_cdf(int H, const float *mrow_hi, const 
 // offset and the row sum, and a second sweep of its bins forms the prefixes.
 // When the map fits one pass the bins stay in registers for P = y / sum y;
 // taller maps re-read them.
+// With W >= 16 (N = 16) every lane also writes entries 7 and 15 of its
+// segment to the row's segment summary (sphi); sz likewise for the marginal.
 template <int N, int T>
 __global__ void __launch_bounds__(256) k_cdf(const float *__restrict__ y, int H, int W, float *__restrict__ P,
                                              float *__restrict__ cphi, float *__restrict__ cz,
+                                             float *__restrict__ sphi, float *__restrict__ sz,
                                              uint8_t *__restrict__ valid) {
   constexpr int RP = 256 / T;
   __shared__ float mrow_hi[256], mrow_lo[256];
@@ -190,9 +196,13 @@ __global__ void __launch_bounds__(256) k_cdf(const float *__restrict__ y, int H,
       for (int e = 0; e < N; ++e) out[e] = (float)(q * N + e + 1) / (float)W;
     }
     store_seg<N>(cphi + o, out);
+    if constexpr (N == 16) {
+      if (sphi)
+        *reinterpret_cast<float2 *>(sphi + ((size_t)blockIdx.x * H + i) * (W >> 3) + 2 * q) = make_float2(out[7], out[15]);
+    }
   }
   __syncthreads();
-  if (tid < 32) marginal_cdf(H, mrow_hi, mrow_lo, cz, valid, &s_total);
+  if (tid < 32) marginal_cdf(H, mrow_hi, mrow_lo, cz, sz, valid, &s_total);
   __syncthreads();
   const df total = s_total;
   const float inv = total.hi > 0.0f ? df_div_to_f32(df{1.0f, 0.0f}, total) : 0.0f;
@@ -219,7 +229,10 @@ pg_status build_cdf(pg_ctx *ctx, const Map *m, Tables *t) {
   cudaStream_t st = ctx->stream;
   switch (m->W) {
 #define PG_CDF_CASE(Wc, Nc, Tc) \
-  case Wc: k_cdf<Nc, Tc><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->valid), PG_COUNT(ctx); break;
+  case Wc:                                                                                                          \
+    k_cdf<Nc, Tc><<<A, 256, 0, st>>>(m->y, m->H, m->W, t->P, t->cdf_phi, t->cdf_z, t->sum_phi, t->sum_z, t->valid), \
+        PG_COUNT(ctx);                                                                                             \
+    break;
     PG_CDF_CASE(4, 4, 1)
     PG_CDF_CASE(8, 8, 1)
     PG_CDF_CASE(16, 16, 1)

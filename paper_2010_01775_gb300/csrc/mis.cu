@@ -19,17 +19,6 @@ namespace {
 
 constexpr float kPi = 3.14159265358979323846f;
 
-// First index i in [0, n) with u < F[i] (F ascends, F[n-1] = 1 > u).
-__device__ __forceinline__ int mis_first_above(const float *__restrict__ F, int n, float u) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (u < __ldg(F + mid)) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
-
 // Tangent frame of a unit normal (Duff, Burgess, Christensen, Hery, Kensler,
 // Liani, Villemin, "Building an Orthonormal Basis, Revisited", JCGT 2017).
 __device__ __forceinline__ void tangent_frame(float nx, float ny, float nz, float3 &b1, float3 &b2) {
@@ -48,6 +37,7 @@ struct MisTab {
   int lut_shift;
   const int32_t *slot_of_leaf;
   const float *P, *Fphi, *Fz, *phi_tab;
+  const float *Sphi, *Sz;  // segment summaries of the CDFs (null for rows under 16 bins)
   const uint8_t *valid;
   const float *alpha;
   int H, W;
@@ -145,9 +135,10 @@ __global__ void k_mis_sample(const float *__restrict__ pos, const float *__restr
     const uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), stream, 0u), key);
     const float u0 = (float)(r.x >> 8) * k24, u1 = (float)(r.y >> 8) * k24;
     const float u2 = (float)(r.z >> 8) * k24, u3 = (float)(r.w >> 8) * k24;
-    const size_t HW = (size_t)tb.H * tb.W;
-    const int i = mis_first_above(tb.Fz + (size_t)s * tb.H, tb.H, u0);
-    const int j = mis_first_above(tb.Fphi + (size_t)s * HW + (size_t)i * tb.W, tb.W, u1);
+    const int i = first_above_seg(tb.Fz + (size_t)s * tb.H, tb.Sz ? tb.Sz + (size_t)s * (tb.H >> 3) : nullptr,
+                                  tb.H, u0);
+    const size_t row = (size_t)s * tb.H + i;
+    const int j = first_above_seg(tb.Fphi + row * tb.W, tb.Sphi ? tb.Sphi + row * (tb.W >> 3) : nullptr, tb.W, u1);
     const float z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
     const float ph = ((float)j + u3) * (2.0f * kPi / (float)tb.W);
     const float stz = sqrtf(fmaxf(0.0f, 1.0f - z * z));
@@ -202,6 +193,8 @@ MisTab make_mis_tab(const Grid *g, const Tables *t, const Mis *m, const float *p
   tb.P = t ? t->P : nullptr;
   tb.Fphi = t ? t->cdf_phi : nullptr;
   tb.Fz = t ? t->cdf_z : nullptr;
+  tb.Sphi = t ? t->sum_phi : nullptr;
+  tb.Sz = t ? t->sum_z : nullptr;
   tb.valid = t ? t->valid : nullptr;
   tb.phi_tab = phi_tab;
   tb.alpha = m->alpha;

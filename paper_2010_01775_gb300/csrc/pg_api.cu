@@ -1105,14 +1105,20 @@ pg_status pg_build_cdf(pg_ctx *c, const pg_map *map, pg_tables **out) {
   t->W = m->W;
   size_t HW = (size_t)m->H * m->W, A = m->A;
   size_t bP = (A * HW * 4 + 255) & ~(size_t)255, bz = (A * m->H * 4 + 255) & ~(size_t)255;
-  t->h.bytes = 2 * bP + bz + ((A + 255) & ~(size_t)255);
+  // Segment summaries (every 8th CDF entry) for rows of 16 or more bins.
+  size_t bsp = m->W >= 16 ? (A * HW / 8 * 4 + 255) & ~(size_t)255 : 0;
+  size_t bsz = m->H >= 16 ? (A * m->H / 8 * 4 + 255) & ~(size_t)255 : 0;
+  size_t bv = (A + 255) & ~(size_t)255;
+  t->h.bytes = 2 * bP + bz + bsp + bsz + bv;
   pg_status s = ctx_alloc(c, t->h.bytes, &t->block);
   if (s != PG_OK) { delete t; return s; }
   uint8_t *p = (uint8_t *)t->block;
   t->P = (float *)p;
   t->cdf_phi = (float *)(p + bP);
   t->cdf_z = (float *)(p + 2 * bP);
-  t->valid = p + 2 * bP + bz;
+  t->sum_phi = bsp ? (float *)(p + 2 * bP + bz) : nullptr;
+  t->sum_z = bsz ? (float *)(p + 2 * bP + bz + bsp) : nullptr;
+  t->valid = p + 2 * bP + bz + bsp + bsz;
   s = build_cdf(c, m, t);
   if (s != PG_OK) { pg_free(t); return s; }
   *out = (pg_tables *)t;

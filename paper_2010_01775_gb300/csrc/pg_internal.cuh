@@ -144,8 +144,44 @@ struct Tables {
   float *cdf_phi;  // [A][HW]
   float *cdf_z;    // [A][H]
   uint8_t *valid;  // [A]
+  // Segment summaries for the samplers' search: every 8th entry of each
+  // CDF (F[8k + 7]); null for rows shorter than 16.
+  float *sum_phi;  // [A][H][W/8]
+  float *sum_z;    // [A][H/8]
   void *block;
 };
+
+// First index i in [0, n) with u < F[i] for an ascending F with F[n-1] = 1 > u
+// (n a power of two, F 16-byte aligned): the number of entries <= u.  With
+// n >= 16, S holds F[8k + 7] for k < n/8 (S 8-byte aligned, 16-byte from n =
+// 32): counting over S picks the 8-entry segment, counting over the segment
+// picks the entry -- two rounds of independent vector loads (one 32-byte
+// sector each for n <= 64) in place of log2(n) dependent probes.  Any
+// correct search of a monotone table gives this index.
+__device__ __forceinline__ int cdf_count4(float4 v, float u) {
+  return (v.x <= u) + (v.y <= u) + (v.z <= u) + (v.w <= u);
+}
+
+__device__ __forceinline__ int first_above_seg(const float *__restrict__ F, const float *__restrict__ S, int n,
+                                               float u) {
+  if (n <= 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(F));
+    return min(cdf_count4(v, u), n - 1);  // entries past n (n < 4) are never read as answers
+  }
+  int k = 0;
+  if (n >= 16) {
+    const int ns = n >> 3;
+    if (ns == 2) {
+      const float2 v = __ldg(reinterpret_cast<const float2 *>(S));
+      k = (v.x <= u) + (v.y <= u);
+    } else {
+      for (int b = 0; b < ns; b += 4) k += cdf_count4(__ldg(reinterpret_cast<const float4 *>(S + b)), u);
+    }
+  }
+  const float *seg = F + 8 * k;
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(seg)), b = __ldg(reinterpret_cast<const float4 *>(seg + 4));
+  return 8 * k + cdf_count4(a, u) + cdf_count4(b, u);
+}
 
 // One-sample MIS state per leaf of a grid (Sec. 7.3): accumulated bounce
 // contributions and counts by the strategy that sampled them, and the BSDF

@@ -4,7 +4,9 @@
 // One thread per query: voxel location (the a1 rule), binary search of the
 // leaf start codes (or, for a grid of the paper's form, a walk down the
 // voxel's binary tree), Philox4x32-10 uniforms, then an inverse-CDF search of the
-// marginal (rows) and the conditional (columns) tables; the direction is
+// marginal (rows) and the conditional (columns) tables, each in two rounds
+// (the 8-entry segment from the table's segment summary, then the entry
+// within it); the direction is
 // uniform in (z, phi) inside the chosen bin, i.e. uniform in solid angle on
 // the equal-area cylindrical map, and its pdf is P_ij * HW / (4 pi).
 #include "pg_internal.cuh"
@@ -13,17 +15,6 @@ namespace pgi {
 
 namespace {
 
-// First index i in [0, n) with u < F[i]; F ascends and F[n-1] = 1 > u.
-__device__ __forceinline__ int first_above(const float *__restrict__ F, int n, float u) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (u < __ldg(F + mid)) hi = mid;
-    else lo = mid + 1;
-  }
-  return lo;
-}
-
 struct Tab {
   const uint64_t *leaf_code;
   const uint32_t *lut;
@@ -31,6 +22,7 @@ struct Tab {
   int lut_shift;
   const int32_t *slot_of_leaf;
   const float *P, *Fphi, *Fz;
+  const float *Sphi, *Sz;  // segment summaries (null for rows under 16 bins)
   const uint8_t *valid;
   uint32_t L;
   int H, W;
@@ -103,8 +95,10 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc,
     bo = 0xFFFFFFFFu;
   } else {
     const size_t HW = (size_t)tb.H * tb.W;
-    int i = first_above(tb.Fz + (size_t)s * tb.H, tb.H, u0);
-    int j = first_above(tb.Fphi + (size_t)s * HW + (size_t)i * tb.W, tb.W, u1);
+    const int i = first_above_seg(tb.Fz + (size_t)s * tb.H, tb.Sz ? tb.Sz + (size_t)s * (tb.H >> 3) : nullptr,
+                                  tb.H, u0);
+    const size_t row = (size_t)s * tb.H + i;
+    const int j = first_above_seg(tb.Fphi + row * tb.W, tb.Sphi ? tb.Sphi + row * (tb.W >> 3) : nullptr, tb.W, u1);
     z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
     phi = ((float)j + u3) * (6.2831853071795865f / (float)tb.W);
     p = __ldg(tb.P + (size_t)s * HW + (size_t)i * tb.W + j) * tb.pdf_scale;
@@ -173,6 +167,8 @@ Tab make_tab(const Grid *g, const Tables *t) {
   tb.P = t->P;
   tb.Fphi = t->cdf_phi;
   tb.Fz = t->cdf_z;
+  tb.Sphi = t->sum_phi;
+  tb.Sz = t->sum_z;
   tb.valid = t->valid;
   tb.L = g->L;
   tb.H = t->H;
