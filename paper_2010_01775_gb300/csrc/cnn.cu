@@ -463,11 +463,23 @@ pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_preci
   const size_t x0_per_leaf = packed ? 0 : 8 * (size_t)HW * 4;
   const size_t per_leaf = x0_per_leaf + (prec == PG_FP32 ? act_floats_per_leaf(net, H, W) * 4
                                                          : tc_bytes_per_leaf(net, prec, H, W));
-  // Activation working set: leaves are processed in chunks of at most ~6 GB.
-  uint32_t chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(A, (6ull << 30) / per_leaf));
-  size_t bytes = per_leaf * chunk + 4096;
-  void *scratch;
-  PG_TRY(ctx_alloc(ctx, bytes, &scratch));
+  // Activation working set: leaves are processed in chunks.  The
+  // tensor-core forms take up to 16 GB at once (fewer, larger launches;
+  // their indexing is 64-bit throughout), falling back to smaller chunks
+  // when the budget or the device refuses; the FP32 and paper-style paths
+  // keep 6 GB chunks (their element offsets stay below 2^31).
+  const bool big = prec != PG_FP32 && net->arch != 2;
+  uint32_t chunk = 0;
+  size_t bytes = 0;
+  void *scratch = nullptr;
+  pg_status as = PG_ERR_OOM;
+  for (size_t limit : {big ? (16ull << 30) : (6ull << 30), 6ull << 30, 2ull << 30, 512ull << 20}) {
+    chunk = (uint32_t)std::max<size_t>(1, std::min<size_t>(A, limit / per_leaf));
+    bytes = per_leaf * chunk + 4096;
+    as = ctx_alloc(ctx, bytes, &scratch);
+    if (as != PG_ERR_OOM || chunk == 1) break;
+  }
+  PG_TRY(as);
   struct Guard {
     pg_ctx *c; void *p; size_t b;
     ~Guard() { ctx_free(c, p, b); }

@@ -123,9 +123,9 @@ __global__ void k_mis_sample(const float *__restrict__ pos, const float *__restr
   if (v0 < a) {
     float3 b1, b2;
     tangent_frame(nx, ny, nz, b1, b2);
-    const float r = sqrtf(v1), phi = 2.0f * kPi * v2, lz = sqrtf(fmaxf(0.0f, 1.0f - v1));
+    const float r = sqrtf(v1), phi = 2.0f * v2, lz = sqrtf(fmaxf(0.0f, 1.0f - v1));  // angle pi * phi
     float sn, cs;
-    sincosf(phi, &sn, &cs);
+    sincospif(phi, &sn, &cs);
     const float lx = r * cs, ly = r * sn;
     dx = b1.x * lx + b2.x * ly + nx * lz;
     dy = b1.y * lx + b2.y * ly + ny * lz;
@@ -140,10 +140,10 @@ __global__ void k_mis_sample(const float *__restrict__ pos, const float *__restr
     const size_t row = (size_t)s * tb.H + i;
     const int j = first_above_seg(tb.Fphi + row * tb.W, tb.Sphi ? tb.Sphi + row * (tb.W >> 3) : nullptr, tb.W, u1);
     const float z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
-    const float ph = ((float)j + u3) * (2.0f * kPi / (float)tb.W);
+    const float ph = ((float)j + u3) * (2.0f / (float)tb.W);  // angle pi * ph
     const float stz = sqrtf(fmaxf(0.0f, 1.0f - z * z));
     float sn, cs;
-    sincosf(ph, &sn, &cs);
+    sincospif(ph, &sn, &cs);
     dx = stz * cs;
     dy = stz * sn;
     dz = z;

@@ -391,17 +391,32 @@ __device__ __forceinline__ bool not_clockwise_f32(float c, float s, float x, flo
 
 // The answer is the last ray of the half plane that the direction is not
 // clockwise of: the first ray always is, and the test holds up to the answer
-// and fails after it.  A guess from atan2 is checked against its own ray and
+// and fails after it.  A guess from the azimuth is checked against its own ray and
 // the next one (one round of table reads, usually the last), and walked from
 // there if either test disagrees, so any guess gives the same column.  Any
 // unsure FP32 test redoes the search with the exact FP64 test (kept out of
 // line: GB300's FP64 rate is a small fraction of FP32's).
+// Approximate azimuth of (x, y) in [0, 2 pi) for the column guess: octant
+// reduction and atan(t) ~ t / (1 + 0.28086 t^2) on [0, 1] (Rajan, Wang,
+// Inkol and Joyal, "Efficient approximations for the arctangent function",
+// IEEE Signal Processing Magazine 23(3), 2006; error under 0.005 rad).  The
+// exact ray tests below decide the column, so the guess only has to be
+// close; it costs a handful of instructions where atan2f costs dozens.
+__device__ __forceinline__ float approx_azimuth(float x, float y) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float t = __fdividef(fminf(ax, ay), fmaxf(ax, ay));
+  float a = __fdividef(t, fmaf(0.28086f, t * t, 1.0f));
+  if (ay > ax) a = 1.5707963267948966f - a;
+  if (x < 0.0f) a = 3.1415926535897932f - a;
+  if (y < 0.0f) a = 6.2831853071795865f - a;
+  return a;
+}
+
 __device__ __forceinline__ int dir_col(float x, float y, int W, const float *tab) {
   if (x == 0.0f && y == 0.0f) return 0;
   const bool upper = (y > 0.0f) || (y == 0.0f && x >= 0.0f);
   const int lo0 = upper ? 0 : (W >> 1), hi0 = lo0 + (W >> 1) - 1;
-  float phi = atan2f(y, x);
-  if (phi < 0.0f) phi += 6.2831853071795865f;
+  const float phi = approx_azimuth(x, y);
   int a = (int)(phi * ((float)W * 0.15915494309189535f));
   a = min(max(a, lo0), hi0);
   const int b = a < hi0 ? a + 1 : a;

@@ -89,7 +89,7 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc,
   uint32_t lo, bo;
   if (s < 0 || !__ldg(tb.valid + s)) {
     z = 1.0f - 2.0f * u0;
-    phi = 6.2831853071795865f * u1;
+    phi = 2.0f * u1;
     p = tb.pdf_uniform;
     lo = l | 0x80000000u;
     bo = 0xFFFFFFFFu;
@@ -100,13 +100,15 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc,
     const size_t row = (size_t)s * tb.H + i;
     const int j = first_above_seg(tb.Fphi + row * tb.W, tb.Sphi ? tb.Sphi + row * (tb.W >> 3) : nullptr, tb.W, u1);
     z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
-    phi = ((float)j + u3) * (6.2831853071795865f / (float)tb.W);
+    phi = ((float)j + u3) * (2.0f / (float)tb.W);  // in half turns: the angle is pi * phi
     p = __ldg(tb.P + (size_t)s * HW + (size_t)i * tb.W + j) * tb.pdf_scale;
     lo = l;
     bo = (uint32_t)(i * tb.W + j);
   }
+  // sin and cos of pi * phi (the argument reduction of sincospif is exact,
+  // cheaper and more accurate than reducing 2 pi-scaled radians).
   float st = sqrtf(fmaxf(0.0f, 1.0f - z * z)), sn, cs;
-  sincosf(phi, &sn, &cs);
+  sincospif(phi, &sn, &cs);
   dir[3 * t] = st * cs;
   dir[3 * t + 1] = st * sn;
   dir[3 * t + 2] = z;

@@ -4,7 +4,8 @@
 // One CTA per active leaf.  The leaf's photons are the contiguous range of
 // the sorted permutation; each thread gathers a 32-byte photon record, takes
 // its direction bin and fixed-point power and adds into a shared-memory
-// histogram (64-bit power, 32-bit count).  Photons of one warp that land in
+// histogram (64-bit power, 32-bit count); the record loads of up to three
+// photons per thread are issued together.  Photons of one warp that land in
 // the same bin are combined first (warp match), so a hot bin costs one shared
 // atomic per warp instead of one per photon.  The finished histogram is
 // written once, coalesced, with the per-leaf power totals.  Histograms up to
@@ -63,26 +64,52 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
   }
   const int tid = threadIdx.x, lane = tid & 31;
 
-  {
-    uint4 *z = reinterpret_cast<uint4 *>(smem);
-    const int n16 = (kPlanes * HW * 12) / 16;
-    for (int i = tid; i < n16; i += kSplatThreads) z[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < 2 * W; i += kSplatThreads) s_tab[i] = phi_tab[i];
-  }
-  __syncthreads();
-
+  // The leaf's photons go in batches of kU x 512: each thread first issues
+  // the permutation loads of its kU photons, then their record loads (all
+  // independent), so a batch costs two memory round trips instead of two per
+  // photon; the first batch's loads are in flight while the shared
+  // histogram is zeroed.
+  constexpr int kU = 3;
   uint32_t bad = 0;
-  for (uint32_t base = b; base < e; base += kSplatThreads) {
-    uint32_t i = base + tid;
-    bool live = i < e;
+  bool zeroed = false;
+  for (uint64_t base = b; base < e || !zeroed; base += kU * kSplatThreads) {
+    uint32_t pidx[kU];
+    bool live[kU];
+    float4 ra[kU], rb[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const uint64_t i = base + (uint64_t)(u * kSplatThreads + tid);
+      live[u] = i < e;
+      pidx[u] = live[u] ? __ldg(perm + i) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (live[u]) {
+        const float4 *r = reinterpret_cast<const float4 *>(ph + pidx[u]);
+        ra[u] = __ldg(r);
+        rb[u] = __ldg(r + 1);
+      } else {
+        ra[u] = rb[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (!zeroed) {
+      uint4 *z = reinterpret_cast<uint4 *>(smem);
+      const int n16 = (kPlanes * HW * 12) / 16;
+      for (int k = tid; k < n16; k += kSplatThreads) z[k] = make_uint4(0, 0, 0, 0);
+      for (int k = tid; k < 2 * W; k += kSplatThreads) s_tab[k] = phi_tab[k];
+      __syncthreads();
+      zeroed = true;
+      if (base >= e) break;  // no photons (not an active leaf): zeroed planes only
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+    if (base + (uint64_t)u * kSplatThreads < e) {  // skip the part of the batch past the leaf (uniform)
     int bin = -1;
     unsigned long long pfx = 0;
     bool prev = false;
-    if (live) {
-      uint32_t p = perm[i];
-      const float4 *r = reinterpret_cast<const float4 *>(ph + p);
-      float4 r0 = __ldg(r), r1 = __ldg(r + 1);
-      float dx = r0.w, dy = r1.x, dz = r1.y, power = r1.z;
+    if (live[u]) {
+      const uint32_t p = pidx[u];
+      float dx = ra[u].w, dy = rb[u].x, dz = rb[u].y, power = rb[u].z;
       int row = 0, col = 0;
       if (isfinite(dx) && isfinite(dy) && isfinite(dz)) {
         row = dir_row(dz, H);
@@ -146,6 +173,8 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
         atomicAdd(&s_cnt[bin], gsum_p_cnt);
       }
     }
+    }  // a live part of the batch
+    }  // kU photons of the batch
   }
   if (bad) atomicOr(status, bad);
   __syncthreads();
