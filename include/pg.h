@@ -228,9 +228,13 @@ pg_status pg_reconstruct(pg_ctx *ctx, const pg_hist *hist, const pg_net *net,
  * number of count_bounds (n_experts - 1 ascending uint32 values, host
  * memory) that are <= the leaf's photon count (the sum of its current count
  * plane).  A leaf's map is the one pg_reconstruct gives it with its expert's
- * net alone.  Each expert with leaves runs once over its leaves; the call
- * reads the counts back to the host (it returns after a stream
- * synchronisation).  1 <= n_experts <= 16. */
+ * net alone.  In BF16 with 2 to 8 U-Net experts (arch 1, equal layer
+ * shapes) the leaves are grouped by expert on the device and the network
+ * runs as one launch per layer over every expert's leaves, with the first
+ * net's tuned launch shapes; nothing is read back to the host.  Otherwise
+ * each expert with leaves runs once over its leaves, and the call reads the
+ * counts back to the host (it returns after a stream synchronisation).
+ * 1 <= n_experts <= 16. */
 pg_status pg_reconstruct_experts(pg_ctx *ctx, const pg_hist *hist, const pg_net *const *nets, int n_experts,
                                  const uint32_t *count_bounds, pg_precision precision, pg_map **out);
 

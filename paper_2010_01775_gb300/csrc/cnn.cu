@@ -64,6 +64,10 @@ __global__ void k_assemble_bf16(const uint64_t *__restrict__ pow_cur, const uint
   if (i >= (size_t)nslots * HW) return;
   const uint32_t pos = slot0 + (uint32_t)(i / HW);
   const uint32_t s = perm ? perm[pos] : pos;
+  if (s == 0xFFFFFFFFu) {  // a padding position of an expert group: zero input
+    out[2 * i] = out[2 * i + 1] = make_uint4(0u, 0u, 0u, 0u);
+    return;
+  }
   size_t g = (size_t)s * HW + i % HW;
   uint64_t tc = tot_cur[s], tp = tot_prev[s];
   float ic = tc ? (float)HW / __ull2float_rn(tc) : 0.0f;
@@ -431,7 +435,71 @@ __global__ void k_scatter_rows(const float *__restrict__ yp, const uint32_t *__r
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)A * HW / 4) return;
   const size_t k = (4 * i) / HW, c = (4 * i) % HW;
-  *reinterpret_cast<float4 *>(y + (size_t)perm[k] * HW + c) = *reinterpret_cast<const float4 *>(yp + 4 * i);
+  const uint32_t s = perm[k];
+  if (s == 0xFFFFFFFFu) return;  // padding position
+  *reinterpret_cast<float4 *>(y + (size_t)s * HW + c) = *reinterpret_cast<const float4 *>(yp + 4 * i);
+}
+
+// Leaves grouped by expert on the device (one CTA): the expert of slot k is
+// the number of count bounds <= counts[k]; expert e's positions are
+// [range[e], range[e+1]), its leaf count rounded up to a multiple of pad;
+// pos_slot[p] is the slot at position p (an expert's slots in slot order)
+// or ~0 at a padding position.
+struct ExpertBounds {
+  uint32_t b[16];
+};
+
+__global__ void __launch_bounds__(1024) k_group_experts(const uint32_t *__restrict__ counts, uint32_t A,
+                                                        ExpertBounds eb, int E, uint32_t pad, uint32_t npos,
+                                                        int *__restrict__ range, uint32_t *__restrict__ pos_slot) {
+  __shared__ uint32_t n[16], base[16], wcnt[32], wofs[32];
+  __shared__ int srange[17];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto expert = [&](uint32_t c) {
+    int e = 0;
+    while (e + 1 < E && c >= eb.b[e]) ++e;
+    return e;
+  };
+  if (tid < 16) n[tid] = base[tid] = 0u;
+  __syncthreads();
+  for (uint32_t k = tid; k < A; k += blockDim.x) atomicAdd(&n[expert(counts[k])], 1u);
+  for (uint32_t p = tid; p < npos; p += blockDim.x) pos_slot[p] = 0xFFFFFFFFu;
+  __syncthreads();
+  if (tid == 0) {
+    int r = 0;
+    for (int e = 0; e < E; ++e) {
+      srange[e] = r;
+      range[e] = r;
+      r += (int)(((n[e] + pad - 1) / pad) * pad);
+    }
+    srange[E] = r;
+    range[E] = r;
+  }
+  __syncthreads();
+  for (uint32_t c0 = 0; c0 < A; c0 += blockDim.x) {
+    const uint32_t k = c0 + tid;
+    const int ek = k < A ? expert(counts[k]) : -1;
+    for (int e = 0; e < E; ++e) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, ek == e);
+      if (lane == 0) wcnt[warp] = __popc(m);
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t v = wcnt[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+          if (lane >= o) x += y;
+        }
+        wofs[lane] = x - v;
+      }
+      __syncthreads();
+      if (ek == e) pos_slot[srange[e] + base[e] + wofs[warp] + __popc(m & ((1u << lane) - 1u))] = k;
+      __syncthreads();
+      if (tid == 0) base[e] += wofs[31] + wcnt[31];
+      __syncthreads();
+    }
+  }
 }
 
 pg_status leaf_counts(pg_ctx *ctx, const Hist *h, uint32_t *d_counts) {
@@ -447,6 +515,66 @@ pg_status scatter_rows(pg_ctx *ctx, const float *yp, const uint32_t *d_perm, uin
   k_scatter_rows<<<ceil_div(n4, 256), 256, 0, ctx->stream>>>(yp, d_perm, A, HW, y), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
   return PG_OK;
+}
+
+pg_status reconstruct_experts_grouped(pg_ctx *ctx, const Hist *h, const Net *const *nets, int E,
+                                     const uint32_t *count_bounds, float *y) {
+  const uint32_t A = h->A;
+  if (A == 0) return PG_OK;
+  if (E < 2 || E > 16 || E > tc_max_experts()) return PG_ERR_UNSUPPORTED;
+  for (int e = 0; e < E; ++e)
+    if (nets[e]->arch != 1 || nets[e]->n_layers != nets[0]->n_layers) return PG_ERR_UNSUPPORTED;
+  const int H = h->H, W = h->W, HW = H * W;
+  // No tile may span two experts: the coarsest level's maps hold HW / 64
+  // pixels, and a tile at most 256.
+  const uint32_t pad = (uint32_t)std::max(1, (256 * 64) / HW);
+  const uint32_t npos = A + (uint32_t)E * (pad - 1);
+  ExpertBounds eb;
+  memset(&eb, 0, sizeof(eb));
+  for (int e = 0; e + 1 < E; ++e) eb.b[e] = count_bounds[e];
+  const size_t b_cnt = align256(4ull * A), b_rng = align256(4ull * (E + 1)), b_pos = align256(4ull * npos);
+  const size_t b_y = align256((size_t)npos * HW * 4);
+  const size_t gbytes = b_cnt + b_rng + b_pos + b_y;
+  void *gblock;
+  PG_TRY(ctx_alloc(ctx, gbytes, &gblock));
+  struct Guard {
+    pg_ctx *c; void *p; size_t b;
+    ~Guard() { ctx_free(c, p, b); }
+  } gguard{ctx, gblock, gbytes};
+  uint8_t *q = (uint8_t *)gblock;
+  uint32_t *d_cnt = (uint32_t *)q; q += b_cnt;
+  int *d_range = (int *)q; q += b_rng;
+  uint32_t *d_pos = (uint32_t *)q; q += b_pos;
+  float *yp = (float *)q;
+  cudaStream_t st = ctx->stream;
+  PG_TRY(leaf_counts(ctx, h, d_cnt));
+  k_group_experts<<<1, 1024, 0, st>>>(d_cnt, A, eb, E, pad, npos, d_range, d_pos), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
+  const size_t per_leaf = tc_bytes_per_leaf(nets[0], PG_BF16, H, W);
+  uint32_t chunk = 0;
+  size_t bytes = 0;
+  void *scratch = nullptr;
+  pg_status as = PG_ERR_OOM;
+  for (size_t limit : {16ull << 30, 6ull << 30, 2ull << 30, 512ull << 20}) {
+    chunk = (uint32_t)std::min<size_t>(npos, std::max<size_t>(pad, (limit / per_leaf) / pad * pad));
+    bytes = per_leaf * chunk + 4096;
+    as = ctx_alloc(ctx, bytes, &scratch);
+    if (as != PG_ERR_OOM || chunk == pad) break;
+  }
+  PG_TRY(as);
+  struct Guard2 {
+    pg_ctx *c; void *p; size_t b;
+    ~Guard2() { ctx_free(c, p, b); }
+  } guard{ctx, scratch, bytes};
+  for (uint32_t p0 = 0; p0 < npos; p0 += chunk) {
+    const uint32_t ns = std::min(chunk, npos - p0);
+    const size_t nx = (size_t)ns * HW;
+    k_assemble_bf16<<<ceil_div(nx, 256), 256, 0, st>>>(h->pow_cur, h->cnt_cur, h->pow_prev, h->cnt_prev, h->tot_cur,
+                                                       h->tot_prev, d_pos, p0, ns, HW, (uint4 *)scratch), PG_COUNT(ctx);
+    PG_CUDA(cudaGetLastError());
+    PG_TRY(forward_tc_experts(ctx, nets, E, d_range, (int)p0, scratch, ns, H, W, yp + (size_t)p0 * HW, st));
+  }
+  return scatter_rows(ctx, yp, d_pos, npos, HW, y);
 }
 
 pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, Map *m, bool tune) {

@@ -40,6 +40,13 @@ pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec);
 pg_status forward_tc(pg_ctx *ctx, const Net *net, pg_precision prec, const float *x0, void *act, uint32_t ns,
                      int H, int W, float *y, cudaStream_t st, bool tune = false);
 size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W);
+// BF16 U-Net mixture of experts, one launch per layer over every expert's
+// tiles: chunk positions [d_range[e] - pos0, d_range[e+1] - pos0) run expert
+// e (ranges padded so that no tile spans two experts); the packed input is
+// already assembled at the start of act.
+pg_status forward_tc_experts(pg_ctx *ctx, const Net *const *nets, int n_exp, const int *d_range, int pos0, void *act,
+                             uint32_t ns, int H, int W, float *y, cudaStream_t st);
+int tc_max_experts();
 
 // Masks and partial-convolution scales of the paper-style network (arch 2),
 // computed once per chunk from the input mask (the B channel): scale[l] is

@@ -52,6 +52,13 @@ namespace pgi {
 namespace {
 
 constexpr int kThreads = 320;  // producer warp, MMA warp, 8 epilogue warps
+constexpr int kMaxExperts = 8;  // networks of one grouped launch (mixture of experts)
+
+// The B (weight) tensor maps of a launch: one per expert network of a
+// grouped launch, [0] only otherwise.
+struct TcMapsB {
+  CUtensorMap b[kMaxExperts];
+};
 constexpr int kEpiWarps = 8;
 constexpr int kBM = 128;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
@@ -82,13 +89,18 @@ struct TcArgs {
   int out_cs, out_co, ups, act, out_fp8;
   float out_mul;   // value multiplier before the output conversion (1/scale for FP8 outputs)
   float acc_mul;   // accumulator multiplier (product of the FP8 operand scales, 1 otherwise)
-  const float *bias;
+  // Mixture of experts in one launch: tiles of leaf positions
+  // [exp_range[e], exp_range[e+1]) (chunk positions offset by pos0) take
+  // expert e's weights, bias and head; n_exp = 1 otherwise.
+  int n_exp, pos0;
+  const int *exp_range;
+  const float *bias[kMaxExperts];
   uint32_t *status;
   unsigned int *amax;  // optional: running max |output| (float bits) for FP8 calibration
   unsigned long long *stats;  // optional: per-role cycle counters (diagnostics)
   // Optional fused 1x1 head (Cout 1) + softplus: the epilogue writes the FP32
   // map y instead of the layer's activations.
-  const float *head_w, *head_b;
+  const float *head_w[kMaxExperts], *head_b[kMaxExperts];
   float *head_y;
   // Paper-style layers: taps dil apart (operand mode 0 only); per output
   // pixel partial-convolution scale (null: plain layer; 0: output act(0));
@@ -220,6 +232,15 @@ __device__ __forceinline__ void tile_origin(const TcArgs &a, int t, int &l0, int
   int r = (int)(m0 % a.HWo);
   y0 = r / a.Wout;
   x0 = r % a.Wout;
+}
+
+// Expert of the tile whose first leaf is chunk position l0 (s_range: the
+// experts' position ranges, n_exp + 1 boundaries).
+__device__ __forceinline__ int tile_expert(const TcArgs &a, const int *s_range, int l0) {
+  int e = 0;
+  const int pos = a.pos0 + l0;
+  while (e + 1 < a.n_exp && pos >= s_range[e + 1]) ++e;
+  return e;
 }
 
 // ELU for the reduced-precision forms: exp(v) - 1 through the fast exponential
@@ -391,7 +412,7 @@ __device__ __forceinline__ void issue_stage(const StageOps &o) {
 
 template <bool kFp8Out, bool kCalib>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const TcArgs a) {
+    k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcMapsB mapsB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;
@@ -403,14 +424,22 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t *drain = acc_empty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  float *s_bias = reinterpret_cast<float *>(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // BN floats
-  float *s_head = s_bias + a.BN;                                                                   // BN + 1 floats
-  uint8_t *s_stage = reinterpret_cast<uint8_t *>(((uintptr_t)(s_head + a.BN + 1) + 15) & ~(uintptr_t)15);  // 8 x 2 KB
-  for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_bias[k] = a.bias[k];
-  if (a.head_y) {
-    for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_head[k] = a.head_w[k];
-    if (threadIdx.x == 0) s_head[a.BN] = a.head_b[0];
+  // Per expert: BN bias floats, then (fused head only) BN + 1 head floats;
+  // then the experts' position ranges.
+  const int head_n = a.head_y ? a.BN + 1 : 0;
+  float *s_bias = reinterpret_cast<float *>(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // n_exp x BN
+  float *s_head = s_bias + a.n_exp * a.BN;                                                         // n_exp x head_n
+  int *s_range = reinterpret_cast<int *>(s_head + a.n_exp * head_n);                              // n_exp + 1
+  uint8_t *s_stage =
+      reinterpret_cast<uint8_t *>(((uintptr_t)(s_range + a.n_exp + 1) + 15) & ~(uintptr_t)15);  // 8 x 2 KB
+  for (int e = 0; e < a.n_exp; ++e) {
+    for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_bias[e * a.BN + k] = a.bias[e][k];
+    if (a.head_y) {
+      for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_head[e * (a.BN + 1) + k] = a.head_w[e][k];
+      if (threadIdx.x == 0) s_head[e * (a.BN + 1) + a.BN] = a.head_b[e][0];
+    }
   }
+  for (int k = threadIdx.x; k <= a.n_exp; k += blockDim.x) s_range[k] = a.n_exp > 1 ? a.exp_range[k] : 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -426,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+    for (int e = 0; e < a.n_exp; ++e) asm volatile("prefetch.tensormap [%0];" ::"l"(&mapsB.b[e]) : "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
@@ -460,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else {
         tile_origin(a, t, l0, y0, x0);
       }
+      const CUtensorMap *mapB = &mapsB.b[a.n_exp > 1 ? tile_expert(a, s_range, l0) : 0];
       for (int ki = 0; ki < a.kiters; ++ki) {
         int got = 1;
         if (lane == 0) {
@@ -480,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (lane == 0)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk, x0, y0, l0);
             else
-              tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 1) * (a.bytes_b / 9),
+              tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 1) * (a.bytes_b / 9),
                           (lane - 1) * a.Cin + cc * a.chunk, 0);
           } else if (a.halo) {
             // Three copies of the haloed input tile (rows y0-1 .. y0+Ht),
@@ -491,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 2)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a + (size_t)lane * a.bytes_ver,
                           cc * a.chunk, x0 + lane - 1, y0 - 1, l0);
             else
-              tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 3) * (a.bytes_b / 9),
+              tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 3) * (a.bytes_b / 9),
                           (lane - 3) * a.Cin + cc * a.chunk, 0);
           } else {
             int tap = ki / a.cchunks, cc = ki - tap * a.cchunks;
@@ -500,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 2)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk,
                           x0 * a.stride + kx * a.dil - a.pad, y0 * a.stride + ky * a.dil - a.pad, l0);
             else
-              tma_load_2d(&mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
+              tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
           }
         }
         ++issued;
@@ -636,6 +666,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else {
         tile_origin(a, t, l0, y0, x0);
       }
+      // The tile's expert: its bias and head.
+      const int te = a.n_exp > 1 ? tile_expert(a, s_range, l0) : 0;
+      const float *eb = s_bias + te * a.BN, *eh = s_head + te * (a.BN + 1);
       if (a.head_y) {
         // Fused head: each thread owns whole pixels (all BN channels), so
         // the two warps of a lane quarter take alternate subtiles.
@@ -667,16 +700,16 @@ __global__ void __launch_bounds__(kThreads, 2)
             tmem_ld16(trow + (uint32_t)c, r);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              float v = a.pscale ? (hps > 0.0f ? fmaf(__uint_as_float(r[j]) * a.acc_mul, hps, s_bias[c + j]) : 0.0f)
-                                 : fmaf(__uint_as_float(r[j]), a.acc_mul, s_bias[c + j]);
+              float v = a.pscale ? (hps > 0.0f ? fmaf(__uint_as_float(r[j]) * a.acc_mul, hps, eb[c + j]) : 0.0f)
+                                 : fmaf(__uint_as_float(r[j]), a.acc_mul, eb[c + j]);
               if (a.act == 1) v = elu_lp(v);
               if (hres) v += __bfloat162float(hres[c + j]);
               if (kCalib) amax_local = fmaxf(amax_local, fabsf(v));
-              hacc = fmaf(s_head[c + j], v, hacc);
+              hacc = fmaf(eh[c + j], v, hacc);
             }
           }
           if (valid) {
-            const float v = hacc + s_head[a.BN];
+            const float v = hacc + eh[a.BN];
             a.head_y[((size_t)leaf * a.Hout + y) * a.Wout + x] = fmaxf(v, 0.0f) + log1pf(__expf(-fabsf(v)));
           }
         }
@@ -716,14 +749,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (cw == 32) {
         uint32_t r[32];
         tmem_ld32(trow, r);
-        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk, ps, resp);
-        epi_convert16<kFp8Out, kCalib>(a, r + 16, s_bias, c + 16, amax_local, chunk + (kFp8Out ? 1 : 2), ps,
+        epi_convert16<kFp8Out, kCalib>(a, r, eb, c, amax_local, chunk, ps, resp);
+        epi_convert16<kFp8Out, kCalib>(a, r + 16, eb, c + 16, amax_local, chunk + (kFp8Out ? 1 : 2), ps,
                                        resp ? resp + 16 : nullptr);
         cpp = kFp8Out ? 2 : 4;
       } else {
         uint32_t r[16];
         tmem_ld16(trow, r);
-        epi_convert16<kFp8Out, kCalib>(a, r, s_bias, c, amax_local, chunk, ps, resp);
+        epi_convert16<kFp8Out, kCalib>(a, r, eb, c, amax_local, chunk, ps, resp);
         cpp = kFp8Out ? 1 : 2;
       }
       if (a.stage_out)
@@ -855,6 +888,12 @@ struct LpLayer {
   int Cout, k, stride, act;
   const void *w;  // [Cout][k*k*Cin] reduced precision, K contiguous
   const float *bias;
+  // Mixture of experts in one launch (see TcArgs): experts 1.. of the
+  // group; expert 0 is w / bias / head_w / head_b.
+  int n_exp = 1, pos0 = 0;
+  const int *exp_range = nullptr;
+  const void *w_e[kMaxExperts] = {};
+  const float *bias_e[kMaxExperts] = {}, *head_w_e[kMaxExperts] = {}, *head_b_e[kMaxExperts] = {};
   float acc_mul, out_mul;
   unsigned int *amax;
   const float *head_w = nullptr, *head_b = nullptr;  // fused 1x1 head (see TcArgs)
@@ -973,13 +1012,29 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   int per_sm = cfg.ctas > 0 ? std::min(cfg.ctas, max_ctas) : std::min(2, max_ctas);
   const size_t stage_bytes = a.bytes_a + a.bytes_b;
   a.stage_out = (cfg.so && !L.head_y) ? 1 : 0;
-  const size_t stage_smem = a.stage_out ? (size_t)kEpiWarps * 2048 : 0;
-  const size_t fixed = 1024 + 8 * 5 + 16 + 2048 + 32 + stage_smem + 1024;  // align, barriers, bias+head, staging, reserve
-  const size_t cap = kSmemPerSM / per_sm - 1024;
-  const int max_stages = (int)std::min<size_t>(24, (cap - fixed) / (stage_bytes + 16));
+  // align, barriers, per-expert bias + head and ranges, staging, reserve
+  const size_t head_n = L.head_y ? (size_t)L.Cout + 1 : 0;
+  const size_t bias_head = 4 * (size_t)L.n_exp * ((size_t)L.Cout + head_n) + 4 * (L.n_exp + 1) + 16;
+  size_t stage_smem = 0;
+  int max_stages = 0;
+  for (;;) {
+    stage_smem = a.stage_out ? (size_t)kEpiWarps * 2048 : 0;
+    const size_t fixed = 1024 + 8 * 5 + 16 + bias_head + 32 + stage_smem + 1024;
+    const size_t cap = kSmemPerSM / per_sm - 1024;
+    max_stages = cap > fixed ? (int)std::min<size_t>(24, (cap - fixed) / (stage_bytes + 16)) : 0;
+    if (max_stages >= 2) break;
+    // A shape tuned for one net may not fit beside several experts' bias
+    // and head tables: give up the staged stores, then a resident CTA.
+    if (L.n_exp > 1 && a.stage_out) {
+      a.stage_out = 0;
+    } else if (L.n_exp > 1 && per_sm > 1) {
+      --per_sm;
+    } else {
+      return PG_ERR_UNSUPPORTED;
+    }
+  }
   a.stages = cfg.stages > 0 ? std::min(cfg.stages, max_stages) : std::min(8, max_stages);
-  if (a.stages < 2) return PG_ERR_UNSUPPORTED;
-  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16 + 4 * (2 * 256 + 4) + 16 + stage_smem;
+  size_t smem = 1024 + a.stages * stage_bytes + 8 * (2 * a.stages + 5) + 16 + bias_head + 16 + stage_smem;
   smem = std::max(smem, kSmemPerSM / (per_sm + 1) + 1024);  // at most per_sm CTAs resident
   a.out = L.out;
   a.out_cs = L.out_cs;
@@ -989,11 +1044,17 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.out_fp8 = fp8_out ? 1 : 0;
   a.out_mul = L.out_mul;
   a.acc_mul = L.acc_mul;
-  a.bias = L.bias;
+  a.n_exp = L.n_exp;
+  a.pos0 = L.pos0;
+  a.exp_range = L.exp_range;
+  if (L.n_exp < 1 || L.n_exp > kMaxExperts || (L.n_exp > 1 && !L.exp_range)) return PG_ERR_UNSUPPORTED;
+  for (int e = 0; e < L.n_exp; ++e) a.bias[e] = e ? L.bias_e[e] : L.bias;
   a.status = status;
   a.amax = L.amax;
-  a.head_w = L.head_w;
-  a.head_b = L.head_b;
+  for (int e = 0; e < L.n_exp; ++e) {
+    a.head_w[e] = e ? L.head_w_e[e] : L.head_w;
+    a.head_b[e] = e ? L.head_b_e[e] : L.head_b;
+  }
   a.head_y = L.head_y;
   a.pscale = L.pscale;
   a.res = L.res;
@@ -1012,7 +1073,9 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   const CUtensorMapDataType dt = es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   const CUtensorMapSwizzle sw =
       cb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : (cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
-  CUtensorMap mA, mB;
+  CUtensorMap mA;
+  TcMapsB mB;
+  memset(&mB, 0, sizeof(mB));
   {
     cuuint64_t dims[4] = {(cuuint64_t)L.Cin, (cuuint64_t)L.Win, (cuuint64_t)L.Hin, (cuuint64_t)ns};
     cuuint64_t strides[3] = {(cuuint64_t)L.in_cs * es, (cuuint64_t)L.Win * L.in_cs * es,
@@ -1036,9 +1099,12 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     cuuint64_t strides[1] = {(cuuint64_t)K * es};
     cuuint32_t box[2] = {(cuuint32_t)a.chunk, (cuuint32_t)L.Cout};
     cuuint32_t estr[2] = {1, 1};
-    if (enc(&mB, dt, 2, const_cast<void *>(L.w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return PG_ERR_UNSUPPORTED;
+    for (int e = 0; e < L.n_exp; ++e) {
+      const void *w = e ? L.w_e[e] : L.w;
+      if (!w || enc(&mB.b[e], dt, 2, const_cast<void *>(w), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return PG_ERR_UNSUPPORTED;
+    }
   }
   if (smem > 227 * 1024) return PG_ERR_UNSUPPORTED;
   const int grid = std::min(a.num_tiles, per_sm * num_sms());
@@ -1203,8 +1269,12 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
 template <typename T>
 pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, void *actv, uint32_t ns, int H, int W,
                      float *y, cudaStream_t st, const float *scale, unsigned int *amax, bool tune = false,
-                     bool mixed = false) {
+                     bool mixed = false, const Net *const *experts = nullptr, int n_exp = 1,
+                     const int *exp_range = nullptr, int pos0 = 0) {
   Net *net = const_cast<Net *>(netc);
+  // Mixture of experts in one launch per layer (BF16 U-Net only): experts[0]
+  // is net; the others share its layer shapes and launch shapes.
+  if (n_exp > 1 && (fp8 || mixed || scale || amax || tune || net->arch != 1 || n_exp > kMaxExperts)) return PG_ERR_UNSUPPORTED;
   // Mixed form (U-Net only): E4M3 operands inside the network (layers 3-11
   // read E4M3, layers 2-10 write it); the full-resolution level, its skip
   // concatenation and the head stay BF16.
@@ -1245,6 +1315,22 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
     L.out = out; L.out_cs = out_cs; L.out_co = out_co; L.ups = ups;
     L.Cout = Lr.cout; L.k = Lr.k; L.stride = Lr.stride; L.act = Lr.act;
     L.bias = Lr.b;
+    if (n_exp > 1) {
+      L.n_exp = n_exp;
+      L.exp_range = exp_range;
+      L.pos0 = pos0;
+      for (int e = 1; e < n_exp; ++e) {
+        const Layer &Le = experts[e]->layers[li];
+        if (!Le.w_bf16 || Le.cout != Lr.cout || Le.cin != Lr.cin || Le.k != Lr.k || Le.stride != Lr.stride)
+          return PG_ERR_UNSUPPORTED;
+        L.w_e[e] = Le.w_bf16;
+        L.bias_e[e] = Le.b;
+        if (head) {
+          L.head_w_e[e] = experts[e]->layers[14].w;
+          L.head_b_e[e] = experts[e]->layers[14].b;
+        }
+      }
+    }
     L.amax = amax ? amax + og[li] : nullptr;
     const bool in8 = in8_of(li), out8 = out8_of(li);
     const int pi = in8 ? 2 : 1;  // tuned shapes are kept per operand type
@@ -1297,7 +1383,11 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       return launch_tc(L, ns, les, out8, st, ctx->d_status, TcCfg());
     }
     PG_COUNT(ctx);
-    return launch_tc(L, ns, les, out8, st, ctx->d_status, cfg);
+    const pg_status s = launch_tc(L, ns, les, out8, st, ctx->d_status, cfg);
+    if (s != PG_OK && getenv("PG_TC_LOG"))
+      fprintf(stderr, "pg: layer %d (%d experts) launch shape halo %d chunk %dB mt %d ctas %d stages %d staged-out %d: status %d\n",
+              li, n_exp, cfg.halo, cfg.cb, cfg.mt, cfg.ctas, cfg.stages, cfg.so, (int)s);
+    return s;
   };
   auto head = [&](int li, const T *in, int in_cs, int Cin) -> pg_status {
     const Layer &Lr = Ls[li];
@@ -1417,6 +1507,15 @@ pg_status forward_tc(pg_ctx *ctx, const Net *netc, pg_precision prec, const floa
                                      true);
   return forward_lp<__nv_fp8_e4m3>(ctx, net, true, x0, actv, ns, H, W, y, st, net->act_scale, nullptr, tune);
 }
+
+pg_status forward_tc_experts(pg_ctx *ctx, const Net *const *nets, int n_exp, const int *d_range, int pos0, void *actv,
+                             uint32_t ns, int H, int W, float *y, cudaStream_t st) {
+  if (n_exp < 2 || n_exp > kMaxExperts) return PG_ERR_UNSUPPORTED;
+  return forward_lp<__nv_bfloat16>(ctx, nets[0], false, nullptr, actv, ns, H, W, y, st, nullptr, nullptr, false, false,
+                                   nets, n_exp, d_range, pos0);
+}
+
+int tc_max_experts() { return kMaxExperts; }
 
 size_t tc_bytes_per_leaf(const Net *net, pg_precision prec, int H, int W) {
   // Sized for 2-byte activations in both forms: an FP8 reconstruction may

@@ -878,6 +878,33 @@ pg_status pg_reconstruct_experts(pg_ctx *c, const pg_hist *hist, const pg_net *c
   }
   const uint32_t A = h->A;
   const size_t HW = (size_t)h->H * h->W;
+  // BF16 U-Net experts: grouped on the device and run as one launch per
+  // layer over every expert's tiles (no host read-back of the counts).
+  bool grouped = prec == PG_BF16 && n_experts > 1 && A > 0;
+  for (int e = 0; e < n_experts && grouped; ++e) grouped = ns[e]->arch == 1;
+  if (grouped) {
+    for (int e = 0; e < n_experts; ++e) PG_TRY(net_prepare(c, ns[e], prec));
+    Map *m = new (std::nothrow) Map();
+    if (!m) return PG_ERR_OOM;
+    memset(m, 0, sizeof(*m));
+    m->h.kind = KIND_MAP;
+    m->h.ctx = c;
+    m->A = A;
+    m->H = h->H;
+    m->W = h->W;
+    m->h.bytes = (size_t)A * HW * sizeof(float);
+    pg_status s = ctx_alloc(c, m->h.bytes, &m->block);
+    if (s == PG_OK) {
+      m->y = (float *)m->block;
+      s = reconstruct_experts_grouped(c, h, (const Net *const *)ns, n_experts, count_bounds, m->y);
+    }
+    if (s == PG_OK) {
+      *out = (pg_map *)m;
+      return PG_OK;
+    }
+    pg_free(m);
+    if (s != PG_ERR_UNSUPPORTED) return s;
+  }
   // Photon count of every leaf -> expert (the number of bounds <= count),
   // and the leaves grouped by expert, each group in slot order.
   std::vector<uint32_t> cnt(A), perm(A);

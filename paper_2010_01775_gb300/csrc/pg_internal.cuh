@@ -280,6 +280,20 @@ __device__ __forceinline__ uint64_t morton3(uint32_t qx, uint32_t qy, uint32_t q
   return spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
 }
 
+// The same interleave for cell indices of at most 10 bits (depth <= 10, a
+// 30-bit code) in 32-bit arithmetic: bit b of v to bit 3b by four
+// shift-or-mask steps (the bit-expansion step of Karras, "Maximizing
+// parallelism in the construction of BVHs, octrees and k-d trees", HPG 2012),
+// half the instructions of the 64-bit form.
+__device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
+  uint32_t x = v & 0x3FFu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
 struct GridGeom {
   float lo[3], scale[3];
   uint32_t top;  // 2^D - 1
@@ -290,6 +304,7 @@ __device__ __forceinline__ uint64_t position_code(const GridGeom &g, float x, fl
   uint32_t qx = quantise(x, g.lo[0], g.scale[0], g.top, bad);
   uint32_t qy = quantise(y, g.lo[1], g.scale[1], g.top, bad);
   uint32_t qz = quantise(z, g.lo[2], g.scale[2], g.top, bad);
+  if (g.D <= 10) return (uint64_t)(spread3_10(qx) | (spread3_10(qy) << 1) | (spread3_10(qz) << 2));
   return morton3(qx, qy, qz);
 }
 
@@ -492,6 +507,11 @@ pg_status reconstruct(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision p
 // d_perm (the identity when null), written to y_out in that position order.
 pg_status reconstruct_range(pg_ctx *ctx, const Hist *h, const Net *net, pg_precision prec, float *y_out,
                             const uint32_t *d_perm, uint32_t first, uint32_t count, bool tune = false);
+// Mixture of experts routed by leaf photon count (BF16 U-Nets): the leaves
+// grouped by expert on the device, then one tensor-core launch per layer
+// over every expert's tiles; maps y in slot order.  No host read-back.
+pg_status reconstruct_experts_grouped(pg_ctx *ctx, const Hist *h, const Net *const *nets, int E,
+                                     const uint32_t *count_bounds, float *y);
 // Photon count of every active leaf (sum of its current count plane).
 pg_status leaf_counts(pg_ctx *ctx, const Hist *h, uint32_t *d_counts);
 // y[perm[k]] = yp[k], rows of HW floats (HW a multiple of 4).

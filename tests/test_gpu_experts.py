@@ -78,3 +78,37 @@ def test_single_expert_and_bad_bounds(setup):
     with pytest.raises(pg.PgError) as ei:
         pg.pg_reconstruct_experts(ctx, h, nets[:3], count_bounds=(500, 100))
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("size,widths,tuned", [(32, (16, 32, 64, 128), False), (64, (16, 32, 64, 128), False),
+                                               (64, (32, 64, 128, 256), True)])
+def test_grouped_unet_experts_one_launch_per_layer(setup, size, widths, tuned):
+    """BF16 U-Net experts run as one tensor-core launch per layer over every
+    expert's tiles (leaves grouped by expert on the device, no host
+    read-back): every leaf's map equals, bit for bit, its expert's network run
+    alone, and the call launches one kernel per layer, not one per expert.
+    The tuned case gives every expert the first net's autotuned launch shapes,
+    which were chosen without the other experts' bias and head tables in
+    shared memory."""
+    ctx, ph, g, _, _, _, _, _ = setup
+    d = torch.from_numpy(ph).cuda()
+    h = pg.pg_splat_photons(ctx, g, d, N, N // 2, size, size)
+    counts = pg.export_hist(h)["cnt_cur"].sum(axis=1)
+    nets = [pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_UNET4, widths, 940 + e)) for e in range(5)]
+    if tuned:
+        pg.pg_autotune(ctx, h, nets[0], pg.PG_BF16)
+        for n in nets[1:]:
+            pg.pg_net_set_tuning(n, pg.pg_net_get_tuning(nets[0]))
+    for n in nets:  # weight copies made up front, outside the counted call
+        pg.export_map(pg.pg_reconstruct(ctx, h, n, pg.PG_BF16))
+    ctx.sync()
+    l0 = ctx.launch_count()
+    y = pg.export_map(pg.pg_reconstruct_experts(ctx, h, nets, precision=pg.PG_BF16))
+    launches = ctx.launch_count() - l0
+    assert launches <= 20, launches  # counts, grouping, assembly, 14 layers, scatter
+    e = O.expert_of(counts)
+    assert len(set(e.tolist())) >= 4
+    for k in range(5):
+        ref = pg.export_map(pg.pg_reconstruct(ctx, h, nets[k], pg.PG_BF16))
+        sel = e == k
+        assert np.array_equal(y[sel], ref[sel]), k
