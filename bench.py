@@ -39,7 +39,7 @@ LO, HI = [0.0, 0.0, 0.0], [1.0, 1.0, 1.0]
 # ncu capture of every kernel of a reconstruct (dram__bytes_read.sum +
 # dram__bytes_write.sum; profiles/k_conv_tc_scale-mid.md), keyed by (H, W,
 # precision).  The traffic of a reconstruct grows in proportion to its leaves.
-CNN_DRAM_BYTES_PER_LEAF = {(64, 64, "bf16"): 7131.7e6 / 1322}
+CNN_DRAM_BYTES_PER_LEAF = {(64, 64, "bf16"): 5659.5e6 / 1322}
 
 
 def unet_flops_per_leaf(H, W, widths, arch):
@@ -59,6 +59,26 @@ def unet_flops_per_leaf(H, W, widths, arch):
              (H // 2, W // 2), (H, W), (H, W), (H, W)]
     for (cout, cin, k, s, a), (ho, wo) in zip(layers, sizes):
         f += 2 * ho * wo * k * k * cin * cout
+    return f
+
+
+def unet_executed_flops_per_leaf(H, W, widths, arch, precision):
+    """The FLOPs the tensor cores execute per map.  In BF16 the U-Net's
+    decoder layers over [upsample2(U), S] whose half-resolution grid is at
+    least 32 wide run in the phase form: U's part is four 2x2 convolutions at
+    half resolution, one per output phase, instead of a 3x3 convolution of
+    the upsampled map, so each output pixel takes 4 instead of 9 taps of U's
+    channels.  The network computes the same function, and the algorithmic
+    count (unet_flops_per_leaf) stays the dense one."""
+    from paper_2010_01775_gb300 import synth
+    f = unet_flops_per_leaf(H, W, widths, arch)
+    if arch != synth.ARCH_UNET4 or precision != "bf16":
+        return f
+    c = list(widths)
+    for lev, (cu, cout) in enumerate(((c[1], c[0]), (c[2], c[1]), (c[3], c[2]))):
+        hl, wl = H >> lev, W >> lev
+        if wl // 2 >= 32 and 2 * (wl // 2 + 2) <= 256 and hl % 2 == 0 and wl % 2 == 0:
+            f -= 2 * hl * wl * cout * 5 * cu
     return f
 
 
@@ -363,6 +383,7 @@ def run_pg(args, wl, prec):
         peak = peaks["bf16_tflops"] * (2.0 if prec == pg.PG_FP8_E4M3 else 1.0)
         bound, unit = "tensor", "TFLOP/s"
     achieved = flops_leaf * A / cnn_s / 1e12
+    executed = unet_executed_flops_per_leaf(H, W, wl.widths, wl.arch, args.precision) * A / cnn_s / 1e12
 
     # The other precisions of the same workload (shorter runs).  For the
     # reduced-precision check each one's sampling map is kept on the leaves
@@ -442,7 +463,11 @@ def run_pg(args, wl, prec):
                                      else None),
                          "kernel": "CNN convolutions (all layers of one reconstruct call)",
                          "peak_source": ("of " + peak_src) if prec != pg.PG_FP32 else
-                         "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock"},
+                         "derived: 152 SM x 128 FP32 FMA/clk x 2 x max SM clock",
+                         "flops_per_leaf": flops_leaf,
+                         "executed_flops_per_leaf": unet_executed_flops_per_leaf(H, W, wl.widths, wl.arch,
+                                                                                 args.precision),
+                         "executed_achieved": executed, "executed_frac": executed / peak},
             "clocks": main["clocks"],
         }
         if sweep:

@@ -74,6 +74,14 @@ struct TcArgs {
   uint32_t bytes_ver;  // halo mode: bytes of one x-shifted input box (Ht + 2 rows)
   int Wt, Ht, Lt;
   int P, Hb, tpl;   // mode 2: padded row pitch, box rows, tiles per leaf
+  // Mode 3 (phase form of a decoder convolution over [upsample(U), S]): the
+  // tile is 128 padded-row positions of the half-resolution grid (pitch P)
+  // in npt of the 4 output phases (py, px), one subtile per phase; output
+  // pixel (2y + py, 2x + px).  kS stages read S, the full-resolution skip
+  // input, as four parity sub-grids (boxes of box_a bytes); kU stages read
+  // U, the half-resolution input, as one box.
+  int npt, kS, kU, CinU;
+  uint32_t box_a, btap, tx_u;
   int num_tiles, kiters, stages;
   uint32_t bytes_a, bytes_b;  // per stage (A rounded up to 1 KB in mode 2)
   uint32_t tx_bytes;          // bytes the TMA copies of one stage deliver
@@ -367,6 +375,7 @@ struct StageOps {
   uint32_t cb, sub_step, row_step, ver16, tap_b16, desc_hi, idesc;
   bool first;
   int sub;  // the 128-row subtile (and accumulator) this issuing lane owns
+  uint32_t box_a;  // mode 3: bytes between the parity sub-grid boxes
 };
 
 // The MMAs of one stage for one subtile, as straight-line code: a
@@ -410,9 +419,65 @@ __device__ __forceinline__ void issue_stage(const StageOps &o) {
   }
 }
 
+// Mode 3: the MMAs of one stage for the subtile of output phase (py, px).
+// An S stage holds the four parity sub-grids of the full-resolution input:
+// tap (ky, kx) reads row 2y + py + ky - 1 = 2 (y + sy / 2 - 1) + sy % 2 with
+// sy = py + ky + 1, i.e. box row sy / 2 of parity sub-grid sy % 2 (likewise
+// for columns).  A U stage holds the half-resolution input: the phase's 2x2
+// taps (i, j) read box row py + i and column px + j, with weights that sum
+// the 3x3 taps falling on the same upsampled pixel.
+template <int kMPS>
+__device__ __forceinline__ void issue_stage3(const StageOps &o, bool u_stage, int py, int px) {
+  const uint32_t d = o.d + (uint32_t)o.sub * o.BN;
+  const uint32_t row0 = o.a_byte0 + (uint32_t)o.off0 * o.cb;
+  if (!u_stage) {
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const int sy = py + ky + 1;
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int sx = px + kx + 1;
+        const uint32_t addr = row0 + (uint32_t)((sy & 1) * 2 + (sx & 1)) * o.box_a +
+                              (uint32_t)((sy >> 1) * o.P + (sx >> 1)) * o.cb;
+        const uint32_t a_tap = ((addr & 0x3FFFFu) >> 4) | (1u << 16);
+        const uint32_t b_tap = o.blo + (uint32_t)(ky * 3 + kx) * o.tap_b16;
+#pragma unroll
+        for (int j = 0; j < kMPS; ++j) {
+          const uint32_t acc = (o.first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
+          mma_issue<false>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi, o.idesc, acc);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+#pragma unroll
+      for (int jx = 0; jx < 2; ++jx) {
+        const uint32_t addr = row0 + (uint32_t)((py + i) * o.P + px + jx) * o.cb;
+        const uint32_t a_tap = ((addr & 0x3FFFFu) >> 4) | (1u << 16);
+        const uint32_t b_tap = o.blo + (uint32_t)(o.sub * 4 + i * 2 + jx) * o.tap_b16;
+#pragma unroll
+        for (int j = 0; j < kMPS; ++j)
+          mma_issue<false>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi, o.idesc, 1u);
+      }
+    }
+  }
+}
+
+// Mode 3 tile t: leaf l0, phase group g (phases g * npt ..) and first
+// position q0 of the half-resolution padded rows.
+__device__ __forceinline__ void tile_origin3(const TcArgs &a, int t, int &l0, int &g, int &q0) {
+  const int groups = 4 / a.npt, per_leaf = groups * a.tpl;
+  l0 = t / per_leaf;
+  const int r = t - l0 * per_leaf;
+  g = r / a.tpl;
+  q0 = (r - g * a.tpl) * kBM;
+}
+
 template <bool kFp8Out, bool kCalib>
 __global__ void __launch_bounds__(kThreads, 2)
-    k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ TcMapsB mapsB, const TcArgs a) {
+    k_conv_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapU,
+              const __grid_constant__ TcMapsB mapsB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t *sA = smem;
@@ -455,6 +520,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+    if (a.halo == 3) asm volatile("prefetch.tensormap [%0];" ::"l"(&mapU) : "memory");
     for (int e = 0; e < a.n_exp; ++e) asm volatile("prefetch.tensormap [%0];" ::"l"(&mapsB.b[e]) : "memory");
   }
   if (warp == 1) {
@@ -477,10 +543,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     bool ok = true;
     long long prod_wait = 0;
     const long long prod_t0 = clock64();
-    const int ntma = a.halo == 2 ? 10 : (a.halo ? 12 : 2);
+    const int ntma = a.halo == 3 ? 17 : (a.halo == 2 ? 10 : (a.halo ? 12 : 2));
     for (int t = blockIdx.x; t < a.num_tiles && ok; t += gridDim.x) {
-      int l0, y0, x0;
-      if (a.halo == 2) {
+      int l0, y0, x0, g = 0;
+      if (a.halo == 3) {
+        int q0;
+        tile_origin3(a, t, l0, g, q0);
+        y0 = q0 / a.P - 1;
+        x0 = -1;
+      } else if (a.halo == 2) {
         // Leaf of the tile, and the first box row: the image row above the
         // tile's first output row (row -1 and rows >= H are zero-filled).
         l0 = t / a.tpl;
@@ -496,7 +567,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           const long long c0 = clock64();
           got = mbar_wait(&empty[stage], phase ^ 1u, abort_flag) ? 1 : 0;
           prod_wait += clock64() - c0;
-          if (got) mbar_expect_tx(&full[stage], a.tx_bytes);
+          if (got) mbar_expect_tx(&full[stage], (a.halo == 3 && ki >= a.kS) ? a.tx_u : a.tx_bytes);
         }
         got = __shfl_sync(0xFFFFFFFFu, got, 0);
         if (!got) {
@@ -505,7 +576,30 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncwarp();
         if (lane < ntma) {
-          if (a.halo == 2) {
+          if (a.halo == 3) {
+            uint8_t *dA = sA + (size_t)stage * a.bytes_a, *dB = sB + (size_t)stage * a.bytes_b;
+            if (ki < a.kS) {
+              // Lane b loads parity sub-grid b (rows 2r + b / 2, columns
+              // 2c + b % 2) of the skip input; lanes 4..12 the 9 taps' weights.
+              const int cc = ki;
+              if (lane < 4)
+                tma_load_4d(&mapA, &full[stage], dA + (size_t)lane * a.box_a, cc * a.chunk, 2 * x0 + (lane & 1),
+                            2 * y0 + (lane >> 1), l0);
+              else if (lane < 13)
+                tma_load_2d(mapB, &full[stage], dB + (size_t)(lane - 4) * a.btap, (lane - 4) * a.Cin + cc * a.chunk, 0);
+            } else {
+              // Lane 0 loads the half-resolution box; lanes 1..4 npt the 2x2
+              // taps' combined weights of the tile's phases.
+              const int cc = ki - a.kS;
+              if (lane == 0) {
+                tma_load_4d(&mapU, &full[stage], dA, cc * a.chunk, x0, y0, l0);
+              } else if (lane <= 4 * a.npt) {
+                const int j = lane - 1, ph = g * a.npt + (j >> 2);
+                tma_load_2d(mapB, &full[stage], dB + (size_t)j * a.btap,
+                            9 * a.Cin + (ph * 4 + (j & 3)) * a.CinU + cc * a.chunk, 0);
+              }
+            }
+          } else if (a.halo == 2) {
             const int cc = ki;
             if (lane == 0)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk, x0, y0, l0);
@@ -572,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const uint32_t sub_step = (uint32_t)kBM * row16;       // next 128-row subtile
       const uint32_t row_step = (uint32_t)a.Wt * row16;      // halo mode: next tap row
       const uint32_t ver16 = a.bytes_ver >> 4;               // halo mode: next x-shifted copy
-      const uint32_t tap_b16 = (a.bytes_b / 9) >> 4;         // halo mode: next tap's weights
+      const uint32_t tap_b16 = (a.halo == 3 ? a.btap : a.bytes_b / 9) >> 4;  // next tap's weights
       long long mma_wait_acc = 0, mma_wait_full = 0;
       const long long mma_t0 = clock64();
       for (int t = blockIdx.x; t < a.num_tiles && !*abort_flag; t += gridDim.x, ++i) {
@@ -583,7 +677,16 @@ __global__ void __launch_bounds__(kThreads, 2)
         mma_wait_acc += clock64() - c0;
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * a.mt * a.BN);
-        const int off0 = a.halo == 2 ? ((t % a.tpl) * kBM * a.mt) % a.P : 0;
+        int off0 = a.halo == 2 ? ((t % a.tpl) * kBM * a.mt) % a.P : 0;
+        int py = 0, px = 0;
+        if (a.halo == 3) {
+          int l0, g, q0;
+          tile_origin3(a, t, l0, g, q0);
+          off0 = q0 % a.P;
+          const int ph = g * a.npt + lane;  // this lane's subtile is one output phase
+          py = ph >> 1;
+          px = ph & 1;
+        }
         bool ok = true;
         for (int ki = 0; ki < a.kiters; ++ki) {
           c0 = clock64();
@@ -603,9 +706,18 @@ __global__ void __launch_bounds__(kThreads, 2)
           const bool first = ki == 0;
           const StageOps so{d,         (uint32_t)a.BN, alo_s,        blo_s,   a_base + (uint32_t)stage * a.bytes_a,
                             off0,      a.P,            (uint32_t)a.chunk_bytes, sub_step, row_step, ver16, tap_b16,
-                            desc_hi,   a.idesc,        first,   lane};
+                            desc_hi,   a.idesc,        first,   lane,                   a.box_a};
           // The MMA kind follows the operands (a.mma_kind), which may differ
           // from the output type (a layer at a BF16/E4M3 boundary).
+          if (a.halo == 3) {
+            const bool u_stage = ki >= a.kS;
+            if (a.mma_per_stage == 1)
+              issue_stage3<1>(so, u_stage, py, px);
+            else if (a.mma_per_stage == 2)
+              issue_stage3<2>(so, u_stage, py, px);
+            else if (a.mma_per_stage == 4)
+              issue_stage3<4>(so, u_stage, py, px);
+          } else
           switch ((a.mma_kind ? 16 : 0) + a.halo * 4 + (a.mma_per_stage >> 1)) {
 #define PG_STAGE_CASE(K, H, MPS) \
   case (K ? 16 : 0) + H * 4 + (MPS >> 1): issue_stage<K, H, MPS>(so); break;
@@ -659,8 +771,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       if (!mbar_wait(&acc_full[buf], use, abort_flag)) break;
       epi_wait += clock64() - c0;
       tc_fence_after();
-      int l0 = 0, y0 = 0, x0 = 0, q0 = 0;
-      if (a.halo == 2) {
+      int l0 = 0, y0 = 0, x0 = 0, q0 = 0, g = 0;
+      if (a.halo == 3) {
+        tile_origin3(a, t, l0, g, q0);
+      } else if (a.halo == 2) {
         l0 = t / a.tpl;
         q0 = (t - l0 * a.tpl) * kBM * a.mt;
       } else {
@@ -723,7 +837,18 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int mm = sub * kBM + m;
       int leaf, y, x;
       bool valid;
-      if (a.halo == 2) {
+      size_t pix0;
+      if (a.halo == 3) {
+        // Half-resolution padded rows; subtile sub is output phase
+        // (py, px) = g * npt + sub, written to pixel (2y + py, 2x + px).
+        const int qq = q0 + m, ph = g * a.npt + sub;
+        leaf = l0;
+        y = qq / a.P;
+        x = qq - y * a.P;
+        valid = y < a.Hout && x < a.Wout;
+        pix0 = ((size_t)leaf * (2 * a.Hout) + (size_t)(2 * y + (ph >> 1))) * (size_t)(2 * a.Wout) +
+               (size_t)(2 * x + (ph & 1));
+      } else if (a.halo == 2) {
         // Padded row space: q = y * P + x; the pad columns and rows past the
         // map are discarded.
         const int qq = q0 + mm;
@@ -739,7 +864,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         valid = (long)leaf * a.HWo + (long)y * a.Wout + x < a.M;
       }
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN + c);
-      const size_t pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
+      if (a.halo != 3) pix0 = ((size_t)leaf * Ho + (size_t)(y * reps)) * Wo + (size_t)(x * reps);
       const size_t opix = ((size_t)leaf * a.Hout + y) * a.Wout + x;  // before the x2 upsampled store
       const float ps = (a.pscale && valid) ? a.pscale[opix] : 0.0f;
       const __nv_bfloat16 *resp =
@@ -902,6 +1027,11 @@ struct LpLayer {
   const float *pscale = nullptr;
   const void *res = nullptr;
   int res_cs = 0, res_co = 0;
+  // Phase form (operand mode 3): the layer's input is [upsample2(U), S]
+  // with S = in (Cin channels, full resolution) and U = in_u (CinU channels,
+  // half resolution); w is then the phase weight layout (see make_phase_weights).
+  const void *in_u = nullptr;
+  int u_cs = 0, u_co = 0, CinU = 0;
 };
 
 // Launch shape: CTAs resident per SM and pipeline stages per CTA.  Zero
@@ -958,6 +1088,8 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   a.M = M;
   a.BN = L.Cout;
   a.mt = cfg.mt > 0 ? cfg.mt : 1;
+  if (cfg.halo < 2 && a.mt > 2) return PG_ERR_UNSUPPORTED;  // up to 4 subtiles: the padded-row modes only
+  if (a.mt != 1 && a.mt != 2 && a.mt != 4) return PG_ERR_UNSUPPORTED;
   const int TP = kBM * a.mt;  // pixels per CTA tile
   if (Wout >= TP) {
     a.Wt = TP; a.Ht = 1; a.Lt = 1;
@@ -992,6 +1124,37 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     const uint32_t box = (uint32_t)(a.Hb * a.P * cb);
     a.bytes_a = (box + 1023u) & ~1023u;
     a.tx_bytes = box + a.bytes_b;
+  }
+  if (a.halo == 3) {
+    // Phase form of a decoder layer: the tile grid is U's half-resolution
+    // map in padded rows (as mode 2), one subtile per output phase.  Each
+    // box holds Hb rows of P positions: Hb = ceil((128 + 1) / P) + 3 rows
+    // cover the tile and every tap's row and column offset of -1..1.
+    if (!L.in_u || es != 2 || fp8_out || L.k != 3 || L.stride != 1 || a.dil != 1 || L.pscale || L.res || L.head_y ||
+        L.ups || (L.Hin & 1) || (L.Win & 1) || L.CinU <= 0 || (L.CinU * es) % cb)
+      return PG_ERR_UNSUPPORTED;
+    if (cfg.mt <= 0) a.mt = L.Cout <= 64 ? 4 : (L.Cout <= 128 ? 2 : 1);  // all phases whose accumulators fit
+    if (a.mt != 1 && a.mt != 2 && a.mt != 4) return PG_ERR_UNSUPPORTED;
+    a.npt = a.mt;
+    a.Hout = L.Hin / 2;
+    a.Wout = L.Win / 2;
+    a.HWo = a.Hout * a.Wout;
+    a.P = a.Wout + 2;
+    a.Hb = (kBM + a.P) / a.P + 3;
+    if (2 * a.P > 256 || 2 * a.Hb > 256) return PG_ERR_UNSUPPORTED;
+    a.tpl = (a.Hout * a.P + kBM - 1) / kBM;
+    a.num_tiles = (int)ns * (4 / a.npt) * a.tpl;
+    a.CinU = L.CinU;
+    a.kS = a.cchunks;
+    a.kU = L.CinU / a.chunk;
+    a.kiters = a.kS + a.kU;
+    const uint32_t box = (uint32_t)(a.Hb * a.P * cb);
+    a.box_a = (box + 1023u) & ~1023u;
+    a.bytes_a = 4u * a.box_a;
+    a.btap = (uint32_t)(L.Cout * cb);
+    a.bytes_b = a.btap * (uint32_t)std::max(9, 4 * a.npt);
+    a.tx_bytes = 4u * box + 9u * a.btap;
+    a.tx_u = box + 4u * (uint32_t)a.npt * a.btap;
   }
   a.sbo = 8u * (uint32_t)cb;
   a.swz = cb == 128 ? 2 : (cb == 64 ? 4 : 6);
@@ -1088,13 +1251,33 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
       box[3] = 1;
     }
     cuuint32_t estr[4] = {1, (cuuint32_t)L.stride, (cuuint32_t)L.stride, 1};
+    if (a.halo == 3) {
+      // One parity sub-grid: every second column and row of the skip input.
+      box[1] = (cuuint32_t)(2 * a.P);
+      box[2] = (cuuint32_t)(2 * a.Hb);
+      box[3] = 1;
+      estr[1] = estr[2] = 2;
+    }
     void *base = (uint8_t *)L.in + (size_t)L.in_co * es;
     if (enc(&mA, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PG_ERR_UNSUPPORTED;
   }
+  CUtensorMap mU;
+  memset(&mU, 0, sizeof(mU));
+  if (a.halo == 3) {
+    const int Hu = L.Hin / 2, Wu = L.Win / 2;
+    cuuint64_t dims[4] = {(cuuint64_t)L.CinU, (cuuint64_t)Wu, (cuuint64_t)Hu, (cuuint64_t)ns};
+    cuuint64_t strides[3] = {(cuuint64_t)L.u_cs * es, (cuuint64_t)Wu * L.u_cs * es, (cuuint64_t)Hu * Wu * L.u_cs * es};
+    cuuint32_t box[4] = {(cuuint32_t)a.chunk, (cuuint32_t)a.P, (cuuint32_t)a.Hb, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    void *base = (uint8_t *)L.in_u + (size_t)L.u_co * es;
+    if (enc(&mU, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return PG_ERR_UNSUPPORTED;
+  }
   {
-    const int K = L.k * L.k * L.Cin;
+    const int K = a.halo == 3 ? 9 * L.Cin + 16 * L.CinU : L.k * L.k * L.Cin;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)L.Cout};
     cuuint64_t strides[1] = {(cuuint64_t)K * es};
     cuuint32_t box[2] = {(cuuint32_t)a.chunk, (cuuint32_t)L.Cout};
@@ -1110,13 +1293,13 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   const int grid = std::min(a.num_tiles, per_sm * num_sms());
   if (fp8_out) {
     PG_CUDA(cudaFuncSetAttribute(k_conv_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    k_conv_tc<true, false><<<grid, kThreads, smem, st>>>(mA, mB, a);
+    k_conv_tc<true, false><<<grid, kThreads, smem, st>>>(mA, mU, mB, a);
   } else if (a.amax) {
     PG_CUDA(cudaFuncSetAttribute(k_conv_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    k_conv_tc<false, true><<<grid, kThreads, smem, st>>>(mA, mB, a);
+    k_conv_tc<false, true><<<grid, kThreads, smem, st>>>(mA, mU, mB, a);
   } else {
     PG_CUDA(cudaFuncSetAttribute(k_conv_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    k_conv_tc<false, false><<<grid, kThreads, smem, st>>>(mA, mB, a);
+    k_conv_tc<false, false><<<grid, kThreads, smem, st>>>(mA, mU, mB, a);
   }
   if (want_stats) {
     unsigned long long h[8];
@@ -1183,6 +1366,51 @@ static pg_status make_lp_weights(pg_ctx *ctx, Layer &L, bool first, pg_precision
   return PG_OK;
 }
 
+// Phase-form weights of a decoder layer whose input is the concatenation
+// [upsample2(U) (Cu channels), S (Cs channels)], nearest-neighbour x2.  The
+// 3x3 tap (ky, kx) of output pixel (2y + py, 2x + px) falls on upsampled
+// pixel row 2y + py + ky - 1, i.e. U row y + floor((py + ky - 1) / 2): for
+// py = 0 the taps ky = 0 | 1, 2 land on U rows y - 1 | y, for py = 1 the
+// taps ky = 0, 1 | 2 on U rows y | y + 1 (columns likewise).  So each of the
+// four output phases convolves U with a 2x2 kernel whose taps sum the 3x3
+// taps landing on the same U pixel (the zero padding agrees: upsampled row
+// -1 or 2H is U row -1 or H), and S keeps its 3x3 taps.  Layout, K
+// contiguous: [cout][9 Cs (tap, channel) | 16 Cu (phase, 2x2 tap, channel)],
+// the sums taken in double and rounded to BF16 once.
+static pg_status make_phase_weights(pg_ctx *ctx, Layer &L, int Cu) {
+  const int Cs = L.cin - Cu;
+  if (L.k != 3 || L.stride != 1 || Cu <= 0 || Cs <= 0) return PG_ERR_UNSUPPORTED;
+  std::vector<float> wf((size_t)9 * L.cin * L.cout);
+  PG_CUDA(cudaMemcpyAsync(wf.data(), L.w, wf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  PG_CUDA(cudaStreamSynchronize(ctx->stream));
+  const size_t K = (size_t)9 * Cs + (size_t)16 * Cu;
+  std::vector<double> wt((size_t)L.cout * K, 0.0);
+  auto w_at = [&](int tap, int c, int o) { return (double)wf[((size_t)tap * L.cin + c) * L.cout + o]; };
+  for (int o = 0; o < L.cout; ++o) {
+    double *row = &wt[(size_t)o * K];
+    for (int tap = 0; tap < 9; ++tap)
+      for (int c = 0; c < Cs; ++c) row[(size_t)tap * Cs + c] = w_at(tap, Cu + c, o);
+    for (int ph = 0; ph < 4; ++ph) {
+      const int py = ph >> 1, px = ph & 1;
+      for (int ky = 0; ky < 3; ++ky)
+        for (int kx = 0; kx < 3; ++kx) {
+          const int i = ((py + ky + 1) >> 1) - py, j = ((px + kx + 1) >> 1) - px;  // U row / column offset + 1 - py
+          double *dst = row + (size_t)9 * Cs + (size_t)(ph * 4 + i * 2 + j) * Cu;
+          for (int c = 0; c < Cu; ++c) dst[c] += w_at(ky * 3 + kx, c, o);
+        }
+    }
+  }
+  std::vector<__nv_bfloat16> host(wt.size());
+  for (size_t i = 0; i < wt.size(); ++i) host[i] = __float2bfloat16_rn((float)wt[i]);
+  void *p;
+  PG_TRY(ctx_alloc(ctx, host.size() * 2, &p));
+  PG_CUDA(cudaMemcpyAsync(p, host.data(), host.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+  PG_CUDA(cudaStreamSynchronize(ctx->stream));
+  L.w_ph_bf16 = p;
+  L.w_ph_bytes = host.size() * 2;
+  return PG_OK;
+}
+
 // Serialises the one-time state changes of a net (reduced-precision weight
 // copies, FP8 activation calibration) between threads that share it.
 std::mutex &net_state_mutex() {
@@ -1200,6 +1428,10 @@ pg_status tc_prepare(pg_ctx *ctx, Net *net, pg_precision prec) {
     Layer &L = net->layers[l];
     // FP8 runs are calibrated by one BF16 pass, so they need both copies.
     if (!L.w_bf16) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_BF16));
+    // The U-Net's decoder layers over [upsample2(U), S] (layers 8, 10, 12):
+    // U is the previous layer's c3, c2 or c1 channels.
+    if (net->arch == 1 && (l == 8 || l == 10 || l == 12) && !L.w_ph_bf16)
+      PG_TRY(make_phase_weights(ctx, L, net->widths[(14 - l) / 2]));
     if ((prec == PG_FP8_E4M3 || prec == PG_FP8_MIXED) && !L.w_fp8) PG_TRY(make_lp_weights(ctx, L, l == 0, PG_FP8_E4M3));
   }
   return PG_OK;
@@ -1227,13 +1459,17 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   float best_ms = 1e30f;
   pg_status last_err = PG_ERR_UNSUPPORTED;
   *best = TcCfg();
+  // The phase form (operand mode 3) is the only mode of its layers, with
+  // one to four output phases per tile.
+  const std::vector<int> halos = L.in_u ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
   for (int so : {0, 1})
-  for (int halo : {0, 1, 2})
+  for (int halo : halos)
   for (int cb : {128, 64, 32})
-  for (int mt : {1, 2})
+  for (int mt : {1, 2, 4})
   for (int ctas : {1, 2, 3, 4})
     for (int stages : {2, 3, 4, 6, 8, 12, 16}) {
       if (halo && stages > 6) continue;
+      if (mt == 4 && halo < 2) continue;  // four subtiles: the padded-row modes only
       if (!halo && cb != 128 && stages < 3) continue;
       TcCfg c;
       c.ctas = ctas;
@@ -1298,9 +1534,16 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
   }
   auto conv = [&](int li, const void *in, int in_cs, int in_co, int Hin, int Win, int Cin, void *out, int out_cs,
                   int out_co, int ups, const Layer *head = nullptr, const float *pscale = nullptr,
-                  const void *res = nullptr, int res_cs = 0, int res_co = 0) -> pg_status {
+                  const void *res = nullptr, int res_cs = 0, int res_co = 0, const void *in_u = nullptr,
+                  int u_cs = 0, int CinU = 0) -> pg_status {
     const Layer &Lr = Ls[li];
+    const bool phase = in_u != nullptr;  // operand mode 3 over [upsample2(in_u), in]
     LpLayer L;
+    if (phase) {
+      L.in_u = in_u;
+      L.u_cs = u_cs;
+      L.CinU = CinU;
+    }
     if (head) {
       L.head_w = head->w;
       L.head_b = head->b;
@@ -1321,9 +1564,10 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       L.pos0 = pos0;
       for (int e = 1; e < n_exp; ++e) {
         const Layer &Le = experts[e]->layers[li];
-        if (!Le.w_bf16 || Le.cout != Lr.cout || Le.cin != Lr.cin || Le.k != Lr.k || Le.stride != Lr.stride)
+        if (!Le.w_bf16 || Le.cout != Lr.cout || Le.cin != Lr.cin || Le.k != Lr.k || Le.stride != Lr.stride ||
+            (phase && !Le.w_ph_bf16))
           return PG_ERR_UNSUPPORTED;
-        L.w_e[e] = Le.w_bf16;
+        L.w_e[e] = phase ? Le.w_ph_bf16 : Le.w_bf16;
         L.bias_e[e] = Le.b;
         if (head) {
           L.head_w_e[e] = experts[e]->layers[14].w;
@@ -1339,7 +1583,7 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       L.w = Lr.w_fp8;
       L.acc_mul = scale[ig[li]] * Lr.w_scale;
     } else {
-      L.w = Lr.w_bf16;
+      L.w = phase ? Lr.w_ph_bf16 : Lr.w_bf16;
       L.acc_mul = 1.0f;
     }
     L.out_mul = out8 ? 1.0f / scale[og[li]] : 1.0f;
@@ -1371,19 +1615,42 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
       cfg.cb = Lw.tc_cb[pi];
       cfg.so = Lw.tc_so[pi];
     }
+    // A shape tuned for the other form of this layer (phase form or not)
+    // does not apply.
+    if (phase != (cfg.halo == 3)) cfg = TcCfg();
+    if (phase) cfg.halo = 3;
+    // Default shape: the built-in heuristic; in the phase form the first of
+    // (chunk bytes, phases per tile) whose two stages fit in shared memory.
+    auto launch_default = [&]() -> pg_status {
+      if (!phase) return launch_tc(L, ns, les, out8, st, ctx->d_status, TcCfg());
+      pg_status r = PG_ERR_UNSUPPORTED;
+      static const int kShapes[5][2] = {{64, 4}, {32, 4}, {64, 2}, {32, 2}, {32, 1}};
+      for (const auto &cm : kShapes) {
+        TcCfg d;
+        d.halo = 3;
+        d.cb = cm[0];
+        d.mt = cm[1];
+        r = launch_tc(L, ns, les, out8, st, ctx->d_status, d);
+        if (r != PG_ERR_UNSUPPORTED) break;
+      }
+      return r;
+    };
     // Diagnostics: PG_TC_FORCE=<mode>[,cb,mt,ctas,stages,staged] runs every layer
     // that supports it with that operand staging mode and launch shape (zero
-    // or missing fields: defaults); other layers run the default shape.
+    // or missing fields: defaults); other layers run the default shape.  The
+    // phase-form layers always run mode 3.
     if (const char *force = getenv("PG_TC_FORCE")) {
       TcCfg f;
       sscanf(force, "%d,%d,%d,%d,%d,%d", &f.halo, &f.cb, &f.mt, &f.ctas, &f.stages, &f.so);
+      if (phase) f.halo = 3;
       PG_COUNT(ctx);
       const pg_status s = launch_tc(L, ns, les, out8, st, ctx->d_status, f);
       if (s != PG_ERR_UNSUPPORTED) return s;
-      return launch_tc(L, ns, les, out8, st, ctx->d_status, TcCfg());
+      return launch_default();
     }
     PG_COUNT(ctx);
-    const pg_status s = launch_tc(L, ns, les, out8, st, ctx->d_status, cfg);
+    pg_status s = (cfg.cb || cfg.mt || !phase) ? launch_tc(L, ns, les, out8, st, ctx->d_status, cfg) : launch_default();
+    if (s == PG_ERR_UNSUPPORTED && (Lw.tuned_hw[pi] == H * W || phase)) s = launch_default();
     if (s != PG_OK && getenv("PG_TC_LOG"))
       fprintf(stderr, "pg: layer %d (%d experts) launch shape halo %d chunk %dB mt %d ctas %d stages %d staged-out %d: status %d\n",
               li, n_exp, cfg.halo, cfg.cb, cfg.mt, cfg.ctas, cfg.stages, cfg.so, (int)s);
@@ -1447,19 +1714,62 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
   T *cat2 = t1 + ns * HW / 4 * c1;
   T *t2 = cat2 + ns * HW / 16 * k2c;
   T *t3 = t2 + ns * HW / 16 * c2;
+  // Phase form of decoder level lev (layer 12 - 2 lev over [upsample2(U), S],
+  // maps of width W >> lev): the skip S goes to its own dense buffer at the
+  // start of the concatenation buffer, and the layer before writes U there
+  // too, at half resolution instead of its x2 upsampled copy.  BF16 only
+  // (the E4M3 forms and their calibration pass keep the concatenation), and
+  // only where the half-resolution grid is at least 32 wide, so the tiles'
+  // tail past each leaf's rows stays small.
+  bool ph[3];
+  for (int lev = 0; lev < 3; ++lev) {
+    const int Wl = W >> lev, Hl = H >> lev;
+    bool ok = !fp8 && !mixed && !scale && !amax && Ls[12 - 2 * lev].w_ph_bf16 && Wl / 2 >= 32 &&
+              2 * (Wl / 2 + 2) <= 256 && Hl % 2 == 0 && Wl % 2 == 0 && getenv("PG_TC_NO_PHASE") == nullptr;
+    for (int e = 1; e < n_exp && ok; ++e) ok = experts[e]->layers[12 - 2 * lev].w_ph_bf16 != nullptr;
+    ph[lev] = ok;
+  }
+  T *u0 = cat0 + ns * HW * c0, *u1 = cat1 + ns * HW / 4 * c1, *u2 = cat2 + ns * HW / 16 * c2;
   PG_TRY(conv(0, xcol, cp, 0, H, W, cp, t0, c0, 0, 0));
-  PG_TRY(conv(1, t0, c0, 0, H, W, c0, cat0, k0c, c1, 0));
-  PG_TRY(conv(2, cat0, k0c, c1, H, W, c0, t1, c1, 0, 0));
-  PG_TRY(conv(3, t1, c1, 0, H1, W1, c1, cat1, k1c, c2, 0));
-  PG_TRY(conv(4, cat1, k1c, c2, H1, W1, c1, t2, c2, 0, 0));
-  PG_TRY(conv(5, t2, c2, 0, H2, W2, c2, cat2, k2c, c3, 0));
-  PG_TRY(conv(6, cat2, k2c, c3, H2, W2, c2, t3, c3, 0, 0));
-  PG_TRY(conv(7, t3, c3, 0, H3, W3, c3, cat2, k2c, 0, 1));
-  PG_TRY(conv(8, cat2, k2c, 0, H2, W2, k2c, t2, c2, 0, 0));
-  PG_TRY(conv(9, t2, c2, 0, H2, W2, c2, cat1, k1c, 0, 1));
-  PG_TRY(conv(10, cat1, k1c, 0, H1, W1, k1c, t1, c1, 0, 0));
-  PG_TRY(conv(11, t1, c1, 0, H1, W1, c1, cat0, k0c, 0, 1));
-  PG_TRY(conv(12, cat0, k0c, 0, H, W, k0c, t0, c0, 0, 0));
+  if (ph[0]) {
+    PG_TRY(conv(1, t0, c0, 0, H, W, c0, cat0, c0, 0, 0));
+    PG_TRY(conv(2, cat0, c0, 0, H, W, c0, t1, c1, 0, 0));
+  } else {
+    PG_TRY(conv(1, t0, c0, 0, H, W, c0, cat0, k0c, c1, 0));
+    PG_TRY(conv(2, cat0, k0c, c1, H, W, c0, t1, c1, 0, 0));
+  }
+  if (ph[1]) {
+    PG_TRY(conv(3, t1, c1, 0, H1, W1, c1, cat1, c1, 0, 0));
+    PG_TRY(conv(4, cat1, c1, 0, H1, W1, c1, t2, c2, 0, 0));
+  } else {
+    PG_TRY(conv(3, t1, c1, 0, H1, W1, c1, cat1, k1c, c2, 0));
+    PG_TRY(conv(4, cat1, k1c, c2, H1, W1, c1, t2, c2, 0, 0));
+  }
+  if (ph[2]) {
+    PG_TRY(conv(5, t2, c2, 0, H2, W2, c2, cat2, c2, 0, 0));
+    PG_TRY(conv(6, cat2, c2, 0, H2, W2, c2, t3, c3, 0, 0));
+    PG_TRY(conv(7, t3, c3, 0, H3, W3, c3, u2, c3, 0, 0));
+    PG_TRY(conv(8, cat2, c2, 0, H2, W2, c2, t2, c2, 0, 0, nullptr, nullptr, nullptr, 0, 0, u2, c3, c3));
+  } else {
+    PG_TRY(conv(5, t2, c2, 0, H2, W2, c2, cat2, k2c, c3, 0));
+    PG_TRY(conv(6, cat2, k2c, c3, H2, W2, c2, t3, c3, 0, 0));
+    PG_TRY(conv(7, t3, c3, 0, H3, W3, c3, cat2, k2c, 0, 1));
+    PG_TRY(conv(8, cat2, k2c, 0, H2, W2, k2c, t2, c2, 0, 0));
+  }
+  if (ph[1]) {
+    PG_TRY(conv(9, t2, c2, 0, H2, W2, c2, u1, c2, 0, 0));
+    PG_TRY(conv(10, cat1, c1, 0, H1, W1, c1, t1, c1, 0, 0, nullptr, nullptr, nullptr, 0, 0, u1, c2, c2));
+  } else {
+    PG_TRY(conv(9, t2, c2, 0, H2, W2, c2, cat1, k1c, 0, 1));
+    PG_TRY(conv(10, cat1, k1c, 0, H1, W1, k1c, t1, c1, 0, 0));
+  }
+  if (ph[0]) {
+    PG_TRY(conv(11, t1, c1, 0, H1, W1, c1, u0, c1, 0, 0));
+    PG_TRY(conv(12, cat0, c0, 0, H, W, c0, t0, c0, 0, 0, nullptr, nullptr, nullptr, 0, 0, u0, c1, c1));
+  } else {
+    PG_TRY(conv(11, t1, c1, 0, H1, W1, c1, cat0, k0c, 0, 1));
+    PG_TRY(conv(12, cat0, k0c, 0, H, W, k0c, t0, c0, 0, 0));
+  }
   // The 1x1 head (Cout 1) + softplus runs in layer 13's epilogue.
   if (Ls[14].k == 1 && Ls[14].cout == 1) return conv(13, t0, c0, 0, H, W, c0, t0b, c0, 0, 0, &Ls[14]);
   PG_TRY(conv(13, t0, c0, 0, H, W, c0, t0b, c0, 0, 0));

@@ -483,8 +483,8 @@ pg_status pg_net_set_tuning(pg_net *netp, const int32_t *in, size_t n) {
   Net *net = as<Net>(netp, KIND_NET);
   if (!net || !in || n != (size_t)net->n_layers * 3 * 7) return PG_ERR_INVALID_ARG;
   for (size_t i = 0; i < n; i += 7)
-    if (in[i] < 0 || in[i] > 4 || in[i + 1] < 0 || in[i + 1] > 24 || in[i + 2] < 0 || in[i + 2] > 2 ||
-        in[i + 3] < 0 || in[i + 3] > 2 || (in[i + 4] != 0 && in[i + 4] != 32 && in[i + 4] != 64 && in[i + 4] != 128) ||
+    if (in[i] < 0 || in[i] > 4 || in[i + 1] < 0 || in[i + 1] > 24 || in[i + 2] < 0 || in[i + 2] > 4 ||
+        in[i + 3] < 0 || in[i + 3] > 3 || (in[i + 4] != 0 && in[i + 4] != 32 && in[i + 4] != 64 && in[i + 4] != 128) ||
         in[i + 5] < 0 || in[i + 6] < 0 || in[i + 6] > 1)
       return PG_ERR_INVALID_ARG;
   for (int l = 0; l < net->n_layers; ++l)
@@ -1558,6 +1558,7 @@ void pg_free(void *handle) {
       for (int i = 0; i < n->n_layers; ++i) {
         if (n->layers[i].w_bf16) ctx_free(b->ctx, n->layers[i].w_bf16, n->layers[i].w_bf16_bytes);
         if (n->layers[i].w_fp8) ctx_free(b->ctx, n->layers[i].w_fp8, n->layers[i].w_fp8_bytes);
+        if (n->layers[i].w_ph_bf16) ctx_free(b->ctx, n->layers[i].w_ph_bf16, n->layers[i].w_ph_bytes);
       }
       break;
     }

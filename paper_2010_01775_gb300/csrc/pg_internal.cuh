@@ -108,7 +108,10 @@ struct Layer {
   float *b;   // device, [cout]
   void *w_bf16;  // device, BF16 copy [cout][K] (tensor-core layout), or null
   void *w_fp8;   // device, FP8 E4M3 copy [cout][K], or null
-  size_t w_bf16_bytes, w_fp8_bytes;
+  // device, BF16 phase-form weights of a U-Net decoder layer over
+  // [upsample2(U), S]: [cout][9 Cs + 16 Cu] (see make_phase_weights), or null
+  void *w_ph_bf16;
+  size_t w_bf16_bytes, w_fp8_bytes, w_ph_bytes;
   float w_scale;  // FP8 per-tensor weight scale (w = w_fp8 * w_scale)
   // Tensor-core launch shape picked by pg_autotune, per reduced precision
   // (index 1 = BF16, 2 = FP8) for maps of tuned_hw[i] bins (0 = not tuned).

@@ -102,3 +102,47 @@ def test_tuning_round_trip(setup):
     bad[3] = 7  # no such staging mode
     with pytest.raises(pg.PgError):
         pg.pg_net_set_tuning(b, bad)
+
+
+def _unset(name):
+    os.environ.pop(name, None)
+
+
+@pytest.mark.parametrize("size", [64, 128])
+def test_phase_form_matches_the_concatenation(setup, size):
+    """A decoder layer over [upsample2(U), S] runs in the phase form: four 2x2
+    convolutions of the half-resolution U (one per output phase, each tap the
+    sum of the 3x3 taps that land on the same upsampled pixel) plus the 3x3
+    taps of S read as four parity sub-grids.  Its maps equal those of the
+    explicit x2 upsample into the concatenation up to the BF16 rounding of
+    the summed weights and the accumulation order."""
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, size, size)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), 906))
+    y_ph = pg.export_map(pg.pg_reconstruct(ctx, h, net, pg.PG_BF16))
+    os.environ["PG_TC_NO_PHASE"] = "1"
+    try:
+        y_cat = pg.export_map(pg.pg_reconstruct(ctx, h, net, pg.PG_BF16))
+    finally:
+        _unset("PG_TC_NO_PHASE")
+    assert np.isfinite(y_ph).all() and (y_ph >= 0).all()
+    assert not np.array_equal(y_ph, y_cat)  # the phase form did run
+    assert np.abs(y_ph - y_cat).sum() / np.abs(y_cat).sum() < 5e-3
+    p = y_ph.reshape(len(y_ph), -1) / y_ph.reshape(len(y_ph), -1).sum(axis=1, keepdims=True)
+    q = y_cat.reshape(len(y_cat), -1) / y_cat.reshape(len(y_cat), -1).sum(axis=1, keepdims=True)
+    kl = (q * np.log(np.maximum(q, 1e-30) / np.maximum(p, 1e-30))).sum(axis=1)
+    assert kl.max() < 1e-4, kl.max()
+
+
+@pytest.mark.parametrize("size", [64, 128])
+def test_phase_tiles_of_one_two_or_four_phases_agree_bit_for_bit(setup, size):
+    # Every output phase gets the same MMAs in the same K order (skip chunks,
+    # taps, then upsampled chunks, 2x2 taps) whether a tile holds one, two or
+    # four phases, so the maps are bit-identical.
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, size, size)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), 907))
+    ys = [_maps(ctx, net, h, pg.PG_BF16, f"3,32,{mt},0,0,0") for mt in (1, 2, 4)]
+    assert np.isfinite(ys[0]).all()
+    for y in ys[1:]:
+        assert np.array_equal(ys[0], y)
