@@ -103,6 +103,10 @@ struct TcArgs {
   int n_exp, pos0;
   const int *exp_range;
   const float *bias[kMaxExperts];
+  // Weight images (per expert): each stage's weight blocks of btap bytes as
+  // they lie in shared memory, in the K order of the operand mode, copied
+  // by one bulk copy per stage; null: per-block tensor loads.
+  const uint8_t *bimg[kMaxExperts];
   uint32_t *status;
   unsigned int *amax;  // optional: running max |output| (float bits) for FP8 calibration
   unsigned long long *stats;  // optional: per-role cycle counters (diagnostics)
@@ -184,6 +188,15 @@ __device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *ba
       "[%2];" ::"r"(saddr(dst)),
       "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1)
       : "memory");
+}
+
+// Plain bulk copy global -> shared (16-byte aligned, a multiple of 16
+// bytes), completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   saddr(dst)),
+               "l"(src), "r"(bytes), "r"(saddr(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -560,7 +573,9 @@ __global__ void __launch_bounds__(kThreads, 2)
       } else {
         tile_origin(a, t, l0, y0, x0);
       }
-      const CUtensorMap *mapB = &mapsB.b[a.n_exp > 1 ? tile_expert(a, s_range, l0) : 0];
+      const int te = a.n_exp > 1 ? tile_expert(a, s_range, l0) : 0;
+      const CUtensorMap *mapB = &mapsB.b[te];
+      const uint8_t *img = a.bimg[te];
       for (int ki = 0; ki < a.kiters; ++ki) {
         int got = 1;
         if (lane == 0) {
@@ -575,6 +590,21 @@ __global__ void __launch_bounds__(kThreads, 2)
           break;
         }
         __syncwarp();
+        if (img && lane == 31) {
+          // The stage's weight blocks, contiguous in the image: mode 0 one
+          // block per (tap, chunk); modes 1-2 the 9 taps of chunk ki; mode 3
+          // the 9 taps of skip chunk ki, or the 2x2 taps of the tile's phases
+          // for U chunk ki - kS (16 blocks per U chunk, 4 per phase).
+          int b0 = ki, nb = 1;
+          if (a.halo == 3 && ki >= a.kS) {
+            b0 = 9 * a.kS + (ki - a.kS) * 16 + g * 4 * a.npt;
+            nb = 4 * a.npt;
+          } else if (a.halo) {
+            b0 = 9 * ki;
+            nb = 9;
+          }
+          bulk_load(sB + (size_t)stage * a.bytes_b, img + (size_t)b0 * a.btap, (uint32_t)nb * a.btap, &full[stage]);
+        }
         if (lane < ntma) {
           if (a.halo == 3) {
             uint8_t *dA = sA + (size_t)stage * a.bytes_a, *dB = sB + (size_t)stage * a.bytes_b;
@@ -585,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 2)
               if (lane < 4)
                 tma_load_4d(&mapA, &full[stage], dA + (size_t)lane * a.box_a, cc * a.chunk, 2 * x0 + (lane & 1),
                             2 * y0 + (lane >> 1), l0);
-              else if (lane < 13)
+              else if (lane < 13 && !img)
                 tma_load_2d(mapB, &full[stage], dB + (size_t)(lane - 4) * a.btap, (lane - 4) * a.Cin + cc * a.chunk, 0);
             } else {
               // Lane 0 loads the half-resolution box; lanes 1..4 npt the 2x2
@@ -593,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 2)
               const int cc = ki - a.kS;
               if (lane == 0) {
                 tma_load_4d(&mapU, &full[stage], dA, cc * a.chunk, x0, y0, l0);
-              } else if (lane <= 4 * a.npt) {
+              } else if (lane <= 4 * a.npt && !img) {
                 const int j = lane - 1, ph = g * a.npt + (j >> 2);
                 tma_load_2d(mapB, &full[stage], dB + (size_t)j * a.btap,
                             9 * a.Cin + (ph * 4 + (j & 3)) * a.CinU + cc * a.chunk, 0);
@@ -603,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int cc = ki;
             if (lane == 0)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk, x0, y0, l0);
-            else
+            else if (!img)
               tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 1) * (a.bytes_b / 9),
                           (lane - 1) * a.Cin + cc * a.chunk, 0);
           } else if (a.halo) {
@@ -614,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (lane < 3)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a + (size_t)lane * a.bytes_ver,
                           cc * a.chunk, x0 + lane - 1, y0 - 1, l0);
-            else
+            else if (!img)
               tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 3) * (a.bytes_b / 9),
                           (lane - 3) * a.Cin + cc * a.chunk, 0);
           } else {
@@ -623,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (lane == 0)
               tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, cc * a.chunk,
                           x0 * a.stride + kx * a.dil - a.pad, y0 * a.stride + ky * a.dil - a.pad, l0);
-            else
+            else if (!img)
               tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b, tap * a.Cin + cc * a.chunk, 0);
           }
         }
@@ -912,6 +942,47 @@ __global__ void __launch_bounds__(kThreads, 2)
   if (threadIdx.x == 0 && *abort_flag) atomicOr(a.status, ST_TIMEOUT);
 }
 
+// Weight image builder: block j (btap bytes, the Cout rows of one K chunk,
+// swizzled exactly as a tensor load writes them) holds the weights' K
+// columns [koff(j), koff(j) + chunk), loaded with the tensor map of the
+// per-block path.  Block orders: 0 (mode 0) block = tap * cchunks + chunk;
+// 1 (modes 1, 2) block = 9 * chunk + tap; 2 (mode 3) the 9 skip taps of
+// each skip chunk, then per U chunk the 16 (phase, 2x2 tap) blocks.
+__global__ void __launch_bounds__(128) k_build_bimage(const __grid_constant__ CUtensorMap mapB, int order, int cchunks,
+                                                      int Cin, int CinU, int chunk, uint32_t btap, uint8_t *out,
+                                                      uint32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *buf = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bar;
+  __shared__ int ok;
+  const int j = blockIdx.x;
+  int koff;
+  if (order == 0) {
+    koff = (j / cchunks) * Cin + (j % cchunks) * chunk;
+  } else if (order == 1 || j < 9 * cchunks) {
+    koff = (j % 9) * Cin + (j / 9) * chunk;
+  } else {
+    const int jj = j - 9 * cchunks;
+    koff = 9 * Cin + (jj % 16) * CinU + (jj / 16) * chunk;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, btap);
+    tma_load_2d(&mapB, &bar, buf, koff, 0);
+    volatile int never = 0;
+    ok = mbar_wait(&bar, 0, &never, 1000000000ull) ? 1 : 0;
+    if (!ok) {
+      atomicOr(status, ST_TIMEOUT);
+      mbar_wait(&bar, 0, &never, 1000000000ull);  // the copy in flight lands before the CTA exits
+    }
+  }
+  __syncthreads();
+  if (!ok) return;
+  for (uint32_t i = threadIdx.x * 16u; i < btap; i += blockDim.x * 16u)
+    *reinterpret_cast<uint4 *>(out + (size_t)j * btap + i) = *reinterpret_cast<const uint4 *>(buf + i);
+}
+
 // ---------------------------------------------------------------- small SIMT kernels
 // First-layer input in the tensor-core layout: the FP32 8-channel x0 as
 // 32-byte rows of T per pixel (16 BF16 or 32 E4M3 channels; channels 8.. are
@@ -1032,6 +1103,10 @@ struct LpLayer {
   // half resolution); w is then the phase weight layout (see make_phase_weights).
   const void *in_u = nullptr;
   int u_cs = 0, u_co = 0, CinU = 0;
+  // The nets' layers (expert e; 0: this net) and the contexts that own the
+  // nets, which hold and are charged for the weight images.
+  Layer *own[kMaxExperts] = {};
+  pg_ctx *own_ctx[kMaxExperts] = {};
 };
 
 // Launch shape: CTAs resident per SM and pipeline stages per CTA.  Zero
@@ -1055,6 +1130,65 @@ int ctas_by_registers() {
     return std::max(1, 65536 / (regs * kThreads));
   }();
   return n;
+}
+
+// Guards the nets' weight-image caches (a lock of its own: the E4M3
+// calibration pass runs under the net-state lock).
+std::mutex &bimg_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
+// The weight image of a layer's weights w (element size es) in block order
+// `order` with chunks of cb bytes (see k_build_bimage), built on first use
+// on stream st and cached in the layer; charged to the context owning the
+// net.  Returns null (the per-block tensor loads then serve) while st is
+// being captured into a graph or when the image cannot be allocated.
+const uint8_t *get_bimage(Layer *Lw, pg_ctx *owner, const void *w, int es, int order, int cb, int Cout, int K,
+                          int nblk, int cchunks, int Cin, int CinU, cudaStream_t st, uint32_t *status) {
+  if (!Lw || !owner || !w) return nullptr;
+  const int ei = es == 1 ? 1 : 0, ci = cb == 128 ? 0 : (cb == 64 ? 1 : 2);
+  std::lock_guard<std::mutex> lock(bimg_mutex());
+  if (Lw->bimg[ei][order][ci]) return (const uint8_t *)Lw->bimg[ei][order][ci];
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return nullptr;
+  const int chunk = cb / es;
+  const uint32_t btap = (uint32_t)(Cout * cb);
+  CUtensorMap map;
+  cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)Cout};
+  cuuint64_t strides[1] = {(cuuint64_t)K * es};
+  cuuint32_t box[2] = {(cuuint32_t)chunk, (cuuint32_t)Cout};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapSwizzle sw =
+      cb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : (cb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+  if (enc(&map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(w),
+          dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return nullptr;
+  const size_t bytes = (size_t)nblk * btap;
+  void *p = nullptr;
+  if (ctx_alloc(owner, bytes, &p) != PG_OK) return nullptr;
+  // The allocation is ordered on the owner's stream, the build on st.
+  if (cudaStreamSynchronize(owner->stream) != cudaSuccess) {
+    cudaGetLastError();
+    ctx_free(owner, p, bytes);
+    return nullptr;
+  }
+  k_build_bimage<<<nblk, 128, btap + 1024, st>>>(map, order, cchunks, Cin, CinU, chunk, btap, (uint8_t *)p, status);
+  // Other streams may use the image as soon as it is cached.
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    ctx_free(owner, p, bytes);
+    return nullptr;
+  }
+  Lw->bimg[ei][order][ci] = p;
+  Lw->bimg_bytes[ei][order][ci] = bytes;
+  return (const uint8_t *)p;
 }
 
 pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStream_t st, uint32_t *status,
@@ -1156,6 +1290,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     a.tx_bytes = 4u * box + 9u * a.btap;
     a.tx_u = box + 4u * (uint32_t)a.npt * a.btap;
   }
+  a.btap = (uint32_t)(L.Cout * cb);
   a.sbo = 8u * (uint32_t)cb;
   a.swz = cb == 128 ? 2 : (cb == 64 ? 4 : 6);
   a.mma_per_stage = cb / 32;
@@ -1290,6 +1425,21 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     }
   }
   if (smem > 227 * 1024) return PG_ERR_UNSUPPORTED;
+  // Weight images: one bulk copy per stage instead of one tensor load per
+  // weight block (all experts or none).
+  {
+    const int order = a.halo == 3 ? 2 : (a.halo ? 1 : 0);
+    const int K = a.halo == 3 ? 9 * L.Cin + 16 * L.CinU : L.k * L.k * L.Cin;
+    const int nblk = a.halo == 3 ? 9 * a.kS + 16 * a.kU : (a.halo ? 9 * a.cchunks : L.k * L.k * a.cchunks);
+    bool all = !getenv("PG_TC_NO_IMAGE");
+    for (int e = 0; e < L.n_exp && all; ++e) {
+      a.bimg[e] = get_bimage(L.own[e], L.own_ctx[e], e ? L.w_e[e] : L.w, es, order, cb, L.Cout, K, nblk,
+                             a.halo == 3 ? a.kS : a.cchunks, L.Cin, L.CinU, st, status);
+      all = a.bimg[e] != nullptr;
+    }
+    if (!all)
+      for (int e = 0; e < kMaxExperts; ++e) a.bimg[e] = nullptr;
+  }
   const int grid = std::min(a.num_tiles, per_sm * num_sms());
   if (fp8_out) {
     PG_CUDA(cudaFuncSetAttribute(k_conv_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -1539,6 +1689,8 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
     const Layer &Lr = Ls[li];
     const bool phase = in_u != nullptr;  // operand mode 3 over [upsample2(in_u), in]
     LpLayer L;
+    L.own[0] = &net->layers[li];
+    L.own_ctx[0] = net->h.ctx;
     if (phase) {
       L.in_u = in_u;
       L.u_cs = u_cs;
@@ -1568,6 +1720,8 @@ pg_status forward_lp(pg_ctx *ctx, const Net *netc, bool fp8, const float *x0, vo
             (phase && !Le.w_ph_bf16))
           return PG_ERR_UNSUPPORTED;
         L.w_e[e] = phase ? Le.w_ph_bf16 : Le.w_bf16;
+        L.own[e] = const_cast<Layer *>(&Le);
+        L.own_ctx[e] = experts[e]->h.ctx;
         L.bias_e[e] = Le.b;
         if (head) {
           L.head_w_e[e] = experts[e]->layers[14].w;

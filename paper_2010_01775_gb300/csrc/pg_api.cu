@@ -1559,6 +1559,10 @@ void pg_free(void *handle) {
         if (n->layers[i].w_bf16) ctx_free(b->ctx, n->layers[i].w_bf16, n->layers[i].w_bf16_bytes);
         if (n->layers[i].w_fp8) ctx_free(b->ctx, n->layers[i].w_fp8, n->layers[i].w_fp8_bytes);
         if (n->layers[i].w_ph_bf16) ctx_free(b->ctx, n->layers[i].w_ph_bf16, n->layers[i].w_ph_bytes);
+        for (int e = 0; e < 2; ++e)
+          for (int o = 0; o < 3; ++o)
+            for (int c = 0; c < 3; ++c)
+              if (n->layers[i].bimg[e][o][c]) ctx_free(b->ctx, n->layers[i].bimg[e][o][c], n->layers[i].bimg_bytes[e][o][c]);
       }
       break;
     }

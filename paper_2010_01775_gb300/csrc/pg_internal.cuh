@@ -112,6 +112,12 @@ struct Layer {
   // [upsample2(U), S]: [cout][9 Cs + 16 Cu] (see make_phase_weights), or null
   void *w_ph_bf16;
   size_t w_bf16_bytes, w_fp8_bytes, w_ph_bytes;
+  // Weight images for the tensor-core layers: every pipeline stage's weight
+  // blocks as they lie in shared memory (swizzled), so that one bulk copy
+  // fills a stage.  Indexed [BF16 / E4M3][block order][128 / 64 / 32-byte
+  // chunk]; built on first use (see conv_tc.cu), freed with the net.
+  void *bimg[2][3][3];
+  size_t bimg_bytes[2][3][3];
   float w_scale;  // FP8 per-tensor weight scale (w = w_fp8 * w_scale)
   // Tensor-core launch shape picked by pg_autotune, per reduced precision
   // (index 1 = BF16, 2 = FP8) for maps of tuned_hw[i] bins (0 = not tuned).

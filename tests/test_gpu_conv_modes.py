@@ -146,3 +146,26 @@ def test_phase_tiles_of_one_two_or_four_phases_agree_bit_for_bit(setup, size):
     assert np.isfinite(ys[0]).all()
     for y in ys[1:]:
         assert np.array_equal(ys[0], y)
+
+
+@pytest.mark.parametrize("size,prec,mode", [(64, pg.PG_BF16, None), (64, pg.PG_BF16, 0), (64, pg.PG_BF16, 1),
+                                            (128, pg.PG_BF16, None), (64, pg.PG_FP8_E4M3, None),
+                                            (64, pg.PG_FP8_E4M3, 1)])
+def test_weight_images_equal_per_block_loads_bit_for_bit(setup, size, prec, mode):
+    # A stage's weights arrive by one bulk copy of the layer's weight image
+    # (the blocks as a tensor load lays them out in shared memory) or by one
+    # tensor load per block: the same bytes, so the same maps.
+    ctx, ph, g = setup
+    h = pg.pg_splat_photons(ctx, g, ph, N, N // 2, size, size)
+    net = pg.pg_net_load(ctx, synth.net_blob(synth.ARCH_UNET4, (32, 64, 128, 256), 908))
+    if mode is not None:
+        os.environ["PG_TC_FORCE"] = str(mode)
+    try:
+        y_img = pg.export_map(pg.pg_reconstruct(ctx, h, net, prec))
+        os.environ["PG_TC_NO_IMAGE"] = "1"
+        y_blk = pg.export_map(pg.pg_reconstruct(ctx, h, net, prec))
+    finally:
+        _unset("PG_TC_NO_IMAGE")
+        _unset("PG_TC_FORCE")
+    assert np.isfinite(y_img).all()
+    assert np.array_equal(y_img, y_blk)
