@@ -1141,8 +1141,8 @@ std::mutex &bimg_mutex() {
 
 // The weight image of a layer's weights w (element size es) in block order
 // `order` with chunks of cb bytes (see k_build_bimage), built on first use
-// on stream st and cached in the layer; charged to the context owning the
-// net.  Returns null (the per-block tensor loads then serve) while st is
+// on stream st and cached in the layer; held outside the stream-ordered
+// pool and charged to the context owning the net.  Returns null (the per-block tensor loads then serve) while st is
 // being captured into a graph or when the image cannot be allocated.
 const uint8_t *get_bimage(Layer *Lw, pg_ctx *owner, const void *w, int es, int order, int cb, int Cout, int K,
                           int nblk, int cchunks, int Cin, int CinU, cudaStream_t st, uint32_t *status) {
@@ -1172,22 +1172,18 @@ const uint8_t *get_bimage(Layer *Lw, pg_ctx *owner, const void *w, int es, int o
     return nullptr;
   const size_t bytes = (size_t)nblk * btap;
   void *p = nullptr;
-  if (ctx_alloc(owner, bytes, &p) != PG_OK) return nullptr;
-  // The allocation is ordered on the owner's stream, the build on st.
-  if (cudaStreamSynchronize(owner->stream) != cudaSuccess) {
-    cudaGetLastError();
-    ctx_free(owner, p, bytes);
-    return nullptr;
-  }
+  if (ctx_alloc_static(owner, bytes, &p) != PG_OK) return nullptr;
   k_build_bimage<<<nblk, 128, btap + 1024, st>>>(map, order, cchunks, Cin, CinU, chunk, btap, (uint8_t *)p, status);
   // Other streams may use the image as soon as it is cached.
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
-    ctx_free(owner, p, bytes);
+    ctx_free_static(owner, p, bytes);
     return nullptr;
   }
   Lw->bimg[ei][order][ci] = p;
   Lw->bimg_bytes[ei][order][ci] = bytes;
+  if (getenv("PG_TC_LOG"))
+    fprintf(stderr, "pg: weight image of %d blocks (order %d, %d-byte chunks): %zu bytes\n", nblk, order, cb, bytes);
   return (const uint8_t *)p;
 }
 

@@ -114,6 +114,36 @@ pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr) {
   return PG_OK;
 }
 
+// Long-lived device memory outside the stream-ordered pool (charged to the
+// same budget): a block taken from the pool in the middle of a call that
+// holds large scratch can split the pool's free space so that the next
+// call's scratch no longer fits and the pool maps new memory every call.
+pg_status ctx_alloc_static(pg_ctx *ctx, size_t bytes, void **ptr) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (ctx->shared) ctx_reap_frees(ctx, false);
+  if (ctx->budget && ctx->in_use + bytes > ctx->budget) return PG_ERR_OOM;
+  if (ctx->shared && !budget_try_charge(ctx->shared, bytes)) return PG_ERR_OOM;
+  if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    if (ctx->shared) budget_release(ctx->shared, bytes);
+    return PG_ERR_OOM;
+  }
+  ctx->in_use += bytes;
+  return PG_OK;
+}
+
+void ctx_free_static(pg_ctx *ctx, void *ptr, size_t bytes) {
+  if (!ptr) return;
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  cudaFree(ptr);  // waits for the device
+  ctx->in_use = ctx->in_use >= bytes ? ctx->in_use - bytes : 0;
+  if (ctx->shared) budget_release(ctx->shared, bytes);
+}
+
 void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes) {
   if (!ptr) return;
   if (bytes == 0) bytes = 256;
@@ -1562,7 +1592,8 @@ void pg_free(void *handle) {
         for (int e = 0; e < 2; ++e)
           for (int o = 0; o < 3; ++o)
             for (int c = 0; c < 3; ++c)
-              if (n->layers[i].bimg[e][o][c]) ctx_free(b->ctx, n->layers[i].bimg[e][o][c], n->layers[i].bimg_bytes[e][o][c]);
+              if (n->layers[i].bimg[e][o][c])
+                ctx_free_static(b->ctx, n->layers[i].bimg[e][o][c], n->layers[i].bimg_bytes[e][o][c]);
       }
       break;
     }

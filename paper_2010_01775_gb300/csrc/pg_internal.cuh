@@ -250,6 +250,8 @@ namespace pgi {
 // ---------------------------------------------------------------- memory
 pg_status ctx_alloc(pg_ctx *ctx, size_t bytes, void **ptr);
 void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes);
+pg_status ctx_alloc_static(pg_ctx *ctx, size_t bytes, void **ptr);
+void ctx_free_static(pg_ctx *ctx, void *ptr, size_t bytes);
 // Returns to the shared budget the bytes of every free that has run on the
 // GPU (all of them when `all`, which waits for the context's stream).
 void ctx_reap_frees(pg_ctx *ctx, bool all);
