@@ -86,7 +86,8 @@ struct TcArgs {
   uint32_t bytes_a, bytes_b;  // per stage (A rounded up to 1 KB in mode 2)
   uint32_t tx_bytes;          // bytes the TMA copies of one stage deliver
   int chunk_bytes;            // bytes of one operand row (the swizzle row)
-  int stage_out;              // epilogue stores staged through shared memory (coalesced)
+  int stage_out;              // epilogue stores: 0 direct, 1 staged through shared memory (coalesced),
+                              // 2 staged and written by bulk async copies (dense rows of 64-byte pixels)
   uint32_t idesc;
   uint32_t sbo;
   int swz;
@@ -379,6 +380,42 @@ __device__ __forceinline__ void store_staged(const TcArgs &a, uint8_t *stg, cons
     }
   }
   __syncwarp();
+}
+
+// Bulk output of one work item (mode 2, a dense output of 32 BF16 channels:
+// every pixel is 64 contiguous bytes, and consecutive valid positions of a
+// padded row are consecutive pixels).  Each lane puts its pixel into the
+// warp's staging buffer; every lane that starts a run of consecutive valid
+// pixels then writes the run with one bulk async copy, so the global stores
+// leave the epilogue's critical path.  A lane waits for the shared-memory
+// reads of its earlier copies before the buffer is rewritten.
+__device__ __forceinline__ void store_bulk(uint8_t *stg, const uint4 *chunk, size_t pix0, bool valid, int lane,
+                                           uint8_t *out) {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncwarp();
+  // Chunk k of the pixel goes out in round (k - lane) mod 4, so that lanes
+  // L and L + 1 of an 8-lane phase hit different banks.
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int kk = (k + lane) & 3;
+    const uint4 v = kk == 0 ? chunk[0] : (kk == 1 ? chunk[1] : (kk == 2 ? chunk[2] : chunk[3]));
+    *reinterpret_cast<uint4 *>(stg + lane * 64 + kk * 16) = v;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  const unsigned vmask = __ballot_sync(0xFFFFFFFFu, valid);
+  const unsigned long long prev = __shfl_up_sync(0xFFFFFFFFu, (unsigned long long)pix0, 1);
+  const bool start = valid && (lane == 0 || !((vmask >> (lane - 1)) & 1u) || prev + 1ull != (unsigned long long)pix0);
+  const unsigned smask = __ballot_sync(0xFFFFFFFFu, start);
+  if (start) {
+    const unsigned brk = (smask | ~vmask) & ~((2u << lane) - 1u);  // lanes after this one that end the run
+    const int end = (lane == 31 || brk == 0u) ? 32 : __ffs(brk) - 1;
+    const uint32_t bytes = (uint32_t)(end - lane) * 64u;
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(out + pix0 * 64ull),
+                 "r"(saddr(stg + lane * 64)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
 }
 
 // Descriptor words and offsets of one pipeline stage (see the MMA issuer).
@@ -914,7 +951,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         epi_convert16<kFp8Out, kCalib>(a, r, eb, c, amax_local, chunk, ps, resp);
         cpp = kFp8Out ? 1 : 2;
       }
-      if (a.stage_out)
+      if (a.stage_out == 2 && cpp == 4)
+        store_bulk(s_stage + (warp - 2) * 2048, chunk, pix0, valid, lane, (uint8_t *)a.out);
+      else if (a.stage_out)
         store_staged(a, s_stage + (warp - 2) * 2048, chunk, cpp, c, pix0, valid, Wo, reps, lane, kFp8Out ? 1 : 2);
       else if (valid)
         store_direct(a, chunk, cpp, c, pix0, Wo, reps, kFp8Out ? 1 : 2);
@@ -923,6 +962,8 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
+    // Bulk output copies complete before the CTA exits.
+    if (a.stage_out == 2) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     if (a.stats && lane == 0 && warp == 2) {
       atomicAdd(&a.stats[5], (unsigned long long)epi_wait);
       atomicAdd(&a.stats[6], (unsigned long long)(clock64() - epi_t0));
@@ -1306,6 +1347,12 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   int per_sm = cfg.ctas > 0 ? std::min(cfg.ctas, max_ctas) : std::min(2, max_ctas);
   const size_t stage_bytes = a.bytes_a + a.bytes_b;
   a.stage_out = (cfg.so && !L.head_y) ? 1 : 0;
+  // Bulk stores: padded-row tiles of a dense 32-channel BF16 output, with
+  // work items of all 32 columns (two or more subtiles); other layers asked
+  // for them take the staged stores.
+  if (cfg.so == 2 && a.halo == 2 && a.mt >= 2 && es == 2 && !fp8_out && L.Cout == 32 && L.out_cs == 32 &&
+      L.out_co == 0 && !L.ups && !L.head_y && !L.pscale && !L.res && !L.amax)
+    a.stage_out = 2;
   // align, barriers, per-expert bias + head and ranges, staging, reserve
   const size_t head_n = L.head_y ? (size_t)L.Cout + 1 : 0;
   const size_t bias_head = 4 * (size_t)L.n_exp * ((size_t)L.Cout + head_n) + 4 * (L.n_exp + 1) + 16;
@@ -1608,7 +1655,7 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   // The phase form (operand mode 3) is the only mode of its layers, with
   // one to four output phases per tile.
   const std::vector<int> halos = L.in_u ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
-  for (int so : {0, 1})
+  for (int so : {0, 1, 2})
   for (int halo : halos)
   for (int cb : {128, 64, 32})
   for (int mt : {1, 2, 4})
@@ -1616,6 +1663,11 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
     for (int stages : {2, 3, 4, 6, 8, 12, 16}) {
       if (halo && stages > 6) continue;
       if (mt == 4 && halo < 2) continue;  // four subtiles: the padded-row modes only
+      // Bulk stores serve padded-row layers with dense 32-channel BF16
+      // outputs; elsewhere they would repeat the staged candidate.
+      if (so == 2 && !(halo == 2 && mt >= 2 && es == 2 && !fp8 && L.Cout == 32 && L.out_cs == 32 && L.out_co == 0 &&
+                       !L.ups && !L.head_y && !L.pscale && !L.res && !L.amax))
+        continue;
       if (!halo && cb != 128 && stages < 3) continue;
       TcCfg c;
       c.ctas = ctas;
