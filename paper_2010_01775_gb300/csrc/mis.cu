@@ -141,7 +141,9 @@ __global__ void k_mis_sample(const float *__restrict__ pos, const float *__restr
     const int j = first_above_seg(tb.Fphi + row * tb.W, tb.Sphi ? tb.Sphi + row * (tb.W >> 3) : nullptr, tb.W, u1);
     const float z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
     const float ph = ((float)j + u3) * (2.0f / (float)tb.W);  // angle pi * ph
-    const float stz = sqrtf(fmaxf(0.0f, 1.0f - z * z));
+    // sin(theta) from (1 + z)(1 - z), each factor formed without cancellation.
+    const float zp = ((float)i + u2) * (2.0f / (float)tb.H), zm = ((float)(tb.H - i) - u2) * (2.0f / (float)tb.H);
+    const float stz = sqrtf(fmaxf(0.0f, zp * zm));
     float sn, cs;
     sincospif(ph, &sn, &cs);
     dx = stz * cs;

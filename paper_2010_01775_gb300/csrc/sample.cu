@@ -86,9 +86,12 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc,
   float u0 = (float)(r.x >> 8) * k24, u1 = (float)(r.y >> 8) * k24;
   float u2 = (float)(r.z >> 8) * k24, u3 = (float)(r.w >> 8) * k24;
   float z, phi, p;
+  float zp, zm;  // 1 + z and 1 - z, each formed without cancellation
   uint32_t lo, bo;
   if (s < 0 || !__ldg(tb.valid + s)) {
     z = 1.0f - 2.0f * u0;
+    zp = 2.0f * (1.0f - u0);
+    zm = 2.0f * u0;
     phi = 2.0f * u1;
     p = tb.pdf_uniform;
     lo = l | 0x80000000u;
@@ -100,14 +103,19 @@ __global__ void k_sample(const float *__restrict__ pos, uint64_t q, QueryCtx qc,
     const size_t row = (size_t)s * tb.H + i;
     const int j = first_above_seg(tb.Fphi + row * tb.W, tb.Sphi ? tb.Sphi + row * (tb.W >> 3) : nullptr, tb.W, u1);
     z = -1.0f + ((float)i + u2) * (2.0f / (float)tb.H);
+    zp = ((float)i + u2) * (2.0f / (float)tb.H);
+    zm = ((float)(tb.H - i) - u2) * (2.0f / (float)tb.H);
     phi = ((float)j + u3) * (2.0f / (float)tb.W);  // in half turns: the angle is pi * phi
     p = __ldg(tb.P + (size_t)s * HW + (size_t)i * tb.W + j) * tb.pdf_scale;
     lo = l;
     bo = (uint32_t)(i * tb.W + j);
   }
-  // sin and cos of pi * phi (the argument reduction of sincospif is exact,
-  // cheaper and more accurate than reducing 2 pi-scaled radians).
-  float st = sqrtf(fmaxf(0.0f, 1.0f - z * z)), sn, cs;
+  // sin(theta) = sqrt((1 + z)(1 - z)) from factors each accurate to a few
+  // ulps relative, so the in-plane part keeps its relative accuracy near the
+  // poles (1 - z * z would lose it to cancellation); sin and cos of pi * phi
+  // (the argument reduction of sincospif is exact, cheaper and more accurate
+  // than reducing 2 pi-scaled radians).
+  float st = sqrtf(fmaxf(0.0f, zp * zm)), sn, cs;
   sincospif(phi, &sn, &cs);
   dir[3 * t] = st * cs;
   dir[3 * t + 1] = st * sn;
