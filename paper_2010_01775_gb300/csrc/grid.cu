@@ -13,6 +13,10 @@
 //                   bottom-up leaf counts and top-down offsets put the leaves
 //                   in Morton order without sorting them
 //   k_leaf_assign   per photon: leaf id by binary search of leaf start codes (a4)
+//   k_tree_all      the same tree in one cooperative launch:
+//                   the levels and phases follow one another through bounded
+//                   grid-wide barriers (the per-level launches remain the
+//                   fallback where cooperative launches are unavailable)
 #include <cuda.h>
 #include <math.h>
 #include <string.h>
@@ -239,9 +243,34 @@ struct Tree {
   uint32_t *nleaf;   // leaves in the subtree
   uint32_t *off;     // Morton rank of the subtree's first leaf
   uint32_t *level_start, *level_count;  // [17]
-  uint32_t *counters;  // [0] = L, [1] = A
+  uint32_t *counters;  // [0] = L, [1] = A, [2] = barrier timeout of the single-launch form
   uint32_t cap;
 };
+
+// Loads of tree data.  The per-level kernels read what earlier launches
+// wrote (plain loads); the single cooperative launch reads what other
+// blocks of the same launch wrote, so it goes around the L1 (ld.global.cg).
+struct PlainLoad {
+  template <class T>
+  __device__ static T ld(const T *p) { return *p; }
+};
+struct L2Load {
+  __device__ static uint32_t ld(const uint32_t *p) { return __ldcg(p); }
+  __device__ static int32_t ld(const int32_t *p) { return __ldcg(p); }
+  __device__ static uint64_t ld(const uint64_t *p) {
+    return (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(p));
+  }
+};
+
+__device__ __forceinline__ void tree_init_cell(const uint64_t *__restrict__ sorted, uint32_t n, int D, int min_depth,
+                                               const Tree &t, uint32_t c) {
+  const uint32_t ncell = 1u << (3 * min_depth);
+  const int shift = 3 * (D - min_depth);
+  t.code[c] = c;
+  t.begin[c] = lower_bound_u64(sorted, n, (uint64_t)c << shift);
+  t.end[c] = (c + 1 == ncell) ? n : lower_bound_u64(sorted, n, (uint64_t)(c + 1) << shift);
+  t.child[c] = -1;
+}
 
 __global__ void k_tree_init(const uint64_t *__restrict__ sorted, uint32_t n, int D, int min_depth, Tree t) {
   uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,22 +280,19 @@ __global__ void k_tree_init(const uint64_t *__restrict__ sorted, uint32_t n, int
     t.level_count[min_depth] = ncell;
   }
   if (c >= ncell) return;
-  int shift = 3 * (D - min_depth);
-  t.code[c] = c;
-  t.begin[c] = lower_bound_u64(sorted, n, (uint64_t)c << shift);
-  t.end[c] = (c + 1 == ncell) ? n : lower_bound_u64(sorted, n, (uint64_t)(c + 1) << shift);
-  t.child[c] = -1;
+  tree_init_cell(sorted, n, D, min_depth, t, c);
 }
 
 // Level d: a cell splits when count > thr and d < D.  Lanes 8j..8j+7 of a
-// warp serve one cell: lane k finds the first photon of child k.
-__global__ void k_tree_split(const uint64_t *__restrict__ sorted, int D, int d, uint32_t thr, Tree t,
-                             uint32_t *status) {
-  uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+// warp serve one cell: lane k finds the first photon of child k.  Called by
+// whole warps (shuffles); gid is the lane's index over the level's 8 cnt
+// lanes.
+template <class Ld>
+__device__ __forceinline__ void tree_split_lane(const uint64_t *__restrict__ sorted, int D, int d, uint32_t thr,
+                                                const Tree &t, uint32_t *status, uint32_t gid, uint32_t cnt,
+                                                uint32_t lstart) {
   uint32_t rel = gid >> 3;
   int k = gid & 7;
-  uint32_t cnt = t.level_count[d];
-  uint32_t lstart = t.level_start[d];
   if (gid == 0) t.level_start[d + 1] = lstart + cnt;
   bool in = rel < cnt;
   uint32_t c = lstart + rel;
@@ -274,9 +300,9 @@ __global__ void k_tree_split(const uint64_t *__restrict__ sorted, int D, int d, 
   bool split = false;
   uint64_t code = 0;
   if (in) {
-    b = t.begin[c];
-    e = t.end[c];
-    code = t.code[c];
+    b = Ld::ld(t.begin + c);
+    e = Ld::ld(t.end + c);
+    code = Ld::ld(t.code + c);
     split = (e - b > thr) && d < D;
   }
   uint32_t base = 0xFFFFFFFFu;
@@ -306,18 +332,29 @@ __global__ void k_tree_split(const uint64_t *__restrict__ sorted, int D, int d, 
   }
 }
 
-__global__ void k_tree_count(int d, Tree t) {
-  uint32_t rel = blockIdx.x * blockDim.x + threadIdx.x;
-  if (rel >= t.level_count[d]) return;
-  uint32_t c = t.level_start[d] + rel;
-  int32_t ch = t.child[c];
+__global__ void k_tree_split(const uint64_t *__restrict__ sorted, int D, int d, uint32_t thr, Tree t,
+                             uint32_t *status) {
+  tree_split_lane<PlainLoad>(sorted, D, d, thr, t, status, blockIdx.x * blockDim.x + threadIdx.x, t.level_count[d],
+                             t.level_start[d]);
+}
+
+template <class Ld>
+__device__ __forceinline__ void tree_count_cell(int d, const Tree &t, uint32_t rel) {
+  uint32_t c = Ld::ld(t.level_start + d) + rel;
+  int32_t ch = Ld::ld(t.child + c);
   uint32_t s = 1;
   if (ch >= 0) {
     s = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s += t.nleaf[ch + k];
+    for (int k = 0; k < 8; ++k) s += Ld::ld(t.nleaf + ch + k);
   }
   t.nleaf[c] = s;
+}
+
+__global__ void k_tree_count(int d, Tree t) {
+  uint32_t rel = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rel >= t.level_count[d]) return;
+  tree_count_cell<PlainLoad>(d, t, rel);
 }
 
 __global__ void __launch_bounds__(1024) k_tree_root_offsets(int min_depth, Tree t) {
@@ -333,26 +370,33 @@ __global__ void __launch_bounds__(1024) k_tree_root_offsets(int min_depth, Tree 
   if (threadIdx.x == 0) t.counters[0] = carry;
 }
 
+template <class Ld>
+__device__ __forceinline__ void tree_offsets_cell(int D, int d, const Tree &t, uint32_t rel,
+                                                  uint64_t *__restrict__ leaf_code, int32_t *__restrict__ leaf_depth,
+                                                  uint32_t *__restrict__ leaf_begin, uint32_t *__restrict__ leaf_end) {
+  uint32_t c = Ld::ld(t.level_start + d) + rel;
+  int32_t ch = Ld::ld(t.child + c);
+  uint32_t o = Ld::ld(t.off + c);
+  if (ch >= 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      t.off[ch + k] = o;
+      o += Ld::ld(t.nleaf + ch + k);
+    }
+  } else {
+    leaf_code[o] = Ld::ld(t.code + c) << (3 * (D - d));
+    leaf_depth[o] = d;
+    leaf_begin[o] = Ld::ld(t.begin + c);
+    leaf_end[o] = Ld::ld(t.end + c);
+  }
+}
+
 __global__ void k_tree_offsets(int D, int d, Tree t, uint64_t *__restrict__ leaf_code,
                                int32_t *__restrict__ leaf_depth, uint32_t *__restrict__ leaf_begin,
                                uint32_t *__restrict__ leaf_end) {
   uint32_t rel = blockIdx.x * blockDim.x + threadIdx.x;
   if (rel >= t.level_count[d]) return;
-  uint32_t c = t.level_start[d] + rel;
-  int32_t ch = t.child[c];
-  uint32_t o = t.off[c];
-  if (ch >= 0) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      t.off[ch + k] = o;
-      o += t.nleaf[ch + k];
-    }
-  } else {
-    leaf_code[o] = t.code[c] << (3 * (D - d));
-    leaf_depth[o] = d;
-    leaf_begin[o] = t.begin[c];
-    leaf_end[o] = t.end[c];
-  }
+  tree_offsets_cell<PlainLoad>(D, d, t, rel, leaf_code, leaf_depth, leaf_begin, leaf_end);
 }
 
 // Active leaves (>= 1 photon) get consecutive map slots in leaf order.
@@ -391,6 +435,106 @@ __global__ void k_scene_leaves(const uint64_t *__restrict__ leaf_code, const uin
   if (s > S) return;
   const uint32_t L = counters[0];
   out[s] = (s == S && full) ? L : find_leaf(leaf_code, L, (uint64_t)s << shift);
+}
+
+// ---------------------------------------------------------------- a3 in one launch
+// The whole tree in one cooperative launch (every block resident): the
+// levels and phases follow one another through grid-wide barriers instead
+// of one launch per level and phase.
+struct TreeAll {
+  const uint64_t *sorted;
+  uint32_t n;
+  int D, dmin;
+  uint32_t thr;
+  Tree t;
+  uint64_t *leaf_code;
+  int32_t *leaf_depth;
+  uint32_t *leaf_begin, *leaf_end;
+  uint32_t *barrier;   // one zeroed arrival counter per barrier
+  uint32_t *status;    // the context's status word (capacity, as the per-level launches)
+  uint32_t *timeout;   // ST_TIMEOUT when a barrier gave up (read back by the host)
+};
+
+__device__ __forceinline__ unsigned long long grid_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier k: thread 0 of every block arrives and waits until all
+// blocks have, at most about a second; then it sets ST_TIMEOUT and the
+// block gives up (returns false).  The fences make the blocks' writes before
+// the barrier visible to the loads after it.
+__device__ bool grid_barrier(uint32_t *counters, int k, uint32_t *status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counters + k, 1u);
+    ok = 1;
+    const unsigned long long t0 = grid_globaltimer();
+    for (uint32_t it = 0; *(volatile uint32_t *)(counters + k) < gridDim.x; ++it) {
+      if ((it & 255u) == 255u && grid_globaltimer() - t0 > 1000000000ull) {
+        atomicOr(status, ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) k_tree_all(TreeAll p) {
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  const Tree &t = p.t;
+  int bk = 0;
+  const uint32_t ncell0 = 1u << (3 * p.dmin);
+  if (tid == 0) {
+    t.level_start[p.dmin] = 0;
+    t.level_count[p.dmin] = ncell0;
+  }
+  for (uint32_t c = tid; c < ncell0; c += nth) tree_init_cell(p.sorted, p.n, p.D, p.dmin, t, c);
+  if (!grid_barrier(p.barrier, bk++, p.timeout)) return;
+  // Top-down splits, one level per barrier, until a level is empty or at
+  // the maximum depth (whose cells never split).
+  int dlast = p.dmin;
+  for (int d = p.dmin; d < p.D; ++d) {
+    const uint32_t cnt = L2Load::ld(t.level_count + d), lstart = L2Load::ld(t.level_start + d);
+    if (cnt == 0) break;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < 8u * cnt; base += nth)
+      tree_split_lane<L2Load>(p.sorted, p.D, d, p.thr, t, p.status, base + threadIdx.x, cnt, lstart);
+    if (!grid_barrier(p.barrier, bk++, p.timeout)) return;
+    if (L2Load::ld(t.level_count + d + 1) == 0) break;
+    dlast = d + 1;
+  }
+  // Bottom-up leaf counts.
+  for (int d = dlast; d >= p.dmin; --d) {
+    const uint32_t cnt = L2Load::ld(t.level_count + d);
+    for (uint32_t r = tid; r < cnt; r += nth) tree_count_cell<L2Load>(d, t, r);
+    if (!grid_barrier(p.barrier, bk++, p.timeout)) return;
+  }
+  // Offsets of the initial cells (one block), then top-down.
+  if (blockIdx.x == 0) {
+    __shared__ uint32_t sh[32];
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < ncell0; base += blockDim.x) {
+      uint32_t i = base + threadIdx.x, tot;
+      uint32_t v = i < ncell0 ? L2Load::ld(t.nleaf + i) : 0u;
+      uint32_t pre = block_excl_scan(v, &tot, sh);
+      if (i < ncell0) t.off[i] = carry + pre;
+      carry += tot;
+    }
+    if (threadIdx.x == 0) t.counters[0] = carry;
+  }
+  if (!grid_barrier(p.barrier, bk++, p.timeout)) return;
+  for (int d = p.dmin; d <= dlast; ++d) {
+    const uint32_t cnt = L2Load::ld(t.level_count + d);
+    for (uint32_t r = tid; r < cnt; r += nth)
+      tree_offsets_cell<L2Load>(p.D, d, t, r, p.leaf_code, p.leaf_depth, p.leaf_begin, p.leaf_end);
+    if (!grid_barrier(p.barrier, bk++, p.timeout)) return;
+  }
 }
 
 // ---------------------------------------------------------------- a4
@@ -483,7 +627,7 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   const int passes = (3 * D + 7) / 8;
   const uint32_t nblocks = n ? ceil_div(n, kSortTile) : 0;
   size_t s_k = align256(8ull * n), s_v = align256(4ull * n), s_h = align256(4ull * kRadix * (nblocks + 1));
-  size_t s_dt = align256(4 * kRadix), s_c8 = align256(8 * cap), s_c4 = align256(4 * cap), s_lv = align256(4 * 64);
+  size_t s_dt = align256(4 * kRadix), s_c8 = align256(8 * cap), s_c4 = align256(4 * cap), s_lv = align256(4 * 128);
   size_t scratch_bytes = 2 * s_k + s_v + s_h + s_dt + s_c8 + 5 * s_c4 + s_lv;
   void *scratch = nullptr;
   pg_status rs = ctx_alloc(ctx, scratch_bytes, &scratch);
@@ -509,7 +653,8 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   t.level_count = t.level_start + 20;
   t.counters = t.level_count + 20;
   t.cap = (uint32_t)cap;
-  PG_CUDA(cudaMemsetAsync(t.level_start, 0, 4 * 64, st));
+  uint32_t *barriers = t.level_start + 64;  // arrival counters of the cooperative launch's barriers
+  PG_CUDA(cudaMemsetAsync(t.level_start, 0, 4 * 128, st));
 
   GridGeom gg = geom_of(g);
   const int TB = 256;
@@ -547,8 +692,41 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
     sorted = kin;
   }
 
-  // a3: tree, level by level.
+  // a3: the tree in one cooperative launch where the device allows it
+  // (PG_GRID_LEVEL_LAUNCHES=1 forces the per-level launches below).
+  bool coop = false;
   {
+    int dev = 0, can = 0, occ = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && can &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tree_all, 256, 0) == cudaSuccess && occ > 0 &&
+        !getenv("PG_GRID_LEVEL_LAUNCHES")) {
+      TreeAll pa;
+      pa.sorted = sorted;
+      pa.n = n;
+      pa.D = D;
+      pa.dmin = dmin;
+      pa.thr = thr;
+      pa.t = t;
+      pa.leaf_code = g->leaf_code;
+      pa.leaf_depth = g->leaf_depth;
+      pa.leaf_begin = g->leaf_begin;
+      pa.leaf_end = g->leaf_end;
+      pa.barrier = barriers;
+      pa.status = ctx->d_status;
+      pa.timeout = t.counters + 2;
+      void *args[] = {&pa};
+      const int blocks = sms;  // one block per SM: the barriers wait for fewer arrivals
+      if (cudaLaunchCooperativeKernel((const void *)k_tree_all, blocks, 256, args, 0, st) == cudaSuccess) {
+        PG_COUNT(ctx);
+        coop = true;
+      }
+    }
+    cudaGetLastError();
+  }
+  if (!coop) {
+    // a3: tree, level by level.
     uint32_t ncell0 = 1u << (3 * dmin);
     k_tree_init<<<ceil_div(ncell0, TB), TB, 0, st>>>(sorted, n, D, dmin, t), PG_COUNT(ctx);
     // Levels whose cell bound is zero cannot hold cells (no launch).
@@ -562,8 +740,8 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
     for (int d = dmin; d <= D && bound[d]; ++d)
       k_tree_offsets<<<ceil_div(bound[d], TB), TB, 0, st>>>(D, d, t, g->leaf_code, g->leaf_depth, g->leaf_begin,
                                                              g->leaf_end), PG_COUNT(ctx);
-    k_active<<<1, 1024, 0, st>>>(t, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf), PG_COUNT(ctx);
   }
+  k_active<<<1, 1024, 0, st>>>(t, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf), PG_COUNT(ctx);
   // a4: leaf of every photon.
   if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of), PG_COUNT(ctx);
   k_leaf_lut<<<ceil_div(lut_cells, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * (D - g->lut_depth), lut_cells,
@@ -572,11 +750,12 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
                                                      S == (1u << (3 * SL)), g->scene_leaf_begin), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
 
-  uint32_t hc[2], status = 0;
-  PG_CUDA(cudaMemcpyAsync(hc, t.counters, 8, cudaMemcpyDeviceToHost, st));
+  uint32_t hc[3], status = 0;
+  PG_CUDA(cudaMemcpyAsync(hc, t.counters, 12, cudaMemcpyDeviceToHost, st));
   PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
   PG_CUDA(cudaStreamSynchronize(st));
   if (status & ST_CAPACITY) return PG_ERR_UNSUPPORTED;
+  if (hc[2] & ST_TIMEOUT) return PG_ERR_TIMEOUT;
   if (status & ST_INVALID_INPUT) {
     PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
     PG_CUDA(cudaStreamSynchronize(st));

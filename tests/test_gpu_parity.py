@@ -67,6 +67,22 @@ def test_grid_bit_exact(ctx, n, blobs, D, min_depth, thr, seed):
     g.free()
 
 
+@pytest.mark.parametrize("n,blobs,D,min_depth,thr,seed", [(100_000, 8, 4, 0, 1000, 51), (77_777, 5, 10, 0, 300, 52),
+                                                       (4097, 3, 6, 2, 20, 53), (513, 2, 16, 0, 5, 54)])
+def test_grid_per_level_launches_equal_the_single_launch(ctx, n, blobs, D, min_depth, thr, seed):
+    # The tree as one cooperative launch (default) and as one launch per
+    # level and phase: both equal the oracle's grid bit for bit.
+    ph = synth.photons(n, blobs, seed)
+    os.environ["PG_GRID_LEVEL_LAUNCHES"] = "1"
+    try:
+        g, got, ref, _ = _grid_case(ctx, ph, D, min_depth, thr)
+    finally:
+        del os.environ["PG_GRID_LEVEL_LAUNCHES"]
+    _assert_grid_equal(got, ref)
+    g2, got2, _, _ = _grid_case(ctx, ph, D, min_depth, thr)
+    _assert_grid_equal(got2, ref)
+
+
 def test_grid_empty_and_odd_domain(ctx):
     g, got, ref, _ = _grid_case(ctx, np.zeros((0, 8), np.float32), 3, 1, 10)
     _assert_grid_equal(got, ref)
