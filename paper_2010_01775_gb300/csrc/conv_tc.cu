@@ -269,12 +269,70 @@ __device__ __forceinline__ int tile_expert(const TcArgs &a, const int *s_range, 
 // (its ~1e-7 absolute error is far below a BF16 or E4M3 output's rounding).
 __device__ __forceinline__ float elu_lp(float v) { return v > 0.0f ? v : __expf(v) - 1.0f; }
 
+// 2^x by the PTX ex2.approx instruction (relative error at most 2^-22,
+// subnormal results flushed to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// e^v - 1 of two values on packed FP32 pairs: e^v = 2^(v log2 e), one
+// multiply and one add for both values.
+__device__ __forceinline__ float2 expm1_pair(float2 v) {
+  constexpr float kLog2e = 1.4426950408889634f;
+  const float2 u = __fmul2_rn(v, make_float2(kLog2e, kLog2e));
+  return __fadd2_rn(make_float2(ex2_approx(u.x), ex2_approx(u.y)), make_float2(-1.0f, -1.0f));
+}
+
+// ELU of two values without a branch: e^v - 1 >= v for every v, so
+// min(e^v - 1, max(v, 0)) is v above zero and e^v - 1 at or below it.
+__device__ __forceinline__ float2 elu_pair(float2 v) {
+  const float2 e = expm1_pair(v);
+  return make_float2(fminf(e.x, fmaxf(v.x, 0.0f)), fminf(e.y, fmaxf(v.y, 0.0f)));
+}
+
+// BF16 output of 16 accumulator columns of one pixel without partial-conv
+// scales, residuals or calibration: bias add and the ELU's arithmetic on
+// packed FP32 pairs (one instruction per two columns), and the ELU's min/max
+// on packed BF16 pairs after the conversion (rounding to BF16 is monotone,
+// so min and max commute with it).
+__device__ __forceinline__ void epi_bf16_pairs(const TcArgs &a, const uint32_t *r, const float *bias, uint4 *chunk) {
+  const float2 m2 = make_float2(a.acc_mul, a.acc_mul);
+  const __nv_bfloat162 zero2 = __float2bfloat162_rn(0.0f);
+  uint32_t w[8];
+#pragma unroll
+  for (int j = 0; j < 8; j += 2) {
+    const float4 b = *reinterpret_cast<const float4 *>(bias + 2 * j);
+    float2 v[2];
+    v[0] = __ffma2_rn(make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1])), m2,
+                      make_float2(b.x, b.y));
+    v[1] = __ffma2_rn(make_float2(__uint_as_float(r[2 * j + 2]), __uint_as_float(r[2 * j + 3])), m2,
+                      make_float2(b.z, b.w));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      __nv_bfloat162 o = __floats2bfloat162_rn(v[h].x, v[h].y);
+      if (a.act == 1) {
+        const float2 e = expm1_pair(v[h]);
+        o = __hmin2(__floats2bfloat162_rn(e.x, e.y), __hmax2(o, zero2));
+      }
+      w[j + h] = *reinterpret_cast<uint32_t *>(&o);
+    }
+  }
+  chunk[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  chunk[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
 // Bias + activation + conversion of 16 accumulator columns of one pixel into
 // output bytes: one 16-byte chunk (E4M3) or two (BF16).
 template <bool kFp8Out, bool kCalib>
 __device__ __forceinline__ void epi_convert16(const TcArgs &a, const uint32_t *r, const float *s_bias, int c,
                                               float &amax, uint4 *chunk, float ps = 1.0f,
                                               const __nv_bfloat16 *resp = nullptr) {
+  if (!kFp8Out && !kCalib && !a.pscale && !resp) {
+    epi_bf16_pairs(a, r, s_bias + c, chunk);
+    return;
+  }
   float v[16];
   if (a.pscale) {
     // Partial convolution: acc * scale + bias where a valid input lies under
@@ -876,9 +934,22 @@ __global__ void __launch_bounds__(kThreads, 2)
           const __nv_bfloat16 *hres =
               (a.res && valid) ? (const __nv_bfloat16 *)a.res + hpix * a.res_cs + a.res_co : nullptr;
           float hacc = 0.0f;
+          float2 hacc2 = make_float2(0.0f, 0.0f);
           for (int c = 0; c < a.BN; c += 16) {
             uint32_t r[16];
             tmem_ld16(trow + (uint32_t)c, r);
+            if (!a.pscale && !hres && !kCalib) {
+              // Bias, ELU and the head's dot product on packed FP32 pairs.
+              const float2 m2 = make_float2(a.acc_mul, a.acc_mul);
+#pragma unroll
+              for (int j = 0; j < 16; j += 2) {
+                float2 v = __ffma2_rn(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])), m2,
+                                      make_float2(eb[c + j], eb[c + j + 1]));
+                if (a.act == 1) v = elu_pair(v);
+                hacc2 = __ffma2_rn(make_float2(eh[c + j], eh[c + j + 1]), v, hacc2);
+              }
+              continue;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               float v = a.pscale ? (hps > 0.0f ? fmaf(__uint_as_float(r[j]) * a.acc_mul, hps, eb[c + j]) : 0.0f)
@@ -890,7 +961,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
           }
           if (valid) {
-            const float v = hacc + eh[a.BN];
+            const float v = hacc + (hacc2.x + hacc2.y) + eh[a.BN];
             a.head_y[((size_t)leaf * a.Hout + y) * a.Wout + x] = fmaxf(v, 0.0f) + log1pf(__expf(-fabsf(v)));
           }
         }
