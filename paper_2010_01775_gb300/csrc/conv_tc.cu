@@ -74,6 +74,7 @@ struct TcArgs {
   uint32_t bytes_ver;  // halo mode: bytes of one x-shifted input box (Ht + 2 rows)
   int Wt, Ht, Lt;
   int P, Hb, tpl;   // mode 2: padded row pitch, box rows, tiles per leaf
+  uint32_t p_magic;  // floor(2^32 / P) + 1: q / P = umulhi(q, p_magic) for q < 2^16 (0: divide)
   // Mode 3 (phase form of a decoder convolution over [upsample(U), S]): the
   // tile is 128 padded-row positions of the half-resolution grid (pitch P)
   // in npt of the 4 output phases (py, px), one subtile per phase; output
@@ -597,9 +598,10 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t *drain = acc_empty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  // Per expert: BN bias floats, then (fused head only) BN + 1 head floats;
+  // Per expert: BN bias floats, then (fused head only) BN head weights and
+  // the head's bias in a block of BN + 4 floats (16-byte aligned per expert);
   // then the experts' position ranges.
-  const int head_n = a.head_y ? a.BN + 1 : 0;
+  const int head_n = a.head_y ? a.BN + 4 : 0;
   float *s_bias = reinterpret_cast<float *>(((uintptr_t)(tmem_slot + 2) + 15) & ~(uintptr_t)15);  // n_exp x BN
   float *s_head = s_bias + a.n_exp * a.BN;                                                         // n_exp x head_n
   int *s_range = reinterpret_cast<int *>(s_head + a.n_exp * head_n);                              // n_exp + 1
@@ -608,8 +610,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int e = 0; e < a.n_exp; ++e) {
     for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_bias[e * a.BN + k] = a.bias[e][k];
     if (a.head_y) {
-      for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_head[e * (a.BN + 1) + k] = a.head_w[e][k];
-      if (threadIdx.x == 0) s_head[e * (a.BN + 1) + a.BN] = a.head_b[e][0];
+      for (int k = threadIdx.x; k < a.BN; k += blockDim.x) s_head[e * head_n + k] = a.head_w[e][k];
+      if (threadIdx.x == 0) s_head[e * head_n + a.BN] = a.head_b[e][0];
     }
   }
   for (int k = threadIdx.x; k <= a.n_exp; k += blockDim.x) s_range[k] = a.n_exp > 1 ? a.exp_range[k] : 0;
@@ -886,6 +888,13 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int Ho = a.Hout * reps, Wo = a.Wout * reps;
     const int cw = (a.BN % 32 == 0 && a.mt * a.BN >= 64) ? 32 : 16;  // columns per work item
     const int per_sub = a.BN / cw, items = a.mt * per_sub;
+    // Lean paths (uniform per launch): padded-row positions (mode 2) without
+    // the x2 upsample, BF16 outputs without partial-conv scales, residuals
+    // or calibration; rows found by one multiply-high instead of a division.
+    const bool lean_in = a.halo == 2 && !a.ups && a.p_magic && !kFp8Out && !kCalib && !a.pscale && !a.res;
+    const bool lean = lean_in && !a.head_y && cw == 32 && (per_sub & (per_sub - 1)) == 0 && a.stage_out < 2;
+    const bool lean_head = lean_in && a.head_y;
+    const int lg_ps = __ffs(per_sub) - 1;
     float amax_local = 0.0f;
     long long epi_wait = 0;
     const long long epi_t0 = clock64();
@@ -907,7 +916,72 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       // The tile's expert: its bias and head.
       const int te = a.n_exp > 1 ? tile_expert(a, s_range, l0) : 0;
-      const float *eb = s_bias + te * a.BN, *eh = s_head + te * (a.BN + 1);
+      const float *eb = s_bias + te * a.BN, *eh = s_head + te * head_n;
+      if (lean_head) {
+        // Fused head, one whole pixel per thread: bias, ELU and the head's
+        // dot product on FP32 pairs.
+        const float2 m2 = make_float2(a.acc_mul, a.acc_mul);
+        for (int sub = h; sub < a.mt; sub += 2) {
+          const uint32_t qq = (uint32_t)(q0 + sub * kBM + m);
+          const int y = (int)__umulhi(qq, a.p_magic), x = (int)qq - y * a.P;
+          const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN);
+          float2 hacc2 = make_float2(0.0f, 0.0f);
+          for (int c = 0; c < a.BN; c += 16) {
+            uint32_t r[16];
+            tmem_ld16(trow + (uint32_t)c, r);
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const float4 b = *reinterpret_cast<const float4 *>(eb + c + j);
+              const float4 w = *reinterpret_cast<const float4 *>(eh + c + j);
+              float2 v0 = __ffma2_rn(make_float2(__uint_as_float(r[j]), __uint_as_float(r[j + 1])), m2,
+                                     make_float2(b.x, b.y));
+              float2 v1 = __ffma2_rn(make_float2(__uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])), m2,
+                                     make_float2(b.z, b.w));
+              if (a.act == 1) {
+                v0 = elu_pair(v0);
+                v1 = elu_pair(v1);
+              }
+              hacc2 = __ffma2_rn(make_float2(w.x, w.y), v0, hacc2);
+              hacc2 = __ffma2_rn(make_float2(w.z, w.w), v1, hacc2);
+            }
+          }
+          if (y < a.Hout && x < a.Wout) {
+            const float v = (hacc2.x + hacc2.y) + eh[a.BN];
+            a.head_y[((size_t)l0 * a.Hout + y) * a.Wout + x] = fmaxf(v, 0.0f) + log1pf(__expf(-fabsf(v)));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        continue;
+      }
+      if (lean) {
+        for (int it = h; it < items; it += 2) {
+          const int sub = it >> lg_ps, c = (it & (per_sub - 1)) * 32;
+          const uint32_t qq = (uint32_t)(q0 + sub * kBM + m);
+          const int y = (int)__umulhi(qq, a.p_magic), x = (int)qq - y * a.P;
+          const bool valid = y < a.Hout && x < a.Wout;
+          uint32_t r[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * a.mt * a.BN + sub * a.BN + c), r);
+          uint4 chunk[4];
+          epi_bf16_pairs(a, r, eb + c, chunk);
+          epi_bf16_pairs(a, r + 16, eb + c + 16, chunk + 2);
+          const size_t pix0 = ((size_t)l0 * a.Hout + y) * a.Wout + x;
+          if (a.stage_out) {
+            store_staged(a, s_stage + (warp - 2) * 2048, chunk, 4, c, pix0, valid, a.Wout, 1, lane, 2);
+          } else if (valid) {
+            uint4 *o = reinterpret_cast<uint4 *>((__nv_bfloat16 *)a.out + pix0 * a.out_cs + a.out_co + c);
+            o[0] = chunk[0];
+            o[1] = chunk[1];
+            o[2] = chunk[2];
+            o[3] = chunk[3];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        continue;
+      }
       if (a.head_y) {
         // Fused head: each thread owns whole pixels (all BN channels), so
         // the two warps of a lane quarter take alternate subtiles.
@@ -1363,6 +1437,9 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     if (a.Hb > 256) return PG_ERR_UNSUPPORTED;
     a.tpl = (Hout * a.P + TP - 1) / TP;
     a.num_tiles = (int)ns * a.tpl;
+    // Exact for every position index below 2^16 and pitches up to 258
+    // (checked exhaustively on the host).
+    a.p_magic = (long)a.tpl * TP <= 65536 ? (uint32_t)((1ull << 32) / (uint64_t)a.P + 1ull) : 0u;
     const uint32_t box = (uint32_t)(a.Hb * a.P * cb);
     a.bytes_a = (box + 1023u) & ~1023u;
     a.tx_bytes = box + a.bytes_b;
@@ -1386,6 +1463,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     if (2 * a.P > 256 || 2 * a.Hb > 256) return PG_ERR_UNSUPPORTED;
     a.tpl = (a.Hout * a.P + kBM - 1) / kBM;
     a.num_tiles = (int)ns * (4 / a.npt) * a.tpl;
+    a.p_magic = (long)a.tpl * kBM <= 65536 ? (uint32_t)((1ull << 32) / (uint64_t)a.P + 1ull) : 0u;
     a.CinU = L.CinU;
     a.kS = a.cchunks;
     a.kU = L.CinU / a.chunk;
@@ -1425,7 +1503,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
       L.out_co == 0 && !L.ups && !L.head_y && !L.pscale && !L.res && !L.amax)
     a.stage_out = 2;
   // align, barriers, per-expert bias + head and ranges, staging, reserve
-  const size_t head_n = L.head_y ? (size_t)L.Cout + 1 : 0;
+  const size_t head_n = L.head_y ? (size_t)L.Cout + 4 : 0;
   const size_t bias_head = 4 * (size_t)L.n_exp * ((size_t)L.Cout + head_n) + 4 * (L.n_exp + 1) + 16;
   size_t stage_smem = 0;
   int max_stages = 0;
