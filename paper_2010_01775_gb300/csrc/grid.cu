@@ -230,6 +230,40 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *_
   }
 }
 
+// The header of a one-scene grid (photon range {0, n}, geometry {lo,
+// scale}) from kernel arguments: no host-to-device copy, which would queue
+// behind the caller's large uploads on the same copy engine.
+__global__ void k_grid_header(uint32_t *scene_begin, float *scene_geom, uint32_t n, float lo0, float lo1, float lo2,
+                              float s0, float s1, float s2) {
+  if (threadIdx.x == 0) {
+    scene_begin[0] = 0u;
+    scene_begin[1] = n;
+    scene_geom[0] = lo0;
+    scene_geom[1] = lo1;
+    scene_geom[2] = lo2;
+    scene_geom[3] = s0;
+    scene_geom[4] = s1;
+    scene_geom[5] = s2;
+  }
+}
+
+__global__ void k_zero_words(uint32_t *p, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0u;
+}
+
+// Leaf count, active count, tree flags and the status word into the
+// context's mapped host words (read after the stream synchronises).
+__global__ void k_grid_readback(const uint32_t *counters, const uint32_t *status, uint32_t *out) {
+  if (threadIdx.x == 0) {
+    volatile uint32_t *o = out;
+    o[0] = counters[0];
+    o[1] = counters[1];
+    o[2] = counters[2];
+    o[3] = *status;
+    __threadfence_system();
+  }
+}
+
 __global__ void k_iota(uint32_t *v, uint32_t n) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = i;
@@ -617,10 +651,8 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
     PG_CUDA(cudaMemcpyAsync(g->scene_begin, sb->d_begin, 4ull * (S + 1), cudaMemcpyDefault, st));
     PG_CUDA(cudaMemcpyAsync(g->scene_geom, sb->h_geom, 24ull * S, cudaMemcpyHostToDevice, st));
   } else {
-    uint32_t hb[2] = {0u, n};
-    float hg[6] = {g->lo[0], g->lo[1], g->lo[2], g->scale[0], g->scale[1], g->scale[2]};
-    PG_CUDA(cudaMemcpyAsync(g->scene_begin, hb, 8, cudaMemcpyHostToDevice, st));
-    PG_CUDA(cudaMemcpyAsync(g->scene_geom, hg, 24, cudaMemcpyHostToDevice, st));
+    k_grid_header<<<1, 32, 0, st>>>(g->scene_begin, g->scene_geom, (uint32_t)n, g->lo[0], g->lo[1], g->lo[2],
+                                     g->scale[0], g->scale[1], g->scale[2]), PG_COUNT(ctx);
   }
 
   // Scratch: sort ping-pong, digit histograms, cells.
@@ -654,7 +686,7 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   t.counters = t.level_count + 20;
   t.cap = (uint32_t)cap;
   uint32_t *barriers = t.level_start + 64;  // arrival counters of the cooperative launch's barriers
-  PG_CUDA(cudaMemsetAsync(t.level_start, 0, 4 * 128, st));
+  k_zero_words<<<1, 128, 0, st>>>(t.level_start, 128), PG_COUNT(ctx);
 
   GridGeom gg = geom_of(g);
   const int TB = 256;
@@ -750,10 +782,14 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
                                                      S == (1u << (3 * SL)), g->scene_leaf_begin), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
 
-  uint32_t hc[3], status = 0;
-  PG_CUDA(cudaMemcpyAsync(hc, t.counters, 12, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
+  // Counts and status come back through mapped host words written by a
+  // kernel, not a device-to-host copy (which would wait behind the caller's
+  // large downloads on the copy engine).
+  k_grid_readback<<<1, 32, 0, st>>>(t.counters, ctx->d_status, ctx->d_words), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
   PG_CUDA(cudaStreamSynchronize(st));
+  const uint32_t hc[3] = {ctx->h_words[0], ctx->h_words[1], ctx->h_words[2]};
+  const uint32_t status = ctx->h_words[3];
   if (status & ST_CAPACITY) return PG_ERR_UNSUPPORTED;
   if (hc[2] & ST_TIMEOUT) return PG_ERR_TIMEOUT;
   if (status & ST_INVALID_INPUT) {

@@ -448,8 +448,19 @@ pg_status pg_create(pg_ctx **out, void *stream, size_t budget) {
     delete c;
     return PG_ERR_CUDA;
   }
+  void *hw = nullptr;
+  if (cudaHostAlloc(&hw, 64, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void **)&c->d_words, hw, 0) != cudaSuccess) {
+    cudaGetLastError();
+    if (hw) cudaFreeHost(hw);
+    cudaFree(c->d_status);
+    delete c;
+    return PG_ERR_CUDA;
+  }
+  c->h_words = (volatile uint32_t *)hw;
   c->pending = new (std::nothrow) PendingFrees();
   if (!c->pending) {
+    cudaFreeHost(hw);
     cudaFree(c->d_status);
     delete c;
     return PG_ERR_OOM;
@@ -466,6 +477,7 @@ pg_status pg_destroy(pg_ctx *c) {
   for (int i = 0; i < 9; ++i)
     if (c->d_phi[i]) cudaFree(c->d_phi[i]);
   cudaFree(c->d_status);
+  cudaFreeHost((void *)c->h_words);
   for (cudaEvent_t e : c->pending->spare) cudaEventDestroy(e);
   delete c->pending;
   delete c;

@@ -239,6 +239,11 @@ struct pg_ctx {
   pgi::PendingFrees *pending;
   uint64_t launches;   // kernels launched for this context (pg_launch_count)
   uint32_t *d_status;  // device status word (pgi::ST_* bits)
+  // Mapped pinned host words that kernels write small results into (leaf
+  // counts, status), so reading them back takes no copy-engine transfer that
+  // could queue behind the caller's large copies on other streams.
+  volatile uint32_t *h_words;
+  uint32_t *d_words;
   float *d_phi[9];     // boundary-ray tables (cos, sin) per log2(W), W <= 256
 };
 
