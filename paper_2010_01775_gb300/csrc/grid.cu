@@ -153,7 +153,15 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t *__restrict__ hist,
   if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
 }
 
-template <bool kFirst>
+// Scatter of one LSD radix pass.  kMode 0: the first pass over the codes
+// (value = original index); 1: a later pass over (key, value) pairs.  The
+// packed forms sort codes of at most 32 bits as one 64-bit word (code << 32
+// | original index), so a pass moves 8 instead of 12 bytes per photon each
+// way: 2 is the first pass (codes in, packed words out), 3 a middle pass,
+// 4 the last pass (packed words in; the sorted codes and the permutation
+// out).  `shift` selects the digit of the word the pass reads from smem
+// (the packed word's for modes 2-4).
+template <int kMode>
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *__restrict__ kin,
                                                                const uint32_t *__restrict__ vin,
                                                                uint64_t *__restrict__ kout,
@@ -161,6 +169,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *_
                                                                const uint32_t *__restrict__ hist,
                                                                const uint32_t *__restrict__ digit_total,
                                                                uint32_t nblocks) {
+  constexpr bool kPacked = kMode >= 2, kVal = !kPacked;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *skey = reinterpret_cast<uint64_t *>(smem);
   uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kSortTile);
@@ -190,7 +199,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *_
     uint32_t gi = tile0 + li;
     bool ok = li < nvalid;
     key[r] = ok ? kin[gi] : ~0ull;
-    val[r] = ok ? (kFirst ? gi : vin[gi]) : 0u;
+    if (kMode == 2 && ok) key[r] = (key[r] << 32) | gi;
+    if (kVal) val[r] = ok ? (kMode == 0 ? gi : vin[gi]) : 0u;
     uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
     unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     uint32_t before = __popc(peers & ((1u << lane) - 1u));
@@ -218,15 +228,20 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t *_
     uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
     uint32_t pos = tstart[d] + whist[warp * kRadix + d] + rank[r];
     skey[pos] = key[r];
-    sval[pos] = val[r];
+    if (kVal) sval[pos] = val[r];
   }
   __syncthreads();
   for (uint32_t p = tid; p < nvalid; p += kSortThreads) {
     uint64_t k = skey[p];
     uint32_t d = (uint32_t)(k >> shift) & 255u;
     uint32_t g = gbase[d] + (p - tstart[d]);
-    kout[g] = k;
-    vout[g] = sval[p];
+    if (kMode == 4) {
+      kout[g] = k >> 32;
+      vout[g] = (uint32_t)k;
+    } else {
+      kout[g] = k;
+      if (kVal) vout[g] = sval[p];
+    }
   }
 }
 
@@ -701,8 +716,17 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
   if (n && passes == 0) {
     k_iota<<<ceil_div(n, TB), TB, 0, st>>>(g->perm, n), PG_COUNT(ctx);
   } else if (n) {
-    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
-    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    // Codes of at most 32 bits sort as packed words (code << 32 | index):
+    // one 8-byte word per photon through every pass but the last, which
+    // writes the sorted codes and the permutation.
+    const bool packed = passes >= 2 && 3 * D <= 32;
+    if (packed) {
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    }
     // Value buffers alternate so that the last pass writes g->perm.
     const uint64_t *kin = g->codes;
     const uint32_t *vin = nullptr;
@@ -710,13 +734,31 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
       uint64_t *kout = (ps & 1) ? kB : kA;
       uint32_t *vout = ((passes - 1 - ps) & 1) ? vT : g->perm;
       int shift = 8 * ps;
+      if (packed) {
+        // The first pass reads the codes themselves; the packed words carry
+        // the code's digit 32 bits higher.
+        k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, ps ? 32 + shift : shift, hist, nblocks),
+            PG_COUNT(ctx);
+        k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
+        if (ps == 0)
+          k_sort_scatter<2><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, nullptr, kout, nullptr, n, 32 + shift,
+                                                                         hist, dtot, nblocks), PG_COUNT(ctx);
+        else if (ps + 1 < passes)
+          k_sort_scatter<3><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, nullptr, kout, nullptr, n, 32 + shift,
+                                                                         hist, dtot, nblocks), PG_COUNT(ctx);
+        else
+          k_sort_scatter<4><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, nullptr, kout, g->perm, n, 32 + shift,
+                                                                         hist, dtot, nblocks), PG_COUNT(ctx);
+        kin = kout;
+        continue;
+      }
       k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
       k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
       if (ps == 0)
-        k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist, dtot,
+        k_sort_scatter<0><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist, dtot,
                                                                           nblocks), PG_COUNT(ctx);
       else
-        k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+        k_sort_scatter<1><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                            dtot, nblocks), PG_COUNT(ctx);
       kin = kout;
       vin = vout;
@@ -1257,9 +1299,9 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
     if (passes == 0) {
       k_iota<<<ceil_div(n, TB), TB, 0, st>>>(perm, n), PG_COUNT(ctx);
     } else {
-      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kScatterSmem));
-      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kScatterSmem));
       const uint64_t *kin = codes;
       const uint32_t *vin = nullptr;
@@ -1270,10 +1312,10 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
         k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
         k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
         if (ps == 0)
-          k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+          k_sort_scatter<0><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                             dtot, nblocks), PG_COUNT(ctx);
         else
-          k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+          k_sort_scatter<1><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                              dtot, nblocks), PG_COUNT(ctx);
         kin = kout;
         vin = vout;
@@ -1456,9 +1498,9 @@ pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint6
     if (passes == 0) {
       k_iota<<<ceil_div(n, TB), TB, 0, st>>>(perm, n), PG_COUNT(ctx);
     } else {
-      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kScatterSmem));
-      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kScatterSmem));
       const uint64_t *kin = codes;
       const uint32_t *vin = nullptr;
@@ -1469,10 +1511,10 @@ pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint6
         k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
         k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
         if (ps == 0)
-          k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+          k_sort_scatter<0><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                             dtot, nblocks), PG_COUNT(ctx);
         else
-          k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+          k_sort_scatter<1><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                              dtot, nblocks), PG_COUNT(ctx);
         kin = kout;
         vin = vout;
@@ -1573,9 +1615,9 @@ pg_status bin_into_grid_kd(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, ui
     if (passes == 0) {
       k_iota<<<ceil_div(n, TB), TB, 0, st>>>(perm, n), PG_COUNT(ctx);
     } else {
-      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kScatterSmem));
-      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kScatterSmem));
       const uint64_t *kin = keys;
       const uint32_t *vin = nullptr;
@@ -1586,10 +1628,10 @@ pg_status bin_into_grid_kd(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, ui
         k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, n, shift, hist, nblocks), PG_COUNT(ctx);
         k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot), PG_COUNT(ctx);
         if (ps == 0)
-          k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+          k_sort_scatter<0><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                             dtot, nblocks), PG_COUNT(ctx);
         else
-          k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
+          k_sort_scatter<1><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, n, shift, hist,
                                                                              dtot, nblocks), PG_COUNT(ctx);
         kin = kout;
         vin = vout;
@@ -1742,8 +1784,8 @@ extern "C" pg_status pg_sort_photons_noalloc(const pg_photon *d_photons, uint64_
   if (passes == 0) {
     k_iota<<<ceil_div(nn, TB), TB, 0, st>>>(d_perm, nn);
   } else {
-    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
-    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
+    PG_CUDA(cudaFuncSetAttribute(k_sort_scatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatterSmem));
     const uint32_t nblocks = ceil_div(nn, kSortTile);
     const uint64_t *kin = d_codes;
     const uint32_t *vin = nullptr;
@@ -1754,10 +1796,10 @@ extern "C" pg_status pg_sort_photons_noalloc(const pg_photon *d_photons, uint64_
       k_sort_upsweep<<<nblocks, kSortThreads, 0, st>>>(kin, nn, shift, hist, nblocks);
       k_sort_scan<<<kRadix, 1024, 0, st>>>(hist, nblocks, dtot);
       if (ps == 0)
-        k_sort_scatter<true><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, nn, shift, hist, dtot,
+        k_sort_scatter<0><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, nn, shift, hist, dtot,
                                                                           nblocks);
       else
-        k_sort_scatter<false><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, nn, shift, hist,
+        k_sort_scatter<1><<<nblocks, kSortThreads, kScatterSmem, st>>>(kin, vin, kout, vout, nn, shift, hist,
                                                                            dtot, nblocks);
       kin = kout;
       vin = vout;
