@@ -92,6 +92,8 @@ struct TcArgs {
   uint32_t idesc;
   uint32_t sbo;
   int swz;
+  uint32_t sbo_b;  // B operand's stride between 8-row groups and swizzle mode (A's, except in mode 4)
+  int swz_b;
   int mma_per_stage, mma_kind;  // 0: kind::f16, 1: kind::f8f6f4
   uint32_t tmem_cols;
   // epilogue
@@ -297,10 +299,9 @@ __device__ __forceinline__ float2 elu_pair(float2 v) {
 // scales, residuals or calibration: bias add and the ELU's arithmetic on
 // packed FP32 pairs (one instruction per two columns), and the ELU's min/max
 // on packed BF16 pairs after the conversion (rounding to BF16 is monotone,
-// so min and max commute with it).
+// so min and max commute with it; the max with 0 is the conversion's .relu).
 __device__ __forceinline__ void epi_bf16_pairs(const TcArgs &a, const uint32_t *r, const float *bias, uint4 *chunk) {
   const float2 m2 = make_float2(a.acc_mul, a.acc_mul);
-  const __nv_bfloat162 zero2 = __float2bfloat162_rn(0.0f);
   uint32_t w[8];
 #pragma unroll
   for (int j = 0; j < 8; j += 2) {
@@ -312,10 +313,15 @@ __device__ __forceinline__ void epi_bf16_pairs(const TcArgs &a, const uint32_t *
                       make_float2(b.z, b.w));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      __nv_bfloat162 o = __floats2bfloat162_rn(v[h].x, v[h].y);
+      __nv_bfloat162 o;
       if (a.act == 1) {
+        // max(v, 0) comes from the conversion itself (cvt .relu).
+        uint32_t pos;
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(pos) : "f"(v[h].y), "f"(v[h].x));
         const float2 e = expm1_pair(v[h]);
-        o = __hmin2(__floats2bfloat162_rn(e.x, e.y), __hmax2(o, zero2));
+        o = __hmin2(__floats2bfloat162_rn(e.x, e.y), *reinterpret_cast<const __nv_bfloat162 *>(&pos));
+      } else {
+        o = __floats2bfloat162_rn(v[h].x, v[h].y);
       }
       w[j + h] = *reinterpret_cast<uint32_t *>(&o);
     }
@@ -483,6 +489,7 @@ struct StageOps {
   int off0, P;
   uint32_t cb, sub_step, row_step, ver16, tap_b16, desc_hi, idesc;
   bool first;
+  uint32_t desc_hi_b;  // B descriptor's high word (A's, except in mode 4)
   int sub;  // the 128-row subtile (and accumulator) this issuing lane owns
   uint32_t box_a;  // mode 3: bytes between the parity sub-grid boxes
 };
@@ -499,7 +506,7 @@ __device__ __forceinline__ void issue_stage(const StageOps &o) {
     const uint32_t a0 = o.alo + (uint32_t)o.sub * o.sub_step;
 #pragma unroll
     for (int j = 0; j < kMPS; ++j)
-      mma_issue<kFp8>(d, a0 + 2u * j, o.desc_hi, o.blo + 2u * j, o.desc_hi, o.idesc, (o.first && j == 0) ? 0u : 1u);
+      mma_issue<kFp8>(d, a0 + 2u * j, o.desc_hi, o.blo + 2u * j, o.desc_hi_b, o.idesc, (o.first && j == 0) ? 0u : 1u);
   } else {
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky) {
@@ -521,7 +528,7 @@ __device__ __forceinline__ void issue_stage(const StageOps &o) {
 #pragma unroll
         for (int j = 0; j < kMPS; ++j) {
           const uint32_t acc = (o.first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
-          mma_issue<kFp8>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi, o.idesc, acc);
+          mma_issue<kFp8>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi_b, o.idesc, acc);
         }
       }
     }
@@ -553,7 +560,7 @@ __device__ __forceinline__ void issue_stage3(const StageOps &o, bool u_stage, in
 #pragma unroll
         for (int j = 0; j < kMPS; ++j) {
           const uint32_t acc = (o.first && ky == 0 && kx == 0 && j == 0) ? 0u : 1u;
-          mma_issue<false>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi, o.idesc, acc);
+          mma_issue<false>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi_b, o.idesc, acc);
         }
       }
     }
@@ -567,9 +574,32 @@ __device__ __forceinline__ void issue_stage3(const StageOps &o, bool u_stage, in
         const uint32_t b_tap = o.blo + (uint32_t)(o.sub * 4 + i * 2 + jx) * o.tap_b16;
 #pragma unroll
         for (int j = 0; j < kMPS; ++j)
-          mma_issue<false>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi, o.idesc, 1u);
+          mma_issue<false>(d, a_tap + 2u * j, o.desc_hi, b_tap + 2u * j, o.desc_hi_b, o.idesc, 1u);
       }
     }
+  }
+}
+
+// Mode 4 (a stride-2 3x3 layer over 32 BF16 channels): the input is read as
+// pixel pairs, one 128-byte row (pixels 2x and 2x + 1) per output column x.
+// Stage 2 ky holds the pairs at x - 1, whose second pixel 2x - 1 is tap
+// (ky, 0) (K steps 2-3 of the row); stage 2 ky + 1 holds the pairs at x: taps
+// (ky, 1) and (ky, 2) are the first and the second 64 bytes of each row (K
+// steps 0-1 and 2-3 against the two taps' weight blocks).  The MMAs follow
+// mode 0's K order (tap, K step), so the accumulators are the same.
+__device__ __forceinline__ void issue_stage4(const StageOps &o, bool prev_pair) {
+  const uint32_t d = o.d + (uint32_t)o.sub * o.BN;
+  const uint32_t a0 = o.alo + (uint32_t)o.sub * o.sub_step;
+  if (prev_pair) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      mma_issue<false>(d, a0 + 2u * (2 + j), o.desc_hi, o.blo + 2u * j, o.desc_hi_b, o.idesc,
+                       (o.first && j == 0) ? 0u : 1u);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      mma_issue<false>(d, a0 + 2u * j, o.desc_hi, o.blo + (uint32_t)(j >> 1) * o.tap_b16 + 2u * (j & 1), o.desc_hi_b,
+                       o.idesc, 1u);
   }
 }
 
@@ -679,7 +709,9 @@ __global__ void __launch_bounds__(kThreads, 2)
           const long long c0 = clock64();
           got = mbar_wait(&empty[stage], phase ^ 1u, abort_flag) ? 1 : 0;
           prod_wait += clock64() - c0;
-          if (got) mbar_expect_tx(&full[stage], (a.halo == 3 && ki >= a.kS) ? a.tx_u : a.tx_bytes);
+          if (got)
+            mbar_expect_tx(&full[stage], ((a.halo == 3 && ki >= a.kS) || (a.halo == 4 && !(ki & 1))) ? a.tx_u
+                                                                                                   : a.tx_bytes);
         }
         got = __shfl_sync(0xFFFFFFFFu, got, 0);
         if (!got) {
@@ -693,7 +725,11 @@ __global__ void __launch_bounds__(kThreads, 2)
           // the 9 taps of skip chunk ki, or the 2x2 taps of the tile's phases
           // for U chunk ki - kS (16 blocks per U chunk, 4 per phase).
           int b0 = ki, nb = 1;
-          if (a.halo == 3 && ki >= a.kS) {
+          if (a.halo == 4) {
+            // Row ky's tap 0 (pairs at x - 1) or taps 1-2 (pairs at x).
+            b0 = 3 * (ki >> 1) + ((ki & 1) ? 1 : 0);
+            nb = (ki & 1) ? 2 : 1;
+          } else if (a.halo == 3 && ki >= a.kS) {
             b0 = 9 * a.kS + (ki - a.kS) * 16 + g * 4 * a.npt;
             nb = 4 * a.npt;
           } else if (a.halo) {
@@ -703,7 +739,14 @@ __global__ void __launch_bounds__(kThreads, 2)
           bulk_load(sB + (size_t)stage * a.bytes_b, img + (size_t)b0 * a.btap, (uint32_t)nb * a.btap, &full[stage]);
         }
         if (lane < ntma) {
-          if (a.halo == 3) {
+          if (a.halo == 4) {
+            const int ky = ki >> 1, prev = (ki & 1) ^ 1;
+            if (lane == 0)
+              tma_load_4d(&mapA, &full[stage], sA + (size_t)stage * a.bytes_a, 0, x0 - prev, 2 * y0 + ky - 1, l0);
+            else if (lane <= 2 - prev && !img)
+              tma_load_2d(mapB, &full[stage], sB + (size_t)stage * a.bytes_b + (size_t)(lane - 1) * a.btap,
+                          (3 * ky + (prev ? 0 : 1) + lane - 1) * a.Cin, 0);
+          } else if (a.halo == 3) {
             uint8_t *dA = sA + (size_t)stage * a.bytes_a, *dB = sB + (size_t)stage * a.bytes_b;
             if (ki < a.kS) {
               // Lane b loads parity sub-grid b (rows 2r + b / 2, columns
@@ -788,12 +831,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       // Descriptor words (see smem_desc): low = start address >> 4 | LBO,
       // high = SBO >> 4 | version | swizzle mode.
       const uint32_t desc_hi = ((a.sbo >> 4) & 0x3FFFu) | (1u << 14) | ((uint32_t)(a.swz & 7) << 29);
+      const uint32_t desc_hi_b = ((a.sbo_b >> 4) & 0x3FFFu) | (1u << 14) | ((uint32_t)(a.swz_b & 7) << 29);
       const uint32_t a_lo0 = ((a_base & 0x3FFFFu) >> 4) | (1u << 16), b_lo0 = ((b_base & 0x3FFFFu) >> 4) | (1u << 16);
       const uint32_t row16 = a.sbo / 8 / 16;                 // one operand row, in 16-byte units
       const uint32_t sub_step = (uint32_t)kBM * row16;       // next 128-row subtile
       const uint32_t row_step = (uint32_t)a.Wt * row16;      // halo mode: next tap row
       const uint32_t ver16 = a.bytes_ver >> 4;               // halo mode: next x-shifted copy
-      const uint32_t tap_b16 = (a.halo == 3 ? a.btap : a.bytes_b / 9) >> 4;  // next tap's weights
+      const uint32_t tap_b16 = (a.halo >= 3 ? a.btap : a.bytes_b / 9) >> 4;  // next tap's weights
       long long mma_wait_acc = 0, mma_wait_full = 0;
       const long long mma_t0 = clock64();
       for (int t = blockIdx.x; t < a.num_tiles && !*abort_flag; t += gridDim.x, ++i) {
@@ -833,10 +877,12 @@ __global__ void __launch_bounds__(kThreads, 2)
           const bool first = ki == 0;
           const StageOps so{d,         (uint32_t)a.BN, alo_s,        blo_s,   a_base + (uint32_t)stage * a.bytes_a,
                             off0,      a.P,            (uint32_t)a.chunk_bytes, sub_step, row_step, ver16, tap_b16,
-                            desc_hi,   a.idesc,        first,   lane,                   a.box_a};
+                            desc_hi,   a.idesc,        first,   desc_hi_b,              lane,     a.box_a};
           // The MMA kind follows the operands (a.mma_kind), which may differ
           // from the output type (a layer at a BF16/E4M3 boundary).
-          if (a.halo == 3) {
+          if (a.halo == 4) {
+            issue_stage4(so, (ki & 1) == 0);
+          } else if (a.halo == 3) {
             const bool u_stage = ki >= a.kS;
             if (a.mma_per_stage == 1)
               issue_stage3<1>(so, u_stage, py, px);
@@ -1476,9 +1522,29 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
     a.tx_bytes = 4u * box + 9u * a.btap;
     a.tx_u = box + 4u * (uint32_t)a.npt * a.btap;
   }
+  if (a.halo == 4) {
+    // Stride-2 3x3 layer over 32 dense BF16 channels, read as pixel pairs
+    // (issue_stage4): six stages per tile -- kernel row ky, pairs at x - 1
+    // then pairs at x -- each one box of TP rows of 128 bytes plus the weight
+    // blocks of one tap or two.
+    if (L.k != 3 || L.stride != 2 || es != 2 || cb != 64 || L.Cin != 32 || L.in_cs != 32 || L.in_co != 0 ||
+        (L.Win & 1) || (L.Hin & 1) || L.pscale || L.res || L.in_u || 2 * a.Ht > 256)
+      return PG_ERR_UNSUPPORTED;
+    a.kiters = 6;
+    a.bytes_a = (uint32_t)TP * 128u;
+    a.bytes_b = 2u * (uint32_t)(L.Cout * cb);
+    a.tx_bytes = a.bytes_a + a.bytes_b;
+    a.tx_u = a.bytes_a + (uint32_t)(L.Cout * cb);
+  }
   a.btap = (uint32_t)(L.Cout * cb);
   a.sbo = 8u * (uint32_t)cb;
   a.swz = cb == 128 ? 2 : (cb == 64 ? 4 : 6);
+  a.sbo_b = a.sbo;
+  a.swz_b = a.swz;
+  if (a.halo == 4) {  // A rows of 128 bytes (128-byte swizzle); B keeps the taps' 64-byte rows
+    a.sbo = 8u * 128u;
+    a.swz = 2;
+  }
   a.mma_per_stage = cb / 32;
   a.mma_kind = es == 1 ? 1 : 0;
   // Instruction descriptor: D = F32, A/B = BF16 (kind::f16) or E4M3
@@ -1585,8 +1651,23 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
       box[3] = 1;
       estr[1] = estr[2] = 2;
     }
+    CUtensorMapSwizzle swA = sw;
+    if (a.halo == 4) {
+      // Pixel pairs: 64 channels (two pixels of 32) per 128-byte row, every
+      // second image row; the leaf and pair index carry the zero padding.
+      dims[0] = 64;
+      dims[1] = (cuuint64_t)(L.Win / 2);
+      strides[0] = 128;
+      box[0] = 64;
+      box[1] = (cuuint32_t)a.Wt;
+      box[2] = (cuuint32_t)(2 * a.Ht);
+      box[3] = (cuuint32_t)a.Lt;
+      estr[1] = 1;
+      estr[2] = 2;
+      swA = CU_TENSOR_MAP_SWIZZLE_128B;
+    }
     void *base = (uint8_t *)L.in + (size_t)L.in_co * es;
-    if (enc(&mA, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+    if (enc(&mA, dt, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swA,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return PG_ERR_UNSUPPORTED;
   }
@@ -1620,7 +1701,7 @@ pg_status launch_tc(const LpLayer &L, uint32_t ns, int es, bool fp8_out, cudaStr
   // Weight images: one bulk copy per stage instead of one tensor load per
   // weight block (all experts or none).
   {
-    const int order = a.halo == 3 ? 2 : (a.halo ? 1 : 0);
+    const int order = a.halo == 3 ? 2 : ((a.halo == 1 || a.halo == 2) ? 1 : 0);
     const int K = a.halo == 3 ? 9 * L.Cin + 16 * L.CinU : L.k * L.k * L.Cin;
     const int nblk = a.halo == 3 ? 9 * a.kS + 16 * a.kU : (a.halo ? 9 * a.cchunks : L.k * L.k * a.cchunks);
     bool all = !getenv("PG_TC_NO_IMAGE");
@@ -1803,7 +1884,7 @@ pg_status tune_layer(const LpLayer &L, uint32_t ns, int es, bool fp8, cudaStream
   *best = TcCfg();
   // The phase form (operand mode 3) is the only mode of its layers, with
   // one to four output phases per tile.
-  const std::vector<int> halos = L.in_u ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
+  const std::vector<int> halos = L.in_u ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4};
   for (int so : {0, 1, 2})
   for (int halo : halos)
   for (int cb : {128, 64, 32})

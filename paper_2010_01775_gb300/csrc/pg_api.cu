@@ -526,7 +526,7 @@ pg_status pg_net_set_tuning(pg_net *netp, const int32_t *in, size_t n) {
   if (!net || !in || n != (size_t)net->n_layers * 3 * 7) return PG_ERR_INVALID_ARG;
   for (size_t i = 0; i < n; i += 7)
     if (in[i] < 0 || in[i] > 4 || in[i + 1] < 0 || in[i + 1] > 24 || in[i + 2] < 0 || in[i + 2] > 4 ||
-        in[i + 3] < 0 || in[i + 3] > 3 || (in[i + 4] != 0 && in[i + 4] != 32 && in[i + 4] != 64 && in[i + 4] != 128) ||
+        in[i + 3] < 0 || in[i + 3] > 4 || (in[i + 4] != 0 && in[i + 4] != 32 && in[i + 4] != 64 && in[i + 4] != 128) ||
         in[i + 5] < 0 || in[i + 6] < 0 || in[i + 6] > 2)
       return PG_ERR_INVALID_ARG;
   for (int l = 0; l < net->n_layers; ++l)

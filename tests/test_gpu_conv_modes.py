@@ -3,7 +3,10 @@
 Modes 1 (three x-shifted haloed boxes) and 2 (one box of zero-padded rows,
 outputs in the padded row space, every tap a descriptor starting at another
 row of the same box) issue the same MMAs in the same K order (channel chunk,
-tap, K step) for every output pixel.  With the 3-layer net, whose one 3x3
+tap, K step) for every output pixel.  Mode 4 reads a stride-2 layer's input
+as pixel pairs (kernel row by kernel row: tap 0 from the second pixel of the
+pairs at x - 1, taps 1 and 2 from the pairs at x) and issues mode 0's MMAs
+in mode 0's order.  With the 3-layer net, whose one 3x3
 layer is eligible for both, the maps must be bit-identical.  In the U-Net
 the modes' eligibility differs per layer, and a layer that falls back to
 mode 0 sums its taps in another order, so there the maps agree to the
@@ -67,6 +70,11 @@ def test_unet_modes_agree(setup, size, prec):
     y2 = _maps(ctx, net, h, prec, 2)
     for y in (y1, y2):
         assert np.abs(y - y0).sum() / np.abs(y0).sum() < 1e-3
+    # Mode 4 (pixel pairs) serves the stride-2 layer over 32 BF16 channels
+    # (the other layers run mode 0); it issues mode 0's MMAs in mode 0's K
+    # order, so the maps are the same bit for bit.
+    y4 = _maps(ctx, net, h, prec, 4)
+    assert np.array_equal(y4, y0)
 
 
 def test_staged_and_direct_output_stores_agree(setup):
