@@ -1337,9 +1337,7 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
                                                                  lv.axis, ctx->d_status), PG_COUNT(ctx);
     PG_TRY(scan_emit(ctx, lv.N, FlagVal{lv.flag}, RankEmit{lv.rank, lv.list}, partial, count));
     uint32_t S = 0, status = 0;
-    PG_CUDA(cudaMemcpyAsync(&S, count, 4, cudaMemcpyDeviceToHost, st));
-    PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
-    PG_CUDA(cudaStreamSynchronize(st));
+    PG_TRY(read_words(ctx, st, count, &S, ctx->d_status, &status));
     if (status & ST_INVALID_INPUT) {
       PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
       PG_CUDA(cudaStreamSynchronize(st));
@@ -1365,8 +1363,7 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
   }
   PG_TRY(scan_emit(ctx, C, FlagVal{levels[0].nleaf}, OffEmit{levels[0].off}, partial, count));
   uint32_t L = 0;
-  PG_CUDA(cudaMemcpyAsync(&L, count, 4, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaStreamSynchronize(st));
+  PG_TRY(read_words(ctx, st, count, &L));
 
   // The handle block.
   const size_t b_codes = align256(8ull * n), b_n4 = align256(4ull * n), b_l8 = align256(8ull * L),
@@ -1423,8 +1420,7 @@ pg_status build_grid_kd(pg_ctx *ctx, const pg_photon *d_ph, const float *d_nrm, 
   PG_CUDA(cudaMemcpyAsync(g->scene_geom, hg, 24, cudaMemcpyHostToDevice, st));
   PG_CUDA(cudaGetLastError());
   uint32_t A = 0;
-  PG_CUDA(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaStreamSynchronize(st));
+  PG_TRY(read_words(ctx, st, count, &A));
   g->A = A;
   return PG_OK;
 }
@@ -1530,9 +1526,7 @@ pg_status bin_into_grid(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, uint6
   }
   PG_CUDA(cudaGetLastError());
   uint32_t A = 0, status = 0;
-  PG_CUDA(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaStreamSynchronize(st));
+  PG_TRY(read_words(ctx, st, count, &A, ctx->d_status, &status));
   if (status & ST_INVALID_INPUT) {
     PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
     PG_CUDA(cudaStreamSynchronize(st));
@@ -1647,9 +1641,7 @@ pg_status bin_into_grid_kd(pg_ctx *ctx, const Grid *g, const pg_photon *d_ph, ui
   }
   PG_CUDA(cudaGetLastError());
   uint32_t A = 0, status = 0;
-  PG_CUDA(cudaMemcpyAsync(&A, count, 4, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaMemcpyAsync(&status, ctx->d_status, 4, cudaMemcpyDeviceToHost, st));
-  PG_CUDA(cudaStreamSynchronize(st));
+  PG_TRY(read_words(ctx, st, count, &A, ctx->d_status, &status));
   if (status & ST_INVALID_INPUT) {
     PG_CUDA(cudaMemsetAsync(ctx->d_status, 0, 4, st));
     PG_CUDA(cudaStreamSynchronize(st));

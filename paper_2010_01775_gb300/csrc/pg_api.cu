@@ -185,6 +185,27 @@ void ctx_free(pg_ctx *ctx, void *ptr, size_t bytes) {
 
 // Boundary rays of the W phi sectors: (float cos, float sin) of 2 pi j / W,
 // exactly (1,0), (0,1), (-1,0), (0,-1) on the quarter turns.
+namespace {
+__global__ void k_read_words(const uint32_t *a, const uint32_t *b, uint32_t *out) {
+  if (threadIdx.x == 0) {
+    volatile uint32_t *o = out;
+    o[0] = *a;
+    if (b) o[1] = *b;
+    __threadfence_system();
+  }
+}
+}  // namespace
+
+pg_status read_words(pg_ctx *ctx, cudaStream_t st, const uint32_t *a, uint32_t *ha, const uint32_t *b,
+                     uint32_t *hb) {
+  k_read_words<<<1, 32, 0, st>>>(a, b, ctx->d_words + 8), PG_COUNT(ctx);
+  PG_CUDA(cudaGetLastError());
+  PG_CUDA(cudaStreamSynchronize(st));
+  *ha = ctx->h_words[8];
+  if (b) *hb = ctx->h_words[9];
+  return PG_OK;
+}
+
 pg_status phi_table(pg_ctx *ctx, int W, const float **d_table) {
   int lg = 0;
   while ((1 << lg) < W) ++lg;
@@ -493,9 +514,8 @@ pg_status pg_set_stream(pg_ctx *c, void *stream) {
 pg_status pg_sync(pg_ctx *c) {
   if (!c) return PG_ERR_INVALID_ARG;
   uint32_t st = 0;
-  PG_CUDA(cudaMemcpyAsync(&st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  PG_TRY(read_words(c, c->stream, c->d_status, &st));
   PG_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(uint32_t), c->stream));
-  PG_CUDA(cudaStreamSynchronize(c->stream));
   ctx_reap_frees(c, false);  // every free enqueued so far has run
   if (st & ST_INVALID_INPUT) return PG_ERR_INVALID_INPUT;
   if (st & ST_OVERFLOW) return PG_ERR_OVERFLOW;

@@ -265,6 +265,12 @@ void budget_release(pg_budget *b, size_t bytes);
 // Device tables (cos, sin) of the W boundary rays, built once per W on the
 // host of the calling process and cached on the context.
 pg_status phi_table(pg_ctx *ctx, int W, const float **d_table);
+// Reads one or two device words (b / hb may be null) once stream `st` has run
+// all work before: a one-thread kernel puts them in the context's mapped host
+// words, then the stream synchronises.  No copy-engine transfer is involved,
+// so the read does not wait behind the caller's large copies.
+pg_status read_words(pg_ctx *ctx, cudaStream_t st, const uint32_t *a, uint32_t *ha, const uint32_t *b = nullptr,
+                     uint32_t *hb = nullptr);
 
 // ---------------------------------------------------------------- device rules
 // Voxel quantisation (Algorithm 1, voxel location): q = clamp(floor(fl32(

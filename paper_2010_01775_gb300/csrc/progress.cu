@@ -137,15 +137,9 @@ pg_status assign_slots(pg_ctx *ctx, uint32_t nA, const uint32_t *d_leaves, Grid 
   PG_TRY(ctx_alloc(ctx, 256, &d_count));
   k_assign_slots<<<1, 1024, 0, ctx->stream>>>(nA, d_leaves, g->slot_of_leaf, g->active, g->A, (uint32_t *)d_count),
       PG_COUNT(ctx);
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(new_slots, d_count, 4, cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  const pg_status s = read_words(ctx, ctx->stream, (const uint32_t *)d_count, new_slots);
   ctx_free(ctx, d_count, 256);
-  if (e != cudaSuccess) {
-    last_cuda_error() = e;
-    return PG_ERR_CUDA;
-  }
-  return PG_OK;
+  return s;
 }
 
 pg_status slots_of(pg_ctx *ctx, uint32_t nA, const uint32_t *d_leaves, const Grid *g, uint32_t *d_out) {
