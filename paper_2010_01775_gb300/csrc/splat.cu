@@ -135,20 +135,8 @@ __global__ void __launch_bounds__(kSplatThreads) k_splat(
       prev = p - prev_base < prev_lim;
       if (kMode == 2 && !prev) bin = -1;
     }
-    // Combine photons of this warp that share a bin.  The peer group comes
-    // from one ballot per bit of the bin (the lanes that share the bit,
-    // ANDed), cheaper than a warp match on this GPU.
-    unsigned peers = 0xFFFFFFFFu;
-    {
-      const int nbits = __ffs(HW);  // log2(HW) + 1: bin -1 differs from every bin in bit log2(HW)
-#pragma unroll
-      for (int bb = 0; bb < 15; ++bb)
-        if (bb < nbits) {
-          const bool bit = ((uint32_t)bin >> bb) & 1u;
-          const unsigned v = __ballot_sync(0xFFFFFFFFu, bit);
-          peers &= bit ? v : ~v;
-        }
-    }
+    // Combine photons of this warp that share a bin.
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
     int leader = __ffs(peers) - 1;
     unsigned long long gsum = pfx;
     uint32_t gcnt = 1, gsum_p_cnt = prev ? 1u : 0u;
