@@ -603,13 +603,17 @@ __global__ void __launch_bounds__(256) k_tree_all(TreeAll p) {
 }
 
 // ---------------------------------------------------------------- a4
+// Leaf of every photon: the last leaf whose start code is at most the
+// photon's, searched only among the leaves of its coarse cell (the table
+// k_leaf_lut writes).
 __global__ void k_leaf_assign(const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ perm, uint32_t n,
                               const uint64_t *__restrict__ leaf_code, const uint32_t *__restrict__ counters,
+                              const uint32_t *__restrict__ lut, uint32_t ncell, int shift,
                               uint32_t *__restrict__ leaf_of) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t L = counters[0];
-  leaf_of[perm[i]] = find_leaf(leaf_code, L, sorted[i]);
+  leaf_of[perm[i]] = find_leaf_lut(leaf_code, L, lut, ncell, shift, sorted[i]);
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -832,10 +836,12 @@ pg_status build_grid(pg_ctx *ctx, const pg_photon *d_ph, uint64_t n64, const pg_
                                                              g->leaf_end), PG_COUNT(ctx);
   }
   k_active<<<1, 1024, 0, st>>>(t, g->leaf_begin, g->leaf_end, g->active, g->slot_of_leaf), PG_COUNT(ctx);
-  // a4: leaf of every photon.
-  if (n) k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->leaf_of), PG_COUNT(ctx);
   k_leaf_lut<<<ceil_div(lut_cells, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * (D - g->lut_depth), lut_cells,
                                                       g->lut), PG_COUNT(ctx);
+  // a4: leaf of every photon.
+  if (n)
+    k_leaf_assign<<<ceil_div(n, TB), TB, 0, st>>>(sorted, g->perm, n, g->leaf_code, t.counters, g->lut, lut_cells,
+                                                   3 * (D - g->lut_depth), g->leaf_of), PG_COUNT(ctx);
   k_scene_leaves<<<ceil_div(S + 1, TB), TB, 0, st>>>(g->leaf_code, t.counters, 3 * Dsp, S,
                                                      S == (1u << (3 * SL)), g->scene_leaf_begin), PG_COUNT(ctx);
   PG_CUDA(cudaGetLastError());
